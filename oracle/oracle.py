@@ -71,7 +71,9 @@ def _bp(a):
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        # TMD_ORACLE_LIB lets the mutation tests load a deliberately broken build
+        override = os.environ.get("TMD_ORACLE_LIB")
+        _lib = C.CDLL(override if override else build())
         L = _lib
         L.tmdo_neighbors_of.restype = C.c_int64
         L.tmdo_neighbors.restype = C.c_int64

@@ -1,0 +1,41 @@
+"""The pins catch plausible mistakes: each case plants one bug in a private
+copy of the oracle's C source (on the CPU), builds it, and checks that the pin
+suite then fails.  The committed oracle is never modified."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "tmd_oracle.c")
+
+MUTANTS = {
+    "tdm_xy_multiplicity": ("{0, 0, 1, 0}, {0, 0, 2, 0}, {0, 0, 2, 0}", "{0, 0, 1, 0}, {0, 0, 1, 0}, {0, 0, 2, 0}"),
+    "sigma_no_sqrt": ("(mm == 0) ? sqrt(s) : s", "s"),
+    "cutoff_derivative_sign": ("dfc = -0.5 * (M_PI / rc)", "dfc = 0.5 * (M_PI / rc)"),
+    "scatter_sign": ("forces[3 * (size_t)j + x] -= g[3 * c + x]", "forces[3 * (size_t)j + x] += g[3 * c + x]"),
+    "projection_dropped": ("(dEdu[x] - u[x] * udotg) / R", "dEdu[x] / R"),
+    "virial_sign": ("W[al * 3 + be] -= Dv[al]", "W[al * 3 + be] += Dv[al]"),
+    "self_pair_kept": ("if (j == i && sx == 0 && sy == 0 && sz == 0) continue;", ""),
+    "min_image_floor": ("-(int)rint((pos[3 * j + x]", "-(int)floor((pos[3 * j + x]"),
+    "act_derivative_wrong_layer": ("g[c] = gn[c] * act_df(m, z[l - 1][c])", "g[c] = gn[c] * act_df(m, z[l][c])"),
+    "rank3_moment_transposed": ("{1, 2, 0}, {1, 1, 1}, {1, 0, 2}", "{1, 1, 1}, {1, 2, 0}, {1, 0, 2}"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_planted_bug(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                    "-D_GNU_SOURCE", "-o", str(so), str(mut), "-lm"], check=True)
+    env = dict(os.environ, TMD_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted bug {name} survived the pins"
