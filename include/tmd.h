@@ -1,0 +1,256 @@
+/*
+ * tmd.h - C ABI of the GB300 (sm_103a) TensorMD energy / force / virial path.
+ *
+ * Method: TensorMD (arXiv 2310.08439), Sec. "The Tensor Formalism".  For every
+ * atom a the library gathers the neighbours inside the cutoff, evaluates the
+ * radial tensor H_abck = f_k(R) f_c(R), the moment tensor M_abcd (ranks 0..3,
+ * Eq. T_dm), contracts P_abkd = sum_c H_abck M_abcd, forms the descriptor
+ * G_abkm = sigma(T_dm P_abkd^2) (Eqs. tensor_formalism, sigma_function), runs
+ * the per-species atomic-energy network E_a = NNP(G_a), and back-propagates
+ * dE/dG through Eqs. dP_abkd, U_abck, F1_abcx, F2_abcx and the ScatterSum into
+ * forces and the virial.  The neighbour table is built by cell binning with a
+ * skin buffer (Sec. "Evaluation", binning with a 1 A buffer), and tmd_step
+ * integrates with velocity-Verlet (1 fs steps in the paper).
+ *
+ * Conventions shared by every entry point
+ *  - Units: A, eV, amu, fs.  Forces eV/A, virial eV, pressure eV/A^3.
+ *  - Boxes are orthorhombic, box[3] = (Lx, Ly, Lz) > 0; pbc[x] != 0 marks a
+ *    periodic axis.  Positions must lie in [0, L) on every axis (wrapped on
+ *    periodic axes, inside the box on open ones).
+ *  - Neighbour pairs: D_ij = x_j + s*L - x_i for an image shift s in Z^3;
+ *    g_ij = dE/dD_ij; F_i += g_ij, F_j -= g_ij; W_ab = -sum_pairs D^a g^b.
+ *  - "dev" pointers are CUDA device pointers on the current device; "host"
+ *    pointers are ordinary host memory.  The caller owns every array it
+ *    passes; the library owns its opaque handles and their workspaces.
+ *  - Work is enqueued on the caller's stream and is asynchronous unless the
+ *    description says the call synchronises.  A NULL stream is the legacy
+ *    default stream.
+ *  - Every call returns a tmd_status.  On error nothing is written to the
+ *    caller's outputs beyond what is stated, and tmd_last_error() returns a
+ *    human-readable reason (thread-local, valid until the next call).
+ *  - Arguments are validated on the host before any launch.  Conditions only
+ *    the device can see (an atom outside the box, a neighbour count above the
+ *    list capacity) are recorded in a device status word and returned by the
+ *    next call that synchronises (tmd_neighbors, tmd_nlist_*, tmd_step).
+ */
+#ifndef TMD_H
+#define TMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tmd_stream_t; /* same handle as cudaStream_t */
+
+typedef enum {
+    TMD_OK = 0,
+    TMD_ERR_INVALID_ARG = 1,   /* a host-side argument check failed            */
+    TMD_ERR_CAPACITY = 2,      /* a size limit of the library was exceeded      */
+    TMD_ERR_CUDA = 3,          /* a CUDA runtime call failed                    */
+    TMD_ERR_OOM = 4,           /* device allocation failed                      */
+    TMD_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                 */
+    TMD_ERR_UNIMPLEMENTED = 6  /* a configuration this build does not support   */
+} tmd_status;
+
+enum { TMD_ACT_TANH = 0, TMD_ACT_SQUAREPLUS = 1 };
+enum { TMD_PREC_FP32 = 0, TMD_PREC_BF16 = 1 };
+
+/* Limits of this build. */
+#define TMD_MAX_SPECIES 4
+#define TMD_MAX_HIDDEN 4
+#define TMD_MAX_WIDTH 256
+#define TMD_MAX_DEGREE 1024 /* neighbour entries per atom inside r_list */
+
+/* Name of a status code (static string). */
+const char *tmd_status_string(int status);
+/* Detail of the last error raised on this thread ("" if none). */
+const char *tmd_last_error(void);
+/* Library version string. */
+const char *tmd_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Potential model                                                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * Description of a TensorMD potential (all pointers host, read at create).
+ *  n_species  S, 1..TMD_MAX_SPECIES.  Species ids are 0..S-1.
+ *  n_radial   K radial channels; this build supports K in {8, 16, 32}.
+ *  rc         cutoff radius (A); pairs with R >= rc contribute nothing.
+ *  mu, eta    [S][S][K] Gaussian centre and width of f_k(R) = exp(-eta (R-mu)^2)
+ *             for (centre species, neighbour species, k).  f_c(R) =
+ *             (cos(pi R / rc) + 1) / 2.  (H_abck definition; the paper leaves
+ *             f_k open and names Gaussians as one choice.)
+ *  n_hidden   L hidden layers, 1..TMD_MAX_HIDDEN; widths[L] each a multiple of
+ *             4 and <= TMD_MAX_WIDTH.  Input width Dd = S*K*4, output 1.
+ *  weights    [S] pointers; weights[s] holds, for l = 0..L, W_l [out][in]
+ *             row-major then b_l [out] (FP64).  Descriptor column
+ *             c = ((b*K) + k)*4 + m, b = neighbour species.
+ *  activation TMD_ACT_TANH or TMD_ACT_SQUAREPLUS (b = squareplus_b); the
+ *             output layer is linear.
+ *  precision  TMD_PREC_FP32: every layer in FP32.  TMD_PREC_BF16: network
+ *             layers on BF16 tensor cores with FP32 accumulation; radial
+ *             basis, moments and contractions stay FP32 in both modes.
+ */
+typedef struct {
+    int32_t n_species;
+    int32_t n_radial;
+    double rc;
+    const double *mu;
+    const double *eta;
+    int32_t n_hidden;
+    const int32_t *widths;
+    const double *const *weights;
+    int32_t activation;
+    double squareplus_b;
+    int32_t precision;
+} tmd_model_desc;
+
+typedef struct tmd_model tmd_model;   /* opaque; device copy of the weights */
+typedef struct tmd_nlist tmd_nlist;   /* opaque; device neighbour table + workspace */
+typedef struct tmd_system tmd_system; /* opaque; resident MD state */
+
+/* Copy a model to the current device.  Errors: INVALID_ARG (bad sizes or a
+ * non-finite weight), UNIMPLEMENTED (K outside {8,16,32}), OOM, CUDA.
+ * Synchronises the device once. */
+tmd_status tmd_model_create(const tmd_model_desc *desc, tmd_model **out);
+tmd_status tmd_model_destroy(tmd_model *model);
+/* Switch the network precision of an existing model (TMD_PREC_*). */
+tmd_status tmd_model_set_precision(tmd_model *model, int32_t precision);
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour table (R_abc of Sec. "The Tensor Formalism"; cell binning with */
+/* a skin buffer, Sec. "Evaluation")                                        */
+/* ------------------------------------------------------------------------ */
+tmd_status tmd_nlist_create(tmd_nlist **out);
+tmd_status tmd_nlist_destroy(tmd_nlist *nl);
+
+/*
+ * Build the neighbour table of n atoms: every (j, s) with
+ * |x_j + s*L - x_i|^2 < r_list^2 and (j, s) != (i, 0), including periodic
+ * self-images when a box side is shorter than 2*r_list.  The distance test
+ * is decided in FP64 with the expression ((x_j + s*L) - x_i) per axis and
+ * (dx*dx + dy*dy) + dz*dz, without fused multiply-add.  Entries of atom i
+ * are ordered by (species of j, j, sx, sy, sz).
+ *  pos    dev [n][3] FP64, in [0, L) per axis.
+ *  types  dev [n] int32 species ids (< TMD_MAX_SPECIES).
+ *  box    host [3]; pbc host [3].
+ *  r_list list radius (cutoff + skin), > 0.
+ * Allocates or grows nl's device arrays and synchronises the stream once (to
+ * size the table).  Errors: INVALID_ARG (bad host argument, or an atom found
+ * outside the box / an invalid species on the device), CAPACITY (an atom has
+ * more than TMD_MAX_DEGREE entries or a shift beyond +-15 boxes), OOM, CUDA.
+ */
+tmd_status tmd_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
+                         const int32_t pbc[3], double r_list, tmd_nlist *nl, tmd_stream_t stream);
+
+/* Atom count and entry count of the last successful build (host outputs). */
+tmd_status tmd_nlist_size(const tmd_nlist *nl, int64_t *n_atoms, int64_t *n_entries);
+
+/*
+ * Copy the table to host arrays: off [n+1] int64 CSR offsets, nbr [nnz]
+ * int32 neighbour ids, shift [nnz][3] int8 image shifts.  Any pointer may be
+ * NULL to skip it.  Synchronises the device.
+ */
+tmd_status tmd_nlist_export(const tmd_nlist *nl, int64_t *off, int32_t *nbr, int8_t *shift);
+
+/* ------------------------------------------------------------------------ */
+/* Energy, forces, virial                                                   */
+/* ------------------------------------------------------------------------ */
+/*
+ * E = sum_a E_a, E_a = NNP(G_a), F_ax = -dE/dx_ax, virial W (Sec. "The
+ * Tensor Formalism": E_a, E, F_ax equations and the backward chain
+ * Eqs. dP_abkd .. F2_abcx with ScatterSum).
+ *  nl      a table built from the same positions' atoms and types with
+ *          r_list >= model rc (a skin is allowed; entries beyond rc are
+ *          skipped).  Its workspace is used and resized here.
+ *  pos     dev [n][3] FP64; types dev [n] int32 (the ones given to
+ *          tmd_neighbors); box host [3].
+ *  energy  dev [1] FP64, sum of E_a accumulated in FP64.
+ *  e_atom  dev [n] FP32 per-atom energies.
+ *  forces  dev [n][3] FP32.
+ *  virial  dev [9] FP64, row-major W_ab.
+ * Any output may be NULL to skip it.  Asynchronous.  Errors: INVALID_ARG
+ * (n differs from the table, r_list < rc), OOM, CUDA.
+ */
+tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                       int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
+                       double *virial, tmd_stream_t stream);
+
+/*
+ * One force evaluation from host buffers: copies pos [n][3] FP64 and types
+ * [n] int32 from host memory (pinned memory gives asynchronous copies),
+ * builds the table with r_list = rc, runs tmd_compute, and copies energy
+ * (FP64 scalar), forces [n][3] FP32 and virial [9] FP64 back to host memory
+ * (any output may be NULL).  Synchronises the stream before returning.
+ */
+tmd_status tmd_evaluate_host(const tmd_model *model, tmd_nlist *nl, const double *pos_host,
+                             const int32_t *types_host, int64_t n, const double box[3],
+                             const int32_t pbc[3], double *energy_host, float *forces_host,
+                             double *virial_host, tmd_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Molecular dynamics (velocity-Verlet, NVE)                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double e_pot;       /* potential energy, eV                        */
+    double e_kin;       /* kinetic energy, eV                          */
+    double temperature; /* K, from e_kin with 3n-3 degrees of freedom  */
+    double virial[9];   /* eV                                          */
+    double pressure[9]; /* (sum m v v + W) / V, eV/A^3                 */
+    int64_t step;       /* steps taken since set_state                 */
+    int64_t rebuilds;   /* neighbour rebuilds since set_state          */
+} tmd_thermo;
+
+/* Resident state of one system: n atoms in an orthorhombic box; the list
+ * radius is rc + skin.  Allocates device memory.  Errors: INVALID_ARG, OOM. */
+tmd_status tmd_system_create(int64_t n, const double box[3], const int32_t pbc[3], double skin,
+                             tmd_system **out);
+tmd_status tmd_system_destroy(tmd_system *sys);
+
+/*
+ * Load positions [n][3] FP64 (A), velocities [n][3] FP64 (A/fs), types [n]
+ * int32 and per-atom masses [n] FP64 (amu).  on_device != 0 means the
+ * pointers are device pointers, else host.  vel and masses may be NULL
+ * (zero velocities / unchanged masses).  Resets the step counter and forces a
+ * neighbour rebuild.  Asynchronous on the stream.
+ */
+tmd_status tmd_system_set_state(tmd_system *sys, const double *pos, const double *vel,
+                                const int32_t *types, const double *masses, int32_t on_device,
+                                tmd_stream_t stream);
+/* Copy positions / velocities [n][3] FP64 and forces [n][3] FP32 out (NULL
+ * skips); on_device as above.  Synchronises the stream. */
+tmd_status tmd_system_get_state(const tmd_system *sys, double *pos, double *vel, float *forces,
+                                int32_t on_device, tmd_stream_t stream);
+
+/*
+ * Advance nsteps velocity-Verlet steps of dt_fs femtoseconds:
+ *   v += dt/2 F/m; x += dt v; wrap periodic axes; rebuild the table when
+ *   rebuild_every > 0 and the step count is a multiple of it, or when any atom
+ *   moved more than skin/2 since the last build; F = F(x); v += dt/2 F/m.
+ * (a = F/m * 1/103.6427 converts eV/(A amu) to A/fs^2.)  The first call after
+ * set_state also computes the initial forces.  thermo (host, may be NULL)
+ * receives the state after the last step.  Synchronises the stream once per
+ * step (to read the rebuild flag).  Errors: as tmd_neighbors / tmd_compute.
+ */
+tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32_t nsteps,
+                    int32_t rebuild_every, tmd_thermo *thermo, tmd_stream_t stream);
+
+/*
+ * tmd_step from host buffers.  pos/vel [n][3] FP64 and forces_host [n][3]
+ * FP32 are the caller's MD state in host memory (pinned memory gives
+ * asynchronous copies).  The call uploads pos and vel, and the forces at pos
+ * when forces_host is non-NULL (otherwise it recomputes them), rebuilds the
+ * neighbour table, runs nsteps steps, and writes pos, vel and forces back into
+ * the same host arrays.  Synchronises the stream.
+ */
+tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_host, double *vel_host,
+                         float *forces_host, double dt_fs, int32_t nsteps, int32_t rebuild_every,
+                         tmd_thermo *thermo, tmd_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMD_H */

@@ -1,0 +1,557 @@
+// C ABI entry points (include/tmd.h): argument validation, handle management,
+// the host-buffer entry points and the velocity-Verlet integrator.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tmd_internal.cuh"
+
+namespace tmd {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+tmd_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return TMD_ERR_OOM;
+    return TMD_ERR_CUDA;
+}
+
+namespace {
+
+// eV/(A amu) -> A/fs^2
+constexpr double ACC_CONV = 1.0 / 103.6427;
+constexpr double KB_EV = 8.617333262e-5;
+
+__global__ void k_vv_first(double *__restrict__ pos, double *__restrict__ vel, const float *__restrict__ F,
+                           const double *__restrict__ inv_mass, int64_t n, double dt, double L0, double L1,
+                           double L2, int p0, int p1, int p2, const double *__restrict__ pos_ref, double lim2,
+                           int32_t *__restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double L[3] = {L0, L1, L2};
+    const int pb[3] = {p0, p1, p2};
+    const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
+    double d2 = 0.0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        double v = vel[3 * i + x] + h * (double)F[3 * i + x];
+        double p = pos[3 * i + x] + dt * v;
+        if (pb[x]) {
+            p = p - floor(p / L[x]) * L[x];
+            if (p >= L[x]) p -= L[x];
+            if (p < 0.0) p += L[x];
+        }
+        vel[3 * i + x] = v;
+        pos[3 * i + x] = p;
+        double d = p - pos_ref[3 * i + x];
+        if (pb[x]) d -= rint(d / L[x]) * L[x];
+        d2 += d * d;
+    }
+    if (d2 > lim2) atomicOr(flag, 1);
+}
+
+__global__ void k_vv_second(double *__restrict__ vel, const float *__restrict__ F, const double *__restrict__ inv_mass,
+                            int64_t n, double dt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) vel[3 * i + x] += h * (double)F[3 * i + x];
+}
+
+// block partials of sum m v_a v_b (FP64), 6 components
+__global__ void k_kinetic(const double *__restrict__ vel, const double *__restrict__ mass, int64_t n,
+                          double *__restrict__ part) {
+    __shared__ double s[6][8];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double m = mass[i], x = vel[3 * i], y = vel[3 * i + 1], z = vel[3 * i + 2];
+        v[0] += m * x * x; v[1] += m * y * y; v[2] += m * z * z;
+        v[3] += m * x * y; v[4] += m * x * z; v[5] += m * y * z;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+        if (lane == 0) s[t][warp] = v[t];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double acc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += s[threadIdx.x][w];
+        part[(size_t)blockIdx.x * 6 + threadIdx.x] = acc;
+    }
+}
+
+__global__ void k_kinetic_total(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    if (threadIdx.x < 6) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += part[(size_t)b * 6 + threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+}
+
+__global__ void k_inv_mass(const double *__restrict__ mass, double *__restrict__ inv, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) inv[i] = 1.0 / mass[i];
+}
+
+bool finite_all(const double *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+inline uint16_t to_bf16(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    const uint32_t rounding = 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)((u + rounding) >> 16);
+}
+
+tmd_status check_box(const double box[3], const int32_t pbc[3]) {
+    if (!box || !pbc) {
+        set_error("box and pbc must be non-NULL host arrays");
+        return TMD_ERR_INVALID_ARG;
+    }
+    for (int x = 0; x < 3; ++x)
+        if (!(std::isfinite(box[x]) && box[x] > 0.0)) {
+            set_error("box[%d] = %g must be finite and > 0", x, box[x]);
+            return TMD_ERR_INVALID_ARG;
+        }
+    return TMD_OK;
+}
+
+}  // namespace
+}  // namespace tmd
+
+using namespace tmd;
+
+extern "C" {
+
+const char *tmd_status_string(int status) {
+    switch (status) {
+        case TMD_OK: return "TMD_OK";
+        case TMD_ERR_INVALID_ARG: return "TMD_ERR_INVALID_ARG";
+        case TMD_ERR_CAPACITY: return "TMD_ERR_CAPACITY";
+        case TMD_ERR_CUDA: return "TMD_ERR_CUDA";
+        case TMD_ERR_OOM: return "TMD_ERR_OOM";
+        case TMD_ERR_TIMEOUT: return "TMD_ERR_TIMEOUT";
+        case TMD_ERR_UNIMPLEMENTED: return "TMD_ERR_UNIMPLEMENTED";
+        default: return "TMD_ERR_UNKNOWN";
+    }
+}
+
+const char *tmd_last_error(void) { return g_err; }
+
+const char *tmd_version(void) { return "tensormd-gb300 0.1 (sm_103a)"; }
+
+// --------------------------------------------------------------------- model
+tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
+    g_err[0] = 0;
+    if (!d || !out) { set_error("null descriptor or output"); return TMD_ERR_INVALID_ARG; }
+    *out = nullptr;
+    const int S = d->n_species, K = d->n_radial, L = d->n_hidden;
+    if (S < 1 || S > TMD_MAX_SPECIES) { set_error("n_species %d outside [1, %d]", S, TMD_MAX_SPECIES); return TMD_ERR_INVALID_ARG; }
+    if (K != 8 && K != 16 && K != 32) { set_error("n_radial %d: this build supports 8, 16, 32", K); return TMD_ERR_UNIMPLEMENTED; }
+    if (K == 32 && S > 3) { set_error("n_radial 32 supports at most 3 species"); return TMD_ERR_UNIMPLEMENTED; }
+    if (!(std::isfinite(d->rc) && d->rc > 0.0)) { set_error("rc must be finite and > 0"); return TMD_ERR_INVALID_ARG; }
+    if (L < 1 || L > TMD_MAX_HIDDEN) { set_error("n_hidden %d outside [1, %d]", L, TMD_MAX_HIDDEN); return TMD_ERR_INVALID_ARG; }
+    if (!d->widths || !d->weights || !d->mu || !d->eta) { set_error("null widths/weights/mu/eta"); return TMD_ERR_INVALID_ARG; }
+    if (d->activation != TMD_ACT_TANH && d->activation != TMD_ACT_SQUAREPLUS) { set_error("unknown activation"); return TMD_ERR_INVALID_ARG; }
+    if (d->activation == TMD_ACT_SQUAREPLUS && !(d->squareplus_b > 0.0)) { set_error("squareplus_b must be > 0"); return TMD_ERR_INVALID_ARG; }
+    if (d->precision != TMD_PREC_FP32 && d->precision != TMD_PREC_BF16) { set_error("unknown precision"); return TMD_ERR_INVALID_ARG; }
+    const int Dd = S * K * 4;
+    int dims[MAX_LAYERS + 1];
+    dims[0] = Dd;
+    for (int l = 0; l < L; ++l) {
+        const int w = d->widths[l];
+        if (w < 4 || w > TMD_MAX_WIDTH || w % 4) { set_error("width %d must be a multiple of 4 in [4, %d]", w, TMD_MAX_WIDTH); return TMD_ERR_INVALID_ARG; }
+        dims[l + 1] = w;
+    }
+    dims[L + 1] = 1;
+    if (!finite_all(d->mu, (size_t)S * S * K) || !finite_all(d->eta, (size_t)S * S * K)) { set_error("non-finite mu/eta"); return TMD_ERR_INVALID_ARG; }
+    for (size_t i = 0; i < (size_t)S * S * K; ++i)
+        if (!(d->eta[i] >= 0.0)) { set_error("eta must be >= 0"); return TMD_ERR_INVALID_ARG; }
+    // per-species float counts
+    size_t nf = 0, nb = 0;
+    int off_f[MAX_LAYERS], off_b[MAX_LAYERS];
+    for (int l = 0; l <= L; ++l) {
+        off_f[l] = (int)nf;
+        off_b[l] = (int)nb;
+        nf += (size_t)dims[l] * dims[l + 1] + dims[l + 1];
+        nb += (size_t)dims[l] * dims[l + 1];
+    }
+    size_t nflat = 0;
+    for (int l = 0; l <= L; ++l) nflat += (size_t)dims[l] * dims[l + 1] + dims[l + 1];
+    for (int s = 0; s < S; ++s) {
+        if (!d->weights[s]) { set_error("weights[%d] is NULL", s); return TMD_ERR_INVALID_ARG; }
+        if (!finite_all(d->weights[s], nflat)) { set_error("non-finite weight in species %d", s); return TMD_ERR_INVALID_ARG; }
+    }
+    // host staging: radial | per species fwd fp32 | bwd fp32 | fwd bf16 | bwd bf16  (16 B aligned parts)
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_rad = al(sizeof(float4) * S * S * K);
+    const size_t b_f = al(sizeof(float) * nf), b_b = al(sizeof(float) * nb);
+    const size_t b_hf = al(sizeof(uint16_t) * nf), b_hb = al(sizeof(uint16_t) * nb);
+    const size_t total = b_rad + S * (b_f + b_b + b_hf + b_hb);
+    std::vector<unsigned char> host(total, 0);
+    float4 *rad = reinterpret_cast<float4 *>(host.data());
+    const double log2e = 1.4426950408889634;
+    for (int i = 0; i < S * S * K; ++i)
+        rad[i] = make_float4((float)d->mu[i], (float)(d->eta[i] * log2e), (float)(2.0 * d->eta[i]), 0.f);
+    tmd_model *m = new (std::nothrow) tmd_model();
+    if (!m) { set_error("host allocation failed"); return TMD_ERR_OOM; }
+    cudaError_t e = cudaMalloc(&m->dev_block, total);
+    if (e != cudaSuccess) { delete m; cudaGetLastError(); set_error("cudaMalloc model: %s", cudaGetErrorString(e)); return TMD_ERR_OOM; }
+    m->dev_bytes = total;
+    DevModel &dm = m->dm;
+    std::memset(&dm, 0, sizeof(dm));
+    dm.S = S; dm.K = K; dm.L = L; dm.act = d->activation; dm.Dd = Dd; dm.nlayers = L + 1;
+    dm.precision = d->precision;
+    dm.rc = (float)d->rc; dm.rc2 = (float)(d->rc * d->rc); dm.inv_rc = (float)(1.0 / d->rc);
+    dm.sp_b = (float)d->squareplus_b;
+    for (int l = 0; l <= L + 1; ++l) dm.dims[l] = dims[l];
+    for (int l = 0; l <= L; ++l) { dm.off_f[l] = off_f[l]; dm.off_b[l] = off_b[l]; }
+    unsigned char *dev = static_cast<unsigned char *>(m->dev_block);
+    dm.radial = reinterpret_cast<const float4 *>(dev);
+    size_t cur = b_rad;
+    for (int s = 0; s < S; ++s) {
+        float *hf = reinterpret_cast<float *>(host.data() + cur);
+        float *hbk = reinterpret_cast<float *>(host.data() + cur + b_f);
+        uint16_t *qf = reinterpret_cast<uint16_t *>(host.data() + cur + b_f + b_b);
+        uint16_t *qb = reinterpret_cast<uint16_t *>(host.data() + cur + b_f + b_b + b_hf);
+        const double *w = d->weights[s];
+        size_t o = 0;
+        for (int l = 0; l <= L; ++l) {
+            const int in = dims[l], outd = dims[l + 1];
+            for (int r = 0; r < outd; ++r)
+                for (int c = 0; c < in; ++c) {
+                    const float v = (float)w[o + (size_t)r * in + c];
+                    hf[off_f[l] + (size_t)c * outd + r] = v;      // W^T [in][out]
+                    hbk[off_b[l] + (size_t)r * in + c] = v;       // W [out][in]
+                    qf[off_f[l] + (size_t)c * outd + r] = to_bf16(v);
+                    qb[off_b[l] + (size_t)r * in + c] = to_bf16(v);
+                }
+            o += (size_t)in * outd;
+            for (int r = 0; r < outd; ++r) hf[off_f[l] + (size_t)in * outd + r] = (float)w[o + r];
+            o += outd;
+        }
+        dm.wf[s] = reinterpret_cast<const float *>(dev + cur);
+        dm.wb[s] = reinterpret_cast<const float *>(dev + cur + b_f);
+        dm.hf[s] = reinterpret_cast<const uint16_t *>(dev + cur + b_f + b_b);
+        dm.hb[s] = reinterpret_cast<const uint16_t *>(dev + cur + b_f + b_b + b_hf);
+        cur += b_f + b_b + b_hf + b_hb;
+    }
+    e = cudaMemcpy(m->dev_block, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(m->dev_block); delete m; return cuda_fail(e, "cudaMemcpy model"); }
+    m->precision = d->precision;
+    *out = m;
+    return TMD_OK;
+}
+
+tmd_status tmd_model_destroy(tmd_model *m) {
+    if (!m) return TMD_OK;
+    if (m->dev_block) cudaFree(m->dev_block);
+    delete m;
+    return TMD_OK;
+}
+
+tmd_status tmd_model_set_precision(tmd_model *m, int32_t precision) {
+    if (!m || (precision != TMD_PREC_FP32 && precision != TMD_PREC_BF16)) {
+        set_error("bad model or precision");
+        return TMD_ERR_INVALID_ARG;
+    }
+    m->precision = precision;
+    m->dm.precision = precision;
+    return TMD_OK;
+}
+
+// --------------------------------------------------------------------- nlist
+tmd_status tmd_nlist_create(tmd_nlist **out) {
+    if (!out) { set_error("null output"); return TMD_ERR_INVALID_ARG; }
+    *out = new (std::nothrow) tmd_nlist();
+    if (!*out) { set_error("host allocation failed"); return TMD_ERR_OOM; }
+    return TMD_OK;
+}
+
+tmd_status tmd_nlist_destroy(tmd_nlist *nl) {
+    if (!nl) return TMD_OK;
+    nlist_free(nl);
+    delete nl;
+    return TMD_OK;
+}
+
+tmd_status tmd_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
+                         const int32_t pbc[3], double r_list, tmd_nlist *nl, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!nl) { set_error("null neighbour table"); return TMD_ERR_INVALID_ARG; }
+    tmd_status st = check_box(box, pbc);
+    if (st != TMD_OK) return st;
+    return build_neighbors(pos, types, n, box, pbc, r_list, nl, (cudaStream_t)stream);
+}
+
+tmd_status tmd_nlist_size(const tmd_nlist *nl, int64_t *n_atoms, int64_t *n_entries) {
+    if (!nl || !nl->built) { set_error("neighbour table not built"); return TMD_ERR_INVALID_ARG; }
+    if (n_atoms) *n_atoms = nl->n;
+    if (n_entries) *n_entries = nl->nnz;
+    return TMD_OK;
+}
+
+tmd_status tmd_nlist_export(const tmd_nlist *nl, int64_t *off, int32_t *nbr, int8_t *shift) {
+    if (!nl || !nl->built) { set_error("neighbour table not built"); return TMD_ERR_INVALID_ARG; }
+    TMD_CUDA(cudaDeviceSynchronize());
+    if (off) TMD_CUDA(cudaMemcpy(off, nl->off, sizeof(int64_t) * (nl->n + 1), cudaMemcpyDeviceToHost));
+    if (nbr && nl->nnz) TMD_CUDA(cudaMemcpy(nbr, nl->nbr, sizeof(int32_t) * nl->nnz, cudaMemcpyDeviceToHost));
+    if (shift && nl->nnz) {
+        std::vector<char4> tmp((size_t)nl->nnz);
+        TMD_CUDA(cudaMemcpy(tmp.data(), nl->shift, sizeof(char4) * nl->nnz, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nl->nnz; ++i) {
+            shift[3 * i] = tmp[i].x;
+            shift[3 * i + 1] = tmp[i].y;
+            shift[3 * i + 2] = tmp[i].z;
+        }
+    }
+    return TMD_OK;
+}
+
+// --------------------------------------------------------------------- compute
+tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
+                       const double box[3], double *energy, float *e_atom, float *forces, double *virial,
+                       tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!box) { set_error("null box"); return TMD_ERR_INVALID_ARG; }
+    if (n > 0 && (!pos || !types)) { set_error("null pos/types"); return TMD_ERR_INVALID_ARG; }
+    return run_compute(model, nl, pos, types, n, box, energy, e_atom, forces, virial, (cudaStream_t)stream);
+}
+
+tmd_status tmd_evaluate_host(const tmd_model *model, tmd_nlist *nl, const double *pos_host, const int32_t *types_host,
+                             int64_t n, const double box[3], const int32_t pbc[3], double *energy_host,
+                             float *forces_host, double *virial_host, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!model || !nl) { set_error("null model or neighbour table"); return TMD_ERR_INVALID_ARG; }
+    tmd_status st = check_box(box, pbc);
+    if (st != TMD_OK) return st;
+    if (n < 0 || (n > 0 && (!pos_host || !types_host))) { set_error("bad n or null host arrays"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = grow(&nl->io_pos, &nl->cap_io_pos, 3 * n)) != TMD_OK) return st;
+    if ((st = grow(&nl->io_types, &nl->cap_io_types, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->io_forces, &nl->cap_io_forces, 3 * n)) != TMD_OK) return st;
+    if ((st = grow(&nl->io_red, &nl->cap_io_red, 10)) != TMD_OK) return st;
+    if (n > 0) {
+        TMD_CUDA(cudaMemcpyAsync(nl->io_pos, pos_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+        TMD_CUDA(cudaMemcpyAsync(nl->io_types, types_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    }
+    if ((st = build_neighbors(nl->io_pos, nl->io_types, n, box, pbc, (double)model->dm.rc, nl, s)) != TMD_OK) return st;
+    if ((st = run_compute(model, nl, nl->io_pos, nl->io_types, n, box, nl->io_red, nullptr, nl->io_forces,
+                          nl->io_red + 1, s)) != TMD_OK)
+        return st;
+    if (energy_host) TMD_CUDA(cudaMemcpyAsync(energy_host, nl->io_red, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (virial_host) TMD_CUDA(cudaMemcpyAsync(virial_host, nl->io_red + 1, 9 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (forces_host && n > 0)
+        TMD_CUDA(cudaMemcpyAsync(forces_host, nl->io_forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    return TMD_OK;
+}
+
+// --------------------------------------------------------------------- MD
+tmd_status tmd_system_create(int64_t n, const double box[3], const int32_t pbc[3], double skin, tmd_system **out) {
+    g_err[0] = 0;
+    if (!out) { set_error("null output"); return TMD_ERR_INVALID_ARG; }
+    *out = nullptr;
+    tmd_status st = check_box(box, pbc);
+    if (st != TMD_OK) return st;
+    if (n < 1 || n >= (int64_t(1) << 28)) { set_error("n = %lld outside [1, 2^28)", (long long)n); return TMD_ERR_INVALID_ARG; }
+    if (!(std::isfinite(skin) && skin >= 0.0)) { set_error("skin must be finite and >= 0"); return TMD_ERR_INVALID_ARG; }
+    tmd_system *sys = new (std::nothrow) tmd_system();
+    if (!sys) { set_error("host allocation failed"); return TMD_ERR_OOM; }
+    sys->n = n;
+    for (int x = 0; x < 3; ++x) { sys->box[x] = box[x]; sys->pbc[x] = pbc[x] ? 1 : 0; }
+    sys->skin = skin;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&sys->pos, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->vel, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->pos_ref, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->inv_mass, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->mass, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->types, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->forces, sizeof(float) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->red, sizeof(double) * 32);
+    if (e == cudaSuccess) e = cudaMallocHost(&sys->h_red, sizeof(double) * 32);
+    if (e == cudaSuccess) e = cudaMemset(sys->vel, 0, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMemset(sys->forces, 0, sizeof(float) * 3 * n);
+    if (e == cudaSuccess) e = cudaMemset(sys->red, 0, sizeof(double) * 32);
+    if (e != cudaSuccess) {
+        tmd_system_destroy(sys);
+        cudaGetLastError();
+        set_error("system allocation: %s", cudaGetErrorString(e));
+        return TMD_ERR_OOM;
+    }
+    *out = sys;
+    return TMD_OK;
+}
+
+tmd_status tmd_system_destroy(tmd_system *sys) {
+    if (!sys) return TMD_OK;
+    void *p[] = {sys->pos, sys->vel, sys->pos_ref, sys->inv_mass, sys->mass, sys->types, sys->forces, sys->red,
+                 sys->part};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    if (sys->h_red) cudaFreeHost(sys->h_red);
+    nlist_free(&sys->nl);
+    delete sys;
+    return TMD_OK;
+}
+
+tmd_status tmd_system_set_state(tmd_system *sys, const double *pos, const double *vel, const int32_t *types,
+                                const double *masses, int32_t on_device, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!sys || !pos || !types) { set_error("null system, pos or types"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const int64_t n = sys->n;
+    TMD_CUDA(cudaMemcpyAsync(sys->pos, pos, sizeof(double) * 3 * n, k, s));
+    TMD_CUDA(cudaMemcpyAsync(sys->types, types, sizeof(int32_t) * n, k, s));
+    if (vel) TMD_CUDA(cudaMemcpyAsync(sys->vel, vel, sizeof(double) * 3 * n, k, s));
+    else TMD_CUDA(cudaMemsetAsync(sys->vel, 0, sizeof(double) * 3 * n, s));
+    if (masses) {
+        if (!on_device)
+            for (int64_t i = 0; i < n; ++i)
+                if (!(masses[i] > 0.0 && std::isfinite(masses[i]))) { set_error("mass[%lld] must be > 0", (long long)i); return TMD_ERR_INVALID_ARG; }
+        TMD_CUDA(cudaMemcpyAsync(sys->mass, masses, sizeof(double) * n, k, s));
+        k_inv_mass<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys->mass, sys->inv_mass, n);
+        TMD_CUDA(cudaGetLastError());
+    }
+    if (!on_device) TMD_CUDA(cudaStreamSynchronize(s));  // host arrays may be pageable and reused
+    sys->step = 0;
+    sys->rebuilds = 0;
+    sys->need_rebuild = 1;
+    sys->have_forces = 0;
+    return TMD_OK;
+}
+
+tmd_status tmd_system_get_state(const tmd_system *sys, double *pos, double *vel, float *forces, int32_t on_device,
+                                tmd_stream_t stream) {
+    if (!sys) { set_error("null system"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const int64_t n = sys->n;
+    if (pos) TMD_CUDA(cudaMemcpyAsync(pos, sys->pos, sizeof(double) * 3 * n, k, s));
+    if (vel) TMD_CUDA(cudaMemcpyAsync(vel, sys->vel, sizeof(double) * 3 * n, k, s));
+    if (forces) TMD_CUDA(cudaMemcpyAsync(forces, sys->forces, sizeof(float) * 3 * n, k, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    return TMD_OK;
+}
+
+static tmd_status rebuild_and_compute(const tmd_model *model, tmd_system *sys, bool rebuild, cudaStream_t s) {
+    tmd_status st;
+    if (rebuild) {
+        const double r_list = (double)model->dm.rc + sys->skin;
+        if ((st = build_neighbors(sys->pos, sys->types, sys->n, sys->box, sys->pbc, r_list, &sys->nl, s)) != TMD_OK)
+            return st;
+        TMD_CUDA(cudaMemcpyAsync(sys->pos_ref, sys->pos, sizeof(double) * 3 * sys->n, cudaMemcpyDeviceToDevice, s));
+        sys->rebuilds++;
+        sys->need_rebuild = 0;
+    }
+    return run_compute(model, &sys->nl, sys->pos, sys->types, sys->n, sys->box, sys->red, nullptr, sys->forces,
+                       sys->red + 1, s);
+}
+
+tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32_t nsteps, int32_t rebuild_every,
+                    tmd_thermo *thermo, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!model || !sys) { set_error("null model or system"); return TMD_ERR_INVALID_ARG; }
+    if (!(std::isfinite(dt_fs)) || nsteps < 0 || rebuild_every < 0) { set_error("bad dt/nsteps/rebuild_every"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    tmd_status st;
+    const int64_t n = sys->n;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    int32_t *flag = reinterpret_cast<int32_t *>(sys->red + 20);
+    if (!sys->have_forces) {
+        if ((st = rebuild_and_compute(model, sys, true, s)) != TMD_OK) return st;
+        sys->have_forces = 1;
+    }
+    const double lim = 0.5 * sys->skin;
+    for (int it = 0; it < nsteps; ++it) {
+        TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+        k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n, dt_fs, sys->box[0],
+                                      sys->box[1], sys->box[2], sys->pbc[0], sys->pbc[1], sys->pbc[2], sys->pos_ref,
+                                      lim * lim, flag);
+        TMD_CUDA(cudaGetLastError());
+        sys->step++;
+        bool rebuild = sys->need_rebuild || (rebuild_every > 0 && (sys->step % rebuild_every) == 0);
+        if (!rebuild) {
+            TMD_CUDA(cudaMemcpyAsync(sys->h_red + 20, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            TMD_CUDA(cudaStreamSynchronize(s));
+            int32_t f = 0;
+            std::memcpy(&f, sys->h_red + 20, sizeof(int32_t));
+            rebuild = f != 0;
+        }
+        if ((st = rebuild_and_compute(model, sys, rebuild, s)) != TMD_OK) return st;
+        k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs);
+        TMD_CUDA(cudaGetLastError());
+    }
+    if (thermo) {
+        const int kb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+        if ((st = grow(&sys->part, &sys->cap_part, 6 * (int64_t)kb)) != TMD_OK) return st;
+        k_kinetic<<<kb, 256, 0, s>>>(sys->vel, sys->mass, n, sys->part);
+        k_kinetic_total<<<1, 32, 0, s>>>(sys->part, kb, sys->red + 10);
+        TMD_CUDA(cudaGetLastError());
+        TMD_CUDA(cudaMemcpyAsync(sys->h_red, sys->red, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaStreamSynchronize(s));
+        const double *r = sys->h_red;
+        const double conv = 1.0 / ACC_CONV;  // amu A^2/fs^2 -> eV
+        const double mvv[9] = {r[10], r[13], r[14], r[13], r[11], r[15], r[14], r[15], r[12]};
+        thermo->e_pot = r[0];
+        thermo->e_kin = 0.5 * (r[10] + r[11] + r[12]) * conv;
+        const double dof = n > 1 ? 3.0 * n - 3.0 : 3.0;
+        thermo->temperature = 2.0 * thermo->e_kin / (dof * KB_EV);
+        const double V = sys->box[0] * sys->box[1] * sys->box[2];
+        for (int t = 0; t < 9; ++t) {
+            thermo->virial[t] = r[1 + t];
+            thermo->pressure[t] = (mvv[t] * conv + r[1 + t]) / V;
+        }
+        thermo->step = sys->step;
+        thermo->rebuilds = sys->rebuilds;
+    }
+    return TMD_OK;
+}
+
+tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_host, double *vel_host, float *forces_host,
+                         double dt_fs, int32_t nsteps, int32_t rebuild_every, tmd_thermo *thermo, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!model || !sys || !pos_host || !vel_host) { set_error("null model, system or host state"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = sys->n;
+    TMD_CUDA(cudaMemcpyAsync(sys->pos, pos_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    TMD_CUDA(cudaMemcpyAsync(sys->vel, vel_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    if (forces_host) {
+        TMD_CUDA(cudaMemcpyAsync(sys->forces, forces_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        sys->have_forces = 1;
+    } else {
+        sys->have_forces = 0;
+    }
+    sys->need_rebuild = 1;
+    tmd_status st = tmd_step(model, sys, dt_fs, nsteps, rebuild_every, thermo, stream);
+    if (st != TMD_OK) return st;
+    TMD_CUDA(cudaMemcpyAsync(pos_host, sys->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaMemcpyAsync(vel_host, sys->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (forces_host) TMD_CUDA(cudaMemcpyAsync(forces_host, sys->forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    return TMD_OK;
+}
+
+}  // extern "C"

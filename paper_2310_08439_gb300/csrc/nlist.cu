@@ -1,0 +1,504 @@
+// Device cell list and neighbour table (the neighbour tensor R_abc of the
+// paper's Sec. "The Tensor Formalism", built by binning with a skin buffer as
+// in Sec. "Evaluation").
+//
+// Layout: atoms are binned into cells of side >= r_list; each atom's
+// candidates come from the (2R+1)^3 stencil of unwrapped cells around its own,
+// so periodic images (including self-images in boxes shorter than 2 r_list)
+// are enumerated as distinct (cell, shift) pairs.  Candidates are screened in
+// FP32 from a cell-sorted float4 copy of the positions; only pairs inside a
+// rounding band around r_list^2 are decided in FP64 with the exact
+// expression ((x_j + s L) - x_i), (dx^2 + dy^2) + dz^2, no FMA, which makes the
+// table bit-identical to the plain definition.  Each atom's entries are sorted
+// by (species of j, j, sx, sy, sz) with a warp bitonic sort in shared memory.
+#include <cmath>
+#include <cstring>
+
+#include "tmd_internal.cuh"
+
+namespace tmd {
+
+namespace {
+
+constexpr int BIN_THREADS = 256;
+constexpr int NBR_WARPS = 4;
+
+__device__ __forceinline__ int floordiv(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+// cell index of each atom, cell occupancy counts (stored at start[c+1]), per
+// block species counts; flags atoms outside the box and bad species.
+__global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict__ types, int64_t n,
+                      double L0, double L1, double L2, int nc0, int nc1, int nc2,
+                      int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_start,
+                      int32_t *__restrict__ type_block, int32_t *__restrict__ status) {
+    __shared__ int32_t s_cnt[TMD_MAX_SPECIES];
+    if (threadIdx.x < TMD_MAX_SPECIES) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int t = -1;
+    if (i < n) {
+        const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        int bad = !(x >= 0.0 && x < L0 && y >= 0.0 && y < L1 && z >= 0.0 && z < L2);
+        int cx = (int)floor(x * nc0 / L0), cy = (int)floor(y * nc1 / L1), cz = (int)floor(z * nc2 / L2);
+        cx = min(max(cx, 0), nc0 - 1);
+        cy = min(max(cy, 0), nc1 - 1);
+        cz = min(max(cz, 0), nc2 - 1);
+        if (bad) atomicOr(status, DEV_ERR_OUTSIDE_BOX);
+        const int c = cx + nc0 * (cy + nc1 * cz);
+        cell_of[i] = c;
+        atomicAdd(&cell_start[c + 1], 1);
+        t = types[i];
+        if (t < 0 || t >= TMD_MAX_SPECIES) {
+            atomicOr(status, DEV_ERR_BAD_TYPE);
+            t = -1;
+        }
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 0; s < TMD_MAX_SPECIES; ++s) {
+        const unsigned m = __ballot_sync(0xffffffffu, t == s);
+        if (lane == 0 && m) atomicAdd(&s_cnt[s], __popc(m));
+    }
+    __syncthreads();
+    if (threadIdx.x < TMD_MAX_SPECIES) type_block[blockIdx.x * TMD_MAX_SPECIES + threadIdx.x] = s_cnt[threadIdx.x];
+}
+
+// exclusive scan of the per-block species counts (single block); writes the
+// species start offsets type_start[0..MAX_SPECIES].
+__global__ void k_type_scan(int32_t *__restrict__ type_block, int nblocks, int32_t *__restrict__ type_start) {
+    __shared__ int32_t s_tot[TMD_MAX_SPECIES];
+    if (threadIdx.x < TMD_MAX_SPECIES) {
+        const int s = threadIdx.x;
+        int32_t run = 0;
+        for (int b = 0; b < nblocks; ++b) {
+            const int32_t v = type_block[b * TMD_MAX_SPECIES + s];
+            type_block[b * TMD_MAX_SPECIES + s] = run;
+            run += v;
+        }
+        s_tot[s] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int s = 0; s < TMD_MAX_SPECIES; ++s) {
+            type_start[s] = acc;
+            acc += s_tot[s];
+        }
+        type_start[TMD_MAX_SPECIES] = acc;
+    }
+}
+
+// scatter atoms into cells (cell-sorted ids + FP32 positions with the species
+// in the top 4 bits of the id) and stably into species order (perm).
+__global__ void k_fill(const double *__restrict__ pos, const int32_t *__restrict__ types, int64_t n,
+                       const int32_t *__restrict__ cell_of, const int32_t *__restrict__ cell_start,
+                       int32_t *__restrict__ cell_fill, int32_t *__restrict__ cell_atoms,
+                       float4 *__restrict__ cell_pos, const int32_t *__restrict__ type_block,
+                       const int32_t *__restrict__ type_start, int32_t *__restrict__ perm) {
+    __shared__ int32_t s_warp[BIN_THREADS / 32][TMD_MAX_SPECIES];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int t = -1;
+    if (i < n) {
+        t = types[i];
+        if (t < 0 || t >= TMD_MAX_SPECIES) t = -1;
+        const int c = cell_of[i];
+        const int slot = cell_start[c] + atomicAdd(&cell_fill[c], 1);
+        cell_atoms[slot] = (int32_t)i;
+        const int tt = t < 0 ? 0 : t;
+        cell_pos[slot] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2],
+                                     __int_as_float((int)((uint32_t)i | ((uint32_t)tt << 28))));
+    }
+    // stable species partition: rank = (earlier warps of the block) + (earlier lanes)
+    unsigned masks[TMD_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < TMD_MAX_SPECIES; ++s) {
+        masks[s] = __ballot_sync(0xffffffffu, t == s);
+        if (lane == 0) s_warp[warp][s] = __popc(masks[s]);
+    }
+    __syncthreads();
+    if (t >= 0) {
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += s_warp[w][t];
+        before += __popc(masks[t] & ((1u << lane) - 1u));
+        perm[type_start[t] + type_block[blockIdx.x * TMD_MAX_SPECIES + t] + before] = (int32_t)i;
+    }
+}
+
+struct NbrParams {
+    const double *pos;
+    const int32_t *cell_of;
+    const int32_t *cell_start;
+    const float4 *cell_pos;
+    int64_t n;
+    int nc[3], R[3], pbc[3];
+    float Lf[3];
+    double L[3];
+    double r2;            // r_list * r_list (FP64, as the definition)
+    float r2lo, r2hi;     // FP32 band outside which the FP32 screen decides
+    int64_t *off;         // count pass: off[i+1] = count; fill pass: offsets
+    int32_t *nbr;
+    char4 *shift;
+    int32_t *status;
+};
+
+__device__ __forceinline__ uint64_t make_key(int t, int j, int sx, int sy, int sz) {
+    return ((uint64_t)t << 60) | ((uint64_t)(uint32_t)j << 15) | ((uint64_t)(sx + 16) << 10) |
+           ((uint64_t)(sy + 16) << 5) | (uint64_t)(sz + 16);
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
+    extern __shared__ uint64_t s_keys[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * NBR_WARPS + warp;
+    if (i >= p.n) return;
+    uint64_t *keys = s_keys + (size_t)warp * TMD_MAX_DEGREE;
+    const double xi = p.pos[3 * i], yi = p.pos[3 * i + 1], zi = p.pos[3 * i + 2];
+    const float xh = (float)xi, yh = (float)yi, zh = (float)zi;
+    const int ci = p.cell_of[i];
+    const int cx = ci % p.nc[0], cy = (ci / p.nc[0]) % p.nc[1], cz = ci / (p.nc[0] * p.nc[1]);
+    const unsigned lt = (1u << lane) - 1u;
+    int count = 0;
+    for (int dz = -p.R[2]; dz <= p.R[2]; ++dz) {
+        const int uz = cz + dz;
+        if (!p.pbc[2] && (uz < 0 || uz >= p.nc[2])) continue;
+        const int sz = p.pbc[2] ? floordiv(uz, p.nc[2]) : 0;
+        const int kz = uz - sz * p.nc[2];
+        const float zs = zh - (float)sz * p.Lf[2];
+        for (int dy = -p.R[1]; dy <= p.R[1]; ++dy) {
+            const int uy = cy + dy;
+            if (!p.pbc[1] && (uy < 0 || uy >= p.nc[1])) continue;
+            const int sy = p.pbc[1] ? floordiv(uy, p.nc[1]) : 0;
+            const int ky = uy - sy * p.nc[1];
+            const float ys = yh - (float)sy * p.Lf[1];
+            const int row = p.nc[0] * (ky + p.nc[1] * kz);
+            int dx = -p.R[0];
+            while (dx <= p.R[0]) {
+                const int ux = cx + dx;
+                if (!p.pbc[0] && (ux < 0 || ux >= p.nc[0])) { ++dx; continue; }
+                const int sx = p.pbc[0] ? floordiv(ux, p.nc[0]) : 0;
+                const int kx = ux - sx * p.nc[0];
+                int len = 1;  // run of consecutive cells with the same shift
+                while (dx + len <= p.R[0] && kx + len < p.nc[0]) ++len;
+                const float xs = xh - (float)sx * p.Lf[0];
+                const int beg = p.cell_start[row + kx], end = p.cell_start[row + kx + len];
+                const bool self_img = (sx == 0 && sy == 0 && sz == 0);
+                for (int b = beg; b < end; b += 32) {
+                    const int q = b + lane;
+                    bool in = false;
+                    int j = 0, tj = 0;
+                    if (q < end) {
+                        const float4 cp = p.cell_pos[q];
+                        const uint32_t w = (uint32_t)__float_as_int(cp.w);
+                        j = (int)(w & 0x0FFFFFFFu);
+                        tj = (int)(w >> 28);
+                        const float ddx = cp.x - xs, ddy = cp.y - ys, ddz = cp.z - zs;
+                        const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        if (d2 < p.r2lo) {
+                            in = true;
+                        } else if (d2 < p.r2hi) {  // rounding band: exact FP64 decision
+                            const double ex = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j], __dmul_rn((double)sx, p.L[0])), xi);
+                            const double ey = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j + 1], __dmul_rn((double)sy, p.L[1])), yi);
+                            const double ez = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j + 2], __dmul_rn((double)sz, p.L[2])), zi);
+                            const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                            in = e2 < p.r2;
+                        }
+                        if (self_img && j == (int)i) in = false;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+                    if (FILL && in) {
+                        const int slot = count + __popc(m & lt);
+                        if (slot < TMD_MAX_DEGREE) keys[slot] = make_key(tj, j, sx, sy, sz);
+                    }
+                    count += __popc(m);
+                }
+                dx += len;
+            }
+        }
+    }
+    if (!FILL) {
+        if (lane == 0) {
+            p.off[i + 1] = count;
+            if (count > TMD_MAX_DEGREE) atomicOr(p.status, DEV_ERR_DEGREE);
+        }
+        return;
+    }
+    if (count > TMD_MAX_DEGREE) return;  // reported by the count pass
+    // bitonic sort of keys[0..P) with P = next power of two >= count
+    int P = 32;
+    while (P < count) P <<= 1;
+    for (int c = count + lane; c < P; c += 32) keys[c] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < (P >> 1); t += 32) {
+                const int i1 = 2 * jj * (t / jj) + (t % jj);
+                const int i2 = i1 + jj;
+                const bool up = (i1 & k) == 0;
+                const uint64_t a = keys[i1], b = keys[i2];
+                if ((a > b) == up) { keys[i1] = b; keys[i2] = a; }
+            }
+            __syncwarp();
+        }
+    }
+    const int64_t o = p.off[i];
+    for (int c = lane; c < count; c += 32) {
+        const uint64_t key = keys[c];
+        const int t = (int)(key >> 60);
+        const int j = (int)((key >> 15) & 0x1FFFFFFFFFFFull);
+        const int sx = (int)((key >> 10) & 31) - 16, sy = (int)((key >> 5) & 31) - 16, sz = (int)(key & 31) - 16;
+        p.nbr[o + c] = j;
+        p.shift[o + c] = make_char4((signed char)sx, (signed char)sy, (signed char)sz, (signed char)t);
+    }
+}
+
+// ---------------------------------------------------------------- scans
+template <typename T>
+__global__ void k_scan_block(T *__restrict__ data, int64_t n, T *__restrict__ block_sums) {
+    // inclusive scan of 2048-element chunks, 1024 threads x 2 items
+    __shared__ T s_w[32];
+    const int64_t base = (int64_t)blockIdx.x * 2048;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i0 = base + 2 * tid;
+    T a = (i0 < n) ? data[i0] : T(0);
+    T b = (i0 + 1 < n) ? data[i0 + 1] : T(0);
+    b += a;
+    T v = b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += u;
+    }
+    if (lane == 31) s_w[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        T w = s_w[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T u = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += u;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    const T pre = (warp > 0 ? s_w[warp - 1] : T(0)) + v - b;  // exclusive prefix of this thread
+    if (i0 < n) data[i0] = pre + a;
+    if (i0 + 1 < n) data[i0 + 1] = pre + b;
+    if (tid == 1023 && block_sums) block_sums[blockIdx.x] = s_w[31];
+}
+
+template <typename T>
+__global__ void k_scan_add(T *__restrict__ data, int64_t n, const T *__restrict__ block_sums) {
+    const int64_t blk = blockIdx.x + 1;  // block 0 needs no offset
+    const T add = block_sums[blk - 1];
+    const int64_t base = blk * 2048;
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+        const int64_t idx = base + t;
+        if (idx < n) data[idx] += add;
+    }
+}
+
+template <typename T>
+tmd_status scan_inclusive(T *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, cudaStream_t s,
+                          int64_t level_start = 0) {
+    // in-place inclusive scan; block sums of each recursion level live in the
+    // int64 scratch at level_start (one int64 slot per block, T fits in it)
+    if (n <= 0) return TMD_OK;
+    const int64_t nb = (n + 2047) / 2048;
+    if (nb == 1) {
+        k_scan_block<T><<<1, 1024, 0, s>>>(data, n, nullptr);
+        return TMD_OK;
+    }
+    if (level_start == 0) {
+        int64_t need = 0, l = nb;
+        while (l > 1) { need += l + 8; l = (l + 2047) / 2048; }
+        tmd_status st = grow(tmp, cap_tmp, need + 64);
+        if (st != TMD_OK) return st;
+    }
+    T *sums = reinterpret_cast<T *>(*tmp + level_start);
+    k_scan_block<T><<<(unsigned)nb, 1024, 0, s>>>(data, n, sums);
+    tmd_status st = scan_inclusive<T>(sums, nb, tmp, cap_tmp, s, level_start + nb + 8);
+    if (st != TMD_OK) return st;
+    k_scan_add<T><<<(unsigned)(nb - 1), 256, 0, s>>>(data, n, sums);
+    return TMD_OK;
+}
+
+}  // namespace
+
+tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, cudaStream_t s) {
+    return scan_inclusive<int64_t>(data, n, tmp, cap_tmp, s);
+}
+
+void nlist_free(tmd_nlist *nl) {
+    void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->off, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
+                    nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->F4, nl->part};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (nl->h_pinned) cudaFreeHost(nl->h_pinned);
+    *nl = tmd_nlist();
+}
+
+tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
+                           const int32_t pbc[3], double r_list, tmd_nlist *nl, cudaStream_t s) {
+    if (n < 0 || n >= (int64_t(1) << 28)) {
+        set_error("n = %lld outside [0, 2^28)", (long long)n);
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (n > 0 && (!pos || !types)) {
+        set_error("pos/types must be device pointers");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (!(std::isfinite(r_list) && r_list > 0.0)) {
+        set_error("r_list must be finite and > 0");
+        return TMD_ERR_INVALID_ARG;
+    }
+    double Lmax = 0.0;
+    int smax = 0;
+    for (int x = 0; x < 3; ++x) {
+        if (!(std::isfinite(box[x]) && box[x] > 0.0)) {
+            set_error("box[%d] must be finite and > 0", x);
+            return TMD_ERR_INVALID_ARG;
+        }
+        const double margin = 1e-6 + 1e-9 * box[x];
+        int nc = (int)std::floor(box[x] / (r_list + margin));
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        const double cs = box[x] / nc;
+        int R = (int)std::ceil((r_list + margin) / cs);
+        if (R < 1) R = 1;
+        nl->nc[x] = nc;
+        nl->R[x] = R;
+        nl->pbc[x] = pbc[x] ? 1 : 0;
+        nl->box[x] = box[x];
+        if (pbc[x]) {
+            const int lo = -((R + nc - 1) / nc), hi = (nc - 1 + R) / nc;
+            smax = std::max(smax, std::max(-lo, hi));
+        }
+        Lmax = std::max(Lmax, box[x]);
+    }
+    if (smax > 15) {
+        set_error("r_list %.3f needs image shifts beyond +-15 boxes", r_list);
+        return TMD_ERR_CAPACITY;
+    }
+    nl->ncell = (int64_t)nl->nc[0] * nl->nc[1] * nl->nc[2];
+    nl->n = n;
+    nl->r_list = r_list;
+    nl->built = 0;
+
+    tmd_status st;
+    const int64_t nb_bin = (n + BIN_THREADS - 1) / BIN_THREADS;
+    if ((st = grow(&nl->cell_of, &nl->cap_atoms, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_atoms, &nl->cap_cell_atoms, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_pos, &nl->cap_cell_pos, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->perm, &nl->cap_perm, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->off, &nl->cap_off, n + 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_start, &nl->cap_cells, nl->ncell + 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_fill, &nl->cap_cell_fill, nl->ncell)) != TMD_OK) return st;
+    if ((st = grow(&nl->type_block, &nl->cap_type_blocks, (nb_bin + 1) * TMD_MAX_SPECIES)) != TMD_OK) return st;
+    if ((st = grow(&nl->status, &nl->cap_status, 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->type_start, &nl->cap_type_start, TMD_MAX_SPECIES + 1)) != TMD_OK) return st;
+    if (!nl->h_pinned) TMD_CUDA(cudaMallocHost((void **)&nl->h_pinned, 16 * sizeof(int64_t)));
+    TMD_CUDA(cudaMemsetAsync(nl->status, 0, sizeof(int32_t), s));
+    TMD_CUDA(cudaMemsetAsync(nl->cell_start, 0, sizeof(int32_t) * (nl->ncell + 1), s));
+    TMD_CUDA(cudaMemsetAsync(nl->cell_fill, 0, sizeof(int32_t) * nl->ncell, s));
+    TMD_CUDA(cudaMemsetAsync(nl->off, 0, sizeof(int64_t), s));
+    TMD_CUDA(cudaMemsetAsync(nl->type_start, 0, sizeof(int32_t) * (TMD_MAX_SPECIES + 1), s));
+
+    if (n > 0) {
+        k_bin<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, box[0], box[1], box[2], nl->nc[0],
+                                                      nl->nc[1], nl->nc[2], nl->cell_of, nl->cell_start,
+                                                      nl->type_block, nl->status);
+        TMD_CUDA(cudaGetLastError());
+        if ((st = scan_inclusive<int32_t>(nl->cell_start + 1, nl->ncell, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK)
+            return st;
+        k_type_scan<<<1, 32, 0, s>>>(nl->type_block, (int)nb_bin, nl->type_start);
+        k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start, nl->cell_fill,
+                                                       nl->cell_atoms, nl->cell_pos, nl->type_block,
+                                                       nl->type_start, nl->perm);
+        TMD_CUDA(cudaGetLastError());
+    }
+
+    NbrParams p;
+    p.pos = pos;
+    p.cell_of = nl->cell_of;
+    p.cell_start = nl->cell_start;
+    p.cell_pos = nl->cell_pos;
+    p.n = n;
+    for (int x = 0; x < 3; ++x) {
+        p.nc[x] = nl->nc[x];
+        p.R[x] = nl->R[x];
+        p.pbc[x] = nl->pbc[x];
+        p.Lf[x] = (float)box[x];
+        p.L[x] = box[x];
+    }
+    p.r2 = r_list * r_list;
+    {
+        // FP32 screen error bound: |x_f - x| <= L 2^-24 per coordinate, the
+        // shift product/difference add (1 + 2|s|) L 2^-24, the final
+        // difference r 2^-24; squared-distance error <= 2 sqrt(3) r e + 3 e^2
+        // + rounding of the sum.  Doubled for safety.
+        const double u = std::ldexp(1.0, -24);
+        const double e = ((4.0 + 4.0 * smax) * Lmax + 2.0 * (r_list + 1.0)) * u;
+        const double rr = r_list + 1.0;
+        const double margin = 2.0 * (2.0 * std::sqrt(3.0) * rr * e + 3.0 * e * e + 4.0 * rr * rr * u);
+        p.r2lo = std::nextafter((float)(p.r2 - margin), -INFINITY);
+        p.r2hi = std::nextafter((float)(p.r2 + margin), INFINITY);
+    }
+    p.off = nl->off;
+    p.nbr = nullptr;
+    p.shift = nullptr;
+    p.status = nl->status;
+    const unsigned nb_nbr = (unsigned)((n + NBR_WARPS - 1) / NBR_WARPS);
+    if (n > 0) {
+        k_nbr<false><<<nb_nbr, NBR_WARPS * 32, 0, s>>>(p);
+        TMD_CUDA(cudaGetLastError());
+        if ((st = scan_inclusive<int64_t>(nl->off + 1, n, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK) return st;
+    }
+    TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[0], nl->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[1], nl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[2], nl->type_start, sizeof(int32_t) * (TMD_MAX_SPECIES + 1),
+                             cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    const int64_t nnz = nl->h_pinned[0];
+    int32_t status = 0;
+    std::memcpy(&status, &nl->h_pinned[1], sizeof(int32_t));
+    int32_t tstart[TMD_MAX_SPECIES + 1];
+    std::memcpy(tstart, &nl->h_pinned[2], sizeof(tstart));
+    if (status & DEV_ERR_OUTSIDE_BOX) {
+        set_error("an atom lies outside [0, L) on some axis (wrap periodic axes first)");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (status & DEV_ERR_BAD_TYPE) {
+        set_error("a species id is outside [0, %d)", TMD_MAX_SPECIES);
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (status & DEV_ERR_DEGREE) {
+        set_error("an atom has more than %d neighbour entries inside r_list", TMD_MAX_DEGREE);
+        return TMD_ERR_CAPACITY;
+    }
+    for (int t = 0; t < TMD_MAX_SPECIES; ++t) nl->type_count[t] = tstart[t + 1] - tstart[t];
+    if ((st = grow(&nl->nbr, &nl->cap_nnz, nnz)) != TMD_OK) return st;
+    if ((st = grow(&nl->shift, &nl->cap_shift, nnz)) != TMD_OK) return st;
+    p.nbr = nl->nbr;
+    p.shift = nl->shift;
+    if (n > 0) {
+        const size_t smem = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
+        static bool attr_set = false;
+        if (!attr_set) {
+            TMD_CUDA(cudaFuncSetAttribute(k_nbr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+        k_nbr<true><<<nb_nbr, NBR_WARPS * 32, smem, s>>>(p);
+        TMD_CUDA(cudaGetLastError());
+    }
+    nl->nnz = nnz;
+    nl->built = 1;
+    return TMD_OK;
+}
+
+}  // namespace tmd

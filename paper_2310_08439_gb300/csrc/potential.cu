@@ -1,0 +1,698 @@
+// TensorMD energy / force / virial kernels for sm_103a.
+//
+// The paper's tensor diagram (Sec. "The Tensor Formalism") is evaluated as:
+//   k_desc   setup (D, R, Dhat), H_abck = f_k f_c, M_abcd, P_abkd = sum_c H M,
+//            G_abkm = sigma(T_dm P^2)            -- Eqs. tensor_formalism, sigma_function
+//   k_mlp    E_a = NNP(G_a) and G' = dE_a/dG_a    -- the E_a / NNP equations
+//   k_force  P' = 2 T sigma' P G', U = P' M, V = P' H, F1 = U H' R', F2 = V M'
+//            with M' formed on the fly, ScatterSum into forces, virial
+//                                                 -- Eqs. dP_abkd, U_abck, F1_abcx, F2_abcx
+//   k_reduce FP64 energy and virial totals, k_forces_out float4 -> [n][3].
+//
+// One warp owns one centre atom.  Neighbour entries beyond rc are dropped and
+// the survivors are compacted through a per-warp shared-memory queue, so every
+// lane works on an in-cutoff pair.  In k_desc each lane computes H and M for
+// one neighbour and stages them in shared memory; the warp then accumulates the
+// per-atom P[b][k][d] outer products with each lane owning a (K/8 x 5) block of
+// P in registers.  In k_force each lane owns one neighbour and reads the atom's
+// P' from shared memory with broadcast loads.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "tmd_internal.cuh"
+
+namespace tmd {
+
+namespace {
+
+constexpr int PW = 4;           // warps per block in the pair kernels
+constexpr int MT = 32;          // atoms per network tile
+constexpr int MLP_THREADS = 128;
+constexpr float PI_F = 3.14159265358979323846f;
+
+// multiplicities T_d and ranks m(d) in the row order of Eq. T_dm:
+// 1 | x y z | xx xy xz yy yz zz | xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+__constant__ float c_T[NMOM] = {1, 1, 1, 1, 1, 2, 2, 1, 2, 1, 1, 3, 3, 3, 6, 3, 1, 3, 3, 1};
+
+__device__ __forceinline__ void moments20(float x, float y, float z, float *M) {
+    M[0] = 1.f;
+    M[1] = x; M[2] = y; M[3] = z;
+    M[4] = x * x; M[5] = x * y; M[6] = x * z; M[7] = y * y; M[8] = y * z; M[9] = z * z;
+    M[10] = M[4] * x; M[11] = M[4] * y; M[12] = M[4] * z; M[13] = x * M[7]; M[14] = M[5] * z;
+    M[15] = x * M[9]; M[16] = M[7] * y; M[17] = M[7] * z; M[18] = y * M[9]; M[19] = M[9] * z;
+}
+
+// f_c and H_k (and dH_k/dr when DERIV) for r < rc; rad[k] = (mu, eta log2 e, 2 eta, 0).
+template <int K, bool DERIV>
+__device__ __forceinline__ void radial(const float4 *rad, float r, float inv_rc, float *H, float *dH) {
+    float sn, cs;
+    sincospif(r * inv_rc, &sn, &cs);
+    const float fc = 0.5f * (cs + 1.f);
+    const float dfc = -0.5f * PI_F * inv_rc * sn;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 p = rad[k];
+        const float t = r - p.x;
+        const float f = exp2f(-p.y * t * t);
+        H[k] = f * fc;
+        if (DERIV) dH[k] = fmaf(-p.z * t * f, fc, f * dfc);
+    }
+}
+
+// Walk the entries [beg, end) of one atom, keep pairs with r^2 < rc^2 and hand
+// them to f in batches of up to 32 (one per lane).  D = x_j + s L - x_i is
+// formed in FP64 and rounded to FP32.  The queue entry is (Dx, Dy, Dz, j | b<<28).
+template <typename F>
+__device__ __forceinline__ void for_pairs(const DevNlist &nl, const double *__restrict__ pos, int64_t beg,
+                                          int64_t end, double xi, double yi, double zi, float rc2,
+                                          float4 *q, int lane, F &&f) {
+    int qn = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = beg; base < end; base += 32) {
+        const int64_t c = base + lane;
+        bool v = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        uint32_t jb = 0;
+        if (c < end) {
+            const int j = nl.nbr[c];
+            const char4 s = nl.shift[c];
+            double ex = pos[3 * (int64_t)j] - xi;
+            double ey = pos[3 * (int64_t)j + 1] - yi;
+            double ez = pos[3 * (int64_t)j + 2] - zi;
+            if (s.x) ex += (double)s.x * nl.box[0];
+            if (s.y) ey += (double)s.y * nl.box[1];
+            if (s.z) ez += (double)s.z * nl.box[2];
+            dx = (float)ex; dy = (float)ey; dz = (float)ez;
+            v = dx * dx + dy * dy + dz * dz < rc2;
+            jb = (uint32_t)j | ((uint32_t)s.w << 28);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, v);
+        if (v) q[qn + __popc(m & lt)] = make_float4(dx, dy, dz, __uint_as_float(jb));
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            const float4 e = q[lane];
+            f(e, true, 32);
+            __syncwarp();
+            if (lane < qn - 32) q[lane] = q[lane + 32];
+            __syncwarp();
+            qn -= 32;
+        }
+    }
+    if (qn > 0) {
+        const float4 e = q[lane];
+        f(e, lane < qn, qn);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// descriptor forward: P and G per atom
+// ---------------------------------------------------------------------------
+template <int K, int S>
+__global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const double *__restrict__ pos,
+                                                  const int32_t *__restrict__ types, float *__restrict__ G,
+                                                  float *__restrict__ Pout) {
+    constexpr int KPL = K / 8;   // k values per lane
+    constexpr int HS = K + 4;    // row stride of staged H (keeps 16 B alignment, no bank conflicts)
+    constexpr int MS = 36;       // row stride of staged M: 4 groups of 5 padded to 8, plus 4
+    constexpr int Dd = S * K * 4;
+    __shared__ float4 s_rad[S * S * K];
+    __shared__ float4 s_q[PW][64];
+    __shared__ __align__(16) float s_H[PW][32 * HS];
+    __shared__ __align__(16) float s_M[PW][32 * MS];
+    __shared__ int s_b[PW][32];
+    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = lane >> 2, g = lane & 3;
+    float Tg[5];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
+    const int64_t total = (int64_t)gridDim.x * PW;
+    for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
+        const int a = nl.perm[p];
+        const int ti = types[a];
+        const double xi = pos[3 * (int64_t)a], yi = pos[3 * (int64_t)a + 1], zi = pos[3 * (int64_t)a + 2];
+        float acc[S][KPL][5];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
+        float *sH = s_H[warp];
+        float *sM = s_M[warp];
+        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2, s_q[warp], lane,
+                  [&](const float4 e, bool valid, int nb) {
+                      if (valid) {
+                          const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
+                          const float ir = rsqrtf(r2);
+                          const float r = r2 * ir;
+                          const uint32_t jb = __float_as_uint(e.w);
+                          const int b = (int)(jb >> 28);
+                          float H[K], M[NMOM];
+                          radial<K, false>(&s_rad[(ti * S + b) * K], r, m.inv_rc, H, nullptr);
+                          moments20(e.x * ir, e.y * ir, e.z * ir, M);
+#pragma unroll
+                          for (int k = 0; k < K; k += 4)
+                              *reinterpret_cast<float4 *>(&sH[lane * HS + k]) = make_float4(H[k], H[k + 1], H[k + 2], H[k + 3]);
+#pragma unroll
+                          for (int gg = 0; gg < 4; ++gg) {
+                              *reinterpret_cast<float4 *>(&sM[lane * MS + gg * 8]) =
+                                  make_float4(M[5 * gg], M[5 * gg + 1], M[5 * gg + 2], M[5 * gg + 3]);
+                              sM[lane * MS + gg * 8 + 4] = M[5 * gg + 4];
+                          }
+                          s_b[warp][lane] = b;
+                      }
+                      __syncwarp();
+                      for (int qi = 0; qi < nb; ++qi) {
+                          const int b = s_b[warp][qi];
+                          float h[KPL];
+                          if constexpr (KPL == 1) {
+                              h[0] = sH[qi * HS + kg];
+                          } else if constexpr (KPL == 2) {
+                              const float2 v = *reinterpret_cast<const float2 *>(&sH[qi * HS + kg * 2]);
+                              h[0] = v.x; h[1] = v.y;
+                          } else {
+#pragma unroll
+                              for (int kk = 0; kk < KPL; kk += 4) {
+                                  const float4 v = *reinterpret_cast<const float4 *>(&sH[qi * HS + kg * KPL + kk]);
+                                  h[kk] = v.x; h[kk + 1] = v.y; h[kk + 2] = v.z; h[kk + 3] = v.w;
+                              }
+                          }
+                          const float4 m4 = *reinterpret_cast<const float4 *>(&sM[qi * MS + g * 8]);
+                          const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sM[qi * MS + g * 8 + 4]};
+#pragma unroll
+                          for (int s = 0; s < S; ++s) {
+                              if (S == 1 || b == s) {
+#pragma unroll
+                                  for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                                      for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = fmaf(h[kk], mv[dd], acc[s][kk][dd]);
+                              }
+                          }
+                      }
+                      __syncwarp();
+                  });
+        // P[b][k][d] for the backward pass
+        float *Pa = Pout + (size_t)a * (S * K * NMOM);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) Pa[(s * K + kg * KPL + kk) * NMOM + 5 * g + dd] = acc[s][kk][dd];
+        // G[b][k][m] = sigma(sum_{d in rank m} T_d P^2)
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk) {
+                float sq[5];
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) sq[dd] = Tg[dd] * acc[s][kk][dd] * acc[s][kk][dd];
+                const float tot = sq[0] + sq[1] + sq[2] + sq[3] + sq[4];
+                float p0 = (g == 0) ? sq[0] : 0.f;
+                float p1 = (g == 0) ? sq[1] + sq[2] + sq[3] : 0.f;
+                float p2 = (g == 0) ? sq[4] : ((g == 1) ? tot : 0.f);
+                float p3 = (g >= 2) ? tot : 0.f;
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1) {
+                    p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+                    p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+                    p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+                    p3 += __shfl_xor_sync(0xffffffffu, p3, o);
+                }
+                const float val = (g == 0) ? sqrtf(p0) : ((g == 1) ? p1 : ((g == 2) ? p2 : p3));
+                G[(size_t)a * Dd + (s * K + kg * KPL + kk) * 4 + g] = val;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// network: E_a = NNP(G_a), G' = dE_a/dG_a (FP32 SIMT)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float act_f(int act, float z, float b) {
+    if (act == TMD_ACT_TANH) return tanhf(z);
+    return 0.5f * (z + sqrtf(fmaf(z, z, b)));
+}
+// derivative expressed through the activation output a
+__device__ __forceinline__ float act_da(int act, float a, float b) {
+    if (act == TMD_ACT_TANH) return 1.f - a * a;
+    const float a2 = 4.f * a * a;
+    return a2 / (a2 + b);
+}
+
+// C[r][o] = epi(bias[o] + sum_c A[r][c] B[c][o]) for an MT-row tile.
+// EPI 0: store; 1: activation; 2: multiply by act'(aux[r][o]).
+template <int EPI>
+__device__ __forceinline__ void gemm_tile(const float *A, int lda, int Kin, const float *__restrict__ B, int N,
+                                          const float *__restrict__ bias, float *C, int ldc, int act, float spb,
+                                          const float *aux, int ldaux) {
+    const int ncb = N >> 2;
+    const int items = (MT / 4) * ncb;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int rb = it / ncb, cb = it - rb * ncb;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) acc[i][o] = bias ? __ldg(bias + cb * 4 + o) : 0.f;
+        const float *a0 = A + (rb * 4) * lda;
+        for (int c = 0; c < Kin; c += 4) {
+            float4 av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(a0 + i * lda + c);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) bv[t] = __ldg(reinterpret_cast<const float4 *>(B + (size_t)(c + t) * N + cb * 4));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float ai[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    acc[i][0] = fmaf(ai[t], bv[t].x, acc[i][0]);
+                    acc[i][1] = fmaf(ai[t], bv[t].y, acc[i][1]);
+                    acc[i][2] = fmaf(ai[t], bv[t].z, acc[i][2]);
+                    acc[i][3] = fmaf(ai[t], bv[t].w, acc[i][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float v[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                float x = acc[i][o];
+                if (EPI == 1) x = act_f(act, x, spb);
+                if (EPI == 2) x *= act_da(act, aux[(rb * 4 + i) * ldaux + cb * 4 + o], spb);
+                v[o] = x;
+            }
+            *reinterpret_cast<float4 *>(C + (rb * 4 + i) * ldc + cb * 4) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp(DevModel m, const int32_t *__restrict__ perm,
+                                                     const int32_t *__restrict__ types, int64_t n,
+                                                     const float *__restrict__ G, float *__restrict__ dG,
+                                                     float *__restrict__ e_atom, double *__restrict__ part_e) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_atom[MT], s_type[MT];
+    __shared__ double s_e[MLP_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t p0 = (int64_t)blockIdx.x * MT;
+    if (tid < MT) {
+        const int64_t p = p0 + tid;
+        const int a = p < n ? perm[p] : -1;
+        s_atom[tid] = a;
+        s_type[tid] = a >= 0 ? types[a] : -1;
+    }
+    const int L = m.L, Dd = m.Dd;
+    int maxw = Dd;
+    for (int l = 1; l <= L; ++l) maxw = max(maxw, m.dims[l]);
+    // shared layout: act[0] (G tile), act[1..L], two ping-pong gradient buffers
+    float *act[MAX_LAYERS + 1];
+    int ld[MAX_LAYERS + 1];
+    float *ptr = sm;
+    for (int l = 0; l <= L; ++l) {
+        act[l] = ptr;
+        ld[l] = m.dims[l] + 4;
+        ptr += MT * ld[l];
+    }
+    const int ldz = maxw + 4;
+    float *dzA = ptr;
+    float *dzB = ptr + MT * ldz;
+    __syncthreads();
+    for (int idx = tid; idx < MT * (Dd / 4); idx += blockDim.x) {
+        const int r = idx / (Dd / 4), c4 = idx - r * (Dd / 4);
+        const int a = s_atom[r];
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a >= 0) v = *reinterpret_cast<const float4 *>(G + (size_t)a * Dd + c4 * 4);
+        *reinterpret_cast<float4 *>(act[0] + r * ld[0] + c4 * 4) = v;
+    }
+    __syncthreads();
+    int s_lo = TMD_MAX_SPECIES, s_hi = -1;
+    for (int r = 0; r < MT; ++r)
+        if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
+    double esum = 0.0;
+    for (int s = s_lo; s <= s_hi; ++s) {
+        const float *wf = m.wf[s], *wb = m.wb[s];
+        for (int l = 0; l < L; ++l) {
+            const int in = m.dims[l], out = m.dims[l + 1];
+            gemm_tile<1>(act[l], ld[l], in, wf + m.off_f[l], out, wf + m.off_f[l] + in * out, act[l + 1], ld[l + 1],
+                         m.act, m.sp_b, nullptr, 0);
+            __syncthreads();
+        }
+        // output layer (linear): E_r = b + w . a_L
+        const int wl = m.dims[L];
+        const float *wout = wb + m.off_b[L];
+        const float bout = __ldg(wf + m.off_f[L] + wl);
+        for (int r = warp; r < MT; r += MLP_THREADS / 32) {
+            float v = 0.f;
+            for (int c = lane; c < wl; c += 32) v = fmaf(act[L][r * ld[L] + c], __ldg(wout + c), v);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && s_type[r] == s) {
+                const float e = v + bout;
+                if (e_atom) e_atom[s_atom[r]] = e;
+                esum += (double)e;
+            }
+        }
+        // backward: dz_L = w_out * act'(a_L)
+        for (int idx = tid; idx < MT * wl; idx += blockDim.x) {
+            const int r = idx / wl, c = idx - r * wl;
+            dzA[r * ldz + c] = __ldg(wout + c) * act_da(m.act, act[L][r * ld[L] + c], m.sp_b);
+        }
+        __syncthreads();
+        float *cur = dzA, *nxt = dzB;
+        for (int l = L - 1; l >= 1; --l) {
+            // dz_l = (dz_{l+1} W_l) * act'(a_l)
+            gemm_tile<2>(cur, ldz, m.dims[l + 1], wb + m.off_b[l], m.dims[l], nullptr, nxt, ldz, m.act, m.sp_b,
+                         act[l], ld[l]);
+            __syncthreads();
+            float *t = cur; cur = nxt; nxt = t;
+        }
+        // G' = dz_1 W_0
+        gemm_tile<0>(cur, ldz, m.dims[1], wb + m.off_b[0], Dd, nullptr, nxt, ldz, m.act, m.sp_b, nullptr, 0);
+        __syncthreads();
+        for (int idx = tid; idx < MT * (Dd / 4); idx += blockDim.x) {
+            const int r = idx / (Dd / 4), c4 = idx - r * (Dd / 4);
+            if (s_type[r] == s)
+                *reinterpret_cast<float4 *>(dG + (size_t)s_atom[r] * Dd + c4 * 4) =
+                    *reinterpret_cast<const float4 *>(nxt + r * ldz + c4 * 4);
+        }
+        __syncthreads();
+    }
+    if (lane == 0) s_e[warp] = esum;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < MLP_THREADS / 32; ++w) t += s_e[w];
+        part_e[blockIdx.x] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward: P', pair gradients, ScatterSum, virial
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+template <int K, int S>
+__global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
+                                                   const int32_t *__restrict__ types, const float *__restrict__ Pin,
+                                                   const float *__restrict__ dG, float4 *__restrict__ F4,
+                                                   double *__restrict__ part_w) {
+    constexpr int KPL = K / 8;
+    constexpr int PSTR = K * NMOM + 4;   // per-species stride of P' (bank offset between species)
+    constexpr int Dd = S * K * 4;
+    __shared__ float4 s_rad[S * S * K];
+    __shared__ float4 s_q[PW][64];
+    __shared__ __align__(16) float s_Pd[PW][S * PSTR];
+    __shared__ double s_w[PW][9];
+    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = lane >> 2, g = lane & 3;
+    float Tg[5];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
+    float wsum[9], wcmp[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) { wsum[t] = 0.f; wcmp[t] = 0.f; }
+    float *sPd = s_Pd[warp];
+    const int64_t total = (int64_t)gridDim.x * PW;
+    for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
+        const int a = nl.perm[p];
+        const int ti = types[a];
+        const double xi = pos[3 * (int64_t)a], yi = pos[3 * (int64_t)a + 1], zi = pos[3 * (int64_t)a + 2];
+        // P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm; for m = 0: G'_bk0 sign(P)  (Eq. dP_abkd)
+        const float *Pa = Pin + (size_t)a * (S * K * NMOM);
+        const float *dGa = dG + (size_t)a * Dd;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk) {
+                const int k = kg * KPL + kk;
+                const float4 gm = *reinterpret_cast<const float4 *>(dGa + (s * K + k) * 4);
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) {
+                    const int d = 5 * g + dd;
+                    const float pv = Pa[(s * K + k) * NMOM + d];
+                    // rank of d: g==0 -> {0,1,1,1,2}, g==1 -> 2, g>=2 -> 3
+                    float gg;
+                    if (g == 0) gg = (dd == 0) ? gm.x : ((dd < 4) ? gm.y : gm.z);
+                    else gg = (g == 1) ? gm.z : gm.w;
+                    float v;
+                    if (g == 0 && dd == 0) v = (pv > 0.f) ? gg : ((pv < 0.f) ? -gg : 0.f);
+                    else v = 2.f * Tg[dd] * pv * gg;
+                    sPd[s * PSTR + k * NMOM + d] = v;
+                }
+            }
+        __syncwarp();
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2, s_q[warp], lane,
+                  [&](const float4 e, bool valid, int) {
+                      if (!valid) return;
+                      const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
+                      const float ir = rsqrtf(r2);
+                      const float r = r2 * ir;
+                      const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
+                      const uint32_t jb = __float_as_uint(e.w);
+                      const int b = (int)(jb >> 28);
+                      const int j = (int)(jb & 0x0FFFFFFFu);
+                      float H[K], dH[K], M[NMOM], V[NMOM];
+                      radial<K, true>(&s_rad[(ti * S + b) * K], r, m.inv_rc, H, dH);
+                      moments20(ux, uy, uz, M);
+#pragma unroll
+                      for (int d = 0; d < NMOM; ++d) V[d] = 0.f;
+                      float dEdr = 0.f;
+                      const float *Pb = sPd + b * PSTR;
+#pragma unroll
+                      for (int k = 0; k < K; ++k) {
+                          float U = 0.f;
+#pragma unroll
+                          for (int q4 = 0; q4 < NMOM / 4; ++q4) {
+                              const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
+                              U = fmaf(pd.x, M[4 * q4], U);
+                              U = fmaf(pd.y, M[4 * q4 + 1], U);
+                              U = fmaf(pd.z, M[4 * q4 + 2], U);
+                              U = fmaf(pd.w, M[4 * q4 + 3], U);
+                              V[4 * q4] = fmaf(pd.x, H[k], V[4 * q4]);
+                              V[4 * q4 + 1] = fmaf(pd.y, H[k], V[4 * q4 + 1]);
+                              V[4 * q4 + 2] = fmaf(pd.z, H[k], V[4 * q4 + 2]);
+                              V[4 * q4 + 3] = fmaf(pd.w, H[k], V[4 * q4 + 3]);
+                          }
+                          dEdr = fmaf(U, dH[k], dEdr);   // F1 = U H' R'
+                      }
+                      // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
+                      const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
+                      const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
+                                       2.f * xy * V[11] + 2.f * xz * V[12] + yy * V[13] + yz * V[14] + zz * V[15];
+                      const float gy = V[2] + ux * V[5] + 2.f * uy * V[7] + uz * V[8] + xx * V[11] + 2.f * xy * V[13] +
+                                       xz * V[14] + 3.f * yy * V[16] + 2.f * yz * V[17] + zz * V[18];
+                      const float gz = V[3] + ux * V[6] + uy * V[8] + 2.f * uz * V[9] + xx * V[12] + xy * V[14] +
+                                       2.f * xz * V[15] + yy * V[17] + 2.f * yz * V[18] + 3.f * zz * V[19];
+                      const float ug = ux * gx + uy * gy + uz * gz;
+                      // g_ij = dE/dD_ij = dE/dr u + (I - u u^T) dE/du / r
+                      const float gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
+                      const float gys = fmaf(dEdr, uy, (gy - uy * ug) * ir);
+                      const float gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
+                      fx += gxs; fy += gys; fz += gzs;
+                      atomicAdd(&F4[j], make_float4(-gxs, -gys, -gzs, 0.f));
+                      const float D[3] = {e.x, e.y, e.z};
+                      const float gv[3] = {gxs, gys, gzs};
+#pragma unroll
+                      for (int al = 0; al < 3; ++al)
+#pragma unroll
+                          for (int be = 0; be < 3; ++be) kahan_add(wsum[al * 3 + be], wcmp[al * 3 + be], -D[al] * gv[be]);
+                  });
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0) atomicAdd(&F4[a], make_float4(fx, fy, fz, 0.f));
+        __syncwarp();
+    }
+    // virial: per-lane compensated sums -> FP64 block total
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        double v = (double)wsum[t] - (double)wcmp[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_w[warp][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double v = 0.0;
+        for (int w = 0; w < PW; ++w) v += s_w[w][threadIdx.x];
+        part_w[(size_t)blockIdx.x * 9 + threadIdx.x] = v;
+    }
+}
+
+// FP64 totals of the block partials, fixed order (deterministic).
+__global__ void k_reduce(const double *__restrict__ part_e, int ne, const double *__restrict__ part_w, int nw,
+                         double *__restrict__ energy, double *__restrict__ virial) {
+    __shared__ double s[10][32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double v[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) v[t] = 0.0;
+    for (int i = tid; i < ne; i += blockDim.x) v[0] += part_e[i];
+    for (int i = tid; i < nw; i += blockDim.x)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) v[1 + t] += part_w[(size_t)i * 9 + t];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+        if (lane == 0) s[t][warp] = v[t];
+    }
+    __syncthreads();
+    if (tid < 10) {
+        double acc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += s[tid][w];
+        if (tid == 0) { if (energy) *energy = acc; }
+        else if (virial) virial[tid - 1] = acc;
+    }
+}
+
+__global__ void k_forces_out(const float4 *__restrict__ F4, int64_t n, float *__restrict__ forces) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float4 f = F4[i];
+        forces[3 * i] = f.x;
+        forces[3 * i + 1] = f.y;
+        forces[3 * i + 2] = f.z;
+    }
+}
+
+template <int K, int S>
+tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
+                               tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool forward) {
+    if (forward)
+        k_desc<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P);
+    else
+        k_force<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->F4, part_w);
+    TMD_CUDA(cudaGetLastError());
+    return TMD_OK;
+}
+
+tmd_status dispatch_pair(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
+                         tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool fwd) {
+#define TMD_CASE(KK, SS) \
+    if (dm.K == KK && dm.S == SS) return launch_pair_kernels<KK, SS>(dm, dn, pos, types, nl, part_w, nblk, s, fwd);
+    TMD_CASE(8, 1) TMD_CASE(8, 2) TMD_CASE(8, 3) TMD_CASE(8, 4)
+    TMD_CASE(16, 1) TMD_CASE(16, 2) TMD_CASE(16, 3) TMD_CASE(16, 4)
+    TMD_CASE(32, 1) TMD_CASE(32, 2) TMD_CASE(32, 3)
+#undef TMD_CASE
+    set_error("no kernel for K=%d S=%d", dm.K, dm.S);
+    return TMD_ERR_UNIMPLEMENTED;
+}
+
+int sm_count() {
+    static int count = 0;
+    if (!count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+        if (count <= 0) count = 132;
+    }
+    return count;
+}
+
+}  // namespace
+
+size_t mlp_smem_bytes(const DevModel &dm) {
+    int maxw = dm.Dd;
+    size_t fl = 0;
+    for (int l = 0; l <= dm.L; ++l) {
+        fl += (size_t)MT * (dm.dims[l] + 4);
+        maxw = std::max(maxw, dm.dims[l]);
+    }
+    fl += 2 * (size_t)MT * (maxw + 4);
+    return fl * sizeof(float);
+}
+
+tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
+                       const double box[3], double *energy, float *e_atom, float *forces, double *virial,
+                       cudaStream_t s) {
+    if (!model || !nl) {
+        set_error("null model or neighbour table");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (!nl->built || nl->n != n) {
+        set_error("neighbour table was built for %lld atoms, compute called with %lld", (long long)nl->n,
+                  (long long)n);
+        return TMD_ERR_INVALID_ARG;
+    }
+    const DevModel &dm = model->dm;
+    if (nl->r_list < (double)dm.rc * (1.0 - 1e-12)) {
+        set_error("neighbour table radius %.6g is below the model cutoff %.6g", nl->r_list, (double)dm.rc);
+        return TMD_ERR_INVALID_ARG;
+    }
+    for (int x = 0; x < 3; ++x)
+        if (box[x] != nl->box[x]) {
+            set_error("box differs from the one the neighbour table was built with");
+            return TMD_ERR_INVALID_ARG;
+        }
+    for (int t = dm.S; t < TMD_MAX_SPECIES; ++t)
+        if (nl->type_count[t] != 0) {
+            set_error("species id %d present but the model has %d species", t, dm.S);
+            return TMD_ERR_INVALID_ARG;
+        }
+    if (n == 0) {
+        if (energy) TMD_CUDA(cudaMemsetAsync(energy, 0, sizeof(double), s));
+        if (virial) TMD_CUDA(cudaMemsetAsync(virial, 0, 9 * sizeof(double), s));
+        return TMD_OK;
+    }
+    tmd_status st;
+    const int64_t Dd = dm.Dd;
+    if ((st = grow(&nl->G, &nl->cap_G, n * Dd)) != TMD_OK) return st;
+    if ((st = grow(&nl->dG, &nl->cap_dG, n * Dd)) != TMD_OK) return st;
+    if ((st = grow(&nl->P, &nl->cap_P, n * dm.S * dm.K * NMOM)) != TMD_OK) return st;
+    if ((st = grow(&nl->F4, &nl->cap_F4, n)) != TMD_OK) return st;
+    const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const int ntile = (int)((n + MT - 1) / MT);
+    if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
+    double *part_e = nl->part;
+    double *part_w = nl->part + ntile;
+
+    DevNlist dn;
+    dn.off = nl->off;
+    dn.nbr = nl->nbr;
+    dn.shift = nl->shift;
+    dn.perm = nl->perm;
+    dn.n = n;
+    for (int x = 0; x < 3; ++x) dn.box[x] = box[x];
+
+    TMD_CUDA(cudaMemsetAsync(nl->F4, 0, sizeof(float4) * n, s));
+    if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
+    const size_t smem = mlp_smem_bytes(dm);
+    static size_t smem_set = 0;
+    if (smem > 48 * 1024 && smem > smem_set) {
+        TMD_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        smem_set = smem;
+    }
+    k_mlp<<<ntile, MLP_THREADS, smem, s>>>(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e);
+    TMD_CUDA(cudaGetLastError());
+    if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, false)) != TMD_OK) return st;
+    k_reduce<<<1, 256, 0, s>>>(part_e, ntile, part_w, nblk, energy, virial);
+    TMD_CUDA(cudaGetLastError());
+    if (forces) {
+        k_forces_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nl->F4, n, forces);
+        TMD_CUDA(cudaGetLastError());
+    }
+    return TMD_OK;
+}
+
+}  // namespace tmd

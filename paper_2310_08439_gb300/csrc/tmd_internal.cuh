@@ -1,0 +1,159 @@
+// Internal declarations of the GB300 TensorMD library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "tmd.h"
+
+namespace tmd {
+
+constexpr int NMOM = 20;        // moment components d, ranks 0..3 (Eq. T_dm)
+constexpr int WARP = 32;
+constexpr int MAX_LAYERS = TMD_MAX_HIDDEN + 1;
+
+// Device status bits recorded by kernels, returned by synchronising calls.
+enum : int32_t {
+    DEV_ERR_OUTSIDE_BOX = 1,
+    DEV_ERR_BAD_TYPE = 2,
+    DEV_ERR_DEGREE = 4,
+    DEV_ERR_SHIFT = 8,
+};
+
+// Model as seen by kernels (passed by value).
+struct DevModel {
+    int S, K, L, act, Dd, nlayers, precision;
+    float rc, rc2, inv_rc, sp_b;
+    int dims[MAX_LAYERS + 1];           // Dd, widths..., 1
+    const float4 *radial;               // [S*S*K] (mu, eta*log2(e), 2*eta, 0)
+    const float *wf[TMD_MAX_SPECIES];   // forward: per layer W^T [in][out], then b [out]
+    const float *wb[TMD_MAX_SPECIES];   // backward: per layer W [out][in]
+    const uint16_t *hf[TMD_MAX_SPECIES]; // BF16 forward copy (same layout as wf, no bias)
+    const uint16_t *hb[TMD_MAX_SPECIES]; // BF16 backward copy (same layout as wb)
+    int off_f[MAX_LAYERS];              // offset of layer l in wf[s] / hf[s]
+    int off_b[MAX_LAYERS];              // offset of layer l in wb[s] / hb[s]
+};
+
+// Neighbour table as seen by kernels.
+struct DevNlist {
+    const int64_t *off;   // [n+1]
+    const int32_t *nbr;   // [nnz]
+    const char4 *shift;   // [nnz] (sx, sy, sz, species of j)
+    const int32_t *perm;  // [n] atoms grouped by species, index order within a species
+    double box[3];
+    int64_t n;
+};
+
+}  // namespace tmd
+
+struct tmd_model {
+    tmd::DevModel dm;
+    void *dev_block = nullptr;  // one allocation holding radial + all weights
+    size_t dev_bytes = 0;
+    int precision = TMD_PREC_FP32;
+};
+
+struct tmd_nlist {
+    // geometry of the last build
+    int64_t n = 0;
+    double box[3] = {0, 0, 0};
+    int32_t pbc[3] = {0, 0, 0};
+    double r_list = 0;
+    int nc[3] = {1, 1, 1};
+    int R[3] = {1, 1, 1};
+    int64_t ncell = 0;
+    int64_t nnz = 0;
+    int built = 0;
+    int32_t type_count[TMD_MAX_SPECIES] = {0, 0, 0, 0};
+
+    // device arrays (capacities in elements)
+    int32_t *cell_of = nullptr;      int64_t cap_atoms = 0;
+    int32_t *cell_atoms = nullptr;   int64_t cap_cell_atoms = 0;
+    float4 *cell_pos = nullptr;      int64_t cap_cell_pos = 0;
+    int32_t *perm = nullptr;         int64_t cap_perm = 0;
+    int64_t *off = nullptr;          int64_t cap_off = 0;
+    int32_t *cell_start = nullptr;   int64_t cap_cells = 0;
+    int32_t *cell_fill = nullptr;    int64_t cap_cell_fill = 0;
+    int32_t *nbr = nullptr;          int64_t cap_nnz = 0;
+    char4 *shift = nullptr;          int64_t cap_shift = 0;
+    int32_t *status = nullptr;       int64_t cap_status = 0;       // [1] device status bits
+    int32_t *type_block = nullptr;   int64_t cap_type_blocks = 0;  // [blocks][MAX_SPECIES]
+    int32_t *type_start = nullptr;   int64_t cap_type_start = 0;   // [MAX_SPECIES + 1]
+    int64_t *scan_tmp = nullptr;     int64_t cap_scan = 0;
+    int64_t *h_pinned = nullptr;     // host pinned scratch (16 int64)
+
+    // compute workspace
+    float *G = nullptr;       int64_t cap_G = 0;    // [n][Dd]
+    float *dG = nullptr;      int64_t cap_dG = 0;   // [n][Dd]
+    float *P = nullptr;       int64_t cap_P = 0;    // [n][S][K][20]
+    float4 *F4 = nullptr;     int64_t cap_F4 = 0;   // [n]
+    double *part = nullptr;   int64_t cap_part = 0; // block partial sums
+
+    // staging for the host-buffer entry point
+    double *io_pos = nullptr;   int64_t cap_io_pos = 0;
+    int32_t *io_types = nullptr; int64_t cap_io_types = 0;
+    float *io_forces = nullptr; int64_t cap_io_forces = 0;
+    double *io_red = nullptr;   int64_t cap_io_red = 0;   // energy + virial
+};
+
+struct tmd_system {
+    int64_t n = 0;
+    double box[3];
+    int32_t pbc[3];
+    double skin = 0;
+    double *pos = nullptr, *vel = nullptr, *pos_ref = nullptr, *inv_mass = nullptr, *mass = nullptr;
+    int32_t *types = nullptr;
+    float *forces = nullptr;
+    double *red = nullptr;       // [32] device reduction outputs (E, W, KE, max disp)
+    double *part = nullptr;      int64_t cap_part = 0;
+    double *h_red = nullptr;     // host pinned mirror of red
+    tmd_nlist nl;
+    int64_t step = 0, rebuilds = 0;
+    int need_rebuild = 1, have_forces = 0;
+};
+
+namespace tmd {
+
+// Thread-local error detail.
+void set_error(const char *fmt, ...);
+tmd_status cuda_fail(cudaError_t e, const char *what);
+
+#define TMD_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::tmd::cuda_fail(_e, #call);       \
+    } while (0)
+
+// Grow a device buffer to at least `need` elements (contents discarded).
+template <typename T>
+tmd_status grow(T **ptr, int64_t *cap, int64_t need) {
+    if (need <= *cap && *ptr) return TMD_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    int64_t n = need < 1 ? 1 : need;
+    n = n + n / 8 + 16;
+    cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * (size_t)n);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc of %lld bytes failed: %s", (long long)(sizeof(T) * n), cudaGetErrorString(e));
+        return TMD_ERR_OOM;
+    }
+    *cap = n;
+    return TMD_OK;
+}
+
+void nlist_free(tmd_nlist *nl);
+
+// Launchers (stream-ordered, no synchronisation unless stated).
+tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
+                           const int32_t pbc[3], double r_list, tmd_nlist *nl, cudaStream_t s);
+tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                       int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
+                       double *virial, cudaStream_t s);
+tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, cudaStream_t s);
+
+}  // namespace tmd

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libtmd.so (include/tmd.h).
+
+Argument marshalling only: every step of the energy / force / virial path runs
+in the CUDA library.  PyTorch supplies device memory and the current stream.
+There is no CPU fallback: if libtmd.so is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtmd.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "tmd.h")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNIMPLEMENTED = range(7)
+ACT = {"tanh": 0, "squareplus": 1}
+PREC = {"fp32": 0, "bf16": 1}
+
+_lib = None
+
+
+class TmdError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(what)
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_radial", C.c_int32), ("rc", C.c_double),
+                ("mu", C.POINTER(C.c_double)), ("eta", C.POINTER(C.c_double)),
+                ("n_hidden", C.c_int32), ("widths", C.POINTER(C.c_int32)),
+                ("weights", C.POINTER(C.POINTER(C.c_double))), ("activation", C.c_int32),
+                ("squareplus_b", C.c_double), ("precision", C.c_int32)]
+
+
+class Thermo(C.Structure):
+    _fields_ = [("e_pot", C.c_double), ("e_kin", C.c_double), ("temperature", C.c_double),
+                ("virial", C.c_double * 9), ("pressure", C.c_double * 9), ("step", C.c_int64),
+                ("rebuilds", C.c_int64)]
+
+    def as_dict(self):
+        return {"e_pot": self.e_pot, "e_kin": self.e_kin, "temperature": self.temperature,
+                "virial": np.array(self.virial[:]).reshape(3, 3),
+                "pressure": np.array(self.pressure[:]).reshape(3, 3),
+                "step": self.step, "rebuilds": self.rebuilds}
+
+
+_P = C.c_void_p
+_SIGS = {
+    "tmd_status_string": (C.c_char_p, [C.c_int]),
+    "tmd_last_error": (C.c_char_p, []),
+    "tmd_version": (C.c_char_p, []),
+    "tmd_model_create": (C.c_int, [C.POINTER(_Desc), C.POINTER(_P)]),
+    "tmd_model_destroy": (C.c_int, [_P]),
+    "tmd_model_set_precision": (C.c_int, [_P, C.c_int32]),
+    "tmd_nlist_create": (C.c_int, [C.POINTER(_P)]),
+    "tmd_nlist_destroy": (C.c_int, [_P]),
+    "tmd_neighbors": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                C.c_double, _P, _P]),
+    "tmd_nlist_size": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "tmd_nlist_export": (C.c_int, [_P, _P, _P, _P]),
+    "tmd_compute": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P, _P, _P, _P]),
+    "tmd_evaluate_host": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int32), _P, _P, _P, _P]),
+    "tmd_system_create": (C.c_int, [C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_double,
+                                    C.POINTER(_P)]),
+    "tmd_system_destroy": (C.c_int, [_P]),
+    "tmd_system_set_state": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, _P]),
+    "tmd_system_get_state": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P]),
+    "tmd_step": (C.c_int, [_P, _P, C.c_double, C.c_int32, C.c_int32, C.POINTER(Thermo), _P]),
+    "tmd_step_host": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32,
+                                C.POINTER(Thermo), _P]),
+}
+
+
+def lib():
+    """Load libtmd.so (built by ``paper_2310_08439_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2310_08439_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/tmd.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(tmd_\w+)\s*\(", txt, flags=re.M)))
+
+
+def check(status):
+    if status != OK:
+        L = lib()
+        raise TmdError(status, f"{L.tmd_status_string(status).decode()}: {L.tmd_last_error().decode()}")
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _box(box):
+    return (C.c_double * 3)(*[float(x) for x in box])
+
+
+def _pbc(pbc):
+    return (C.c_int32 * 3)(*[int(x) for x in pbc])
+
+
+class Model:
+    """Device copy of a potential (``inputs.ModelParams``)."""
+
+    def __init__(self, params, precision="fp32"):
+        self.params = params
+        S, K = params.n_species, params.n_radial
+        self._mu = np.ascontiguousarray(params.mu, dtype=np.float64).ravel()
+        self._eta = np.ascontiguousarray(params.eta, dtype=np.float64).ravel()
+        self._widths = np.ascontiguousarray(params.widths, dtype=np.int32)
+        self._w = [np.ascontiguousarray(w, dtype=np.float64) for w in params.weights]
+        wp = (C.POINTER(C.c_double) * S)(*[w.ctypes.data_as(C.POINTER(C.c_double)) for w in self._w])
+        d = _Desc(S, K, float(params.rc), self._mu.ctypes.data_as(C.POINTER(C.c_double)),
+                  self._eta.ctypes.data_as(C.POINTER(C.c_double)), len(params.widths),
+                  self._widths.ctypes.data_as(C.POINTER(C.c_int32)),
+                  C.cast(wp, C.POINTER(C.POINTER(C.c_double))), ACT[params.activation],
+                  float(params.squareplus_b), PREC[precision])
+        h = _P()
+        check(lib().tmd_model_create(C.byref(d), C.byref(h)))
+        self.handle = h
+        self.precision = precision
+
+    def set_precision(self, precision):
+        check(lib().tmd_model_set_precision(self.handle, PREC[precision]))
+        self.precision = precision
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tmd_model_destroy(self.handle)
+            self.handle = None
+
+
+class NeighborList:
+    """Device neighbour table + compute workspace (opaque tmd_nlist)."""
+
+    def __init__(self):
+        h = _P()
+        check(lib().tmd_nlist_create(C.byref(h)))
+        self.handle = h
+
+    def build(self, pos, types, box, pbc, r_list, stream=None):
+        """pos: cuda float64 [n,3]; types: cuda int32 [n]."""
+        check(lib().tmd_neighbors(_dptr(pos), _dptr(types), int(pos.shape[0]), _box(box), _pbc(pbc),
+                                  float(r_list), self.handle, _stream(stream)))
+        return self
+
+    def size(self):
+        n, nnz = C.c_int64(0), C.c_int64(0)
+        check(lib().tmd_nlist_size(self.handle, C.byref(n), C.byref(nnz)))
+        return n.value, nnz.value
+
+    def export(self):
+        n, nnz = self.size()
+        off = np.zeros(n + 1, dtype=np.int64)
+        nbr = np.zeros(max(nnz, 1), dtype=np.int32)
+        sh = np.zeros((max(nnz, 1), 3), dtype=np.int8)
+        check(lib().tmd_nlist_export(self.handle, off.ctypes.data_as(_P), nbr.ctypes.data_as(_P),
+                                     sh.ctypes.data_as(_P)))
+        return off, nbr[:nnz], sh[:nnz]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tmd_nlist_destroy(self.handle)
+            self.handle = None
+
+
+def compute(model, nl, pos, types, box, energy=None, e_atom=None, forces=None, virial=None, stream=None):
+    """tmd_compute into caller-provided cuda tensors (any may be None)."""
+    check(lib().tmd_compute(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box),
+                            _dptr(energy), _dptr(e_atom), _dptr(forces), _dptr(virial), _stream(stream)))
+
+
+def evaluate(model, nl, pos, types, box, stream=None):
+    """Allocate outputs and run tmd_compute; returns dict of cuda tensors."""
+    import torch
+    n = pos.shape[0]
+    dev = pos.device
+    out = {"energy": torch.zeros(1, dtype=torch.float64, device=dev),
+           "e_atom": torch.zeros(n, dtype=torch.float32, device=dev),
+           "forces": torch.zeros((n, 3), dtype=torch.float32, device=dev),
+           "virial": torch.zeros(9, dtype=torch.float64, device=dev)}
+    compute(model, nl, pos, types, box, out["energy"], out["e_atom"], out["forces"], out["virial"], stream)
+    return out
+
+
+def evaluate_host(model, nl, pos, types, box, pbc, energy, forces, virial, stream=None):
+    """tmd_evaluate_host with host numpy (or pinned torch CPU) buffers."""
+    def hp(a):
+        if a is None:
+            return None
+        return C.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data_as(_P)
+    check(lib().tmd_evaluate_host(model.handle, nl.handle, hp(pos), hp(types), int(pos.shape[0]), _box(box),
+                                  _pbc(pbc), hp(energy), hp(forces), hp(virial), _stream(stream)))
+
+
+class System:
+    """Resident MD state (opaque tmd_system)."""
+
+    def __init__(self, n, box, pbc, skin):
+        h = _P()
+        check(lib().tmd_system_create(int(n), _box(box), _pbc(pbc), float(skin), C.byref(h)))
+        self.handle = h
+        self.n = int(n)
+
+    def set_state(self, pos, vel, types, masses, stream=None):
+        """Tensors on the GPU (on_device) or numpy arrays (host)."""
+        on_dev = hasattr(pos, "is_cuda") and pos.is_cuda
+
+        def p(a):
+            if a is None:
+                return None
+            return C.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data_as(_P)
+        check(lib().tmd_system_set_state(self.handle, p(pos), p(vel), p(types), p(masses), int(on_dev),
+                                         _stream(stream)))
+
+    def get_state(self, stream=None):
+        pos = np.zeros((self.n, 3))
+        vel = np.zeros((self.n, 3))
+        f = np.zeros((self.n, 3), dtype=np.float32)
+        check(lib().tmd_system_get_state(self.handle, pos.ctypes.data_as(_P), vel.ctypes.data_as(_P),
+                                         f.ctypes.data_as(_P), 0, _stream(stream)))
+        return pos, vel, f
+
+    def step(self, model, dt, nsteps, rebuild_every=0, stream=None, thermo=True):
+        th = Thermo()
+        check(lib().tmd_step(model.handle, self.handle, float(dt), int(nsteps), int(rebuild_every),
+                             C.byref(th) if thermo else None, _stream(stream)))
+        return th.as_dict() if thermo else None
+
+    def step_host(self, model, pos, vel, forces, dt, nsteps, rebuild_every=0, stream=None):
+        def hp(a):
+            if a is None:
+                return None
+            return C.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data_as(_P)
+        th = Thermo()
+        check(lib().tmd_step_host(model.handle, self.handle, hp(pos), hp(vel), hp(forces), float(dt),
+                                  int(nsteps), int(rebuild_every), C.byref(th), _stream(stream)))
+        return th.as_dict()
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tmd_system_destroy(self.handle)
+            self.handle = None

@@ -1,0 +1,60 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/tmd.h declares, and host-side argument validation rejects bad input
+before any CUDA call."""
+import ctypes as C
+
+import pytest
+
+from paper_2310_08439_gb300 import build, tmd
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return tmd.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = tmd.header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(tmd._SIGS), "binding and header disagree"
+
+
+def test_status_strings_and_version(L):
+    assert L.tmd_status_string(0) == b"TMD_OK"
+    assert L.tmd_status_string(2) == b"TMD_ERR_CAPACITY"
+    assert L.tmd_status_string(99) == b"TMD_ERR_UNKNOWN"
+    assert b"sm_103a" in L.tmd_version()
+
+
+def test_model_create_rejects_bad_descriptors(L):
+    h = C.c_void_p()
+    assert L.tmd_model_create(None, C.byref(h)) == tmd.ERR_INVALID_ARG
+    d = tmd._Desc()
+    d.n_species = 0
+    assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_INVALID_ARG
+    assert b"n_species" in L.tmd_last_error()
+    d.n_species = 1
+    d.n_radial = 12
+    assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_UNIMPLEMENTED
+    d.n_radial = 16
+    d.rc = float("nan")
+    assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_INVALID_ARG
+    d.rc = 6.0
+    d.n_hidden = 9
+    assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_INVALID_ARG
+
+
+def test_neighbors_and_system_reject_bad_host_args(L):
+    box = (C.c_double * 3)(5.0, -1.0, 5.0)
+    pbc = (C.c_int32 * 3)(1, 1, 1)
+    assert L.tmd_neighbors(None, None, 4, box, pbc, 3.0, None, None) == tmd.ERR_INVALID_ARG
+    h = C.c_void_p()
+    assert L.tmd_system_create(10, box, pbc, 1.0, C.byref(h)) == tmd.ERR_INVALID_ARG
+    assert b"box[1]" in L.tmd_last_error()
+    box[1] = 5.0
+    assert L.tmd_system_create(0, box, pbc, 1.0, C.byref(h)) == tmd.ERR_INVALID_ARG
+    assert L.tmd_system_create(10, box, pbc, float("inf"), C.byref(h)) == tmd.ERR_INVALID_ARG
+    assert L.tmd_compute(None, None, None, None, 0, box, None, None, None, None, None) == tmd.ERR_INVALID_ARG
