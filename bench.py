@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark: TensorMD molecular-dynamics steps on one GB300 (or N replicas).
+
+One step = one velocity-Verlet step of the whole hot path: half kick + drift +
+wrap, cell binning and neighbour table rebuild, fused descriptor kernel,
+per-species network forward/backward, backward pair kernel with ScatterSum and
+virial, final reductions, second half kick.  The neighbour table is rebuilt
+every step inside the timed region.
+
+Default workload: the 1,048,576-atom fcc cell (64^3, a = 4.05 A, sigma = 0.1 A
+jitter, rc = 6 A, 1 A skin, K = 16, network 64-64-1 tanh, random weights).
+Inputs are larger than L2 (the neighbour table alone is ~0.7 GB).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+(the only reference implementation: the paper ships no code) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "force-eval atom-steps/s on 1 GB300 (plain FP32 vs BF16 form); serving p50/p99"
+UNIT = "atom-steps/s"
+CONV = 1.0 / 103.6427
+
+# algorithmic flops per in-cutoff pair (FMA = 2 flops), from the operation
+# counts of the tensor chain: forward P = sum H M (K x 20 FMA) + radial basis
+# (~8 per channel) + geometry/moments (~50); backward U and V (2 x K x 20 FMA),
+# H' (K FMA), radial basis with derivative (~10 per channel), M' contraction
+# and projection (~120), virial (~45).
+def fwd_flops_per_pair(K):
+    return 2 * 20 * K + 8 * K + 50
+
+
+def bwd_flops_per_pair(K):
+    return 2 * (2 * 20 * K + K) + 10 * K + 165
+
+
+def mlp_flops_per_atom(dims):
+    # forward + input-gradient backward: 2 GEMV passes of sum(in*out) FMAs
+    return 4 * sum(dims[i] * dims[i + 1] for i in range(len(dims) - 1))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(name):
+    """Per-launch DRAM bytes of ``name`` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2310_08439_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("csrc_sha256") != h.hexdigest():
+        return None
+    k = d.get("kernels", {}).get(name)
+    return None if k is None else k.get("bytes_per_launch_full")
+
+
+def workload(name):
+    from paper_2310_08439_gb300 import inputs as I
+    if name == "large":
+        w = I.large()
+        desc = ("large: 64^3 fcc bulk, 1,048,576 atoms, a=4.05 A, jitter 0.1 A, 1 species; rc 6 A, skin 1 A, "
+                "K=16, ranks 0-3, network 64-64-1 tanh (random init); velocity-Verlet dt=1 fs, "
+                "neighbour rebuild every step")
+    elif name == "medium":
+        w = I.medium()
+        desc = ("medium: 16^3 fcc bulk, 16,384 atoms, a=3.61 A, 2 species, jitter 0.1 A; rc 6 A, skin 1 A, "
+                "K=16, network 64-64-1 per species; velocity-Verlet dt=1 fs, neighbour rebuild every step")
+    else:
+        raise SystemExit(f"unknown config {name}")
+    return w, desc
+
+
+def oracle_sample_rate(wname, min_seconds=10.0, max_steps=50):
+    """Oracle MD steps (neighbours + energy/forces/virial + velocity-Verlet) on a
+    bounded sample of the workload: a 12^3 cell of the same lattice, model and
+    jitter (6,912 atoms).  Returns (atom-steps/s, threads, description)."""
+    from oracle import oracle as O
+    from paper_2310_08439_gb300 import inputs as I
+    w, _ = workload(wname)
+    if wname == "large":
+        sw = I.large(reps=12)
+        s = sw.systems[0]
+    else:
+        s = w.systems[0]
+    om = O.OracleModel(w.model)
+    pos, vel = s.pos.copy(), (s.vel.copy() if s.vel is not None else np.zeros_like(s.pos))
+    out = O.evaluate(om, pos, s.types, s.box, s.pbc)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        O.vv_first(pos, vel, out["forces"], s.masses, s.box, s.pbc, 1.0)
+        out = O.evaluate(om, pos, s.types, s.box, s.pbc)
+        O.vv_second(vel, out["forces"], s.masses, 1.0)
+        steps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    desc = (f"FP64 C oracle (OpenMP), {steps} full MD steps (O(N^2) neighbour search + evaluation + "
+            f"velocity-Verlet) on a {s.n}-atom cell of the same lattice/model")
+    return s.n * steps / dt, O.num_threads(), desc, s.n, steps, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2310_08439_gb300 import inputs as I
+    w, desc = workload(args.config)
+    sw = I.large(reps=12) if args.config == "large" else w
+    s = sw.systems[0]
+    om = O.OracleModel(w.model)
+    pos, vel = s.pos.copy(), (s.vel.copy() if s.vel is not None else np.zeros_like(s.pos))
+    out = O.evaluate(om, pos, s.types, s.box, s.pbc)
+
+    def step():
+        nonlocal out
+        O.vv_first(pos, vel, out["forces"], s.masses, s.box, s.pbc, 1.0)
+        out = O.evaluate(om, pos, s.types, s.box, s.pbc)
+        O.vv_second(vel, out["forces"], s.masses, 1.0)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = s.n * args.steps / dt
+    sample = f"{s.n}-atom cell of the same lattice and model, {args.steps} MD steps per run"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "reference": "FP64 CPU oracle (no code ships "
+                                            "with the paper)", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large", choices=["large", "medium"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2310_08439_gb300 import build as B
+    from paper_2310_08439_gb300 import tmd
+    B.build()
+    w, desc = workload(args.config)
+    s = w.systems[0]
+    n = s.n
+    model = tmd.Model(w.model, precision=args.precision)
+    sysm = tmd.System(n, s.box, s.pbc, skin=w.skin)
+    vel = s.vel if s.vel is not None else np.zeros_like(s.pos)
+    sysm.set_state(s.pos, vel, s.types, s.masses)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    tmd.profile_read(reset=True)
+    tmd.profile_enable(True)
+    launches0 = tmd.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = tmd.launch_count() - launches0
+    tmd.profile_enable(False)
+    kstats = tmd.profile_read(reset=True)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    value = world * n * args.steps / (elapsed_ms * 1e-3)
+
+    # end to end through the host-buffer C-ABI call (pinned host state)
+    e2e = None
+    if not args.no_e2e:
+        th = tmd.Thermo  # noqa: F841
+        pos_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        vel_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        f_h = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+        p_, v_, f_ = sysm.get_state()
+        pos_h.numpy()[:] = p_
+        vel_h.numpy()[:] = v_
+        f_h.numpy()[:] = f_
+        sysm.step_host(model, pos_h, vel_h, f_h, w.dt_fs, 1, rebuild_every=1)  # warm
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sysm.step_host(model, pos_h, vel_h, f_h, w.dt_fs, 1, rebuild_every=1)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+        e2e = {"value": world * n * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * (24 + 24 + 12)), "d2h_bytes_per_step": int(n * (24 + 24 + 12))}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel
+    peaks = load_peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = nsm * 128 * 2 * clk_mhz * 1e6 / 1e12  # TFLOP/s
+    # units: in-cutoff pairs of the configuration at the timed state
+    nl = tmd.NeighborList()
+    p_now, _, _ = sysm.get_state()
+    pos_d = torch.as_tensor(p_now, device=dev)
+    types_d = torch.as_tensor(s.types, device=dev)
+    nl.build(pos_d, types_d, s.box, s.pbc, w.model.rc)
+    pairs = nl.size()[1]          # entries inside rc = in-cutoff pairs
+    nl.build(pos_d, types_d, s.box, s.pbc, w.model.rc + w.skin)
+    K = w.model.n_radial
+    dims = [w.model.n_desc] + list(w.model.widths) + [1]
+    per_launch_flops = {"k_force": pairs * bwd_flops_per_pair(K), "k_desc": pairs * fwd_flops_per_pair(K),
+                        "k_mlp": n * mlp_flops_per_atom(dims)}
+    ranked = sorted(kstats.items(), key=lambda kv: -kv[1][1])
+    dom, (dl, dms) = ranked[0]
+    avg_ms = dms / max(dl, 1)
+    roof = None
+    if dom in per_launch_flops:
+        ach = per_launch_flops[dom] / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": kernel_traffic(dom),
+                "peak_source": f"FP32 FMA peak {nsm} SMs x 128 lanes x 2 flops x {clk_mhz:.0f} MHz "
+                               f"(max SM clock, {peaks['source']} peaks file)"}
+    total_ms = sum(v[1] for v in kstats.values())
+    kernels = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1), "share": v[1] / total_ms}
+               for k, v in ranked}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, cores, sdesc, sn, ssteps, sdt = oracle_sample_rate(args.config)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f32+bf16-network",
+            "data": "synthetic",
+            "config": {"workload": desc, "atoms_per_gpu": n, "precision": args.precision,
+                       "l2": "inputs larger than L2 (neighbour table ~%.2f GB, %d in-cutoff pairs)"
+                             % (nl.size()[1] * 8 / 1e9, pairs),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

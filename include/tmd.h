@@ -179,6 +179,15 @@ tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
                        double *virial, tmd_stream_t stream);
 
 /*
+ * Descriptor matrix only: G_abkm = sigma(T_dm (H_abck M_abcd)^2) (Eqs.
+ * tensor_formalism, sigma_function), written to G dev [n][Dd] FP32, row a,
+ * column ((b*K) + k)*4 + m.  Same arguments and errors as tmd_compute.
+ * Asynchronous.
+ */
+tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                           int64_t n, const double box[3], float *G, tmd_stream_t stream);
+
+/*
  * One force evaluation from host buffers: copies pos [n][3] FP64 and types
  * [n] int32 from host memory (pinned memory gives asynchronous copies),
  * builds the table with r_list = rc, runs tmd_compute, and copies energy
@@ -248,6 +257,26 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
 tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_host, double *vel_host,
                          float *forces_host, double dt_fs, int32_t nsteps, int32_t rebuild_every,
                          tmd_thermo *thermo, tmd_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Profiling (per-kernel CUDA-event timing, launch counting)                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    char name[32];      /* kernel name                                         */
+    int64_t launches;   /* launches recorded since the last reset              */
+    double total_ms;    /* summed device time between the events around them   */
+} tmd_kernel_stat;
+
+/* Enable (on != 0) or disable event recording around every kernel launch of
+ * the library.  The events are recorded on the launching stream, so the
+ * durations are device times of each launch. */
+tmd_status tmd_profile_enable(int32_t on);
+/* Collect the recorded launches: waits for their events, writes at most cap
+ * entries (one per kernel name that ran) and their number to *count, and
+ * clears the records when reset != 0.  Synchronises on the recorded events. */
+tmd_status tmd_profile_read(tmd_kernel_stat *out, int32_t cap, int32_t *count, int32_t reset);
+/* Total number of kernel launches issued by the library in this process. */
+int64_t tmd_launch_count(void);
 
 #ifdef __cplusplus
 }

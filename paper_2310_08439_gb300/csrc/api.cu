@@ -211,8 +211,11 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     std::vector<unsigned char> host(total, 0);
     float4 *rad = reinterpret_cast<float4 *>(host.data());
     const double log2e = 1.4426950408889634;
-    for (int i = 0; i < S * S * K; ++i)
-        rad[i] = make_float4((float)d->mu[i], (float)(d->eta[i] * log2e), (float)(2.0 * d->eta[i]), 0.f);
+    for (int i = 0; i < S * S * K; ++i) {
+        const float mu_hi = (float)d->mu[i];
+        const float mu_lo = (float)(d->mu[i] - (double)mu_hi);
+        rad[i] = make_float4(mu_hi, mu_lo, (float)(d->eta[i] * log2e), (float)(2.0 * d->eta[i]));
+    }
     tmd_model *m = new (std::nothrow) tmd_model();
     if (!m) { set_error("host allocation failed"); return TMD_ERR_OOM; }
     cudaError_t e = cudaMalloc(&m->dev_block, total);
@@ -223,6 +226,7 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     dm.S = S; dm.K = K; dm.L = L; dm.act = d->activation; dm.Dd = Dd; dm.nlayers = L + 1;
     dm.precision = d->precision;
     dm.rc = (float)d->rc; dm.rc2 = (float)(d->rc * d->rc); dm.inv_rc = (float)(1.0 / d->rc);
+    dm.rc2d = d->rc * d->rc;
     dm.sp_b = (float)d->squareplus_b;
     for (int l = 0; l <= L + 1; ++l) dm.dims[l] = dims[l];
     for (int l = 0; l <= L; ++l) { dm.off_f[l] = off_f[l]; dm.off_b[l] = off_b[l]; }
@@ -338,6 +342,13 @@ tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     return run_compute(model, nl, pos, types, n, box, energy, e_atom, forces, virial, (cudaStream_t)stream);
 }
 
+tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                           int64_t n, const double box[3], float *G, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!box || (n > 0 && (!pos || !types || !G))) { set_error("null box/pos/types/G"); return TMD_ERR_INVALID_ARG; }
+    return run_descriptors(model, nl, pos, types, n, box, G, (cudaStream_t)stream);
+}
+
 tmd_status tmd_evaluate_host(const tmd_model *model, tmd_nlist *nl, const double *pos_host, const int32_t *types_host,
                              int64_t n, const double box[3], const int32_t pbc[3], double *energy_host,
                              float *forces_host, double *virial_host, tmd_stream_t stream) {
@@ -432,7 +443,7 @@ tmd_status tmd_system_set_state(tmd_system *sys, const double *pos, const double
             for (int64_t i = 0; i < n; ++i)
                 if (!(masses[i] > 0.0 && std::isfinite(masses[i]))) { set_error("mass[%lld] must be > 0", (long long)i); return TMD_ERR_INVALID_ARG; }
         TMD_CUDA(cudaMemcpyAsync(sys->mass, masses, sizeof(double) * n, k, s));
-        k_inv_mass<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys->mass, sys->inv_mass, n);
+        TMD_LAUNCH("k_inv_mass", s, k_inv_mass<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys->mass, sys->inv_mass, n));
         TMD_CUDA(cudaGetLastError());
     }
     if (!on_device) TMD_CUDA(cudaStreamSynchronize(s));  // host arrays may be pageable and reused
@@ -487,9 +498,9 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
     const double lim = 0.5 * sys->skin;
     for (int it = 0; it < nsteps; ++it) {
         TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
-        k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n, dt_fs, sys->box[0],
+        TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n, dt_fs, sys->box[0],
                                       sys->box[1], sys->box[2], sys->pbc[0], sys->pbc[1], sys->pbc[2], sys->pos_ref,
-                                      lim * lim, flag);
+                                      lim * lim, flag));
         TMD_CUDA(cudaGetLastError());
         sys->step++;
         bool rebuild = sys->need_rebuild || (rebuild_every > 0 && (sys->step % rebuild_every) == 0);
@@ -501,14 +512,14 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
             rebuild = f != 0;
         }
         if ((st = rebuild_and_compute(model, sys, rebuild, s)) != TMD_OK) return st;
-        k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs);
+        TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
         TMD_CUDA(cudaGetLastError());
     }
     if (thermo) {
         const int kb = (int)std::min<int64_t>((n + 255) / 256, 1024);
         if ((st = grow(&sys->part, &sys->cap_part, 6 * (int64_t)kb)) != TMD_OK) return st;
-        k_kinetic<<<kb, 256, 0, s>>>(sys->vel, sys->mass, n, sys->part);
-        k_kinetic_total<<<1, 32, 0, s>>>(sys->part, kb, sys->red + 10);
+        TMD_LAUNCH("k_kinetic", s, k_kinetic<<<kb, 256, 0, s>>>(sys->vel, sys->mass, n, sys->part));
+        TMD_LAUNCH("k_kinetic_total", s, k_kinetic_total<<<1, 32, 0, s>>>(sys->part, kb, sys->red + 10));
         TMD_CUDA(cudaGetLastError());
         TMD_CUDA(cudaMemcpyAsync(sys->h_red, sys->red, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
         TMD_CUDA(cudaStreamSynchronize(s));

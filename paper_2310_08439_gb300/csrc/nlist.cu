@@ -311,7 +311,7 @@ tmd_status scan_inclusive(T *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, c
     if (n <= 0) return TMD_OK;
     const int64_t nb = (n + 2047) / 2048;
     if (nb == 1) {
-        k_scan_block<T><<<1, 1024, 0, s>>>(data, n, nullptr);
+        TMD_LAUNCH("k_scan_block", s, k_scan_block<T><<<1, 1024, 0, s>>>(data, n, nullptr));
         return TMD_OK;
     }
     if (level_start == 0) {
@@ -321,10 +321,10 @@ tmd_status scan_inclusive(T *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, c
         if (st != TMD_OK) return st;
     }
     T *sums = reinterpret_cast<T *>(*tmp + level_start);
-    k_scan_block<T><<<(unsigned)nb, 1024, 0, s>>>(data, n, sums);
+    TMD_LAUNCH("k_scan_block", s, k_scan_block<T><<<(unsigned)nb, 1024, 0, s>>>(data, n, sums));
     tmd_status st = scan_inclusive<T>(sums, nb, tmp, cap_tmp, s, level_start + nb + 8);
     if (st != TMD_OK) return st;
-    k_scan_add<T><<<(unsigned)(nb - 1), 256, 0, s>>>(data, n, sums);
+    TMD_LAUNCH("k_scan_add", s, k_scan_add<T><<<(unsigned)(nb - 1), 256, 0, s>>>(data, n, sums));
     return TMD_OK;
 }
 
@@ -410,16 +410,16 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
     TMD_CUDA(cudaMemsetAsync(nl->type_start, 0, sizeof(int32_t) * (TMD_MAX_SPECIES + 1), s));
 
     if (n > 0) {
-        k_bin<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, box[0], box[1], box[2], nl->nc[0],
+        TMD_LAUNCH("k_bin", s, k_bin<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, box[0], box[1], box[2], nl->nc[0],
                                                       nl->nc[1], nl->nc[2], nl->cell_of, nl->cell_start,
-                                                      nl->type_block, nl->status);
+                                                      nl->type_block, nl->status));
         TMD_CUDA(cudaGetLastError());
         if ((st = scan_inclusive<int32_t>(nl->cell_start + 1, nl->ncell, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK)
             return st;
-        k_type_scan<<<1, 32, 0, s>>>(nl->type_block, (int)nb_bin, nl->type_start);
-        k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start, nl->cell_fill,
+        TMD_LAUNCH("k_type_scan", s, k_type_scan<<<1, 32, 0, s>>>(nl->type_block, (int)nb_bin, nl->type_start));
+        TMD_LAUNCH("k_fill", s, k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start, nl->cell_fill,
                                                        nl->cell_atoms, nl->cell_pos, nl->type_block,
-                                                       nl->type_start, nl->perm);
+                                                       nl->type_start, nl->perm));
         TMD_CUDA(cudaGetLastError());
     }
 
@@ -455,7 +455,7 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
     p.status = nl->status;
     const unsigned nb_nbr = (unsigned)((n + NBR_WARPS - 1) / NBR_WARPS);
     if (n > 0) {
-        k_nbr<false><<<nb_nbr, NBR_WARPS * 32, 0, s>>>(p);
+        TMD_LAUNCH("k_nbr_count", s, k_nbr<false><<<nb_nbr, NBR_WARPS * 32, 0, s>>>(p));
         TMD_CUDA(cudaGetLastError());
         if ((st = scan_inclusive<int64_t>(nl->off + 1, n, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK) return st;
     }
@@ -493,7 +493,7 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
             TMD_CUDA(cudaFuncSetAttribute(k_nbr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        k_nbr<true><<<nb_nbr, NBR_WARPS * 32, smem, s>>>(p);
+        TMD_LAUNCH("k_nbr_fill", s, k_nbr<true><<<nb_nbr, NBR_WARPS * 32, smem, s>>>(p));
         TMD_CUDA(cudaGetLastError());
     }
     nl->nnz = nnz;

@@ -44,37 +44,47 @@ __device__ __forceinline__ void moments20(float x, float y, float z, float *M) {
     M[15] = x * M[9]; M[16] = M[7] * y; M[17] = M[7] * z; M[18] = y * M[9]; M[19] = M[9] * z;
 }
 
-// f_c and H_k (and dH_k/dr when DERIV) for r < rc; rad[k] = (mu, eta log2 e, 2 eta, 0).
+// f_c and H_k (and dH_k/dr when DERIV) for r < rc.  rad[k] = (mu_hi, mu_lo,
+// eta log2 e, 2 eta); r = r_hi + r_lo so that t = r - mu keeps ~FP64 accuracy
+// (the Gaussians are steep: dlnH/dr = -2 eta t amplifies any rounding of r).
 template <int K, bool DERIV>
-__device__ __forceinline__ void radial(const float4 *rad, float r, float inv_rc, float *H, float *dH) {
+__device__ __forceinline__ void radial(const float4 *rad, float r_hi, float r_lo, float inv_rc, float *H, float *dH) {
     float sn, cs;
-    sincospif(r * inv_rc, &sn, &cs);
+    sincospif(r_hi * inv_rc, &sn, &cs);
     const float fc = 0.5f * (cs + 1.f);
     const float dfc = -0.5f * PI_F * inv_rc * sn;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float4 p = rad[k];
-        const float t = r - p.x;
-        const float f = exp2f(-p.y * t * t);
+        const float t = (r_hi - p.x) + (r_lo - p.y);
+        const float f = exp2f(-p.z * t * t);
         H[k] = f * fc;
-        if (DERIV) dH[k] = fmaf(-p.z * t * f, fc, f * dfc);
+        if (DERIV) dH[k] = fmaf(-p.w * t * f, fc, f * dfc);
     }
 }
 
-// Walk the entries [beg, end) of one atom, keep pairs with r^2 < rc^2 and hand
-// them to f in batches of up to 32 (one per lane).  D = x_j + s L - x_i is
-// formed in FP64 and rounded to FP32.  The queue entry is (Dx, Dy, Dz, j | b<<28).
+// r = |D| as an unevaluated sum r_hi + r_lo from r^2 = r2_hi + r2_lo.
+__device__ __forceinline__ void split_sqrt(float r2_hi, float r2_lo, float &r_hi, float &r_lo, float &ir) {
+    r_hi = sqrtf(r2_hi);
+    ir = 1.f / r_hi;
+    r_lo = (fmaf(-r_hi, r_hi, r2_hi) + r2_lo) * 0.5f * ir;
+}
+
+// Walk the entries [beg, end) of one atom, keep pairs with r^2 < rc^2 (decided
+// in FP64, as the definition) and hand them to f in batches of up to 32 (one
+// per lane).  D = x_j + s L - x_i and r^2 are formed in FP64; the queue holds
+// (Dx, Dy, Dz, j | b<<28) in FP32 and r^2 as a hi/lo FP32 pair.
 template <typename F>
 __device__ __forceinline__ void for_pairs(const DevNlist &nl, const double *__restrict__ pos, int64_t beg,
-                                          int64_t end, double xi, double yi, double zi, float rc2,
-                                          float4 *q, int lane, F &&f) {
+                                          int64_t end, double xi, double yi, double zi, double rc2,
+                                          float4 *q, float2 *q2, int lane, F &&f) {
     int qn = 0;
     const unsigned lt = (1u << lane) - 1u;
     for (int64_t base = beg; base < end; base += 32) {
         const int64_t c = base + lane;
         bool v = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f;
-        uint32_t jb = 0;
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 e2 = make_float2(0.f, 0.f);
         if (c < end) {
             const int j = nl.nbr[c];
             const char4 s = nl.shift[c];
@@ -84,26 +94,33 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, const double *__re
             if (s.x) ex += (double)s.x * nl.box[0];
             if (s.y) ey += (double)s.y * nl.box[1];
             if (s.z) ez += (double)s.z * nl.box[2];
-            dx = (float)ex; dy = (float)ey; dz = (float)ez;
-            v = dx * dx + dy * dy + dz * dz < rc2;
-            jb = (uint32_t)j | ((uint32_t)s.w << 28);
+            const double r2 = ex * ex + ey * ey + ez * ez;
+            v = r2 < rc2;
+            const float r2h = (float)r2;
+            e = make_float4((float)ex, (float)ey, (float)ez, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
+            e2 = make_float2(r2h, (float)(r2 - (double)r2h));
         }
         const unsigned m = __ballot_sync(0xffffffffu, v);
-        if (v) q[qn + __popc(m & lt)] = make_float4(dx, dy, dz, __uint_as_float(jb));
+        if (v) {
+            const int slot = qn + __popc(m & lt);
+            q[slot] = e;
+            q2[slot] = e2;
+        }
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
-            const float4 e = q[lane];
-            f(e, true, 32);
+            f(q[lane], q2[lane], true, 32);
             __syncwarp();
-            if (lane < qn - 32) q[lane] = q[lane + 32];
+            if (lane < qn - 32) {
+                q[lane] = q[lane + 32];
+                q2[lane] = q2[lane + 32];
+            }
             __syncwarp();
             qn -= 32;
         }
     }
     if (qn > 0) {
-        const float4 e = q[lane];
-        f(e, lane < qn, qn);
+        f(q[lane], q2[lane], lane < qn, qn);
         __syncwarp();
     }
 }
@@ -121,6 +138,7 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
     constexpr int Dd = S * K * 4;
     __shared__ float4 s_rad[S * S * K];
     __shared__ float4 s_q[PW][64];
+    __shared__ float2 s_q2[PW][64];
     __shared__ __align__(16) float s_H[PW][32 * HS];
     __shared__ __align__(16) float s_M[PW][32 * MS];
     __shared__ int s_b[PW][32];
@@ -145,16 +163,15 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                 for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
         float *sH = s_H[warp];
         float *sM = s_M[warp];
-        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2, s_q[warp], lane,
-                  [&](const float4 e, bool valid, int nb) {
+        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2d, s_q[warp], s_q2[warp], lane,
+                  [&](const float4 e, const float2 e2, bool valid, int nb) {
                       if (valid) {
-                          const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
-                          const float ir = rsqrtf(r2);
-                          const float r = r2 * ir;
+                          float r_hi, r_lo, ir;
+                          split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
                           const uint32_t jb = __float_as_uint(e.w);
                           const int b = (int)(jb >> 28);
                           float H[K], M[NMOM];
-                          radial<K, false>(&s_rad[(ti * S + b) * K], r, m.inv_rc, H, nullptr);
+                          radial<K, false>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, nullptr);
                           moments20(e.x * ir, e.y * ir, e.z * ir, M);
 #pragma unroll
                           for (int k = 0; k < K; k += 4)
@@ -415,6 +432,7 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
     constexpr int Dd = S * K * 4;
     __shared__ float4 s_rad[S * S * K];
     __shared__ float4 s_q[PW][64];
+    __shared__ float2 s_q2[PW][64];
     __shared__ __align__(16) float s_Pd[PW][S * PSTR];
     __shared__ double s_w[PW][9];
     for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
@@ -458,18 +476,17 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
             }
         __syncwarp();
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2, s_q[warp], lane,
-                  [&](const float4 e, bool valid, int) {
+        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2d, s_q[warp], s_q2[warp], lane,
+                  [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
-                      const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
-                      const float ir = rsqrtf(r2);
-                      const float r = r2 * ir;
+                      float r_hi, r_lo, ir;
+                      split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
                       const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
                       const uint32_t jb = __float_as_uint(e.w);
                       const int b = (int)(jb >> 28);
                       const int j = (int)(jb & 0x0FFFFFFFu);
                       float H[K], dH[K], M[NMOM], V[NMOM];
-                      radial<K, true>(&s_rad[(ti * S + b) * K], r, m.inv_rc, H, dH);
+                      radial<K, true>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, dH);
                       moments20(ux, uy, uz, M);
 #pragma unroll
                       for (int d = 0; d < NMOM; ++d) V[d] = 0.f;
@@ -580,9 +597,9 @@ template <int K, int S>
 tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
                                tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool forward) {
     if (forward)
-        k_desc<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P);
+        TMD_LAUNCH("k_desc", s, k_desc<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
     else
-        k_force<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->F4, part_w);
+        TMD_LAUNCH("k_force", s, k_force<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->F4, part_w));
     TMD_CUDA(cudaGetLastError());
     return TMD_OK;
 }
@@ -623,9 +640,7 @@ size_t mlp_smem_bytes(const DevModel &dm) {
     return fl * sizeof(float);
 }
 
-tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
-                       const double box[3], double *energy, float *e_atom, float *forces, double *virial,
-                       cudaStream_t s) {
+static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, const double box[3]) {
     if (!model || !nl) {
         set_error("null model or neighbour table");
         return TMD_ERR_INVALID_ARG;
@@ -650,6 +665,42 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
             set_error("species id %d present but the model has %d species", t, dm.S);
             return TMD_ERR_INVALID_ARG;
         }
+    return TMD_OK;
+}
+
+static DevNlist dev_nlist(const tmd_nlist *nl, int64_t n, const double box[3]) {
+    DevNlist dn;
+    dn.off = nl->off;
+    dn.nbr = nl->nbr;
+    dn.shift = nl->shift;
+    dn.perm = nl->perm;
+    dn.n = n;
+    for (int x = 0; x < 3; ++x) dn.box[x] = box[x];
+    return dn;
+}
+
+tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                           int64_t n, const double box[3], float *G, cudaStream_t s) {
+    tmd_status st = validate(model, nl, n, box);
+    if (st != TMD_OK) return st;
+    if (n == 0) return TMD_OK;
+    const DevModel &dm = model->dm;
+    if ((st = grow(&nl->P, &nl->cap_P, n * dm.S * dm.K * NMOM)) != TMD_OK) return st;
+    const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const DevNlist dn = dev_nlist(nl, n, box);
+    float *keep = nl->G;
+    nl->G = G;
+    st = dispatch_pair(dm, dn, pos, types, nl, nullptr, nblk, s, true);
+    nl->G = keep;
+    return st;
+}
+
+tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
+                       const double box[3], double *energy, float *e_atom, float *forces, double *virial,
+                       cudaStream_t s) {
+    tmd_status st0 = validate(model, nl, n, box);
+    if (st0 != TMD_OK) return st0;
+    const DevModel &dm = model->dm;
     if (n == 0) {
         if (energy) TMD_CUDA(cudaMemsetAsync(energy, 0, sizeof(double), s));
         if (virial) TMD_CUDA(cudaMemsetAsync(virial, 0, 9 * sizeof(double), s));
@@ -667,13 +718,7 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     double *part_e = nl->part;
     double *part_w = nl->part + ntile;
 
-    DevNlist dn;
-    dn.off = nl->off;
-    dn.nbr = nl->nbr;
-    dn.shift = nl->shift;
-    dn.perm = nl->perm;
-    dn.n = n;
-    for (int x = 0; x < 3; ++x) dn.box[x] = box[x];
+    const DevNlist dn = dev_nlist(nl, n, box);
 
     TMD_CUDA(cudaMemsetAsync(nl->F4, 0, sizeof(float4) * n, s));
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
@@ -683,13 +728,13 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
         TMD_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         smem_set = smem;
     }
-    k_mlp<<<ntile, MLP_THREADS, smem, s>>>(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e);
+    TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, smem, s>>>(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e));
     TMD_CUDA(cudaGetLastError());
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, false)) != TMD_OK) return st;
-    k_reduce<<<1, 256, 0, s>>>(part_e, ntile, part_w, nblk, energy, virial);
+    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ntile, part_w, nblk, energy, virial));
     TMD_CUDA(cudaGetLastError());
     if (forces) {
-        k_forces_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nl->F4, n, forces);
+        TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nl->F4, n, forces));
         TMD_CUDA(cudaGetLastError());
     }
     return TMD_OK;

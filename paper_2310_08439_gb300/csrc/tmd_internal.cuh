@@ -26,8 +26,9 @@ enum : int32_t {
 struct DevModel {
     int S, K, L, act, Dd, nlayers, precision;
     float rc, rc2, inv_rc, sp_b;
+    double rc2d;                        // rc*rc in FP64 (cutoff decision)
     int dims[MAX_LAYERS + 1];           // Dd, widths..., 1
-    const float4 *radial;               // [S*S*K] (mu, eta*log2(e), 2*eta, 0)
+    const float4 *radial;               // [S*S*K] (mu_hi, mu_lo, eta*log2(e), 2*eta)
     const float *wf[TMD_MAX_SPECIES];   // forward: per layer W^T [in][out], then b [out]
     const float *wb[TMD_MAX_SPECIES];   // backward: per layer W [out][in]
     const uint16_t *hf[TMD_MAX_SPECIES]; // BF16 forward copy (same layout as wf, no bias)
@@ -116,6 +117,25 @@ struct tmd_system {
 
 namespace tmd {
 
+// Counts every kernel launch and, while profiling is enabled, records a pair
+// of events around it on the launching stream.
+class ProfScope {
+   public:
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+
+   private:
+    cudaStream_t stream_;
+    int kernel_;
+    cudaEvent_t start_;
+};
+
+#define TMD_LAUNCH(name, stream, ...)                   \
+    do {                                                \
+        ::tmd::ProfScope _prof_scope((name), (stream)); \
+        __VA_ARGS__;                                    \
+    } while (0)
+
 // Thread-local error detail.
 void set_error(const char *fmt, ...);
 tmd_status cuda_fail(cudaError_t e, const char *what);
@@ -154,6 +174,8 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                        int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
                        double *virial, cudaStream_t s);
+tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                           int64_t n, const double box[3], float *G, cudaStream_t s);
 tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, cudaStream_t s);
 
 }  // namespace tmd

@@ -64,6 +64,7 @@ _SIGS = {
     "tmd_nlist_size": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "tmd_nlist_export": (C.c_int, [_P, _P, _P, _P]),
     "tmd_compute": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P, _P, _P, _P]),
+    "tmd_descriptors": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P]),
     "tmd_evaluate_host": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int32), _P, _P, _P, _P]),
     "tmd_system_create": (C.c_int, [C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_double,
@@ -74,7 +75,30 @@ _SIGS = {
     "tmd_step": (C.c_int, [_P, _P, C.c_double, C.c_int32, C.c_int32, C.POINTER(Thermo), _P]),
     "tmd_step_host": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32,
                                 C.POINTER(Thermo), _P]),
+    "tmd_profile_enable": (C.c_int, [C.c_int32]),
+    "tmd_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
+    "tmd_launch_count": (C.c_int64, []),
 }
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+def profile_enable(on=True):
+    check(lib().tmd_profile_enable(1 if on else 0))
+
+
+def profile_read(reset=True):
+    """{kernel name: (launches, total device ms)} recorded since the last reset."""
+    arr = (KernelStat * 64)()
+    n = C.c_int32(0)
+    check(lib().tmd_profile_read(C.cast(arr, C.c_void_p), 64, C.byref(n), 1 if reset else 0))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def launch_count():
+    return int(lib().tmd_launch_count())
 
 
 def lib():
@@ -193,6 +217,15 @@ def compute(model, nl, pos, types, box, energy=None, e_atom=None, forces=None, v
     """tmd_compute into caller-provided cuda tensors (any may be None)."""
     check(lib().tmd_compute(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box),
                             _dptr(energy), _dptr(e_atom), _dptr(forces), _dptr(virial), _stream(stream)))
+
+
+def descriptors(model, nl, pos, types, box, stream=None):
+    """G [n, Dd] float32 cuda tensor (tmd_descriptors)."""
+    import torch
+    G = torch.zeros((pos.shape[0], model.params.n_desc), dtype=torch.float32, device=pos.device)
+    check(lib().tmd_descriptors(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box),
+                                _dptr(G), _stream(stream)))
+    return G
 
 
 def evaluate(model, nl, pos, types, box, stream=None):

@@ -357,3 +357,21 @@ def test_evaluate_host_matches_device(tmdlib):
     g = gpu_eval(tmdlib, w.model, s, r_list=6.0)
     assert e[0] == g["energy"]
     assert np.abs(f - g["forces"]).max() <= 1e-6 * np.abs(g["forces"]).max()
+
+
+@pytest.mark.parametrize("wname", ["tiny", "medium"])
+def test_descriptor_matrix_elementwise(tmdlib, wname):
+    """G_abkm element by element (Eq. tensor_formalism) against the oracle:
+    |dG| <= 1e-5 of the column's largest magnitude."""
+    torch = _torch()
+    w = getattr(I, wname)()
+    s = w.systems[0]
+    o = O.evaluate(O.OracleModel(w.model), s.pos, s.types, s.box, s.pbc, want_G=True)["G"]
+    m = tmdlib.Model(w.model)
+    nl, pos, types = gpu_nlist(tmdlib, s, w.model.rc + (0.0 if wname == "tiny" else 1.0))
+    G = tmdlib.descriptors(m, nl, pos, types, s.box)
+    torch.cuda.synchronize()
+    G = G.double().cpu().numpy()
+    scale = np.maximum(np.abs(o).max(axis=0), 1e-30)
+    err = (np.abs(G - o) / scale).max()
+    assert err <= 1e-5, err
