@@ -134,11 +134,11 @@ def kernel_traffic(name):
     return None if k is None else k.get("bytes_per_launch_full")
 
 
-def workload(name):
+def workload(name, reps=64):
     from paper_2310_08439_gb300 import inputs as I
     if name == "large":
-        w = I.large()
-        desc = ("large: 64^3 fcc bulk, 1,048,576 atoms, a=4.05 A, jitter 0.1 A, 1 species; rc 6 A, skin 1 A, "
+        w = I.large(reps=reps)
+        desc = (f"large: {reps}^3 fcc bulk, {w.systems[0].n:,} atoms, a=4.05 A, jitter 0.1 A, 1 species; rc 6 A, skin 1 A, "
                 "K=16, ranks 0-3, network 64-64-1 tanh (random init); velocity-Verlet dt=1 fs, "
                 "neighbour rebuild every step")
     elif name == "medium":
@@ -227,6 +227,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reps", type=int, default=64, help="fcc repeats of the large cell (64 = 1,048,576 atoms)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -249,7 +250,7 @@ def main():
     from paper_2310_08439_gb300 import build as B
     from paper_2310_08439_gb300 import tmd
     B.build()
-    w, desc = workload(args.config)
+    w, desc = workload(args.config, args.reps)
     s = w.systems[0]
     n = s.n
     model = tmd.Model(w.model, precision=args.precision)

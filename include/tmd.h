@@ -235,9 +235,12 @@ tmd_status tmd_system_get_state(const tmd_system *sys, double *pos, double *vel,
 
 /*
  * Advance nsteps velocity-Verlet steps of dt_fs femtoseconds:
- *   v += dt/2 F/m; x += dt v; wrap periodic axes; rebuild the table when
- *   rebuild_every > 0 and the step count is a multiple of it, or when any atom
- *   moved more than skin/2 since the last build; F = F(x); v += dt/2 F/m.
+ *   v += dt/2 F/m; x += dt v; rebuild the table when rebuild_every > 0 and
+ *   the step count is a multiple of it, or when any atom moved more than
+ *   skin/2 since the last build (a rebuild first wraps the positions into the
+ *   box); F = F(x); v += dt/2 F/m.  Between rebuilds positions are left
+ *   unwrapped (they may lie up to skin/2 outside the box), because the
+ *   table's image shifts refer to the positions at the last build.
  * (a = F/m * 1/103.6427 converts eV/(A amu) to A/fs^2.)  The first call after
  * set_state also computes the initial forces.  thermo (host, may be NULL)
  * receives the state after the last step.  Synchronises the stream once per

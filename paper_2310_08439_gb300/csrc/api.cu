@@ -34,32 +34,44 @@ namespace {
 constexpr double ACC_CONV = 1.0 / 103.6427;
 constexpr double KB_EV = 8.617333262e-5;
 
+// Half kick and drift.  Positions are not wrapped here: the neighbour table's
+// image shifts refer to the positions at the last build, so atoms move
+// continuously until the next rebuild, which wraps them first.
 __global__ void k_vv_first(double *__restrict__ pos, double *__restrict__ vel, const float *__restrict__ F,
-                           const double *__restrict__ inv_mass, int64_t n, double dt, double L0, double L1,
-                           double L2, int p0, int p1, int p2, const double *__restrict__ pos_ref, double lim2,
-                           int32_t *__restrict__ flag) {
+                           const double *__restrict__ inv_mass, int64_t n, double dt,
+                           const double *__restrict__ pos_ref, double lim2, int32_t *__restrict__ flag) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double L[3] = {L0, L1, L2};
-    const int pb[3] = {p0, p1, p2};
     const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
     double d2 = 0.0;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-        double v = vel[3 * i + x] + h * (double)F[3 * i + x];
-        double p = pos[3 * i + x] + dt * v;
-        if (pb[x]) {
-            p = p - floor(p / L[x]) * L[x];
-            if (p >= L[x]) p -= L[x];
-            if (p < 0.0) p += L[x];
-        }
+        const double v = vel[3 * i + x] + h * (double)F[3 * i + x];
+        const double p = pos[3 * i + x] + dt * v;
         vel[3 * i + x] = v;
         pos[3 * i + x] = p;
-        double d = p - pos_ref[3 * i + x];
-        if (pb[x]) d -= rint(d / L[x]) * L[x];
+        const double d = p - pos_ref[3 * i + x];
         d2 += d * d;
     }
     if (d2 > lim2) atomicOr(flag, 1);
+}
+
+// Wrap positions into [0, L) on periodic axes (before a neighbour rebuild).
+__global__ void k_wrap(double *__restrict__ pos, int64_t n, double L0, double L1, double L2, int p0, int p1,
+                       int p2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double L[3] = {L0, L1, L2};
+    const int pb[3] = {p0, p1, p2};
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        if (!pb[x]) continue;
+        double p = pos[3 * i + x];
+        p = p - floor(p / L[x]) * L[x];
+        if (p >= L[x]) p -= L[x];
+        if (p < 0.0) p += L[x];
+        pos[3 * i + x] = p;
+    }
 }
 
 __global__ void k_vv_second(double *__restrict__ vel, const float *__restrict__ F, const double *__restrict__ inv_mass,
@@ -471,6 +483,10 @@ static tmd_status rebuild_and_compute(const tmd_model *model, tmd_system *sys, b
     tmd_status st;
     if (rebuild) {
         const double r_list = (double)model->dm.rc + sys->skin;
+        const int64_t n = sys->n;
+        TMD_LAUNCH("k_wrap", s, k_wrap<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys->pos, n, sys->box[0], sys->box[1],
+                                                                                  sys->box[2], sys->pbc[0], sys->pbc[1],
+                                                                                  sys->pbc[2]));
         if ((st = build_neighbors(sys->pos, sys->types, sys->n, sys->box, sys->pbc, r_list, &sys->nl, s)) != TMD_OK)
             return st;
         TMD_CUDA(cudaMemcpyAsync(sys->pos_ref, sys->pos, sizeof(double) * 3 * sys->n, cudaMemcpyDeviceToDevice, s));
@@ -498,9 +514,8 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
     const double lim = 0.5 * sys->skin;
     for (int it = 0; it < nsteps; ++it) {
         TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
-        TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n, dt_fs, sys->box[0],
-                                      sys->box[1], sys->box[2], sys->pbc[0], sys->pbc[1], sys->pbc[2], sys->pos_ref,
-                                      lim * lim, flag));
+        TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n,
+                                                                  dt_fs, sys->pos_ref, lim * lim, flag));
         TMD_CUDA(cudaGetLastError());
         sys->step++;
         bool rebuild = sys->need_rebuild || (rebuild_every > 0 && (sys->step % rebuild_every) == 0);
