@@ -238,7 +238,8 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     dm.S = S; dm.K = K; dm.L = L; dm.act = d->activation; dm.Dd = Dd; dm.nlayers = L + 1;
     dm.precision = d->precision;
     dm.rc = (float)d->rc; dm.rc2 = (float)(d->rc * d->rc); dm.inv_rc = (float)(1.0 / d->rc);
-    dm.rc2d = d->rc * d->rc;
+    dm.rc2h = (float)(d->rc * d->rc);
+    dm.rc2l = (float)(d->rc * d->rc - (double)dm.rc2h);
     dm.sp_b = (float)d->squareplus_b;
     for (int l = 0; l <= L + 1; ++l) dm.dims[l] = dims[l];
     for (int l = 0; l <= L; ++l) { dm.off_f[l] = off_f[l]; dm.off_b[l] = off_b[l]; }

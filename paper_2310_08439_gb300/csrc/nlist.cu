@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
                 const bool self_img = (sx == 0 && sy == 0 && sz == 0);
                 for (int b = beg; b < end; b += 32) {
                     const int q = b + lane;
-                    bool in = false;
+                    bool in = false, band = false;
                     int j = 0, tj = 0;
                     if (q < end) {
                         const float4 cp = p.cell_pos[q];
@@ -199,17 +199,22 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
                         tj = (int)(w >> 28);
                         const float ddx = cp.x - xs, ddy = cp.y - ys, ddz = cp.z - zs;
                         const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (d2 < p.r2lo) {
-                            in = true;
-                        } else if (d2 < p.r2hi) {  // rounding band: exact FP64 decision
+                        in = d2 < p.r2lo;
+                        band = !in && d2 < p.r2hi;
+                    }
+                    // rounding band: exact FP64 decision.  Entered through a
+                    // warp-uniform branch so the (rare) FP64 work is not
+                    // predicated onto every candidate.
+                    if (__any_sync(0xffffffffu, band)) {
+                        if (band) {
                             const double ex = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j], __dmul_rn((double)sx, p.L[0])), xi);
                             const double ey = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j + 1], __dmul_rn((double)sy, p.L[1])), yi);
                             const double ez = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j + 2], __dmul_rn((double)sz, p.L[2])), zi);
                             const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
                             in = e2 < p.r2;
                         }
-                        if (self_img && j == (int)i) in = false;
                     }
+                    if (self_img && j == (int)i) in = false;
                     const unsigned m = __ballot_sync(0xffffffffu, in);
                     if (FILL && in) {
                         const int slot = count + __popc(m & lt);
@@ -336,7 +341,8 @@ tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *
 
 void nlist_free(tmd_nlist *nl) {
     void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->off, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
-                    nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->F4, nl->part};
+                    nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->F4, nl->part, nl->ph, nl->pl,
+                    nl->io_pos, nl->io_types, nl->io_forces, nl->io_red};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (nl->h_pinned) cudaFreeHost(nl->h_pinned);

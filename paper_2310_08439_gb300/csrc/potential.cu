@@ -70,16 +70,58 @@ __device__ __forceinline__ void split_sqrt(float r2_hi, float r2_lo, float &r_hi
     r_lo = (fmaf(-r_hi, r_hi, r2_hi) + r2_lo) * 0.5f * ir;
 }
 
-// Walk the entries [beg, end) of one atom, keep pairs with r^2 < rc^2 (decided
-// in FP64, as the definition) and hand them to f in batches of up to 32 (one
-// per lane).  D = x_j + s L - x_i and r^2 are formed in FP64; the queue holds
-// (Dx, Dy, Dz, j | b<<28) in FP32 and r^2 as a hi/lo FP32 pair.
+// Double-float helpers: a value is carried as an unevaluated sum hi + lo of two
+// floats.  two_sum is Knuth's error-free addition.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// D = (x_j + s L) - x_i on one axis from hi/lo positions and box length.
+__device__ __forceinline__ void diff_df(float xjh, float xjl, float xih, float xil, int s, float Lh, float Ll,
+                                        float &dh, float &dl) {
+    float u, e1;
+    two_sum(xjh, -xih, u, e1);
+    float lo = (xjl - xil) + e1;
+    if (s != 0) {
+        const float sf = (float)s;
+        const float p = sf * Lh;
+        const float pe = fmaf(sf, Lh, -p);  // exact error of the product
+        float v, e2;
+        two_sum(u, p, v, e2);
+        u = v;
+        lo += e2 + fmaf(sf, Ll, pe);
+    }
+    dh = u + lo;
+    dl = lo - (dh - u);
+}
+
+// |D|^2 as hi + lo from hi/lo components (exact products, error-free sums).
+__device__ __forceinline__ void norm2_df(float xh, float xl, float yh, float yl, float zh, float zl, float &r2h,
+                                         float &r2l) {
+    const float px = xh * xh, ex = fmaf(xh, xh, -px);
+    const float py = yh * yh, ey = fmaf(yh, yh, -py);
+    const float pz = zh * zh, ez = fmaf(zh, zh, -pz);
+    float s1, e1, s2, e2;
+    two_sum(px, py, s1, e1);
+    two_sum(s1, pz, s2, e2);
+    const float lo = ((ex + ey) + ez) + (e1 + e2) + 2.f * fmaf(xh, xl, fmaf(yh, yl, zh * zl));
+    r2h = s2 + lo;
+    r2l = lo - (r2h - s2);
+}
+
+// Walk the entries [beg, end) of atom a, keep pairs with r^2 < rc^2 and hand
+// them to f in batches of up to 32 (one per lane).  D = x_j + s L - x_i and r^2
+// are formed in double-float FP32 arithmetic from hi/lo positions (no FP64
+// instructions: on this GPU FP64 runs at a small fraction of the FP32 rate).
+// The queue holds (Dx, Dy, Dz, j | b<<28) rounded to FP32 and r^2 as hi/lo.
 template <typename F>
-__device__ __forceinline__ void for_pairs(const DevNlist &nl, const double *__restrict__ pos, int64_t beg,
-                                          int64_t end, double xi, double yi, double zi, double rc2,
+__device__ __forceinline__ void for_pairs(const DevNlist &nl, int a, int64_t beg, int64_t end, float rc2h, float rc2l,
                                           float4 *q, float2 *q2, int lane, F &&f) {
     int qn = 0;
     const unsigned lt = (1u << lane) - 1u;
+    const float4 ih = nl.ph[a], il = nl.pl[a];
     for (int64_t base = beg; base < end; base += 32) {
         const int64_t c = base + lane;
         bool v = false;
@@ -88,17 +130,15 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, const double *__re
         if (c < end) {
             const int j = nl.nbr[c];
             const char4 s = nl.shift[c];
-            double ex = pos[3 * (int64_t)j] - xi;
-            double ey = pos[3 * (int64_t)j + 1] - yi;
-            double ez = pos[3 * (int64_t)j + 2] - zi;
-            if (s.x) ex += (double)s.x * nl.box[0];
-            if (s.y) ey += (double)s.y * nl.box[1];
-            if (s.z) ez += (double)s.z * nl.box[2];
-            const double r2 = ex * ex + ey * ey + ez * ez;
-            v = r2 < rc2;
-            const float r2h = (float)r2;
-            e = make_float4((float)ex, (float)ey, (float)ez, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
-            e2 = make_float2(r2h, (float)(r2 - (double)r2h));
+            const float4 jh = nl.ph[j], jl = nl.pl[j];
+            float dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l;
+            diff_df(jh.x, jl.x, ih.x, il.x, s.x, nl.Lh[0], nl.Ll[0], dxh, dxl);
+            diff_df(jh.y, jl.y, ih.y, il.y, s.y, nl.Lh[1], nl.Ll[1], dyh, dyl);
+            diff_df(jh.z, jl.z, ih.z, il.z, s.z, nl.Lh[2], nl.Ll[2], dzh, dzl);
+            norm2_df(dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l);
+            v = (r2h < rc2h) || (r2h == rc2h && r2l < rc2l);
+            e = make_float4(dxh, dyh, dzh, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
+            e2 = make_float2(r2h, r2l);
         }
         const unsigned m = __ballot_sync(0xffffffffu, v);
         if (v) {
@@ -123,6 +163,17 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, const double *__re
         f(q[lane], q2[lane], lane < qn, qn);
         __syncwarp();
     }
+}
+
+// positions -> hi/lo FP32 pairs (once per evaluation)
+__global__ void k_split_pos(const double *__restrict__ pos, int64_t n, float4 *__restrict__ ph,
+                            float4 *__restrict__ pl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    const float xh = (float)x, yh = (float)y, zh = (float)z;
+    ph[i] = make_float4(xh, yh, zh, 0.f);
+    pl[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -153,7 +204,6 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
     for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
         const int a = nl.perm[p];
         const int ti = types[a];
-        const double xi = pos[3 * (int64_t)a], yi = pos[3 * (int64_t)a + 1], zi = pos[3 * (int64_t)a + 2];
         float acc[S][KPL][5];
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -163,7 +213,7 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                 for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
         float *sH = s_H[warp];
         float *sM = s_M[warp];
-        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2d, s_q[warp], s_q2[warp], lane,
+        for_pairs(nl, a, nl.off[a], nl.off[a + 1], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int nb) {
                       if (valid) {
                           float r_hi, r_lo, ir;
@@ -450,7 +500,6 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
     for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
         const int a = nl.perm[p];
         const int ti = types[a];
-        const double xi = pos[3 * (int64_t)a], yi = pos[3 * (int64_t)a + 1], zi = pos[3 * (int64_t)a + 2];
         // P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm; for m = 0: G'_bk0 sign(P)  (Eq. dP_abkd)
         const float *Pa = Pin + (size_t)a * (S * K * NMOM);
         const float *dGa = dG + (size_t)a * Dd;
@@ -476,7 +525,7 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
             }
         __syncwarp();
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for_pairs(nl, pos, nl.off[a], nl.off[a + 1], xi, yi, zi, m.rc2d, s_q[warp], s_q2[warp], lane,
+        for_pairs(nl, a, nl.off[a], nl.off[a + 1], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
                       float r_hi, r_lo, ir;
@@ -668,14 +717,29 @@ static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, con
     return TMD_OK;
 }
 
+static tmd_status split_positions(tmd_nlist *nl, const double *pos, int64_t n, cudaStream_t s) {
+    tmd_status st;
+    if ((st = grow(&nl->ph, &nl->cap_ph, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->pl, &nl->cap_pl, n)) != TMD_OK) return st;
+    TMD_LAUNCH("k_split_pos", s, k_split_pos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, nl->ph, nl->pl));
+    TMD_CUDA(cudaGetLastError());
+    return TMD_OK;
+}
+
 static DevNlist dev_nlist(const tmd_nlist *nl, int64_t n, const double box[3]) {
     DevNlist dn;
     dn.off = nl->off;
     dn.nbr = nl->nbr;
     dn.shift = nl->shift;
     dn.perm = nl->perm;
+    dn.ph = nl->ph;
+    dn.pl = nl->pl;
     dn.n = n;
-    for (int x = 0; x < 3; ++x) dn.box[x] = box[x];
+    for (int x = 0; x < 3; ++x) {
+        dn.box[x] = box[x];
+        dn.Lh[x] = (float)box[x];
+        dn.Ll[x] = (float)(box[x] - (double)dn.Lh[x]);
+    }
     return dn;
 }
 
@@ -687,6 +751,7 @@ tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
     const DevModel &dm = model->dm;
     if ((st = grow(&nl->P, &nl->cap_P, n * dm.S * dm.K * NMOM)) != TMD_OK) return st;
     const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
     const DevNlist dn = dev_nlist(nl, n, box);
     float *keep = nl->G;
     nl->G = G;
@@ -718,6 +783,7 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     double *part_e = nl->part;
     double *part_w = nl->part + ntile;
 
+    if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
     const DevNlist dn = dev_nlist(nl, n, box);
 
     TMD_CUDA(cudaMemsetAsync(nl->F4, 0, sizeof(float4) * n, s));

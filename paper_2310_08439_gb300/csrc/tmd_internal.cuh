@@ -26,7 +26,7 @@ enum : int32_t {
 struct DevModel {
     int S, K, L, act, Dd, nlayers, precision;
     float rc, rc2, inv_rc, sp_b;
-    double rc2d;                        // rc*rc in FP64 (cutoff decision)
+    float rc2h, rc2l;                   // rc*rc as hi + lo (cutoff decision)
     int dims[MAX_LAYERS + 1];           // Dd, widths..., 1
     const float4 *radial;               // [S*S*K] (mu_hi, mu_lo, eta*log2(e), 2*eta)
     const float *wf[TMD_MAX_SPECIES];   // forward: per layer W^T [in][out], then b [out]
@@ -43,7 +43,10 @@ struct DevNlist {
     const int32_t *nbr;   // [nnz]
     const char4 *shift;   // [nnz] (sx, sy, sz, species of j)
     const int32_t *perm;  // [n] atoms grouped by species, index order within a species
+    const float4 *ph;     // [n] positions, FP32 high part
+    const float4 *pl;     // [n] positions, FP32 low part (x = hi + lo)
     double box[3];
+    float Lh[3], Ll[3];   // box as hi + lo
     int64_t n;
 };
 
@@ -90,6 +93,8 @@ struct tmd_nlist {
     float *dG = nullptr;      int64_t cap_dG = 0;   // [n][Dd]
     float *P = nullptr;       int64_t cap_P = 0;    // [n][S][K][20]
     float4 *F4 = nullptr;     int64_t cap_F4 = 0;   // [n]
+    float4 *ph = nullptr;     int64_t cap_ph = 0;   // [n] positions hi
+    float4 *pl = nullptr;     int64_t cap_pl = 0;   // [n] positions lo
     double *part = nullptr;   int64_t cap_part = 0; // block partial sums
 
     // staging for the host-buffer entry point
