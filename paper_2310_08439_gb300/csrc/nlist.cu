@@ -151,6 +151,18 @@ __device__ __forceinline__ uint64_t make_key(int t, int j, int sx, int sy, int s
            ((uint64_t)(sy + 16) << 5) | (uint64_t)(sz + 16);
 }
 
+// The exact FP64 decision for a candidate inside the FP32 rounding band: the
+// definition's expression, evaluated without FMA.  Kept out of line so that the
+// compiler cannot predicate this (rarely needed) FP64 work onto every candidate.
+__device__ __noinline__ bool exact_inside(const double *__restrict__ pos, int j, int sx, int sy, int sz, double xi,
+                                          double yi, double zi, double L0, double L1, double L2, double r2) {
+    const double ex = __dsub_rn(__dadd_rn(pos[3 * (int64_t)j], __dmul_rn((double)sx, L0)), xi);
+    const double ey = __dsub_rn(__dadd_rn(pos[3 * (int64_t)j + 1], __dmul_rn((double)sy, L1)), yi);
+    const double ez = __dsub_rn(__dadd_rn(pos[3 * (int64_t)j + 2], __dmul_rn((double)sz, L2)), zi);
+    const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+    return e2 < r2;
+}
+
 template <bool FILL>
 __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
     extern __shared__ uint64_t s_keys[];
@@ -206,13 +218,7 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
                     // warp-uniform branch so the (rare) FP64 work is not
                     // predicated onto every candidate.
                     if (__any_sync(0xffffffffu, band)) {
-                        if (band) {
-                            const double ex = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j], __dmul_rn((double)sx, p.L[0])), xi);
-                            const double ey = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j + 1], __dmul_rn((double)sy, p.L[1])), yi);
-                            const double ez = __dsub_rn(__dadd_rn(p.pos[3 * (int64_t)j + 2], __dmul_rn((double)sz, p.L[2])), zi);
-                            const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-                            in = e2 < p.r2;
-                        }
+                        if (band) in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, p.L[0], p.L[1], p.L[2], p.r2);
                     }
                     if (self_img && j == (int)i) in = false;
                     const unsigned m = __ballot_sync(0xffffffffu, in);

@@ -129,15 +129,19 @@ def default_radial(n_species: int, n_radial: int, rc: float):
 
 
 def random_model(n_species, n_radial, rc, widths, seed, feature_scale=None,
-                 out_bias=-4.0, activation="tanh", masses=None, scale_floor=1e-2):
-    """W_l ~ N(0, 1/fan_in); first-layer columns divided by ``feature_scale``.
+                 out_bias=-4.0, activation="tanh", masses=None, scale_floor=1e-2, out_scale=0.1):
+    """W_l ~ N(0, 1/fan_in); first-layer columns divided by ``feature_scale``;
+    output layer ~ N(0, out_scale^2/fan_in).
 
     ``feature_scale`` ([S, Dd] or None) is the per-column RMS of the descriptor
     over the workload's initial configuration (a stored model statistic, the
     way trained potentials store input normalisation), floored at
     ``scale_floor`` so that nearly empty channels are not blown up.
     ``out_bias`` is the output-layer bias, a cohesive-energy-like offset in
-    eV/atom.
+    eV/atom.  ``out_scale`` = 0.1 gives forces of ~0.1 eV/A RMS on the jittered
+    lattices, like thermal forces of a metal near equilibrium; with 1.0 the
+    random potential drives 300 K runs of the medium cell to pair distances
+    below 1 A within 50 fs.
     """
     rng = np.random.default_rng(seed)
     mu, eta = default_radial(n_species, n_radial, rc)
@@ -149,6 +153,8 @@ def random_model(n_species, n_radial, rc, widths, seed, feature_scale=None,
         for l in range(len(dims) - 1):
             fan_in, fan_out = dims[l], dims[l + 1]
             W = rng.normal(0.0, 1.0 / math.sqrt(fan_in), size=(fan_out, fan_in))
+            if l == len(dims) - 2:
+                W = W * out_scale
             if l == 0 and feature_scale is not None:
                 sc = np.maximum(np.asarray(feature_scale[s], dtype=np.float64), scale_floor)
                 W = W / sc[None, :]
