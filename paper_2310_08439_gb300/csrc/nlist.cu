@@ -347,7 +347,7 @@ tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *
 
 void nlist_free(tmd_nlist *nl) {
     void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->off, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
-                    nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->F4, nl->part, nl->ph, nl->pl,
+                    nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->Fq, nl->part, nl->ph, nl->pl,
                     nl->io_pos, nl->io_types, nl->io_forces, nl->io_red};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -31,6 +31,8 @@ constexpr int PW = 4;           // warps per block in the pair kernels
 constexpr int MT = 32;          // atoms per network tile
 constexpr int MLP_THREADS = 128;
 constexpr float PI_F = 3.14159265358979323846f;
+constexpr float FQ_SCALE = 4294967296.0f;        // forces accumulate in units of 2^-32 eV/A
+constexpr double FQ_INV = 1.0 / 4294967296.0;
 
 // multiplicities T_d and ranks m(d) in the row order of Eq. T_dm:
 // 1 | x y z | xx xy xz yy yz zz | xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
@@ -475,7 +477,8 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 template <int K, int S>
 __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                    const int32_t *__restrict__ types, const float *__restrict__ Pin,
-                                                   const float *__restrict__ dG, float4 *__restrict__ F4,
+                                                   const float *__restrict__ dG,
+                                                   unsigned long long *__restrict__ Fq,
                                                    double *__restrict__ part_w) {
     constexpr int KPL = K / 8;
     constexpr int PSTR = K * NMOM + 4;   // per-species stride of P' (bank offset between species)
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
                 }
             }
         __syncwarp();
-        float fx = 0.f, fy = 0.f, fz = 0.f;
+        long long fx = 0, fy = 0, fz = 0;
         for_pairs(nl, a, nl.off[a], nl.off[a + 1], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
@@ -571,8 +574,15 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
                       const float gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
                       const float gys = fmaf(dEdr, uy, (gy - uy * ug) * ir);
                       const float gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
-                      fx += gxs; fy += gys; fz += gzs;
-                      atomicAdd(&F4[j], make_float4(-gxs, -gys, -gzs, 0.f));
+                      // ScatterSum in 2^-32 fixed point: integer adds are exact and
+                      // order independent, so forces are bitwise reproducible.
+                      const long long qx = __float2ll_rn(gxs * FQ_SCALE);
+                      const long long qy = __float2ll_rn(gys * FQ_SCALE);
+                      const long long qz = __float2ll_rn(gzs * FQ_SCALE);
+                      fx += qx; fy += qy; fz += qz;
+                      atomicAdd(&Fq[3 * (int64_t)j], (unsigned long long)(-qx));
+                      atomicAdd(&Fq[3 * (int64_t)j + 1], (unsigned long long)(-qy));
+                      atomicAdd(&Fq[3 * (int64_t)j + 2], (unsigned long long)(-qz));
                       const float D[3] = {e.x, e.y, e.z};
                       const float gv[3] = {gxs, gys, gzs};
 #pragma unroll
@@ -586,7 +596,11 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
             fy += __shfl_xor_sync(0xffffffffu, fy, o);
             fz += __shfl_xor_sync(0xffffffffu, fz, o);
         }
-        if (lane == 0) atomicAdd(&F4[a], make_float4(fx, fy, fz, 0.f));
+        if (lane == 0) {
+            atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fx);
+            atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fy);
+            atomicAdd(&Fq[3 * (int64_t)a + 2], (unsigned long long)fz);
+        }
         __syncwarp();
     }
     // virial: per-lane compensated sums -> FP64 block total
@@ -632,14 +646,9 @@ __global__ void k_reduce(const double *__restrict__ part_e, int ne, const double
     }
 }
 
-__global__ void k_forces_out(const float4 *__restrict__ F4, int64_t n, float *__restrict__ forces) {
+__global__ void k_forces_out(const long long *__restrict__ Fq, int64_t n, float *__restrict__ forces) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        const float4 f = F4[i];
-        forces[3 * i] = f.x;
-        forces[3 * i + 1] = f.y;
-        forces[3 * i + 2] = f.z;
-    }
+    if (i < 3 * n) forces[i] = (float)((double)Fq[i] * FQ_INV);
 }
 
 template <int K, int S>
@@ -648,7 +657,7 @@ tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const dou
     if (forward)
         TMD_LAUNCH("k_desc", s, k_desc<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
     else
-        TMD_LAUNCH("k_force", s, k_force<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->F4, part_w));
+        TMD_LAUNCH("k_force", s, k_force<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->Fq, part_w));
     TMD_CUDA(cudaGetLastError());
     return TMD_OK;
 }
@@ -776,7 +785,7 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     if ((st = grow(&nl->G, &nl->cap_G, n * Dd)) != TMD_OK) return st;
     if ((st = grow(&nl->dG, &nl->cap_dG, n * Dd)) != TMD_OK) return st;
     if ((st = grow(&nl->P, &nl->cap_P, n * dm.S * dm.K * NMOM)) != TMD_OK) return st;
-    if ((st = grow(&nl->F4, &nl->cap_F4, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * n)) != TMD_OK) return st;
     const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
     const int ntile = (int)((n + MT - 1) / MT);
     if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
@@ -786,7 +795,7 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
     const DevNlist dn = dev_nlist(nl, n, box);
 
-    TMD_CUDA(cudaMemsetAsync(nl->F4, 0, sizeof(float4) * n, s));
+    TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n, s));
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
     const size_t smem = mlp_smem_bytes(dm);
     static size_t smem_set = 0;
@@ -800,7 +809,8 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ntile, part_w, nblk, energy, virial));
     TMD_CUDA(cudaGetLastError());
     if (forces) {
-        TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nl->F4, n, forces));
+        TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
+                                           reinterpret_cast<const long long *>(nl->Fq), n, forces));
         TMD_CUDA(cudaGetLastError());
     }
     return TMD_OK;

@@ -92,7 +92,7 @@ struct tmd_nlist {
     float *G = nullptr;       int64_t cap_G = 0;    // [n][Dd]
     float *dG = nullptr;      int64_t cap_dG = 0;   // [n][Dd]
     float *P = nullptr;       int64_t cap_P = 0;    // [n][S][K][20]
-    float4 *F4 = nullptr;     int64_t cap_F4 = 0;   // [n]
+    unsigned long long *Fq = nullptr; int64_t cap_Fq = 0; // [n][3] forces, 2^-32 fixed point
     float4 *ph = nullptr;     int64_t cap_ph = 0;   // [n] positions hi
     float4 *pl = nullptr;     int64_t cap_pl = 0;   // [n] positions lo
     double *part = nullptr;   int64_t cap_part = 0; // block partial sums

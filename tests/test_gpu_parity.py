@@ -250,7 +250,8 @@ def test_compute_argument_errors(tmdlib):
 
 
 def test_deterministic_reruns(tmdlib):
-    """Energy and virial are reduced in a fixed order: bitwise repeatable."""
+    """Energy and virial are reduced in a fixed order and forces accumulate in
+    integer fixed point: every output is bitwise repeatable."""
     w = I.medium()
     s = w.systems[0]
     a = gpu_eval(tmdlib, w.model, s, r_list=7.0)
@@ -258,6 +259,7 @@ def test_deterministic_reruns(tmdlib):
     assert a["energy"] == b["energy"]
     assert np.array_equal(a["virial"], b["virial"])
     assert np.array_equal(a["e_atom"], b["e_atom"])
+    assert np.array_equal(a["forces"], b["forces"])
 
 
 # ------------------------------------------------------------------ full size (sampled)
@@ -341,8 +343,8 @@ def test_step_host_matches_device_path(tmdlib):
     # continue from host state, passing the resident forces back in
     _, _, forces = b.get_state()
     b.step_host(m, pos, vel, forces, 1.0, 4, rebuild_every=1)
-    # forces are summed with float atomics, so the two paths agree to rounding
-    assert np.abs(pos - pa).max() < 1e-8 and np.abs(vel - va).max() < 1e-8
+    # same arithmetic in both paths (forces are accumulated in fixed point)
+    assert np.abs(pos - pa).max() < 1e-12 and np.abs(vel - va).max() < 1e-12
 
 
 def test_evaluate_host_matches_device(tmdlib):
