@@ -179,13 +179,15 @@ tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
                        double *virial, tmd_stream_t stream);
 
 /*
- * Descriptor matrix only: G_abkm = sigma(T_dm (H_abck M_abcd)^2) (Eqs.
+ * Descriptor matrix G_abkm = sigma(T_dm (H_abck M_abcd)^2) (Eqs.
  * tensor_formalism, sigma_function), written to G dev [n][Dd] FP32, row a,
- * column ((b*K) + k)*4 + m.  Same arguments and errors as tmd_compute.
- * Asynchronous.
+ * column ((b*K) + k)*4 + m.  When dEdG (dev [n][Dd] FP32) is non-NULL the
+ * network is also run and its input gradient G'_abkm = dE_a/dG_abkm (the
+ * quantity the backward chain starts from) is written there.  Same arguments
+ * and errors as tmd_compute.  Asynchronous.
  */
 tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
-                           int64_t n, const double box[3], float *G, tmd_stream_t stream);
+                           int64_t n, const double box[3], float *G, float *dEdG, tmd_stream_t stream);
 
 /*
  * One force evaluation from host buffers: copies pos [n][3] FP64 and types

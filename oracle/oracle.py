@@ -185,7 +185,7 @@ def neighbors_of(pos, box, pbc, r_list, i):
 # energy / forces / virial
 # --------------------------------------------------------------------------
 def compute(model: OracleModel, pos, types, box, nl, want_G=False):
-    """E, E_a, F [n,3], W [3,3] (and G [n,Dd]) for a neighbour list ``nl``."""
+    """E, E_a, F [n,3], W [3,3] (and G, dE/dG [n,Dd]) for a neighbour list ``nl``."""
     off, nbr, shift = nl
     pos = _f64(pos)
     n = pos.shape[0]
@@ -202,12 +202,14 @@ def compute(model: OracleModel, pos, types, box, nl, want_G=False):
     F = np.zeros((n, 3))
     W = np.zeros(9)
     G = np.zeros((n, model.n_desc)) if want_G else None
+    dG = np.zeros((n, model.n_desc)) if want_G else None
     lib().tmdo_compute(C.byref(model.c), C.c_int64(n), _dp(pos), _ip(types), _dp(box), _lp(off),
                        _ip(nbr), _bp(shift), C.byref(E), _dp(ea), _dp(F), _dp(W),
-                       _dp(G) if want_G else None)
+                       _dp(G) if want_G else None, _dp(dG) if want_G else None)
     out = {"energy": E.value, "e_atom": ea, "forces": F, "virial": W.reshape(3, 3)}
     if want_G:
         out["G"] = G
+        out["dEdG"] = dG
     return out
 
 
@@ -229,7 +231,7 @@ def atom_terms(model: OracleModel, pos, types, box, a, nbr, shift, want_G=False)
     G = np.zeros(model.n_desc)
     Ea = lib().tmdo_atom_terms(C.byref(model.c), _dp(pos), _ip(types), _dp(box), C.c_int64(a),
                                C.c_int64(deg), _ip(nbr if deg else np.zeros(1, np.int32)),
-                               _bp(shift if deg else np.zeros((1, 3), np.int8)), _dp(G), _dp(g))
+                               _bp(shift if deg else np.zeros((1, 3), np.int8)), _dp(G), _dp(g), None)
     return (Ea, g[:deg], G) if want_G else (Ea, g[:deg])
 
 

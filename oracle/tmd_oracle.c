@@ -287,7 +287,7 @@ static double nnp(const tmdo_model *m, int s, const double *G, double *dEdG) {
 /* ------------------------------------------------------------------------- */
 double tmdo_atom_terms(const tmdo_model *m, const double *pos, const int32_t *types,
                        const double *box, int64_t a, int64_t deg, const int32_t *nbr,
-                       const int8_t *shift, double *G_out, double *g) {
+                       const int8_t *shift, double *G_out, double *g, double *dG_out) {
     const int S = m->S, K = m->K;
     const int D = S * K * MMAX;
     const int ti = types[a];
@@ -326,7 +326,8 @@ double tmdo_atom_terms(const tmdo_model *m, const double *pos, const int32_t *ty
                 G[((size_t)b * K + k) * MMAX + mm] = (mm == 0) ? sqrt(s) : s;
             }
     if (G_out) memcpy(G_out, G, sizeof(double) * D);
-    const double Ea = nnp(m, ti, G, g ? dG : NULL);
+    const double Ea = nnp(m, ti, G, (g || dG_out) ? dG : NULL);
+    if (dG_out) memcpy(dG_out, dG, sizeof(double) * D);
     if (g) {
         /* P' = 2 T sigma' P * dE/dG;  for m = 0: d|P|/dP = sign(P) */
         for (int b = 0; b < S; ++b)
@@ -385,12 +386,12 @@ double tmdo_atom_terms(const tmdo_model *m, const double *pos, const int32_t *ty
 /* ------------------------------------------------------------------------- */
 /* Whole-system evaluation: E, E_a, F_ax, virial (Sec. Tensor Formalism,     */
 /* E = sum_a E_a, F_ax = -G' dG/dr_ax, F = ScatterSum(F1 + F2)).             */
-/* forces / e_atom / virial / G / work may be NULL.  work (if given) holds   */
-/* the per-entry pair gradients, 3 x nnz.                                    */
+/* forces / e_atom / virial / G / dG may be NULL; dG receives dE_a/dG_a.    */
 /* ------------------------------------------------------------------------- */
 int tmdo_compute(const tmdo_model *m, int64_t n, const double *pos, const int32_t *types,
                  const double *box, const int64_t *off, const int32_t *nbr, const int8_t *shift,
-                 double *energy, double *e_atom, double *forces, double *virial, double *G) {
+                 double *energy, double *e_atom, double *forces, double *virial, double *G,
+                 double *dG) {
     const int D = m->S * m->K * MMAX;
     const int64_t nnz = off[n];
     double *g = (forces || virial) ? malloc(sizeof(double) * 3 * (size_t)(nnz > 0 ? nnz : 1)) : NULL;
@@ -399,7 +400,7 @@ int tmdo_compute(const tmdo_model *m, int64_t n, const double *pos, const int32_
     for (int64_t a = 0; a < n; ++a)
         ea[a] = tmdo_atom_terms(m, pos, types, box, a, off[a + 1] - off[a], nbr + off[a],
                                 shift + 3 * off[a], G ? G + (size_t)a * D : NULL,
-                                g ? g + 3 * off[a] : NULL);
+                                g ? g + 3 * off[a] : NULL, dG ? dG + (size_t)a * D : NULL);
     double E = 0.0;
     for (int64_t a = 0; a < n; ++a) E += ea[a];
     if (energy) *energy = E;

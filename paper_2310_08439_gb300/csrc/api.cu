@@ -356,10 +356,10 @@ tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
 }
 
 tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
-                           int64_t n, const double box[3], float *G, tmd_stream_t stream) {
+                           int64_t n, const double box[3], float *G, float *dEdG, tmd_stream_t stream) {
     g_err[0] = 0;
     if (!box || (n > 0 && (!pos || !types || !G))) { set_error("null box/pos/types/G"); return TMD_ERR_INVALID_ARG; }
-    return run_descriptors(model, nl, pos, types, n, box, G, (cudaStream_t)stream);
+    return run_descriptors(model, nl, pos, types, n, box, G, dEdG, (cudaStream_t)stream);
 }
 
 tmd_status tmd_evaluate_host(const tmd_model *model, tmd_nlist *nl, const double *pos_host, const int32_t *types_host,

@@ -726,6 +726,16 @@ static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, con
     return TMD_OK;
 }
 
+static tmd_status set_mlp_smem(const DevModel &dm) {
+    static size_t smem_set = 0;
+    const size_t smem = mlp_smem_bytes(dm);
+    if (smem > 48 * 1024 && smem > smem_set) {
+        TMD_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        smem_set = smem;
+    }
+    return TMD_OK;
+}
+
 static tmd_status split_positions(tmd_nlist *nl, const double *pos, int64_t n, cudaStream_t s) {
     tmd_status st;
     if ((st = grow(&nl->ph, &nl->cap_ph, n)) != TMD_OK) return st;
@@ -753,7 +763,7 @@ static DevNlist dev_nlist(const tmd_nlist *nl, int64_t n, const double box[3]) {
 }
 
 tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
-                           int64_t n, const double box[3], float *G, cudaStream_t s) {
+                           int64_t n, const double box[3], float *G, float *dEdG, cudaStream_t s) {
     tmd_status st = validate(model, nl, n, box);
     if (st != TMD_OK) return st;
     if (n == 0) return TMD_OK;
@@ -766,7 +776,14 @@ tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
     nl->G = G;
     st = dispatch_pair(dm, dn, pos, types, nl, nullptr, nblk, s, true);
     nl->G = keep;
-    return st;
+    if (st != TMD_OK || !dEdG) return st;
+    const int ntile = (int)((n + MT - 1) / MT);
+    if ((st = grow(&nl->part, &nl->cap_part, ntile + 16)) != TMD_OK) return st;
+    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
+    TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, nl->perm, types, n, G, dEdG,
+                                                                                 nullptr, nl->part));
+    TMD_CUDA(cudaGetLastError());
+    return TMD_OK;
 }
 
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
@@ -798,11 +815,7 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n, s));
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
     const size_t smem = mlp_smem_bytes(dm);
-    static size_t smem_set = 0;
-    if (smem > 48 * 1024 && smem > smem_set) {
-        TMD_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-    }
+    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
     TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, smem, s>>>(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e));
     TMD_CUDA(cudaGetLastError());
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, false)) != TMD_OK) return st;

@@ -64,7 +64,7 @@ _SIGS = {
     "tmd_nlist_size": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "tmd_nlist_export": (C.c_int, [_P, _P, _P, _P]),
     "tmd_compute": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P, _P, _P, _P]),
-    "tmd_descriptors": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P]),
+    "tmd_descriptors": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P, _P]),
     "tmd_evaluate_host": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int32), _P, _P, _P, _P]),
     "tmd_system_create": (C.c_int, [C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_double,
@@ -219,13 +219,14 @@ def compute(model, nl, pos, types, box, energy=None, e_atom=None, forces=None, v
                             _dptr(energy), _dptr(e_atom), _dptr(forces), _dptr(virial), _stream(stream)))
 
 
-def descriptors(model, nl, pos, types, box, stream=None):
-    """G [n, Dd] float32 cuda tensor (tmd_descriptors)."""
+def descriptors(model, nl, pos, types, box, stream=None, with_grad=False):
+    """G [n, Dd] float32 cuda tensor (tmd_descriptors); with_grad also returns dE/dG."""
     import torch
     G = torch.zeros((pos.shape[0], model.params.n_desc), dtype=torch.float32, device=pos.device)
+    dG = torch.zeros_like(G) if with_grad else None
     check(lib().tmd_descriptors(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box),
-                                _dptr(G), _stream(stream)))
-    return G
+                                _dptr(G), _dptr(dG), _stream(stream)))
+    return (G, dG) if with_grad else G
 
 
 def evaluate(model, nl, pos, types, box, stream=None):
