@@ -190,6 +190,34 @@ tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
                            int64_t n, const double box[3], float *G, float *dEdG, tmd_stream_t stream);
 
 /*
+ * tmd_compute without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they run (codes that give all GPU memory to their own pool allocator
+ * at start-up, or that must not allocate, or synchronise on an allocation,
+ * inside their time-stepping loop).  The caller supplies the neighbour table
+ * and every input and output; all scratch comes from one static device array
+ * of 64 MiB (held by every GPU that loads the library until the process
+ * exits), which bounds n: about 34,000 atoms for S=1, K=16 and about 18,000
+ * for S=2, K=16 (beyond the bound the call returns TMD_ERR_CAPACITY before
+ * touching the GPU).
+ *  off      dev [n+1] int64 CSR offsets, off[0] = 0, off[n] = nnz.
+ *  nbr      dev [nnz] int32 neighbour ids in [0, n).
+ *  shift4   dev [nnz][4] int8 (sx, sy, sz, species of j), 4-byte aligned;
+ *           the table must hold every pair closer than rc (entries beyond rc
+ *           are skipped).
+ *  pos, types, box, energy, e_atom, forces, virial: as tmd_compute.
+ * The first call on a device looks up the array's device address (make that
+ * first call before any stream capture).  Each call checks the table and the
+ * species on the device and synchronises the stream once to read the verdict
+ * (TMD_ERR_INVALID_ARG on a bad table).  Every call shares the one array and
+ * clears what must start at zero; calls that overlap on the GPU (several
+ * streams or threads at once) race on it and must be serialised by the caller.
+ */
+tmd_status tmd_compute_noalloc(const tmd_model *model, const int64_t *off, const int32_t *nbr, const int8_t *shift4,
+                               int64_t nnz, const double *pos, const int32_t *types, int64_t n, const double box[3],
+                               double *energy, float *e_atom, float *forces, double *virial, tmd_stream_t stream);
+
+/*
  * One force evaluation from host buffers: copies pos [n][3] FP64 and types
  * [n] int32 from host memory (pinned memory gives asynchronous copies),
  * builds the table with r_list = rc, runs tmd_compute, and copies energy

@@ -362,6 +362,14 @@ tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
     return run_descriptors(model, nl, pos, types, n, box, G, dEdG, (cudaStream_t)stream);
 }
 
+tmd_status tmd_compute_noalloc(const tmd_model *model, const int64_t *off, const int32_t *nbr, const int8_t *shift4,
+                               int64_t nnz, const double *pos, const int32_t *types, int64_t n, const double box[3],
+                               double *energy, float *e_atom, float *forces, double *virial, tmd_stream_t stream) {
+    g_err[0] = 0;
+    return run_compute_noalloc(model, off, nbr, shift4, nnz, pos, types, n, box, energy, e_atom, forces, virial,
+                               (cudaStream_t)stream);
+}
+
 tmd_status tmd_evaluate_host(const tmd_model *model, tmd_nlist *nl, const double *pos_host, const int32_t *types_host,
                              int64_t n, const double box[3], const int32_t pbc[3], double *energy_host,
                              float *forces_host, double *virial_host, tmd_stream_t stream) {

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "tmd_internal.cuh"
 
@@ -824,6 +825,197 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     if (forces) {
         TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
                                            reinterpret_cast<const long long *>(nl->Fq), n, forces));
+        TMD_CUDA(cudaGetLastError());
+    }
+    return TMD_OK;
+}
+
+}  // namespace tmd
+
+// ---------------------------------------------------------------------------
+// Allocation-free force evaluation (tmd_compute_noalloc).
+//
+// For callers that cannot allocate device memory while they run: codes that
+// hand all GPU memory to their own pool allocator up front, or that must not
+// pay for or synchronise on an allocation inside their time-stepping loop.
+// The caller passes the neighbour table and every input and output; all
+// scratch (position split, identity atom order, P, G, G', fixed-point force
+// accumulator, block partials) lives in one static device array, which every
+// GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace tmd {
+
+namespace {
+
+constexpr size_t NOALLOC_BYTES = size_t(64) << 20;  // 64 MiB of scratch per device
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256] = {nullptr};
+
+__global__ void k_iota(int32_t *__restrict__ perm, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[i] = (int32_t)i;
+}
+
+// Checks the caller's table and species (the kernels index per-species
+// tables with them) and records a violation in *flag.
+__global__ void k_noalloc_check(const int64_t *__restrict__ off, const int32_t *__restrict__ nbr,
+                                const char4 *__restrict__ shift, const int32_t *__restrict__ types, int64_t n,
+                                int64_t nnz, int S, int32_t *__restrict__ flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(flag, 1);
+    for (int64_t i = t0; i < n; i += stride) {
+        if (off[i + 1] < off[i]) atomicOr(flag, 1);
+        if (types[i] < 0 || types[i] >= S) atomicOr(flag, 2);
+    }
+    for (int64_t c = t0; c < nnz; c += stride) {
+        if (nbr[c] < 0 || nbr[c] >= n) atomicOr(flag, 4);
+        if (shift[c].w < 0 || shift[c].w >= S) atomicOr(flag, 8);
+    }
+}
+
+}  // namespace
+
+tmd_status noalloc_capacity(const tmd_model *model, int64_t n, size_t *need) {
+    const DevModel &dm = model->dm;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const int64_t nblk = std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const int64_t ntile = (n + MT - 1) / MT;
+    size_t b = 0;
+    b += al(sizeof(int32_t) * n);                              // identity order
+    b += 2 * al(sizeof(float4) * n);                           // positions hi / lo
+    b += al(sizeof(float) * n * dm.S * dm.K * NMOM);           // P
+    b += 2 * al(sizeof(float) * n * dm.Dd);                    // G, G'
+    b += al(sizeof(unsigned long long) * 3 * n);               // force accumulator
+    b += al(sizeof(double) * (ntile + 9 * nblk + 16));         // block partials
+    b += al(sizeof(int32_t) * 4);                              // check flag
+    *need = b;
+    return b <= NOALLOC_BYTES ? TMD_OK : TMD_ERR_CAPACITY;
+}
+
+tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const int32_t *nbr, const int8_t *shift4,
+                               int64_t nnz, const double *pos, const int32_t *types, int64_t n, const double box[3],
+                               double *energy, float *e_atom, float *forces, double *virial, cudaStream_t s) {
+    if (!model || !box) {
+        set_error("null model or box");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (n < 0 || n >= (int64_t(1) << 28) || nnz < 0) {
+        set_error("n = %lld or nnz = %lld out of range", (long long)n, (long long)nnz);
+        return TMD_ERR_INVALID_ARG;
+    }
+    for (int x = 0; x < 3; ++x)
+        if (!(std::isfinite(box[x]) && box[x] > 0.0)) {
+            set_error("box[%d] must be finite and > 0", x);
+            return TMD_ERR_INVALID_ARG;
+        }
+    if (n > 0 && (!off || !pos || !types || (nnz > 0 && (!nbr || !shift4)))) {
+        set_error("null off/nbr/shift4/pos/types");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(shift4) & 3) != 0) {
+        set_error("shift4 must be 4-byte aligned");
+        return TMD_ERR_INVALID_ARG;
+    }
+    size_t need = 0;
+    if (noalloc_capacity(model, n, &need) != TMD_OK) {
+        set_error("%lld atoms need %zu bytes of scratch; the static scratch holds %zu", (long long)n, need,
+                  NOALLOC_BYTES);
+        return TMD_ERR_CAPACITY;
+    }
+    int dev = 0;
+    TMD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        set_error("device ordinal %d out of range", dev);
+        return TMD_ERR_INVALID_ARG;
+    }
+    void *base = nullptr;
+    {
+        // once per device, with that device current: the host-side name of a
+        // __device__ array is not a device address; ask the runtime for it.
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            TMD_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    const DevModel &dm = model->dm;
+    if (n == 0) {
+        if (energy) TMD_CUDA(cudaMemsetAsync(energy, 0, sizeof(double), s));
+        if (virial) TMD_CUDA(cudaMemsetAsync(virial, 0, 9 * sizeof(double), s));
+        return TMD_OK;
+    }
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    unsigned char *cur = static_cast<unsigned char *>(base);
+    auto take = [&](size_t bytes) {
+        void *p = cur;
+        cur += al(bytes);
+        return p;
+    };
+    const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const int ntile = (int)((n + MT - 1) / MT);
+    tmd_nlist w;  // a view onto the static scratch; never freed
+    w.perm = static_cast<int32_t *>(take(sizeof(int32_t) * n));
+    w.ph = static_cast<float4 *>(take(sizeof(float4) * n));
+    w.pl = static_cast<float4 *>(take(sizeof(float4) * n));
+    w.P = static_cast<float *>(take(sizeof(float) * n * dm.S * dm.K * NMOM));
+    w.G = static_cast<float *>(take(sizeof(float) * n * dm.Dd));
+    w.dG = static_cast<float *>(take(sizeof(float) * n * dm.Dd));
+    w.Fq = static_cast<unsigned long long *>(take(sizeof(unsigned long long) * 3 * n));
+    w.part = static_cast<double *>(take(sizeof(double) * (ntile + 9 * (size_t)nblk + 16)));
+    int32_t *flag = static_cast<int32_t *>(take(sizeof(int32_t) * 4));
+
+    // validate the caller's table on the device, then read the verdict
+    TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    const int cb = (int)std::min<int64_t>((std::max(n, nnz) + 255) / 256, 4096);
+    TMD_LAUNCH("k_noalloc_check", s, k_noalloc_check<<<cb, 256, 0, s>>>(off, nbr, reinterpret_cast<const char4 *>(shift4),
+                                                                        types, n, nnz, dm.S, flag));
+    TMD_CUDA(cudaGetLastError());
+    int32_t bad = 0;
+    TMD_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    if (bad) {
+        set_error("invalid neighbour table or species (check code %d: 1 offsets, 2 types, 4 nbr ids, 8 shift4 species)",
+                  bad);
+        return TMD_ERR_INVALID_ARG;
+    }
+
+    TMD_LAUNCH("k_iota", s, k_iota<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.perm, n));
+    TMD_LAUNCH("k_split_pos", s, k_split_pos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, w.ph, w.pl));
+    TMD_CUDA(cudaGetLastError());
+    DevNlist dn;
+    dn.off = off;
+    dn.nbr = nbr;
+    dn.shift = reinterpret_cast<const char4 *>(shift4);
+    dn.perm = w.perm;
+    dn.ph = w.ph;
+    dn.pl = w.pl;
+    dn.n = n;
+    for (int x = 0; x < 3; ++x) {
+        dn.box[x] = box[x];
+        dn.Lh[x] = (float)box[x];
+        dn.Ll[x] = (float)(box[x] - (double)dn.Lh[x]);
+    }
+    double *part_e = w.part;
+    double *part_w = w.part + ntile;
+    tmd_status st;
+    // the accumulator keeps the previous call's contents: clear it
+    TMD_CUDA(cudaMemsetAsync(w.Fq, 0, sizeof(unsigned long long) * 3 * n, s));
+    if ((st = dispatch_pair(dm, dn, pos, types, &w, part_w, nblk, s, true)) != TMD_OK) return st;
+    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
+    TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, w.perm, types, n, w.G, w.dG, e_atom,
+                                                                                 part_e));
+    TMD_CUDA(cudaGetLastError());
+    if ((st = dispatch_pair(dm, dn, pos, types, &w, part_w, nblk, s, false)) != TMD_OK) return st;
+    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ntile, part_w, nblk, energy, virial));
+    TMD_CUDA(cudaGetLastError());
+    if (forces) {
+        TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
+                                           reinterpret_cast<const long long *>(w.Fq), n, forces));
         TMD_CUDA(cudaGetLastError());
     }
     return TMD_OK;

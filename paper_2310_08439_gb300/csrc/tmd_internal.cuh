@@ -181,6 +181,9 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
                        double *virial, cudaStream_t s);
 tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                            int64_t n, const double box[3], float *G, float *dEdG, cudaStream_t s);
+tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const int32_t *nbr, const int8_t *shift4,
+                               int64_t nnz, const double *pos, const int32_t *types, int64_t n, const double box[3],
+                               double *energy, float *e_atom, float *forces, double *virial, cudaStream_t s);
 tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, cudaStream_t s);
 
 }  // namespace tmd

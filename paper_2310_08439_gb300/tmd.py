@@ -65,6 +65,8 @@ _SIGS = {
     "tmd_nlist_export": (C.c_int, [_P, _P, _P, _P]),
     "tmd_compute": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P, _P, _P, _P]),
     "tmd_descriptors": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), _P, _P, _P]),
+    "tmd_compute_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P, _P, C.c_int64, C.POINTER(C.c_double),
+                                      _P, _P, _P, _P, _P]),
     "tmd_evaluate_host": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int32), _P, _P, _P, _P]),
     "tmd_system_create": (C.c_int, [C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_double,
@@ -240,6 +242,15 @@ def evaluate(model, nl, pos, types, box, stream=None):
            "virial": torch.zeros(9, dtype=torch.float64, device=dev)}
     compute(model, nl, pos, types, box, out["energy"], out["e_atom"], out["forces"], out["virial"], stream)
     return out
+
+
+def compute_noalloc(model, off, nbr, shift4, pos, types, box, energy=None, e_atom=None, forces=None, virial=None,
+                    stream=None):
+    """tmd_compute_noalloc: cuda tensors off [n+1] int64, nbr [nnz] int32,
+    shift4 [nnz, 4] int8 (sx, sy, sz, species of j); outputs as ``compute``."""
+    check(lib().tmd_compute_noalloc(model.handle, _dptr(off), _dptr(nbr), _dptr(shift4), int(nbr.shape[0]),
+                                    _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box), _dptr(energy),
+                                    _dptr(e_atom), _dptr(forces), _dptr(virial), _stream(stream)))
 
 
 def evaluate_host(model, nl, pos, types, box, pbc, energy, forces, virial, stream=None):
