@@ -131,8 +131,9 @@ tmd_status tmd_nlist_destroy(tmd_nlist *nl);
  * |x_j + s*L - x_i|^2 < r_list^2 and (j, s) != (i, 0), including periodic
  * self-images when a box side is shorter than 2*r_list.  The distance test
  * is decided in FP64 with the expression ((x_j + s*L) - x_i) per axis and
- * (dx*dx + dy*dy) + dz*dz, without fused multiply-add.  Entries of atom i
- * are ordered by (species of j, j, sx, sy, sz).
+ * (dx*dx + dy*dy) + dz*dz, without fused multiply-add.  On the device each
+ * atom's entries form one contiguous segment in a deterministic order (cell
+ * stencil order, ascending atom id within a cell).
  *  pos    dev [n][3] FP64, in [0, L) per axis.
  *  types  dev [n] int32 species ids (< TMD_MAX_SPECIES).
  *  box    host [3]; pbc host [3].
@@ -149,9 +150,10 @@ tmd_status tmd_neighbors(const double *pos, const int32_t *types, int64_t n, con
 tmd_status tmd_nlist_size(const tmd_nlist *nl, int64_t *n_atoms, int64_t *n_entries);
 
 /*
- * Copy the table to host arrays: off [n+1] int64 CSR offsets, nbr [nnz]
- * int32 neighbour ids, shift [nnz][3] int8 image shifts.  Any pointer may be
- * NULL to skip it.  Synchronises the device.
+ * Copy the table to host arrays in CSR form: off [n+1] int64 offsets, nbr
+ * [nnz] int32 neighbour ids, shift [nnz][3] int8 image shifts, each atom's
+ * entries ordered by (species of j, j, sx, sy, sz).  Any pointer may be NULL
+ * to skip it.  Synchronises the device.
  */
 tmd_status tmd_nlist_export(const tmd_nlist *nl, int64_t *off, int32_t *nbr, int8_t *shift);
 

@@ -67,10 +67,12 @@ __global__ void k_wrap(double *__restrict__ pos, int64_t n, double L0, double L1
     for (int x = 0; x < 3; ++x) {
         if (!pb[x]) continue;
         double p = pos[3 * i + x];
-        p = p - floor(p / L[x]) * L[x];
-        if (p >= L[x]) p -= L[x];
-        if (p < 0.0) p += L[x];
-        pos[3 * i + x] = p;
+        if (p < 0.0 || p >= L[x]) {  // rare: only atoms that left the box
+            p = p - floor(p * (1.0 / L[x])) * L[x];
+            if (p >= L[x]) p -= L[x];
+            if (p < 0.0) p += L[x];
+            pos[3 * i + x] = p;
+        }
     }
 }
 
@@ -331,15 +333,40 @@ tmd_status tmd_nlist_size(const tmd_nlist *nl, int64_t *n_atoms, int64_t *n_entr
 tmd_status tmd_nlist_export(const tmd_nlist *nl, int64_t *off, int32_t *nbr, int8_t *shift) {
     if (!nl || !nl->built) { set_error("neighbour table not built"); return TMD_ERR_INVALID_ARG; }
     TMD_CUDA(cudaDeviceSynchronize());
-    if (off) TMD_CUDA(cudaMemcpy(off, nl->off, sizeof(int64_t) * (nl->n + 1), cudaMemcpyDeviceToHost));
-    if (nbr && nl->nnz) TMD_CUDA(cudaMemcpy(nbr, nl->nbr, sizeof(int32_t) * nl->nnz, cudaMemcpyDeviceToHost));
-    if (shift && nl->nnz) {
-        std::vector<char4> tmp((size_t)nl->nnz);
-        TMD_CUDA(cudaMemcpy(tmp.data(), nl->shift, sizeof(char4) * nl->nnz, cudaMemcpyDeviceToHost));
-        for (int64_t i = 0; i < nl->nnz; ++i) {
-            shift[3 * i] = tmp[i].x;
-            shift[3 * i + 1] = tmp[i].y;
-            shift[3 * i + 2] = tmp[i].z;
+    const int64_t n = nl->n, nnz = nl->nnz;
+    std::vector<int64_t> b((size_t)n), e((size_t)n);
+    std::vector<int32_t> nb((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<char4> sh((size_t)std::max<int64_t>(nnz, 1));
+    if (n > 0) {
+        TMD_CUDA(cudaMemcpy(b.data(), nl->beg, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+        TMD_CUDA(cudaMemcpy(e.data(), nl->end, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+    }
+    if (nnz > 0) {
+        TMD_CUDA(cudaMemcpy(nb.data(), nl->nbr, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+        TMD_CUDA(cudaMemcpy(sh.data(), nl->shift, sizeof(char4) * nnz, cudaMemcpyDeviceToHost));
+    }
+    // CSR in atom order, each atom's entries sorted by (species of j, j, sx, sy, sz)
+    std::vector<int64_t> o((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) o[i + 1] = o[i] + (e[i] - b[i]);
+    if (off) std::memcpy(off, o.data(), sizeof(int64_t) * (n + 1));
+    std::vector<uint64_t> keys;
+    for (int64_t i = 0; i < n; ++i) {
+        keys.clear();
+        for (int64_t c = b[i]; c < e[i]; ++c) {
+            const char4 v = sh[c];
+            keys.push_back(((uint64_t)(uint8_t)v.w << 60) | ((uint64_t)(uint32_t)nb[c] << 15) |
+                           ((uint64_t)(v.x + 16) << 10) | ((uint64_t)(v.y + 16) << 5) | (uint64_t)(v.z + 16));
+        }
+        std::sort(keys.begin(), keys.end());
+        for (size_t k = 0; k < keys.size(); ++k) {
+            const uint64_t key = keys[k];
+            const int64_t dst = o[i] + (int64_t)k;
+            if (nbr) nbr[dst] = (int32_t)((key >> 15) & 0x1FFFFFFFFFFFull);
+            if (shift) {
+                shift[3 * dst] = (int8_t)((int)((key >> 10) & 31) - 16);
+                shift[3 * dst + 1] = (int8_t)((int)((key >> 5) & 31) - 16);
+                shift[3 * dst + 2] = (int8_t)((int)(key & 31) - 16);
+            }
         }
     }
     return TMD_OK;

@@ -9,8 +9,12 @@
 // FP32 from a cell-sorted float4 copy of the positions; only pairs inside a
 // rounding band around r_list^2 are decided in FP64 with the exact
 // expression ((x_j + s L) - x_i), (dx^2 + dy^2) + dz^2, no FMA, which makes the
-// table bit-identical to the plain definition.  Each atom's entries are sorted
-// by (species of j, j, sx, sy, sz) with a warp bitonic sort in shared memory.
+// table bit-identical to the plain definition.  The table is built in one
+// pass: each warp buffers its atom's entries in shared memory, reserves room
+// with one atomicAdd on a global counter and writes a contiguous segment
+// [beg[i], end[i]).  Atom ids are sorted inside every cell first, so the entry
+// order of each atom (stencil order, ascending id within a cell) is
+// deterministic.
 #include <cmath>
 #include <cstring>
 
@@ -23,16 +27,10 @@ namespace {
 constexpr int BIN_THREADS = 256;
 constexpr int NBR_WARPS = 4;
 
-__device__ __forceinline__ int floordiv(int a, int b) {
-    int q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-    return q;
-}
-
 // cell index of each atom, cell occupancy counts (stored at start[c+1]), per
 // block species counts; flags atoms outside the box and bad species.
 __global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict__ types, int64_t n,
-                      double L0, double L1, double L2, int nc0, int nc1, int nc2,
+                      double L0, double L1, double L2, double ic0, double ic1, double ic2, int nc0, int nc1, int nc2,
                       int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_start,
                       int32_t *__restrict__ type_block, int32_t *__restrict__ status) {
     __shared__ int32_t s_cnt[TMD_MAX_SPECIES];
@@ -43,7 +41,7 @@ __global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict_
     if (i < n) {
         const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
         int bad = !(x >= 0.0 && x < L0 && y >= 0.0 && y < L1 && z >= 0.0 && z < L2);
-        int cx = (int)floor(x * nc0 / L0), cy = (int)floor(y * nc1 / L1), cz = (int)floor(z * nc2 / L2);
+        int cx = (int)(x * ic0), cy = (int)(y * ic1), cz = (int)(z * ic2);
         cx = min(max(cx, 0), nc0 - 1);
         cy = min(max(cy, 0), nc1 - 1);
         cz = min(max(cz, 0), nc2 - 1);
@@ -67,37 +65,42 @@ __global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict_
     if (threadIdx.x < TMD_MAX_SPECIES) type_block[blockIdx.x * TMD_MAX_SPECIES + threadIdx.x] = s_cnt[threadIdx.x];
 }
 
-// exclusive scan of the per-block species counts (single block); writes the
-// species start offsets type_start[0..MAX_SPECIES].
+// exclusive scan of the per-block species counts (one warp per species);
+// writes the species start offsets type_start[0..MAX_SPECIES].
 __global__ void k_type_scan(int32_t *__restrict__ type_block, int nblocks, int32_t *__restrict__ type_start) {
     __shared__ int32_t s_tot[TMD_MAX_SPECIES];
-    if (threadIdx.x < TMD_MAX_SPECIES) {
-        const int s = threadIdx.x;
-        int32_t run = 0;
-        for (int b = 0; b < nblocks; ++b) {
-            const int32_t v = type_block[b * TMD_MAX_SPECIES + s];
-            type_block[b * TMD_MAX_SPECIES + s] = run;
-            run += v;
+    const int s = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t run = 0;
+    for (int b0 = 0; b0 < nblocks; b0 += 32) {
+        const int b = b0 + lane;
+        const int32_t v = b < nblocks ? type_block[b * TMD_MAX_SPECIES + s] : 0;
+        int32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
         }
-        s_tot[s] = run;
+        if (b < nblocks) type_block[b * TMD_MAX_SPECIES + s] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
     }
+    if (lane == 0) s_tot[s] = run;
     __syncthreads();
     if (threadIdx.x == 0) {
         int32_t acc = 0;
-        for (int s = 0; s < TMD_MAX_SPECIES; ++s) {
-            type_start[s] = acc;
-            acc += s_tot[s];
+        for (int t = 0; t < TMD_MAX_SPECIES; ++t) {
+            type_start[t] = acc;
+            acc += s_tot[t];
         }
         type_start[TMD_MAX_SPECIES] = acc;
     }
 }
 
-// scatter atoms into cells (cell-sorted ids + FP32 positions with the species
-// in the top 4 bits of the id) and stably into species order (perm).
+// scatter atom ids into cells (order within a cell fixed by k_cell_sort) and
+// stably into species order (perm).
 __global__ void k_fill(const double *__restrict__ pos, const int32_t *__restrict__ types, int64_t n,
                        const int32_t *__restrict__ cell_of, const int32_t *__restrict__ cell_start,
                        int32_t *__restrict__ cell_fill, int32_t *__restrict__ cell_atoms,
-                       float4 *__restrict__ cell_pos, const int32_t *__restrict__ type_block,
+                       const int32_t *__restrict__ type_block,
                        const int32_t *__restrict__ type_start, int32_t *__restrict__ perm) {
     __shared__ int32_t s_warp[BIN_THREADS / 32][TMD_MAX_SPECIES];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,9 +112,6 @@ __global__ void k_fill(const double *__restrict__ pos, const int32_t *__restrict
         const int c = cell_of[i];
         const int slot = cell_start[c] + atomicAdd(&cell_fill[c], 1);
         cell_atoms[slot] = (int32_t)i;
-        const int tt = t < 0 ? 0 : t;
-        cell_pos[slot] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2],
-                                     __int_as_float((int)((uint32_t)i | ((uint32_t)tt << 28))));
     }
     // stable species partition: rank = (earlier warps of the block) + (earlier lanes)
     unsigned masks[TMD_MAX_SPECIES];
@@ -129,6 +129,67 @@ __global__ void k_fill(const double *__restrict__ pos, const int32_t *__restrict
     }
 }
 
+constexpr int CELL_SORT_WARPS = 4;
+constexpr int MAX_CELL = 1024;
+
+// Sort the ids of every cell ascending (one warp per cell) and write the
+// cell-sorted FP32 positions with the species in the top 4 bits of the id.
+__global__ void __launch_bounds__(CELL_SORT_WARPS * 32)
+    k_cell_sort(const int32_t *__restrict__ cell_start, int64_t ncell, int32_t *__restrict__ cell_atoms,
+                const double *__restrict__ pos, const int32_t *__restrict__ types, float4 *__restrict__ cell_pos,
+                int32_t *__restrict__ status) {
+    __shared__ int32_t s_ids[CELL_SORT_WARPS][MAX_CELL];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)gridDim.x * CELL_SORT_WARPS;
+    for (int64_t c = (int64_t)blockIdx.x * CELL_SORT_WARPS + warp; c < ncell; c += total) {
+        const int beg = cell_start[c], cnt = cell_start[c + 1] - beg;
+        if (cnt <= 32) {
+            int v = lane < cnt ? cell_atoms[beg + lane] : 0x7fffffff;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const int w = __shfl_xor_sync(0xffffffffu, v, j);
+                    const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                    v = (lower == up) ? min(v, w) : max(v, w);
+                }
+            if (lane < cnt) cell_atoms[beg + lane] = v;
+        } else if (cnt <= MAX_CELL) {
+            int32_t *ids = s_ids[warp];
+            for (int t = lane; t < cnt; t += 32) ids[t] = cell_atoms[beg + t];
+            __syncwarp();
+            for (int t = lane; t < cnt; t += 32) {  // rank sort (ids are distinct)
+                const int e = ids[t];
+                int rank = 0;
+                for (int u = 0; u < cnt; ++u) rank += ids[u] < e;
+                cell_atoms[beg + rank] = e;
+            }
+            __syncwarp();
+        } else {
+            if (lane == 0) atomicOr(status, DEV_ERR_CELL);
+        }
+        __syncwarp();
+        for (int t = lane; t < cnt; t += 32) {
+            const int i = cell_atoms[beg + t];
+            int tt = types[i];
+            tt = (tt < 0 || tt >= TMD_MAX_SPECIES) ? 0 : tt;
+            cell_pos[beg + t] = make_float4((float)pos[3 * (int64_t)i], (float)pos[3 * (int64_t)i + 1],
+                                            (float)pos[3 * (int64_t)i + 2],
+                                            __int_as_float((int)((uint32_t)i | ((uint32_t)tt << 28))));
+        }
+    }
+}
+
+// cell index of u on one axis with its image shift (no division: |u| is
+// within a few boxes of the range)
+__device__ __forceinline__ int wrap_cell(int u, int nc, int &k) {
+    int s = 0;
+    k = u;
+    while (k < 0) { k += nc; --s; }
+    while (k >= nc) { k -= nc; ++s; }
+    return s;
+}
+
 struct NbrParams {
     const double *pos;
     const int32_t *cell_of;
@@ -140,9 +201,11 @@ struct NbrParams {
     double L[3];
     double r2;            // r_list * r_list (FP64, as the definition)
     float r2lo, r2hi;     // FP32 band outside which the FP32 screen decides
-    int64_t *off;         // count pass: off[i+1] = count; fill pass: offsets
+    int64_t *beg, *end;   // per-atom segment of the table
     int32_t *nbr;
     char4 *shift;
+    unsigned long long *counter;  // entries reserved so far
+    int64_t cap;          // capacity of nbr / shift
     int32_t *status;
 };
 
@@ -163,7 +226,6 @@ __device__ __noinline__ bool exact_inside(const double *__restrict__ pos, int j,
     return e2 < r2;
 }
 
-template <bool FILL>
 __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
     extern __shared__ uint64_t s_keys[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -179,22 +241,22 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
     for (int dz = -p.R[2]; dz <= p.R[2]; ++dz) {
         const int uz = cz + dz;
         if (!p.pbc[2] && (uz < 0 || uz >= p.nc[2])) continue;
-        const int sz = p.pbc[2] ? floordiv(uz, p.nc[2]) : 0;
-        const int kz = uz - sz * p.nc[2];
+        int kz;
+        const int sz = wrap_cell(uz, p.nc[2], kz);
         const float zs = zh - (float)sz * p.Lf[2];
         for (int dy = -p.R[1]; dy <= p.R[1]; ++dy) {
             const int uy = cy + dy;
             if (!p.pbc[1] && (uy < 0 || uy >= p.nc[1])) continue;
-            const int sy = p.pbc[1] ? floordiv(uy, p.nc[1]) : 0;
-            const int ky = uy - sy * p.nc[1];
+            int ky;
+            const int sy = wrap_cell(uy, p.nc[1], ky);
             const float ys = yh - (float)sy * p.Lf[1];
             const int row = p.nc[0] * (ky + p.nc[1] * kz);
             int dx = -p.R[0];
             while (dx <= p.R[0]) {
                 const int ux = cx + dx;
                 if (!p.pbc[0] && (ux < 0 || ux >= p.nc[0])) { ++dx; continue; }
-                const int sx = p.pbc[0] ? floordiv(ux, p.nc[0]) : 0;
-                const int kx = ux - sx * p.nc[0];
+                int kx;
+                const int sx = wrap_cell(ux, p.nc[0], kx);
                 int len = 1;  // run of consecutive cells with the same shift
                 while (dx + len <= p.R[0] && kx + len < p.nc[0]) ++len;
                 const float xs = xh - (float)sx * p.Lf[0];
@@ -214,15 +276,15 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
                         in = d2 < p.r2lo;
                         band = !in && d2 < p.r2hi;
                     }
-                    // rounding band: exact FP64 decision.  Entered through a
-                    // warp-uniform branch so the (rare) FP64 work is not
-                    // predicated onto every candidate.
+                    // rounding band: exact FP64 decision, reached through a
+                    // warp-uniform branch and an out-of-line call so that the
+                    // (rare) FP64 work is not predicated onto every candidate.
                     if (__any_sync(0xffffffffu, band)) {
                         if (band) in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, p.L[0], p.L[1], p.L[2], p.r2);
                     }
                     if (self_img && j == (int)i) in = false;
                     const unsigned m = __ballot_sync(0xffffffffu, in);
-                    if (FILL && in) {
+                    if (in) {
                         const int slot = count + __popc(m & lt);
                         if (slot < TMD_MAX_DEGREE) keys[slot] = make_key(tj, j, sx, sy, sz);
                     }
@@ -232,39 +294,31 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
             }
         }
     }
-    if (!FILL) {
+    if (count > TMD_MAX_DEGREE) {
         if (lane == 0) {
-            p.off[i + 1] = count;
-            if (count > TMD_MAX_DEGREE) atomicOr(p.status, DEV_ERR_DEGREE);
+            atomicOr(p.status, DEV_ERR_DEGREE);
+            p.beg[i] = 0;
+            p.end[i] = 0;
         }
         return;
     }
-    if (count > TMD_MAX_DEGREE) return;  // reported by the count pass
-    // bitonic sort of keys[0..P) with P = next power of two >= count
-    int P = 32;
-    while (P < count) P <<= 1;
-    for (int c = count + lane; c < P; c += 32) keys[c] = ~0ull;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.counter, (unsigned long long)count);
+    base = __shfl_sync(0xffffffffu, base, 0);
     __syncwarp();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int t = lane; t < (P >> 1); t += 32) {
-                const int i1 = 2 * jj * (t / jj) + (t % jj);
-                const int i2 = i1 + jj;
-                const bool up = (i1 & k) == 0;
-                const uint64_t a = keys[i1], b = keys[i2];
-                if ((a > b) == up) { keys[i1] = b; keys[i2] = a; }
-            }
-            __syncwarp();
+    if ((int64_t)base + count <= p.cap) {
+        for (int c = lane; c < count; c += 32) {
+            const uint64_t key = keys[c];
+            const int t = (int)(key >> 60);
+            const int j = (int)((key >> 15) & 0x1FFFFFFFFFFFull);
+            const int sx = (int)((key >> 10) & 31) - 16, sy = (int)((key >> 5) & 31) - 16, sz = (int)(key & 31) - 16;
+            p.nbr[base + c] = j;
+            p.shift[base + c] = make_char4((signed char)sx, (signed char)sy, (signed char)sz, (signed char)t);
         }
     }
-    const int64_t o = p.off[i];
-    for (int c = lane; c < count; c += 32) {
-        const uint64_t key = keys[c];
-        const int t = (int)(key >> 60);
-        const int j = (int)((key >> 15) & 0x1FFFFFFFFFFFull);
-        const int sx = (int)((key >> 10) & 31) - 16, sy = (int)((key >> 5) & 31) - 16, sz = (int)(key & 31) - 16;
-        p.nbr[o + c] = j;
-        p.shift[o + c] = make_char4((signed char)sx, (signed char)sy, (signed char)sz, (signed char)t);
+    if (lane == 0) {
+        p.beg[i] = (int64_t)base;
+        p.end[i] = (int64_t)base + count;
     }
 }
 
@@ -341,12 +395,8 @@ tmd_status scan_inclusive(T *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, c
 
 }  // namespace
 
-tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, cudaStream_t s) {
-    return scan_inclusive<int64_t>(data, n, tmp, cap_tmp, s);
-}
-
 void nlist_free(tmd_nlist *nl) {
-    void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->off, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
+    void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->beg, nl->end, nl->counter, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
                     nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->Fq, nl->part, nl->ph, nl->pl,
                     nl->io_pos, nl->io_types, nl->io_forces, nl->io_red};
     for (void *p : ptrs)
@@ -369,13 +419,16 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
         set_error("r_list must be finite and > 0");
         return TMD_ERR_INVALID_ARG;
     }
-    double Lmax = 0.0;
+    double Lmax = 0.0, vol = 1.0;
     int smax = 0;
     for (int x = 0; x < 3; ++x) {
         if (!(std::isfinite(box[x]) && box[x] > 0.0)) {
             set_error("box[%d] must be finite and > 0", x);
             return TMD_ERR_INVALID_ARG;
         }
+        // cells are at least r_list + margin wide: the margin covers the
+        // rounding of the cell assignment (an atom a hair inside a cell
+        // boundary may be binned on either side of it)
         const double margin = 1e-6 + 1e-9 * box[x];
         int nc = (int)std::floor(box[x] / (r_list + margin));
         if (nc < 1) nc = 1;
@@ -392,6 +445,7 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
             smax = std::max(smax, std::max(-lo, hi));
         }
         Lmax = std::max(Lmax, box[x]);
+        vol *= box[x];
     }
     if (smax > 15) {
         set_error("r_list %.3f needs image shifts beyond +-15 boxes", r_list);
@@ -408,30 +462,51 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
     if ((st = grow(&nl->cell_atoms, &nl->cap_cell_atoms, n)) != TMD_OK) return st;
     if ((st = grow(&nl->cell_pos, &nl->cap_cell_pos, n)) != TMD_OK) return st;
     if ((st = grow(&nl->perm, &nl->cap_perm, n)) != TMD_OK) return st;
-    if ((st = grow(&nl->off, &nl->cap_off, n + 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->beg, &nl->cap_beg, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->end, &nl->cap_end, n)) != TMD_OK) return st;
     if ((st = grow(&nl->cell_start, &nl->cap_cells, nl->ncell + 1)) != TMD_OK) return st;
     if ((st = grow(&nl->cell_fill, &nl->cap_cell_fill, nl->ncell)) != TMD_OK) return st;
     if ((st = grow(&nl->type_block, &nl->cap_type_blocks, (nb_bin + 1) * TMD_MAX_SPECIES)) != TMD_OK) return st;
-    if ((st = grow(&nl->status, &nl->cap_status, 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->status, &nl->cap_status, 4)) != TMD_OK) return st;
     if ((st = grow(&nl->type_start, &nl->cap_type_start, TMD_MAX_SPECIES + 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->counter, &nl->cap_counter, 1)) != TMD_OK) return st;
     if (!nl->h_pinned) TMD_CUDA(cudaMallocHost((void **)&nl->h_pinned, 16 * sizeof(int64_t)));
+    // capacity for the entries: the previous table's size, or the uniform
+    // density estimate, with headroom; a build that overflows is rerun once
+    // with the exact size
+    {
+        const double est = (double)n * ((double)n / vol) * (4.0 / 3.0) * M_PI * r_list * r_list * r_list;
+        const int64_t want = (int64_t)std::max<double>(1.2 * est, 1.1 * (double)nl->nnz) + 1024;
+        if (nl->cap_nnz < want) {
+            if ((st = grow(&nl->nbr, &nl->cap_nnz, want)) != TMD_OK) return st;
+        }
+        if (nl->cap_shift < nl->cap_nnz) {
+            if ((st = grow(&nl->shift, &nl->cap_shift, nl->cap_nnz)) != TMD_OK) return st;
+        }
+    }
     TMD_CUDA(cudaMemsetAsync(nl->status, 0, sizeof(int32_t), s));
     TMD_CUDA(cudaMemsetAsync(nl->cell_start, 0, sizeof(int32_t) * (nl->ncell + 1), s));
     TMD_CUDA(cudaMemsetAsync(nl->cell_fill, 0, sizeof(int32_t) * nl->ncell, s));
-    TMD_CUDA(cudaMemsetAsync(nl->off, 0, sizeof(int64_t), s));
     TMD_CUDA(cudaMemsetAsync(nl->type_start, 0, sizeof(int32_t) * (TMD_MAX_SPECIES + 1), s));
+    TMD_CUDA(cudaMemsetAsync(nl->counter, 0, sizeof(unsigned long long), s));
 
     if (n > 0) {
-        TMD_LAUNCH("k_bin", s, k_bin<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, box[0], box[1], box[2], nl->nc[0],
-                                                      nl->nc[1], nl->nc[2], nl->cell_of, nl->cell_start,
-                                                      nl->type_block, nl->status));
+        TMD_LAUNCH("k_bin", s, k_bin<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, box[0], box[1], box[2],
+                                                                            nl->nc[0] / box[0], nl->nc[1] / box[1],
+                                                                            nl->nc[2] / box[2], nl->nc[0], nl->nc[1],
+                                                                            nl->nc[2], nl->cell_of, nl->cell_start,
+                                                                            nl->type_block, nl->status));
         TMD_CUDA(cudaGetLastError());
         if ((st = scan_inclusive<int32_t>(nl->cell_start + 1, nl->ncell, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK)
             return st;
-        TMD_LAUNCH("k_type_scan", s, k_type_scan<<<1, 32, 0, s>>>(nl->type_block, (int)nb_bin, nl->type_start));
-        TMD_LAUNCH("k_fill", s, k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start, nl->cell_fill,
-                                                       nl->cell_atoms, nl->cell_pos, nl->type_block,
-                                                       nl->type_start, nl->perm));
+        TMD_LAUNCH("k_type_scan", s, k_type_scan<<<1, 32 * TMD_MAX_SPECIES, 0, s>>>(nl->type_block, (int)nb_bin,
+                                                                                    nl->type_start));
+        TMD_LAUNCH("k_fill", s, k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start,
+                                                                              nl->cell_fill, nl->cell_atoms,
+                                                                              nl->type_block, nl->type_start, nl->perm));
+        const unsigned nb_cell = (unsigned)std::min<int64_t>((nl->ncell + CELL_SORT_WARPS - 1) / CELL_SORT_WARPS, 65535);
+        TMD_LAUNCH("k_cell_sort", s, k_cell_sort<<<nb_cell, CELL_SORT_WARPS * 32, 0, s>>>(
+                                          nl->cell_start, nl->ncell, nl->cell_atoms, pos, types, nl->cell_pos, nl->status));
         TMD_CUDA(cudaGetLastError());
     }
 
@@ -461,53 +536,60 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
         p.r2lo = std::nextafter((float)(p.r2 - margin), -INFINITY);
         p.r2hi = std::nextafter((float)(p.r2 + margin), INFINITY);
     }
-    p.off = nl->off;
-    p.nbr = nullptr;
-    p.shift = nullptr;
+    p.beg = nl->beg;
+    p.end = nl->end;
+    p.counter = nl->counter;
     p.status = nl->status;
     const unsigned nb_nbr = (unsigned)((n + NBR_WARPS - 1) / NBR_WARPS);
-    if (n > 0) {
-        TMD_LAUNCH("k_nbr_count", s, k_nbr<false><<<nb_nbr, NBR_WARPS * 32, 0, s>>>(p));
-        TMD_CUDA(cudaGetLastError());
-        if ((st = scan_inclusive<int64_t>(nl->off + 1, n, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK) return st;
+    const size_t smem = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
+    static bool attr_set = false;
+    if (!attr_set) {
+        TMD_CUDA(cudaFuncSetAttribute(k_nbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
     }
-    TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[0], nl->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[1], nl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[2], nl->type_start, sizeof(int32_t) * (TMD_MAX_SPECIES + 1),
-                             cudaMemcpyDeviceToHost, s));
-    TMD_CUDA(cudaStreamSynchronize(s));
-    const int64_t nnz = nl->h_pinned[0];
-    int32_t status = 0;
-    std::memcpy(&status, &nl->h_pinned[1], sizeof(int32_t));
+    int64_t nnz = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        p.nbr = nl->nbr;
+        p.shift = nl->shift;
+        p.cap = std::min(nl->cap_nnz, nl->cap_shift);
+        if (n > 0) {
+            TMD_LAUNCH("k_nbr", s, k_nbr<<<nb_nbr, NBR_WARPS * 32, smem, s>>>(p));
+            TMD_CUDA(cudaGetLastError());
+        }
+        TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[0], nl->counter, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[1], nl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[2], nl->type_start, sizeof(int32_t) * (TMD_MAX_SPECIES + 1),
+                                 cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaStreamSynchronize(s));
+        nnz = nl->h_pinned[0];
+        int32_t status = 0;
+        std::memcpy(&status, &nl->h_pinned[1], sizeof(int32_t));
+        if (status & DEV_ERR_OUTSIDE_BOX) {
+            set_error("an atom lies outside [0, L) on some axis (wrap periodic axes first)");
+            return TMD_ERR_INVALID_ARG;
+        }
+        if (status & DEV_ERR_BAD_TYPE) {
+            set_error("a species id is outside [0, %d)", TMD_MAX_SPECIES);
+            return TMD_ERR_INVALID_ARG;
+        }
+        if (status & DEV_ERR_CELL) {
+            set_error("a binning cell holds more than %d atoms", MAX_CELL);
+            return TMD_ERR_CAPACITY;
+        }
+        if (status & DEV_ERR_DEGREE) {
+            set_error("an atom has more than %d neighbour entries inside r_list", TMD_MAX_DEGREE);
+            return TMD_ERR_CAPACITY;
+        }
+        if (nnz <= std::min(nl->cap_nnz, nl->cap_shift)) break;
+        // overflow: nothing past the capacity was written; grow to the exact
+        // size and build again
+        if ((st = grow(&nl->nbr, &nl->cap_nnz, nnz)) != TMD_OK) return st;
+        if ((st = grow(&nl->shift, &nl->cap_shift, nl->cap_nnz)) != TMD_OK) return st;
+        TMD_CUDA(cudaMemsetAsync(nl->counter, 0, sizeof(unsigned long long), s));
+    }
     int32_t tstart[TMD_MAX_SPECIES + 1];
     std::memcpy(tstart, &nl->h_pinned[2], sizeof(tstart));
-    if (status & DEV_ERR_OUTSIDE_BOX) {
-        set_error("an atom lies outside [0, L) on some axis (wrap periodic axes first)");
-        return TMD_ERR_INVALID_ARG;
-    }
-    if (status & DEV_ERR_BAD_TYPE) {
-        set_error("a species id is outside [0, %d)", TMD_MAX_SPECIES);
-        return TMD_ERR_INVALID_ARG;
-    }
-    if (status & DEV_ERR_DEGREE) {
-        set_error("an atom has more than %d neighbour entries inside r_list", TMD_MAX_DEGREE);
-        return TMD_ERR_CAPACITY;
-    }
     for (int t = 0; t < TMD_MAX_SPECIES; ++t) nl->type_count[t] = tstart[t + 1] - tstart[t];
-    if ((st = grow(&nl->nbr, &nl->cap_nnz, nnz)) != TMD_OK) return st;
-    if ((st = grow(&nl->shift, &nl->cap_shift, nnz)) != TMD_OK) return st;
-    p.nbr = nl->nbr;
-    p.shift = nl->shift;
-    if (n > 0) {
-        const size_t smem = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
-        static bool attr_set = false;
-        if (!attr_set) {
-            TMD_CUDA(cudaFuncSetAttribute(k_nbr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
-        }
-        TMD_LAUNCH("k_nbr_fill", s, k_nbr<true><<<nb_nbr, NBR_WARPS * 32, smem, s>>>(p));
-        TMD_CUDA(cudaGetLastError());
-    }
     nl->nnz = nnz;
     nl->built = 1;
     return TMD_OK;

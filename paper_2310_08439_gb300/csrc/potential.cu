@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                 for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
         float *sH = s_H[warp];
         float *sM = s_M[warp];
-        for_pairs(nl, a, nl.off[a], nl.off[a + 1], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
+        for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int nb) {
                       if (valid) {
                           float r_hi, r_lo, ir;
@@ -326,13 +326,17 @@ __device__ __forceinline__ void gemm_tile(const float *A, int lda, int Kin, cons
     const int items = (MT / 4) * ncb;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int rb = it / ncb, cb = it - rb * ncb;
-        float acc[4][4];
+        // two partial sums over alternating 4-wide chunks of the reduction
+        // dimension (halves the length of each FP32 accumulation chain)
+        float acc[2][4][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int o = 0; o < 4; ++o) acc[i][o] = bias ? __ldg(bias + cb * 4 + o) : 0.f;
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int o = 0; o < 4; ++o) acc[h][i][o] = 0.f;
         const float *a0 = A + (rb * 4) * lda;
-        for (int c = 0; c < Kin; c += 4) {
+        auto chunk = [&](int c, float (&ac)[4][4]) {
             float4 av[4], bv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(a0 + i * lda + c);
@@ -343,19 +347,31 @@ __device__ __forceinline__ void gemm_tile(const float *A, int lda, int Kin, cons
                 const float ai[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    acc[i][0] = fmaf(ai[t], bv[t].x, acc[i][0]);
-                    acc[i][1] = fmaf(ai[t], bv[t].y, acc[i][1]);
-                    acc[i][2] = fmaf(ai[t], bv[t].z, acc[i][2]);
-                    acc[i][3] = fmaf(ai[t], bv[t].w, acc[i][3]);
+                    ac[i][0] = fmaf(ai[t], bv[t].x, ac[i][0]);
+                    ac[i][1] = fmaf(ai[t], bv[t].y, ac[i][1]);
+                    ac[i][2] = fmaf(ai[t], bv[t].z, ac[i][2]);
+                    ac[i][3] = fmaf(ai[t], bv[t].w, ac[i][3]);
                 }
             }
+        };
+        int c = 0;
+        for (; c + 8 <= Kin; c += 8) {
+            chunk(c, acc[0]);
+            chunk(c + 4, acc[1]);
         }
+        if (c < Kin) chunk(c, acc[0]);
+        float accs[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+                accs[i][o] = (bias ? __ldg(bias + cb * 4 + o) : 0.f) + (acc[0][i][o] + acc[1][i][o]);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float v[4];
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
-                float x = acc[i][o];
+                float x = accs[i][o];
                 if (EPI == 1) x = act_f(act, x, spb);
                 if (EPI == 2) x *= act_da(act, aux[(rb * 4 + i) * ldaux + cb * 4 + o], spb);
                 v[o] = x;
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
             }
         __syncwarp();
         long long fx = 0, fy = 0, fz = 0;
-        for_pairs(nl, a, nl.off[a], nl.off[a + 1], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
+        for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
                       float r_hi, r_lo, ir;
@@ -748,7 +764,8 @@ static tmd_status split_positions(tmd_nlist *nl, const double *pos, int64_t n, c
 
 static DevNlist dev_nlist(const tmd_nlist *nl, int64_t n, const double box[3]) {
     DevNlist dn;
-    dn.off = nl->off;
+    dn.beg = nl->beg;
+    dn.end = nl->end;
     dn.nbr = nl->nbr;
     dn.shift = nl->shift;
     dn.perm = nl->perm;
@@ -988,7 +1005,8 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     TMD_LAUNCH("k_split_pos", s, k_split_pos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, w.ph, w.pl));
     TMD_CUDA(cudaGetLastError());
     DevNlist dn;
-    dn.off = off;
+    dn.beg = off;        // CSR: the segment of atom a is [off[a], off[a + 1])
+    dn.end = off + 1;
     dn.nbr = nbr;
     dn.shift = reinterpret_cast<const char4 *>(shift4);
     dn.perm = w.perm;

@@ -20,6 +20,7 @@ enum : int32_t {
     DEV_ERR_BAD_TYPE = 2,
     DEV_ERR_DEGREE = 4,
     DEV_ERR_SHIFT = 8,
+    DEV_ERR_CELL = 16,
 };
 
 // Model as seen by kernels (passed by value).
@@ -39,7 +40,8 @@ struct DevModel {
 
 // Neighbour table as seen by kernels.
 struct DevNlist {
-    const int64_t *off;   // [n+1]
+    const int64_t *beg;   // [n] first entry of atom a
+    const int64_t *end;   // [n] one past its last entry
     const int32_t *nbr;   // [nnz]
     const char4 *shift;   // [nnz] (sx, sy, sz, species of j)
     const int32_t *perm;  // [n] atoms grouped by species, index order within a species
@@ -77,7 +79,9 @@ struct tmd_nlist {
     int32_t *cell_atoms = nullptr;   int64_t cap_cell_atoms = 0;
     float4 *cell_pos = nullptr;      int64_t cap_cell_pos = 0;
     int32_t *perm = nullptr;         int64_t cap_perm = 0;
-    int64_t *off = nullptr;          int64_t cap_off = 0;
+    int64_t *beg = nullptr;          int64_t cap_beg = 0;          // [n] segment of atom i
+    int64_t *end = nullptr;          int64_t cap_end = 0;          // [n]
+    unsigned long long *counter = nullptr; int64_t cap_counter = 0;
     int32_t *cell_start = nullptr;   int64_t cap_cells = 0;
     int32_t *cell_fill = nullptr;    int64_t cap_cell_fill = 0;
     int32_t *nbr = nullptr;          int64_t cap_nnz = 0;
@@ -184,6 +188,5 @@ tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
 tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const int32_t *nbr, const int8_t *shift4,
                                int64_t nnz, const double *pos, const int32_t *types, int64_t n, const double box[3],
                                double *energy, float *e_atom, float *forces, double *virial, cudaStream_t s);
-tmd_status scan_inclusive_i64(int64_t *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, cudaStream_t s);
 
 }  // namespace tmd
