@@ -492,7 +492,7 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 }
 
 template <int K, int S>
-__global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
+__global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                    const int32_t *__restrict__ types, const float *__restrict__ Pin,
                                                    const float *__restrict__ dG,
                                                    unsigned long long *__restrict__ Fq,
@@ -554,29 +554,40 @@ __global__ void __launch_bounds__(PW * 32) k_force(DevModel m, DevNlist nl, cons
                       const uint32_t jb = __float_as_uint(e.w);
                       const int b = (int)(jb >> 28);
                       const int j = (int)(jb & 0x0FFFFFFFu);
-                      float H[K], dH[K], M[NMOM], V[NMOM];
-                      radial<K, true>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, dH);
+                      float M[NMOM], V[NMOM];
                       moments20(ux, uy, uz, M);
 #pragma unroll
                       for (int d = 0; d < NMOM; ++d) V[d] = 0.f;
                       float dEdr = 0.f;
                       const float *Pb = sPd + b * PSTR;
+                      const float4 *rad = &s_rad[(ti * S + b) * K];
+                      float sn, cs;
+                      sincospif(r_hi * m.inv_rc, &sn, &cs);
+                      const float fc = 0.5f * (cs + 1.f);
+                      const float dfc = -0.5f * PI_F * m.inv_rc * sn;
 #pragma unroll
                       for (int k = 0; k < K; ++k) {
-                          float U = 0.f;
+                          // H_k and H'_k formed inside the loop (no per-pair arrays)
+                          const float4 rp = rad[k];
+                          const float t = (r_hi - rp.x) + (r_lo - rp.y);
+                          const float f = exp2f(-rp.z * t * t);
+                          const float Hk = f * fc;
+                          const float dHk = fmaf(-rp.w * t * f, fc, f * dfc);
+                          // U_k = sum_d P'_kd M_d in four independent chains
+                          float u0 = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
 #pragma unroll
                           for (int q4 = 0; q4 < NMOM / 4; ++q4) {
                               const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
-                              U = fmaf(pd.x, M[4 * q4], U);
-                              U = fmaf(pd.y, M[4 * q4 + 1], U);
-                              U = fmaf(pd.z, M[4 * q4 + 2], U);
-                              U = fmaf(pd.w, M[4 * q4 + 3], U);
-                              V[4 * q4] = fmaf(pd.x, H[k], V[4 * q4]);
-                              V[4 * q4 + 1] = fmaf(pd.y, H[k], V[4 * q4 + 1]);
-                              V[4 * q4 + 2] = fmaf(pd.z, H[k], V[4 * q4 + 2]);
-                              V[4 * q4 + 3] = fmaf(pd.w, H[k], V[4 * q4 + 3]);
+                              u0 = fmaf(pd.x, M[4 * q4], u0);
+                              u1 = fmaf(pd.y, M[4 * q4 + 1], u1);
+                              u2 = fmaf(pd.z, M[4 * q4 + 2], u2);
+                              u3 = fmaf(pd.w, M[4 * q4 + 3], u3);
+                              V[4 * q4] = fmaf(pd.x, Hk, V[4 * q4]);
+                              V[4 * q4 + 1] = fmaf(pd.y, Hk, V[4 * q4 + 1]);
+                              V[4 * q4 + 2] = fmaf(pd.z, Hk, V[4 * q4 + 2]);
+                              V[4 * q4 + 3] = fmaf(pd.w, Hk, V[4 * q4 + 3]);
                           }
-                          dEdr = fmaf(U, dH[k], dEdr);   // F1 = U H' R'
+                          dEdr = fmaf((u0 + u1) + (u2 + u3), dHk, dEdr);   // F1 = U H' R'
                       }
                       // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
                       const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
