@@ -129,14 +129,18 @@ def default_radial(n_species: int, n_radial: int, rc: float):
 
 
 def random_model(n_species, n_radial, rc, widths, seed, feature_scale=None,
-                 out_bias=-4.0, activation="tanh", masses=None, scale_floor=1e-2, out_scale=0.1):
+                 out_bias=-4.0, activation="tanh", masses=None, scale_floor=0.1, out_scale=0.1):
     """W_l ~ N(0, 1/fan_in); first-layer columns divided by ``feature_scale``;
     output layer ~ N(0, out_scale^2/fan_in).
 
     ``feature_scale`` ([S, Dd] or None) is the per-column RMS of the descriptor
     over the workload's initial configuration (a stored model statistic, the
     way trained potentials store input normalisation), floored at
-    ``scale_floor`` so that nearly empty channels are not blown up.
+    ``scale_floor`` so that channels that are nearly empty in that
+    configuration (short-range radial channels, odd ranks in symmetric
+    environments) are not amplified more than 10x: with a 1e-2 floor a pair
+    that closes to 1.5 A during MD lights up channels whose weights were
+    scaled by 100 and dominates the forces.
     ``out_bias`` is the output-layer bias, a cohesive-energy-like offset in
     eV/atom.  ``out_scale`` = 0.1 gives forces of ~0.1 eV/A RMS on the jittered
     lattices, like thermal forces of a metal near equilibrium; with 1.0 the
