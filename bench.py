@@ -292,6 +292,28 @@ def main():
     elapsed_ms = float(t.item())
     value = world * n * args.steps / (elapsed_ms * 1e-3)
 
+    # the BF16-network form of the same step (same state, same timing rules)
+    other = "bf16" if args.precision == "fp32" else "fp32"
+    model.set_precision(other)
+    for _ in range(args.warmup):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_other = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_other, op=dist.ReduceOp.MAX)
+    forms = {args.precision: {"value": value, "ms_per_step": elapsed_ms / args.steps},
+             other: {"value": world * n * args.steps / (float(t_other.item()) * 1e-3),
+                     "ms_per_step": float(t_other.item()) / args.steps}}
+    model.set_precision(args.precision)
+
     # end to end through the host-buffer C-ABI call (pinned host state)
     e2e = None
     if not args.no_e2e:
@@ -368,7 +390,7 @@ def main():
                        "l2": "inputs larger than L2 (neighbour table ~%.2f GB, %d in-cutoff pairs)"
                              % (nl.size()[1] * 8 / 1e9, pairs),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "forms": forms, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -90,8 +90,10 @@ const char *tmd_version(void);
  *  activation TMD_ACT_TANH or TMD_ACT_SQUAREPLUS (b = squareplus_b); the
  *             output layer is linear.
  *  precision  TMD_PREC_FP32: every layer in FP32.  TMD_PREC_BF16: network
- *             layers on BF16 tensor cores with FP32 accumulation; radial
- *             basis, moments and contractions stay FP32 in both modes.
+ *             layers on BF16 tensor cores with FP32 accumulation (input,
+ *             activations and weights rounded to BF16; hidden widths must be
+ *             multiples of 16, else TMD_ERR_UNIMPLEMENTED); radial basis,
+ *             moments and contractions stay FP32 in both modes.
  */
 typedef struct {
     int32_t n_species;

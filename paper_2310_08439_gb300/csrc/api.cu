@@ -278,6 +278,10 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     e = cudaMemcpy(m->dev_block, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(m->dev_block); delete m; return cuda_fail(e, "cudaMemcpy model"); }
     m->precision = d->precision;
+    if (d->precision == TMD_PREC_BF16) {
+        tmd_status st = tmd_model_set_precision(m, TMD_PREC_BF16);
+        if (st != TMD_OK) { cudaFree(m->dev_block); delete m; return st; }
+    }
     *out = m;
     return TMD_OK;
 }
@@ -294,6 +298,13 @@ tmd_status tmd_model_set_precision(tmd_model *m, int32_t precision) {
         set_error("bad model or precision");
         return TMD_ERR_INVALID_ARG;
     }
+    if (precision == TMD_PREC_BF16)
+        for (int l = 0; l <= m->dm.L; ++l)
+            if (m->dm.dims[l] % 16) {
+                set_error("the BF16 network needs layer widths that are multiples of 16 (layer %d has %d)", l,
+                          m->dm.dims[l]);
+                return TMD_ERR_UNIMPLEMENTED;
+            }
     m->precision = precision;
     m->dm.precision = precision;
     return TMD_OK;

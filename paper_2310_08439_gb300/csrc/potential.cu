@@ -482,6 +482,193 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp(DevModel m, const int32_t *
 }
 
 // ---------------------------------------------------------------------------
+// network on BF16 tensor cores (FP32 accumulation): the same forward / input-
+// gradient chain as k_mlp for a 64-atom tile; warp w owns rows 16w..16w+15 and
+// issues mma m16n8k16 per (16 x 8) output block.  Activations and the
+// activation derivatives are kept in shared memory as BF16.
+// ---------------------------------------------------------------------------
+constexpr int BT = 64;            // atoms per BF16 tile
+constexpr int BF_THREADS = 128;   // 4 warps x 16 rows
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// C[16 rows of this warp][n0 .. n0 + 8 nt) = A[rows][0..K) * B with
+// B[k][n] = Bt[n * ldb + k] (K contiguous per output column), nt <= 8.
+__device__ __forceinline__ void warp_gemm_bf16(const uint16_t *A, int lda, int K, const uint16_t *__restrict__ Bt,
+                                               int ldb, int n0, int nt, int lane, float (&acc)[8][4]) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const uint32_t a0 = *reinterpret_cast<const uint32_t *>(A + g * lda + k0 + 2 * t);
+        const uint32_t a1 = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + k0 + 2 * t);
+        const uint32_t a2 = *reinterpret_cast<const uint32_t *>(A + g * lda + k0 + 8 + 2 * t);
+        const uint32_t a3 = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + k0 + 8 + 2 * t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < nt) {
+                const uint16_t *bp = Bt + (size_t)(n0 + 8 * j + g) * ldb + k0 + 2 * t;
+                const uint32_t b0 = __ldg(reinterpret_cast<const unsigned int *>(bp));
+                const uint32_t b1 = __ldg(reinterpret_cast<const unsigned int *>(bp + 8));
+                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32_t *__restrict__ perm,
+                                                         const int32_t *__restrict__ types, int64_t n,
+                                                         const float *__restrict__ G, float *__restrict__ dG,
+                                                         float *__restrict__ e_atom, double *__restrict__ part_e) {
+    extern __shared__ __align__(16) uint16_t smh[];
+    __shared__ int s_atom[BT], s_type[BT];
+    __shared__ double s_e[BF_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t p0 = (int64_t)blockIdx.x * BT;
+    if (tid < BT) {
+        const int64_t p = p0 + tid;
+        const int a = p < n ? perm[p] : -1;
+        s_atom[tid] = a;
+        s_type[tid] = a >= 0 ? types[a] : -1;
+    }
+    const int L = m.L, Dd = m.Dd;
+    int maxw = Dd;
+    for (int l = 1; l <= L; ++l) maxw = max(maxw, m.dims[l]);
+    // shared layout (BF16): act[0] = G tile, act[l] / der[l] for hidden layers, two gradient buffers
+    uint16_t *act[MAX_LAYERS + 1], *der[MAX_LAYERS + 1];
+    int ld[MAX_LAYERS + 1];
+    uint16_t *ptr = smh;
+    for (int l = 0; l <= L; ++l) {
+        ld[l] = m.dims[l] + 8;
+        act[l] = ptr;
+        ptr += BT * ld[l];
+        der[l] = ptr;
+        ptr += (l > 0) ? BT * ld[l] : 0;
+    }
+    const int ldz = maxw + 8;
+    uint16_t *dzA = ptr, *dzB = ptr + BT * ldz;
+    __syncthreads();
+    for (int idx = tid; idx < BT * (Dd / 2); idx += blockDim.x) {
+        const int r = idx / (Dd / 2), c2 = idx - r * (Dd / 2);
+        const int a = s_atom[r];
+        float2 v = make_float2(0.f, 0.f);
+        if (a >= 0) v = *reinterpret_cast<const float2 *>(G + (size_t)a * Dd + 2 * c2);
+        *reinterpret_cast<uint32_t *>(act[0] + r * ld[0] + 2 * c2) = pack_bf16(v.x, v.y);
+    }
+    __syncthreads();
+    int s_lo = TMD_MAX_SPECIES, s_hi = -1;
+    for (int r = 0; r < BT; ++r)
+        if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
+    const int r0 = warp * 16;
+    double esum = 0.0;
+    for (int s = s_lo; s <= s_hi; ++s) {
+        const float *wf = m.wf[s];
+        // forward: z = a W^T + b, a' = act(z); B[k=i][n=o] = W[o][i] (BF16 [out][in])
+        for (int l = 0; l < L; ++l) {
+            const int in = m.dims[l], out = m.dims[l + 1];
+            const uint16_t *W = m.hb[s] + m.off_b[l];
+            const float *bias = wf + m.off_f[l] + in * out;
+            for (int n0 = 0; n0 < out; n0 += 64) {
+                float acc[8][4];
+                const int nt = min(8, (out - n0) / 8);
+                warp_gemm_bf16(act[l] + r0 * ld[l], ld[l], in, W, in, n0, nt, lane, acc);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j >= nt) continue;
+                    const int col = n0 + 8 * j + 2 * t;
+                    const float b0 = __ldg(bias + col), b1 = __ldg(bias + col + 1);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = r0 + g + 8 * h;
+                        const float z0 = acc[j][2 * h] + b0, z1 = acc[j][2 * h + 1] + b1;
+                        const float a0v = act_f(m.act, z0, m.sp_b), a1v = act_f(m.act, z1, m.sp_b);
+                        *reinterpret_cast<uint32_t *>(act[l + 1] + row * ld[l + 1] + col) = pack_bf16(a0v, a1v);
+                        *reinterpret_cast<uint32_t *>(der[l + 1] + row * ld[l + 1] + col) =
+                            pack_bf16(act_da(m.act, a0v, m.sp_b), act_da(m.act, a1v, m.sp_b));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // output layer (FP32 dot over the BF16 activations)
+        const int wl = m.dims[L];
+        const float *wout = m.wb[s] + m.off_b[L];
+        const float bout = __ldg(wf + m.off_f[L] + wl);
+        for (int r = warp; r < BT; r += BF_THREADS / 32) {
+            float v = 0.f;
+            for (int c = lane; c < wl; c += 32)
+                v = fmaf(__bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(act[L] + r * ld[L] + c)),
+                         __ldg(wout + c), v);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && s_type[r] == s) {
+                const float e = v + bout;
+                if (e_atom) e_atom[s_atom[r]] = e;
+                esum += (double)e;
+            }
+        }
+        // dz_L = w_out * act'(a_L)
+        for (int idx = tid; idx < BT * (wl / 2); idx += blockDim.x) {
+            const int r = idx / (wl / 2), c = 2 * (idx - r * (wl / 2));
+            const __nv_bfloat162 d2 = *reinterpret_cast<const __nv_bfloat162 *>(der[L] + r * ld[L] + c);
+            *reinterpret_cast<uint32_t *>(dzA + r * ldz + c) =
+                pack_bf16(__ldg(wout + c) * __low2float(d2), __ldg(wout + c + 1) * __high2float(d2));
+        }
+        __syncthreads();
+        uint16_t *cur = dzA, *nxt = dzB;
+        // backward: da_l = dz_{l+1} W_l; B[k=o][n=i] = W[o][i] = W^T[i][o] (BF16 [in][out])
+        for (int l = L - 1; l >= 0; --l) {
+            const int in = m.dims[l], out = m.dims[l + 1];
+            const uint16_t *Wt = m.hf[s] + m.off_f[l];
+            for (int n0 = 0; n0 < in; n0 += 64) {
+                float acc[8][4];
+                const int nt = min(8, (in - n0) / 8);
+                warp_gemm_bf16(cur + r0 * ldz, ldz, out, Wt, out, n0, nt, lane, acc);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j >= nt) continue;
+                    const int col = n0 + 8 * j + 2 * t;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = r0 + g + 8 * h;
+                        if (l > 0) {
+                            const __nv_bfloat162 d2 = *reinterpret_cast<const __nv_bfloat162 *>(der[l] + row * ld[l] + col);
+                            *reinterpret_cast<uint32_t *>(nxt + row * ldz + col) =
+                                pack_bf16(acc[j][2 * h] * __low2float(d2), acc[j][2 * h + 1] * __high2float(d2));
+                        } else if (s_type[row] == s) {
+                            *reinterpret_cast<float2 *>(dG + (size_t)s_atom[row] * Dd + col) =
+                                make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            uint16_t *tmp = cur; cur = nxt; nxt = tmp;
+        }
+    }
+    if (lane == 0) s_e[warp] = esum;
+    __syncthreads();
+    if (tid == 0) {
+        double tsum = 0.0;
+        for (int w = 0; w < BF_THREADS / 32; ++w) tsum += s_e[w];
+        part_e[blockIdx.x] = tsum;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // backward: P', pair gradients, ScatterSum, virial
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
@@ -715,6 +902,17 @@ int sm_count() {
 
 }  // namespace
 
+size_t mlp_bf16_smem_bytes(const DevModel &dm) {
+    int maxw = dm.Dd;
+    size_t el = (size_t)BT * (dm.dims[0] + 8);
+    for (int l = 1; l <= dm.L; ++l) {
+        el += 2 * (size_t)BT * (dm.dims[l] + 8);
+        maxw = std::max(maxw, dm.dims[l]);
+    }
+    el += 2 * (size_t)BT * (maxw + 8);
+    return el * sizeof(uint16_t);
+}
+
 size_t mlp_smem_bytes(const DevModel &dm) {
     int maxw = dm.Dd;
     size_t fl = 0;
@@ -755,12 +953,40 @@ static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, con
 }
 
 static tmd_status set_mlp_smem(const DevModel &dm) {
-    static size_t smem_set = 0;
+    static size_t smem_set = 0, smem_bf_set = 0;
     const size_t smem = mlp_smem_bytes(dm);
     if (smem > 48 * 1024 && smem > smem_set) {
         TMD_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         smem_set = smem;
     }
+    const size_t sb = mlp_bf16_smem_bytes(dm);
+    if (sb > 48 * 1024 && sb > smem_bf_set) {
+        TMD_CUDA(cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+        smem_bf_set = sb;
+    }
+    return TMD_OK;
+}
+
+// network forward + input gradient for n atoms in perm order (FP32 SIMT or
+// BF16 tensor cores, by the model's precision); part_e receives the per-tile
+// energy sums and *ntile_out their count.
+static tmd_status launch_network(const DevModel &dm, const int32_t *perm, const int32_t *types, int64_t n,
+                                 const float *G, float *dG, float *e_atom, double *part_e, int *ntile_out,
+                                 cudaStream_t s) {
+    tmd_status st;
+    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
+    if (dm.precision == TMD_PREC_BF16) {
+        const int ntile = (int)((n + BT - 1) / BT);
+        TMD_LAUNCH("k_mlp_bf16", s, k_mlp_bf16<<<ntile, BF_THREADS, mlp_bf16_smem_bytes(dm), s>>>(
+                                        dm, perm, types, n, G, dG, e_atom, part_e));
+        *ntile_out = ntile;
+    } else {
+        const int ntile = (int)((n + MT - 1) / MT);
+        TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, perm, types, n, G, dG,
+                                                                                     e_atom, part_e));
+        *ntile_out = ntile;
+    }
+    TMD_CUDA(cudaGetLastError());
     return TMD_OK;
 }
 
@@ -808,11 +1034,8 @@ tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
     if (st != TMD_OK || !dEdG) return st;
     const int ntile = (int)((n + MT - 1) / MT);
     if ((st = grow(&nl->part, &nl->cap_part, ntile + 16)) != TMD_OK) return st;
-    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
-    TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, nl->perm, types, n, G, dEdG,
-                                                                                 nullptr, nl->part));
-    TMD_CUDA(cudaGetLastError());
-    return TMD_OK;
+    int nt = 0;
+    return launch_network(dm, nl->perm, types, n, G, dEdG, nullptr, nl->part, &nt, s);
 }
 
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
@@ -844,11 +1067,10 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n, s));
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
     const size_t smem = mlp_smem_bytes(dm);
-    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
-    TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, smem, s>>>(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e));
-    TMD_CUDA(cudaGetLastError());
+    int ne = 0;
+    if ((st = launch_network(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e, &ne, s)) != TMD_OK) return st;
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, false)) != TMD_OK) return st;
-    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ntile, part_w, nblk, energy, virial));
+    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ne, part_w, nblk, energy, virial));
     TMD_CUDA(cudaGetLastError());
     if (forces) {
         TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
@@ -1035,12 +1257,10 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     // the accumulator keeps the previous call's contents: clear it
     TMD_CUDA(cudaMemsetAsync(w.Fq, 0, sizeof(unsigned long long) * 3 * n, s));
     if ((st = dispatch_pair(dm, dn, pos, types, &w, part_w, nblk, s, true)) != TMD_OK) return st;
-    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
-    TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, w.perm, types, n, w.G, w.dG, e_atom,
-                                                                                 part_e));
-    TMD_CUDA(cudaGetLastError());
+    int ne = 0;
+    if ((st = launch_network(dm, w.perm, types, n, w.G, w.dG, e_atom, part_e, &ne, s)) != TMD_OK) return st;
     if ((st = dispatch_pair(dm, dn, pos, types, &w, part_w, nblk, s, false)) != TMD_OK) return st;
-    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ntile, part_w, nblk, energy, virial));
+    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ne, part_w, nblk, energy, virial));
     TMD_CUDA(cudaGetLastError());
     if (forces) {
         TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(

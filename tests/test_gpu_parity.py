@@ -377,3 +377,37 @@ def test_descriptor_matrix_elementwise(tmdlib, wname):
     scale = np.maximum(np.abs(o).max(axis=0), 1e-30)
     err = (np.abs(G - o) / scale).max()
     assert err <= 1e-5, err
+
+
+# ------------------------------------------------------------------ BF16 network form
+@pytest.mark.parametrize("wname", ["tiny", "medium"])
+def test_bf16_network_form_errors(tmdlib, wname, capsys):
+    """BF16 tensor-core network (radial basis, moments and contractions FP32):
+    errors against the FP64 oracle are reported; the bounds only catch gross
+    mistakes (BF16 has an 8-bit significand)."""
+    w = getattr(I, wname)()
+    s = w.systems[0]
+    o = O.evaluate(O.OracleModel(w.model), s.pos, s.types, s.box, s.pbc)
+    g = gpu_eval(tmdlib, w.model, s, precision="bf16")
+    f32 = gpu_eval(tmdlib, w.model, s, precision="fp32")
+    rms = np.sqrt((o["forces"] ** 2).mean())
+    dE = abs(g["energy"] - o["energy"]) / abs(o["energy"])
+    dF = np.abs(g["forces"] - o["forces"]).max() / rms
+    dFr = np.sqrt(((g["forces"] - o["forces"]) ** 2).mean()) / rms
+    dEa = np.abs(g["e_atom"] - o["e_atom"]).max()
+    with capsys.disabled():
+        print(f"\n[bf16 {wname}] dE/E={dE:.2e} max|dF|/rms={dF:.2e} rms(dF)/rms={dFr:.2e} max|dEa|={dEa:.2e} eV "
+              f"(fp32: dF/rms={np.abs(f32['forces'] - o['forces']).max() / rms:.2e})")
+    assert dE < 1e-3 and dFr < 5e-2 and dF < 0.5
+    # the forms differ only in the network
+    assert np.abs(g["forces"] - f32["forces"]).max() > 0.0
+
+
+def test_bf16_rejects_widths_not_multiple_of_16(tmdlib):
+    p = I.random_model(1, 8, 4.0, [12, 8], seed=3)
+    with pytest.raises(tmdlib.TmdError) as e:
+        tmdlib.Model(p, precision="bf16")
+    assert e.value.status == tmdlib.ERR_UNIMPLEMENTED
+    m = tmdlib.Model(p)   # FP32 accepts them
+    with pytest.raises(tmdlib.TmdError):
+        m.set_precision("bf16")
