@@ -296,6 +296,47 @@ tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_ho
                          tmd_thermo *thermo, tmd_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batches: many independent systems resident at once (continuous batching) */
+/* ------------------------------------------------------------------------ */
+/*
+ * A batch keeps n_systems independent periodic systems resident on the device
+ * (concatenated atoms, one box per system).  Any subset of them is evaluated
+ * or advanced by one set of launches: the cell list, neighbour table, pair
+ * kernels and network run over the atoms of the listed systems only, each atom
+ * using its own system's box, and energies / virials are reduced per system in
+ * FP64.  The neighbour tables of the listed systems are rebuilt (r_list = rc)
+ * on every evaluation.  Each system's energy, forces and virial are those of
+ * tmd_compute on that system alone (the method is per system; Sec. "The
+ * Tensor Formalism").
+ */
+typedef struct tmd_batch tmd_batch;
+
+/* n_atoms host [S] (>= 1 each), boxes host [S][3], pbc host [S][3].
+ * Allocates the resident state.  Errors: INVALID_ARG, OOM. */
+tmd_status tmd_batch_create(int32_t n_systems, const int64_t *n_atoms, const double *boxes, const int32_t *pbc,
+                            tmd_batch **out);
+tmd_status tmd_batch_destroy(tmd_batch *batch);
+/* Load one system from host arrays: pos [n][3] FP64 (A), vel [n][3] FP64
+ * (A/fs, NULL = zero), types [n] int32, masses [n] FP64 (amu).  Synchronises. */
+tmd_status tmd_batch_set_system(tmd_batch *batch, int32_t sys, const double *pos, const double *vel,
+                                const int32_t *types, const double *masses, tmd_stream_t stream);
+/* Copy one system's positions / velocities (FP64 [n][3]) and forces (FP32
+ * [n][3]) to host arrays (NULL skips).  Synchronises. */
+tmd_status tmd_batch_get_system(const tmd_batch *batch, int32_t sys, double *pos, double *vel, float *forces,
+                                tmd_stream_t stream);
+/* Evaluate the listed systems (systems host [n_active], distinct ids):
+ * energy host [n_active] FP64, virial host [n_active][9] FP64 (NULL skips);
+ * forces stay resident (tmd_batch_get_system).  Synchronises once. */
+tmd_status tmd_batch_compute(const tmd_model *model, tmd_batch *batch, const int32_t *systems, int32_t n_active,
+                             double *energy, double *virial, tmd_stream_t stream);
+/* Advance the listed systems by nsteps velocity-Verlet steps of dt_fs (as
+ * tmd_step, neighbour tables rebuilt every step); thermo host [n_active]
+ * (may be NULL) receives each system's state after the last step.  Systems
+ * evaluated for the first time get their initial forces first. */
+tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *batch, const int32_t *systems, int32_t n_active,
+                          double dt_fs, int32_t nsteps, tmd_thermo *thermo, tmd_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Profiling (per-kernel CUDA-event timing, launch counting)                */
 /* ------------------------------------------------------------------------ */
 typedef struct {

@@ -123,6 +123,51 @@ __global__ void k_inv_mass(const double *__restrict__ mass, double *__restrict__
     if (i < n) inv[i] = 1.0 / mass[i];
 }
 
+// velocity-Verlet halves and wrap for the atoms of the active systems of a batch
+__global__ void k_vv_first_b(double *__restrict__ pos, double *__restrict__ vel, const float *__restrict__ F,
+                             const double *__restrict__ inv_mass, int64_t n, double dt,
+                             const int32_t *__restrict__ sys_of, const uint8_t *__restrict__ active) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !active[sys_of[i]]) return;
+    const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const double v = vel[3 * i + x] + h * (double)F[3 * i + x];
+        vel[3 * i + x] = v;
+        pos[3 * i + x] += dt * v;
+    }
+}
+
+__global__ void k_vv_second_b(double *__restrict__ vel, const float *__restrict__ F, const double *__restrict__ inv_mass,
+                              int64_t n, double dt, const int32_t *__restrict__ sys_of,
+                              const uint8_t *__restrict__ active) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !active[sys_of[i]]) return;
+    const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) vel[3 * i + x] += h * (double)F[3 * i + x];
+}
+
+__global__ void k_wrap_b(double *__restrict__ pos, int64_t n, const SysParams *__restrict__ sp,
+                         const int32_t *__restrict__ sys_of, const uint8_t *__restrict__ active) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int sys = sys_of[i];
+    if (!active[sys]) return;
+    const SysParams &q = sp[sys];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        if (!q.pbc[x]) continue;
+        double p = pos[3 * i + x];
+        if (p < 0.0 || p >= q.L[x]) {
+            p = p - floor(p * (1.0 / q.L[x])) * q.L[x];
+            if (p >= q.L[x]) p -= q.L[x];
+            if (p < 0.0) p += q.L[x];
+            pos[3 * i + x] = p;
+        }
+    }
+}
+
 bool finite_all(const double *p, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return false;
@@ -624,6 +669,281 @@ tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_ho
     TMD_CUDA(cudaMemcpyAsync(vel_host, sys->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
     if (forces_host) TMD_CUDA(cudaMemcpyAsync(forces_host, sys->forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
     TMD_CUDA(cudaStreamSynchronize(s));
+    return TMD_OK;
+}
+
+
+// --------------------------------------------------------------------- batches
+}  // extern "C"
+
+struct tmd_batch {
+    int32_t S = 0;
+    std::vector<int64_t> off;        // [S+1] atom offsets
+    std::vector<double> box;         // [S][3]
+    std::vector<int32_t> pbc;        // [S][3]
+    std::vector<tmd::SysParams> sp;  // for the current list radius
+    std::vector<int32_t> cell_off;
+    int64_t ncell = 0;
+    double r_list = -1.0;
+    int64_t n = 0;
+    double *pos = nullptr, *vel = nullptr, *mass = nullptr, *inv_mass = nullptr;
+    int32_t *types = nullptr, *sys_of = nullptr;
+    float *forces = nullptr, *e_atom = nullptr, *w_atom = nullptr;
+    int64_t *d_off = nullptr;
+    uint8_t *active = nullptr;       // [S] device flags
+    int32_t *act_list = nullptr;     // [S] device list of active systems
+    double *sys_out = nullptr;       // [S][16] device per-system sums
+    double *h_out = nullptr;         // pinned mirror
+    int32_t *h_act = nullptr;        // pinned staging of the active list
+    uint8_t *h_flags = nullptr;      // pinned staging of the flags
+    std::vector<uint8_t> has_forces;
+    std::vector<int64_t> steps;
+    tmd_nlist nl;
+};
+
+namespace {
+
+tmd_status batch_params(tmd_batch *b, double r_list) {
+    if (b->r_list == r_list && !b->sp.empty()) return TMD_OK;
+    b->sp.resize(b->S);
+    b->cell_off.resize(b->S);
+    int64_t total = 0;
+    for (int k = 0; k < b->S; ++k) {
+        int64_t nc = 0;
+        tmd_status st = tmd::make_sys_params(&b->box[3 * k], &b->pbc[3 * k], r_list, &b->sp[k], &nc);
+        if (st != TMD_OK) return st;
+        b->sp[k].cell_off = (int)total;
+        total += nc;
+    }
+    b->ncell = total;
+    b->r_list = r_list;
+    return TMD_OK;
+}
+
+// flags + list of the active systems to the device (pinned staging)
+tmd_status batch_activate(tmd_batch *b, const int32_t *systems, int32_t n_act, cudaStream_t s, int64_t *atoms) {
+    std::memset(b->h_flags, 0, b->S);
+    int64_t na = 0;
+    for (int k = 0; k < n_act; ++k) {
+        const int32_t sys = systems[k];
+        if (sys < 0 || sys >= b->S || b->h_flags[sys]) {
+            tmd::set_error("active system %d out of range or repeated", sys);
+            return TMD_ERR_INVALID_ARG;
+        }
+        b->h_flags[sys] = 1;
+        b->h_act[k] = sys;
+        na += b->off[sys + 1] - b->off[sys];
+    }
+    TMD_CUDA(cudaMemcpyAsync(b->active, b->h_flags, b->S, cudaMemcpyHostToDevice, s));
+    TMD_CUDA(cudaMemcpyAsync(b->act_list, b->h_act, sizeof(int32_t) * n_act, cudaMemcpyHostToDevice, s));
+    *atoms = na;
+    return TMD_OK;
+}
+
+// wrap, rebuild and evaluate the active systems (flags already set)
+tmd_status batch_eval(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
+    tmd_status st;
+    if ((st = batch_params(b, (double)model->dm.rc)) != TMD_OK) return st;
+    // the device copy of the parameters is made by build_tables; wrapping reads it
+    const unsigned nb = (unsigned)((b->n + 255) / 256);
+    std::vector<int64_t> nsys(b->S);
+    for (int k = 0; k < b->S; ++k) nsys[k] = b->h_flags[k] ? b->off[k + 1] - b->off[k] : 0;
+    if ((st = tmd::grow(&b->nl.sp, &b->nl.cap_sp, b->S)) != TMD_OK) return st;
+    TMD_CUDA(cudaMemcpyAsync(b->nl.sp, b->sp.data(), sizeof(tmd::SysParams) * b->S, cudaMemcpyHostToDevice, s));
+    TMD_LAUNCH("k_wrap_b", s, k_wrap_b<<<nb, 256, 0, s>>>(b->pos, b->n, b->nl.sp, b->sys_of, b->active));
+    if ((st = tmd::build_tables(b->pos, b->types, b->n, b->S, b->sp.data(), b->sys_of, b->active, nsys.data(),
+                                b->ncell, &b->nl, s)) != TMD_OK)
+        return st;
+    return tmd::run_compute_batch(model, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom, b->w_atom,
+                                  b->act_list, n_act, b->d_off, b->vel, b->mass, b->sys_out, s);
+}
+
+void batch_results(tmd_batch *b, int32_t n_act, double *energy, double *virial, tmd_thermo *thermo) {
+    const double conv = 103.6427;  // amu A^2/fs^2 -> eV
+    for (int k = 0; k < n_act; ++k) {
+        const double *r = b->h_out + 16 * k;
+        const int sys = b->h_act[k];
+        if (energy) energy[k] = r[0];
+        if (virial)
+            for (int t = 0; t < 9; ++t) virial[9 * k + t] = r[1 + t];
+        if (thermo) {
+            tmd_thermo &th = thermo[k];
+            const int64_t na = b->off[sys + 1] - b->off[sys];
+            const double mvv[9] = {r[10], r[13], r[14], r[13], r[11], r[15], r[14], r[15], r[12]};
+            th.e_pot = r[0];
+            th.e_kin = 0.5 * (r[10] + r[11] + r[12]) * conv;
+            const double dof = na > 1 ? 3.0 * na - 3.0 : 3.0;
+            th.temperature = 2.0 * th.e_kin / (dof * KB_EV);
+            const double V = b->box[3 * sys] * b->box[3 * sys + 1] * b->box[3 * sys + 2];
+            for (int t = 0; t < 9; ++t) {
+                th.virial[t] = r[1 + t];
+                th.pressure[t] = (mvv[t] * conv + r[1 + t]) / V;
+            }
+            th.step = b->steps[sys];
+            th.rebuilds = b->steps[sys];
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+tmd_status tmd_batch_create(int32_t n_systems, const int64_t *n_atoms, const double *boxes, const int32_t *pbc,
+                            tmd_batch **out) {
+    g_err[0] = 0;
+    if (!out || !n_atoms || !boxes || !pbc || n_systems < 1) { set_error("bad batch arguments"); return TMD_ERR_INVALID_ARG; }
+    *out = nullptr;
+    tmd_batch *b = new (std::nothrow) tmd_batch();
+    if (!b) { set_error("host allocation failed"); return TMD_ERR_OOM; }
+    b->S = n_systems;
+    b->off.assign(n_systems + 1, 0);
+    b->box.assign(boxes, boxes + 3 * (size_t)n_systems);
+    b->pbc.assign(pbc, pbc + 3 * (size_t)n_systems);
+    for (int k = 0; k < n_systems; ++k) {
+        if (n_atoms[k] < 1) { delete b; set_error("system %d has no atoms", k); return TMD_ERR_INVALID_ARG; }
+        tmd_status st = check_box(&boxes[3 * k], &pbc[3 * k]);
+        if (st != TMD_OK) { delete b; return st; }
+        b->off[k + 1] = b->off[k] + n_atoms[k];
+    }
+    b->n = b->off[n_systems];
+    if (b->n >= (int64_t(1) << 28)) { delete b; set_error("too many atoms in the batch"); return TMD_ERR_INVALID_ARG; }
+    b->has_forces.assign(n_systems, 0);
+    b->steps.assign(n_systems, 0);
+    const int64_t n = b->n;
+    cudaError_t e = cudaMalloc(&b->pos, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->vel, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->mass, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->inv_mass, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->types, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->sys_of, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->forces, sizeof(float) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->e_atom, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->w_atom, sizeof(float) * 9 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_off, sizeof(int64_t) * (n_systems + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->active, n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->act_list, sizeof(int32_t) * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->sys_out, sizeof(double) * 16 * n_systems);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, sizeof(double) * 16 * n_systems);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_act, sizeof(int32_t) * n_systems);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_flags, n_systems);
+    if (e == cudaSuccess) e = cudaMemset(b->vel, 0, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMemset(b->forces, 0, sizeof(float) * 3 * n);
+    if (e == cudaSuccess) {
+        std::vector<int32_t> so((size_t)n);
+        for (int k = 0; k < n_systems; ++k)
+            for (int64_t i = b->off[k]; i < b->off[k + 1]; ++i) so[i] = k;
+        e = cudaMemcpy(b->sys_of, so.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_off, b->off.data(), sizeof(int64_t) * (n_systems + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        tmd_batch_destroy(b);
+        cudaGetLastError();
+        set_error("batch allocation: %s", cudaGetErrorString(e));
+        return TMD_ERR_OOM;
+    }
+    *out = b;
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_destroy(tmd_batch *b) {
+    if (!b) return TMD_OK;
+    void *p[] = {b->pos, b->vel, b->mass, b->inv_mass, b->types, b->sys_of, b->forces, b->e_atom, b->w_atom,
+                 b->d_off, b->active, b->act_list, b->sys_out};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->h_act) cudaFreeHost(b->h_act);
+    if (b->h_flags) cudaFreeHost(b->h_flags);
+    nlist_free(&b->nl);
+    delete b;
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_set_system(tmd_batch *b, int32_t sys, const double *pos, const double *vel, const int32_t *types,
+                                const double *masses, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!b || sys < 0 || sys >= b->S || !pos || !types || !masses) { set_error("bad arguments"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t o = b->off[sys], n = b->off[sys + 1] - o;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(masses[i] > 0.0 && std::isfinite(masses[i]))) { set_error("mass[%lld] must be > 0", (long long)i); return TMD_ERR_INVALID_ARG; }
+    TMD_CUDA(cudaMemcpyAsync(b->pos + 3 * o, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    TMD_CUDA(cudaMemcpyAsync(b->types + o, types, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    TMD_CUDA(cudaMemcpyAsync(b->mass + o, masses, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    if (vel) TMD_CUDA(cudaMemcpyAsync(b->vel + 3 * o, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    else TMD_CUDA(cudaMemsetAsync(b->vel + 3 * o, 0, sizeof(double) * 3 * n, s));
+    TMD_LAUNCH("k_inv_mass", s, k_inv_mass<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b->mass + o, b->inv_mass + o, n));
+    TMD_CUDA(cudaGetLastError());
+    TMD_CUDA(cudaStreamSynchronize(s));  // host arrays may be pageable and reused
+    b->has_forces[sys] = 0;
+    b->steps[sys] = 0;
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_get_system(const tmd_batch *b, int32_t sys, double *pos, double *vel, float *forces,
+                                tmd_stream_t stream) {
+    if (!b || sys < 0 || sys >= b->S) { set_error("bad arguments"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t o = b->off[sys], n = b->off[sys + 1] - o;
+    if (pos) TMD_CUDA(cudaMemcpyAsync(pos, b->pos + 3 * o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (vel) TMD_CUDA(cudaMemcpyAsync(vel, b->vel + 3 * o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (forces) TMD_CUDA(cudaMemcpyAsync(forces, b->forces + 3 * o, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_compute(const tmd_model *model, tmd_batch *b, const int32_t *systems, int32_t n_act,
+                             double *energy, double *virial, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!model || !b || !systems || n_act < 1 || n_act > b->S) { set_error("bad arguments"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t na = 0;
+    tmd_status st;
+    if ((st = batch_activate(b, systems, n_act, s, &na)) != TMD_OK) return st;
+    if ((st = batch_eval(model, b, n_act, s)) != TMD_OK) return st;
+    TMD_CUDA(cudaMemcpyAsync(b->h_out, b->sys_out, sizeof(double) * 16 * n_act, cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < n_act; ++k) b->has_forces[systems[k]] = 1;
+    batch_results(b, n_act, energy, virial, nullptr);
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *b, const int32_t *systems, int32_t n_act, double dt_fs,
+                          int32_t nsteps, tmd_thermo *thermo, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!model || !b || !systems || n_act < 1 || n_act > b->S || nsteps < 0 || !std::isfinite(dt_fs)) {
+        set_error("bad arguments");
+        return TMD_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t na = 0;
+    tmd_status st;
+    if ((st = batch_activate(b, systems, n_act, s, &na)) != TMD_OK) return st;
+    bool need_init = false;
+    for (int k = 0; k < n_act; ++k) need_init = need_init || !b->has_forces[systems[k]];
+    if (need_init) {  // initial forces (the systems that have them are recomputed identically)
+        if ((st = batch_eval(model, b, n_act, s)) != TMD_OK) return st;
+        for (int k = 0; k < n_act; ++k) b->has_forces[systems[k]] = 1;
+    }
+    const unsigned nb = (unsigned)((b->n + 255) / 256);
+    for (int it = 0; it < nsteps; ++it) {
+        TMD_LAUNCH("k_vv_first_b", s, k_vv_first_b<<<nb, 256, 0, s>>>(b->pos, b->vel, b->forces, b->inv_mass, b->n, dt_fs,
+                                                                      b->sys_of, b->active));
+        if ((st = batch_eval(model, b, n_act, s)) != TMD_OK) return st;
+        TMD_LAUNCH("k_vv_second_b", s, k_vv_second_b<<<nb, 256, 0, s>>>(b->vel, b->forces, b->inv_mass, b->n, dt_fs,
+                                                                        b->sys_of, b->active));
+        TMD_CUDA(cudaGetLastError());
+        for (int k = 0; k < n_act; ++k) b->steps[systems[k]]++;
+    }
+    if (thermo || nsteps == 0) {
+        // kinetic terms after the second half kick
+        TMD_LAUNCH("k_sys_reduce", s, tmd::sys_reduce_launch(b->act_list, n_act, b->d_off, b->e_atom, b->w_atom, b->vel,
+                                                             b->mass, b->sys_out, s));
+    }
+    TMD_CUDA(cudaMemcpyAsync(b->h_out, b->sys_out, sizeof(double) * 16 * n_act, cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    batch_results(b, n_act, nullptr, nullptr, thermo);
     return TMD_OK;
 }
 

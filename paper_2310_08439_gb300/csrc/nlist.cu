@@ -27,32 +27,41 @@ namespace {
 constexpr int BIN_THREADS = 256;
 constexpr int NBR_WARPS = 4;
 
-// cell index of each atom, cell occupancy counts (stored at start[c+1]), per
-// block species counts; flags atoms outside the box and bad species.
+// cell index of each atom of an active system (global cell = the system's
+// first cell + local cell), cell occupancy counts (stored at start[c+1]), per
+// block species counts; flags atoms outside their box and bad species.  Atoms
+// of inactive systems get cell -1 and are skipped by the later passes.
 __global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict__ types, int64_t n,
-                      double L0, double L1, double L2, double ic0, double ic1, double ic2, int nc0, int nc1, int nc2,
-                      int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_start,
-                      int32_t *__restrict__ type_block, int32_t *__restrict__ status) {
+                      const SysParams *__restrict__ sp, const int32_t *__restrict__ sys_of,
+                      const uint8_t *__restrict__ active, int32_t *__restrict__ cell_of,
+                      int32_t *__restrict__ cell_start, int32_t *__restrict__ type_block,
+                      int32_t *__restrict__ status) {
     __shared__ int32_t s_cnt[TMD_MAX_SPECIES];
     if (threadIdx.x < TMD_MAX_SPECIES) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int t = -1;
     if (i < n) {
-        const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-        int bad = !(x >= 0.0 && x < L0 && y >= 0.0 && y < L1 && z >= 0.0 && z < L2);
-        int cx = (int)(x * ic0), cy = (int)(y * ic1), cz = (int)(z * ic2);
-        cx = min(max(cx, 0), nc0 - 1);
-        cy = min(max(cy, 0), nc1 - 1);
-        cz = min(max(cz, 0), nc2 - 1);
-        if (bad) atomicOr(status, DEV_ERR_OUTSIDE_BOX);
-        const int c = cx + nc0 * (cy + nc1 * cz);
-        cell_of[i] = c;
-        atomicAdd(&cell_start[c + 1], 1);
-        t = types[i];
-        if (t < 0 || t >= TMD_MAX_SPECIES) {
-            atomicOr(status, DEV_ERR_BAD_TYPE);
-            t = -1;
+        const int sys = sys_of ? sys_of[i] : 0;
+        if (active && !active[sys]) {
+            cell_of[i] = -1;
+        } else {
+            const SysParams &q = sp[sys];
+            const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+            const int bad = !(x >= 0.0 && x < q.L[0] && y >= 0.0 && y < q.L[1] && z >= 0.0 && z < q.L[2]);
+            int cx = (int)(x * q.ic[0]), cy = (int)(y * q.ic[1]), cz = (int)(z * q.ic[2]);
+            cx = min(max(cx, 0), q.nc[0] - 1);
+            cy = min(max(cy, 0), q.nc[1] - 1);
+            cz = min(max(cz, 0), q.nc[2] - 1);
+            if (bad) atomicOr(status, DEV_ERR_OUTSIDE_BOX);
+            const int c = q.cell_off + cx + q.nc[0] * (cy + q.nc[1] * cz);
+            cell_of[i] = c;
+            atomicAdd(&cell_start[c + 1], 1);
+            t = types[i];
+            if (t < 0 || t >= TMD_MAX_SPECIES) {
+                atomicOr(status, DEV_ERR_BAD_TYPE);
+                t = -1;
+            }
         }
     }
     const int lane = threadIdx.x & 31;
@@ -106,7 +115,7 @@ __global__ void k_fill(const double *__restrict__ pos, const int32_t *__restrict
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int t = -1;
-    if (i < n) {
+    if (i < n && cell_of[i] >= 0) {
         t = types[i];
         if (t < 0 || t >= TMD_MAX_SPECIES) t = -1;
         const int c = cell_of[i];
@@ -195,12 +204,9 @@ struct NbrParams {
     const int32_t *cell_of;
     const int32_t *cell_start;
     const float4 *cell_pos;
+    const SysParams *sp;
+    const int32_t *sys_of;
     int64_t n;
-    int nc[3], R[3], pbc[3];
-    float Lf[3];
-    double L[3];
-    double r2;            // r_list * r_list (FP64, as the definition)
-    float r2lo, r2hi;     // FP32 band outside which the FP32 screen decides
     int64_t *beg, *end;   // per-atom segment of the table
     int32_t *nbr;
     char4 *shift;
@@ -232,34 +238,41 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
     const int64_t i = (int64_t)blockIdx.x * NBR_WARPS + warp;
     if (i >= p.n) return;
     uint64_t *keys = s_keys + (size_t)warp * TMD_MAX_DEGREE;
+    const int cg = p.cell_of[i];
+    if (cg < 0) {  // atom of an inactive system
+        if (lane == 0) { p.beg[i] = 0; p.end[i] = 0; }
+        return;
+    }
+    const SysParams &sysp = p.sp[p.sys_of ? p.sys_of[i] : 0];
+    const int nc0 = sysp.nc[0], nc1 = sysp.nc[1], nc2 = sysp.nc[2];
     const double xi = p.pos[3 * i], yi = p.pos[3 * i + 1], zi = p.pos[3 * i + 2];
     const float xh = (float)xi, yh = (float)yi, zh = (float)zi;
-    const int ci = p.cell_of[i];
-    const int cx = ci % p.nc[0], cy = (ci / p.nc[0]) % p.nc[1], cz = ci / (p.nc[0] * p.nc[1]);
+    const int ci = cg - sysp.cell_off;
+    const int cx = ci % nc0, cy = (ci / nc0) % nc1, cz = ci / (nc0 * nc1);
     const unsigned lt = (1u << lane) - 1u;
     int count = 0;
-    for (int dz = -p.R[2]; dz <= p.R[2]; ++dz) {
+    for (int dz = -sysp.R[2]; dz <= sysp.R[2]; ++dz) {
         const int uz = cz + dz;
-        if (!p.pbc[2] && (uz < 0 || uz >= p.nc[2])) continue;
+        if (!sysp.pbc[2] && (uz < 0 || uz >= nc2)) continue;
         int kz;
-        const int sz = wrap_cell(uz, p.nc[2], kz);
-        const float zs = zh - (float)sz * p.Lf[2];
-        for (int dy = -p.R[1]; dy <= p.R[1]; ++dy) {
+        const int sz = wrap_cell(uz, nc2, kz);
+        const float zs = zh - (float)sz * sysp.Lh[2];
+        for (int dy = -sysp.R[1]; dy <= sysp.R[1]; ++dy) {
             const int uy = cy + dy;
-            if (!p.pbc[1] && (uy < 0 || uy >= p.nc[1])) continue;
+            if (!sysp.pbc[1] && (uy < 0 || uy >= nc1)) continue;
             int ky;
-            const int sy = wrap_cell(uy, p.nc[1], ky);
-            const float ys = yh - (float)sy * p.Lf[1];
-            const int row = p.nc[0] * (ky + p.nc[1] * kz);
-            int dx = -p.R[0];
-            while (dx <= p.R[0]) {
+            const int sy = wrap_cell(uy, nc1, ky);
+            const float ys = yh - (float)sy * sysp.Lh[1];
+            const int row = sysp.cell_off + nc0 * (ky + nc1 * kz);
+            int dx = -sysp.R[0];
+            while (dx <= sysp.R[0]) {
                 const int ux = cx + dx;
-                if (!p.pbc[0] && (ux < 0 || ux >= p.nc[0])) { ++dx; continue; }
+                if (!sysp.pbc[0] && (ux < 0 || ux >= nc0)) { ++dx; continue; }
                 int kx;
-                const int sx = wrap_cell(ux, p.nc[0], kx);
+                const int sx = wrap_cell(ux, nc0, kx);
                 int len = 1;  // run of consecutive cells with the same shift
-                while (dx + len <= p.R[0] && kx + len < p.nc[0]) ++len;
-                const float xs = xh - (float)sx * p.Lf[0];
+                while (dx + len <= sysp.R[0] && kx + len < nc0) ++len;
+                const float xs = xh - (float)sx * sysp.Lh[0];
                 const int beg = p.cell_start[row + kx], end = p.cell_start[row + kx + len];
                 const bool self_img = (sx == 0 && sy == 0 && sz == 0);
                 for (int b = beg; b < end; b += 32) {
@@ -273,14 +286,14 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
                         tj = (int)(w >> 28);
                         const float ddx = cp.x - xs, ddy = cp.y - ys, ddz = cp.z - zs;
                         const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        in = d2 < p.r2lo;
-                        band = !in && d2 < p.r2hi;
+                        in = d2 < sysp.r2lo;
+                        band = !in && d2 < sysp.r2hi;
                     }
                     // rounding band: exact FP64 decision, reached through a
                     // warp-uniform branch and an out-of-line call so that the
                     // (rare) FP64 work is not predicated onto every candidate.
                     if (__any_sync(0xffffffffu, band)) {
-                        if (band) in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, p.L[0], p.L[1], p.L[2], p.r2);
+                        if (band) in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, sysp.L[0], sysp.L[1], sysp.L[2], sysp.r2);
                     }
                     if (self_img && j == (int)i) in = false;
                     const unsigned m = __ballot_sync(0xffffffffu, in);
@@ -396,7 +409,7 @@ tmd_status scan_inclusive(T *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, c
 }  // namespace
 
 void nlist_free(tmd_nlist *nl) {
-    void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->beg, nl->end, nl->counter, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
+    void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->beg, nl->end, nl->counter, nl->sp, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
                     nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->Fq, nl->part, nl->ph, nl->pl,
                     nl->io_pos, nl->io_types, nl->io_forces, nl->io_red};
     for (void *p : ptrs)
@@ -405,22 +418,14 @@ void nlist_free(tmd_nlist *nl) {
     *nl = tmd_nlist();
 }
 
-tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
-                           const int32_t pbc[3], double r_list, tmd_nlist *nl, cudaStream_t s) {
-    if (n < 0 || n >= (int64_t(1) << 28)) {
-        set_error("n = %lld outside [0, 2^28)", (long long)n);
-        return TMD_ERR_INVALID_ARG;
-    }
-    if (n > 0 && (!pos || !types)) {
-        set_error("pos/types must be device pointers");
-        return TMD_ERR_INVALID_ARG;
-    }
+tmd_status make_sys_params(const double box[3], const int32_t pbc[3], double r_list, SysParams *q, int64_t *ncell) {
     if (!(std::isfinite(r_list) && r_list > 0.0)) {
         set_error("r_list must be finite and > 0");
         return TMD_ERR_INVALID_ARG;
     }
-    double Lmax = 0.0, vol = 1.0;
+    double Lmax = 0.0;
     int smax = 0;
+    int64_t nct = 1;
     for (int x = 0; x < 3; ++x) {
         if (!(std::isfinite(box[x]) && box[x] > 0.0)) {
             set_error("box[%d] must be finite and > 0", x);
@@ -436,94 +441,25 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
         const double cs = box[x] / nc;
         int R = (int)std::ceil((r_list + margin) / cs);
         if (R < 1) R = 1;
-        nl->nc[x] = nc;
-        nl->R[x] = R;
-        nl->pbc[x] = pbc[x] ? 1 : 0;
-        nl->box[x] = box[x];
+        q->nc[x] = nc;
+        q->R[x] = R;
+        q->pbc[x] = pbc[x] ? 1 : 0;
+        q->L[x] = box[x];
+        q->ic[x] = nc / box[x];
+        q->Lh[x] = (float)box[x];
+        q->Ll[x] = (float)(box[x] - (double)q->Lh[x]);
         if (pbc[x]) {
             const int lo = -((R + nc - 1) / nc), hi = (nc - 1 + R) / nc;
             smax = std::max(smax, std::max(-lo, hi));
         }
         Lmax = std::max(Lmax, box[x]);
-        vol *= box[x];
+        nct *= nc;
     }
     if (smax > 15) {
         set_error("r_list %.3f needs image shifts beyond +-15 boxes", r_list);
         return TMD_ERR_CAPACITY;
     }
-    nl->ncell = (int64_t)nl->nc[0] * nl->nc[1] * nl->nc[2];
-    nl->n = n;
-    nl->r_list = r_list;
-    nl->built = 0;
-
-    tmd_status st;
-    const int64_t nb_bin = (n + BIN_THREADS - 1) / BIN_THREADS;
-    if ((st = grow(&nl->cell_of, &nl->cap_atoms, n)) != TMD_OK) return st;
-    if ((st = grow(&nl->cell_atoms, &nl->cap_cell_atoms, n)) != TMD_OK) return st;
-    if ((st = grow(&nl->cell_pos, &nl->cap_cell_pos, n)) != TMD_OK) return st;
-    if ((st = grow(&nl->perm, &nl->cap_perm, n)) != TMD_OK) return st;
-    if ((st = grow(&nl->beg, &nl->cap_beg, n)) != TMD_OK) return st;
-    if ((st = grow(&nl->end, &nl->cap_end, n)) != TMD_OK) return st;
-    if ((st = grow(&nl->cell_start, &nl->cap_cells, nl->ncell + 1)) != TMD_OK) return st;
-    if ((st = grow(&nl->cell_fill, &nl->cap_cell_fill, nl->ncell)) != TMD_OK) return st;
-    if ((st = grow(&nl->type_block, &nl->cap_type_blocks, (nb_bin + 1) * TMD_MAX_SPECIES)) != TMD_OK) return st;
-    if ((st = grow(&nl->status, &nl->cap_status, 4)) != TMD_OK) return st;
-    if ((st = grow(&nl->type_start, &nl->cap_type_start, TMD_MAX_SPECIES + 1)) != TMD_OK) return st;
-    if ((st = grow(&nl->counter, &nl->cap_counter, 1)) != TMD_OK) return st;
-    if (!nl->h_pinned) TMD_CUDA(cudaMallocHost((void **)&nl->h_pinned, 16 * sizeof(int64_t)));
-    // capacity for the entries: the previous table's size, or the uniform
-    // density estimate, with headroom; a build that overflows is rerun once
-    // with the exact size
-    {
-        const double est = (double)n * ((double)n / vol) * (4.0 / 3.0) * M_PI * r_list * r_list * r_list;
-        const int64_t want = (int64_t)std::max<double>(1.2 * est, 1.1 * (double)nl->nnz) + 1024;
-        if (nl->cap_nnz < want) {
-            if ((st = grow(&nl->nbr, &nl->cap_nnz, want)) != TMD_OK) return st;
-        }
-        if (nl->cap_shift < nl->cap_nnz) {
-            if ((st = grow(&nl->shift, &nl->cap_shift, nl->cap_nnz)) != TMD_OK) return st;
-        }
-    }
-    TMD_CUDA(cudaMemsetAsync(nl->status, 0, sizeof(int32_t), s));
-    TMD_CUDA(cudaMemsetAsync(nl->cell_start, 0, sizeof(int32_t) * (nl->ncell + 1), s));
-    TMD_CUDA(cudaMemsetAsync(nl->cell_fill, 0, sizeof(int32_t) * nl->ncell, s));
-    TMD_CUDA(cudaMemsetAsync(nl->type_start, 0, sizeof(int32_t) * (TMD_MAX_SPECIES + 1), s));
-    TMD_CUDA(cudaMemsetAsync(nl->counter, 0, sizeof(unsigned long long), s));
-
-    if (n > 0) {
-        TMD_LAUNCH("k_bin", s, k_bin<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, box[0], box[1], box[2],
-                                                                            nl->nc[0] / box[0], nl->nc[1] / box[1],
-                                                                            nl->nc[2] / box[2], nl->nc[0], nl->nc[1],
-                                                                            nl->nc[2], nl->cell_of, nl->cell_start,
-                                                                            nl->type_block, nl->status));
-        TMD_CUDA(cudaGetLastError());
-        if ((st = scan_inclusive<int32_t>(nl->cell_start + 1, nl->ncell, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK)
-            return st;
-        TMD_LAUNCH("k_type_scan", s, k_type_scan<<<1, 32 * TMD_MAX_SPECIES, 0, s>>>(nl->type_block, (int)nb_bin,
-                                                                                    nl->type_start));
-        TMD_LAUNCH("k_fill", s, k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start,
-                                                                              nl->cell_fill, nl->cell_atoms,
-                                                                              nl->type_block, nl->type_start, nl->perm));
-        const unsigned nb_cell = (unsigned)std::min<int64_t>((nl->ncell + CELL_SORT_WARPS - 1) / CELL_SORT_WARPS, 65535);
-        TMD_LAUNCH("k_cell_sort", s, k_cell_sort<<<nb_cell, CELL_SORT_WARPS * 32, 0, s>>>(
-                                          nl->cell_start, nl->ncell, nl->cell_atoms, pos, types, nl->cell_pos, nl->status));
-        TMD_CUDA(cudaGetLastError());
-    }
-
-    NbrParams p;
-    p.pos = pos;
-    p.cell_of = nl->cell_of;
-    p.cell_start = nl->cell_start;
-    p.cell_pos = nl->cell_pos;
-    p.n = n;
-    for (int x = 0; x < 3; ++x) {
-        p.nc[x] = nl->nc[x];
-        p.R[x] = nl->R[x];
-        p.pbc[x] = nl->pbc[x];
-        p.Lf[x] = (float)box[x];
-        p.L[x] = box[x];
-    }
-    p.r2 = r_list * r_list;
+    q->r2 = r_list * r_list;
     {
         // FP32 screen error bound: |x_f - x| <= L 2^-24 per coordinate, the
         // shift product/difference add (1 + 2|s|) L 2^-24, the final
@@ -533,9 +469,99 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
         const double e = ((4.0 + 4.0 * smax) * Lmax + 2.0 * (r_list + 1.0)) * u;
         const double rr = r_list + 1.0;
         const double margin = 2.0 * (2.0 * std::sqrt(3.0) * rr * e + 3.0 * e * e + 4.0 * rr * rr * u);
-        p.r2lo = std::nextafter((float)(p.r2 - margin), -INFINITY);
-        p.r2hi = std::nextafter((float)(p.r2 + margin), INFINITY);
+        q->r2lo = std::nextafter((float)(q->r2 - margin), -INFINITY);
+        q->r2hi = std::nextafter((float)(q->r2 + margin), INFINITY);
     }
+    q->cell_off = 0;
+    *ncell = nct;
+    return TMD_OK;
+}
+
+tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int n_sys, const SysParams *sp_host,
+                        const int32_t *sys_of, const uint8_t *active, const int64_t *n_of_sys, int64_t ncell_total,
+                        tmd_nlist *nl, cudaStream_t s) {
+    if (n < 0 || n >= (int64_t(1) << 28)) {
+        set_error("n = %lld outside [0, 2^28)", (long long)n);
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (n > 0 && (!pos || !types)) {
+        set_error("pos/types must be device pointers");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (ncell_total >= (int64_t(1) << 31)) {
+        set_error("too many binning cells");
+        return TMD_ERR_CAPACITY;
+    }
+    nl->ncell = ncell_total;
+    nl->n = n;
+    nl->built = 0;
+    tmd_status st;
+    const int64_t nb_bin = (n + BIN_THREADS - 1) / BIN_THREADS;
+    if ((st = grow(&nl->cell_of, &nl->cap_atoms, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_atoms, &nl->cap_cell_atoms, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_pos, &nl->cap_cell_pos, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->perm, &nl->cap_perm, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->beg, &nl->cap_beg, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->end, &nl->cap_end, n)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_start, &nl->cap_cells, ncell_total + 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->cell_fill, &nl->cap_cell_fill, ncell_total)) != TMD_OK) return st;
+    if ((st = grow(&nl->type_block, &nl->cap_type_blocks, (nb_bin + 1) * TMD_MAX_SPECIES)) != TMD_OK) return st;
+    if ((st = grow(&nl->status, &nl->cap_status, 4)) != TMD_OK) return st;
+    if ((st = grow(&nl->type_start, &nl->cap_type_start, TMD_MAX_SPECIES + 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->counter, &nl->cap_counter, 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->sp, &nl->cap_sp, n_sys)) != TMD_OK) return st;
+    if (!nl->h_pinned) TMD_CUDA(cudaMallocHost((void **)&nl->h_pinned, 16 * sizeof(int64_t)));
+    TMD_CUDA(cudaMemcpyAsync(nl->sp, sp_host, sizeof(SysParams) * n_sys, cudaMemcpyHostToDevice, s));
+    // capacity for the entries: the previous table's size, or the uniform
+    // density estimate, with headroom; a build that overflows is rerun once
+    // with the exact size
+    {
+        double est = 0.0;
+        for (int k = 0; k < n_sys; ++k) {
+            const double nk = (double)(n_of_sys ? n_of_sys[k] : n);
+            const double vol = sp_host[k].L[0] * sp_host[k].L[1] * sp_host[k].L[2];
+            const double r = std::sqrt(sp_host[k].r2);
+            est += nk * (nk / vol) * (4.0 / 3.0) * M_PI * r * r * r;
+        }
+        const int64_t want = (int64_t)std::max<double>(1.2 * est, 1.1 * (double)nl->nnz) + 1024;
+        if (nl->cap_nnz < want)
+            if ((st = grow(&nl->nbr, &nl->cap_nnz, want)) != TMD_OK) return st;
+        if (nl->cap_shift < nl->cap_nnz)
+            if ((st = grow(&nl->shift, &nl->cap_shift, nl->cap_nnz)) != TMD_OK) return st;
+    }
+    TMD_CUDA(cudaMemsetAsync(nl->status, 0, sizeof(int32_t), s));
+    TMD_CUDA(cudaMemsetAsync(nl->cell_start, 0, sizeof(int32_t) * (ncell_total + 1), s));
+    TMD_CUDA(cudaMemsetAsync(nl->cell_fill, 0, sizeof(int32_t) * ncell_total, s));
+    TMD_CUDA(cudaMemsetAsync(nl->type_start, 0, sizeof(int32_t) * (TMD_MAX_SPECIES + 1), s));
+    TMD_CUDA(cudaMemsetAsync(nl->counter, 0, sizeof(unsigned long long), s));
+
+    if (n > 0) {
+        TMD_LAUNCH("k_bin", s, k_bin<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->sp, sys_of, active,
+                                                                            nl->cell_of, nl->cell_start,
+                                                                            nl->type_block, nl->status));
+        TMD_CUDA(cudaGetLastError());
+        if ((st = scan_inclusive<int32_t>(nl->cell_start + 1, ncell_total, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK)
+            return st;
+        TMD_LAUNCH("k_type_scan", s, k_type_scan<<<1, 32 * TMD_MAX_SPECIES, 0, s>>>(nl->type_block, (int)nb_bin,
+                                                                                    nl->type_start));
+        TMD_LAUNCH("k_fill", s, k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start,
+                                                                              nl->cell_fill, nl->cell_atoms,
+                                                                              nl->type_block, nl->type_start, nl->perm));
+        const unsigned nb_cell = (unsigned)std::min<int64_t>((ncell_total + CELL_SORT_WARPS - 1) / CELL_SORT_WARPS, 65535);
+        TMD_LAUNCH("k_cell_sort", s, k_cell_sort<<<nb_cell, CELL_SORT_WARPS * 32, 0, s>>>(
+                                          nl->cell_start, ncell_total, nl->cell_atoms, pos, types, nl->cell_pos,
+                                          nl->status));
+        TMD_CUDA(cudaGetLastError());
+    }
+
+    NbrParams p;
+    p.pos = pos;
+    p.cell_of = nl->cell_of;
+    p.cell_start = nl->cell_start;
+    p.cell_pos = nl->cell_pos;
+    p.sp = nl->sp;
+    p.sys_of = sys_of;
+    p.n = n;
     p.beg = nl->beg;
     p.end = nl->end;
     p.counter = nl->counter;
@@ -590,9 +616,26 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
     int32_t tstart[TMD_MAX_SPECIES + 1];
     std::memcpy(tstart, &nl->h_pinned[2], sizeof(tstart));
     for (int t = 0; t < TMD_MAX_SPECIES; ++t) nl->type_count[t] = tstart[t + 1] - tstart[t];
+    nl->n_active = tstart[TMD_MAX_SPECIES];
     nl->nnz = nnz;
     nl->built = 1;
     return TMD_OK;
+}
+
+tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
+                           const int32_t pbc[3], double r_list, tmd_nlist *nl, cudaStream_t s) {
+    SysParams q;
+    int64_t ncell = 0;
+    tmd_status st = make_sys_params(box, pbc, r_list, &q, &ncell);
+    if (st != TMD_OK) return st;
+    for (int x = 0; x < 3; ++x) {
+        nl->nc[x] = q.nc[x];
+        nl->R[x] = q.R[x];
+        nl->pbc[x] = q.pbc[x];
+        nl->box[x] = box[x];
+    }
+    nl->r_list = r_list;
+    return build_tables(pos, types, n, 1, &q, nullptr, nullptr, nullptr, ncell, nl, s);
 }
 
 }  // namespace tmd

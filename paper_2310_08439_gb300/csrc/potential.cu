@@ -125,6 +125,12 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, int a, int64_t beg
     int qn = 0;
     const unsigned lt = (1u << lane) - 1u;
     const float4 ih = nl.ph[a], il = nl.pl[a];
+    float Lh0 = nl.Lh[0], Lh1 = nl.Lh[1], Lh2 = nl.Lh[2], Ll0 = nl.Ll[0], Ll1 = nl.Ll[1], Ll2 = nl.Ll[2];
+    if (nl.sys_of) {  // batched: the box of this atom's system
+        const SysParams &q = nl.sp[nl.sys_of[a]];
+        Lh0 = q.Lh[0]; Lh1 = q.Lh[1]; Lh2 = q.Lh[2];
+        Ll0 = q.Ll[0]; Ll1 = q.Ll[1]; Ll2 = q.Ll[2];
+    }
     for (int64_t base = beg; base < end; base += 32) {
         const int64_t c = base + lane;
         bool v = false;
@@ -135,9 +141,9 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, int a, int64_t beg
             const char4 s = nl.shift[c];
             const float4 jh = nl.ph[j], jl = nl.pl[j];
             float dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l;
-            diff_df(jh.x, jl.x, ih.x, il.x, s.x, nl.Lh[0], nl.Ll[0], dxh, dxl);
-            diff_df(jh.y, jl.y, ih.y, il.y, s.y, nl.Lh[1], nl.Ll[1], dyh, dyl);
-            diff_df(jh.z, jl.z, ih.z, il.z, s.z, nl.Lh[2], nl.Ll[2], dzh, dzl);
+            diff_df(jh.x, jl.x, ih.x, il.x, s.x, Lh0, Ll0, dxh, dxl);
+            diff_df(jh.y, jl.y, ih.y, il.y, s.y, Lh1, Ll1, dyh, dyl);
+            diff_df(jh.z, jl.z, ih.z, il.z, s.z, Lh2, Ll2, dzh, dzl);
             norm2_df(dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l);
             v = (r2h < rc2h) || (r2h == rc2h && r2l < rc2l);
             e = make_float4(dxh, dyh, dzh, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
@@ -678,12 +684,15 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
-template <int K, int S>
+// PAW (batched): each atom's virial is summed over its own pairs and written
+// to w_atom [atoms][9] for per-system reductions; otherwise lanes keep
+// compensated running sums and each block writes one FP64 partial.
+template <int K, int S, bool PAW>
 __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                    const int32_t *__restrict__ types, const float *__restrict__ Pin,
                                                    const float *__restrict__ dG,
                                                    unsigned long long *__restrict__ Fq,
-                                                   double *__restrict__ part_w) {
+                                                   double *__restrict__ part_w, float *__restrict__ w_atom) {
     constexpr int KPL = K / 8;
     constexpr int PSTR = K * NMOM + 4;   // per-species stride of P' (bank offset between species)
     constexpr int Dd = S * K * 4;
@@ -732,6 +741,9 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
             }
         __syncwarp();
         long long fx = 0, fy = 0, fz = 0;
+        float wa[PAW ? 9 : 1];
+#pragma unroll
+        for (int t = 0; t < (PAW ? 9 : 1); ++t) wa[t] = 0.f;
         for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
@@ -803,7 +815,10 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
 #pragma unroll
                       for (int al = 0; al < 3; ++al)
 #pragma unroll
-                          for (int be = 0; be < 3; ++be) kahan_add(wsum[al * 3 + be], wcmp[al * 3 + be], -D[al] * gv[be]);
+                          for (int be = 0; be < 3; ++be) {
+                              if constexpr (PAW) wa[al * 3 + be] -= D[al] * gv[be];
+                              else kahan_add(wsum[al * 3 + be], wcmp[al * 3 + be], -D[al] * gv[be]);
+                          }
                   });
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -816,6 +831,15 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
             atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fy);
             atomicAdd(&Fq[3 * (int64_t)a + 2], (unsigned long long)fz);
         }
+        if constexpr (PAW) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                float v = wa[t];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) w_atom[(size_t)a * 9 + t] = v;
+            }
+        }
         __syncwarp();
     }
     // virial: per-lane compensated sums -> FP64 block total
@@ -827,7 +851,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
         if (lane == 0) s_w[warp][t] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 9) {
+    if (!PAW && threadIdx.x < 9) {
         double v = 0.0;
         for (int w = 0; w < PW; ++w) v += s_w[w][threadIdx.x];
         part_w[(size_t)blockIdx.x * 9 + threadIdx.x] = v;
@@ -866,21 +890,74 @@ __global__ void k_forces_out(const long long *__restrict__ Fq, int64_t n, float 
     if (i < 3 * n) forces[i] = (float)((double)Fq[i] * FQ_INV);
 }
 
+// forces of the atoms listed in perm (batched: only the active systems' atoms)
+__global__ void k_forces_out_perm(const long long *__restrict__ Fq, const int32_t *__restrict__ perm, int64_t n,
+                                  float *__restrict__ forces) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t a = perm[p];
+    forces[3 * a] = (float)((double)Fq[3 * a] * FQ_INV);
+    forces[3 * a + 1] = (float)((double)Fq[3 * a + 1] * FQ_INV);
+    forces[3 * a + 2] = (float)((double)Fq[3 * a + 2] * FQ_INV);
+}
+
+// Per-system FP64 sums over each active system's atom range (one block per
+// system, fixed order): out[b] = (E, W[9], sum m v_a v_b [xx yy zz xy xz yz]).
+__global__ void k_sys_reduce(const int32_t *__restrict__ act, const int64_t *__restrict__ off,
+                             const float *__restrict__ e_atom, const float *__restrict__ w_atom,
+                             const double *__restrict__ vel, const double *__restrict__ mass, double *__restrict__ out) {
+    __shared__ double s[16][8];
+    const int sys = act[blockIdx.x];
+    const int64_t beg = off[sys], end = off[sys + 1];
+    double v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = 0.0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        v[0] += (double)e_atom[i];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) v[1 + t] += (double)w_atom[i * 9 + t];
+        if (vel) {
+            const double m = mass[i], x = vel[3 * i], y = vel[3 * i + 1], z = vel[3 * i + 2];
+            v[10] += m * x * x; v[11] += m * y * y; v[12] += m * z * z;
+            v[13] += m * x * y; v[14] += m * x * z; v[15] += m * y * z;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+        if (lane == 0) s[t][warp] = v[t];
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        double acc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += s[threadIdx.x][w];
+        out[(size_t)blockIdx.x * 16 + threadIdx.x] = acc;
+    }
+}
+
 template <int K, int S>
 tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
-                               tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool forward) {
+                               tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool forward,
+                               float *w_atom) {
     if (forward)
         TMD_LAUNCH("k_desc", s, k_desc<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+    else if (w_atom)
+        TMD_LAUNCH("k_force", s, k_force<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->Fq,
+                                                                            part_w, w_atom));
     else
-        TMD_LAUNCH("k_force", s, k_force<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->Fq, part_w));
+        TMD_LAUNCH("k_force", s, k_force<K, S, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->Fq,
+                                                                             part_w, nullptr));
     TMD_CUDA(cudaGetLastError());
     return TMD_OK;
 }
 
 tmd_status dispatch_pair(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
-                         tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool fwd) {
+                         tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool fwd, float *w_atom = nullptr) {
 #define TMD_CASE(KK, SS) \
-    if (dm.K == KK && dm.S == SS) return launch_pair_kernels<KK, SS>(dm, dn, pos, types, nl, part_w, nblk, s, fwd);
+    if (dm.K == KK && dm.S == SS)                                                                    \
+        return launch_pair_kernels<KK, SS>(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
     TMD_CASE(8, 1) TMD_CASE(8, 2) TMD_CASE(8, 3) TMD_CASE(8, 4)
     TMD_CASE(16, 1) TMD_CASE(16, 2) TMD_CASE(16, 3) TMD_CASE(16, 4)
     TMD_CASE(32, 1) TMD_CASE(32, 2) TMD_CASE(32, 3)
@@ -901,6 +978,11 @@ int sm_count() {
 }
 
 }  // namespace
+
+tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                             int64_t n_total, const int32_t *sys_of, float *forces, float *e_atom, float *w_atom,
+                             const int32_t *act_list, int n_act, const int64_t *sys_off, const double *vel,
+                             const double *mass, double *sys_out, cudaStream_t s);
 
 size_t mlp_bf16_smem_bytes(const DevModel &dm) {
     int maxw = dm.Dd;
@@ -1265,6 +1347,62 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     if (forces) {
         TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
                                            reinterpret_cast<const long long *>(w.Fq), n, forces));
+        TMD_CUDA(cudaGetLastError());
+    }
+    return TMD_OK;
+}
+
+}  // namespace tmd
+
+namespace tmd {
+
+void sys_reduce_launch(const int32_t *act, int n_act, const int64_t *off, const float *e_atom, const float *w_atom,
+                       const double *vel, const double *mass, double *out, cudaStream_t s) {
+    k_sys_reduce<<<n_act, 256, 0, s>>>(act, off, e_atom, w_atom, vel, mass, out);
+}
+
+tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                             int64_t n_total, const int32_t *sys_of, float *forces, float *e_atom, float *w_atom,
+                             const int32_t *act_list, int n_act, const int64_t *sys_off, const double *vel,
+                             const double *mass, double *sys_out, cudaStream_t s) {
+    if (!model || !nl || !nl->built) {
+        set_error("null model or table not built");
+        return TMD_ERR_INVALID_ARG;
+    }
+    const DevModel &dm = model->dm;
+    for (int t = dm.S; t < TMD_MAX_SPECIES; ++t)
+        if (nl->type_count[t] != 0) {
+            set_error("species id %d present but the model has %d species", t, dm.S);
+            return TMD_ERR_INVALID_ARG;
+        }
+    const int64_t na = nl->n_active;  // atoms of the active systems, in perm
+    tmd_status st;
+    if (na > 0) {
+        if ((st = grow(&nl->G, &nl->cap_G, n_total * dm.Dd)) != TMD_OK) return st;
+        if ((st = grow(&nl->dG, &nl->cap_dG, n_total * dm.Dd)) != TMD_OK) return st;
+        if ((st = grow(&nl->P, &nl->cap_P, n_total * dm.S * dm.K * NMOM)) != TMD_OK) return st;
+        if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * n_total)) != TMD_OK) return st;
+        const int nblk = (int)std::min<int64_t>((na + PW - 1) / PW, (int64_t)sm_count() * 16);
+        const int ntile = (int)((na + MT - 1) / MT);
+        if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
+        if ((st = split_positions(nl, pos, n_total, s)) != TMD_OK) return st;
+        DevNlist dn = dev_nlist(nl, na, nl->box);
+        dn.sp = nl->sp;
+        dn.sys_of = sys_of;
+        TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n_total, s));
+        if ((st = dispatch_pair(dm, dn, pos, types, nl, nullptr, nblk, s, true)) != TMD_OK) return st;
+        int ne = 0;
+        if ((st = launch_network(dm, nl->perm, types, na, nl->G, nl->dG, e_atom, nl->part, &ne, s)) != TMD_OK)
+            return st;
+        if ((st = dispatch_pair(dm, dn, pos, types, nl, nl->part + ntile, nblk, s, false, w_atom)) != TMD_OK)
+            return st;
+        TMD_LAUNCH("k_forces_out_perm", s, k_forces_out_perm<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(
+                                               reinterpret_cast<const long long *>(nl->Fq), nl->perm, na, forces));
+        TMD_CUDA(cudaGetLastError());
+    }
+    if (n_act > 0) {
+        TMD_LAUNCH("k_sys_reduce", s, k_sys_reduce<<<n_act, 256, 0, s>>>(act_list, sys_off, e_atom, w_atom, vel, mass,
+                                                                         sys_out));
         TMD_CUDA(cudaGetLastError());
     }
     return TMD_OK;

@@ -38,18 +38,32 @@ struct DevModel {
     int off_b[MAX_LAYERS];              // offset of layer l in wb[s] / hb[s]
 };
 
+// One system of a batch (a single evaluation is a batch of one): box, cell
+// grid, first global cell, list radius and the FP32 screening band.
+struct SysParams {
+    double L[3];        // box lengths
+    double ic[3];       // cells per unit length (nc / L)
+    double r2;          // list radius squared (FP64, as the definition)
+    float Lh[3], Ll[3]; // box as FP32 hi + lo
+    float r2lo, r2hi;   // FP32 band outside which the FP32 screen decides
+    int nc[3], R[3], pbc[3];
+    int cell_off;       // first global cell of this system
+};
+
 // Neighbour table as seen by kernels.
 struct DevNlist {
-    const int64_t *beg;   // [n] first entry of atom a
-    const int64_t *end;   // [n] one past its last entry
-    const int32_t *nbr;   // [nnz]
-    const char4 *shift;   // [nnz] (sx, sy, sz, species of j)
-    const int32_t *perm;  // [n] atoms grouped by species, index order within a species
-    const float4 *ph;     // [n] positions, FP32 high part
-    const float4 *pl;     // [n] positions, FP32 low part (x = hi + lo)
-    double box[3];
-    float Lh[3], Ll[3];   // box as hi + lo
-    int64_t n;
+    const int64_t *beg = nullptr;   // [n] first entry of atom a
+    const int64_t *end = nullptr;   // [n] one past its last entry
+    const int32_t *nbr = nullptr;   // [nnz]
+    const char4 *shift = nullptr;   // [nnz] (sx, sy, sz, species of j)
+    const int32_t *perm = nullptr;  // [n] atoms grouped by species, index order within a species
+    const float4 *ph = nullptr;     // [n] positions, FP32 high part
+    const float4 *pl = nullptr;     // [n] positions, FP32 low part (x = hi + lo)
+    const SysParams *sp = nullptr;  // per-system boxes (batched), or nullptr
+    const int32_t *sys_of = nullptr; // [atoms] system of each atom (batched), or nullptr
+    double box[3] = {0, 0, 0};
+    float Lh[3] = {0, 0, 0}, Ll[3] = {0, 0, 0};  // box as hi + lo (single system)
+    int64_t n = 0;                  // atoms in perm
 };
 
 }  // namespace tmd
@@ -71,6 +85,7 @@ struct tmd_nlist {
     int R[3] = {1, 1, 1};
     int64_t ncell = 0;
     int64_t nnz = 0;
+    int64_t n_active = 0;   // atoms binned and listed by the last build
     int built = 0;
     int32_t type_count[TMD_MAX_SPECIES] = {0, 0, 0, 0};
 
@@ -89,6 +104,7 @@ struct tmd_nlist {
     int32_t *status = nullptr;       int64_t cap_status = 0;       // [1] device status bits
     int32_t *type_block = nullptr;   int64_t cap_type_blocks = 0;  // [blocks][MAX_SPECIES]
     int32_t *type_start = nullptr;   int64_t cap_type_start = 0;   // [MAX_SPECIES + 1]
+    tmd::SysParams *sp = nullptr;    int64_t cap_sp = 0;           // per-system parameters (device)
     int64_t *scan_tmp = nullptr;     int64_t cap_scan = 0;
     int64_t *h_pinned = nullptr;     // host pinned scratch (16 int64)
 
@@ -178,6 +194,23 @@ tmd_status grow(T **ptr, int64_t *cap, int64_t need) {
 void nlist_free(tmd_nlist *nl);
 
 // Launchers (stream-ordered, no synchronisation unless stated).
+// Per-system grid for a list radius (host); returns CAPACITY if the radius
+// needs image shifts beyond +-15 boxes.
+tmd_status make_sys_params(const double box[3], const int32_t pbc[3], double r_list, SysParams *sp, int64_t *ncell);
+// Bin and list the atoms of the active systems (sys_of / active may be
+// nullptr for a single system); synchronises once.
+tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int n_sys, const SysParams *sp_host,
+                        const int32_t *sys_of, const uint8_t *active, const int64_t *n_of_sys, int64_t ncell_total,
+                        tmd_nlist *nl, cudaStream_t s);
+// Evaluate the atoms listed by the last build_tables of nl (batched): per
+// atom energies and virials, forces of the active atoms, per-system FP64
+// reductions (energy, virial, m v v) for the active systems in act_list.
+tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                             int64_t n_total, const int32_t *sys_of, float *forces, float *e_atom, float *w_atom,
+                             const int32_t *act_list, int n_act, const int64_t *sys_off, const double *vel,
+                             const double *mass, double *sys_out, cudaStream_t s);
+void sys_reduce_launch(const int32_t *act, int n_act, const int64_t *off, const float *e_atom, const float *w_atom,
+                       const double *vel, const double *mass, double *out, cudaStream_t s);
 tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
                            const int32_t pbc[3], double r_list, tmd_nlist *nl, cudaStream_t s);
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,

@@ -77,6 +77,12 @@ _SIGS = {
     "tmd_step": (C.c_int, [_P, _P, C.c_double, C.c_int32, C.c_int32, C.POINTER(Thermo), _P]),
     "tmd_step_host": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32,
                                 C.POINTER(Thermo), _P]),
+    "tmd_batch_create": (C.c_int, [C.c_int32, _P, _P, _P, C.POINTER(_P)]),
+    "tmd_batch_destroy": (C.c_int, [_P]),
+    "tmd_batch_set_system": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
+    "tmd_batch_get_system": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "tmd_batch_compute": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, _P]),
+    "tmd_batch_step": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int32, _P, _P]),
     "tmd_profile_enable": (C.c_int, [C.c_int32]),
     "tmd_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
     "tmd_launch_count": (C.c_int64, []),
@@ -310,4 +316,57 @@ class System:
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.tmd_system_destroy(self.handle)
+            self.handle = None
+
+
+class Batch:
+    """Many resident systems evaluated / advanced together (tmd_batch)."""
+
+    def __init__(self, systems):
+        """systems: list of inputs.System (pos, types, box, pbc, vel, masses)."""
+        S = len(systems)
+        n = np.array([x.n for x in systems], dtype=np.int64)
+        boxes = np.ascontiguousarray(np.array([x.box for x in systems], dtype=np.float64))
+        pbc = np.ascontiguousarray(np.array([x.pbc for x in systems], dtype=np.int32))
+        h = _P()
+        check(lib().tmd_batch_create(S, n.ctypes.data_as(_P), boxes.ctypes.data_as(_P), pbc.ctypes.data_as(_P),
+                                     C.byref(h)))
+        self.handle = h
+        self.n = n
+        for k, x in enumerate(systems):
+            self.set_system(k, x)
+
+    def set_system(self, k, x, stream=None):
+        pos = np.ascontiguousarray(x.pos, dtype=np.float64)
+        vel = None if x.vel is None else np.ascontiguousarray(x.vel, dtype=np.float64)
+        types = np.ascontiguousarray(x.types, dtype=np.int32)
+        masses = np.ascontiguousarray(x.masses if x.masses is not None else np.full(x.n, 55.845), dtype=np.float64)
+        check(lib().tmd_batch_set_system(self.handle, int(k), pos.ctypes.data_as(_P),
+                                         None if vel is None else vel.ctypes.data_as(_P),
+                                         types.ctypes.data_as(_P), masses.ctypes.data_as(_P), _stream(stream)))
+
+    def get_system(self, k, stream=None):
+        m = int(self.n[k])
+        pos = np.zeros((m, 3)); vel = np.zeros((m, 3)); f = np.zeros((m, 3), dtype=np.float32)
+        check(lib().tmd_batch_get_system(self.handle, int(k), pos.ctypes.data_as(_P), vel.ctypes.data_as(_P),
+                                         f.ctypes.data_as(_P), _stream(stream)))
+        return pos, vel, f
+
+    def compute(self, model, systems, stream=None):
+        ids = np.ascontiguousarray(systems, dtype=np.int32)
+        e = np.zeros(ids.size); w = np.zeros((ids.size, 9))
+        check(lib().tmd_batch_compute(model.handle, self.handle, ids.ctypes.data_as(_P), int(ids.size),
+                                      e.ctypes.data_as(_P), w.ctypes.data_as(_P), _stream(stream)))
+        return e, w.reshape(-1, 3, 3)
+
+    def step(self, model, systems, dt, nsteps, stream=None):
+        ids = np.ascontiguousarray(systems, dtype=np.int32)
+        th = (Thermo * max(ids.size, 1))()
+        check(lib().tmd_batch_step(model.handle, self.handle, ids.ctypes.data_as(_P), int(ids.size), float(dt),
+                                   int(nsteps), C.cast(th, _P), _stream(stream)))
+        return [th[k].as_dict() for k in range(ids.size)]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tmd_batch_destroy(self.handle)
             self.handle = None

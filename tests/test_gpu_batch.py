@@ -1,0 +1,88 @@
+"""Batches (many resident systems evaluated by one set of launches) against
+single-system evaluations and the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2310_08439_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _single(tmd, model, s):
+    import torch
+    m = tmd.Model(model)
+    nl = tmd.NeighborList()
+    pos = torch.as_tensor(s.pos, dtype=torch.float64, device="cuda")
+    types = torch.as_tensor(s.types, dtype=torch.int32, device="cuda")
+    nl.build(pos, types, s.box, s.pbc, model.rc)
+    out = tmd.evaluate(m, nl, pos, types, s.box)
+    torch.cuda.synchronize()
+    return (float(out["energy"].item()), out["forces"].double().cpu().numpy(),
+            out["virial"].cpu().numpy().reshape(3, 3))
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    w = I.batch(n_systems=10, seed=21)
+    # keep the test quick: drop the largest systems
+    w.systems = [s for s in w.systems if s.n <= 3000][:8]
+    return w
+
+
+def test_batch_equals_single_and_oracle(tmdlib, small_batch):
+    w = small_batch
+    m = tmdlib.Model(w.model)
+    b = tmdlib.Batch(w.systems)
+    ids = list(range(len(w.systems)))
+    E, W = b.compute(m, ids)
+    om = O.OracleModel(w.model)
+    for k, s in enumerate(w.systems):
+        e1, f1, w1 = _single(tmdlib, w.model, s)
+        _, _, fb = b.get_system(k)
+        assert abs(E[k] - e1) <= 1e-12 * abs(e1) + 1e-9, k
+        assert np.abs(fb - f1).max() <= 1e-6 * max(np.abs(f1).max(), 1e-6), k
+        assert np.abs(W[k] - w1).max() <= 1e-6 * max(np.abs(w1).max(), 1e-6), k
+        if s.n <= 1200:
+            o = O.evaluate(om, s.pos, s.types, s.box, s.pbc)
+            rms = np.sqrt((o["forces"] ** 2).mean())
+            assert abs(E[k] - o["energy"]) <= 1e-6 * abs(o["energy"]), k
+            assert np.abs(fb - o["forces"]).max() <= 1e-5 * rms, k
+            assert np.abs(W[k] - o["virial"]).max() <= 1e-5 * np.abs(o["virial"]).max(), k
+
+
+def test_batch_subset_leaves_others_untouched(tmdlib, small_batch):
+    w = small_batch
+    m = tmdlib.Model(w.model)
+    b = tmdlib.Batch(w.systems)
+    E_all, _ = b.compute(m, list(range(len(w.systems))))
+    before = [b.get_system(k)[2].copy() for k in range(len(w.systems))]
+    sub = [5, 1, 3]
+    E_sub, _ = b.compute(m, sub)
+    for j, k in enumerate(sub):
+        assert E_sub[j] == E_all[k]
+    for k in range(len(w.systems)):
+        assert np.array_equal(b.get_system(k)[2], before[k])
+
+
+def test_batch_step_matches_system_step(tmdlib, small_batch):
+    w = small_batch
+    m = tmdlib.Model(w.model)
+    systems = [s for s in w.systems[:3]]
+    rng = np.random.default_rng(0)
+    for s in systems:
+        s.vel = I.maxwell_velocities(s.masses, 300.0, rng)
+    b = tmdlib.Batch(systems)
+    th = b.step(m, [0, 1, 2], 1.0, 5)
+    for k, s in enumerate(systems):
+        g = tmdlib.System(s.n, s.box, s.pbc, skin=0.0)
+        g.set_state(s.pos, s.vel, s.types, s.masses)
+        ths = g.step(m, 1.0, 5, rebuild_every=1)
+        p1, v1, f1 = g.get_state()
+        p2, v2, f2 = b.get_system(k)
+        d = p2 - p1
+        d -= np.rint(d / s.box) * s.box
+        assert np.abs(d).max() < 1e-10, k
+        assert np.abs(v2 - v1).max() < 1e-10, k
+        assert abs(th[k]["e_pot"] - ths["e_pot"]) <= 1e-9 * abs(ths["e_pot"]), k
+        assert abs(th[k]["e_kin"] - ths["e_kin"]) <= 1e-9 * abs(ths["e_kin"]) + 1e-12, k
