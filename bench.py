@@ -150,6 +150,99 @@ def workload(name, reps=64):
     return w, desc
 
 
+def compute_only_rate(tmd, model, sysm, s, w, steps, torch, stream):
+    """tmd_compute alone (descriptors + network + backward + scatter), table built once."""
+    p, _, _ = sysm.get_state()
+    pos = torch.as_tensor(np.mod(p, s.box), device="cuda")
+    types = torch.as_tensor(s.types, device="cuda")
+    nl = tmd.NeighborList()
+    nl.build(pos, types, s.box, s.pbc, w.model.rc)
+    n = s.n
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    W = torch.zeros(9, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        tmd.compute(model, nl, pos, types, s.box, E, None, F, W)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        tmd.compute(model, nl, pos, types, s.box, E, None, F, W)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_eval": ms,
+            "what": "tmd_compute on a fixed table (no neighbour build, no integration)"}
+
+
+def batch_measure(tmd, torch, steps=5):
+    """512 uneven systems (configs: batch) evaluated by one set of launches, FP32
+    and BF16 network forms; errors against the FP64 oracle on a sample."""
+    from oracle import oracle as O
+    from paper_2310_08439_gb300 import inputs as I
+    w = I.batch()
+    n_tot = int(sum(x.n for x in w.systems))
+    ids = list(range(len(w.systems)))
+    out = {"workload": "512 periodic systems, n ~ logU(32, 8192) (total %d atoms), fcc/bcc/hcp a ~ U(2.9, 4.1), "
+                       "1-3 species, rc 6, K 16, network 192-128-128-1" % n_tot}
+    m = tmd.Model(w.model)
+    b = tmd.Batch(w.systems)
+    rng = np.random.default_rng(0)
+    sample = [k for k in rng.permutation(len(w.systems)) if w.systems[k].n <= 1500][:8]
+    om = O.OracleModel(w.model)
+    ref = {k: O.evaluate(om, w.systems[k].pos, w.systems[k].types, w.systems[k].box, w.systems[k].pbc)
+           for k in sample}
+    for prec in ("fp32", "bf16"):
+        m.set_precision(prec)
+        b.compute(m, ids)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            E, Wv = b.compute(m, ids)
+        dt = (time.perf_counter() - t0) / steps
+        errs = []
+        for k in sample:
+            _, _, f = b.get_system(k)
+            o = ref[k]
+            rms = float(np.sqrt((o["forces"] ** 2).mean()))
+            errs.append({"system": int(k), "n": int(w.systems[k].n),
+                         "dE_rel": abs(E[k] - o["energy"]) / abs(o["energy"]),
+                         "dF_max_over_rms": float(np.abs(f - o["forces"]).max() / rms)})
+        out[prec] = {"atom_evals_per_s": n_tot / dt, "ms_per_batch_eval": dt * 1e3,
+                     "max_dE_rel": max(e["dE_rel"] for e in errs),
+                     "max_dF_over_rms": max(e["dF_max_over_rms"] for e in errs), "per_system": errs}
+    return out
+
+
+def serving_measure(tmd, seconds, torch):
+    """Serving workload: 256 resident systems, Poisson requests (2,000/s, 1-10
+    MD steps each); continuous batching vs each request alone (plain FP32)."""
+    from paper_2310_08439_gb300 import inputs as I
+    from paper_2310_08439_gb300 import serve
+    w = I.serve()
+    free, _ = torch.cuda.mem_get_info()
+    ids, used = serve.admit(w.systems, w.model, int(0.5 * free))
+    systems = [w.systems[k] for k in ids]
+    m = tmd.Model(w.model)
+    res = {"workload": "%d resident systems (%d atoms, 64-50,000 each, fcc/bcc, 1-2 species), Poisson 2,000 "
+                       "requests/s, 1-10 MD steps each, network 128-128-1" % (len(systems), sum(x.n for x in systems)),
+           "admitted": len(ids), "admission_bytes": used}
+    for prec in ("fp32", "bf16"):
+        m.set_precision(prec)
+        b = tmd.Batch(systems)
+        b.step(m, list(range(len(systems))), 1.0, 0)   # initial forces, warm-up
+        reqs = serve.poisson_requests(len(systems), 2000.0, seconds, seed=7)
+        _, st = serve.serve_batched(b, m, reqs)
+        res["batched_" + prec] = st
+    m.set_precision("fp32")
+    b = tmd.Batch(systems)
+    b.step(m, list(range(len(systems))), 1.0, 0)
+    reqs = serve.poisson_requests(len(systems), 2000.0, min(seconds, 0.25), seed=7)
+    _, st = serve.serve_alone(b, m, reqs)
+    res["per_request_fp32"] = st
+    return res
+
+
 def oracle_sample_rate(wname, min_seconds=10.0, max_steps=50):
     """Oracle MD steps (neighbours + energy/forces/virial + velocity-Verlet) on a
     bounded sample of the workload: a 12^3 cell of the same lattice, model and
@@ -228,6 +321,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reps", type=int, default=64, help="fcc repeats of the large cell (64 = 1,048,576 atoms)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -376,6 +471,12 @@ def main():
     kernels = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1), "share": v[1] / total_ms}
                for k, v in ranked}
 
+    compute_only = compute_only_rate(tmd, model, sysm, s, w, args.steps, torch, stream)
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras["batch"] = batch_measure(tmd, torch)
+        extras["serving"] = serving_measure(tmd, args.serve_seconds, torch)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sdesc, sn, ssteps, sdt = oracle_sample_rate(args.config)
@@ -390,8 +491,9 @@ def main():
                        "l2": "inputs larger than L2 (neighbour table ~%.2f GB, %d in-cutoff pairs)"
                              % (nl.size()[1] * 8 / 1e9, pairs),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "forms": forms, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk}
+            "forms": forms, "compute_only": compute_only, "roofline": roof, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

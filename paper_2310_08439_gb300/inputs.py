@@ -268,13 +268,18 @@ def large(feature_scale=True, reps=64):
 
 
 def _best_reps(n_target, n_basis, cell):
-    """(nx, ny, nz) minimising |basis*nx*ny*nz - n| with box aspect ratio <= 2."""
+    """(nx, ny, nz) minimising |basis*nx*ny*nz - n| with box aspect ratio <= 2
+    (ties: the first found scanning nx, ny ascending)."""
     best, best_err = (1, 1, 1), None
     lim = max(1, int(round((n_target / n_basis) ** (1.0 / 3.0) * 2.5)) + 1)
+    cell = np.asarray(cell)
     for nx in range(1, lim + 1):
         for ny in range(1, lim + 1):
-            for nz in range(1, lim + 1):
-                L = np.array([nx, ny, nz]) * np.asarray(cell)
+            z0 = max(1, int(round(n_target / (n_basis * nx * ny))))
+            for nz in (z0 - 1, z0, z0 + 1):
+                if nz < 1:
+                    continue
+                L = np.array([nx, ny, nz]) * cell
                 if L.max() > 2.0 * L.min():
                     continue
                 err = abs(n_basis * nx * ny * nz - n_target)
