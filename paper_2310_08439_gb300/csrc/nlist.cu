@@ -200,6 +200,7 @@ __device__ __forceinline__ int wrap_cell(int u, int nc, int &k) {
 }
 
 struct NbrParams {
+    const int32_t *todo;  // per-atom pass: atoms to list (nullptr = all n)
     const double *pos;
     const int32_t *cell_of;
     const int32_t *cell_start;
@@ -232,11 +233,44 @@ __device__ __noinline__ bool exact_inside(const double *__restrict__ pos, int j,
     return e2 < r2;
 }
 
+// Reserve room for one atom's entries (one atomicAdd) and write its segment.
+__device__ __forceinline__ void emit_entries(const NbrParams &p, int64_t i, const uint64_t *keys, int count, int lane) {
+    if (count > TMD_MAX_DEGREE) {
+        if (lane == 0) {
+            atomicOr(p.status, DEV_ERR_DEGREE);
+            p.beg[i] = 0;
+            p.end[i] = 0;
+        }
+        return;
+    }
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.counter, (unsigned long long)count);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    if ((int64_t)base + count <= p.cap) {
+        for (int c = lane; c < count; c += 32) {
+            const uint64_t key = keys[c];
+            const int t = (int)(key >> 60);
+            const int j = (int)((key >> 15) & 0x1FFFFFFFFFFFull);
+            const int sx = (int)((key >> 10) & 31) - 16, sy = (int)((key >> 5) & 31) - 16, sz = (int)(key & 31) - 16;
+            p.nbr[base + c] = j;
+            p.shift[base + c] = make_char4((signed char)sx, (signed char)sy, (signed char)sz, (signed char)t);
+        }
+    }
+    if (lane == 0) {
+        p.beg[i] = (int64_t)base;
+        p.end[i] = (int64_t)base + count;
+    }
+}
+
+// Per-atom pass (one warp per atom walks its own stencil): used for the atoms
+// of cells whose stencil is too large for the cell-cooperative pass.
 __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
     extern __shared__ uint64_t s_keys[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * NBR_WARPS + warp;
-    if (i >= p.n) return;
+    const int64_t w = (int64_t)blockIdx.x * NBR_WARPS + warp;
+    if (w >= p.n) return;
+    const int64_t i = p.todo ? (int64_t)p.todo[w] : w;
     uint64_t *keys = s_keys + (size_t)warp * TMD_MAX_DEGREE;
     const int cg = p.cell_of[i];
     if (cg < 0) {  // atom of an inactive system
@@ -307,32 +341,150 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
             }
         }
     }
-    if (count > TMD_MAX_DEGREE) {
-        if (lane == 0) {
-            atomicOr(p.status, DEV_ERR_DEGREE);
-            p.beg[i] = 0;
-            p.end[i] = 0;
+    emit_entries(p, i, keys, count, lane);
+}
+
+// Cell-cooperative pass: one block per cell stages the cell's whole stencil
+// (cell-sorted candidates, image-shifted, FP32) in shared memory once; its
+// warps then test each of the cell's atoms against the staged set.  The
+// candidate order (stencil rows, runs, ascending ids) is the per-atom pass's,
+// so both produce identical entries.  Cells whose stencil exceeds the staging
+// capacity hand their atoms to the per-atom pass through `todo`.
+constexpr int CELL_WARPS = 4;
+constexpr int CAND_CAP = 2048;
+constexpr int MAX_SEG = 343;
+
+__global__ void __launch_bounds__(CELL_WARPS * 32)
+    k_nbr_cell(NbrParams p, int64_t ncell, const int32_t *__restrict__ cell_sys,
+               const int32_t *__restrict__ cell_atoms, int32_t *__restrict__ todo,
+               unsigned long long *__restrict__ todo_count) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *cand = reinterpret_cast<float4 *>(smem_raw);                               // [CAND_CAP]
+    uint64_t *keys_all = reinterpret_cast<uint64_t *>(cand + CAND_CAP);               // [CELL_WARPS][MAX_DEGREE]
+    __shared__ int s_seg_start[MAX_SEG], s_seg_pos[MAX_SEG + 1], s_seg_shift[MAX_SEG];
+    __shared__ int s_nseg, s_total;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t *keys = keys_all + (size_t)warp * TMD_MAX_DEGREE;
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int abeg = p.cell_start[c], na = p.cell_start[c + 1] - abeg;
+        if (na == 0) continue;  // uniform across the block
+        const SysParams &sysp = p.sp[cell_sys ? cell_sys[c] : 0];
+        const int nc0 = sysp.nc[0], nc1 = sysp.nc[1], nc2 = sysp.nc[2];
+        if (tid == 0) {
+            const int ci = (int)(c - sysp.cell_off);
+            const int cx = ci % nc0, cy = (ci / nc0) % nc1, cz = ci / (nc0 * nc1);
+            int nseg = 0, total = 0;
+            bool over = false;
+            for (int dz = -sysp.R[2]; dz <= sysp.R[2] && !over; ++dz) {
+                const int uz = cz + dz;
+                if (!sysp.pbc[2] && (uz < 0 || uz >= nc2)) continue;
+                int kz;
+                const int sz = wrap_cell(uz, nc2, kz);
+                for (int dy = -sysp.R[1]; dy <= sysp.R[1] && !over; ++dy) {
+                    const int uy = cy + dy;
+                    if (!sysp.pbc[1] && (uy < 0 || uy >= nc1)) continue;
+                    int ky;
+                    const int sy = wrap_cell(uy, nc1, ky);
+                    const int row = sysp.cell_off + nc0 * (ky + nc1 * kz);
+                    int dx = -sysp.R[0];
+                    while (dx <= sysp.R[0]) {
+                        const int ux = cx + dx;
+                        if (!sysp.pbc[0] && (ux < 0 || ux >= nc0)) { ++dx; continue; }
+                        int kx;
+                        const int sx = wrap_cell(ux, nc0, kx);
+                        int len = 1;
+                        while (dx + len <= sysp.R[0] && kx + len < nc0) ++len;
+                        const int b0 = p.cell_start[row + kx], b1 = p.cell_start[row + kx + len];
+                        if (nseg == MAX_SEG) { over = true; break; }
+                        s_seg_start[nseg] = b0;
+                        s_seg_pos[nseg] = total;
+                        s_seg_shift[nseg] = (sx + 16) | ((sy + 16) << 5) | ((sz + 16) << 10);
+                        total += b1 - b0;
+                        ++nseg;
+                        dx += len;
+                    }
+                }
+            }
+            s_seg_pos[nseg] = total;
+            s_nseg = nseg;
+            s_total = over ? CAND_CAP + 1 : total;
         }
-        return;
-    }
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(p.counter, (unsigned long long)count);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    __syncwarp();
-    if ((int64_t)base + count <= p.cap) {
-        for (int c = lane; c < count; c += 32) {
-            const uint64_t key = keys[c];
-            const int t = (int)(key >> 60);
-            const int j = (int)((key >> 15) & 0x1FFFFFFFFFFFull);
-            const int sx = (int)((key >> 10) & 31) - 16, sy = (int)((key >> 5) & 31) - 16, sz = (int)(key & 31) - 16;
-            p.nbr[base + c] = j;
-            p.shift[base + c] = make_char4((signed char)sx, (signed char)sy, (signed char)sz, (signed char)t);
+        __syncthreads();
+        const int total = s_total, nseg = s_nseg;
+        if (total > CAND_CAP) {
+            for (int q = tid; q < na; q += blockDim.x)
+                todo[atomicAdd(todo_count, 1ull)] = cell_atoms[abeg + q];
+            __syncthreads();
+            continue;
         }
+        // stage the stencil: candidate position + image shift, FP32
+        for (int k = 0; k < nseg; ++k) {
+            const int b0 = s_seg_start[k], pos0 = s_seg_pos[k], cnt = s_seg_pos[k + 1] - pos0;
+            const int code = s_seg_shift[k];
+            const float ox = (float)((code & 31) - 16) * sysp.Lh[0];
+            const float oy = (float)(((code >> 5) & 31) - 16) * sysp.Lh[1];
+            const float oz = (float)(((code >> 10) & 31) - 16) * sysp.Lh[2];
+            for (int q = tid; q < cnt; q += blockDim.x) {
+                const float4 cp = p.cell_pos[b0 + q];
+                cand[pos0 + q] = make_float4(cp.x + ox, cp.y + oy, cp.z + oz, cp.w);
+            }
+        }
+        __syncthreads();
+        for (int ai = warp; ai < na; ai += CELL_WARPS) {
+            const int i = cell_atoms[abeg + ai];
+            const double xi = p.pos[3 * (int64_t)i], yi = p.pos[3 * (int64_t)i + 1], zi = p.pos[3 * (int64_t)i + 2];
+            const float xh = (float)xi, yh = (float)yi, zh = (float)zi;
+            int count = 0;
+            for (int b = 0; b < total; b += 32) {
+                const int q = b + lane;
+                bool in = false, band = false;
+                int j = 0, tj = 0, code = 0;
+                if (q < total) {
+                    const float4 cp = cand[q];
+                    const uint32_t w = (uint32_t)__float_as_int(cp.w);
+                    j = (int)(w & 0x0FFFFFFFu);
+                    tj = (int)(w >> 28);
+                    const float ddx = cp.x - xh, ddy = cp.y - yh, ddz = cp.z - zh;
+                    const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    in = d2 < sysp.r2lo;
+                    band = !in && d2 < sysp.r2hi;
+                }
+                const bool need = in || band;
+                if (need) {  // image shift of this candidate: its segment
+                    int lo = 0, hi = nseg - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_seg_pos[mid] <= q) lo = mid; else hi = mid - 1;
+                    }
+                    code = s_seg_shift[lo];
+                }
+                const int sx = (code & 31) - 16, sy = ((code >> 5) & 31) - 16, sz = ((code >> 10) & 31) - 16;
+                if (__any_sync(0xffffffffu, band)) {
+                    if (band) in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, sysp.L[0], sysp.L[1], sysp.L[2], sysp.r2);
+                }
+                if (in && j == i && sx == 0 && sy == 0 && sz == 0) in = false;
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) {
+                    const int slot = count + __popc(m & lt);
+                    if (slot < TMD_MAX_DEGREE) keys[slot] = make_key(tj, j, sx, sy, sz);
+                }
+                count += __popc(m);
+            }
+            __syncwarp();
+            emit_entries(p, i, keys, count, lane);
+            __syncwarp();
+        }
+        __syncthreads();
     }
-    if (lane == 0) {
-        p.beg[i] = (int64_t)base;
-        p.end[i] = (int64_t)base + count;
-    }
+}
+
+// system of every cell (batched builds)
+__global__ void k_cell_sys(const SysParams *__restrict__ sp, int n_sys, int32_t *__restrict__ cell_sys) {
+    const int k = blockIdx.y;
+    if (k >= n_sys) return;
+    const int c0 = sp[k].cell_off, nc = sp[k].nc[0] * sp[k].nc[1] * sp[k].nc[2];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) cell_sys[c0 + c] = k;
 }
 
 // ---------------------------------------------------------------- scans
@@ -409,7 +561,7 @@ tmd_status scan_inclusive(T *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, c
 }  // namespace
 
 void nlist_free(tmd_nlist *nl) {
-    void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->beg, nl->end, nl->counter, nl->sp, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
+    void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->beg, nl->end, nl->counter, nl->sp, nl->cell_sys, nl->todo, nl->todo_count, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
                     nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->Fq, nl->part, nl->ph, nl->pl,
                     nl->io_pos, nl->io_types, nl->io_forces, nl->io_red};
     for (void *p : ptrs)
@@ -554,7 +706,18 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
         TMD_CUDA(cudaGetLastError());
     }
 
+    const int32_t *cell_sys = nullptr;
+    if (sys_of && n_sys > 1) {
+        if ((st = grow(&nl->cell_sys, &nl->cap_cell_sys, ncell_total)) != TMD_OK) return st;
+        dim3 g((unsigned)std::min<int64_t>(1024, 64), (unsigned)n_sys);
+        TMD_LAUNCH("k_cell_sys", s, k_cell_sys<<<g, 256, 0, s>>>(nl->sp, n_sys, nl->cell_sys));
+        cell_sys = nl->cell_sys;
+    }
+    if ((st = grow(&nl->todo, &nl->cap_todo, n + 1)) != TMD_OK) return st;
+    if ((st = grow(&nl->todo_count, &nl->cap_todo_count, 1)) != TMD_OK) return st;
+
     NbrParams p;
+    p.todo = nullptr;
     p.pos = pos;
     p.cell_of = nl->cell_of;
     p.cell_start = nl->cell_start;
@@ -566,27 +729,47 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     p.end = nl->end;
     p.counter = nl->counter;
     p.status = nl->status;
-    const unsigned nb_nbr = (unsigned)((n + NBR_WARPS - 1) / NBR_WARPS);
-    const size_t smem = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
+    const size_t smem_atom = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
+    const size_t smem_cell = sizeof(float4) * CAND_CAP + sizeof(uint64_t) * TMD_MAX_DEGREE * CELL_WARPS;
     static bool attr_set = false;
     if (!attr_set) {
-        TMD_CUDA(cudaFuncSetAttribute(k_nbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TMD_CUDA(cudaFuncSetAttribute(k_nbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_atom));
+        TMD_CUDA(cudaFuncSetAttribute(k_nbr_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cell));
         attr_set = true;
     }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned nb_cell = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ncell_total, (int64_t)std::max(nsm, 1) * 12));
     int64_t nnz = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         p.nbr = nl->nbr;
         p.shift = nl->shift;
         p.cap = std::min(nl->cap_nnz, nl->cap_shift);
+        p.todo = nullptr;
+        p.n = n;
+        TMD_CUDA(cudaMemsetAsync(nl->todo_count, 0, sizeof(unsigned long long), s));
         if (n > 0) {
-            TMD_LAUNCH("k_nbr", s, k_nbr<<<nb_nbr, NBR_WARPS * 32, smem, s>>>(p));
+            TMD_LAUNCH("k_nbr_cell", s, k_nbr_cell<<<nb_cell, CELL_WARPS * 32, smem_cell, s>>>(
+                                            p, ncell_total, cell_sys, nl->cell_atoms, nl->todo, nl->todo_count));
             TMD_CUDA(cudaGetLastError());
         }
         TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[0], nl->counter, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[1], nl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[2], nl->type_start, sizeof(int32_t) * (TMD_MAX_SPECIES + 1),
                                  cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[6], nl->todo_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         TMD_CUDA(cudaStreamSynchronize(s));
+        const int64_t ntodo = nl->h_pinned[6];
+        if (ntodo > 0) {  // atoms of cells with oversized stencils: per-atom pass
+            p.todo = nl->todo;
+            p.n = ntodo;
+            TMD_LAUNCH("k_nbr", s, k_nbr<<<(unsigned)((ntodo + NBR_WARPS - 1) / NBR_WARPS), NBR_WARPS * 32, smem_atom, s>>>(p));
+            TMD_CUDA(cudaGetLastError());
+            TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[0], nl->counter, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            TMD_CUDA(cudaMemcpyAsync(&nl->h_pinned[1], nl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            TMD_CUDA(cudaStreamSynchronize(s));
+        }
         nnz = nl->h_pinned[0];
         int32_t status = 0;
         std::memcpy(&status, &nl->h_pinned[1], sizeof(int32_t));

@@ -105,6 +105,9 @@ struct tmd_nlist {
     int32_t *type_block = nullptr;   int64_t cap_type_blocks = 0;  // [blocks][MAX_SPECIES]
     int32_t *type_start = nullptr;   int64_t cap_type_start = 0;   // [MAX_SPECIES + 1]
     tmd::SysParams *sp = nullptr;    int64_t cap_sp = 0;           // per-system parameters (device)
+    int32_t *cell_sys = nullptr;     int64_t cap_cell_sys = 0;     // [ncell] system of each cell (batched)
+    int32_t *todo = nullptr;         int64_t cap_todo = 0;         // atoms left to the per-atom pass
+    unsigned long long *todo_count = nullptr; int64_t cap_todo_count = 0;
     int64_t *scan_tmp = nullptr;     int64_t cap_scan = 0;
     int64_t *h_pinned = nullptr;     // host pinned scratch (16 int64)
 
