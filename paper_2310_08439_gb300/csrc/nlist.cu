@@ -352,7 +352,14 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
 // capacity hand their atoms to the per-atom pass through `todo`.
 constexpr int CELL_WARPS = 4;
 constexpr int CAND_CAP = 2048;
-constexpr int MAX_SEG = 343;
+constexpr int MAX_ROWS = 49;   // (2R+1)^2 stencil rows for R <= 3
+constexpr int MAX_RUNS = 7;    // runs of cells per row
+
+// small integer -> float without a conversion instruction (|v| < 2^22):
+// 1.5 * 2^23 + v has v in the low significand bits.
+__device__ __forceinline__ float small_int_to_float(int v) {
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
 
 __global__ void __launch_bounds__(CELL_WARPS * 32)
     k_nbr_cell(NbrParams p, int64_t ncell, const int32_t *__restrict__ cell_sys,
@@ -361,8 +368,10 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *cand = reinterpret_cast<float4 *>(smem_raw);                               // [CAND_CAP]
     uint64_t *keys_all = reinterpret_cast<uint64_t *>(cand + CAND_CAP);               // [CELL_WARPS][MAX_DEGREE]
-    __shared__ int s_seg_start[MAX_SEG], s_seg_pos[MAX_SEG + 1], s_seg_shift[MAX_SEG];
-    __shared__ int s_nseg, s_total;
+    uint16_t *cand_code = reinterpret_cast<uint16_t *>(keys_all + (size_t)CELL_WARPS * TMD_MAX_DEGREE);  // [CAND_CAP]
+    __shared__ int s_nseg[MAX_ROWS], s_ncand[MAX_ROWS], s_cand0[MAX_ROWS];
+    __shared__ int s_start[MAX_ROWS][MAX_RUNS], s_cnt[MAX_ROWS][MAX_RUNS], s_code[MAX_ROWS][MAX_RUNS];
+    __shared__ int s_total;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint64_t *keys = keys_all + (size_t)warp * TMD_MAX_DEGREE;
@@ -371,70 +380,88 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
         if (na == 0) continue;  // uniform across the block
         const SysParams &sysp = p.sp[cell_sys ? cell_sys[c] : 0];
         const int nc0 = sysp.nc[0], nc1 = sysp.nc[1], nc2 = sysp.nc[2];
-        if (tid == 0) {
-            const int ci = (int)(c - sysp.cell_off);
-            const int cx = ci % nc0, cy = (ci / nc0) % nc1, cz = ci / (nc0 * nc1);
-            int nseg = 0, total = 0;
-            bool over = false;
-            for (int dz = -sysp.R[2]; dz <= sysp.R[2] && !over; ++dz) {
-                const int uz = cz + dz;
-                if (!sysp.pbc[2] && (uz < 0 || uz >= nc2)) continue;
-                int kz;
-                const int sz = wrap_cell(uz, nc2, kz);
-                for (int dy = -sysp.R[1]; dy <= sysp.R[1] && !over; ++dy) {
-                    const int uy = cy + dy;
-                    if (!sysp.pbc[1] && (uy < 0 || uy >= nc1)) continue;
-                    int ky;
-                    const int sy = wrap_cell(uy, nc1, ky);
-                    const int row = sysp.cell_off + nc0 * (ky + nc1 * kz);
-                    int dx = -sysp.R[0];
-                    while (dx <= sysp.R[0]) {
-                        const int ux = cx + dx;
-                        if (!sysp.pbc[0] && (ux < 0 || ux >= nc0)) { ++dx; continue; }
-                        int kx;
-                        const int sx = wrap_cell(ux, nc0, kx);
-                        int len = 1;
-                        while (dx + len <= sysp.R[0] && kx + len < nc0) ++len;
-                        const int b0 = p.cell_start[row + kx], b1 = p.cell_start[row + kx + len];
-                        if (nseg == MAX_SEG) { over = true; break; }
-                        s_seg_start[nseg] = b0;
-                        s_seg_pos[nseg] = total;
-                        s_seg_shift[nseg] = (sx + 16) | ((sy + 16) << 5) | ((sz + 16) << 10);
-                        total += b1 - b0;
-                        ++nseg;
-                        dx += len;
-                    }
-                }
-            }
-            s_seg_pos[nseg] = total;
-            s_nseg = nseg;
-            s_total = over ? CAND_CAP + 1 : total;
-        }
-        __syncthreads();
-        const int total = s_total, nseg = s_nseg;
-        if (total > CAND_CAP) {
-            for (int q = tid; q < na; q += blockDim.x)
-                todo[atomicAdd(todo_count, 1ull)] = cell_atoms[abeg + q];
+        const int w1 = 2 * sysp.R[1] + 1, nrows = w1 * (2 * sysp.R[2] + 1);
+        if (nrows > MAX_ROWS || 2 * sysp.R[0] + 1 > MAX_RUNS) {  // wide stencil: per-atom pass
+            for (int q = tid; q < na; q += blockDim.x) todo[atomicAdd(todo_count, 1ull)] = cell_atoms[abeg + q];
             __syncthreads();
             continue;
         }
-        // stage the stencil: candidate position + image shift, FP32
-        for (int k = 0; k < nseg; ++k) {
-            const int b0 = s_seg_start[k], pos0 = s_seg_pos[k], cnt = s_seg_pos[k + 1] - pos0;
-            const int code = s_seg_shift[k];
-            const float ox = (float)((code & 31) - 16) * sysp.Lh[0];
-            const float oy = (float)(((code >> 5) & 31) - 16) * sysp.Lh[1];
-            const float oz = (float)(((code >> 10) & 31) - 16) * sysp.Lh[2];
-            for (int q = tid; q < cnt; q += blockDim.x) {
-                const float4 cp = p.cell_pos[b0 + q];
-                cand[pos0 + q] = make_float4(cp.x + ox, cp.y + oy, cp.z + oz, cp.w);
+        const int ci = (int)(c - sysp.cell_off);
+        const int cx = ci % nc0, cy = (ci / nc0) % nc1, cz = ci / (nc0 * nc1);
+        if (tid < nrows) {  // one thread per stencil row: its runs of cells
+            const int dz = tid / w1 - sysp.R[2], dy = tid % w1 - sysp.R[1];
+            const int uz = cz + dz, uy = cy + dy;
+            int nseg = 0, ncand = 0;
+            if ((sysp.pbc[2] || (uz >= 0 && uz < nc2)) && (sysp.pbc[1] || (uy >= 0 && uy < nc1))) {
+                int kz, ky;
+                const int sz = wrap_cell(uz, nc2, kz);
+                const int sy = wrap_cell(uy, nc1, ky);
+                const int row = sysp.cell_off + nc0 * (ky + nc1 * kz);
+                int dx = -sysp.R[0];
+                while (dx <= sysp.R[0]) {
+                    const int ux = cx + dx;
+                    if (!sysp.pbc[0] && (ux < 0 || ux >= nc0)) { ++dx; continue; }
+                    int kx;
+                    const int sx = wrap_cell(ux, nc0, kx);
+                    int len = 1;
+                    while (dx + len <= sysp.R[0] && kx + len < nc0) ++len;
+                    const int b0 = p.cell_start[row + kx], b1 = p.cell_start[row + kx + len];
+                    s_start[tid][nseg] = b0;
+                    s_cnt[tid][nseg] = b1 - b0;
+                    s_code[tid][nseg] = (sx + 16) | ((sy + 16) << 5) | ((sz + 16) << 10);
+                    ncand += b1 - b0;
+                    ++nseg;
+                    dx += len;
+                }
+            }
+            s_nseg[tid] = nseg;
+            s_ncand[tid] = ncand;
+        }
+        __syncthreads();
+        if (warp == 0) {  // exclusive scan of the rows' candidate counts
+            int run = 0;
+            for (int r0 = 0; r0 < nrows; r0 += 32) {
+                const int r = r0 + lane;
+                const int v = r < nrows ? s_ncand[r] : 0;
+                int x = v;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, d);
+                    if (lane >= d) x += y;
+                }
+                if (r < nrows) s_cand0[r] = run + x - v;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) s_total = run;
+        }
+        __syncthreads();
+        const int total = s_total;
+        if (total > CAND_CAP) {
+            for (int q = tid; q < na; q += blockDim.x) todo[atomicAdd(todo_count, 1ull)] = cell_atoms[abeg + q];
+            __syncthreads();
+            continue;
+        }
+        // stage the stencil in candidate order: image-shifted FP32 positions
+        // (x, y, z, id | species << 28) and the 15-bit shift code
+        for (int r = 0; r < nrows; ++r) {
+            int pos0 = s_cand0[r];
+            for (int k = 0; k < s_nseg[r]; ++k) {
+                const int b0 = s_start[r][k], cnt = s_cnt[r][k], code = s_code[r][k];
+                const float ox = small_int_to_float((code & 31) - 16) * sysp.Lh[0];
+                const float oy = small_int_to_float(((code >> 5) & 31) - 16) * sysp.Lh[1];
+                const float oz = small_int_to_float(((code >> 10) & 31) - 16) * sysp.Lh[2];
+                for (int q = tid; q < cnt; q += blockDim.x) {
+                    const float4 cp = p.cell_pos[b0 + q];
+                    cand[pos0 + q] = make_float4(cp.x + ox, cp.y + oy, cp.z + oz, cp.w);
+                    cand_code[pos0 + q] = (uint16_t)code;
+                }
+                pos0 += cnt;
             }
         }
         __syncthreads();
         for (int ai = warp; ai < na; ai += CELL_WARPS) {
             const int i = cell_atoms[abeg + ai];
-            const double xi = p.pos[3 * (int64_t)i], yi = p.pos[3 * (int64_t)i + 1], zi = p.pos[3 * (int64_t)i + 2];
-            const float xh = (float)xi, yh = (float)yi, zh = (float)zi;
+            const float4 ip = p.cell_pos[abeg + ai];  // the atom's own FP32 position
             int count = 0;
             for (int b = 0; b < total; b += 32) {
                 const int q = b + lane;
@@ -445,25 +472,20 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                     const uint32_t w = (uint32_t)__float_as_int(cp.w);
                     j = (int)(w & 0x0FFFFFFFu);
                     tj = (int)(w >> 28);
-                    const float ddx = cp.x - xh, ddy = cp.y - yh, ddz = cp.z - zh;
+                    code = cand_code[q];
+                    const float ddx = cp.x - ip.x, ddy = cp.y - ip.y, ddz = cp.z - ip.z;
                     const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
                     in = d2 < sysp.r2lo;
                     band = !in && d2 < sysp.r2hi;
                 }
-                const bool need = in || band;
-                if (need) {  // image shift of this candidate: its segment
-                    int lo = 0, hi = nseg - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_seg_pos[mid] <= q) lo = mid; else hi = mid - 1;
-                    }
-                    code = s_seg_shift[lo];
-                }
                 const int sx = (code & 31) - 16, sy = ((code >> 5) & 31) - 16, sz = ((code >> 10) & 31) - 16;
                 if (__any_sync(0xffffffffu, band)) {
-                    if (band) in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, sysp.L[0], sysp.L[1], sysp.L[2], sysp.r2);
+                    if (band) {
+                        const double xi = p.pos[3 * (int64_t)i], yi = p.pos[3 * (int64_t)i + 1], zi = p.pos[3 * (int64_t)i + 2];
+                        in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, sysp.L[0], sysp.L[1], sysp.L[2], sysp.r2);
+                    }
                 }
-                if (in && j == i && sx == 0 && sy == 0 && sz == 0) in = false;
+                if (in && j == i && code == (16 | (16 << 5) | (16 << 10))) in = false;
                 const unsigned m = __ballot_sync(0xffffffffu, in);
                 if (in) {
                     const int slot = count + __popc(m & lt);
@@ -730,7 +752,8 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     p.counter = nl->counter;
     p.status = nl->status;
     const size_t smem_atom = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
-    const size_t smem_cell = sizeof(float4) * CAND_CAP + sizeof(uint64_t) * TMD_MAX_DEGREE * CELL_WARPS;
+    const size_t smem_cell =
+        sizeof(float4) * CAND_CAP + sizeof(uint64_t) * TMD_MAX_DEGREE * CELL_WARPS + sizeof(uint16_t) * CAND_CAP;
     static bool attr_set = false;
     if (!attr_set) {
         TMD_CUDA(cudaFuncSetAttribute(k_nbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_atom));

@@ -88,7 +88,7 @@ __device__ __forceinline__ void diff_df(float xjh, float xjl, float xih, float x
     two_sum(xjh, -xih, u, e1);
     float lo = (xjl - xil) + e1;
     if (s != 0) {
-        const float sf = (float)s;
+        const float sf = __int_as_float(0x4B400000 + s) - 12582912.0f;  // (float)s, |s| <= 15
         const float p = sf * Lh;
         const float pe = fmaf(sf, Lh, -p);  // exact error of the product
         float v, e2;
@@ -677,6 +677,22 @@ __global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32
 // ---------------------------------------------------------------------------
 // backward: P', pair gradients, ScatterSum, virial
 // ---------------------------------------------------------------------------
+// round(g * 2^32) as int64 without a conversion instruction (on this GPU
+// float<->int64 conversions issue on the slow FP64 pipe): two exact 16-bit
+// stages with the 1.5 * 2^23 rounding constant, valid for |g| < 64; larger
+// values (never seen in practice) take the conversion instruction.
+__device__ __forceinline__ long long to_fixed(float g) {
+    if (fabsf(g) >= 64.f) return __float2ll_rn(g * FQ_SCALE);
+    const float M = 12582912.0f;
+    const float v1 = g * 65536.0f;               // exact, |v1| < 2^22
+    const float t1 = v1 + M;
+    const int h = __float_as_int(t1) - 0x4B400000;   // round(v1)
+    const float r = v1 - (t1 - M);               // exact remainder, |r| <= 1/2
+    const float t2 = r * 65536.0f + M;           // |r * 2^16| <= 2^15
+    const int l = __float_as_int(t2) - 0x4B400000;   // round(r * 2^16)
+    return (long long)h * 65536LL + (long long)l;
+}
+
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     const float y = x - comp;
     const float t = sum + y;
@@ -803,9 +819,9 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
                       const float gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
                       // ScatterSum in 2^-32 fixed point: integer adds are exact and
                       // order independent, so forces are bitwise reproducible.
-                      const long long qx = __float2ll_rn(gxs * FQ_SCALE);
-                      const long long qy = __float2ll_rn(gys * FQ_SCALE);
-                      const long long qz = __float2ll_rn(gzs * FQ_SCALE);
+                      const long long qx = to_fixed(gxs);
+                      const long long qy = to_fixed(gys);
+                      const long long qz = to_fixed(gzs);
                       fx += qx; fy += qy; fz += qz;
                       atomicAdd(&Fq[3 * (int64_t)j], (unsigned long long)(-qx));
                       atomicAdd(&Fq[3 * (int64_t)j + 1], (unsigned long long)(-qy));
