@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
 // candidate order (stencil rows, runs, ascending ids) is the per-atom pass's,
 // so both produce identical entries.  Cells whose stencil exceeds the staging
 // capacity hand their atoms to the per-atom pass through `todo`.
-constexpr int CELL_WARPS = 4;
+constexpr int CELL_WARPS = 8;
 constexpr int CAND_CAP = 2048;
 constexpr int MAX_ROWS = 49;   // (2R+1)^2 stencil rows for R <= 3
 constexpr int MAX_RUNS = 7;    // runs of cells per row
@@ -367,14 +367,14 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                unsigned long long *__restrict__ todo_count) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *cand = reinterpret_cast<float4 *>(smem_raw);                               // [CAND_CAP]
-    uint64_t *keys_all = reinterpret_cast<uint64_t *>(cand + CAND_CAP);               // [CELL_WARPS][MAX_DEGREE]
-    uint16_t *cand_code = reinterpret_cast<uint16_t *>(keys_all + (size_t)CELL_WARPS * TMD_MAX_DEGREE);  // [CAND_CAP]
+    uint16_t *cand_code = reinterpret_cast<uint16_t *>(cand + CAND_CAP);              // [CAND_CAP]
+    uint16_t *hits_all = cand_code + CAND_CAP;                                        // [CELL_WARPS][MAX_DEGREE]
     __shared__ int s_nseg[MAX_ROWS], s_ncand[MAX_ROWS], s_cand0[MAX_ROWS];
     __shared__ int s_start[MAX_ROWS][MAX_RUNS], s_cnt[MAX_ROWS][MAX_RUNS], s_code[MAX_ROWS][MAX_RUNS];
     __shared__ int s_total;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    uint64_t *keys = keys_all + (size_t)warp * TMD_MAX_DEGREE;
+    uint16_t *hits = hits_all + (size_t)warp * TMD_MAX_DEGREE;  // accepted candidate indices
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int abeg = p.cell_start[c], na = p.cell_start[c + 1] - abeg;
         if (na == 0) continue;  // uniform across the block
@@ -466,12 +466,11 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
             for (int b = 0; b < total; b += 32) {
                 const int q = b + lane;
                 bool in = false, band = false;
-                int j = 0, tj = 0, code = 0;
+                int j = 0, code = 0;
                 if (q < total) {
                     const float4 cp = cand[q];
                     const uint32_t w = (uint32_t)__float_as_int(cp.w);
                     j = (int)(w & 0x0FFFFFFFu);
-                    tj = (int)(w >> 28);
                     code = cand_code[q];
                     const float ddx = cp.x - ip.x, ddy = cp.y - ip.y, ddz = cp.z - ip.z;
                     const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
@@ -489,12 +488,37 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                 const unsigned m = __ballot_sync(0xffffffffu, in);
                 if (in) {
                     const int slot = count + __popc(m & lt);
-                    if (slot < TMD_MAX_DEGREE) keys[slot] = make_key(tj, j, sx, sy, sz);
+                    if (slot < TMD_MAX_DEGREE) hits[slot] = (uint16_t)q;
                 }
                 count += __popc(m);
             }
             __syncwarp();
-            emit_entries(p, i, keys, count, lane);
+            // reserve this atom's segment and write it from the staged candidates
+            if (count > TMD_MAX_DEGREE) {
+                if (lane == 0) {
+                    atomicOr(p.status, DEV_ERR_DEGREE);
+                    p.beg[i] = 0;
+                    p.end[i] = 0;
+                }
+            } else {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(p.counter, (unsigned long long)count);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if ((int64_t)base + count <= p.cap) {
+                    for (int e = lane; e < count; e += 32) {
+                        const int q = hits[e];
+                        const uint32_t w = (uint32_t)__float_as_int(cand[q].w);
+                        const int code = cand_code[q];
+                        p.nbr[base + e] = (int)(w & 0x0FFFFFFFu);
+                        p.shift[base + e] = make_char4((signed char)((code & 31) - 16), (signed char)(((code >> 5) & 31) - 16),
+                                                       (signed char)(((code >> 10) & 31) - 16), (signed char)(w >> 28));
+                    }
+                }
+                if (lane == 0) {
+                    p.beg[i] = (int64_t)base;
+                    p.end[i] = (int64_t)base + count;
+                }
+            }
             __syncwarp();
         }
         __syncthreads();
@@ -753,7 +777,7 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     p.status = nl->status;
     const size_t smem_atom = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
     const size_t smem_cell =
-        sizeof(float4) * CAND_CAP + sizeof(uint64_t) * TMD_MAX_DEGREE * CELL_WARPS + sizeof(uint16_t) * CAND_CAP;
+        sizeof(float4) * CAND_CAP + sizeof(uint16_t) * CAND_CAP + sizeof(uint16_t) * TMD_MAX_DEGREE * CELL_WARPS;
     static bool attr_set = false;
     if (!attr_set) {
         TMD_CUDA(cudaFuncSetAttribute(k_nbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_atom));

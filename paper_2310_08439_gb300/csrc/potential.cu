@@ -32,8 +32,7 @@ constexpr int PW = 4;           // warps per block in the pair kernels
 constexpr int MT = 32;          // atoms per network tile
 constexpr int MLP_THREADS = 128;
 constexpr float PI_F = 3.14159265358979323846f;
-constexpr float FQ_SCALE = 4294967296.0f;        // forces accumulate in units of 2^-32 eV/A
-constexpr double FQ_INV = 1.0 / 4294967296.0;
+constexpr double FQ_INV = 1.0 / 4294967296.0;   // forces accumulate in units of 2^-32 eV/A
 
 // multiplicities T_d and ranks m(d) in the row order of Eq. T_dm:
 // 1 | x y z | xx xy xz yy yz zz | xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
@@ -678,19 +677,22 @@ __global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32
 // backward: P', pair gradients, ScatterSum, virial
 // ---------------------------------------------------------------------------
 // round(g * 2^32) as int64 without a conversion instruction (on this GPU
-// float<->int64 conversions issue on the slow FP64 pipe): two exact 16-bit
-// stages with the 1.5 * 2^23 rounding constant, valid for |g| < 64; larger
-// values (never seen in practice) take the conversion instruction.
+// float <-> int64 conversions issue on the slow FP64 pipe): three exact
+// 16-bit stages with the 1.5 * 2^23 rounding constant (valid for |g| < 2^21).
+__device__ __forceinline__ int round_magic(float v, float &vr) {
+    const float t = v + 12582912.0f;   // integer part in the low significand bits
+    vr = t - 12582912.0f;              // round(v) as a float
+    return __float_as_int(t) - 0x4B400000;
+}
+
 __device__ __forceinline__ long long to_fixed(float g) {
-    if (fabsf(g) >= 64.f) return __float2ll_rn(g * FQ_SCALE);
-    const float M = 12582912.0f;
-    const float v1 = g * 65536.0f;               // exact, |v1| < 2^22
-    const float t1 = v1 + M;
-    const int h = __float_as_int(t1) - 0x4B400000;   // round(v1)
-    const float r = v1 - (t1 - M);               // exact remainder, |r| <= 1/2
-    const float t2 = r * 65536.0f + M;           // |r * 2^16| <= 2^15
-    const int l = __float_as_int(t2) - 0x4B400000;   // round(r * 2^16)
-    return (long long)h * 65536LL + (long long)l;
+    float f1, f2, f3;
+    const int h1 = round_magic(g, f1);
+    const float v2 = (g - f1) * 65536.0f;      // exact, |v2| <= 2^15
+    const int h2 = round_magic(v2, f2);
+    const float v3 = (v2 - f2) * 65536.0f;     // exact, |v3| <= 2^15
+    const int h3 = round_magic(v3, f3);
+    return (long long)h1 * 4294967296LL + (long long)h2 * 65536LL + (long long)h3;
 }
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
@@ -757,9 +759,9 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
             }
         __syncwarp();
         long long fx = 0, fy = 0, fz = 0;
-        float wa[PAW ? 9 : 1];
+        float wa[9];  // this lane's pairs of this atom
 #pragma unroll
-        for (int t = 0; t < (PAW ? 9 : 1); ++t) wa[t] = 0.f;
+        for (int t = 0; t < 9; ++t) wa[t] = 0.f;
         for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
@@ -831,10 +833,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
 #pragma unroll
                       for (int al = 0; al < 3; ++al)
 #pragma unroll
-                          for (int be = 0; be < 3; ++be) {
-                              if constexpr (PAW) wa[al * 3 + be] -= D[al] * gv[be];
-                              else kahan_add(wsum[al * 3 + be], wcmp[al * 3 + be], -D[al] * gv[be]);
-                          }
+                          for (int be = 0; be < 3; ++be) wa[al * 3 + be] = fmaf(-D[al], gv[be], wa[al * 3 + be]);
                   });
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -855,6 +854,9 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) w_atom[(size_t)a * 9 + t] = v;
             }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) kahan_add(wsum[t], wcmp[t], wa[t]);
         }
         __syncwarp();
     }
