@@ -29,8 +29,8 @@ namespace tmd {
 namespace {
 
 constexpr int PW = 4;           // warps per block in the pair kernels
-constexpr int MT = 32;          // atoms per network tile
-constexpr int MLP_THREADS = 128;
+constexpr int MT = 32;          // smallest network tile (sizes the per-tile energy partials)
+constexpr int MLP_THREADS = 256;
 constexpr float PI_F = 3.14159265358979323846f;
 constexpr double FQ_INV = 1.0 / 4294967296.0;   // forces accumulate in units of 2^-32 eV/A
 
@@ -46,30 +46,77 @@ __device__ __forceinline__ void moments20(float x, float y, float z, float *M) {
     M[15] = x * M[9]; M[16] = M[7] * y; M[17] = M[7] * z; M[18] = y * M[9]; M[19] = M[9] * z;
 }
 
-// f_c and H_k (and dH_k/dr when DERIV) for r < rc.  rad[k] = (mu_hi, mu_lo,
+// 2^x and 1/sqrt(x) from the special-function unit (PTX ex2.approx /
+// rsqrt.approx, relative error about 2^-22; flush-to-zero: a result below
+// 2^-126 becomes 0, and no argument here is subnormal)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// sin(pi t) and cos(pi t) for |t| <= 1/2 from their Taylor series in
+// y = pi t (|y| <= pi/2): the sine through y^13 and the cosine through y^12
+// leave truncation errors of at most 7e-10 and 7e-9.
+__device__ __forceinline__ void sincospi_half(float t, float &sn, float &cs) {
+    const float y = PI_F * t, u = y * y;
+    float p = 1.f / 6227020800.f;
+    p = fmaf(p, u, -1.f / 39916800.f);
+    p = fmaf(p, u, 1.f / 362880.f);
+    p = fmaf(p, u, -1.f / 5040.f);
+    p = fmaf(p, u, 1.f / 120.f);
+    p = fmaf(p, u, -1.f / 6.f);
+    sn = fmaf(y * u, p, y);
+    float q = 1.f / 479001600.f;
+    q = fmaf(q, u, -1.f / 3628800.f);
+    q = fmaf(q, u, 1.f / 40320.f);
+    q = fmaf(q, u, -1.f / 720.f);
+    q = fmaf(q, u, 1.f / 24.f);
+    q = fmaf(q, u, -0.5f);
+    cs = fmaf(u, q, 1.f);
+}
+
+// f_c = (cos(pi r / rc) + 1) / 2 and df_c/dr for r < rc, through t = r / rc - 1/2:
+// cos(pi r / rc) = -sin(pi t), sin(pi r / rc) = cos(pi t).
+__device__ __forceinline__ void cutoff_fn(float r, float inv_rc, float &fc, float &dfc) {
+    float sn, cs;
+    sincospi_half(fmaf(r, inv_rc, -0.5f), sn, cs);
+    fc = 0.5f - 0.5f * sn;
+    dfc = -0.5f * PI_F * inv_rc * cs;
+}
+
+// H_k = f_k f_c (and dH_k/dr when DERIV) for r < rc.  rad[k] = (mu_hi, mu_lo,
 // eta log2 e, 2 eta); r = r_hi + r_lo so that t = r - mu keeps ~FP64 accuracy
 // (the Gaussians are steep: dlnH/dr = -2 eta t amplifies any rounding of r).
 template <int K, bool DERIV>
 __device__ __forceinline__ void radial(const float4 *rad, float r_hi, float r_lo, float inv_rc, float *H, float *dH) {
-    float sn, cs;
-    sincospif(r_hi * inv_rc, &sn, &cs);
-    const float fc = 0.5f * (cs + 1.f);
-    const float dfc = -0.5f * PI_F * inv_rc * sn;
+    float fc, dfc;
+    cutoff_fn(r_hi, inv_rc, fc, dfc);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float4 p = rad[k];
         const float t = (r_hi - p.x) + (r_lo - p.y);
-        const float f = exp2f(-p.z * t * t);
+        const float f = ex2_ftz(-p.z * t * t);
         H[k] = f * fc;
-        if (DERIV) dH[k] = fmaf(-p.w * t * f, fc, f * dfc);
+        if (DERIV) dH[k] = f * fmaf(-p.w * t, fc, dfc);
     }
 }
 
-// r = |D| as an unevaluated sum r_hi + r_lo from r^2 = r2_hi + r2_lo.
+// r = |D| as an unevaluated sum r_hi + r_lo from r^2 = r2_hi + r2_lo, and 1/r.
+// r_hi = r2 y with y ~ 1/sqrt(r2_hi) (pairs never coincide, r2_hi >= ~1); r_lo is the Newton correction (exact
+// residual by FMA), so r_hi + r_lo is accurate to ~1e-13 whatever the error of
+// y; 1/r is y refined by one Newton step against r_hi + r_lo.
 __device__ __forceinline__ void split_sqrt(float r2_hi, float r2_lo, float &r_hi, float &r_lo, float &ir) {
-    r_hi = sqrtf(r2_hi);
-    ir = 1.f / r_hi;
-    r_lo = (fmaf(-r_hi, r_hi, r2_hi) + r2_lo) * 0.5f * ir;
+    const float y = rsqrt_ftz(r2_hi);
+    r_hi = r2_hi * y;
+    r_lo = (fmaf(-r_hi, r_hi, r2_hi) + r2_lo) * 0.5f * y;
+    const float e = fmaf(-r_hi, y, 1.f) - r_lo * y;
+    ir = fmaf(y, e, y);
 }
 
 // Double-float helpers: a value is carried as an unevaluated sum hi + lo of two
@@ -130,46 +177,47 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, int a, int64_t beg
         Lh0 = q.Lh[0]; Lh1 = q.Lh[1]; Lh2 = q.Lh[2];
         Ll0 = q.Ll[0]; Ll1 = q.Ll[1]; Ll2 = q.Ll[2];
     }
-    for (int64_t base = beg; base < end; base += 32) {
-        const int64_t c = base + lane;
-        bool v = false;
-        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 e2 = make_float2(0.f, 0.f);
-        if (c < end) {
-            const int j = nl.nbr[c];
-            const char4 s = nl.shift[c];
-            const float4 jh = nl.ph[j], jl = nl.pl[j];
-            float dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l;
-            diff_df(jh.x, jl.x, ih.x, il.x, s.x, Lh0, Ll0, dxh, dxl);
-            diff_df(jh.y, jl.y, ih.y, il.y, s.y, Lh1, Ll1, dyh, dyl);
-            diff_df(jh.z, jl.z, ih.z, il.z, s.z, Lh2, Ll2, dzh, dzl);
-            norm2_df(dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l);
-            v = (r2h < rc2h) || (r2h == rc2h && r2l < rc2l);
-            e = make_float4(dxh, dyh, dzh, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
-            e2 = make_float2(r2h, r2l);
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, v);
-        if (v) {
-            const int slot = qn + __popc(m & lt);
-            q[slot] = e;
-            q2[slot] = e2;
-        }
-        qn += __popc(m);
-        __syncwarp();
-        if (qn >= 32) {
-            f(q[lane], q2[lane], true, 32);
-            __syncwarp();
-            if (lane < qn - 32) {
-                q[lane] = q[lane + 32];
-                q2[lane] = q2[lane + 32];
+    int64_t base = beg;
+    while (true) {
+        while (qn < 32 && base < end) {
+            const int64_t c = base + lane;
+            bool v = false;
+            float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 e2 = make_float2(0.f, 0.f);
+            if (c < end) {
+                const int j = nl.nbr[c];
+                const char4 s = nl.shift[c];
+                const float4 jh = nl.ph[j], jl = nl.pl[j];
+                float dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l;
+                diff_df(jh.x, jl.x, ih.x, il.x, s.x, Lh0, Ll0, dxh, dxl);
+                diff_df(jh.y, jl.y, ih.y, il.y, s.y, Lh1, Ll1, dyh, dyl);
+                diff_df(jh.z, jl.z, ih.z, il.z, s.z, Lh2, Ll2, dzh, dzl);
+                norm2_df(dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l);
+                v = (r2h < rc2h) || (r2h == rc2h && r2l < rc2l);
+                e = make_float4(dxh, dyh, dzh, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
+                e2 = make_float2(r2h, r2l);
             }
-            __syncwarp();
-            qn -= 32;
+            const unsigned m = __ballot_sync(0xffffffffu, v);
+            if (v) {
+                const int slot = qn + __popc(m & lt);
+                q[slot] = e;
+                q2[slot] = e2;
+            }
+            qn += __popc(m);
+            base += 32;
         }
-    }
-    if (qn > 0) {
-        f(q[lane], q2[lane], lane < qn, qn);
+        if (qn == 0) break;
+        // one call site: full batches while entries remain, then the tail
+        const int nb = min(qn, 32);
         __syncwarp();
+        f(q[lane], q2[lane], lane < nb, nb);
+        __syncwarp();
+        if (lane < qn - nb) {
+            q[lane] = q[lane + 32];
+            q2[lane] = q2[lane + 32];
+        }
+        __syncwarp();
+        qn -= nb;
     }
 }
 
@@ -192,19 +240,21 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                                                   const int32_t *__restrict__ types, float *__restrict__ G,
                                                   float *__restrict__ Pout) {
     constexpr int KPL = K / 8;   // k values per lane
-    constexpr int HS = K + 4;    // row stride of staged H (keeps 16 B alignment, no bank conflicts)
-    constexpr int MS = 36;       // row stride of staged M: 4 groups of 5 padded to 8, plus 4
+    constexpr int RS = 44;       // row stride of the staged pair columns (>= 32 + 3 (S - 1) slots)
     constexpr int Dd = S * K * 4;
     __shared__ float4 s_rad[S * S * K];
     __shared__ float4 s_q[PW][64];
     __shared__ float2 s_q2[PW][64];
-    __shared__ __align__(16) float s_H[PW][32 * HS];
-    __shared__ __align__(16) float s_M[PW][32 * MS];
-    __shared__ int s_b[PW][32];
+    // staged pair data, one column per pair: H_k in row (k % KPL) 8 + k / KPL,
+    // M_d in row (d % 5) 4 + d / 5, so that the lane owning k-group kg and
+    // d-group g reads four pairs of a row with one conflict-free vector load
+    __shared__ __align__(16) float s_H[PW][K * RS];
+    __shared__ __align__(16) float s_M[PW][NMOM * RS];
     for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kg = lane >> 2, g = lane & 3;
+    const unsigned lt = (1u << lane) - 1u;
     float Tg[5];
 #pragma unroll
     for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
@@ -222,53 +272,69 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
         float *sH = s_H[warp];
         float *sM = s_M[warp];
         for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
-                  [&](const float4 e, const float2 e2, bool valid, int nb) {
+                  [&](const float4 e, const float2 e2, bool valid, int) {
+                      const uint32_t jb = __float_as_uint(e.w);
+                      const int b = valid ? (int)(jb >> 28) : S;
+                      // columns grouped by neighbour species, each group starting
+                      // on a multiple of 4
+                      int cnt[S], slot = 0, start = 0;
+#pragma unroll
+                      for (int s = 0; s < S; ++s) {
+                          const unsigned ms = __ballot_sync(0xffffffffu, b == s);
+                          if (b == s) slot = start + __popc(ms & lt);
+                          cnt[s] = __popc(ms);
+                          start += (cnt[s] + 3) & ~3;
+                      }
                       if (valid) {
                           float r_hi, r_lo, ir;
                           split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
-                          const uint32_t jb = __float_as_uint(e.w);
-                          const int b = (int)(jb >> 28);
                           float H[K], M[NMOM];
                           radial<K, false>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, nullptr);
                           moments20(e.x * ir, e.y * ir, e.z * ir, M);
 #pragma unroll
-                          for (int k = 0; k < K; k += 4)
-                              *reinterpret_cast<float4 *>(&sH[lane * HS + k]) = make_float4(H[k], H[k + 1], H[k + 2], H[k + 3]);
+                          for (int k = 0; k < K; ++k) sH[((k % KPL) * 8 + k / KPL) * RS + slot] = H[k];
 #pragma unroll
-                          for (int gg = 0; gg < 4; ++gg) {
-                              *reinterpret_cast<float4 *>(&sM[lane * MS + gg * 8]) =
-                                  make_float4(M[5 * gg], M[5 * gg + 1], M[5 * gg + 2], M[5 * gg + 3]);
-                              sM[lane * MS + gg * 8 + 4] = M[5 * gg + 4];
-                          }
-                          s_b[warp][lane] = b;
+                          for (int d = 0; d < NMOM; ++d) sM[((d % 5) * 4 + d / 5) * RS + slot] = M[d];
                       }
                       __syncwarp();
-                      for (int qi = 0; qi < nb; ++qi) {
-                          const int b = s_b[warp][qi];
-                          float h[KPL];
-                          if constexpr (KPL == 1) {
-                              h[0] = sH[qi * HS + kg];
-                          } else if constexpr (KPL == 2) {
-                              const float2 v = *reinterpret_cast<const float2 *>(&sH[qi * HS + kg * 2]);
-                              h[0] = v.x; h[1] = v.y;
-                          } else {
+                      // P[b][k][d] += H_k M_d: four pairs per step, the rest one at a time
+                      start = 0;
 #pragma unroll
-                              for (int kk = 0; kk < KPL; kk += 4) {
-                                  const float4 v = *reinterpret_cast<const float4 *>(&sH[qi * HS + kg * KPL + kk]);
-                                  h[kk] = v.x; h[kk + 1] = v.y; h[kk + 2] = v.z; h[kk + 3] = v.w;
-                              }
+                      for (int s = 0; s < S; ++s) {
+                          const int stop = start + cnt[s];
+                          int q = start;
+                          for (; q + 4 <= stop; q += 4) {
+                              float4 hv[KPL], mv[5];
+#pragma unroll
+                              for (int kk = 0; kk < KPL; ++kk)
+                                  hv[kk] = *reinterpret_cast<const float4 *>(&sH[(kk * 8 + kg) * RS + q]);
+#pragma unroll
+                              for (int dd = 0; dd < 5; ++dd)
+                                  mv[dd] = *reinterpret_cast<const float4 *>(&sM[(dd * 4 + g) * RS + q]);
+#pragma unroll
+                              for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                                  for (int dd = 0; dd < 5; ++dd) {
+                                      float x = acc[s][kk][dd];
+                                      x = fmaf(hv[kk].x, mv[dd].x, x);
+                                      x = fmaf(hv[kk].y, mv[dd].y, x);
+                                      x = fmaf(hv[kk].z, mv[dd].z, x);
+                                      x = fmaf(hv[kk].w, mv[dd].w, x);
+                                      acc[s][kk][dd] = x;
+                                  }
                           }
-                          const float4 m4 = *reinterpret_cast<const float4 *>(&sM[qi * MS + g * 8]);
-                          const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sM[qi * MS + g * 8 + 4]};
+                          for (; q < stop; ++q) {
+                              float hv[KPL], mv[5];
 #pragma unroll
-                          for (int s = 0; s < S; ++s) {
-                              if (S == 1 || b == s) {
+                              for (int kk = 0; kk < KPL; ++kk) hv[kk] = sH[(kk * 8 + kg) * RS + q];
 #pragma unroll
-                                  for (int kk = 0; kk < KPL; ++kk)
+                              for (int dd = 0; dd < 5; ++dd) mv[dd] = sM[(dd * 4 + g) * RS + q];
 #pragma unroll
-                                      for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = fmaf(h[kk], mv[dd], acc[s][kk][dd]);
-                              }
+                              for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                                  for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = fmaf(hv[kk], mv[dd], acc[s][kk][dd]);
                           }
+                          start += (cnt[s] + 3) & ~3;
                       }
                       __syncwarp();
                   });
@@ -307,11 +373,18 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
     }
 }
 
-// ---------------------------------------------------------------------------
-// network: E_a = NNP(G_a), G' = dE_a/dG_a (FP32 SIMT)
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ float act_f(int act, float z, float b) {
     if (act == TMD_ACT_TANH) return tanhf(z);
+    return 0.5f * (z + sqrtf(fmaf(z, z, b)));
+}
+// BF16 form: tanh from the hardware approximation (relative error about
+// 2^-11, below the 2^-9 rounding of the BF16 activation it feeds)
+__device__ __forceinline__ float act_f_bf16(int act, float z, float b) {
+    if (act == TMD_ACT_TANH) {
+        float r;
+        asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(z));
+        return r;
+    }
     return 0.5f * (z + sqrtf(fmaf(z, z, b)));
 }
 // derivative expressed through the activation output a
@@ -321,168 +394,213 @@ __device__ __forceinline__ float act_da(int act, float a, float b) {
     return a2 / (a2 + b);
 }
 
-// C[r][o] = epi(bias[o] + sum_c A[r][c] B[c][o]) for an MT-row tile.
-// EPI 0: store; 1: activation; 2: multiply by act'(aux[r][o]).
-template <int EPI>
-__device__ __forceinline__ void gemm_tile(const float *A, int lda, int Kin, const float *__restrict__ B, int N,
-                                          const float *__restrict__ bias, float *C, int ldc, int act, float spb,
-                                          const float *aux, int ldaux) {
-    const int ncb = N >> 2;
-    const int items = (MT / 4) * ncb;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int rb = it / ncb, cb = it - rb * ncb;
-        // two partial sums over alternating 4-wide chunks of the reduction
-        // dimension (halves the length of each FP32 accumulation chain)
+// ---------------------------------------------------------------------------
+// network: E_a = NNP(G_a), G' = dE_a/dG_a (FP32 SIMT)
+//
+// A block of MLP_THREADS threads takes a tile of TR atoms in perm order (so a
+// tile holds one species except at species boundaries).  Activations stay in
+// shared memory transposed, [unit][atom] with row stride TR + 4, so a thread
+// reads the 4 atoms of its row block for one unit with one vector load.  The
+// weights of the current layer are staged in shared memory in chunks of MLP_KC
+// input rows by at most MLP_NP output columns; every thread accumulates a
+// 4 x 4 block of outputs per item (one or two items per pass).
+// ---------------------------------------------------------------------------
+constexpr int MLP_KC = 32;     // staged weight rows per chunk
+constexpr int MLP_NP = 128;    // output columns per pass
+
+// EPI 1: C^T[col][row] = act(acc + bias[col])           (hidden layer forward)
+// EPI 2: C^T[col][row] = acc * act'(C^T[col][row])      (hidden layer backward, in place)
+// EPI 3: gout[atom][col] = acc for rows of species s    (input gradient G')
+template <int TR, int EPI>
+__device__ __forceinline__ void mlp_gemm(const float *At, int Kin, const float *__restrict__ W, int N,
+                                         const float *__restrict__ bias, float *Ct, int act, float spb, float *wbuf,
+                                         float *__restrict__ gout, const int *s_atom, const int *s_type, int s) {
+    constexpr int LDT = TR + 4;
+    constexpr int NRB = TR / 4;    // row blocks
+    const int tid = threadIdx.x;
+    for (int n0 = 0; n0 < N; n0 += MLP_NP) {
+        const int np = min(MLP_NP, N - n0);
+        const int ncb = np >> 2;
+        const int items = NRB * ncb;
+        int rb[2], cb[2];
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii) {
+            const int item = tid + ii * MLP_THREADS;
+            rb[ii] = item / ncb;
+            cb[ii] = item - rb[ii] * ncb;
+        }
         float acc[2][4][4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int ii = 0; ii < 2; ++ii)
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int o = 0; o < 4; ++o) acc[h][i][o] = 0.f;
-        const float *a0 = A + (rb * 4) * lda;
-        auto chunk = [&](int c, float (&ac)[4][4]) {
-            float4 av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(a0 + i * lda + c);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) bv[t] = __ldg(reinterpret_cast<const float4 *>(B + (size_t)(c + t) * N + cb * 4));
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float ai[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    ac[i][0] = fmaf(ai[t], bv[t].x, ac[i][0]);
-                    ac[i][1] = fmaf(ai[t], bv[t].y, ac[i][1]);
-                    ac[i][2] = fmaf(ai[t], bv[t].z, ac[i][2]);
-                    ac[i][3] = fmaf(ai[t], bv[t].w, ac[i][3]);
+                for (int o = 0; o < 4; ++o) acc[ii][i][o] = 0.f;
+        for (int k0 = 0; k0 < Kin; k0 += MLP_KC) {
+            const int kc = min(MLP_KC, Kin - k0);
+            __syncthreads();   // earlier readers of wbuf (and writers of At) are done
+            if (np == N) {     // the chunk is one contiguous block of W
+                const float4 *src = reinterpret_cast<const float4 *>(W + (size_t)k0 * N);
+                float4 *dst = reinterpret_cast<float4 *>(wbuf);
+                for (int idx = tid; idx < kc * ncb; idx += MLP_THREADS) dst[idx] = __ldg(src + idx);
+            } else {
+                for (int kr = tid / ncb, c4 = tid - (tid / ncb) * ncb; kr < kc;) {
+                    *reinterpret_cast<float4 *>(wbuf + kr * np + 4 * c4) =
+                        __ldg(reinterpret_cast<const float4 *>(W + (size_t)(k0 + kr) * N + n0 + 4 * c4));
+                    c4 += MLP_THREADS;
+                    while (c4 >= ncb) { c4 -= ncb; ++kr; }
                 }
             }
-        };
-        int c = 0;
-        for (; c + 8 <= Kin; c += 8) {
-            chunk(c, acc[0]);
-            chunk(c + 4, acc[1]);
-        }
-        if (c < Kin) chunk(c, acc[0]);
-        float accs[4][4];
+            __syncthreads();
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int ii = 0; ii < 2; ++ii) {
+                if (tid + ii * MLP_THREADS < items) {
+                    const float *a = At + (size_t)k0 * LDT + rb[ii] * 4;
+                    const float *b = wbuf + cb[ii] * 4;
+#pragma unroll 8
+                    for (int k = 0; k < kc; ++k) {
+                        const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
+                        const float4 bv = *reinterpret_cast<const float4 *>(b + k * np);
+                        const float ai[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
-            for (int o = 0; o < 4; ++o)
-                accs[i][o] = (bias ? __ldg(bias + cb * 4 + o) : 0.f) + (acc[0][i][o] + acc[1][i][o]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float v[4];
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                float x = accs[i][o];
-                if (EPI == 1) x = act_f(act, x, spb);
-                if (EPI == 2) x *= act_da(act, aux[(rb * 4 + i) * ldaux + cb * 4 + o], spb);
-                v[o] = x;
+                        for (int i = 0; i < 4; ++i) {
+                            acc[ii][i][0] = fmaf(ai[i], bv.x, acc[ii][i][0]);
+                            acc[ii][i][1] = fmaf(ai[i], bv.y, acc[ii][i][1]);
+                            acc[ii][i][2] = fmaf(ai[i], bv.z, acc[ii][i][2]);
+                            acc[ii][i][3] = fmaf(ai[i], bv.w, acc[ii][i][3]);
+                        }
+                    }
+                }
             }
-            *reinterpret_cast<float4 *>(C + (rb * 4 + i) * ldc + cb * 4) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii) {
+            if (tid + ii * MLP_THREADS >= items) continue;
+            const int col = n0 + cb[ii] * 4;
+            if (EPI == 3) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int row = rb[ii] * 4 + i;
+                    if (s_type[row] == s)
+                        *reinterpret_cast<float4 *>(gout + (size_t)s_atom[row] * N + col) =
+                            make_float4(acc[ii][i][0], acc[ii][i][1], acc[ii][i][2], acc[ii][i][3]);
+                }
+            } else {
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    float *c = Ct + (size_t)(col + o) * LDT + rb[ii] * 4;
+                    float4 v;
+                    if (EPI == 1) {
+                        const float bo = __ldg(bias + col + o);
+                        v.x = act_f(act, acc[ii][0][o] + bo, spb);
+                        v.y = act_f(act, acc[ii][1][o] + bo, spb);
+                        v.z = act_f(act, acc[ii][2][o] + bo, spb);
+                        v.w = act_f(act, acc[ii][3][o] + bo, spb);
+                    } else {
+                        const float4 a = *reinterpret_cast<const float4 *>(c);
+                        v.x = acc[ii][0][o] * act_da(act, a.x, spb);
+                        v.y = acc[ii][1][o] * act_da(act, a.y, spb);
+                        v.z = acc[ii][2][o] * act_da(act, a.z, spb);
+                        v.w = acc[ii][3][o] * act_da(act, a.w, spb);
+                    }
+                    *reinterpret_cast<float4 *>(c) = v;
+                }
+            }
         }
     }
 }
 
-__global__ void __launch_bounds__(MLP_THREADS) k_mlp(DevModel m, const int32_t *__restrict__ perm,
+template <int TR>
+__global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_t *__restrict__ perm,
                                                      const int32_t *__restrict__ types, int64_t n,
                                                      const float *__restrict__ G, float *__restrict__ dG,
                                                      float *__restrict__ e_atom, double *__restrict__ part_e) {
+    constexpr int LDT = TR + 4;     // row stride of the transposed activations
     extern __shared__ __align__(16) float sm[];
-    __shared__ int s_atom[MT], s_type[MT];
-    __shared__ double s_e[MLP_THREADS / 32];
+    __shared__ int s_atom[TR], s_type[TR];
+    __shared__ float s_e[TR];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t p0 = (int64_t)blockIdx.x * MT;
-    if (tid < MT) {
+    const int64_t p0 = (int64_t)blockIdx.x * TR;
+    if (tid < TR) {
         const int64_t p = p0 + tid;
         const int a = p < n ? perm[p] : -1;
         s_atom[tid] = a;
         s_type[tid] = a >= 0 ? types[a] : -1;
+        s_e[tid] = 0.f;
     }
     const int L = m.L, Dd = m.Dd;
-    int maxw = Dd;
-    for (int l = 1; l <= L; ++l) maxw = max(maxw, m.dims[l]);
-    // shared layout: act[0] (G tile), act[1..L], two ping-pong gradient buffers
+    // shared layout: act[l] = [dims[l]][LDT] for l = 0..L, then the weight chunk
     float *act[MAX_LAYERS + 1];
-    int ld[MAX_LAYERS + 1];
     float *ptr = sm;
     for (int l = 0; l <= L; ++l) {
         act[l] = ptr;
-        ld[l] = m.dims[l] + 4;
-        ptr += MT * ld[l];
+        ptr += (size_t)m.dims[l] * LDT;
     }
-    const int ldz = maxw + 4;
-    float *dzA = ptr;
-    float *dzB = ptr + MT * ldz;
+    float *wbuf = ptr;
     __syncthreads();
-    for (int idx = tid; idx < MT * (Dd / 4); idx += blockDim.x) {
-        const int r = idx / (Dd / 4), c4 = idx - r * (Dd / 4);
+    // G rows -> act[0] transposed (warp per atom row)
+    for (int r = warp; r < TR; r += MLP_THREADS / 32) {
         const int a = s_atom[r];
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (a >= 0) v = *reinterpret_cast<const float4 *>(G + (size_t)a * Dd + c4 * 4);
-        *reinterpret_cast<float4 *>(act[0] + r * ld[0] + c4 * 4) = v;
+        for (int c4 = lane; c4 < (Dd >> 2); c4 += 32) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a >= 0) v = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + 4 * c4));
+            act[0][(4 * c4) * LDT + r] = v.x;
+            act[0][(4 * c4 + 1) * LDT + r] = v.y;
+            act[0][(4 * c4 + 2) * LDT + r] = v.z;
+            act[0][(4 * c4 + 3) * LDT + r] = v.w;
+        }
     }
     __syncthreads();
     int s_lo = TMD_MAX_SPECIES, s_hi = -1;
-    for (int r = 0; r < MT; ++r)
+    for (int r = 0; r < TR; ++r)
         if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
-    double esum = 0.0;
     for (int s = s_lo; s <= s_hi; ++s) {
         const float *wf = m.wf[s], *wb = m.wb[s];
         for (int l = 0; l < L; ++l) {
             const int in = m.dims[l], out = m.dims[l + 1];
-            gemm_tile<1>(act[l], ld[l], in, wf + m.off_f[l], out, wf + m.off_f[l] + in * out, act[l + 1], ld[l + 1],
-                         m.act, m.sp_b, nullptr, 0);
-            __syncthreads();
+            mlp_gemm<TR, 1>(act[l], in, wf + m.off_f[l], out, wf + m.off_f[l] + in * out, act[l + 1], m.act, m.sp_b,
+                            wbuf, nullptr, s_atom, s_type, s);
         }
-        // output layer (linear): E_r = b + w . a_L
+        __syncthreads();
+        // output layer (linear): E_r = b + w . a_L, then dz_L = w * act'(a_L) in place
         const int wl = m.dims[L];
+        float *aL = act[L];
         const float *wout = wb + m.off_b[L];
-        const float bout = __ldg(wf + m.off_f[L] + wl);
-        for (int r = warp; r < MT; r += MLP_THREADS / 32) {
-            float v = 0.f;
-            for (int c = lane; c < wl; c += 32) v = fmaf(act[L][r * ld[L] + c], __ldg(wout + c), v);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && s_type[r] == s) {
-                const float e = v + bout;
-                if (e_atom) e_atom[s_atom[r]] = e;
-                esum += (double)e;
+        if (tid < TR) {
+            float v0 = 0.f, v1 = 0.f;
+            int c = 0;
+            for (; c + 2 <= wl; c += 2) {
+                v0 = fmaf(aL[c * LDT + tid], __ldg(wout + c), v0);
+                v1 = fmaf(aL[(c + 1) * LDT + tid], __ldg(wout + c + 1), v1);
+            }
+            if (c < wl) v0 = fmaf(aL[c * LDT + tid], __ldg(wout + c), v0);
+            if (s_type[tid] == s) {
+                const float e = (v0 + v1) + __ldg(wf + m.off_f[L] + wl);
+                s_e[tid] = e;
+                if (e_atom) e_atom[s_atom[tid]] = e;
             }
         }
-        // backward: dz_L = w_out * act'(a_L)
-        for (int idx = tid; idx < MT * wl; idx += blockDim.x) {
-            const int r = idx / wl, c = idx - r * wl;
-            dzA[r * ldz + c] = __ldg(wout + c) * act_da(m.act, act[L][r * ld[L] + c], m.sp_b);
-        }
         __syncthreads();
-        float *cur = dzA, *nxt = dzB;
-        for (int l = L - 1; l >= 1; --l) {
-            // dz_l = (dz_{l+1} W_l) * act'(a_l)
-            gemm_tile<2>(cur, ldz, m.dims[l + 1], wb + m.off_b[l], m.dims[l], nullptr, nxt, ldz, m.act, m.sp_b,
-                         act[l], ld[l]);
-            __syncthreads();
-            float *t = cur; cur = nxt; nxt = t;
+        for (int c = warp; c < wl; c += MLP_THREADS / 32) {
+            const float w = __ldg(wout + c);
+            for (int r = lane; r < TR; r += 32) aL[c * LDT + r] = w * act_da(m.act, aL[c * LDT + r], m.sp_b);
         }
-        // G' = dz_1 W_0
-        gemm_tile<0>(cur, ldz, m.dims[1], wb + m.off_b[0], Dd, nullptr, nxt, ldz, m.act, m.sp_b, nullptr, 0);
-        __syncthreads();
-        for (int idx = tid; idx < MT * (Dd / 4); idx += blockDim.x) {
-            const int r = idx / (Dd / 4), c4 = idx - r * (Dd / 4);
-            if (s_type[r] == s)
-                *reinterpret_cast<float4 *>(dG + (size_t)s_atom[r] * Dd + c4 * 4) =
-                    *reinterpret_cast<const float4 *>(nxt + r * ldz + c4 * 4);
-        }
-        __syncthreads();
+        // dz_l = (dz_{l+1} W_l^T) * act'(a_l), in place over a_l; B[k = o][n = i] = W_l[i][o]
+        for (int l = L - 1; l >= 1; --l)
+            mlp_gemm<TR, 2>(act[l + 1], m.dims[l + 1], wb + m.off_b[l], m.dims[l], nullptr, act[l], m.act, m.sp_b,
+                            wbuf, nullptr, s_atom, s_type, s);
+        // G' = dz_1 W_0^T
+        mlp_gemm<TR, 3>(act[1], m.dims[1], wb + m.off_b[0], Dd, nullptr, nullptr, m.act, m.sp_b, wbuf, dG, s_atom,
+                        s_type, s);
     }
-    if (lane == 0) s_e[warp] = esum;
     __syncthreads();
-    if (tid == 0) {
+    // tile energy in FP64, fixed order
+    if (tid < 32) {
         double t = 0.0;
-        for (int w = 0; w < MLP_THREADS / 32; ++w) t += s_e[w];
-        part_e[blockIdx.x] = t;
+        for (int r = lane; r < TR; r += 32) t += (double)s_e[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) part_e[blockIdx.x] = t;
     }
 }
 
@@ -509,25 +627,43 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// C[16 rows of this warp][n0 .. n0 + 8 nt) = A[rows][0..K) * B with
-// B[k][n] = Bt[n * ldb + k] (K contiguous per output column), nt <= 8.
-__device__ __forceinline__ void warp_gemm_bf16(const uint16_t *A, int lda, int K, const uint16_t *__restrict__ Bt,
-                                               int ldb, int n0, int nt, int lane, float (&acc)[8][4]) {
-    const int g = lane >> 2, t = lane & 3;
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const uint16_t *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+// Bt[n0 .. n0 + nrows)[0 .. K) -> wsm with row stride K + 8 (all threads of the block)
+__device__ __forceinline__ void stage_bt(const uint16_t *__restrict__ Bt, int n0, int nrows, int K, uint16_t *wsm) {
+    const int c8 = K >> 3;
+    for (int idx = threadIdx.x; idx < nrows * c8; idx += blockDim.x) {
+        const int r = idx / c8, c = idx - r * c8;
+        *reinterpret_cast<uint4 *>(wsm + r * (K + 8) + 8 * c) =
+            __ldg(reinterpret_cast<const uint4 *>(Bt + (size_t)(n0 + r) * K + 8 * c));
+    }
+}
+
+// C[16 rows of this warp][8 nt columns] = A[rows][0..K) * B with B[k][n] =
+// wsm[n * (K + 8) + k] (the staged chunk), nt <= 8 and even.  A and B
+// fragments come from ldmatrix (rows padded by 8 elements: conflict-free).
+__device__ __forceinline__ void warp_gemm_bf16(const uint16_t *A, int lda, int K, const uint16_t *wsm, int nt,
+                                               int lane, float (&acc)[8][4]) {
+    const int ldw = K + 8;
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const uint16_t *pa = A + (lane & 15) * lda + (lane >> 4) * 8;
+    const uint16_t *pb = wsm + ((lane & 7) + ((lane >> 4) << 3)) * ldw + ((lane >> 3) & 1) * 8;
     for (int k0 = 0; k0 < K; k0 += 16) {
-        const uint32_t a0 = *reinterpret_cast<const uint32_t *>(A + g * lda + k0 + 2 * t);
-        const uint32_t a1 = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + k0 + 2 * t);
-        const uint32_t a2 = *reinterpret_cast<const uint32_t *>(A + g * lda + k0 + 8 + 2 * t);
-        const uint32_t a3 = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + k0 + 8 + 2 * t);
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(a0, a1, a2, a3, pa + k0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 8; j += 2) {
             if (j < nt) {
-                const uint16_t *bp = Bt + (size_t)(n0 + 8 * j + g) * ldb + k0 + 2 * t;
-                const uint32_t b0 = __ldg(reinterpret_cast<const unsigned int *>(bp));
-                const uint32_t b1 = __ldg(reinterpret_cast<const unsigned int *>(bp + 8));
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4(b0, b1, b2, b3, pb + j * 8 * ldw + k0);
                 mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
             }
         }
     }
@@ -565,6 +701,7 @@ __global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32
     }
     const int ldz = maxw + 8;
     uint16_t *dzA = ptr, *dzB = ptr + BT * ldz;
+    uint16_t *wsm = dzB + BT * ldz;   // staged weight chunk: 64 rows x (maxw + 8)
     __syncthreads();
     for (int idx = tid; idx < BT * (Dd / 2); idx += blockDim.x) {
         const int r = idx / (Dd / 2), c2 = idx - r * (Dd / 2);
@@ -589,7 +726,10 @@ __global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32
             for (int n0 = 0; n0 < out; n0 += 64) {
                 float acc[8][4];
                 const int nt = min(8, (out - n0) / 8);
-                warp_gemm_bf16(act[l] + r0 * ld[l], ld[l], in, W, in, n0, nt, lane, acc);
+                __syncthreads();   // earlier readers of wsm are done
+                stage_bt(W, n0, 8 * nt, in, wsm);
+                __syncthreads();
+                warp_gemm_bf16(act[l] + r0 * ld[l], ld[l], in, wsm, nt, lane, acc);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (j >= nt) continue;
@@ -599,7 +739,7 @@ __global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32
                     for (int h = 0; h < 2; ++h) {
                         const int row = r0 + g + 8 * h;
                         const float z0 = acc[j][2 * h] + b0, z1 = acc[j][2 * h + 1] + b1;
-                        const float a0v = act_f(m.act, z0, m.sp_b), a1v = act_f(m.act, z1, m.sp_b);
+                        const float a0v = act_f_bf16(m.act, z0, m.sp_b), a1v = act_f_bf16(m.act, z1, m.sp_b);
                         *reinterpret_cast<uint32_t *>(act[l + 1] + row * ld[l + 1] + col) = pack_bf16(a0v, a1v);
                         *reinterpret_cast<uint32_t *>(der[l + 1] + row * ld[l + 1] + col) =
                             pack_bf16(act_da(m.act, a0v, m.sp_b), act_da(m.act, a1v, m.sp_b));
@@ -641,7 +781,10 @@ __global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32
             for (int n0 = 0; n0 < in; n0 += 64) {
                 float acc[8][4];
                 const int nt = min(8, (in - n0) / 8);
-                warp_gemm_bf16(cur + r0 * ldz, ldz, out, Wt, out, n0, nt, lane, acc);
+                __syncthreads();
+                stage_bt(Wt, n0, 8 * nt, out, wsm);
+                __syncthreads();
+                warp_gemm_bf16(cur + r0 * ldz, ldz, out, wsm, nt, lane, acc);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (j >= nt) continue;
@@ -771,41 +914,47 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
                       const uint32_t jb = __float_as_uint(e.w);
                       const int b = (int)(jb >> 28);
                       const int j = (int)(jb & 0x0FFFFFFFu);
-                      float M[NMOM], V[NMOM];
-                      moments20(ux, uy, uz, M);
+                      // V_d = sum_k P'_kd H_k and W_d = sum_k P'_kd H'_k, so that
+                      // F1 = U H' R' = sum_d W_d M_d and F2 = V M'
+                      float V[NMOM], Wd[NMOM];
 #pragma unroll
-                      for (int d = 0; d < NMOM; ++d) V[d] = 0.f;
-                      float dEdr = 0.f;
+                      for (int d = 0; d < NMOM; ++d) V[d] = Wd[d] = 0.f;
                       const float *Pb = sPd + b * PSTR;
                       const float4 *rad = &s_rad[(ti * S + b) * K];
-                      float sn, cs;
-                      sincospif(r_hi * m.inv_rc, &sn, &cs);
-                      const float fc = 0.5f * (cs + 1.f);
-                      const float dfc = -0.5f * PI_F * m.inv_rc * sn;
+                      float fc, dfc;
+                      cutoff_fn(r_hi, m.inv_rc, fc, dfc);
 #pragma unroll
                       for (int k = 0; k < K; ++k) {
                           // H_k and H'_k formed inside the loop (no per-pair arrays)
                           const float4 rp = rad[k];
                           const float t = (r_hi - rp.x) + (r_lo - rp.y);
-                          const float f = exp2f(-rp.z * t * t);
+                          const float f = ex2_ftz(-rp.z * t * t);
                           const float Hk = f * fc;
-                          const float dHk = fmaf(-rp.w * t * f, fc, f * dfc);
-                          // U_k = sum_d P'_kd M_d in four independent chains
-                          float u0 = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
+                          const float dHk = f * fmaf(-rp.w * t, fc, dfc);
 #pragma unroll
                           for (int q4 = 0; q4 < NMOM / 4; ++q4) {
                               const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
-                              u0 = fmaf(pd.x, M[4 * q4], u0);
-                              u1 = fmaf(pd.y, M[4 * q4 + 1], u1);
-                              u2 = fmaf(pd.z, M[4 * q4 + 2], u2);
-                              u3 = fmaf(pd.w, M[4 * q4 + 3], u3);
                               V[4 * q4] = fmaf(pd.x, Hk, V[4 * q4]);
                               V[4 * q4 + 1] = fmaf(pd.y, Hk, V[4 * q4 + 1]);
                               V[4 * q4 + 2] = fmaf(pd.z, Hk, V[4 * q4 + 2]);
                               V[4 * q4 + 3] = fmaf(pd.w, Hk, V[4 * q4 + 3]);
+                              Wd[4 * q4] = fmaf(pd.x, dHk, Wd[4 * q4]);
+                              Wd[4 * q4 + 1] = fmaf(pd.y, dHk, Wd[4 * q4 + 1]);
+                              Wd[4 * q4 + 2] = fmaf(pd.z, dHk, Wd[4 * q4 + 2]);
+                              Wd[4 * q4 + 3] = fmaf(pd.w, dHk, Wd[4 * q4 + 3]);
                           }
-                          dEdr = fmaf((u0 + u1) + (u2 + u3), dHk, dEdr);   // F1 = U H' R'
                       }
+                      float M[NMOM];
+                      moments20(ux, uy, uz, M);
+                      float w0 = Wd[0], w1 = 0.f, w2 = 0.f, w3 = 0.f;
+#pragma unroll
+                      for (int d = 1; d < NMOM; d += 4) {
+                          w1 = fmaf(Wd[d], M[d], w1);
+                          w2 = fmaf(Wd[d + 1], M[d + 1], w2);
+                          w3 = fmaf(Wd[d + 2], M[d + 2], w3);
+                          if (d + 3 < NMOM) w0 = fmaf(Wd[d + 3], M[d + 3], w0);
+                      }
+                      const float dEdr = (w0 + w1) + (w2 + w3);
                       // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
                       const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
                       const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
@@ -860,13 +1009,20 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
         }
         __syncwarp();
     }
-    // virial: per-lane compensated sums -> FP64 block total
+    // virial: per-lane compensated sums (value = sum - comp) -> warp total as
+    // an FP32 double-float (error-free additions) -> FP64 block total
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-        double v = (double)wsum[t] - (double)wcmp[t];
+        float hi = wsum[t], lo = -wcmp[t];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_w[warp][t] = v;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float sh, se;
+            two_sum(hi, oh, sh, se);
+            lo = (lo + ol) + se;
+            two_sum(sh, lo, hi, lo);
+        }
+        if (lane == 0) s_w[warp][t] = (double)hi + (double)lo;
     }
     __syncthreads();
     if (!PAW && threadIdx.x < 9) {
@@ -1010,19 +1166,24 @@ size_t mlp_bf16_smem_bytes(const DevModel &dm) {
         maxw = std::max(maxw, dm.dims[l]);
     }
     el += 2 * (size_t)BT * (maxw + 8);
+    el += (size_t)64 * (maxw + 8);   // staged weight chunk
     return el * sizeof(uint16_t);
 }
 
-size_t mlp_smem_bytes(const DevModel &dm) {
-    int maxw = dm.Dd;
+// dynamic shared memory of k_mlp<TR>: transposed activations of every layer
+// plus one staged weight chunk
+static size_t mlp_smem_tr(const DevModel &dm, int tr) {
     size_t fl = 0;
-    for (int l = 0; l <= dm.L; ++l) {
-        fl += (size_t)MT * (dm.dims[l] + 4);
-        maxw = std::max(maxw, dm.dims[l]);
-    }
-    fl += 2 * (size_t)MT * (maxw + 4);
+    for (int l = 0; l <= dm.L; ++l) fl += (size_t)dm.dims[l] * (tr + 4);
+    fl += (size_t)MLP_KC * MLP_NP;
     return fl * sizeof(float);
 }
+
+// atoms per tile: 64 unless the activations of the wider networks would leave
+// room for fewer than two blocks per SM
+static int mlp_tr(const DevModel &dm) { return mlp_smem_tr(dm, 64) <= 100 * 1024 ? 64 : 32; }
+
+size_t mlp_smem_bytes(const DevModel &dm) { return mlp_smem_tr(dm, mlp_tr(dm)); }
 
 static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, const double box[3]) {
     if (!model || !nl) {
@@ -1053,11 +1214,16 @@ static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, con
 }
 
 static tmd_status set_mlp_smem(const DevModel &dm) {
-    static size_t smem_set = 0, smem_bf_set = 0;
+    static size_t smem_set[2] = {0, 0}, smem_bf_set = 0;
+    const int tr = mlp_tr(dm);
     const size_t smem = mlp_smem_bytes(dm);
-    if (smem > 48 * 1024 && smem > smem_set) {
-        TMD_CUDA(cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
+    size_t &done = smem_set[tr == 64 ? 1 : 0];
+    if (smem > 48 * 1024 && smem > done) {
+        if (tr == 64)
+            TMD_CUDA(cudaFuncSetAttribute(k_mlp<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else
+            TMD_CUDA(cudaFuncSetAttribute(k_mlp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        done = smem;
     }
     const size_t sb = mlp_bf16_smem_bytes(dm);
     if (sb > 48 * 1024 && sb > smem_bf_set) {
@@ -1081,9 +1247,14 @@ static tmd_status launch_network(const DevModel &dm, const int32_t *perm, const 
                                         dm, perm, types, n, G, dG, e_atom, part_e));
         *ntile_out = ntile;
     } else {
-        const int ntile = (int)((n + MT - 1) / MT);
-        TMD_LAUNCH("k_mlp", s, k_mlp<<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, perm, types, n, G, dG,
-                                                                                     e_atom, part_e));
+        const int tr = mlp_tr(dm);
+        const int ntile = (int)((n + tr - 1) / tr);
+        if (tr == 64)
+            TMD_LAUNCH("k_mlp", s, k_mlp<64><<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, perm, types, n, G, dG,
+                                                                                             e_atom, part_e));
+        else
+            TMD_LAUNCH("k_mlp", s, k_mlp<32><<<ntile, MLP_THREADS, mlp_smem_bytes(dm), s>>>(dm, perm, types, n, G, dG,
+                                                                                             e_atom, part_e));
         *ntile_out = ntile;
     }
     TMD_CUDA(cudaGetLastError());
@@ -1166,7 +1337,6 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
 
     TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n, s));
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
-    const size_t smem = mlp_smem_bytes(dm);
     int ne = 0;
     if ((st = launch_network(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e, &ne, s)) != TMD_OK) return st;
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, false)) != TMD_OK) return st;
