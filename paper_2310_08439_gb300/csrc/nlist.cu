@@ -351,9 +351,10 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
 // so both produce identical entries.  Cells whose stencil exceeds the staging
 // capacity hand their atoms to the per-atom pass through `todo`.
 constexpr int CELL_WARPS = 8;
-constexpr int CAND_CAP = 2048;
-constexpr int MAX_ROWS = 49;   // (2R+1)^2 stencil rows for R <= 3
-constexpr int MAX_RUNS = 7;    // runs of cells per row
+constexpr int CAND_CAP = 1920;   // staged candidates per cell (60 groups of 32)
+constexpr int LIST_CAP = 256;    // per-warp list of one atom's hits (longer lists: slower path)
+constexpr int MAX_SEGS = 343;  // stencil cells ((2R+1)^3 for R <= 3)
+
 
 // small integer -> float without a conversion instruction (|v| < 2^22):
 // 1.5 * 2^23 + v has v in the low significand bits.
@@ -367,69 +368,64 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                unsigned long long *__restrict__ todo_count) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *cand = reinterpret_cast<float4 *>(smem_raw);                               // [CAND_CAP]
-    uint16_t *cand_code = reinterpret_cast<uint16_t *>(cand + CAND_CAP);              // [CAND_CAP]
-    uint16_t *hits_all = cand_code + CAND_CAP;                                        // [CELL_WARPS][MAX_DEGREE]
-    __shared__ int s_nseg[MAX_ROWS], s_ncand[MAX_ROWS], s_cand0[MAX_ROWS];
-    __shared__ int s_start[MAX_ROWS][MAX_RUNS], s_cnt[MAX_ROWS][MAX_RUNS], s_code[MAX_ROWS][MAX_RUNS];
+    char4 *cand_sh = reinterpret_cast<char4 *>(cand + CAND_CAP);                       // [CAND_CAP]
+    // hit words of the current 32 atoms, [atom][group] (row padded by one word)
+    uint32_t(*bits)[CAND_CAP / 32 + 1] = reinterpret_cast<uint32_t(*)[CAND_CAP / 32 + 1]>(cand_sh + CAND_CAP);
+    // one segment per stencil cell: first atom in cell order, count, shift
+    // code, and position among the candidates
+    __shared__ int s_seg_b0[MAX_SEGS], s_seg_cnt[MAX_SEGS], s_seg_pos[MAX_SEGS];
+    __shared__ uint16_t s_seg_code[MAX_SEGS];
     __shared__ int s_total;
+    __shared__ uint16_t s_list[CELL_WARPS][LIST_CAP];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    uint16_t *hits = hits_all + (size_t)warp * TMD_MAX_DEGREE;  // accepted candidate indices
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int abeg = p.cell_start[c], na = p.cell_start[c + 1] - abeg;
         if (na == 0) continue;  // uniform across the block
         const SysParams &sysp = p.sp[cell_sys ? cell_sys[c] : 0];
         const int nc0 = sysp.nc[0], nc1 = sysp.nc[1], nc2 = sysp.nc[2];
-        const int w1 = 2 * sysp.R[1] + 1, nrows = w1 * (2 * sysp.R[2] + 1);
-        if (nrows > MAX_ROWS || 2 * sysp.R[0] + 1 > MAX_RUNS) {  // wide stencil: per-atom pass
+        const int w0 = 2 * sysp.R[0] + 1, w1 = 2 * sysp.R[1] + 1;
+        const int nseg = w0 * w1 * (2 * sysp.R[2] + 1);
+        if (nseg > MAX_SEGS) {  // wide stencil: per-atom pass
             for (int q = tid; q < na; q += blockDim.x) todo[atomicAdd(todo_count, 1ull)] = cell_atoms[abeg + q];
             __syncthreads();
             continue;
         }
         const int ci = (int)(c - sysp.cell_off);
         const int cx = ci % nc0, cy = (ci / nc0) % nc1, cz = ci / (nc0 * nc1);
-        if (tid < nrows) {  // one thread per stencil row: its runs of cells
-            const int dz = tid / w1 - sysp.R[2], dy = tid % w1 - sysp.R[1];
-            const int uz = cz + dz, uy = cy + dy;
-            int nseg = 0, ncand = 0;
-            if ((sysp.pbc[2] || (uz >= 0 && uz < nc2)) && (sysp.pbc[1] || (uy >= 0 && uy < nc1))) {
-                int kz, ky;
-                const int sz = wrap_cell(uz, nc2, kz);
+        // stencil cells in (dz, dy, dx) order, all looked up at once
+        for (int t = tid; t < nseg; t += blockDim.x) {
+            const int tx = t % w0, tyz = t / w0;
+            const int ux = cx + tx - sysp.R[0], uy = cy + tyz % w1 - sysp.R[1], uz = cz + tyz / w1 - sysp.R[2];
+            int b0 = 0, cnt = 0, code = 0;
+            if ((sysp.pbc[0] || (ux >= 0 && ux < nc0)) && (sysp.pbc[1] || (uy >= 0 && uy < nc1)) &&
+                (sysp.pbc[2] || (uz >= 0 && uz < nc2))) {
+                int kx, ky, kz;
+                const int sx = wrap_cell(ux, nc0, kx);
                 const int sy = wrap_cell(uy, nc1, ky);
-                const int row = sysp.cell_off + nc0 * (ky + nc1 * kz);
-                int dx = -sysp.R[0];
-                while (dx <= sysp.R[0]) {
-                    const int ux = cx + dx;
-                    if (!sysp.pbc[0] && (ux < 0 || ux >= nc0)) { ++dx; continue; }
-                    int kx;
-                    const int sx = wrap_cell(ux, nc0, kx);
-                    int len = 1;
-                    while (dx + len <= sysp.R[0] && kx + len < nc0) ++len;
-                    const int b0 = p.cell_start[row + kx], b1 = p.cell_start[row + kx + len];
-                    s_start[tid][nseg] = b0;
-                    s_cnt[tid][nseg] = b1 - b0;
-                    s_code[tid][nseg] = (sx + 16) | ((sy + 16) << 5) | ((sz + 16) << 10);
-                    ncand += b1 - b0;
-                    ++nseg;
-                    dx += len;
-                }
+                const int sz = wrap_cell(uz, nc2, kz);
+                const int cell = sysp.cell_off + kx + nc0 * (ky + nc1 * kz);
+                b0 = p.cell_start[cell];
+                cnt = p.cell_start[cell + 1] - b0;
+                code = (sx + 16) | ((sy + 16) << 5) | ((sz + 16) << 10);
             }
-            s_nseg[tid] = nseg;
-            s_ncand[tid] = ncand;
+            s_seg_b0[t] = b0;
+            s_seg_cnt[t] = cnt;
+            s_seg_code[t] = (uint16_t)code;
         }
         __syncthreads();
-        if (warp == 0) {  // exclusive scan of the rows' candidate counts
+        if (warp == 0) {  // exclusive scan of the segments' candidate counts
             int run = 0;
-            for (int r0 = 0; r0 < nrows; r0 += 32) {
+            for (int r0 = 0; r0 < nseg; r0 += 32) {
                 const int r = r0 + lane;
-                const int v = r < nrows ? s_ncand[r] : 0;
+                const int v = r < nseg ? s_seg_cnt[r] : 0;
                 int x = v;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, x, d);
                     if (lane >= d) x += y;
                 }
-                if (r < nrows) s_cand0[r] = run + x - v;
+                if (r < nseg) s_seg_pos[r] = run + x - v;
                 run += __shfl_sync(0xffffffffu, x, 31);
             }
             if (lane == 0) s_total = run;
@@ -441,77 +437,127 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
             __syncthreads();
             continue;
         }
-        // stage the stencil in candidate order: image-shifted FP32 positions
-        // (x, y, z, id | species << 28) and the 15-bit shift code
-        for (int r = 0; r < nrows; ++r) {
-            int pos0 = s_cand0[r];
-            for (int k = 0; k < s_nseg[r]; ++k) {
-                const int b0 = s_start[r][k], cnt = s_cnt[r][k], code = s_code[r][k];
-                const float ox = small_int_to_float((code & 31) - 16) * sysp.Lh[0];
-                const float oy = small_int_to_float(((code >> 5) & 31) - 16) * sysp.Lh[1];
-                const float oz = small_int_to_float(((code >> 10) & 31) - 16) * sysp.Lh[2];
-                for (int q = tid; q < cnt; q += blockDim.x) {
-                    const float4 cp = p.cell_pos[b0 + q];
-                    cand[pos0 + q] = make_float4(cp.x + ox, cp.y + oy, cp.z + oz, cp.w);
-                    cand_code[pos0 + q] = (uint16_t)code;
-                }
-                pos0 += cnt;
+        // stage the stencil in candidate order (a warp per stencil cell):
+        // image-shifted FP32 positions (x, y, z, id | species << 28) and the
+        // table entry's shift (sx, sy, sz, species)
+        for (int t = warp; t < nseg; t += CELL_WARPS) {
+            const int cnt = s_seg_cnt[t];
+            if (cnt == 0) continue;
+            const int b0 = s_seg_b0[t], pos0 = s_seg_pos[t], code = s_seg_code[t];
+            const int sx = (code & 31) - 16, sy = ((code >> 5) & 31) - 16, sz = ((code >> 10) & 31) - 16;
+            const float ox = small_int_to_float(sx) * sysp.Lh[0];
+            const float oy = small_int_to_float(sy) * sysp.Lh[1];
+            const float oz = small_int_to_float(sz) * sysp.Lh[2];
+            for (int q = lane; q < cnt; q += 32) {
+                const float4 cp = p.cell_pos[b0 + q];
+                cand[pos0 + q] = make_float4(cp.x + ox, cp.y + oy, cp.z + oz, cp.w);
+                cand_sh[pos0 + q] = make_char4((signed char)sx, (signed char)sy, (signed char)sz,
+                                               (signed char)((uint32_t)__float_as_int(cp.w) >> 28));
             }
         }
         __syncthreads();
-        for (int ai = warp; ai < na; ai += CELL_WARPS) {
-            const int i = cell_atoms[abeg + ai];
-            const float4 ip = p.cell_pos[abeg + ai];  // the atom's own FP32 position
-            int count = 0;
-            for (int b = 0; b < total; b += 32) {
-                const int q = b + lane;
-                bool in = false, band = false;
-                int j = 0, code = 0;
-                if (q < total) {
-                    const float4 cp = cand[q];
-                    const uint32_t w = (uint32_t)__float_as_int(cp.w);
-                    j = (int)(w & 0x0FFFFFFFu);
-                    code = cand_code[q];
+        // the cell's own atoms: the centre segment (zero shift)
+        const int qself = s_seg_pos[(sysp.R[2] * w1 + sysp.R[1]) * w0 + sysp.R[0]];
+        const int ngroup = (total + 31) >> 5;
+
+        for (int a0 = 0; a0 < na; a0 += 32) {
+            // screen: lane = atom of the cell, candidates broadcast from shared
+            // memory; bit k of a group word marks candidate 32 g + k inside r_list
+            const int ai = a0 + lane;
+            const bool act = ai < na;
+            const float4 ip = act ? p.cell_pos[abeg + ai] : make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f);
+            for (int gi = warp; gi < ngroup; gi += CELL_WARPS) {   // candidate groups interleaved over warps
+                const int qb = gi * 32;
+                // the sign of d2 - r2 is the comparison; each candidate shifts
+                // one bit in from the right, so candidate k ends at bit 31 - k
+                uint32_t in_rev = 0, band_rev = 0;
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) {
+                    const float4 cp = cand[qb + k];
                     const float ddx = cp.x - ip.x, ddy = cp.y - ip.y, ddz = cp.z - ip.z;
                     const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    in = d2 < sysp.r2lo;
-                    band = !in && d2 < sysp.r2hi;
+                    in_rev = __funnelshift_l((uint32_t)__float_as_int(d2 - sysp.r2lo), in_rev, 1);
+                    band_rev = __funnelshift_l((uint32_t)__float_as_int(d2 - sysp.r2hi), band_rev, 1);
                 }
-                const int sx = (code & 31) - 16, sy = ((code >> 5) & 31) - 16, sz = ((code >> 10) & 31) - 16;
-                if (__any_sync(0xffffffffu, band)) {
-                    if (band) {
+                uint32_t in_bits = __brev(in_rev), band_bits = __brev(band_rev);
+                const uint32_t valid = (total - qb >= 32) ? 0xffffffffu : ((1u << (total - qb)) - 1u);
+                in_bits &= valid;
+                band_bits &= valid & ~in_bits;
+                if (__any_sync(0xffffffffu, band_bits != 0)) {
+                    // inside the FP32 rounding band: the exact FP64 decision
+                    if (band_bits) {
+                        const int i = cell_atoms[abeg + ai];
                         const double xi = p.pos[3 * (int64_t)i], yi = p.pos[3 * (int64_t)i + 1], zi = p.pos[3 * (int64_t)i + 2];
-                        in = exact_inside(p.pos, j, sx, sy, sz, xi, yi, zi, sysp.L[0], sysp.L[1], sysp.L[2], sysp.r2);
+                        uint32_t bb = band_bits;
+                        while (bb) {
+                            const int k = __ffs(bb) - 1;
+                            bb &= bb - 1;
+                            const int q = qb + k;
+                            const int j = (int)((uint32_t)__float_as_int(cand[q].w) & 0x0FFFFFFFu);
+                            const char4 sh = cand_sh[q];
+                            if (exact_inside(p.pos, j, sh.x, sh.y, sh.z, xi, yi, zi, sysp.L[0], sysp.L[1], sysp.L[2], sysp.r2))
+                                in_bits |= 1u << k;
+                        }
                     }
                 }
-                if (in && j == i && code == (16 | (16 << 5) | (16 << 10))) in = false;
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                if (in) {
-                    const int slot = count + __popc(m & lt);
-                    if (slot < TMD_MAX_DEGREE) hits[slot] = (uint16_t)q;
-                }
-                count += __popc(m);
+                if (act && ((qself + ai) >> 5) == gi) in_bits &= ~(1u << ((qself + ai) & 31));  // (i, i, 0)
+                if (act) bits[ai - a0][gi] = in_bits;
             }
-            __syncwarp();
-            // reserve this atom's segment and write it from the staged candidates
-            if (count > TMD_MAX_DEGREE) {
-                if (lane == 0) {
-                    atomicOr(p.status, DEV_ERR_DEGREE);
-                    p.beg[i] = 0;
-                    p.end[i] = 0;
+            __syncthreads();
+            // write-out: warp per atom, lane per candidate group (two groups a lane)
+            const int nact = min(32, na - a0);
+            for (int aj = warp; aj < nact; aj += CELL_WARPS) {
+                const int i = cell_atoms[abeg + a0 + aj];
+                const uint32_t wd0 = lane < ngroup ? bits[aj][lane] : 0u;
+                const uint32_t wd1 = lane + 32 < ngroup ? bits[aj][lane + 32] : 0u;
+                const int count = __reduce_add_sync(0xffffffffu, __popc(wd0) + __popc(wd1));
+                if (count > TMD_MAX_DEGREE) {
+                    if (lane == 0) {
+                        atomicOr(p.status, DEV_ERR_DEGREE);
+                        p.beg[i] = 0;
+                        p.end[i] = 0;
+                    }
+                    continue;
                 }
-            } else {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(p.counter, (unsigned long long)count);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if ((int64_t)base + count <= p.cap) {
-                    for (int e = lane; e < count; e += 32) {
-                        const int q = hits[e];
-                        const uint32_t w = (uint32_t)__float_as_int(cand[q].w);
-                        const int code = cand_code[q];
-                        p.nbr[base + e] = (int)(w & 0x0FFFFFFFu);
-                        p.shift[base + e] = make_char4((signed char)((code & 31) - 16), (signed char)(((code >> 5) & 31) - 16),
-                                                       (signed char)(((code >> 10) & 31) - 16), (signed char)(w >> 28));
+                if ((int64_t)base + count <= p.cap && count <= LIST_CAP) {
+                    // expand the words into the warp's list of candidate indices
+                    // (lane per group, groups in order), then write the entries
+                    // with consecutive lanes on consecutive entries
+                    const int c0 = __popc(wd0);
+                    int x0 = c0, x1 = __popc(wd1);
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y0 = __shfl_up_sync(0xffffffffu, x0, d), y1 = __shfl_up_sync(0xffffffffu, x1, d);
+                        if (lane >= d) { x0 += y0; x1 += y1; }
+                    }
+                    uint16_t *list = s_list[warp];
+                    int e = x0 - c0;
+                    for (uint32_t wd = wd0; wd; wd &= wd - 1) list[e++] = (uint16_t)(lane * 32 + __ffs(wd) - 1);
+                    e = __shfl_sync(0xffffffffu, x0, 31) + x1 - __popc(wd1);
+                    for (uint32_t wd = wd1; wd; wd &= wd - 1) list[e++] = (uint16_t)((lane + 32) * 32 + __ffs(wd) - 1);
+                    __syncwarp();
+                    for (int k = lane; k < count; k += 32) {
+                        const int q = list[k];
+                        p.nbr[base + k] = (int)((uint32_t)__float_as_int(cand[q].w) & 0x0FFFFFFFu);
+                        p.shift[base + k] = cand_sh[q];
+                    }
+                    __syncwarp();
+                } else if ((int64_t)base + count <= p.cap) {
+                    // long lists: groups in order, lane k takes bit k
+                    int off = 0;
+                    for (int gi = 0; gi < ngroup; ++gi) {
+                        const uint32_t wd = bits[aj][gi];
+                        if (wd == 0u) continue;
+                        if ((wd >> lane) & 1u) {
+                            const int q = gi * 32 + lane;
+                            const int64_t e = (int64_t)base + off + __popc(wd & lt);
+                            p.nbr[e] = (int)((uint32_t)__float_as_int(cand[q].w) & 0x0FFFFFFFu);
+                            p.shift[e] = cand_sh[q];
+                        }
+                        off += __popc(wd);
                     }
                 }
                 if (lane == 0) {
@@ -519,9 +565,8 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                     p.end[i] = (int64_t)base + count;
                 }
             }
-            __syncwarp();
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -777,7 +822,7 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     p.status = nl->status;
     const size_t smem_atom = sizeof(uint64_t) * TMD_MAX_DEGREE * NBR_WARPS;
     const size_t smem_cell =
-        sizeof(float4) * CAND_CAP + sizeof(uint16_t) * CAND_CAP + sizeof(uint16_t) * TMD_MAX_DEGREE * CELL_WARPS;
+        sizeof(float4) * CAND_CAP + sizeof(char4) * CAND_CAP + sizeof(uint32_t) * 32 * (CAND_CAP / 32 + 1);
     static bool attr_set = false;
     if (!attr_set) {
         TMD_CUDA(cudaFuncSetAttribute(k_nbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_atom));

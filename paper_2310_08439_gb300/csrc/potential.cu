@@ -401,33 +401,101 @@ __device__ __forceinline__ float act_da(int act, float a, float b) {
 // tile holds one species except at species boundaries).  Activations stay in
 // shared memory transposed, [unit][atom] with row stride TR + 4, so a thread
 // reads the 4 atoms of its row block for one unit with one vector load.  The
-// weights of the current layer are staged in shared memory in chunks of MLP_KC
-// input rows by at most MLP_NP output columns; every thread accumulates a
-// 4 x 4 block of outputs per item (one or two items per pass).
+// weights are streamed through two shared-memory buffers in chunks of MLP_KC
+// input rows by at most MLP_NP output columns: while the block multiplies with
+// one chunk, cp.async brings in the next chunk of the tile's fixed sequence of
+// products (forward layers, then the backward chain).  Every thread
+// accumulates a 4 x 4 block of outputs per item (one or two items per pass).
 // ---------------------------------------------------------------------------
-constexpr int MLP_KC = 32;     // staged weight rows per chunk
+constexpr int MLP_KC = 16;     // streamed weight rows per chunk
 constexpr int MLP_NP = 128;    // output columns per pass
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// The products of one species, in order: step l < L is hidden layer l forward
+// (A = a_l, B = W_l [in][out]); step L + t is the backward product for layer
+// L - 1 - t (B = W^T [out][in]); the last one (layer 0) yields G'.
+struct MlpStep {
+    const float *W;
+    int Kin, N;
+};
+__device__ __forceinline__ MlpStep mlp_step(const DevModel &m, int s, int step) {
+    const int L = m.L;
+    if (step < L) return {m.wf[s] + m.off_f[step], m.dims[step], m.dims[step + 1]};
+    const int l = 2 * L - 1 - step;
+    return {m.wb[s] + m.off_b[l], m.dims[l + 1], m.dims[l]};
+}
+
+// Issue the copy of chunk (n0, k0) of product st into buf (all threads).
+__device__ __forceinline__ void mlp_issue(const MlpStep &st, int n0, int k0, float *buf) {
+    const int np = min(MLP_NP, st.N - n0), ncb = np >> 2, kc = min(MLP_KC, st.Kin - k0);
+    if (np == st.N) {   // one contiguous block of W
+        const float *src = st.W + (size_t)k0 * st.N;
+        for (int idx = threadIdx.x; idx < kc * ncb; idx += MLP_THREADS) cp_async16(buf + 4 * idx, src + 4 * idx);
+    } else {
+        for (int idx = threadIdx.x; idx < kc * ncb; idx += MLP_THREADS) {
+            const int kr = idx / ncb, c4 = idx - kr * ncb;
+            cp_async16(buf + kr * np + 4 * c4, st.W + (size_t)(k0 + kr) * st.N + n0 + 4 * c4);
+        }
+    }
+}
+
+// Position in the weight stream: product st (sequence index step of species
+// s), pass n0, chunk k0; buffer parity par.
+struct MlpStream {
+    int s, s_hi, step, n0, k0, par;
+};
+
+// Advance to the chunk after (n0, k0) of the current product (possibly the
+// first chunk of the next product or species) and issue it; always commits a
+// group so that wait_group 1 leaves exactly the current chunk pending.
+__device__ __forceinline__ void mlp_prefetch_next(const DevModel &m, const MlpStream &cur, const MlpStep &st,
+                                                  float *wbuf) {
+    int s = cur.s, step = cur.step, n0 = cur.n0, k0 = cur.k0 + MLP_KC;
+    if (k0 >= st.Kin) {
+        k0 = 0;
+        n0 += MLP_NP;
+        if (n0 >= st.N) {
+            n0 = 0;
+            if (++step == 2 * m.L) { step = 0; ++s; }
+        }
+    }
+    if (s <= cur.s_hi) {
+        const MlpStep nx = (step == cur.step && s == cur.s) ? st : mlp_step(m, s, step);
+        mlp_issue(nx, n0, k0, wbuf + (cur.par ^ 1) * (MLP_KC * MLP_NP));
+    }
+    cp_async_commit();
+}
+
+// One product of the stream.
 // EPI 1: C^T[col][row] = act(acc + bias[col])           (hidden layer forward)
 // EPI 2: C^T[col][row] = acc * act'(C^T[col][row])      (hidden layer backward, in place)
 // EPI 3: gout[atom][col] = acc for rows of species s    (input gradient G')
 template <int TR, int EPI>
-__device__ __forceinline__ void mlp_gemm(const float *At, int Kin, const float *__restrict__ W, int N,
-                                         const float *__restrict__ bias, float *Ct, int act, float spb, float *wbuf,
-                                         float *__restrict__ gout, const int *s_atom, const int *s_type, int s) {
+__device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const float *At,
+                                         const float *__restrict__ bias, float *Ct, float *wbuf,
+                                         float *__restrict__ gout, const int *s_atom, const int *s_type) {
     constexpr int LDT = TR + 4;
     constexpr int NRB = TR / 4;    // row blocks
     const int tid = threadIdx.x;
+    const MlpStep st = mlp_step(m, ws.s, ws.step);
+    const int N = st.N;
     for (int n0 = 0; n0 < N; n0 += MLP_NP) {
         const int np = min(MLP_NP, N - n0);
         const int ncb = np >> 2;
         const int items = NRB * ncb;
+        // row block fastest across the threads: conflict-free transposed loads and stores
         int rb[2], cb[2];
 #pragma unroll
         for (int ii = 0; ii < 2; ++ii) {
             const int item = tid + ii * MLP_THREADS;
-            rb[ii] = item / ncb;
-            cb[ii] = item - rb[ii] * ncb;
+            cb[ii] = item / NRB;
+            rb[ii] = item - cb[ii] * NRB;
         }
         float acc[2][4][4];
 #pragma unroll
@@ -436,27 +504,19 @@ __device__ __forceinline__ void mlp_gemm(const float *At, int Kin, const float *
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int o = 0; o < 4; ++o) acc[ii][i][o] = 0.f;
-        for (int k0 = 0; k0 < Kin; k0 += MLP_KC) {
-            const int kc = min(MLP_KC, Kin - k0);
-            __syncthreads();   // earlier readers of wbuf (and writers of At) are done
-            if (np == N) {     // the chunk is one contiguous block of W
-                const float4 *src = reinterpret_cast<const float4 *>(W + (size_t)k0 * N);
-                float4 *dst = reinterpret_cast<float4 *>(wbuf);
-                for (int idx = tid; idx < kc * ncb; idx += MLP_THREADS) dst[idx] = __ldg(src + idx);
-            } else {
-                for (int kr = tid / ncb, c4 = tid - (tid / ncb) * ncb; kr < kc;) {
-                    *reinterpret_cast<float4 *>(wbuf + kr * np + 4 * c4) =
-                        __ldg(reinterpret_cast<const float4 *>(W + (size_t)(k0 + kr) * N + n0 + 4 * c4));
-                    c4 += MLP_THREADS;
-                    while (c4 >= ncb) { c4 -= ncb; ++kr; }
-                }
-            }
-            __syncthreads();
+        for (int k0 = 0; k0 < st.Kin; k0 += MLP_KC) {
+            const int kc = min(MLP_KC, st.Kin - k0);
+            ws.n0 = n0;
+            ws.k0 = k0;
+            mlp_prefetch_next(m, ws, st, wbuf);
+            cp_async_wait1();
+            __syncthreads();   // this chunk has landed for every thread; At is complete
+            const float *w = wbuf + ws.par * (MLP_KC * MLP_NP);
 #pragma unroll
             for (int ii = 0; ii < 2; ++ii) {
                 if (tid + ii * MLP_THREADS < items) {
                     const float *a = At + (size_t)k0 * LDT + rb[ii] * 4;
-                    const float *b = wbuf + cb[ii] * 4;
+                    const float *b = w + cb[ii] * 4;
 #pragma unroll 8
                     for (int k = 0; k < kc; ++k) {
                         const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
@@ -472,6 +532,8 @@ __device__ __forceinline__ void mlp_gemm(const float *At, int Kin, const float *
                     }
                 }
             }
+            __syncthreads();   // every thread is done with this buffer
+            ws.par ^= 1;
         }
 #pragma unroll
         for (int ii = 0; ii < 2; ++ii) {
@@ -481,7 +543,7 @@ __device__ __forceinline__ void mlp_gemm(const float *At, int Kin, const float *
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int row = rb[ii] * 4 + i;
-                    if (s_type[row] == s)
+                    if (s_type[row] == ws.s)
                         *reinterpret_cast<float4 *>(gout + (size_t)s_atom[row] * N + col) =
                             make_float4(acc[ii][i][0], acc[ii][i][1], acc[ii][i][2], acc[ii][i][3]);
                 }
@@ -492,35 +554,45 @@ __device__ __forceinline__ void mlp_gemm(const float *At, int Kin, const float *
                     float4 v;
                     if (EPI == 1) {
                         const float bo = __ldg(bias + col + o);
-                        v.x = act_f(act, acc[ii][0][o] + bo, spb);
-                        v.y = act_f(act, acc[ii][1][o] + bo, spb);
-                        v.z = act_f(act, acc[ii][2][o] + bo, spb);
-                        v.w = act_f(act, acc[ii][3][o] + bo, spb);
+                        v.x = act_f(m.act, acc[ii][0][o] + bo, m.sp_b);
+                        v.y = act_f(m.act, acc[ii][1][o] + bo, m.sp_b);
+                        v.z = act_f(m.act, acc[ii][2][o] + bo, m.sp_b);
+                        v.w = act_f(m.act, acc[ii][3][o] + bo, m.sp_b);
                     } else {
                         const float4 a = *reinterpret_cast<const float4 *>(c);
-                        v.x = acc[ii][0][o] * act_da(act, a.x, spb);
-                        v.y = acc[ii][1][o] * act_da(act, a.y, spb);
-                        v.z = acc[ii][2][o] * act_da(act, a.z, spb);
-                        v.w = acc[ii][3][o] * act_da(act, a.w, spb);
+                        v.x = acc[ii][0][o] * act_da(m.act, a.x, m.sp_b);
+                        v.y = acc[ii][1][o] * act_da(m.act, a.y, m.sp_b);
+                        v.z = acc[ii][2][o] * act_da(m.act, a.z, m.sp_b);
+                        v.w = acc[ii][3][o] * act_da(m.act, a.w, m.sp_b);
                     }
                     *reinterpret_cast<float4 *>(c) = v;
                 }
             }
         }
     }
+    if (++ws.step == 2 * m.L) { ws.step = 0; ++ws.s; }
 }
 
 template <int TR>
 __global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_t *__restrict__ perm,
-                                                     const int32_t *__restrict__ types, int64_t n,
-                                                     const float *__restrict__ G, float *__restrict__ dG,
-                                                     float *__restrict__ e_atom, double *__restrict__ part_e) {
+                                                        const int32_t *__restrict__ types, int64_t n,
+                                                        const float *__restrict__ G, float *__restrict__ dG,
+                                                        float *__restrict__ e_atom, double *__restrict__ part_e) {
     constexpr int LDT = TR + 4;     // row stride of the transposed activations
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_atom[TR], s_type[TR];
     __shared__ float s_e[TR];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * TR;
+    const int L = m.L, Dd = m.Dd;
+    // shared layout: two weight buffers, then act[l] = [dims[l]][LDT] for l = 0..L
+    float *wbuf = sm;
+    float *act[MAX_LAYERS + 1];
+    float *ptr = sm + 2 * MLP_KC * MLP_NP;
+    for (int l = 0; l <= L; ++l) {
+        act[l] = ptr;
+        ptr += (size_t)m.dims[l] * LDT;
+    }
     if (tid < TR) {
         const int64_t p = p0 + tid;
         const int a = p < n ? perm[p] : -1;
@@ -528,20 +600,17 @@ __global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_
         s_type[tid] = a >= 0 ? types[a] : -1;
         s_e[tid] = 0.f;
     }
-    const int L = m.L, Dd = m.Dd;
-    // shared layout: act[l] = [dims[l]][LDT] for l = 0..L, then the weight chunk
-    float *act[MAX_LAYERS + 1];
-    float *ptr = sm;
-    for (int l = 0; l <= L; ++l) {
-        act[l] = ptr;
-        ptr += (size_t)m.dims[l] * LDT;
-    }
-    float *wbuf = ptr;
     __syncthreads();
-    // G rows -> act[0] transposed (warp per atom row)
-    for (int r = warp; r < TR; r += MLP_THREADS / 32) {
+    int s_lo = TMD_MAX_SPECIES, s_hi = -1;
+    for (int r = 0; r < TR; ++r)
+        if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
+    MlpStream ws{s_lo, s_hi, 0, 0, 0, 0};
+    if (s_lo <= s_hi) mlp_issue(mlp_step(m, s_lo, 0), 0, 0, wbuf);   // first chunk, under the G loads
+    cp_async_commit();
+    // G rows -> act[0] transposed (lane per atom row: conflict-free stores)
+    for (int r = lane; r < TR; r += 32) {
         const int a = s_atom[r];
-        for (int c4 = lane; c4 < (Dd >> 2); c4 += 32) {
+        for (int c4 = warp; c4 < (Dd >> 2); c4 += MLP_THREADS / 32) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (a >= 0) v = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + 4 * c4));
             act[0][(4 * c4) * LDT + r] = v.x;
@@ -550,17 +619,11 @@ __global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_
             act[0][(4 * c4 + 3) * LDT + r] = v.w;
         }
     }
-    __syncthreads();
-    int s_lo = TMD_MAX_SPECIES, s_hi = -1;
-    for (int r = 0; r < TR; ++r)
-        if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
     for (int s = s_lo; s <= s_hi; ++s) {
         const float *wf = m.wf[s], *wb = m.wb[s];
-        for (int l = 0; l < L; ++l) {
-            const int in = m.dims[l], out = m.dims[l + 1];
-            mlp_gemm<TR, 1>(act[l], in, wf + m.off_f[l], out, wf + m.off_f[l] + in * out, act[l + 1], m.act, m.sp_b,
-                            wbuf, nullptr, s_atom, s_type, s);
-        }
+        for (int l = 0; l < L; ++l)
+            mlp_gemm<TR, 1>(m, ws, act[l], wf + m.off_f[l] + m.dims[l] * m.dims[l + 1], act[l + 1], wbuf, nullptr,
+                            s_atom, s_type);
         __syncthreads();
         // output layer (linear): E_r = b + w . a_L, then dz_L = w * act'(a_L) in place
         const int wl = m.dims[L];
@@ -587,12 +650,11 @@ __global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_
         }
         // dz_l = (dz_{l+1} W_l^T) * act'(a_l), in place over a_l; B[k = o][n = i] = W_l[i][o]
         for (int l = L - 1; l >= 1; --l)
-            mlp_gemm<TR, 2>(act[l + 1], m.dims[l + 1], wb + m.off_b[l], m.dims[l], nullptr, act[l], m.act, m.sp_b,
-                            wbuf, nullptr, s_atom, s_type, s);
+            mlp_gemm<TR, 2>(m, ws, act[l + 1], nullptr, act[l], wbuf, nullptr, s_atom, s_type);
         // G' = dz_1 W_0^T
-        mlp_gemm<TR, 3>(act[1], m.dims[1], wb + m.off_b[0], Dd, nullptr, nullptr, m.act, m.sp_b, wbuf, dG, s_atom,
-                        s_type, s);
+        mlp_gemm<TR, 3>(m, ws, act[1], nullptr, nullptr, wbuf, dG, s_atom, s_type);
     }
+    asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
     // tile energy in FP64, fixed order
     if (tid < 32) {
@@ -1175,7 +1237,7 @@ size_t mlp_bf16_smem_bytes(const DevModel &dm) {
 static size_t mlp_smem_tr(const DevModel &dm, int tr) {
     size_t fl = 0;
     for (int l = 0; l <= dm.L; ++l) fl += (size_t)dm.dims[l] * (tr + 4);
-    fl += (size_t)MLP_KC * MLP_NP;
+    fl += (size_t)2 * MLP_KC * MLP_NP;
     return fl * sizeof(float);
 }
 
