@@ -166,9 +166,9 @@ __device__ __forceinline__ void norm2_df(float xh, float xl, float yh, float yl,
 // instructions: on this GPU FP64 runs at a small fraction of the FP32 rate).
 // The queue holds (Dx, Dy, Dz, j | b<<28) rounded to FP32 and r^2 as hi/lo.
 template <typename F>
-__device__ __forceinline__ void for_pairs(const DevNlist &nl, int a, int64_t beg, int64_t end, float rc2h, float rc2l,
-                                          float4 *q, float2 *q2, int lane, F &&f) {
-    int qn = 0;
+__device__ __forceinline__ int for_pairs(const DevNlist &nl, int a, int64_t beg, int64_t end, float rc2h, float rc2l,
+                                         float4 *q, float2 *q2, int lane, F &&f, bool to_cache = false) {
+    int qn = 0, kept = 0;
     const unsigned lt = (1u << lane) - 1u;
     const float4 ih = nl.ph[a], il = nl.pl[a];
     float Lh0 = nl.Lh[0], Lh1 = nl.Lh[1], Lh2 = nl.Lh[2], Ll0 = nl.Ll[0], Ll1 = nl.Ll[1], Ll2 = nl.Ll[2];
@@ -202,8 +202,13 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, int a, int64_t beg
                 const int slot = qn + __popc(m & lt);
                 q[slot] = e;
                 q2[slot] = e2;
+                if (to_cache) {   // compacted in order at [beg, beg + kept)
+                    nl.pq[beg + kept + __popc(m & lt)] = e;
+                    nl.pq2[beg + kept + __popc(m & lt)] = e2;
+                }
             }
             qn += __popc(m);
+            kept += __popc(m);
             base += 32;
         }
         if (qn == 0) break;
@@ -218,6 +223,25 @@ __device__ __forceinline__ void for_pairs(const DevNlist &nl, int a, int64_t beg
         }
         __syncwarp();
         qn -= nb;
+    }
+    return kept;
+}
+
+// The in-cutoff pairs of atom a from the pair cache written by the
+// descriptor pass, in batches of up to 32 (one per lane).
+template <typename F>
+__device__ __forceinline__ void cached_pairs(const DevNlist &nl, int a, int lane, F &&f) {
+    const int64_t pb = nl.beg[a];
+    const int np = nl.npair[a];
+    for (int base = 0; base < np; base += 32) {
+        const int nb = min(32, np - base);
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 e2 = make_float2(1.f, 0.f);
+        if (lane < nb) {
+            e = nl.pq[pb + base + lane];
+            e2 = nl.pq2[pb + base + lane];
+        }
+        f(e, e2, lane < nb, nb);
     }
 }
 
@@ -271,7 +295,8 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                 for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
         float *sH = s_H[warp];
         float *sM = s_M[warp];
-        for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
+        // the in-cutoff pairs also go to the pair cache, when there is one
+        const int written = for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
                   [&](const float4 e, const float2 e2, bool valid, int) {
                       const uint32_t jb = __float_as_uint(e.w);
                       const int b = valid ? (int)(jb >> 28) : S;
@@ -337,7 +362,9 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                           start += (cnt[s] + 3) & ~3;
                       }
                       __syncwarp();
-                  });
+                  },
+                  nl.pq != nullptr);
+        if (nl.npair && lane == 0) nl.npair[a] = written;
         // P[b][k][d] for the backward pass
         float *Pa = Pout + (size_t)a * (S * K * NMOM);
 #pragma unroll
@@ -910,7 +937,7 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 // PAW (batched): each atom's virial is summed over its own pairs and written
 // to w_atom [atoms][9] for per-system reductions; otherwise lanes keep
 // compensated running sums and each block writes one FP64 partial.
-template <int K, int S, bool PAW>
+template <int K, int S, bool PAW, bool CACHED>
 __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                    const int32_t *__restrict__ types, const float *__restrict__ Pin,
                                                    const float *__restrict__ dG,
@@ -967,8 +994,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
         float wa[9];  // this lane's pairs of this atom
 #pragma unroll
         for (int t = 0; t < 9; ++t) wa[t] = 0.f;
-        for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
-                  [&](const float4 e, const float2 e2, bool valid, int) {
+        auto pair_fn = [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
                       float r_hi, r_lo, ir;
                       split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
@@ -1045,7 +1071,11 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
                       for (int al = 0; al < 3; ++al)
 #pragma unroll
                           for (int be = 0; be < 3; ++be) wa[al * 3 + be] = fmaf(-D[al], gv[be], wa[al * 3 + be]);
-                  });
+                  };
+        if constexpr (CACHED)
+            cached_pairs(nl, a, lane, pair_fn);
+        else
+            for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane, pair_fn);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -1179,12 +1209,15 @@ tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const dou
                                float *w_atom) {
     if (forward)
         TMD_LAUNCH("k_desc", s, k_desc<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
-    else if (w_atom)
-        TMD_LAUNCH("k_force", s, k_force<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->Fq,
-                                                                            part_w, w_atom));
+    else if (w_atom)   // batched evaluations always run with the pair cache
+        TMD_LAUNCH("k_force", s, k_force<K, S, true, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
+                                                                                  nl->Fq, part_w, w_atom));
+    else if (dn.pq)
+        TMD_LAUNCH("k_force", s, k_force<K, S, false, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
+                                                                                   nl->Fq, part_w, nullptr));
     else
-        TMD_LAUNCH("k_force", s, k_force<K, S, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG, nl->Fq,
-                                                                             part_w, nullptr));
+        TMD_LAUNCH("k_force", s, k_force<K, S, false, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
+                                                                                    nl->Fq, part_w, nullptr));
     TMD_CUDA(cudaGetLastError());
     return TMD_OK;
 }
@@ -1332,6 +1365,15 @@ static tmd_status split_positions(tmd_nlist *nl, const double *pos, int64_t n, c
     return TMD_OK;
 }
 
+// room for the in-cutoff pair cache: one slot per table entry, a count per atom
+static tmd_status pair_cache(tmd_nlist *nl, int64_t n_atoms, cudaStream_t) {
+    tmd_status st;
+    const int64_t cap = std::max<int64_t>(nl->nnz, 1);
+    if ((st = grow(&nl->pq, &nl->cap_pq, cap)) != TMD_OK) return st;
+    if ((st = grow(&nl->pq2, &nl->cap_pq2, cap)) != TMD_OK) return st;
+    return grow(&nl->npair, &nl->cap_npair, std::max<int64_t>(n_atoms, 1));
+}
+
 static DevNlist dev_nlist(const tmd_nlist *nl, int64_t n, const double box[3]) {
     DevNlist dn;
     dn.beg = nl->beg;
@@ -1395,7 +1437,11 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     double *part_w = nl->part + ntile;
 
     if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
-    const DevNlist dn = dev_nlist(nl, n, box);
+    if ((st = pair_cache(nl, n, s)) != TMD_OK) return st;
+    DevNlist dn = dev_nlist(nl, n, box);
+    dn.pq = nl->pq;
+    dn.pq2 = nl->pq2;
+    dn.npair = nl->npair;
 
     TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n, s));
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
@@ -1636,9 +1682,13 @@ tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double
         const int ntile = (int)((na + MT - 1) / MT);
         if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
         if ((st = split_positions(nl, pos, n_total, s)) != TMD_OK) return st;
+        if ((st = pair_cache(nl, n_total, s)) != TMD_OK) return st;
         DevNlist dn = dev_nlist(nl, na, nl->box);
         dn.sp = nl->sp;
         dn.sys_of = sys_of;
+        dn.pq = nl->pq;
+        dn.pq2 = nl->pq2;
+        dn.npair = nl->npair;
         TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n_total, s));
         if ((st = dispatch_pair(dm, dn, pos, types, nl, nullptr, nblk, s, true)) != TMD_OK) return st;
         int ne = 0;

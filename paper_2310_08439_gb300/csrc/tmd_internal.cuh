@@ -64,6 +64,12 @@ struct DevNlist {
     double box[3] = {0, 0, 0};
     float Lh[3] = {0, 0, 0}, Ll[3] = {0, 0, 0};  // box as hi + lo (single system)
     int64_t n = 0;                  // atoms in perm
+    // in-cutoff pairs of atom a, compacted at [beg[a], beg[a] + npair[a]):
+    // (Dx, Dy, Dz, j | b << 28) and r^2 as hi + lo; written by the descriptor
+    // pass when non-null, read by the force pass
+    float4 *pq = nullptr;
+    float2 *pq2 = nullptr;
+    int32_t *npair = nullptr;
 };
 
 }  // namespace tmd
@@ -119,6 +125,9 @@ struct tmd_nlist {
     float4 *ph = nullptr;     int64_t cap_ph = 0;   // [n] positions hi
     float4 *pl = nullptr;     int64_t cap_pl = 0;   // [n] positions lo
     double *part = nullptr;   int64_t cap_part = 0; // block partial sums
+    float4 *pq = nullptr;     int64_t cap_pq = 0;   // [nnz] in-cutoff pair cache (geometry)
+    float2 *pq2 = nullptr;    int64_t cap_pq2 = 0;  // [nnz] r^2 hi / lo
+    int32_t *npair = nullptr; int64_t cap_npair = 0; // [n] in-cutoff pairs per atom
 
     // staging for the host-buffer entry point
     double *io_pos = nullptr;   int64_t cap_io_pos = 0;
