@@ -121,6 +121,53 @@ tmd_status tmd_model_destroy(tmd_model *model);
 /* Switch the network precision of an existing model (TMD_PREC_*). */
 tmd_status tmd_model_set_precision(tmd_model *model, int32_t precision);
 
+/*
+ * CUDA graphs (the paper has no counterpart: a launch-overhead measure of this
+ * implementation).  The MD step loops (tmd_step, tmd_batch_step) and
+ * tmd_batch_compute run their fixed evaluation sequence through a captured
+ * CUDA graph: the first call with a given table layout, model and step size
+ * runs eagerly, the second captures and instantiates, later calls replay.
+ * Layout changes (a reallocated workspace, another set of active systems)
+ * start over.  Graphs are never used on the legacy default stream (NULL),
+ * while profiling is enabled, or after tmd_set_graphs(0) (process-wide;
+ * default on).  tmd_graph_replays counts the replays so far.
+ */
+tmd_status tmd_set_graphs(int32_t on);
+int64_t tmd_graph_replays(void);
+
+/*
+ * Tile shapes of this implementation's kernels (the paper has no counterpart:
+ * they are launch choices of the GPU path and do not change any result beyond
+ * the order of FP64 partial sums).
+ *  tile_rows           atoms per tile of the FP32 network kernel: 32 or 64
+ *                      (0 = built-in choice by shared-memory footprint);
+ *  pair_blocks_per_sm  blocks per SM of the persistent descriptor / force
+ *                      grids (0 = built-in 16);
+ *  ms                  output of the tuners: measured milliseconds of one
+ *                      evaluation with these shapes (ignored on input).
+ */
+typedef struct {
+    int32_t tile_rows;
+    int32_t pair_blocks_per_sm;
+    float ms;
+} tmd_tuning;
+
+/* Set / read a model's tile shapes.  set rejects tile_rows other than 0, 32,
+ * 64 and pair_blocks_per_sm outside [0, 64] (TMD_ERR_INVALID_ARG). */
+tmd_status tmd_model_set_tuning(tmd_model *model, const tmd_tuning *tuning);
+tmd_status tmd_model_get_tuning(const tmd_model *model, tmd_tuning *tuning);
+
+/*
+ * Autotuner: times tmd_compute on the caller's own system (dev pos [n][3],
+ * dev types [n], built table nl) for every candidate tile shape (tile_rows
+ * 32 / 64 where the shared memory allows it, pair_blocks_per_sm 4, 8, 16,
+ * 32), with CUDA events on the stream, keeps the fastest in the model and
+ * writes it to *best (host).  Results computed while tuning are discarded.
+ * Synchronises the stream.  Errors: as tmd_compute.
+ */
+tmd_status tmd_autotune(tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
+                        const double box[3], tmd_tuning *best, tmd_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Neighbour table (R_abc of Sec. "The Tensor Formalism"; cell binning with */
 /* a skin buffer, Sec. "Evaluation")                                        */
@@ -335,6 +382,16 @@ tmd_status tmd_batch_compute(const tmd_model *model, tmd_batch *batch, const int
  * evaluated for the first time get their initial forces first. */
 tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *batch, const int32_t *systems, int32_t n_active,
                           double dt_fs, int32_t nsteps, tmd_thermo *thermo, tmd_stream_t stream);
+
+/*
+ * Autotuner for batched evaluations: builds the tables of the listed systems
+ * once, then times the batched force evaluation for every candidate tile shape
+ * (as tmd_autotune) and keeps the fastest in the model; *best (host) receives
+ * it.  The systems' positions are wrapped (as tmd_batch_compute does) but not
+ * moved.  Synchronises the stream.
+ */
+tmd_status tmd_batch_autotune(tmd_model *model, tmd_batch *batch, const int32_t *systems, int32_t n_active,
+                              tmd_tuning *best, tmd_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Profiling (per-kernel CUDA-event timing, launch counting)                */

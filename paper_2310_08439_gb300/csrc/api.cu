@@ -28,6 +28,81 @@ tmd_status cuda_fail(cudaError_t e, const char *what) {
     return TMD_ERR_CUDA;
 }
 
+static bool g_graphs = true;   // tmd_set_graphs
+static int64_t g_replays = 0;  // graph launches that replayed a captured sequence
+
+// Run launch() (a fixed sequence of launches on s) through gc: eagerly the
+// first time a key is seen, captured into a graph the second time, replayed
+// after that.  Eager whenever graphs are off, profiling is on (per-launch
+// events) or s is the legacy default stream (which cannot be captured).
+template <typename F>
+tmd_status graphed(GraphCache &gc, const std::vector<uintptr_t> &key, cudaStream_t s, F &&launch) {
+    if (!g_graphs || s == nullptr || profiling_on()) return launch();
+    if (gc.exec && gc.key == key) {
+        TMD_CUDA(cudaGraphLaunch(gc.exec, s));
+        add_launches(gc.kernels);
+        ++g_replays;
+        return TMD_OK;
+    }
+    if (gc.pending != key) {
+        gc.pending = key;
+        return launch();
+    }
+    cudaGraph_t g = nullptr;
+    TMD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const tmd_status st = launch();
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != TMD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    int64_t nk = 0;
+    for (cudaGraphNode_t v : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(v, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    if (gc.exec) {
+        cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        gc.exec = nullptr;
+        return cuda_fail(ei, "cudaGraphInstantiate");
+    }
+    gc.key = key;
+    gc.kernels = nk;
+    TMD_CUDA(cudaGraphLaunch(gc.exec, s));   // the capture itself counted these launches
+    return TMD_OK;
+}
+
+// addresses and sizes a neighbour table's evaluation launches depend on
+void nlist_key(const tmd_nlist &nl, std::vector<uintptr_t> &k) {
+    const void *p[] = {nl.perm, nl.beg, nl.end, nl.nbr, nl.shift, nl.G, nl.dG, nl.P, nl.Fq, nl.part,
+                       nl.ph, nl.pl, nl.pq, nl.pq2, nl.npair, nl.sp};
+    for (const void *q : p) k.push_back((uintptr_t)q);
+    k.push_back((uintptr_t)nl.n_active);
+}
+
+void model_key(const tmd_model *m, std::vector<uintptr_t> &k) {
+    k.push_back((uintptr_t)m);
+    k.push_back((uintptr_t)m->dm.precision);
+    k.push_back((uintptr_t)m->dm.tile_rows);
+    k.push_back((uintptr_t)m->dm.pair_bps);
+}
+
+uintptr_t bits_of(double x) {
+    uintptr_t u = 0;
+    std::memcpy(&u, &x, sizeof(double) < sizeof(uintptr_t) ? sizeof(double) : sizeof(uintptr_t));
+    return u;
+}
+
 namespace {
 
 // eV/(A amu) -> A/fs^2
@@ -355,6 +430,94 @@ tmd_status tmd_model_set_precision(tmd_model *m, int32_t precision) {
     return TMD_OK;
 }
 
+tmd_status tmd_set_graphs(int32_t on) {
+    g_graphs = on != 0;
+    return TMD_OK;
+}
+
+int64_t tmd_graph_replays(void) { return g_replays; }
+
+tmd_status tmd_model_set_tuning(tmd_model *m, const tmd_tuning *t) {
+    g_err[0] = 0;
+    if (!m || !t || (t->tile_rows != 0 && t->tile_rows != 32 && t->tile_rows != 64) || t->pair_blocks_per_sm < 0 ||
+        t->pair_blocks_per_sm > 64) {
+        set_error("bad model or tuning (tile_rows 0/32/64, pair_blocks_per_sm 0..64)");
+        return TMD_ERR_INVALID_ARG;
+    }
+    m->dm.tile_rows = t->tile_rows;
+    m->dm.pair_bps = t->pair_blocks_per_sm;
+    return TMD_OK;
+}
+
+tmd_status tmd_model_get_tuning(const tmd_model *m, tmd_tuning *t) {
+    if (!m || !t) { set_error("null model or output"); return TMD_ERR_INVALID_ARG; }
+    t->tile_rows = m->dm.tile_rows;
+    t->pair_blocks_per_sm = m->dm.pair_bps;
+    t->ms = 0.f;
+    return TMD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Time run() (one evaluation enqueued on s) for every candidate tile shape and
+// keep the fastest in the model: one untimed run per candidate (it also sizes
+// the workspaces), then three timed back to back.
+template <typename F>
+tmd_status tune_shapes(tmd_model *m, cudaStream_t s, tmd_tuning *best, F &&run) {
+    const int rows_fp32[2] = {32, 64};
+    const int bps[4] = {4, 8, 16, 32};
+    const int nrows = (m->dm.precision == TMD_PREC_FP32) ? 2 : 1;
+    cudaEvent_t e0, e1;
+    TMD_CUDA(cudaEventCreate(&e0));
+    TMD_CUDA(cudaEventCreate(&e1));
+    tmd_tuning top = {0, 0, 1e30f};
+    const tmd::DevModel keep = m->dm;
+    tmd_status st = TMD_OK;
+    for (int r = 0; r < nrows && st == TMD_OK; ++r) {
+        m->dm.tile_rows = (m->dm.precision == TMD_PREC_FP32) ? rows_fp32[r] : 0;
+        if (m->dm.tile_rows && tmd::mlp_smem_tr_public(m->dm, m->dm.tile_rows) > 227 * 1024) continue;
+        for (int b = 0; b < 4 && st == TMD_OK; ++b) {
+            m->dm.pair_bps = bps[b];
+            if ((st = run()) != TMD_OK) break;
+            if (cudaEventRecord(e0, s) != cudaSuccess) { st = TMD_ERR_CUDA; break; }
+            for (int k = 0; k < 3 && st == TMD_OK; ++k) st = run();
+            if (st != TMD_OK) break;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { st = TMD_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            if (ms < top.ms) top = {m->dm.tile_rows, m->dm.pair_bps, ms};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->dm = keep;
+    if (st != TMD_OK) return st;
+    m->dm.tile_rows = top.tile_rows;
+    m->dm.pair_bps = top.pair_blocks_per_sm;
+    if (best) *best = top;
+    return TMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tmd_status tmd_autotune(tmd_model *m, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
+                        const double box[3], tmd_tuning *best, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!m || !nl || !nl->built || n < 1) { set_error("null model, unbuilt table or no atoms"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    tmd_status st;
+    if ((st = grow(&nl->io_forces, &nl->cap_io_forces, 3 * n)) != TMD_OK) return st;
+    if ((st = grow(&nl->io_red, &nl->cap_io_red, 16)) != TMD_OK) return st;
+    return tune_shapes(m, s, best, [&]() {
+        return run_compute(m, nl, pos, types, n, box, nl->io_red, nullptr, nl->io_forces, nl->io_red + 1, s);
+    });
+}
+
 // --------------------------------------------------------------------- nlist
 tmd_status tmd_nlist_create(tmd_nlist **out) {
     if (!out) { set_error("null output"); return TMD_ERR_INVALID_ARG; }
@@ -571,9 +734,9 @@ tmd_status tmd_system_get_state(const tmd_system *sys, double *pos, double *vel,
     return TMD_OK;
 }
 
-static tmd_status rebuild_and_compute(const tmd_model *model, tmd_system *sys, bool rebuild, cudaStream_t s) {
+static tmd_status rebuild_only(const tmd_model *model, tmd_system *sys, cudaStream_t s) {
     tmd_status st;
-    if (rebuild) {
+    {
         const double r_list = (double)model->dm.rc + sys->skin;
         const int64_t n = sys->n;
         TMD_LAUNCH("k_wrap", s, k_wrap<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys->pos, n, sys->box[0], sys->box[1],
@@ -585,6 +748,12 @@ static tmd_status rebuild_and_compute(const tmd_model *model, tmd_system *sys, b
         sys->rebuilds++;
         sys->need_rebuild = 0;
     }
+    return TMD_OK;
+}
+
+static tmd_status rebuild_and_compute(const tmd_model *model, tmd_system *sys, bool rebuild, cudaStream_t s) {
+    tmd_status st;
+    if (rebuild && (st = rebuild_only(model, sys, s)) != TMD_OK) return st;
     return run_compute(model, &sys->nl, sys->pos, sys->types, sys->n, sys->box, sys->red, nullptr, sys->forces,
                        sys->red + 1, s);
 }
@@ -618,9 +787,26 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
             std::memcpy(&f, sys->h_red + 20, sizeof(int32_t));
             rebuild = f != 0;
         }
-        if ((st = rebuild_and_compute(model, sys, rebuild, s)) != TMD_OK) return st;
-        TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
-        TMD_CUDA(cudaGetLastError());
+        if (rebuild && (st = rebuild_only(model, sys, s)) != TMD_OK) return st;
+        // force evaluation and second half kick: one captured graph per table layout
+        if ((st = reserve_compute(model->dm, &sys->nl, n, n)) != TMD_OK) return st;
+        std::vector<uintptr_t> key;
+        model_key(model, key);
+        nlist_key(sys->nl, key);
+        const void *sp[] = {sys->pos, sys->vel, sys->types, sys->forces, sys->red, sys->inv_mass};
+        for (const void *q : sp) key.push_back((uintptr_t)q);
+        key.push_back((uintptr_t)n);
+        key.push_back(bits_of(dt_fs));
+        for (int x = 0; x < 3; ++x) key.push_back(bits_of(sys->box[x]));
+        st = graphed(sys->g_step, key, s, [&]() {
+            tmd_status st2 = run_compute(model, &sys->nl, sys->pos, sys->types, sys->n, sys->box, sys->red, nullptr,
+                                         sys->forces, sys->red + 1, s);
+            if (st2 != TMD_OK) return st2;
+            TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
+            TMD_CUDA(cudaGetLastError());
+            return TMD_OK;
+        });
+        if (st != TMD_OK) return st;
     }
     if (thermo) {
         const int kb = (int)std::min<int64_t>((n + 255) / 256, 1024);
@@ -699,6 +885,7 @@ struct tmd_batch {
     std::vector<uint8_t> has_forces;
     std::vector<int64_t> steps;
     tmd_nlist nl;
+    tmd::GraphCache g_eval, g_step;   // captured evaluation / evaluation + second half kick
 };
 
 namespace {
@@ -740,8 +927,8 @@ tmd_status batch_activate(tmd_batch *b, const int32_t *systems, int32_t n_act, c
     return TMD_OK;
 }
 
-// wrap, rebuild and evaluate the active systems (flags already set)
-tmd_status batch_eval(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
+// wrap and rebuild the tables of the active systems (flags already set)
+tmd_status batch_prepare(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
     tmd_status st;
     if ((st = batch_params(b, (double)model->dm.rc)) != TMD_OK) return st;
     // the device copy of the parameters is made by build_tables; wrapping reads it
@@ -751,11 +938,38 @@ tmd_status batch_eval(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaS
     if ((st = tmd::grow(&b->nl.sp, &b->nl.cap_sp, b->S)) != TMD_OK) return st;
     TMD_CUDA(cudaMemcpyAsync(b->nl.sp, b->sp.data(), sizeof(tmd::SysParams) * b->S, cudaMemcpyHostToDevice, s));
     TMD_LAUNCH("k_wrap_b", s, k_wrap_b<<<nb, 256, 0, s>>>(b->pos, b->n, b->nl.sp, b->sys_of, b->active));
-    if ((st = tmd::build_tables(b->pos, b->types, b->n, b->S, b->sp.data(), b->sys_of, b->active, nsys.data(),
-                                b->ncell, &b->nl, s)) != TMD_OK)
-        return st;
-    return tmd::run_compute_batch(model, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom, b->w_atom,
-                                  b->act_list, n_act, b->d_off, b->vel, b->mass, b->sys_out, s);
+    (void)n_act;
+    return tmd::build_tables(b->pos, b->types, b->n, b->S, b->sp.data(), b->sys_of, b->active, nsys.data(), b->ncell,
+                             &b->nl, s);
+}
+
+void batch_key(const tmd_model *model, const tmd_batch *b, int32_t n_act, std::vector<uintptr_t> &key) {
+    model_key(model, key);
+    nlist_key(b->nl, key);
+    const void *bp[] = {b->pos, b->vel, b->mass, b->inv_mass, b->types, b->sys_of, b->forces, b->e_atom, b->w_atom,
+                        b->d_off, b->active, b->act_list, b->sys_out};
+    for (const void *q : bp) key.push_back((uintptr_t)q);
+    key.push_back((uintptr_t)n_act);
+    key.push_back((uintptr_t)b->n);
+}
+
+// evaluate the active systems on their current tables (captured graph when repeated)
+tmd_status batch_compute_only(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
+    tmd_status st;
+    if ((st = tmd::reserve_compute(model->dm, &b->nl, b->n, b->nl.n_active)) != TMD_OK) return st;
+    std::vector<uintptr_t> key;
+    batch_key(model, b, n_act, key);
+    return graphed(b->g_eval, key, s, [&]() {
+        return tmd::run_compute_batch(model, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom,
+                                      b->w_atom, b->act_list, n_act, b->d_off, b->vel, b->mass, b->sys_out, s);
+    });
+}
+
+// wrap, rebuild and evaluate the active systems (flags already set)
+tmd_status batch_eval(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
+    tmd_status st;
+    if ((st = batch_prepare(model, b, n_act, s)) != TMD_OK) return st;
+    return batch_compute_only(model, b, n_act, s);
 }
 
 void batch_results(tmd_batch *b, int32_t n_act, double *energy, double *virial, tmd_thermo *thermo) {
@@ -930,10 +1144,23 @@ tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *b, const int32_t *s
     for (int it = 0; it < nsteps; ++it) {
         TMD_LAUNCH("k_vv_first_b", s, k_vv_first_b<<<nb, 256, 0, s>>>(b->pos, b->vel, b->forces, b->inv_mass, b->n, dt_fs,
                                                                       b->sys_of, b->active));
-        if ((st = batch_eval(model, b, n_act, s)) != TMD_OK) return st;
-        TMD_LAUNCH("k_vv_second_b", s, k_vv_second_b<<<nb, 256, 0, s>>>(b->vel, b->forces, b->inv_mass, b->n, dt_fs,
-                                                                        b->sys_of, b->active));
-        TMD_CUDA(cudaGetLastError());
+        if ((st = batch_prepare(model, b, n_act, s)) != TMD_OK) return st;
+        // evaluation and second half kick: one captured graph per table layout
+        if ((st = tmd::reserve_compute(model->dm, &b->nl, b->n, b->nl.n_active)) != TMD_OK) return st;
+        std::vector<uintptr_t> key;
+        batch_key(model, b, n_act, key);
+        key.push_back(bits_of(dt_fs));
+        st = graphed(b->g_step, key, s, [&]() {
+            tmd_status st2 = tmd::run_compute_batch(model, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces,
+                                                    b->e_atom, b->w_atom, b->act_list, n_act, b->d_off, b->vel,
+                                                    b->mass, b->sys_out, s);
+            if (st2 != TMD_OK) return st2;
+            TMD_LAUNCH("k_vv_second_b", s, k_vv_second_b<<<nb, 256, 0, s>>>(b->vel, b->forces, b->inv_mass, b->n,
+                                                                            dt_fs, b->sys_of, b->active));
+            TMD_CUDA(cudaGetLastError());
+            return TMD_OK;
+        });
+        if (st != TMD_OK) return st;
         for (int k = 0; k < n_act; ++k) b->steps[systems[k]]++;
     }
     if (thermo || nsteps == 0) {
@@ -945,6 +1172,21 @@ tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *b, const int32_t *s
     TMD_CUDA(cudaStreamSynchronize(s));
     batch_results(b, n_act, nullptr, nullptr, thermo);
     return TMD_OK;
+}
+
+tmd_status tmd_batch_autotune(tmd_model *m, tmd_batch *b, const int32_t *systems, int32_t n_act, tmd_tuning *best,
+                              tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!m || !b || !systems || n_act < 1 || n_act > b->S) { set_error("bad arguments"); return TMD_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t na = 0;
+    tmd_status st;
+    if ((st = batch_activate(b, systems, n_act, s, &na)) != TMD_OK) return st;
+    if ((st = batch_eval(m, b, n_act, s)) != TMD_OK) return st;   // tables of the listed systems
+    return tune_shapes(m, s, best, [&]() {
+        return tmd::run_compute_batch(m, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom, b->w_atom,
+                                      b->act_list, n_act, b->d_off, b->vel, b->mass, b->sys_out, s);
+    });
 }
 
 }  // extern "C"

@@ -1248,6 +1248,15 @@ int sm_count() {
 
 }  // namespace
 
+int pair_blocks(const DevModel &dm, int64_t n) {
+    const int bps = dm.pair_bps > 0 ? dm.pair_bps : 16;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * bps));
+}
+
+namespace {
+
+}  // namespace
+
 tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                              int64_t n_total, const int32_t *sys_of, float *forces, float *e_atom, float *w_atom,
                              const int32_t *act_list, int n_act, const int64_t *sys_off, const double *vel,
@@ -1276,9 +1285,14 @@ static size_t mlp_smem_tr(const DevModel &dm, int tr) {
 
 // atoms per tile: 64 unless the activations of the wider networks would leave
 // room for fewer than two blocks per SM
-static int mlp_tr(const DevModel &dm) { return mlp_smem_tr(dm, 64) <= 100 * 1024 ? 64 : 32; }
+static int mlp_tr(const DevModel &dm) {
+    if ((dm.tile_rows == 32 || dm.tile_rows == 64) && mlp_smem_tr(dm, dm.tile_rows) <= 227 * 1024) return dm.tile_rows;
+    return mlp_smem_tr(dm, 64) <= 100 * 1024 ? 64 : 32;
+}
 
 size_t mlp_smem_bytes(const DevModel &dm) { return mlp_smem_tr(dm, mlp_tr(dm)); }
+
+size_t mlp_smem_tr_public(const DevModel &dm, int tr) { return mlp_smem_tr(dm, tr); }
 
 static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, const double box[3]) {
     if (!model || !nl) {
@@ -1374,6 +1388,23 @@ static tmd_status pair_cache(tmd_nlist *nl, int64_t n_atoms, cudaStream_t) {
     return grow(&nl->npair, &nl->cap_npair, std::max<int64_t>(n_atoms, 1));
 }
 
+// Every workspace an evaluation of n_active atoms (arrays of n_total atoms)
+// uses, sized before any launch: a captured launch sequence must find them
+// already in place.
+tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, int64_t n_active) {
+    tmd_status st;
+    const int64_t nt = std::max<int64_t>(n_total, 1), na = std::max<int64_t>(n_active, 1);
+    if ((st = grow(&nl->G, &nl->cap_G, nt * dm.Dd)) != TMD_OK) return st;
+    if ((st = grow(&nl->dG, &nl->cap_dG, nt * dm.Dd)) != TMD_OK) return st;
+    if ((st = grow(&nl->P, &nl->cap_P, nt * dm.S * dm.K * NMOM)) != TMD_OK) return st;
+    if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * nt)) != TMD_OK) return st;
+    if ((st = grow(&nl->ph, &nl->cap_ph, nt)) != TMD_OK) return st;
+    if ((st = grow(&nl->pl, &nl->cap_pl, nt)) != TMD_OK) return st;
+    const int64_t nblk = pair_blocks(dm, na), ntile = (na + MT - 1) / MT;
+    if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * nblk + 16)) != TMD_OK) return st;
+    return pair_cache(nl, nt, nullptr);
+}
+
 static DevNlist dev_nlist(const tmd_nlist *nl, int64_t n, const double box[3]) {
     DevNlist dn;
     dn.beg = nl->beg;
@@ -1399,7 +1430,7 @@ tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
     if (n == 0) return TMD_OK;
     const DevModel &dm = model->dm;
     if ((st = grow(&nl->P, &nl->cap_P, n * dm.S * dm.K * NMOM)) != TMD_OK) return st;
-    const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const int nblk = pair_blocks(dm, n);
     if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
     const DevNlist dn = dev_nlist(nl, n, box);
     float *keep = nl->G;
@@ -1430,7 +1461,7 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     if ((st = grow(&nl->dG, &nl->cap_dG, n * Dd)) != TMD_OK) return st;
     if ((st = grow(&nl->P, &nl->cap_P, n * dm.S * dm.K * NMOM)) != TMD_OK) return st;
     if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * n)) != TMD_OK) return st;
-    const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const int nblk = pair_blocks(dm, n);
     const int ntile = (int)((n + MT - 1) / MT);
     if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
     double *part_e = nl->part;
@@ -1509,7 +1540,7 @@ __global__ void k_noalloc_check(const int64_t *__restrict__ off, const int32_t *
 tmd_status noalloc_capacity(const tmd_model *model, int64_t n, size_t *need) {
     const DevModel &dm = model->dm;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const int64_t nblk = std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const int64_t nblk = (int64_t)pair_blocks(dm, n);
     const int64_t ntile = (n + MT - 1) / MT;
     size_t b = 0;
     b += al(sizeof(int32_t) * n);                              // identity order
@@ -1584,7 +1615,7 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
         cur += al(bytes);
         return p;
     };
-    const int nblk = (int)std::min<int64_t>((n + PW - 1) / PW, (int64_t)sm_count() * 16);
+    const int nblk = pair_blocks(dm, n);
     const int ntile = (int)((n + MT - 1) / MT);
     tmd_nlist w;  // a view onto the static scratch; never freed
     w.perm = static_cast<int32_t *>(take(sizeof(int32_t) * n));
@@ -1678,7 +1709,7 @@ tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double
         if ((st = grow(&nl->dG, &nl->cap_dG, n_total * dm.Dd)) != TMD_OK) return st;
         if ((st = grow(&nl->P, &nl->cap_P, n_total * dm.S * dm.K * NMOM)) != TMD_OK) return st;
         if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * n_total)) != TMD_OK) return st;
-        const int nblk = (int)std::min<int64_t>((na + PW - 1) / PW, (int64_t)sm_count() * 16);
+        const int nblk = pair_blocks(dm, na);
         const int ntile = (int)((na + MT - 1) / MT);
         if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
         if ((st = split_positions(nl, pos, n_total, s)) != TMD_OK) return st;

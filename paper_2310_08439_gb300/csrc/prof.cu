@@ -71,6 +71,18 @@ ProfScope::~ProfScope() {
     r.pending.push_back({kernel_, start_, stop});
 }
 
+bool profiling_on() {
+    Registry &r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    return r.on;
+}
+
+void add_launches(int64_t k) {
+    Registry &r = reg();
+    std::lock_guard<std::mutex> lk(r.mu);
+    r.total_launches += k;
+}
+
 }  // namespace tmd
 
 using namespace tmd;

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -36,7 +38,15 @@ struct DevModel {
     const uint16_t *hb[TMD_MAX_SPECIES]; // BF16 backward copy (same layout as wb)
     int off_f[MAX_LAYERS];              // offset of layer l in wf[s] / hf[s]
     int off_b[MAX_LAYERS];              // offset of layer l in wb[s] / hb[s]
+    // tile shapes (host-side launch choices; 0 = built-in default)
+    int tile_rows;                      // atoms per FP32 network tile: 32 or 64
+    int pair_bps;                       // blocks per SM of the persistent pair-kernel grid
 };
+
+// persistent grid of the pair kernels for n atoms
+int pair_blocks(const DevModel &dm, int64_t n);
+// shared memory of the FP32 network kernel with tr-atom tiles
+size_t mlp_smem_tr_public(const DevModel &dm, int tr);
 
 // One system of a batch (a single evaluation is a batch of one): box, cell
 // grid, first global cell, list radius and the FP32 screening band.
@@ -136,6 +146,23 @@ struct tmd_nlist {
     double *io_red = nullptr;   int64_t cap_io_red = 0;   // energy + virial
 };
 
+namespace tmd {
+
+// A captured CUDA graph of one fixed launch sequence, keyed by everything the
+// sequence's launches depend on (buffer addresses, sizes, scalars).  The first
+// call with a new key runs eagerly (it sizes the workspaces); the second
+// captures and instantiates; later calls replay.
+struct GraphCache {
+    std::vector<uintptr_t> key, pending;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    ~GraphCache() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+}  // namespace tmd
+
 struct tmd_system {
     int64_t n = 0;
     double box[3];
@@ -150,6 +177,7 @@ struct tmd_system {
     tmd_nlist nl;
     int64_t step = 0, rebuilds = 0;
     int need_rebuild = 1, have_forces = 0;
+    tmd::GraphCache g_step;      // force evaluation + second half kick
 };
 
 namespace tmd {
@@ -166,6 +194,11 @@ class ProfScope {
     int kernel_;
     cudaEvent_t start_;
 };
+
+// profiling switch and launch counter (kernels replayed from a CUDA graph
+// are added to the counter by the replaying code)
+bool profiling_on();
+void add_launches(int64_t k);
 
 #define TMD_LAUNCH(name, stream, ...)                   \
     do {                                                \
@@ -225,6 +258,7 @@ void sys_reduce_launch(const int32_t *act, int n_act, const int64_t *off, const 
                        const double *vel, const double *mass, double *out, cudaStream_t s);
 tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
                            const int32_t pbc[3], double r_list, tmd_nlist *nl, cudaStream_t s);
+tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, int64_t n_active);
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                        int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
                        double *virial, cudaStream_t s);

@@ -49,6 +49,13 @@ class Thermo(C.Structure):
                 "step": self.step, "rebuilds": self.rebuilds}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("tile_rows", C.c_int32), ("pair_blocks_per_sm", C.c_int32), ("ms", C.c_float)]
+
+    def as_dict(self):
+        return {"tile_rows": self.tile_rows, "pair_blocks_per_sm": self.pair_blocks_per_sm, "ms": self.ms}
+
+
 _P = C.c_void_p
 _SIGS = {
     "tmd_status_string": (C.c_char_p, [C.c_int]),
@@ -57,6 +64,10 @@ _SIGS = {
     "tmd_model_create": (C.c_int, [C.POINTER(_Desc), C.POINTER(_P)]),
     "tmd_model_destroy": (C.c_int, [_P]),
     "tmd_model_set_precision": (C.c_int, [_P, C.c_int32]),
+    "tmd_model_set_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "tmd_model_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "tmd_autotune": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), C.POINTER(Tuning), _P]),
+    "tmd_batch_autotune": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(Tuning), _P]),
     "tmd_nlist_create": (C.c_int, [C.POINTER(_P)]),
     "tmd_nlist_destroy": (C.c_int, [_P]),
     "tmd_neighbors": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32),
@@ -86,6 +97,8 @@ _SIGS = {
     "tmd_profile_enable": (C.c_int, [C.c_int32]),
     "tmd_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
     "tmd_launch_count": (C.c_int64, []),
+    "tmd_set_graphs": (C.c_int, [C.c_int32]),
+    "tmd_graph_replays": (C.c_int64, []),
 }
 
 
@@ -107,6 +120,15 @@ def profile_read(reset=True):
 
 def launch_count():
     return int(lib().tmd_launch_count())
+
+
+def set_graphs(on=True):
+    """Process-wide switch for the captured CUDA graphs of the MD / batch loops."""
+    check(lib().tmd_set_graphs(1 if on else 0))
+
+
+def graph_replays():
+    return int(lib().tmd_graph_replays())
 
 
 def lib():
@@ -181,6 +203,20 @@ class Model:
         check(lib().tmd_model_set_precision(self.handle, PREC[precision]))
         self.precision = precision
 
+    @property
+    def tuning(self):
+        """Tile shapes in use: {tile_rows, pair_blocks_per_sm} (0 = built-in choice)."""
+        t = Tuning()
+        check(lib().tmd_model_get_tuning(self.handle, C.byref(t)))
+        d = t.as_dict()
+        d.pop("ms")
+        return d
+
+    @tuning.setter
+    def tuning(self, d):
+        t = Tuning(int(d.get("tile_rows", 0)), int(d.get("pair_blocks_per_sm", 0)), 0.0)
+        check(lib().tmd_model_set_tuning(self.handle, C.byref(t)))
+
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.tmd_model_destroy(self.handle)
@@ -225,6 +261,14 @@ def compute(model, nl, pos, types, box, energy=None, e_atom=None, forces=None, v
     """tmd_compute into caller-provided cuda tensors (any may be None)."""
     check(lib().tmd_compute(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box),
                             _dptr(energy), _dptr(e_atom), _dptr(forces), _dptr(virial), _stream(stream)))
+
+
+def autotune(model, nl, pos, types, box, stream=None):
+    """Time every candidate tile shape on this system and keep the fastest in the model."""
+    t = Tuning()
+    check(lib().tmd_autotune(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box),
+                             C.byref(t), _stream(stream)))
+    return t.as_dict()
 
 
 def descriptors(model, nl, pos, types, box, stream=None, with_grad=False):
@@ -365,6 +409,14 @@ class Batch:
         check(lib().tmd_batch_step(model.handle, self.handle, ids.ctypes.data_as(_P), int(ids.size), float(dt),
                                    int(nsteps), C.cast(th, _P), _stream(stream)))
         return [th[k].as_dict() for k in range(ids.size)]
+
+    def autotune(self, model, systems, stream=None):
+        """Time every candidate tile shape on these systems and keep the fastest in the model."""
+        ids = np.ascontiguousarray(systems, dtype=np.int32)
+        t = Tuning()
+        check(lib().tmd_batch_autotune(model.handle, self.handle, ids.ctypes.data_as(_P), int(ids.size), C.byref(t),
+                                       _stream(stream)))
+        return t.as_dict()
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
