@@ -194,6 +194,7 @@ def batch_measure(tmd, torch, steps=5):
            for k in sample}
     for prec in ("fp32", "bf16"):
         m.set_precision(prec)
+        tuning = b.autotune(m, ids)   # tile shapes for this batch and form
         b.compute(m, ids)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -208,9 +209,40 @@ def batch_measure(tmd, torch, steps=5):
             errs.append({"system": int(k), "n": int(w.systems[k].n),
                          "dE_rel": abs(E[k] - o["energy"]) / abs(o["energy"]),
                          "dF_max_over_rms": float(np.abs(f - o["forces"]).max() / rms)})
-        out[prec] = {"atom_evals_per_s": n_tot / dt, "ms_per_batch_eval": dt * 1e3,
+        out[prec] = {"atom_evals_per_s": n_tot / dt, "ms_per_batch_eval": dt * 1e3, "tuning": tuning,
                      "max_dE_rel": max(e["dE_rel"] for e in errs),
                      "max_dF_over_rms": max(e["dF_max_over_rms"] for e in errs), "per_system": errs}
+    return out
+
+
+def graphs_measure(tmd, torch, steps=60):
+    """Launch overhead: the medium cell (16,384 atoms) advanced one step per
+    call with the skin check (rebuild only when an atom moved > skin/2), eager
+    launches vs the captured CUDA graph of the evaluation + half kick."""
+    from paper_2310_08439_gb300 import inputs as I
+    w = I.medium()
+    s = w.systems[0]
+    m = tmd.Model(w.model)
+    side = torch.cuda.Stream()
+    out = {"workload": "medium: 16^3 fcc, 16,384 atoms, 2 species, K 16, 64-64-1; one MD step per call, skin 1 A"}
+    for graphs in (False, True):
+        tmd.set_graphs(graphs)
+        g = tmd.System(s.n, s.box, s.pbc, skin=w.skin)
+        g.set_state(s.pos, s.vel, s.types, s.masses, stream=side)
+        for _ in range(4):
+            g.step(m, w.dt_fs, 1, rebuild_every=0, stream=side, thermo=False)
+        side.synchronize()
+        r0 = tmd.graph_replays()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(steps):
+            g.step(m, w.dt_fs, 1, rebuild_every=0, stream=side, thermo=False)
+        e1.record(side)
+        side.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["graphs" if graphs else "eager"] = {"value": s.n * steps / (ms * 1e-3), "unit": UNIT,
+                                               "ms_per_step": ms / steps, "replays": tmd.graph_replays() - r0}
+    tmd.set_graphs(True)
     return out
 
 
@@ -323,6 +355,8 @@ def main():
     ap.add_argument("--reps", type=int, default=64, help="fcc repeats of the large cell (64 = 1,048,576 atoms)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--tuning", default="auto",
+                    help="tile shapes 'ROWS,BLOCKS_PER_SM' instead of the autotuner (e.g. for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -358,6 +392,22 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    for _ in range(args.warmup):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+    torch.cuda.synchronize()
+    # tile shapes picked by the autotuner on this system (kept in the model)
+    if args.tuning == "auto":
+        p_w, _, _ = sysm.get_state()
+        nl_t = tmd.NeighborList()
+        pos_t = torch.as_tensor(p_w, device=dev)
+        types_t = torch.as_tensor(s.types, device=dev)
+        nl_t.build(pos_t, types_t, s.box, s.pbc, w.model.rc + w.skin)
+        tuning = tmd.autotune(model, nl_t, pos_t, types_t, s.box)
+        del nl_t, pos_t, types_t
+    else:
+        rows, bps = (int(x) for x in args.tuning.split(","))
+        model.tuning = {"tile_rows": rows, "pair_blocks_per_sm": bps}
+        tuning = dict(model.tuning, ms=None)
     for _ in range(args.warmup):
         sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
     torch.cuda.synchronize()
@@ -475,6 +525,7 @@ def main():
     extras = {}
     if not args.no_extras and world == 1:
         extras["batch"] = batch_measure(tmd, torch)
+        extras["graphs"] = graphs_measure(tmd, torch)
         extras["serving"] = serving_measure(tmd, args.serve_seconds, torch)
 
     cpu = None
@@ -491,7 +542,7 @@ def main():
                        "l2": "inputs larger than L2 (neighbour table ~%.2f GB, %d in-cutoff pairs)"
                              % (nl.size()[1] * 8 / 1e9, pairs),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "forms": forms, "compute_only": compute_only, "roofline": roof, "kernels": kernels,
+            "forms": forms, "compute_only": compute_only, "tuning": tuning, "roofline": roof, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     line.update(extras)
     print(json.dumps(line), flush=True)

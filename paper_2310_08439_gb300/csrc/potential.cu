@@ -432,7 +432,10 @@ __device__ __forceinline__ float act_da(int act, float a, float b) {
 // input rows by at most MLP_NP output columns: while the block multiplies with
 // one chunk, cp.async brings in the next chunk of the tile's fixed sequence of
 // products (forward layers, then the backward chain).  Every thread
-// accumulates a 4 x 4 block of outputs per item (one or two items per pass).
+// accumulates a 4 x 4 block of outputs per item (one or two items per pass),
+// summing each chunk of MLP_KC products separately before adding it to the
+// running total: the rounding error grows with MLP_KC + Kin / MLP_KC instead
+// of Kin, which halves the error of G' for the 192-128-128 networks.
 // ---------------------------------------------------------------------------
 constexpr int MLP_KC = 16;     // streamed weight rows per chunk
 constexpr int MLP_NP = 128;    // output columns per pass
@@ -544,6 +547,11 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
                 if (tid + ii * MLP_THREADS < items) {
                     const float *a = At + (size_t)k0 * LDT + rb[ii] * 4;
                     const float *b = w + cb[ii] * 4;
+                    float pp[4][4];   // this chunk's sums, added to acc once (two-level summation)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) pp[i][o] = 0.f;
 #pragma unroll 8
                     for (int k = 0; k < kc; ++k) {
                         const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
@@ -551,12 +559,16 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
                         const float ai[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            acc[ii][i][0] = fmaf(ai[i], bv.x, acc[ii][i][0]);
-                            acc[ii][i][1] = fmaf(ai[i], bv.y, acc[ii][i][1]);
-                            acc[ii][i][2] = fmaf(ai[i], bv.z, acc[ii][i][2]);
-                            acc[ii][i][3] = fmaf(ai[i], bv.w, acc[ii][i][3]);
+                            pp[i][0] = fmaf(ai[i], bv.x, pp[i][0]);
+                            pp[i][1] = fmaf(ai[i], bv.y, pp[i][1]);
+                            pp[i][2] = fmaf(ai[i], bv.z, pp[i][2]);
+                            pp[i][3] = fmaf(ai[i], bv.w, pp[i][3]);
                         }
                     }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) acc[ii][i][o] += pp[i][o];
                 }
             }
             __syncthreads();   // every thread is done with this buffer

@@ -86,3 +86,19 @@ def test_batch_step_matches_system_step(tmdlib, small_batch):
         assert np.abs(v2 - v1).max() < 1e-10, k
         assert abs(th[k]["e_pot"] - ths["e_pot"]) <= 1e-9 * abs(ths["e_pot"]), k
         assert abs(th[k]["e_kin"] - ths["e_kin"]) <= 1e-9 * abs(ths["e_kin"]) + 1e-12, k
+
+
+@pytest.mark.parametrize("k", [285, 68])
+def test_fp32_batch_network_small_force_systems(tmdlib, k):
+    """Two systems of the 512-system workload whose net forces are small
+    against the pair terms (RMS ~0.004 eV/A): the FP32 path must still be
+    within 1e-5 of the force RMS (the 192-128-128 network's input gradient
+    is the largest error source there)."""
+    w = I.batch()
+    s = w.systems[k]
+    e, f, v = _single(tmdlib, w.model, s)
+    o = O.evaluate(O.OracleModel(w.model), s.pos, s.types, s.box, s.pbc)
+    rms = np.sqrt((o["forces"] ** 2).mean())
+    assert abs(e - o["energy"]) <= 1e-6 * abs(o["energy"])
+    assert np.abs(f - o["forces"]).max() <= 1e-5 * rms
+    assert np.abs(v - o["virial"]).max() <= 1e-5 * np.abs(o["virial"]).max()
