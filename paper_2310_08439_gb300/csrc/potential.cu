@@ -707,16 +707,26 @@ __global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_
 
 // ---------------------------------------------------------------------------
 // network on BF16 tensor cores (FP32 accumulation): the same forward / input-
-// gradient chain as k_mlp for a 64-atom tile; warp w owns rows 16w..16w+15 and
-// issues mma m16n8k16 per (16 x 8) output block.  Activations and the
-// activation derivatives are kept in shared memory as BF16.
+// gradient chain as k_mlp for a 64-atom tile.  Eight warps: warp w owns rows
+// 16 (w % 4) .. + 16 and one half of each weight chunk's output columns, and
+// issues mma m16n8k16 with ldmatrix operands.  Activations and activation
+// derivatives stay in shared memory as BF16; the weights stream through two
+// shared buffers in chunks of BF_NC output rows (cp.async, one chunk ahead,
+// across the whole product sequence).  The output layer (E_a) and dz_L are
+// formed in the epilogue of the last forward product.
 // ---------------------------------------------------------------------------
 constexpr int BT = 64;            // atoms per BF16 tile
-constexpr int BF_THREADS = 128;   // 4 warps x 16 rows
+constexpr int BF_THREADS = 256;   // 8 warps: 4 row slabs x 2 column halves
+constexpr int BF_NC = 64;         // output columns per streamed weight chunk
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float2 unpack_bf16(uint32_t u) {
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&u);
+    return __bfloat1622float2(v);
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
@@ -735,65 +745,57 @@ __device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2
                  : "r"(a));
 }
 
-// Bt[n0 .. n0 + nrows)[0 .. K) -> wsm with row stride K + 8 (all threads of the block)
-__device__ __forceinline__ void stage_bt(const uint16_t *__restrict__ Bt, int n0, int nrows, int K, uint16_t *wsm) {
-    const int c8 = K >> 3;
-    for (int idx = threadIdx.x; idx < nrows * c8; idx += blockDim.x) {
-        const int r = idx / c8, c = idx - r * c8;
-        *reinterpret_cast<uint4 *>(wsm + r * (K + 8) + 8 * c) =
-            __ldg(reinterpret_cast<const uint4 *>(Bt + (size_t)(n0 + r) * K + 8 * c));
-    }
+// Product `step` of species s as Bt[n][k] (K contiguous per output column):
+// forward layer l: Bt = W_l [out][in]; backward layer l: Bt = W_l^T [in][out].
+struct BfStep {
+    const uint16_t *Bt;
+    int K, N;
+};
+__device__ __forceinline__ BfStep bf_step(const DevModel &m, int s, int step) {
+    const int L = m.L;
+    if (step < L) return {m.hb[s] + m.off_b[step], m.dims[step], m.dims[step + 1]};
+    const int l = 2 * L - 1 - step;
+    return {m.hf[s] + m.off_f[l], m.dims[l + 1], m.dims[l]};
 }
 
-// C[16 rows of this warp][8 nt columns] = A[rows][0..K) * B with B[k][n] =
-// wsm[n * (K + 8) + k] (the staged chunk), nt <= 8 and even.  A and B
-// fragments come from ldmatrix (rows padded by 8 elements: conflict-free).
-__device__ __forceinline__ void warp_gemm_bf16(const uint16_t *A, int lda, int K, const uint16_t *wsm, int nt,
-                                               int lane, float (&acc)[8][4]) {
-    const int ldw = K + 8;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const uint16_t *pa = A + (lane & 15) * lda + (lane >> 4) * 8;
-    const uint16_t *pb = wsm + ((lane & 7) + ((lane >> 4) << 3)) * ldw + ((lane >> 3) & 1) * 8;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(a0, a1, a2, a3, pa + k0);
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-            if (j < nt) {
-                uint32_t b0, b1, b2, b3;
-                ldsm_x4(b0, b1, b2, b3, pb + j * 8 * ldw + k0);
-                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
-                mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
-            }
-        }
-    }
+// Bt rows [n0, n0 + min(BF_NC, N - n0)) into buf (row stride K + 8), one
+// warp per row (K <= 256: a row is at most 32 16-byte copies)
+__device__ __forceinline__ void bf_issue(const BfStep &st, int n0, uint16_t *buf) {
+    const int nc = min(BF_NC, st.N - n0), c8 = st.K >> 3;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < nc; r += BF_THREADS / 32)
+        if (lane < c8) cp_async16(buf + r * (st.K + 8) + 8 * lane, st.Bt + (size_t)(n0 + r) * st.K + 8 * lane);
 }
 
-__global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32_t *__restrict__ perm,
+struct BfStream {
+    int s, s_hi, step, par;
+};
+
+__global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const int32_t *__restrict__ perm,
                                                          const int32_t *__restrict__ types, int64_t n,
                                                          const float *__restrict__ G, float *__restrict__ dG,
                                                          float *__restrict__ e_atom, double *__restrict__ part_e) {
     extern __shared__ __align__(16) uint16_t smh[];
-    __shared__ int s_atom[BT], s_type[BT];
-    __shared__ double s_e[BF_THREADS / 32];
+    __shared__ int s_atom[BT], s_type[BT], s_range[2];
+    __shared__ float s_e[BT], s_epart[2][BT];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
+    const int slab = warp & 3, half = warp >> 2;
     const int64_t p0 = (int64_t)blockIdx.x * BT;
-    if (tid < BT) {
-        const int64_t p = p0 + tid;
-        const int a = p < n ? perm[p] : -1;
-        s_atom[tid] = a;
-        s_type[tid] = a >= 0 ? types[a] : -1;
-    }
     const int L = m.L, Dd = m.Dd;
-    int maxw = Dd;
-    for (int l = 1; l <= L; ++l) maxw = max(maxw, m.dims[l]);
-    // shared layout (BF16): act[0] = G tile, act[l] / der[l] for hidden layers, two gradient buffers
+    int maxw = 0, kmax = Dd;
+    for (int l = 1; l <= L; ++l) {
+        maxw = max(maxw, m.dims[l]);
+        kmax = max(kmax, m.dims[l]);
+    }
+    // shared layout (BF16 elements): two weight buffers, act[0] = G tile,
+    // act[l] / der[l] for hidden layers 1..L-1, two gradient buffers
+    const int ldw_max = kmax + 8;
+    uint16_t *wbuf = smh;
     uint16_t *act[MAX_LAYERS + 1], *der[MAX_LAYERS + 1];
     int ld[MAX_LAYERS + 1];
-    uint16_t *ptr = smh;
-    for (int l = 0; l <= L; ++l) {
+    uint16_t *ptr = smh + 2 * BF_NC * ldw_max;
+    for (int l = 0; l < L; ++l) {
         ld[l] = m.dims[l] + 8;
         act[l] = ptr;
         ptr += BT * ld[l];
@@ -802,118 +804,156 @@ __global__ void __launch_bounds__(BF_THREADS) k_mlp_bf16(DevModel m, const int32
     }
     const int ldz = maxw + 8;
     uint16_t *dzA = ptr, *dzB = ptr + BT * ldz;
-    uint16_t *wsm = dzB + BT * ldz;   // staged weight chunk: 64 rows x (maxw + 8)
-    __syncthreads();
-    for (int idx = tid; idx < BT * (Dd / 2); idx += blockDim.x) {
-        const int r = idx / (Dd / 2), c2 = idx - r * (Dd / 2);
-        const int a = s_atom[r];
-        float2 v = make_float2(0.f, 0.f);
-        if (a >= 0) v = *reinterpret_cast<const float2 *>(G + (size_t)a * Dd + 2 * c2);
-        *reinterpret_cast<uint32_t *>(act[0] + r * ld[0] + 2 * c2) = pack_bf16(v.x, v.y);
+    if (tid < BT) {
+        const int64_t p = p0 + tid;
+        const int a = p < n ? perm[p] : -1;
+        s_atom[tid] = a;
+        s_type[tid] = a >= 0 ? types[a] : -1;
+        s_e[tid] = 0.f;
     }
     __syncthreads();
-    int s_lo = TMD_MAX_SPECIES, s_hi = -1;
-    for (int r = 0; r < BT; ++r)
-        if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
-    const int r0 = warp * 16;
-    double esum = 0.0;
+    if (warp == 0) {   // species present in the tile (perm groups atoms by species)
+        int lo = TMD_MAX_SPECIES, hi = -1;
+        for (int r = lane; r < BT; r += 32)
+            if (s_type[r] >= 0) { lo = min(lo, s_type[r]); hi = max(hi, s_type[r]); }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) { s_range[0] = lo; s_range[1] = hi; }
+    }
+    __syncthreads();
+    const int s_lo = s_range[0], s_hi = s_range[1];
+    BfStream ws{s_lo, s_hi, 0, 0};
+    if (s_lo <= s_hi) bf_issue(bf_step(m, s_lo, 0), 0, wbuf);   // first chunk, under the G loads
+    cp_async_commit();
+    // G rows -> act[0] as BF16 (warp per atom row)
+    for (int r = warp; r < BT; r += BF_THREADS / 32) {
+        const int a = s_atom[r];
+        for (int c2 = lane; c2 < (Dd >> 1); c2 += 32) {
+            float2 v = make_float2(0.f, 0.f);
+            if (a >= 0) v = __ldg(reinterpret_cast<const float2 *>(G + (size_t)a * Dd + 2 * c2));
+            *reinterpret_cast<uint32_t *>(act[0] + r * ld[0] + 2 * c2) = pack_bf16(v.x, v.y);
+        }
+    }
     for (int s = s_lo; s <= s_hi; ++s) {
         const float *wf = m.wf[s];
-        // forward: z = a W^T + b, a' = act(z); B[k=i][n=o] = W[o][i] (BF16 [out][in])
-        for (int l = 0; l < L; ++l) {
-            const int in = m.dims[l], out = m.dims[l + 1];
-            const uint16_t *W = m.hb[s] + m.off_b[l];
-            const float *bias = wf + m.off_f[l] + in * out;
-            for (int n0 = 0; n0 < out; n0 += 64) {
-                float acc[8][4];
-                const int nt = min(8, (out - n0) / 8);
-                __syncthreads();   // earlier readers of wsm are done
-                stage_bt(W, n0, 8 * nt, in, wsm);
-                __syncthreads();
-                warp_gemm_bf16(act[l] + r0 * ld[l], ld[l], in, wsm, nt, lane, acc);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j >= nt) continue;
-                    const int col = n0 + 8 * j + 2 * t;
-                    const float b0 = __ldg(bias + col), b1 = __ldg(bias + col + 1);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int row = r0 + g + 8 * h;
-                        const float z0 = acc[j][2 * h] + b0, z1 = acc[j][2 * h + 1] + b1;
-                        const float a0v = act_f_bf16(m.act, z0, m.sp_b), a1v = act_f_bf16(m.act, z1, m.sp_b);
-                        *reinterpret_cast<uint32_t *>(act[l + 1] + row * ld[l + 1] + col) = pack_bf16(a0v, a1v);
-                        *reinterpret_cast<uint32_t *>(der[l + 1] + row * ld[l + 1] + col) =
-                            pack_bf16(act_da(m.act, a0v, m.sp_b), act_da(m.act, a1v, m.sp_b));
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        // output layer (FP32 dot over the BF16 activations)
-        const int wl = m.dims[L];
         const float *wout = m.wb[s] + m.off_b[L];
-        const float bout = __ldg(wf + m.off_f[L] + wl);
-        for (int r = warp; r < BT; r += BF_THREADS / 32) {
-            float v = 0.f;
-            for (int c = lane; c < wl; c += 32)
-                v = fmaf(__bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(act[L] + r * ld[L] + c)),
-                         __ldg(wout + c), v);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && s_type[r] == s) {
-                const float e = v + bout;
-                if (e_atom) e_atom[s_atom[r]] = e;
-                esum += (double)e;
-            }
-        }
-        // dz_L = w_out * act'(a_L)
-        for (int idx = tid; idx < BT * (wl / 2); idx += blockDim.x) {
-            const int r = idx / (wl / 2), c = 2 * (idx - r * (wl / 2));
-            const __nv_bfloat162 d2 = *reinterpret_cast<const __nv_bfloat162 *>(der[L] + r * ld[L] + c);
-            *reinterpret_cast<uint32_t *>(dzA + r * ldz + c) =
-                pack_bf16(__ldg(wout + c) * __low2float(d2), __ldg(wout + c + 1) * __high2float(d2));
-        }
-        __syncthreads();
+        float epart[2] = {0.f, 0.f};   // E partial sums of rows g and g + 8 (last forward product)
         uint16_t *cur = dzA, *nxt = dzB;
-        // backward: da_l = dz_{l+1} W_l; B[k=o][n=i] = W[o][i] = W^T[i][o] (BF16 [in][out])
-        for (int l = L - 1; l >= 0; --l) {
-            const int in = m.dims[l], out = m.dims[l + 1];
-            const uint16_t *Wt = m.hf[s] + m.off_f[l];
-            for (int n0 = 0; n0 < in; n0 += 64) {
-                float acc[8][4];
-                const int nt = min(8, (in - n0) / 8);
-                __syncthreads();
-                stage_bt(Wt, n0, 8 * nt, out, wsm);
-                __syncthreads();
-                warp_gemm_bf16(cur + r0 * ldz, ldz, out, wsm, nt, lane, acc);
+        for (int step = 0; step < 2 * L; ++step) {
+            const BfStep st = bf_step(m, s, step);
+            const bool fwd = step < L, last_fwd = step == L - 1, last = step == 2 * L - 1;
+            const int l_out = fwd ? step + 1 : 2 * L - 1 - step;   // layer whose activation / gradient is formed
+            const uint16_t *A = fwd ? act[step] : cur;
+            const int lda = fwd ? ld[step] : ldz;
+            const int ldw = st.K + 8;
+            for (int n0 = 0; n0 < st.N; n0 += BF_NC) {
+                // next chunk of the stream (same product, next product or next species)
+                {
+                    int s2 = s, step2 = step, n2 = n0 + BF_NC;
+                    if (n2 >= st.N) {
+                        n2 = 0;
+                        if (++step2 == 2 * L) { step2 = 0; ++s2; }
+                    }
+                    if (s2 <= s_hi) bf_issue(bf_step(m, s2, step2), n2, wbuf + (ws.par ^ 1) * (BF_NC * ldw_max));
+                    cp_async_commit();
+                }
+                cp_async_wait1();
+                __syncthreads();   // this chunk has landed; A is complete
+                const uint16_t *w = wbuf + ws.par * (BF_NC * ldw_max);
+                const int nc = min(BF_NC, st.N - n0);
+                const int hc = nc >> 1;                // columns of this warp's half
+                const int nt = hc >> 3;                // n-tiles of 8 (1..4)
+                float acc[4][4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j >= nt) continue;
-                    const int col = n0 + 8 * j + 2 * t;
+                for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+                const uint16_t *pa = A + (slab * 16 + (lane & 15)) * lda + (lane >> 4) * 8;
+                const uint16_t *pb = w + (half * hc + (lane & 7) + ((lane >> 4) << 3)) * ldw + ((lane >> 3) & 1) * 8;
+                for (int k0 = 0; k0 < st.K; k0 += 16) {
+                    uint32_t a0, a1, a2, a3;
+                    ldsm_x4(a0, a1, a2, a3, pa + k0);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int row = r0 + g + 8 * h;
-                        if (l > 0) {
-                            const __nv_bfloat162 d2 = *reinterpret_cast<const __nv_bfloat162 *>(der[l] + row * ld[l] + col);
-                            *reinterpret_cast<uint32_t *>(nxt + row * ldz + col) =
-                                pack_bf16(acc[j][2 * h] * __low2float(d2), acc[j][2 * h + 1] * __high2float(d2));
-                        } else if (s_type[row] == s) {
-                            *reinterpret_cast<float2 *>(dG + (size_t)s_atom[row] * Dd + col) =
-                                make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
+                    for (int j = 0; j < 4; j += 2) {
+                        if (j < nt) {
+                            uint32_t b0, b1, b2, b3;
+                            ldsm_x4(b0, b1, b2, b3, pb + j * 8 * ldw + k0);
+                            mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                            mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
                         }
                     }
                 }
+                // epilogue: element (row, col) of this lane is acc[j][2 h + e],
+                // row = 16 slab + g + 8 h, col = n0 + half * hc + 8 j + 2 t + e
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j >= nt) continue;
+                    const int col = n0 + half * hc + 8 * j + 2 * t;
+                    if (fwd) {
+                        const float b0 = __ldg(wf + m.off_f[step] + st.K * st.N + col);
+                        const float b1 = __ldg(wf + m.off_f[step] + st.K * st.N + col + 1);
+                        float w0 = 0.f, w1 = 0.f;
+                        if (last_fwd) { w0 = __ldg(wout + col); w1 = __ldg(wout + col + 1); }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int row = slab * 16 + g + 8 * h;
+                            const float a0v = act_f_bf16(m.act, acc[j][2 * h] + b0, m.sp_b);
+                            const float a1v = act_f_bf16(m.act, acc[j][2 * h + 1] + b1, m.sp_b);
+                            const float d0 = act_da(m.act, a0v, m.sp_b), d1 = act_da(m.act, a1v, m.sp_b);
+                            if (last_fwd) {   // E_r partial and dz_L = w_out * act'(a_L)
+                                epart[h] = fmaf(w0, a0v, fmaf(w1, a1v, epart[h]));
+                                *reinterpret_cast<uint32_t *>(dzA + row * ldz + col) = pack_bf16(w0 * d0, w1 * d1);
+                            } else {
+                                *reinterpret_cast<uint32_t *>(act[l_out] + row * ld[l_out] + col) = pack_bf16(a0v, a1v);
+                                *reinterpret_cast<uint32_t *>(der[l_out] + row * ld[l_out] + col) = pack_bf16(d0, d1);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int row = slab * 16 + g + 8 * h;
+                            if (!last) {   // dz_l = (dz_{l+1} W_l^T) * act'(a_l)
+                                const float2 d = unpack_bf16(*reinterpret_cast<const uint32_t *>(der[l_out] + row * ld[l_out] + col));
+                                *reinterpret_cast<uint32_t *>(nxt + row * ldz + col) =
+                                    pack_bf16(acc[j][2 * h] * d.x, acc[j][2 * h + 1] * d.y);
+                            } else if (s_type[row] == s) {   // G'
+                                *reinterpret_cast<float2 *>(dG + (size_t)s_atom[row] * Dd + col) =
+                                    make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
+                            }
+                        }
+                    }
+                }
+                __syncthreads();   // every warp is done with this weight buffer and with A
+                ws.par ^= 1;
             }
-            __syncthreads();
-            uint16_t *tmp = cur; cur = nxt; nxt = tmp;
+            if (last_fwd) {
+                // E_r = b + w . a_L: reduce the quad (the four lanes of a row), then the two halves
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    epart[h] += __shfl_xor_sync(0xffffffffu, epart[h], 1);
+                    epart[h] += __shfl_xor_sync(0xffffffffu, epart[h], 2);
+                    if (t == 0) s_epart[half][slab * 16 + g + 8 * h] = epart[h];
+                }
+                __syncthreads();
+                if (tid < BT && s_type[tid] == s) {
+                    const float e = (s_epart[0][tid] + s_epart[1][tid]) + __ldg(wf + m.off_f[L] + m.dims[L]);
+                    s_e[tid] = e;
+                    if (e_atom) e_atom[s_atom[tid]] = e;
+                }
+            }
+            if (!fwd) { uint16_t *tmp = cur; cur = nxt; nxt = tmp; }
         }
     }
-    if (lane == 0) s_e[warp] = esum;
+    asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
-    if (tid == 0) {
+    // tile energy in FP64, fixed order
+    if (tid < 32) {
         double tsum = 0.0;
-        for (int w = 0; w < BF_THREADS / 32; ++w) tsum += s_e[w];
-        part_e[blockIdx.x] = tsum;
+        for (int r = lane; r < BT; r += 32) tsum += (double)s_e[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+        if (lane == 0) part_e[blockIdx.x] = tsum;
     }
 }
 
@@ -1275,14 +1315,15 @@ tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double
                              const double *mass, double *sys_out, cudaStream_t s);
 
 size_t mlp_bf16_smem_bytes(const DevModel &dm) {
-    int maxw = dm.Dd;
-    size_t el = (size_t)BT * (dm.dims[0] + 8);
+    int maxw = 0, kmax = dm.Dd;
     for (int l = 1; l <= dm.L; ++l) {
-        el += 2 * (size_t)BT * (dm.dims[l] + 8);
         maxw = std::max(maxw, dm.dims[l]);
+        kmax = std::max(kmax, dm.dims[l]);
     }
-    el += 2 * (size_t)BT * (maxw + 8);
-    el += (size_t)64 * (maxw + 8);   // staged weight chunk
+    size_t el = (size_t)2 * BF_NC * (kmax + 8);           // two weight buffers
+    el += (size_t)BT * (dm.dims[0] + 8);                   // G tile
+    for (int l = 1; l < dm.L; ++l) el += 2 * (size_t)BT * (dm.dims[l] + 8);   // act, act'
+    el += 2 * (size_t)BT * (maxw + 8);                     // gradient buffers
     return el * sizeof(uint16_t);
 }
 
