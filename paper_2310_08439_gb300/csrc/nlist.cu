@@ -353,13 +353,51 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
 constexpr int CELL_WARPS = 8;
 constexpr int CAND_CAP = 1920;   // staged candidates per cell (60 groups of 32)
 constexpr int LIST_CAP = 256;    // per-warp list of one atom's hits (longer lists: slower path)
-constexpr int MAX_SEGS = 343;  // stencil cells ((2R+1)^3 for R <= 3)
+constexpr int MAX_SEGS = 125;  // stencil cells ((2R+1)^3 for R <= 2; wider stencils take the per-atom pass)
 
 
 // small integer -> float without a conversion instruction (|v| < 2^22):
 // 1.5 * 2^23 + v has v in the low significand bits.
 __device__ __forceinline__ float small_int_to_float(int v) {
     return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
+// The stencil of cell c as one segment per stencil cell, in (dz, dy, dx)
+// order: first atom in cell order, count and shift code (all threads of the
+// block; nothing when the stencil exceeds MAX_SEGS).
+__device__ __forceinline__ void cell_lookup(const NbrParams &p, int64_t c, const int32_t *__restrict__ cell_sys,
+                                            int *seg_b0, int *seg_cnt, uint16_t *seg_code) {
+    const SysParams &sysp = p.sp[cell_sys ? cell_sys[c] : 0];
+    const int nc0 = sysp.nc[0], nc1 = sysp.nc[1], nc2 = sysp.nc[2];
+    const int w0 = 2 * sysp.R[0] + 1, w1 = 2 * sysp.R[1] + 1;
+    const int nseg = w0 * w1 * (2 * sysp.R[2] + 1);
+    if (nseg > MAX_SEGS) return;
+    const int ci = (int)(c - sysp.cell_off);
+    const int cx = ci % nc0, cy = (ci / nc0) % nc1, cz = ci / (nc0 * nc1);
+    for (int t = threadIdx.x; t < nseg; t += blockDim.x) {
+        const int tx = t % w0, tyz = t / w0;
+        const int ux = cx + tx - sysp.R[0], uy = cy + tyz % w1 - sysp.R[1], uz = cz + tyz / w1 - sysp.R[2];
+        int b0 = 0, cnt = 0, code = 0;
+        if ((sysp.pbc[0] || (ux >= 0 && ux < nc0)) && (sysp.pbc[1] || (uy >= 0 && uy < nc1)) &&
+            (sysp.pbc[2] || (uz >= 0 && uz < nc2))) {
+            int kx, ky, kz;
+            const int sx = wrap_cell(ux, nc0, kx);
+            const int sy = wrap_cell(uy, nc1, ky);
+            const int sz = wrap_cell(uz, nc2, kz);
+            const int cell = sysp.cell_off + kx + nc0 * (ky + nc1 * kz);
+            b0 = p.cell_start[cell];
+            cnt = p.cell_start[cell + 1] - b0;
+            code = (sx + 16) | ((sy + 16) << 5) | ((sz + 16) << 10);
+        }
+        seg_b0[t] = b0;
+        seg_cnt[t] = cnt;
+        seg_code[t] = (uint16_t)code;
+    }
+}
+
+__device__ __forceinline__ void cp_async16_nbr(void *smem, const void *gmem) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem));
 }
 
 __global__ void __launch_bounds__(CELL_WARPS * 32)
@@ -371,54 +409,38 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
     char4 *cand_sh = reinterpret_cast<char4 *>(cand + CAND_CAP);                       // [CAND_CAP]
     // hit words of the current 32 atoms, [atom][group] (row padded by one word)
     uint32_t(*bits)[CAND_CAP / 32 + 1] = reinterpret_cast<uint32_t(*)[CAND_CAP / 32 + 1]>(cand_sh + CAND_CAP);
-    // one segment per stencil cell: first atom in cell order, count, shift
-    // code, and position among the candidates
-    __shared__ int s_seg_b0[MAX_SEGS], s_seg_cnt[MAX_SEGS], s_seg_pos[MAX_SEGS];
-    __shared__ uint16_t s_seg_code[MAX_SEGS];
+    // stencil segments, double-buffered: the next cell's are looked up while
+    // this cell is processed; positions among the candidates for this cell
+    __shared__ int s_seg_b0[2][MAX_SEGS], s_seg_cnt[2][MAX_SEGS], s_seg_pos[MAX_SEGS];
+    __shared__ uint16_t s_seg_code[2][MAX_SEGS];
     __shared__ int s_total;
     __shared__ uint16_t s_list[CELL_WARPS][LIST_CAP];
+    __shared__ int s_cnt[32];
+    __shared__ int64_t s_off[32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+    int par = 0;
+    if (blockIdx.x < ncell) cell_lookup(p, blockIdx.x, cell_sys, s_seg_b0[0], s_seg_cnt[0], s_seg_code[0]);
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x, par ^= 1) {
+        __syncthreads();   // this cell's segments are in place; the previous cell is done
+        if (c + gridDim.x < ncell)
+            cell_lookup(p, c + gridDim.x, cell_sys, s_seg_b0[par ^ 1], s_seg_cnt[par ^ 1], s_seg_code[par ^ 1]);
         const int abeg = p.cell_start[c], na = p.cell_start[c + 1] - abeg;
         if (na == 0) continue;  // uniform across the block
         const SysParams &sysp = p.sp[cell_sys ? cell_sys[c] : 0];
-        const int nc0 = sysp.nc[0], nc1 = sysp.nc[1], nc2 = sysp.nc[2];
         const int w0 = 2 * sysp.R[0] + 1, w1 = 2 * sysp.R[1] + 1;
         const int nseg = w0 * w1 * (2 * sysp.R[2] + 1);
         if (nseg > MAX_SEGS) {  // wide stencil: per-atom pass
             for (int q = tid; q < na; q += blockDim.x) todo[atomicAdd(todo_count, 1ull)] = cell_atoms[abeg + q];
-            __syncthreads();
             continue;
         }
-        const int ci = (int)(c - sysp.cell_off);
-        const int cx = ci % nc0, cy = (ci / nc0) % nc1, cz = ci / (nc0 * nc1);
-        // stencil cells in (dz, dy, dx) order, all looked up at once
-        for (int t = tid; t < nseg; t += blockDim.x) {
-            const int tx = t % w0, tyz = t / w0;
-            const int ux = cx + tx - sysp.R[0], uy = cy + tyz % w1 - sysp.R[1], uz = cz + tyz / w1 - sysp.R[2];
-            int b0 = 0, cnt = 0, code = 0;
-            if ((sysp.pbc[0] || (ux >= 0 && ux < nc0)) && (sysp.pbc[1] || (uy >= 0 && uy < nc1)) &&
-                (sysp.pbc[2] || (uz >= 0 && uz < nc2))) {
-                int kx, ky, kz;
-                const int sx = wrap_cell(ux, nc0, kx);
-                const int sy = wrap_cell(uy, nc1, ky);
-                const int sz = wrap_cell(uz, nc2, kz);
-                const int cell = sysp.cell_off + kx + nc0 * (ky + nc1 * kz);
-                b0 = p.cell_start[cell];
-                cnt = p.cell_start[cell + 1] - b0;
-                code = (sx + 16) | ((sy + 16) << 5) | ((sz + 16) << 10);
-            }
-            s_seg_b0[t] = b0;
-            s_seg_cnt[t] = cnt;
-            s_seg_code[t] = (uint16_t)code;
-        }
-        __syncthreads();
+        const int *seg_b0 = s_seg_b0[par], *seg_cnt = s_seg_cnt[par];
+        const uint16_t *seg_code = s_seg_code[par];
         if (warp == 0) {  // exclusive scan of the segments' candidate counts
             int run = 0;
             for (int r0 = 0; r0 < nseg; r0 += 32) {
                 const int r = r0 + lane;
-                const int v = r < nseg ? s_seg_cnt[r] : 0;
+                const int v = r < nseg ? seg_cnt[r] : 0;
                 int x = v;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
@@ -434,22 +456,29 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
         const int total = s_total;
         if (total > CAND_CAP) {
             for (int q = tid; q < na; q += blockDim.x) todo[atomicAdd(todo_count, 1ull)] = cell_atoms[abeg + q];
-            __syncthreads();
             continue;
         }
-        // stage the stencil in candidate order (a warp per stencil cell):
-        // image-shifted FP32 positions (x, y, z, id | species << 28) and the
-        // table entry's shift (sx, sy, sz, species)
+        // stage the stencil in candidate order: every copy issued at once
+        // (cp.async), then each stencil cell's image shift applied in place:
+        // positions (x + sx Lx, y + sy Ly, z + sz Lz, id | species << 28) and
+        // the table entry's shift (sx, sy, sz, species)
         for (int t = warp; t < nseg; t += CELL_WARPS) {
-            const int cnt = s_seg_cnt[t];
+            const int cnt = seg_cnt[t], b0 = seg_b0[t], pos0 = s_seg_pos[t];
+            for (int q = lane; q < cnt; q += 32) cp_async16_nbr(&cand[pos0 + q], &p.cell_pos[b0 + q]);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_all;\n" ::);
+        __syncthreads();
+        for (int t = warp; t < nseg; t += CELL_WARPS) {
+            const int cnt = seg_cnt[t];
             if (cnt == 0) continue;
-            const int b0 = s_seg_b0[t], pos0 = s_seg_pos[t], code = s_seg_code[t];
+            const int pos0 = s_seg_pos[t], code = seg_code[t];
             const int sx = (code & 31) - 16, sy = ((code >> 5) & 31) - 16, sz = ((code >> 10) & 31) - 16;
             const float ox = small_int_to_float(sx) * sysp.Lh[0];
             const float oy = small_int_to_float(sy) * sysp.Lh[1];
             const float oz = small_int_to_float(sz) * sysp.Lh[2];
             for (int q = lane; q < cnt; q += 32) {
-                const float4 cp = p.cell_pos[b0 + q];
+                const float4 cp = cand[pos0 + q];
                 cand[pos0 + q] = make_float4(cp.x + ox, cp.y + oy, cp.z + oz, cp.w);
                 cand_sh[pos0 + q] = make_char4((signed char)sx, (signed char)sy, (signed char)sz,
                                                (signed char)((uint32_t)__float_as_int(cp.w) >> 28));
@@ -504,25 +533,49 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                 if (act) bits[ai - a0][gi] = in_bits;
             }
             __syncthreads();
-            // write-out: warp per atom, lane per candidate group (two groups a lane)
+            // write-out.  Counts first (warp per atom, lane per candidate group),
+            // then one reservation for the whole cell, then the entries.
             const int nact = min(32, na - a0);
             for (int aj = warp; aj < nact; aj += CELL_WARPS) {
-                const int i = cell_atoms[abeg + a0 + aj];
                 const uint32_t wd0 = lane < ngroup ? bits[aj][lane] : 0u;
                 const uint32_t wd1 = lane + 32 < ngroup ? bits[aj][lane + 32] : 0u;
                 const int count = __reduce_add_sync(0xffffffffu, __popc(wd0) + __popc(wd1));
-                if (count > TMD_MAX_DEGREE) {
+                if (lane == 0) s_cnt[aj] = count;
+            }
+            __syncthreads();
+            if (warp == 0) {   // exclusive scan of the counts and one atomicAdd for the cell
+                int c = lane < nact ? s_cnt[lane] : 0;
+                if (c > TMD_MAX_DEGREE) {
+                    atomicOr(p.status, DEV_ERR_DEGREE);
+                    c = 0;
+                    s_cnt[lane] = -1;
+                }
+                int x = c;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, d);
+                    if (lane >= d) x += y;
+                }
+                unsigned long long cb = 0;
+                if (lane == 31) cb = atomicAdd(p.counter, (unsigned long long)x);
+                cb = __shfl_sync(0xffffffffu, cb, 31);
+                if (lane < nact) s_off[lane] = (int64_t)cb + (x - c);
+            }
+            __syncthreads();
+            for (int aj = warp; aj < nact; aj += CELL_WARPS) {
+                const int i = cell_atoms[abeg + a0 + aj];
+                const int count = s_cnt[aj];
+                if (count < 0) {   // over the degree limit: empty segment, status set
                     if (lane == 0) {
-                        atomicOr(p.status, DEV_ERR_DEGREE);
                         p.beg[i] = 0;
                         p.end[i] = 0;
                     }
                     continue;
                 }
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(p.counter, (unsigned long long)count);
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if ((int64_t)base + count <= p.cap && count <= LIST_CAP) {
+                const int64_t base = s_off[aj];
+                const uint32_t wd0 = lane < ngroup ? bits[aj][lane] : 0u;
+                const uint32_t wd1 = lane + 32 < ngroup ? bits[aj][lane + 32] : 0u;
+                if (base + count <= p.cap && count <= LIST_CAP) {
                     // expand the words into the warp's list of candidate indices
                     // (lane per group, groups in order), then write the entries
                     // with consecutive lanes on consecutive entries
@@ -545,7 +598,7 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                         p.shift[base + k] = cand_sh[q];
                     }
                     __syncwarp();
-                } else if ((int64_t)base + count <= p.cap) {
+                } else if (base + count <= p.cap) {
                     // long lists: groups in order, lane k takes bit k
                     int off = 0;
                     for (int gi = 0; gi < ngroup; ++gi) {
@@ -553,16 +606,16 @@ __global__ void __launch_bounds__(CELL_WARPS * 32)
                         if (wd == 0u) continue;
                         if ((wd >> lane) & 1u) {
                             const int q = gi * 32 + lane;
-                            const int64_t e = (int64_t)base + off + __popc(wd & lt);
-                            p.nbr[e] = (int)((uint32_t)__float_as_int(cand[q].w) & 0x0FFFFFFFu);
-                            p.shift[e] = cand_sh[q];
+                            const int64_t ei = base + off + __popc(wd & lt);
+                            p.nbr[ei] = (int)((uint32_t)__float_as_int(cand[q].w) & 0x0FFFFFFFu);
+                            p.shift[ei] = cand_sh[q];
                         }
                         off += __popc(wd);
                     }
                 }
                 if (lane == 0) {
-                    p.beg[i] = (int64_t)base;
-                    p.end[i] = (int64_t)base + count;
+                    p.beg[i] = base;
+                    p.end[i] = base + count;
                 }
             }
             __syncthreads();
