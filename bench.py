@@ -53,6 +53,20 @@ def mlp_flops_per_atom(dims):
     return 4 * sum(dims[i] * dims[i + 1] for i in range(len(dims) - 1))
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (times are reported as the max over ranks)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, atoms_per_rank, steps, seconds):
+    """Whole-job atom-steps/s of `world` independent replicas (weak scaling)."""
+    return world * atoms_per_rank * steps / seconds
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -430,12 +444,8 @@ def main():
     launches = tmd.launch_count() - launches0
     tmd.profile_enable(False)
     kstats = tmd.profile_read(reset=True)
-    elapsed_ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = world * n * args.steps / (elapsed_ms * 1e-3)
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    value = replica_throughput(world, n, args.steps, elapsed_ms * 1e-3)
 
     # the BF16-network form of the same step (same state, same timing rules)
     other = "bf16" if args.precision == "fp32" else "fp32"
@@ -451,12 +461,10 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    t_other = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_other, op=dist.ReduceOp.MAX)
+    t_other = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     forms = {args.precision: {"value": value, "ms_per_step": elapsed_ms / args.steps},
-             other: {"value": world * n * args.steps / (float(t_other.item()) * 1e-3),
-                     "ms_per_step": float(t_other.item()) / args.steps}}
+             other: {"value": replica_throughput(world, n, args.steps, t_other * 1e-3),
+                     "ms_per_step": t_other / args.steps}}
     model.set_precision(args.precision)
 
     # end to end through the host-buffer C-ABI call (pinned host state)
@@ -477,12 +485,8 @@ def main():
         for _ in range(args.steps):
             sysm.step_host(model, pos_h, vel_h, f_h, w.dt_fs, 1, rebuild_every=1)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-        e2e = {"value": world * n * args.steps / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": replica_throughput(world, n, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(n * (24 + 24 + 12)), "d2h_bytes_per_step": int(n * (24 + 24 + 12))}
 
     if rank != 0:
