@@ -428,16 +428,19 @@ __device__ __forceinline__ float act_da(int act, float a, float b) {
 // tile holds one species except at species boundaries).  Activations stay in
 // shared memory transposed, [unit][atom] with row stride TR + 4, so a thread
 // reads the 4 atoms of its row block for one unit with one vector load.  The
-// weights are streamed through two shared-memory buffers in chunks of MLP_KC
+// weights are streamed through two shared-memory buffers in chunks of KC
 // input rows by at most MLP_NP output columns: while the block multiplies with
 // one chunk, cp.async brings in the next chunk of the tile's fixed sequence of
 // products (forward layers, then the backward chain).  Every thread
 // accumulates a 4 x 4 block of outputs per item (one or two items per pass),
-// summing each chunk of MLP_KC products separately before adding it to the
-// running total: the rounding error grows with MLP_KC + Kin / MLP_KC instead
-// of Kin, which halves the error of G' for the 192-128-128 networks.
+// summing each group of 16 products separately before adding it to the
+// running total: the rounding error grows with 16 + Kin / 16 instead of Kin,
+// which halves the error of G' for the 192-128-128 networks.
 // ---------------------------------------------------------------------------
-constexpr int MLP_KC = 16;     // streamed weight rows per chunk
+// streamed weight rows per chunk: 16 for 64-atom tiles, 32 for 32-atom tiles
+// (whose activations leave the room)
+template <int TR>
+__host__ __device__ constexpr int mlp_kc() { return TR == 32 ? 32 : 16; }
 constexpr int MLP_NP = 128;    // output columns per pass
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -462,8 +465,9 @@ __device__ __forceinline__ MlpStep mlp_step(const DevModel &m, int s, int step) 
 }
 
 // Issue the copy of chunk (n0, k0) of product st into buf (all threads).
+template <int KC>
 __device__ __forceinline__ void mlp_issue(const MlpStep &st, int n0, int k0, float *buf) {
-    const int np = min(MLP_NP, st.N - n0), ncb = np >> 2, kc = min(MLP_KC, st.Kin - k0);
+    const int np = min(MLP_NP, st.N - n0), ncb = np >> 2, kc = min(KC, st.Kin - k0);
     if (np == st.N) {   // one contiguous block of W
         const float *src = st.W + (size_t)k0 * st.N;
         for (int idx = threadIdx.x; idx < kc * ncb; idx += MLP_THREADS) cp_async16(buf + 4 * idx, src + 4 * idx);
@@ -484,9 +488,10 @@ struct MlpStream {
 // Advance to the chunk after (n0, k0) of the current product (possibly the
 // first chunk of the next product or species) and issue it; always commits a
 // group so that wait_group 1 leaves exactly the current chunk pending.
+template <int KC>
 __device__ __forceinline__ void mlp_prefetch_next(const DevModel &m, const MlpStream &cur, const MlpStep &st,
                                                   float *wbuf) {
-    int s = cur.s, step = cur.step, n0 = cur.n0, k0 = cur.k0 + MLP_KC;
+    int s = cur.s, step = cur.step, n0 = cur.n0, k0 = cur.k0 + KC;
     if (k0 >= st.Kin) {
         k0 = 0;
         n0 += MLP_NP;
@@ -497,7 +502,7 @@ __device__ __forceinline__ void mlp_prefetch_next(const DevModel &m, const MlpSt
     }
     if (s <= cur.s_hi) {
         const MlpStep nx = (step == cur.step && s == cur.s) ? st : mlp_step(m, s, step);
-        mlp_issue(nx, n0, k0, wbuf + (cur.par ^ 1) * (MLP_KC * MLP_NP));
+        mlp_issue<KC>(nx, n0, k0, wbuf + (cur.par ^ 1) * (KC * MLP_NP));
     }
     cp_async_commit();
 }
@@ -512,6 +517,7 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
                                          float *__restrict__ gout, const int *s_atom, const int *s_type) {
     constexpr int LDT = TR + 4;
     constexpr int NRB = TR / 4;    // row blocks
+    constexpr int KC = mlp_kc<TR>();
     const int tid = threadIdx.x;
     const MlpStep st = mlp_step(m, ws.s, ws.step);
     const int N = st.N;
@@ -534,41 +540,47 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int o = 0; o < 4; ++o) acc[ii][i][o] = 0.f;
-        for (int k0 = 0; k0 < st.Kin; k0 += MLP_KC) {
-            const int kc = min(MLP_KC, st.Kin - k0);
+        for (int k0 = 0; k0 < st.Kin; k0 += KC) {
+            const int kc = min(KC, st.Kin - k0);
             ws.n0 = n0;
             ws.k0 = k0;
-            mlp_prefetch_next(m, ws, st, wbuf);
+            mlp_prefetch_next<KC>(m, ws, st, wbuf);
             cp_async_wait1();
             __syncthreads();   // this chunk has landed for every thread; At is complete
-            const float *w = wbuf + ws.par * (MLP_KC * MLP_NP);
+            const float *w = wbuf + ws.par * (KC * MLP_NP);
 #pragma unroll
             for (int ii = 0; ii < 2; ++ii) {
                 if (tid + ii * MLP_THREADS < items) {
                     const float *a = At + (size_t)k0 * LDT + rb[ii] * 4;
                     const float *b = w + cb[ii] * 4;
-                    float pp[4][4];   // this chunk's sums, added to acc once (two-level summation)
+                    // groups of 16 products summed separately, then added to acc
+                    // (two-level summation; the same grouping for every KC, so
+                    // the result does not depend on the tile shape)
+                    for (int kg = 0; kg < kc; kg += 16) {
+                        float pp[4][4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                        for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int o = 0; o < 4; ++o) pp[i][o] = 0.f;
+                            for (int o = 0; o < 4; ++o) pp[i][o] = 0.f;
+                        const int ke = min(kg + 16, kc);
 #pragma unroll 8
-                    for (int k = 0; k < kc; ++k) {
-                        const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
-                        const float4 bv = *reinterpret_cast<const float4 *>(b + k * np);
-                        const float ai[4] = {av.x, av.y, av.z, av.w};
+                        for (int k = kg; k < ke; ++k) {
+                            const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
+                            const float4 bv = *reinterpret_cast<const float4 *>(b + k * np);
+                            const float ai[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            pp[i][0] = fmaf(ai[i], bv.x, pp[i][0]);
-                            pp[i][1] = fmaf(ai[i], bv.y, pp[i][1]);
-                            pp[i][2] = fmaf(ai[i], bv.z, pp[i][2]);
-                            pp[i][3] = fmaf(ai[i], bv.w, pp[i][3]);
+                            for (int i = 0; i < 4; ++i) {
+                                pp[i][0] = fmaf(ai[i], bv.x, pp[i][0]);
+                                pp[i][1] = fmaf(ai[i], bv.y, pp[i][1]);
+                                pp[i][2] = fmaf(ai[i], bv.z, pp[i][2]);
+                                pp[i][3] = fmaf(ai[i], bv.w, pp[i][3]);
+                            }
                         }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int o = 0; o < 4; ++o) acc[ii][i][o] += pp[i][o];
                     }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int o = 0; o < 4; ++o) acc[ii][i][o] += pp[i][o];
                 }
             }
             __syncthreads();   // every thread is done with this buffer
@@ -613,7 +625,7 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
 }
 
 template <int TR>
-__global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_t *__restrict__ perm,
+__global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 3 : 2) k_mlp(DevModel m, const int32_t *__restrict__ perm,
                                                         const int32_t *__restrict__ types, int64_t n,
                                                         const float *__restrict__ G, float *__restrict__ dG,
                                                         float *__restrict__ e_atom, double *__restrict__ part_e) {
@@ -627,7 +639,8 @@ __global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_
     // shared layout: two weight buffers, then act[l] = [dims[l]][LDT] for l = 0..L
     float *wbuf = sm;
     float *act[MAX_LAYERS + 1];
-    float *ptr = sm + 2 * MLP_KC * MLP_NP;
+    constexpr int KC = mlp_kc<TR>();
+    float *ptr = sm + 2 * KC * MLP_NP;
     for (int l = 0; l <= L; ++l) {
         act[l] = ptr;
         ptr += (size_t)m.dims[l] * LDT;
@@ -644,7 +657,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 3) k_mlp(DevModel m, const int32_
     for (int r = 0; r < TR; ++r)
         if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
     MlpStream ws{s_lo, s_hi, 0, 0, 0, 0};
-    if (s_lo <= s_hi) mlp_issue(mlp_step(m, s_lo, 0), 0, 0, wbuf);   // first chunk, under the G loads
+    if (s_lo <= s_hi) mlp_issue<KC>(mlp_step(m, s_lo, 0), 0, 0, wbuf);   // first chunk, under the G loads
     cp_async_commit();
     // G rows -> act[0] transposed (lane per atom row: conflict-free stores)
     for (int r = lane; r < TR; r += 32) {
@@ -1332,7 +1345,7 @@ size_t mlp_bf16_smem_bytes(const DevModel &dm) {
 static size_t mlp_smem_tr(const DevModel &dm, int tr) {
     size_t fl = 0;
     for (int l = 0; l <= dm.L; ++l) fl += (size_t)dm.dims[l] * (tr + 4);
-    fl += (size_t)2 * MLP_KC * MLP_NP;
+    fl += (size_t)2 * (tr == 32 ? 32 : 16) * MLP_NP;   // two weight chunks (mlp_kc)
     return fl * sizeof(float);
 }
 
