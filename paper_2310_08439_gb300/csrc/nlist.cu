@@ -10,10 +10,13 @@
 // rounding band around r_list^2 are decided in FP64 with the exact
 // expression ((x_j + s L) - x_i), (dx^2 + dy^2) + dz^2, no FMA, which makes the
 // table bit-identical to the plain definition.  The table is built in one
-// pass: each warp buffers its atom's entries in shared memory, reserves room
-// with one atomicAdd on a global counter and writes a contiguous segment
-// [beg[i], end[i]).  Atom ids are sorted inside every cell first, so the entry
-// order of each atom (stencil order, ascending id within a cell) is
+// pass: k_nbr_cell stages a cell's whole stencil in shared memory and screens
+// it for all the cell's atoms at once (lane = atom, candidates broadcast, one
+// hit bit per candidate), reserves room for the cell's atoms with one
+// atomicAdd on a global counter and writes each atom's contiguous segment
+// [beg[i], end[i]); atoms of cells whose stencil does not fit take the
+// per-atom pass k_nbr.  Atom ids are sorted inside every cell first, so the
+// entry order of each atom (stencil order, ascending id within a cell) is
 // deterministic.
 #include <cmath>
 #include <cstring>

@@ -4,18 +4,21 @@
 //   k_desc   setup (D, R, Dhat), H_abck = f_k f_c, M_abcd, P_abkd = sum_c H M,
 //            G_abkm = sigma(T_dm P^2)            -- Eqs. tensor_formalism, sigma_function
 //   k_mlp    E_a = NNP(G_a) and G' = dE_a/dG_a    -- the E_a / NNP equations
-//   k_force  P' = 2 T sigma' P G', U = P' M, V = P' H, F1 = U H' R', F2 = V M'
-//            with M' formed on the fly, ScatterSum into forces, virial
+//            (k_mlp_bf16: the same chain on BF16 tensor cores)
+//   k_force  P' = 2 T sigma' P G'; V = P' H and W = P' H' (so that
+//            F1 = U H' R' = W . M and F2 = V M' with M' formed on the fly);
+//            ScatterSum into forces, virial
 //                                                 -- Eqs. dP_abkd, U_abck, F1_abcx, F2_abcx
-//   k_reduce FP64 energy and virial totals, k_forces_out float4 -> [n][3].
+//   k_reduce FP64 energy and virial totals, k_forces_out int64 -> [n][3] FP32.
 //
-// One warp owns one centre atom.  Neighbour entries beyond rc are dropped and
-// the survivors are compacted through a per-warp shared-memory queue, so every
-// lane works on an in-cutoff pair.  In k_desc each lane computes H and M for
-// one neighbour and stages them in shared memory; the warp then accumulates the
-// per-atom P[b][k][d] outer products with each lane owning a (K/8 x 5) block of
-// P in registers.  In k_force each lane owns one neighbour and reads the atom's
-// P' from shared memory with broadcast loads.
+// One warp owns one centre atom.  In k_desc, neighbour entries beyond rc are
+// dropped and the survivors are compacted through a per-warp shared-memory
+// queue (and into the pair cache, from which k_force reads them back), so
+// every lane works on an in-cutoff pair.  Each lane computes H and M for one
+// neighbour and stages them in shared memory; the warp then accumulates the
+// per-atom P[b][k][d] outer products with each lane owning a (K/8 x 5) block
+// of P in registers.  In k_force each lane owns one cached pair and reads the
+// atom's P' from shared memory with broadcast loads.
 #include <cuda_bf16.h>
 
 #include <algorithm>

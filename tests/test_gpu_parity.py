@@ -73,7 +73,7 @@ def assert_parity(g, o, label=""):
 
 
 # ------------------------------------------------------------------ neighbour table
-@pytest.mark.parametrize("case", ["tiny", "tiny_skin", "selfimage", "open", "mixed", "medium", "dense"])
+@pytest.mark.parametrize("case", ["tiny", "tiny_skin", "selfimage", "open", "mixed", "medium", "dense", "wide"])
 def test_neighbor_table_bit_exact(tmdlib, case):
     rng = np.random.default_rng(11)
     if case in ("tiny", "tiny_skin"):
@@ -93,11 +93,17 @@ def test_neighbor_table_bit_exact(tmdlib, case):
                      box, np.array([1, 1, 0], np.int32))
         r = 6.0
     elif case == "dense":
-        # stencils of > 2048 candidates: the cell-cooperative pass hands these
+        # stencils of > 1,920 candidates: the cell-cooperative pass hands these
         # atoms to the per-atom pass
         pos, box = I.lattice("fcc", (9, 9, 9), 2.9)
         s = I.System(I.jitter_and_wrap(pos, box, 0.05, rng), np.zeros(len(pos), np.int32), box, np.ones(3, np.int32))
         r = 8.5
+    elif case == "wide":
+        # a 2.9 A box with a 7 A list radius: stencils of 7^3 cells (images up
+        # to 3 boxes away) go to the per-atom pass as well
+        pos, box = I.lattice("bcc", (1, 1, 1), 2.9)
+        s = I.System(I.jitter_and_wrap(pos, box, 0.05, rng), np.zeros(len(pos), np.int32), box, np.ones(3, np.int32))
+        r = 7.0
     else:
         s = I.medium().systems[0]
         r = 7.0
