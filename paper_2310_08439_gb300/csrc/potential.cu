@@ -1002,6 +1002,241 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
+// g_ij = dE/dD_ij of one in-cutoff pair (Eqs. dP_abkd, U_abck, F1_abcx,
+// F2_abcx): Pb = the centre atom's P' for the neighbour's species, rad = the
+// radial parameters of the (centre, neighbour) species pair.
+template <int K>
+__device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, const float2 e2, const float *Pb,
+                                          const float4 *rad, float &gxs, float &gys, float &gzs) {
+    float r_hi, r_lo, ir;
+    split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
+    const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
+    // V_d = sum_k P'_kd H_k and W_d = sum_k P'_kd H'_k, so that
+    // F1 = U H' R' = sum_d W_d M_d and F2 = V M'
+    float V[NMOM], Wd[NMOM];
+#pragma unroll
+    for (int d = 0; d < NMOM; ++d) V[d] = Wd[d] = 0.f;
+    float fc, dfc;
+    cutoff_fn(r_hi, m.inv_rc, fc, dfc);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        // H_k and H'_k formed inside the loop (no per-pair arrays)
+        const float4 rp = rad[k];
+        const float t = (r_hi - rp.x) + (r_lo - rp.y);
+        const float f = ex2_ftz(-rp.z * t * t);
+        const float Hk = f * fc;
+        const float dHk = f * fmaf(-rp.w * t, fc, dfc);
+#pragma unroll
+        for (int q4 = 0; q4 < NMOM / 4; ++q4) {
+            const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
+            V[4 * q4] = fmaf(pd.x, Hk, V[4 * q4]);
+            V[4 * q4 + 1] = fmaf(pd.y, Hk, V[4 * q4 + 1]);
+            V[4 * q4 + 2] = fmaf(pd.z, Hk, V[4 * q4 + 2]);
+            V[4 * q4 + 3] = fmaf(pd.w, Hk, V[4 * q4 + 3]);
+            Wd[4 * q4] = fmaf(pd.x, dHk, Wd[4 * q4]);
+            Wd[4 * q4 + 1] = fmaf(pd.y, dHk, Wd[4 * q4 + 1]);
+            Wd[4 * q4 + 2] = fmaf(pd.z, dHk, Wd[4 * q4 + 2]);
+            Wd[4 * q4 + 3] = fmaf(pd.w, dHk, Wd[4 * q4 + 3]);
+        }
+    }
+    float M[NMOM];
+    moments20(ux, uy, uz, M);
+    float w0 = Wd[0], w1 = 0.f, w2 = 0.f, w3 = 0.f;
+#pragma unroll
+    for (int d = 1; d < NMOM; d += 4) {
+        w1 = fmaf(Wd[d], M[d], w1);
+        w2 = fmaf(Wd[d + 1], M[d + 1], w2);
+        w3 = fmaf(Wd[d + 2], M[d + 2], w3);
+        if (d + 3 < NMOM) w0 = fmaf(Wd[d + 3], M[d + 3], w0);
+    }
+    const float dEdr = (w0 + w1) + (w2 + w3);
+    // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
+    const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
+    const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
+                     2.f * xy * V[11] + 2.f * xz * V[12] + yy * V[13] + yz * V[14] + zz * V[15];
+    const float gy = V[2] + ux * V[5] + 2.f * uy * V[7] + uz * V[8] + xx * V[11] + 2.f * xy * V[13] +
+                     xz * V[14] + 3.f * yy * V[16] + 2.f * yz * V[17] + zz * V[18];
+    const float gz = V[3] + ux * V[6] + uy * V[8] + 2.f * uz * V[9] + xx * V[12] + xy * V[14] +
+                     2.f * xz * V[15] + yy * V[17] + 2.f * yz * V[18] + 3.f * zz * V[19];
+    const float ug = ux * gx + uy * gy + uz * gz;
+    // g_ij = dE/dD_ij = dE/dr u + (I - u u^T) dE/du / r
+    gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
+    gys = fmaf(dEdr, uy, (gy - uy * ug) * ir);
+    gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
+}
+
+// P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm (for m = 0: G'_bk0 sign(P)) of atom a
+// into a shared slot, each lane its (K/8 x 5) block  (Eq. dP_abkd)
+template <int K, int S>
+__device__ __forceinline__ void pprime_setup(const float *__restrict__ Pin, const float *__restrict__ dG, int a,
+                                             float *slot, int kg, int g, const float (&Tg)[5]) {
+    constexpr int KPL = K / 8;
+    constexpr int PSTR = K * NMOM + 4;
+    constexpr int Dd = S * K * 4;
+    const float *Pa = Pin + (size_t)a * (S * K * NMOM);
+    const float *dGa = dG + (size_t)a * Dd;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int kk = 0; kk < KPL; ++kk) {
+            const int k = kg * KPL + kk;
+            const float4 gm = *reinterpret_cast<const float4 *>(dGa + (s * K + k) * 4);
+#pragma unroll
+            for (int dd = 0; dd < 5; ++dd) {
+                const int d = 5 * g + dd;
+                const float pv = Pa[(s * K + k) * NMOM + d];
+                float gg;
+                if (g == 0) gg = (dd == 0) ? gm.x : ((dd < 4) ? gm.y : gm.z);
+                else gg = (g == 1) ? gm.z : gm.w;
+                float v;
+                if (g == 0 && dd == 0) v = (pv > 0.f) ? gg : ((pv < 0.f) ? -gg : 0.f);
+                else v = 2.f * Tg[dd] * pv * gg;
+                slot[s * PSTR + k * NMOM + d] = v;
+            }
+        }
+}
+
+// Force pass over the pair cache with full lane batches: each warp walks a
+// contiguous run of atoms (perm order) and fills every batch of 32 lanes with
+// the rest of the current atom's pairs followed by the first pairs of the
+// next atom (two P' slots per warp, two self-force accumulators).
+template <int K, int S>
+__global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlist nl, const int32_t *__restrict__ types,
+                                                          const float *__restrict__ Pin, const float *__restrict__ dG,
+                                                          unsigned long long *__restrict__ Fq,
+                                                          double *__restrict__ part_w) {
+    constexpr int PSTR = K * NMOM + 4;
+    __shared__ float4 s_rad[S * S * K];
+    __shared__ __align__(16) float s_Pd[PW][2][S * PSTR];
+    __shared__ double s_w[PW][9];
+    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = lane >> 2, g = lane & 3;
+    float Tg[5];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
+    float wsum[9], wcmp[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) { wsum[t] = 0.f; wcmp[t] = 0.f; }
+    const int64_t nw = (int64_t)gridDim.x * PW, wid = (int64_t)blockIdx.x * PW + warp;
+    const int64_t chunk = (nl.n + nw - 1) / nw;
+    int64_t p = wid * chunk;
+    const int64_t pend = min(nl.n, p + chunk);
+    if (p < pend) {
+        int slot = 0;
+        int a = nl.perm[p], ta = types[a];
+        pprime_setup<K, S>(Pin, dG, a, s_Pd[warp][0], kg, g, Tg);
+        int64_t cb = nl.beg[a];
+        int cr = nl.npair[a];
+        long long fcx = 0, fcy = 0, fcz = 0;
+        while (p < pend) {
+            const int take_c = min(cr, 32);
+            const bool has_n = cr < 32 && p + 1 < pend;
+            int take_n = 0, an = 0, tn = 0, nr = 0;
+            int64_t nb = 0;
+            if (has_n) {   // bring in the next atom
+                an = nl.perm[p + 1];
+                tn = types[an];
+                pprime_setup<K, S>(Pin, dG, an, s_Pd[warp][slot ^ 1], kg, g, Tg);
+                nb = nl.beg[an];
+                nr = nl.npair[an];
+                take_n = min(nr, 32 - cr);
+            }
+            __syncwarp();
+            long long fnx = 0, fny = 0, fnz = 0;
+            float wa[9];   // this lane's pair of this batch
+#pragma unroll
+            for (int t = 0; t < 9; ++t) wa[t] = 0.f;
+            const bool isc = lane < take_c, isn = !isc && lane < take_c + take_n;
+            if (isc || isn) {
+                const int64_t c = isc ? cb + lane : nb + (lane - take_c);
+                const float4 e = nl.pq[c];
+                const float2 e2 = nl.pq2[c];
+                const uint32_t jb = __float_as_uint(e.w);
+                const int b = (int)(jb >> 28);
+                const int j = (int)(jb & 0x0FFFFFFFu);
+                const float *Pb = s_Pd[warp][isc ? slot : slot ^ 1] + b * PSTR;
+                const float4 *rad = &s_rad[((isc ? ta : tn) * S + b) * K];
+                float gxs, gys, gzs;
+                pair_grad<K>(m, e, e2, Pb, rad, gxs, gys, gzs);
+                // ScatterSum in 2^-32 fixed point (exact, order independent)
+                const long long qx = to_fixed(gxs);
+                const long long qy = to_fixed(gys);
+                const long long qz = to_fixed(gzs);
+                if (isc) { fcx += qx; fcy += qy; fcz += qz; }
+                else { fnx = qx; fny = qy; fnz = qz; }
+                atomicAdd(&Fq[3 * (int64_t)j], (unsigned long long)(-qx));
+                atomicAdd(&Fq[3 * (int64_t)j + 1], (unsigned long long)(-qy));
+                atomicAdd(&Fq[3 * (int64_t)j + 2], (unsigned long long)(-qz));
+                const float D[3] = {e.x, e.y, e.z};
+                const float gv[3] = {gxs, gys, gzs};
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) wa[al * 3 + be] = -D[al] * gv[be];
+            }
+#pragma unroll
+            for (int t = 0; t < 9; ++t) kahan_add(wsum[t], wcmp[t], wa[t]);
+            cb += take_c;
+            cr -= take_c;
+            if (cr == 0) {   // the current atom is complete: its own force
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    fcx += __shfl_xor_sync(0xffffffffu, fcx, o);
+                    fcy += __shfl_xor_sync(0xffffffffu, fcy, o);
+                    fcz += __shfl_xor_sync(0xffffffffu, fcz, o);
+                }
+                if (lane == 0) {
+                    atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fcx);
+                    atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fcy);
+                    atomicAdd(&Fq[3 * (int64_t)a + 2], (unsigned long long)fcz);
+                }
+                ++p;
+                if (p < pend) {
+                    if (has_n) {   // the next atom (already set up) becomes the current one
+                        a = an;
+                        ta = tn;
+                        slot ^= 1;
+                        cb = nb + take_n;
+                        cr = nr - take_n;
+                        fcx = fnx; fcy = fny; fcz = fnz;
+                    } else {
+                        __syncwarp();
+                        a = nl.perm[p];
+                        ta = types[a];
+                        pprime_setup<K, S>(Pin, dG, a, s_Pd[warp][slot], kg, g, Tg);
+                        cb = nl.beg[a];
+                        cr = nl.npair[a];
+                        fcx = fcy = fcz = 0;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // virial: per-lane compensated sums -> warp total as an FP32 double-float -> FP64 block total
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        float hi = wsum[t], lo = -wcmp[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float sh, se;
+            two_sum(hi, oh, sh, se);
+            lo = (lo + ol) + se;
+            two_sum(sh, lo, hi, lo);
+        }
+        if (lane == 0) s_w[warp][t] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double v = 0.0;
+        for (int w = 0; w < PW; ++w) v += s_w[w][threadIdx.x];
+        part_w[(size_t)blockIdx.x * 9 + threadIdx.x] = v;
+    }
+}
+
 // PAW (batched): each atom's virial is summed over its own pairs and written
 // to w_atom [atoms][9] for per-system reductions; otherwise lanes keep
 // compensated running sums and each block writes one FP64 partial.
@@ -1064,66 +1299,11 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
         for (int t = 0; t < 9; ++t) wa[t] = 0.f;
         auto pair_fn = [&](const float4 e, const float2 e2, bool valid, int) {
                       if (!valid) return;
-                      float r_hi, r_lo, ir;
-                      split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
-                      const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
                       const uint32_t jb = __float_as_uint(e.w);
                       const int b = (int)(jb >> 28);
                       const int j = (int)(jb & 0x0FFFFFFFu);
-                      // V_d = sum_k P'_kd H_k and W_d = sum_k P'_kd H'_k, so that
-                      // F1 = U H' R' = sum_d W_d M_d and F2 = V M'
-                      float V[NMOM], Wd[NMOM];
-#pragma unroll
-                      for (int d = 0; d < NMOM; ++d) V[d] = Wd[d] = 0.f;
-                      const float *Pb = sPd + b * PSTR;
-                      const float4 *rad = &s_rad[(ti * S + b) * K];
-                      float fc, dfc;
-                      cutoff_fn(r_hi, m.inv_rc, fc, dfc);
-#pragma unroll
-                      for (int k = 0; k < K; ++k) {
-                          // H_k and H'_k formed inside the loop (no per-pair arrays)
-                          const float4 rp = rad[k];
-                          const float t = (r_hi - rp.x) + (r_lo - rp.y);
-                          const float f = ex2_ftz(-rp.z * t * t);
-                          const float Hk = f * fc;
-                          const float dHk = f * fmaf(-rp.w * t, fc, dfc);
-#pragma unroll
-                          for (int q4 = 0; q4 < NMOM / 4; ++q4) {
-                              const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
-                              V[4 * q4] = fmaf(pd.x, Hk, V[4 * q4]);
-                              V[4 * q4 + 1] = fmaf(pd.y, Hk, V[4 * q4 + 1]);
-                              V[4 * q4 + 2] = fmaf(pd.z, Hk, V[4 * q4 + 2]);
-                              V[4 * q4 + 3] = fmaf(pd.w, Hk, V[4 * q4 + 3]);
-                              Wd[4 * q4] = fmaf(pd.x, dHk, Wd[4 * q4]);
-                              Wd[4 * q4 + 1] = fmaf(pd.y, dHk, Wd[4 * q4 + 1]);
-                              Wd[4 * q4 + 2] = fmaf(pd.z, dHk, Wd[4 * q4 + 2]);
-                              Wd[4 * q4 + 3] = fmaf(pd.w, dHk, Wd[4 * q4 + 3]);
-                          }
-                      }
-                      float M[NMOM];
-                      moments20(ux, uy, uz, M);
-                      float w0 = Wd[0], w1 = 0.f, w2 = 0.f, w3 = 0.f;
-#pragma unroll
-                      for (int d = 1; d < NMOM; d += 4) {
-                          w1 = fmaf(Wd[d], M[d], w1);
-                          w2 = fmaf(Wd[d + 1], M[d + 1], w2);
-                          w3 = fmaf(Wd[d + 2], M[d + 2], w3);
-                          if (d + 3 < NMOM) w0 = fmaf(Wd[d + 3], M[d + 3], w0);
-                      }
-                      const float dEdr = (w0 + w1) + (w2 + w3);
-                      // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
-                      const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
-                      const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
-                                       2.f * xy * V[11] + 2.f * xz * V[12] + yy * V[13] + yz * V[14] + zz * V[15];
-                      const float gy = V[2] + ux * V[5] + 2.f * uy * V[7] + uz * V[8] + xx * V[11] + 2.f * xy * V[13] +
-                                       xz * V[14] + 3.f * yy * V[16] + 2.f * yz * V[17] + zz * V[18];
-                      const float gz = V[3] + ux * V[6] + uy * V[8] + 2.f * uz * V[9] + xx * V[12] + xy * V[14] +
-                                       2.f * xz * V[15] + yy * V[17] + 2.f * yz * V[18] + 3.f * zz * V[19];
-                      const float ug = ux * gx + uy * gy + uz * gz;
-                      // g_ij = dE/dD_ij = dE/dr u + (I - u u^T) dE/du / r
-                      const float gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
-                      const float gys = fmaf(dEdr, uy, (gy - uy * ug) * ir);
-                      const float gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
+                      float gxs, gys, gzs;
+                      pair_grad<K>(m, e, e2, sPd + b * PSTR, &s_rad[(ti * S + b) * K], gxs, gys, gzs);
                       // ScatterSum in 2^-32 fixed point: integer adds are exact and
                       // order independent, so forces are bitwise reproducible.
                       const long long qx = to_fixed(gxs);
@@ -1281,8 +1461,8 @@ tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const dou
         TMD_LAUNCH("k_force", s, k_force<K, S, true, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
                                                                                   nl->Fq, part_w, w_atom));
     else if (dn.pq)
-        TMD_LAUNCH("k_force", s, k_force<K, S, false, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
-                                                                                   nl->Fq, part_w, nullptr));
+        TMD_LAUNCH("k_force", s, k_force_merged<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, types, nl->P, nl->dG, nl->Fq,
+                                                                             part_w));
     else
         TMD_LAUNCH("k_force", s, k_force<K, S, false, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
                                                                                     nl->Fq, part_w, nullptr));
