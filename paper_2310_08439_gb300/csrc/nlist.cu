@@ -79,31 +79,57 @@ __global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict_
 
 // exclusive scan of the per-block species counts (one warp per species);
 // writes the species start offsets type_start[0..MAX_SPECIES].
-__global__ void k_type_scan(int32_t *__restrict__ type_block, int nblocks, int32_t *__restrict__ type_start) {
-    __shared__ int32_t s_tot[TMD_MAX_SPECIES];
-    const int s = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int32_t run = 0;
-    for (int b0 = 0; b0 < nblocks; b0 += 32) {
-        const int b = b0 + lane;
-        const int32_t v = b < nblocks ? type_block[b * TMD_MAX_SPECIES + s] : 0;
-        int32_t x = v;
+__global__ void __launch_bounds__(128) k_type_scan(int32_t *__restrict__ type_block, int nblocks,
+                                                  int32_t *__restrict__ type_start) {
+    // exclusive scan over the binning blocks, every species at once: thread t
+    // owns a contiguous run of blocks (sums it, block-wide scan of the run
+    // totals, then writes its run's offsets)
+    static_assert(TMD_MAX_SPECIES == 4, "one int4 per block");
+    __shared__ int4 s_tot[128];
+    const int t = threadIdx.x;
+    const int per = (nblocks + 127) / 128;
+    const int b0 = min(nblocks, t * per), b1 = min(nblocks, b0 + per);
+    int4 *tb = reinterpret_cast<int4 *>(type_block);
+    int4 sum = make_int4(0, 0, 0, 0);
+    for (int b = b0; b < b1; ++b) {
+        const int4 v = tb[b];
+        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+    }
+    s_tot[t] = sum;
+    __syncthreads();
+    if (t < 32) {   // scan of the 128 run totals: 4 per lane, then across lanes
+        int4 r[4], acc = make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            r[q] = acc;
+            const int4 v = s_tot[4 * t + q];
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+        }
+        int4 x = acc;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
+            const int yx = __shfl_up_sync(0xffffffffu, x.x, d), yy = __shfl_up_sync(0xffffffffu, x.y, d);
+            const int yz = __shfl_up_sync(0xffffffffu, x.z, d), yw = __shfl_up_sync(0xffffffffu, x.w, d);
+            if (t >= d) { x.x += yx; x.y += yy; x.z += yz; x.w += yw; }
         }
-        if (b < nblocks) type_block[b * TMD_MAX_SPECIES + s] = run + x - v;
-        run += __shfl_sync(0xffffffffu, x, 31);
+        const int4 ex = make_int4(x.x - acc.x, x.y - acc.y, x.z - acc.z, x.w - acc.w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            s_tot[4 * t + q] = make_int4(ex.x + r[q].x, ex.y + r[q].y, ex.z + r[q].z, ex.w + r[q].w);
+        if (t == 31) {
+            type_start[0] = 0;
+            type_start[1] = x.x;
+            type_start[2] = x.x + x.y;
+            type_start[3] = x.x + x.y + x.z;
+            type_start[4] = x.x + x.y + x.z + x.w;
+        }
     }
-    if (lane == 0) s_tot[s] = run;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t acc = 0;
-        for (int t = 0; t < TMD_MAX_SPECIES; ++t) {
-            type_start[t] = acc;
-            acc += s_tot[t];
-        }
-        type_start[TMD_MAX_SPECIES] = acc;
+    int4 run = s_tot[t];
+    for (int b = b0; b < b1; ++b) {
+        const int4 v = tb[b];
+        tb[b] = run;
+        run.x += v.x; run.y += v.y; run.z += v.z; run.w += v.w;
     }
 }
 
@@ -841,7 +867,7 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
         TMD_CUDA(cudaGetLastError());
         if ((st = scan_inclusive<int32_t>(nl->cell_start + 1, ncell_total, &nl->scan_tmp, &nl->cap_scan, s)) != TMD_OK)
             return st;
-        TMD_LAUNCH("k_type_scan", s, k_type_scan<<<1, 32 * TMD_MAX_SPECIES, 0, s>>>(nl->type_block, (int)nb_bin,
+        TMD_LAUNCH("k_type_scan", s, k_type_scan<<<1, 128, 0, s>>>(nl->type_block, (int)nb_bin,
                                                                                     nl->type_start));
         TMD_LAUNCH("k_fill", s, k_fill<<<(unsigned)nb_bin, BIN_THREADS, 0, s>>>(pos, types, n, nl->cell_of, nl->cell_start,
                                                                               nl->cell_fill, nl->cell_atoms,

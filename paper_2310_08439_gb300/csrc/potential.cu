@@ -1372,16 +1372,25 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
     }
 }
 
-// FP64 totals of the block partials, fixed order (deterministic).
-__global__ void k_reduce(const double *__restrict__ part_e, int ne, const double *__restrict__ part_w, int nw,
-                         double *__restrict__ energy, double *__restrict__ virial) {
-    __shared__ double s[10][32];
+// FP64 totals of the block partials, fixed order (deterministic): RED_BLOCKS
+// blocks each sum a fixed slice into RED_PART scratch doubles, then one warp
+// adds those in block order.
+constexpr int RED_BLOCKS = 64;
+constexpr int RED_PART = RED_BLOCKS * 10;
+
+__global__ void __launch_bounds__(256) k_reduce_part(const double *__restrict__ part_e, int ne,
+                                                     const double *__restrict__ part_w, int nw,
+                                                     double *__restrict__ red) {
+    __shared__ double s[10][8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ce = (ne + RED_BLOCKS - 1) / RED_BLOCKS, cw = (nw + RED_BLOCKS - 1) / RED_BLOCKS;
+    const int e0 = min(ne, (int)blockIdx.x * ce), e1 = min(ne, e0 + ce);
+    const int w0 = min(nw, (int)blockIdx.x * cw), w1 = min(nw, w0 + cw);
     double v[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) v[t] = 0.0;
-    for (int i = tid; i < ne; i += blockDim.x) v[0] += part_e[i];
-    for (int i = tid; i < nw; i += blockDim.x)
+    for (int i = e0 + tid; i < e1; i += blockDim.x) v[0] += part_e[i];
+    for (int i = w0 + tid; i < w1; i += blockDim.x)
 #pragma unroll
         for (int t = 0; t < 9; ++t) v[1 + t] += part_w[(size_t)i * 9 + t];
 #pragma unroll
@@ -1393,10 +1402,18 @@ __global__ void k_reduce(const double *__restrict__ part_e, int ne, const double
     __syncthreads();
     if (tid < 10) {
         double acc = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += s[tid][w];
-        if (tid == 0) { if (energy) *energy = acc; }
-        else if (virial) virial[tid - 1] = acc;
+        for (int w = 0; w < 8; ++w) acc += s[tid][w];
+        red[blockIdx.x * 10 + tid] = acc;
     }
+}
+
+__global__ void k_reduce(const double *__restrict__ red, double *__restrict__ energy, double *__restrict__ virial) {
+    const int t = threadIdx.x;
+    if (t >= 10) return;
+    double acc = 0.0;
+    for (int b = 0; b < RED_BLOCKS; ++b) acc += red[b * 10 + t];
+    if (t == 0) { if (energy) *energy = acc; }
+    else if (virial) virial[t - 1] = acc;
 }
 
 __global__ void k_forces_out(const long long *__restrict__ Fq, int64_t n, float *__restrict__ forces) {
@@ -1650,7 +1667,7 @@ tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, i
     if ((st = grow(&nl->ph, &nl->cap_ph, nt)) != TMD_OK) return st;
     if ((st = grow(&nl->pl, &nl->cap_pl, nt)) != TMD_OK) return st;
     const int64_t nblk = pair_blocks(dm, na), ntile = (na + MT - 1) / MT;
-    if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * nblk + 16)) != TMD_OK) return st;
+    if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * nblk + 16 + RED_PART)) != TMD_OK) return st;
     return pair_cache(nl, nt, nullptr);
 }
 
@@ -1712,7 +1729,7 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * n)) != TMD_OK) return st;
     const int nblk = pair_blocks(dm, n);
     const int ntile = (int)((n + MT - 1) / MT);
-    if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
+    if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16 + RED_PART)) != TMD_OK) return st;
     double *part_e = nl->part;
     double *part_w = nl->part + ntile;
 
@@ -1728,7 +1745,8 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     int ne = 0;
     if ((st = launch_network(dm, nl->perm, types, n, nl->G, nl->dG, e_atom, part_e, &ne, s)) != TMD_OK) return st;
     if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, false)) != TMD_OK) return st;
-    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ne, part_w, nblk, energy, virial));
+    TMD_LAUNCH("k_reduce", s, k_reduce_part<<<RED_BLOCKS, 256, 0, s>>>(part_e, ne, part_w, nblk, part_w + 9 * (size_t)nblk + 16));
+    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 32, 0, s>>>(part_w + 9 * (size_t)nblk + 16, energy, virial));
     TMD_CUDA(cudaGetLastError());
     if (forces) {
         TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
@@ -1797,7 +1815,7 @@ tmd_status noalloc_capacity(const tmd_model *model, int64_t n, size_t *need) {
     b += al(sizeof(float) * n * dm.S * dm.K * NMOM);           // P
     b += 2 * al(sizeof(float) * n * dm.Dd);                    // G, G'
     b += al(sizeof(unsigned long long) * 3 * n);               // force accumulator
-    b += al(sizeof(double) * (ntile + 9 * nblk + 16));         // block partials
+    b += al(sizeof(double) * (ntile + 9 * nblk + 16 + RED_PART));         // block partials
     b += al(sizeof(int32_t) * 4);                              // check flag
     *need = b;
     return b <= NOALLOC_BYTES ? TMD_OK : TMD_ERR_CAPACITY;
@@ -1874,7 +1892,7 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     w.G = static_cast<float *>(take(sizeof(float) * n * dm.Dd));
     w.dG = static_cast<float *>(take(sizeof(float) * n * dm.Dd));
     w.Fq = static_cast<unsigned long long *>(take(sizeof(unsigned long long) * 3 * n));
-    w.part = static_cast<double *>(take(sizeof(double) * (ntile + 9 * (size_t)nblk + 16)));
+    w.part = static_cast<double *>(take(sizeof(double) * (ntile + 9 * (size_t)nblk + 16 + RED_PART)));
     int32_t *flag = static_cast<int32_t *>(take(sizeof(int32_t) * 4));
 
     // validate the caller's table on the device, then read the verdict
@@ -1918,7 +1936,8 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     int ne = 0;
     if ((st = launch_network(dm, w.perm, types, n, w.G, w.dG, e_atom, part_e, &ne, s)) != TMD_OK) return st;
     if ((st = dispatch_pair(dm, dn, pos, types, &w, part_w, nblk, s, false)) != TMD_OK) return st;
-    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 256, 0, s>>>(part_e, ne, part_w, nblk, energy, virial));
+    TMD_LAUNCH("k_reduce", s, k_reduce_part<<<RED_BLOCKS, 256, 0, s>>>(part_e, ne, part_w, nblk, part_w + 9 * (size_t)nblk + 16));
+    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 32, 0, s>>>(part_w + 9 * (size_t)nblk + 16, energy, virial));
     TMD_CUDA(cudaGetLastError());
     if (forces) {
         TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
@@ -1960,7 +1979,7 @@ tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double
         if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * n_total)) != TMD_OK) return st;
         const int nblk = pair_blocks(dm, na);
         const int ntile = (int)((na + MT - 1) / MT);
-        if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16)) != TMD_OK) return st;
+        if ((st = grow(&nl->part, &nl->cap_part, ntile + 9 * (int64_t)nblk + 16 + RED_PART)) != TMD_OK) return st;
         if ((st = split_positions(nl, pos, n_total, s)) != TMD_OK) return st;
         if ((st = pair_cache(nl, n_total, s)) != TMD_OK) return st;
         DevNlist dn = dev_nlist(nl, na, nl->box);
