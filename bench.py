@@ -164,7 +164,7 @@ def workload(name, reps=64):
     return w, desc
 
 
-def compute_only_rate(tmd, model, sysm, s, w, steps, torch, stream):
+def compute_only_rate(tmd, model, sysm, s, w, steps, torch, stream, want_forces=False):
     """tmd_compute alone (descriptors + network + backward + scatter), table built once."""
     p, _, _ = sysm.get_state()
     pos = torch.as_tensor(np.mod(p, s.box), device="cuda")
@@ -185,8 +185,32 @@ def compute_only_rate(tmd, model, sysm, s, w, steps, torch, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_eval": ms,
-            "what": "tmd_compute on a fixed table (no neighbour build, no integration)"}
+    out = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_eval": ms,
+           "what": "tmd_compute on a fixed table (no neighbour build, no integration)"}
+    if want_forces:
+        out["forces"] = F.double().cpu().numpy()
+    return out
+
+
+def radial_table_measure(tmd, model, sysm, s, w, steps, torch, stream):
+    """Tabulated radial basis (H and H' interpolated from a table, cutoff
+    folded in) against direct evaluation of the Gaussians and the cutoff:
+    tmd_compute rate on the same fixed neighbour table, and the largest force
+    difference from the direct path on this workload."""
+    out = {"what": "tmd_compute with H, H' from a table of ppa points per A (cubic Hermite) vs direct"}
+    ref = compute_only_rate(tmd, model, sysm, s, w, steps, torch, stream, want_forces=True)
+    rms = float(np.sqrt((ref["forces"] ** 2).mean()))
+    out["direct"] = {"value": ref["value"], "ms_per_eval": ref["ms_per_eval"]}
+    try:
+        for ppa in (128, 1024):
+            model.set_radial_table(ppa)
+            r = compute_only_rate(tmd, model, sysm, s, w, steps, torch, stream, want_forces=True)
+            out[f"ppa_{ppa}"] = {"value": r["value"], "ms_per_eval": r["ms_per_eval"],
+                                 "speedup": ref["ms_per_eval"] / r["ms_per_eval"],
+                                 "dF_max_over_rms_vs_direct": float(np.abs(r["forces"] - ref["forces"]).max()) / rms}
+    finally:
+        model.set_radial_table(0)
+    return out
 
 
 def batch_measure(tmd, torch, steps=5):
@@ -529,6 +553,7 @@ def main():
     extras = {}
     if not args.no_extras and world == 1:
         extras["batch"] = batch_measure(tmd, torch)
+        extras["radial_table"] = radial_table_measure(tmd, model, sysm, s, w, args.steps, torch, stream)
         extras["graphs"] = graphs_measure(tmd, torch)
         extras["serving"] = serving_measure(tmd, args.serve_seconds, torch)
 

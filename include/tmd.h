@@ -121,6 +121,23 @@ tmd_status tmd_model_destroy(tmd_model *model);
 /* Switch the network precision of an existing model (TMD_PREC_*). */
 tmd_status tmd_model_set_precision(tmd_model *model, int32_t precision);
 
+/* Tabulated radial basis (Sec. "The H_abck tensor and Batch Rational 1D
+ * Interpolation": H_abck = f_k(R) f_c(R) and its derivative read from a
+ * precomputed table instead of evaluating the Gaussians and the cutoff per
+ * pair).  points_per_angstrom = 0 returns to direct evaluation (the default);
+ * otherwise a power of two in [16, 1024].  Between grid points
+ * R_g = g / points_per_angstrom the kernels interpolate H and H' with the
+ * cubic Hermite polynomial through the exact H and H' at both ends (the paper
+ * interpolates with rational functions; this reading uses the same table with
+ * an O(h^4) error for H and O(h^3) for H', h = 1/ppa).  The table holds, for
+ * every species pair and interval, the polynomial's four coefficients per k
+ * (computed in FP64 on the host, stored FP32; H is zero from rc on):
+ * [S][S][floor(rc*ppa)+2][K][4] floats on the device, owned by the model.
+ * Errors: INVALID_ARG (ppa not 0 or a power of two in range), OOM/CUDA on
+ * allocation or upload (the model is then back on direct evaluation).
+ * Synchronises the device. */
+tmd_status tmd_model_set_radial_table(tmd_model *model, int32_t points_per_angstrom);
+
 /*
  * CUDA graphs (the paper has no counterpart: a launch-overhead measure of this
  * implementation).  The MD step loops (tmd_step, tmd_batch_step) and

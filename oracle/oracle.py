@@ -8,7 +8,11 @@ code with the CUDA library.  The C source is compiled with gcc
 Every wrapper below names the paper passage its C function follows (TensorMD,
 arXiv 2310.08439, Sec. "The Tensor Formalism"):
   moments / moment_grad / tdm      -> Eq. T_dm (moment tensor M_d, multiplicities)
-  radial                           -> H_abck = f_k(R) f_c(R)
+  radial                           -> H_abck = f_k(R) f_c(R); with radial_table > 0
+                                      the tabulated H of Sec. "The H_abck tensor
+                                      and Batch Rational 1D Interpolation"
+  hermite                          -> the interpolation step of that section
+                                      (cubic Hermite: a reading, see radial_tab)
   neighbors / neighbors_of         -> the neighbour table R_abc (all images)
   compute / atom_terms             -> Eqs. tensor_formalism, sigma_function,
                                       dP_abkd, U_abck, F1_abcx, F2_abcx, ScatterSum
@@ -49,7 +53,8 @@ class _CModel(C.Structure):
     _fields_ = [("S", C.c_int32), ("K", C.c_int32), ("L", C.c_int32), ("act", C.c_int32),
                 ("rc", C.c_double), ("sp_b", C.c_double),
                 ("mu", C.POINTER(C.c_double)), ("eta", C.POINTER(C.c_double)),
-                ("widths", C.POINTER(C.c_int32)), ("w", C.POINTER(C.POINTER(C.c_double)))]
+                ("widths", C.POINTER(C.c_int32)), ("w", C.POINTER(C.POINTER(C.c_double))),
+                ("tab_ppa", C.c_int32)]
 
 
 def _dp(a):
@@ -84,10 +89,13 @@ def lib():
 
 
 class OracleModel:
-    """Holds a C view of ``inputs.ModelParams`` (keeps the arrays alive)."""
+    """Holds a C view of ``inputs.ModelParams`` (keeps the arrays alive).
+    radial_table = 0: H evaluated directly; > 0: H and H' interpolated from a
+    table with that many grid points per Angstrom."""
 
-    def __init__(self, params):
+    def __init__(self, params, radial_table=0):
         self.params = params
+        self.radial_table = int(radial_table)
         S, K = params.n_species, params.n_radial
         self._mu = np.ascontiguousarray(params.mu, dtype=np.float64).reshape(S * S * K)
         self._eta = np.ascontiguousarray(params.eta, dtype=np.float64).reshape(S * S * K)
@@ -99,7 +107,8 @@ class OracleModel:
         act = {"tanh": 0, "squareplus": 1}[params.activation]
         self.c = _CModel(S, K, len(params.widths), act, float(params.rc),
                          float(params.squareplus_b), _dp(self._mu), _dp(self._eta),
-                         _ip(self._widths), C.cast(self._wptr, C.POINTER(C.POINTER(C.c_double))))
+                         _ip(self._widths), C.cast(self._wptr, C.POINTER(C.POINTER(C.c_double))),
+                         self.radial_table)
 
     @property
     def n_desc(self):
@@ -141,6 +150,14 @@ def radial(model: OracleModel, ti: int, tj: int, r: float):
     H, dH = np.zeros(K), np.zeros(K)
     lib().tmdo_radial(C.byref(model.c), C.c_int(ti), C.c_int(tj), C.c_double(r), _dp(H), _dp(dH))
     return H, dH
+
+
+def hermite(y0, d0, y1, d1, h, t):
+    """Cubic Hermite interpolant on [x0, x0 + h] at x0 + t h: (y, dy/dx)."""
+    y, dy = C.c_double(), C.c_double()
+    lib().tmdo_hermite(C.c_double(y0), C.c_double(d0), C.c_double(y1), C.c_double(d1), C.c_double(h),
+                       C.c_double(t), C.byref(y), C.byref(dy))
+    return y.value, dy.value
 
 
 # --------------------------------------------------------------------------

@@ -50,6 +50,8 @@ typedef struct {
     const double *eta;  /* [S][S][K]                                         */
     const int32_t *widths;      /* [L] hidden widths                         */
     const double *const *w;     /* [S] flat weights: per layer W[out][in], b */
+    int32_t tab_ppa;    /* 0: H evaluated directly; > 0: tabulated H with    */
+                        /* this many grid points per Angstrom (see below)    */
 } tmdo_model;
 
 #define NMOM 20
@@ -109,7 +111,7 @@ void tmdo_tdm(double *T) { memcpy(T, T_DM, sizeof(T_DM)); }
 /* Radial tensor H_k = f_k(r) f_c(r) and dH_k/dr   (Sec. Tensor Formalism,   */
 /* the definition of H_abck from h^(k) = f_k f_c)                            */
 /* ------------------------------------------------------------------------- */
-void tmdo_radial(const tmdo_model *m, int ti, int tj, double r, double *H, double *dH) {
+static void radial_direct(const tmdo_model *m, int ti, int tj, double r, double *H, double *dH) {
     const int K = m->K;
     const double rc = m->rc;
     double fc = 0.0, dfc = 0.0;
@@ -125,6 +127,49 @@ void tmdo_radial(const tmdo_model *m, int ti, int tj, double r, double *H, doubl
         H[k] = fk * fc;
         dH[k] = dfk * fc + fk * dfc;
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cubic Hermite interpolation on [x0, x0 + h] from the end values y0, y1 and */
+/* slopes d0, d1, at x = x0 + t h (textbook basis h00 = 2t^3 - 3t^2 + 1,      */
+/* h10 = t^3 - 2t^2 + t, h01 = -2t^3 + 3t^2, h11 = t^3 - t^2).  Exact for     */
+/* cubic polynomials; error O(h^4) in y and O(h^3) in dy/dx.                  */
+/* ------------------------------------------------------------------------- */
+void tmdo_hermite(double y0, double d0, double y1, double d1, double h, double t, double *y, double *dy) {
+    const double t2 = t * t, t3 = t2 * t;
+    *y = (2.0 * t3 - 3.0 * t2 + 1.0) * y0 + (t3 - 2.0 * t2 + t) * h * d0
+       + (-2.0 * t3 + 3.0 * t2) * y1 + (t3 - t2) * h * d1;
+    *dy = ((6.0 * t2 - 6.0 * t) * y0 + (3.0 * t2 - 4.0 * t + 1.0) * h * d0
+         + (-6.0 * t2 + 6.0 * t) * y1 + (3.0 * t2 - 2.0 * t) * h * d1) / h;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tabulated radial tensor (Sec. "The H_abck tensor and Batch Rational 1D     */
+/* Interpolation"): H and H' are read from a table of H_k(R_g), H'_k(R_g) on  */
+/* the grid R_g = g / ppa, with the cutoff folded in (entries zero from rc    */
+/* on), and interpolated between grid points.  The paper uses Kerley's        */
+/* rational interpolation, whose formulas it does not print; this reading     */
+/* interpolates the same table with cubic Hermite polynomials.  The grid      */
+/* values are computed here directly in FP64 (the table is never stored).     */
+/* ------------------------------------------------------------------------- */
+static void radial_tab(const tmdo_model *m, int ti, int tj, double r, double *H, double *dH) {
+    const int K = m->K;
+    const double h = 1.0 / (double)m->tab_ppa;
+    const double x = r * (double)m->tab_ppa;
+    const double g = floor(x);
+    const double t = x - g;
+    double H0[256], dH0[256], H1[256], dH1[256];
+    const double r0 = g * h, r1 = (g + 1.0) * h;
+    radial_direct(m, ti, tj, r0, H0, dH0);   /* zero for r0 >= rc */
+    radial_direct(m, ti, tj, r1, H1, dH1);
+    for (int k = 0; k < K; ++k) tmdo_hermite(H0[k], dH0[k], H1[k], dH1[k], h, t, &H[k], &dH[k]);
+}
+
+void tmdo_radial(const tmdo_model *m, int ti, int tj, double r, double *H, double *dH) {
+    if (m->tab_ppa > 0 && r < m->rc)
+        radial_tab(m, ti, tj, r, H, dH);
+    else
+        radial_direct(m, ti, tj, r, H, dH);
 }
 
 /* ------------------------------------------------------------------------- */

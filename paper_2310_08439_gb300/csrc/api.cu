@@ -95,6 +95,9 @@ void model_key(const tmd_model *m, std::vector<uintptr_t> &k) {
     k.push_back((uintptr_t)m->dm.precision);
     k.push_back((uintptr_t)m->dm.tile_rows);
     k.push_back((uintptr_t)m->dm.pair_bps);
+    k.push_back((uintptr_t)m->dm.rtab);
+    k.push_back((uintptr_t)m->dm.rtab_n);
+    k.push_back((uintptr_t)m->dm.rtab_scale);
 }
 
 uintptr_t bits_of(double x) {
@@ -398,6 +401,9 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     e = cudaMemcpy(m->dev_block, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(m->dev_block); delete m; return cuda_fail(e, "cudaMemcpy model"); }
     m->precision = d->precision;
+    m->mu.assign(d->mu, d->mu + (size_t)S * S * K);
+    m->eta.assign(d->eta, d->eta + (size_t)S * S * K);
+    m->rc_exact = d->rc;
     if (d->precision == TMD_PREC_BF16) {
         tmd_status st = tmd_model_set_precision(m, TMD_PREC_BF16);
         if (st != TMD_OK) { cudaFree(m->dev_block); delete m; return st; }
@@ -409,7 +415,69 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
 tmd_status tmd_model_destroy(tmd_model *m) {
     if (!m) return TMD_OK;
     if (m->dev_block) cudaFree(m->dev_block);
+    if (m->dev_rtab) cudaFree(m->dev_rtab);
     delete m;
+    return TMD_OK;
+}
+
+tmd_status tmd_model_set_radial_table(tmd_model *m, int32_t ppa) {
+    g_err[0] = 0;
+    if (!m || ppa < 0 || (ppa != 0 && (ppa < 16 || ppa > 1024 || (ppa & (ppa - 1)) != 0))) {
+        set_error("points_per_angstrom must be 0 or a power of two in [16, 1024]");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (m->dev_rtab) {
+        cudaFree(m->dev_rtab);
+        m->dev_rtab = nullptr;
+    }
+    m->dm.rtab = nullptr;
+    m->dm.rtab_scale = 0.f;
+    m->dm.rtab_n = 0;
+    if (ppa == 0) return TMD_OK;
+    const int S = m->dm.S, K = m->dm.K;
+    const double rcd = m->rc_exact;
+    // Interval g = [g h, (g + 1) h), h = 1/ppa, holds the cubic Hermite
+    // polynomial through H and H' at both ends as coefficients in
+    // t = (r - g h)/h: H = c0 + c1 t + c2 t^2 + c3 t^3, H' = (c1 + 2 c2 t +
+    // 3 c3 t^2) ppa.  The coefficients are formed in FP64 and rounded to FP32
+    // (storing node values instead would lose H' to cancellation in
+    // (H_g+1 - H_g) ppa once the grid is fine).  Node values are zero from rc
+    // on (the cutoff folded into the table).  Intervals up to floor(rc ppa) + 1:
+    // an FP32 r just below rc can round into the interval one past
+    // floor(rc ppa) when rc ppa sits within an ulp of an integer.
+    const int n = (int)std::floor(rcd * ppa) + 2;
+    std::vector<float> h((size_t)S * S * n * 4 * K, 0.f);
+    const double pi = 3.14159265358979323846, hs = 1.0 / ppa;
+    auto node = [&](int p, int k, double r, double &H, double &dH) {
+        H = dH = 0.0;
+        if (!(r < rcd)) return;
+        const double fc = 0.5 * (std::cos(pi * r / rcd) + 1.0);
+        const double dfc = -0.5 * pi / rcd * std::sin(pi * r / rcd);
+        const double mu = m->mu[(size_t)p * K + k], eta = m->eta[(size_t)p * K + k];
+        const double t = r - mu, f = std::exp(-eta * t * t);
+        H = f * fc;
+        dH = f * (-2.0 * eta * t * fc + dfc);
+    };
+    for (int p = 0; p < S * S; ++p)
+        for (int g = 0; g < n; ++g)
+            for (int k = 0; k < K; ++k) {
+                double y0, d0, y1, d1;
+                node(p, k, g * hs, y0, d0);
+                node(p, k, (g + 1) * hs, y1, d1);
+                const double dy = y1 - y0, s0 = d0 * hs, s1 = d1 * hs;
+                float *c = &h[(((size_t)p * n + g) * K + k) * 4];
+                c[0] = (float)y0;
+                c[1] = (float)s0;
+                c[2] = (float)(3.0 * dy - 2.0 * s0 - s1);
+                c[3] = (float)(-2.0 * dy + s0 + s1);
+            }
+    cudaError_t e = cudaMalloc(&m->dev_rtab, sizeof(float) * h.size());
+    if (e != cudaSuccess) { m->dev_rtab = nullptr; return cuda_fail(e, "cudaMalloc radial table"); }
+    e = cudaMemcpy(m->dev_rtab, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(m->dev_rtab); m->dev_rtab = nullptr; return cuda_fail(e, "cudaMemcpy radial table"); }
+    m->dm.rtab = m->dev_rtab;
+    m->dm.rtab_scale = (float)ppa;
+    m->dm.rtab_n = n;
     return TMD_OK;
 }
 

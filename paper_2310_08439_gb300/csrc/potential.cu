@@ -110,6 +110,48 @@ __device__ __forceinline__ void radial(const float4 *rad, float r_hi, float r_lo
     }
 }
 
+// Tabulated radial basis (Sec. "The H_abck tensor and Batch Rational 1D
+// Interpolation": H and H' read from a table with the cutoff folded in).
+// Interval g = [g/scale, (g+1)/scale) holds, per k, the coefficients
+// (c0, c1, c2, c3) of the cubic Hermite polynomial in t = r scale - g through
+// H and H' at both ends; H = c0 + t (c1 + t (c2 + t c3)) and
+// H' = scale (c1 + t (2 c2 + 3 t c3)).  scale is a power of two, so r_hi scale
+// and its integer part are exact and t carries r_lo.  tab = the intervals of
+// this species pair, [interval][k] float4.
+struct TabCell {
+    const float4 *c;   // this pair's interval: K float4
+    float t, t3;       // t and 3 t
+};
+
+__device__ __forceinline__ TabCell tab_cell(const float *tab, int K, float scale, float r_hi, float r_lo) {
+    const float x = r_hi * scale;
+    const float gf = floorf(x);
+    const int g = __float_as_int(gf + 12582912.0f) - 0x4B400000;   // exact: 0 <= gf < 2^22
+    TabCell c;
+    c.c = reinterpret_cast<const float4 *>(tab) + (size_t)g * K;
+    c.t = (x - gf) + r_lo * scale;
+    c.t3 = 3.f * c.t;
+    return c;
+}
+
+__device__ __forceinline__ void tab_eval(const TabCell &tc, int k, float scale, float &H, float &dH) {
+    const float4 q = __ldg(tc.c + k);
+    H = fmaf(tc.t, fmaf(tc.t, fmaf(tc.t, q.w, q.z), q.y), q.x);
+    dH = scale * fmaf(tc.t, fmaf(tc.t3, q.w, 2.f * q.z), q.y);
+}
+
+template <int K, bool DERIV>
+__device__ __forceinline__ void radial_tab(const float *tab, float scale, float r_hi, float r_lo, float *H, float *dH) {
+    const TabCell tc = tab_cell(tab, K, scale, r_hi, r_lo);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float h, d;
+        tab_eval(tc, k, scale, h, d);
+        H[k] = h;
+        if (DERIV) dH[k] = d;
+    }
+}
+
 // r = |D| as an unevaluated sum r_hi + r_lo from r^2 = r2_hi + r2_lo, and 1/r.
 // r_hi = r2 y with y ~ 1/sqrt(r2_hi) (pairs never coincide, r2_hi >= ~1); r_lo is the Newton correction (exact
 // residual by FMA), so r_hi + r_lo is accurate to ~1e-13 whatever the error of
@@ -262,7 +304,7 @@ __global__ void k_split_pos(const double *__restrict__ pos, int64_t n, float4 *_
 // ---------------------------------------------------------------------------
 // descriptor forward: P and G per atom
 // ---------------------------------------------------------------------------
-template <int K, int S>
+template <int K, int S, bool TAB>
 __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                   const int32_t *__restrict__ types, float *__restrict__ G,
                                                   float *__restrict__ Pout) {
@@ -317,7 +359,11 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                           float r_hi, r_lo, ir;
                           split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
                           float H[K], M[NMOM];
-                          radial<K, false>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, nullptr);
+                          if (TAB)
+                              radial_tab<K, false>(m.rtab + (size_t)(ti * S + b) * m.rtab_n * 4 * K, m.rtab_scale,
+                                                   r_hi, r_lo, H, nullptr);
+                          else
+                              radial<K, false>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, nullptr);
                           moments20(e.x * ir, e.y * ir, e.z * ir, M);
 #pragma unroll
                           for (int k = 0; k < K; ++k) sH[((k % KPL) * 8 + k / KPL) * RS + slot] = H[k];
@@ -1005,9 +1051,9 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 // g_ij = dE/dD_ij of one in-cutoff pair (Eqs. dP_abkd, U_abck, F1_abcx,
 // F2_abcx): Pb = the centre atom's P' for the neighbour's species, rad = the
 // radial parameters of the (centre, neighbour) species pair.
-template <int K>
+template <int K, bool TAB>
 __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, const float2 e2, const float *Pb,
-                                          const float4 *rad, float &gxs, float &gys, float &gzs) {
+                                          const float4 *rad, const float *tab, float &gxs, float &gys, float &gzs) {
     float r_hi, r_lo, ir;
     split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
     const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
@@ -1016,16 +1062,25 @@ __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, con
     float V[NMOM], Wd[NMOM];
 #pragma unroll
     for (int d = 0; d < NMOM; ++d) V[d] = Wd[d] = 0.f;
-    float fc, dfc;
-    cutoff_fn(r_hi, m.inv_rc, fc, dfc);
+    float fc = 0.f, dfc = 0.f;
+    TabCell tc;
+    if (TAB)
+        tc = tab_cell(tab, K, m.rtab_scale, r_hi, r_lo);
+    else
+        cutoff_fn(r_hi, m.inv_rc, fc, dfc);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         // H_k and H'_k formed inside the loop (no per-pair arrays)
-        const float4 rp = rad[k];
-        const float t = (r_hi - rp.x) + (r_lo - rp.y);
-        const float f = ex2_ftz(-rp.z * t * t);
-        const float Hk = f * fc;
-        const float dHk = f * fmaf(-rp.w * t, fc, dfc);
+        float Hk, dHk;
+        if (TAB) {
+            tab_eval(tc, k, m.rtab_scale, Hk, dHk);
+        } else {
+            const float4 rp = rad[k];
+            const float t = (r_hi - rp.x) + (r_lo - rp.y);
+            const float f = ex2_ftz(-rp.z * t * t);
+            Hk = f * fc;
+            dHk = f * fmaf(-rp.w * t, fc, dfc);
+        }
 #pragma unroll
         for (int q4 = 0; q4 < NMOM / 4; ++q4) {
             const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
@@ -1100,7 +1155,7 @@ __device__ __forceinline__ void pprime_setup(const float *__restrict__ Pin, cons
 // contiguous run of atoms (perm order) and fills every batch of 32 lanes with
 // the rest of the current atom's pairs followed by the first pairs of the
 // next atom (two P' slots per warp, two self-force accumulators).
-template <int K, int S>
+template <int K, int S, bool TAB>
 __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlist nl, const int32_t *__restrict__ types,
                                                           const float *__restrict__ Pin, const float *__restrict__ dG,
                                                           unsigned long long *__restrict__ Fq,
@@ -1157,9 +1212,10 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
                 const int b = (int)(jb >> 28);
                 const int j = (int)(jb & 0x0FFFFFFFu);
                 const float *Pb = s_Pd[warp][isc ? slot : slot ^ 1] + b * PSTR;
-                const float4 *rad = &s_rad[((isc ? ta : tn) * S + b) * K];
+                const int tp = (isc ? ta : tn) * S + b;
                 float gxs, gys, gzs;
-                pair_grad<K>(m, e, e2, Pb, rad, gxs, gys, gzs);
+                pair_grad<K, TAB>(m, e, e2, Pb, &s_rad[tp * K], TAB ? m.rtab + (size_t)tp * m.rtab_n * 4 * K : nullptr,
+                                  gxs, gys, gzs);
                 // ScatterSum in 2^-32 fixed point (exact, order independent)
                 const long long qx = to_fixed(gxs);
                 const long long qy = to_fixed(gys);
@@ -1240,7 +1296,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
 // PAW (batched): each atom's virial is summed over its own pairs and written
 // to w_atom [atoms][9] for per-system reductions; otherwise lanes keep
 // compensated running sums and each block writes one FP64 partial.
-template <int K, int S, bool PAW, bool CACHED>
+template <int K, int S, bool PAW, bool CACHED, bool TAB>
 __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                    const int32_t *__restrict__ types, const float *__restrict__ Pin,
                                                    const float *__restrict__ dG,
@@ -1303,7 +1359,8 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
                       const int b = (int)(jb >> 28);
                       const int j = (int)(jb & 0x0FFFFFFFu);
                       float gxs, gys, gzs;
-                      pair_grad<K>(m, e, e2, sPd + b * PSTR, &s_rad[(ti * S + b) * K], gxs, gys, gzs);
+                      pair_grad<K, TAB>(m, e, e2, sPd + b * PSTR, &s_rad[(ti * S + b) * K],
+                                        TAB ? m.rtab + (size_t)(ti * S + b) * m.rtab_n * 4 * K : nullptr, gxs, gys, gzs);
                       // ScatterSum in 2^-32 fixed point: integer adds are exact and
                       // order independent, so forces are bitwise reproducible.
                       const long long qx = to_fixed(gxs);
@@ -1472,17 +1529,28 @@ template <int K, int S>
 tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
                                tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool forward,
                                float *w_atom) {
-    if (forward)
-        TMD_LAUNCH("k_desc", s, k_desc<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
-    else if (w_atom)   // batched evaluations always run with the pair cache
-        TMD_LAUNCH("k_force", s, k_force<K, S, true, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
-                                                                                  nl->Fq, part_w, w_atom));
+    if (forward && dm.rtab)
+        TMD_LAUNCH("k_desc", s, k_desc<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+    else if (forward)
+        TMD_LAUNCH("k_desc", s, k_desc<K, S, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+    else if (w_atom && dm.rtab)   // batched evaluations always run with the pair cache
+        TMD_LAUNCH("k_force", s, k_force<K, S, true, true, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                        nl->dG, nl->Fq, part_w, w_atom));
+    else if (w_atom)
+        TMD_LAUNCH("k_force", s, k_force<K, S, true, true, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                         nl->dG, nl->Fq, part_w, w_atom));
+    else if (dn.pq && dm.rtab)
+        TMD_LAUNCH("k_force", s, k_force_merged<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, types, nl->P, nl->dG,
+                                                                                   nl->Fq, part_w));
     else if (dn.pq)
-        TMD_LAUNCH("k_force", s, k_force_merged<K, S><<<nblk, PW * 32, 0, s>>>(dm, dn, types, nl->P, nl->dG, nl->Fq,
-                                                                             part_w));
+        TMD_LAUNCH("k_force", s, k_force_merged<K, S, false><<<nblk, PW * 32, 0, s>>>(dm, dn, types, nl->P, nl->dG,
+                                                                                    nl->Fq, part_w));
+    else if (dm.rtab)
+        TMD_LAUNCH("k_force", s, k_force<K, S, false, false, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                          nl->dG, nl->Fq, part_w, nullptr));
     else
-        TMD_LAUNCH("k_force", s, k_force<K, S, false, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P, nl->dG,
-                                                                                    nl->Fq, part_w, nullptr));
+        TMD_LAUNCH("k_force", s, k_force<K, S, false, false, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                           nl->dG, nl->Fq, part_w, nullptr));
     TMD_CUDA(cudaGetLastError());
     return TMD_OK;
 }

@@ -41,6 +41,12 @@ struct DevModel {
     // tile shapes (host-side launch choices; 0 = built-in default)
     int tile_rows;                      // atoms per FP32 network tile: 32 or 64
     int pair_bps;                       // blocks per SM of the persistent pair-kernel grid
+    // tabulated radial basis (nullptr = direct evaluation): per species pair
+    // p = t_i S + t_j, rtab_n grid points r_g = g / rtab_scale, each row
+    // [H_0 .. H_{K-1}, H'_0 .. H'_{K-1}] with the cutoff function folded in
+    const float *rtab;
+    float rtab_scale;                   // grid points per Angstrom (a power of two)
+    int rtab_n;
 };
 
 // persistent grid of the pair kernels for n atoms
@@ -89,6 +95,9 @@ struct tmd_model {
     void *dev_block = nullptr;  // one allocation holding radial + all weights
     size_t dev_bytes = 0;
     int precision = TMD_PREC_FP32;
+    float *dev_rtab = nullptr;  // tabulated radial basis (tmd_model_set_radial_table)
+    std::vector<double> mu, eta; // radial parameters [S][S][K] (host copy, for tables)
+    double rc_exact = 0.0;
 };
 
 struct tmd_nlist {

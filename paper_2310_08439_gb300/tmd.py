@@ -65,6 +65,7 @@ _SIGS = {
     "tmd_model_destroy": (C.c_int, [_P]),
     "tmd_model_set_precision": (C.c_int, [_P, C.c_int32]),
     "tmd_model_set_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "tmd_model_set_radial_table": (C.c_int, [_P, C.c_int32]),
     "tmd_model_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
     "tmd_autotune": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), C.POINTER(Tuning), _P]),
     "tmd_batch_autotune": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(Tuning), _P]),
@@ -198,10 +199,17 @@ class Model:
         check(lib().tmd_model_create(C.byref(d), C.byref(h)))
         self.handle = h
         self.precision = precision
+        self.radial_table = 0
 
     def set_precision(self, precision):
         check(lib().tmd_model_set_precision(self.handle, PREC[precision]))
         self.precision = precision
+
+    def set_radial_table(self, points_per_angstrom):
+        """Read H and H' from a table with this many points per Angstrom
+        (a power of two in [16, 1024]); 0 returns to direct evaluation."""
+        check(lib().tmd_model_set_radial_table(self.handle, int(points_per_angstrom)))
+        self.radial_table = int(points_per_angstrom)
 
     @property
     def tuning(self):

@@ -21,6 +21,9 @@ MUTANTS = {
     "min_image_floor": ("-(int)rint((pos[3 * j + x]", "-(int)floor((pos[3 * j + x]"),
     "act_derivative_wrong_layer": ("g[c] = gn[c] * act_df(m, z[l - 1][c])", "g[c] = gn[c] * act_df(m, z[l][c])"),
     "rank3_moment_transposed": ("{1, 2, 0}, {1, 1, 1}, {1, 0, 2}", "{1, 1, 1}, {1, 2, 0}, {1, 0, 2}"),
+    "hermite_end_slope_sign": ("+ (t3 - t2) * h * d1;", "- (t3 - t2) * h * d1;"),
+    "hermite_slope_unscaled": ("(t3 - 2.0 * t2 + t) * h * d0", "(t3 - 2.0 * t2 + t) * d0"),
+    "table_wrong_upper_node": ("r1 = (g + 1.0) * h;", "r1 = (g + 2.0) * h;"),
 }
 
 

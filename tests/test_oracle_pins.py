@@ -92,6 +92,76 @@ def test_radial_special_values_and_derivative():
         assert np.allclose(dH, (hp - hm) / 2e-6, atol=1e-8)
 
 
+# ---------------------------------------------------------------- tabulated H
+def test_hermite_reproduces_cubics_and_quartic_error():
+    """Cubic Hermite interpolation from end values and slopes reproduces every
+    cubic (value and slope) on the interval; for x^4 on [0, 1] its error is the
+    closed form t^2 (t - 1)^2 (the remainder f^(4)/4! (x - x0)^2 (x - x1)^2)."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        p = np.polynomial.Polynomial(rng.normal(size=4))
+        dp = p.deriv()
+        x0, h = rng.uniform(-2.0, 2.0), rng.uniform(0.01, 1.0)
+        for t in (0.0, 0.13, 0.5, 0.77, 1.0):
+            y, dy = O.hermite(p(x0), dp(x0), p(x0 + h), dp(x0 + h), h, t)
+            x = x0 + t * h
+            assert abs(y - p(x)) <= 1e-12 * (1.0 + abs(p(x)))
+            assert abs(dy - dp(x)) <= 1e-10 * (1.0 + abs(dp(x)))
+    for t in (0.1, 0.5, 0.8):
+        y, dy = O.hermite(0.0, 0.0, 1.0, 4.0, 1.0, t)
+        assert abs((t ** 4 - y) - t * t * (t - 1.0) ** 2) < 1e-14
+        assert abs((4 * t ** 3 - dy) - (2 * t * (t - 1.0) ** 2 + 2 * t * t * (t - 1.0))) < 1e-14
+
+
+def test_radial_table_nodes_order_and_cutoff():
+    """Tabulated H (Sec. "The H_abck tensor and Batch Rational 1D
+    Interpolation"): equal to the direct H and H' at every grid point, zero
+    from rc on, and converging to the direct values as h^4 (H) and h^3 (H')
+    when the spacing h = 1/ppa halves."""
+    w = I.medium()
+    direct = O.OracleModel(w.model)
+    rc = w.model.rc
+    for ppa in (16, 64):
+        tab = O.OracleModel(w.model, radial_table=ppa)
+        for g in (7, 40, int(rc * ppa) - 1):
+            r = g / ppa
+            Ht, dHt = O.radial(tab, 0, 1, r)
+            Hd, dHd = O.radial(direct, 0, 1, r)
+            assert np.allclose(Ht, Hd, rtol=0, atol=1e-15) and np.allclose(dHt, dHd, rtol=0, atol=1e-14)
+        for r in (rc, rc + 0.3):
+            Ht, dHt = O.radial(tab, 1, 0, r)
+            assert np.all(Ht == 0.0) and np.all(dHt == 0.0)
+        Ht, _ = O.radial(tab, 1, 0, rc - 1e-9)
+        assert np.abs(Ht).max() < 1e-12
+    rs = np.linspace(0.8, rc - 1e-3, 1201)
+    ref = [O.radial(direct, 1, 1, r) for r in rs]
+    errs = []
+    for ppa in (32, 64, 128):
+        tab = O.OracleModel(w.model, radial_table=ppa)
+        eH = eD = 0.0
+        for r, (Hd, dHd) in zip(rs, ref):
+            Ht, dHt = O.radial(tab, 1, 1, r)
+            eH, eD = max(eH, np.abs(Ht - Hd).max()), max(eD, np.abs(dHt - dHd).max())
+        errs.append((eH, eD))
+    for (h1, d1), (h2, d2) in zip(errs, errs[1:]):
+        assert 12.0 < h1 / h2 < 20.0 and 6.0 < d1 / d2 < 10.0, errs
+
+
+def test_tabulated_forces_are_negative_energy_gradient():
+    """With the tabulated H the slope used for forces is the derivative of the
+    interpolant itself, so the forces stay the exact gradient of the
+    (interpolated) energy."""
+    p = I.random_model(2, 6, 4.5, [12, 10], seed=3)
+    om = O.OracleModel(p, radial_table=32)
+    c = I.cluster(16, 3.6, seed=5, n_species=2)
+    F = O.evaluate(om, c.pos, c.types, c.box, c.pbc)["forces"]
+    rng = np.random.default_rng(2)
+    for _ in range(8):
+        i, x = int(rng.integers(c.n)), int(rng.integers(3))
+        fd = _fd_force(om, c.pos, c.types, c.box, c.pbc, i, x)
+        assert abs(fd - F[i, x]) <= 1e-7 * max(1.0, abs(F[i, x])) + 1e-8
+
+
 # ---------------------------------------------------------------- neighbours
 def _brute_pairs(pos, box, pbc, r):
     """Independent image enumeration: every s in a generous cube."""
