@@ -1,0 +1,875 @@
+// Pair kernels of the TensorMD evaluation (Sec. "The Tensor Formalism"):
+//   k_desc          setup (D, R, Dhat), H_abck = f_k f_c, M_abcd,
+//                   P_abkd = sum_c H M, G_abkm = sigma(T_dm P^2)
+//                                        -- Eqs. tensor_formalism, sigma_function
+//   k_force(_merged) P' = 2 T sigma' P G'; V = P' H and W = P' H' (so that
+//                   F1 = U H' R' = W . M and F2 = V M' with M' formed on the
+//                   fly); ScatterSum into forces, virial
+//                                        -- Eqs. dP_abkd, U_abck, F1_abcx, F2_abcx
+//
+// One warp owns one centre atom.  In k_desc, neighbour entries beyond rc are
+// dropped and the survivors are compacted through a per-warp shared-memory
+// queue (and into the pair cache, from which k_force reads them back), so
+// every lane works on an in-cutoff pair.  Each lane computes H and M for one
+// neighbour and stages them in shared memory; the warp then accumulates the
+// per-atom P[b][k][d] outer products with each lane owning a (K/8 x 5) block
+// of P in registers.  In k_force each lane owns one cached pair and reads the
+// atom's P' from shared memory with broadcast loads.
+//
+// Templates over the radial channel count K and the species count S; each
+// pair_k<K>.cu translation unit instantiates one K (compiled in parallel).
+#pragma once
+
+#include "tmd_internal.cuh"
+
+namespace tmd {
+
+namespace {
+
+constexpr int PW = PAIR_WARPS;   // warps per block in the pair kernels
+constexpr float PI_F = 3.14159265358979323846f;
+
+// multiplicities T_d and ranks m(d) in the row order of Eq. T_dm:
+// 1 | x y z | xx xy xz yy yz zz | xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+__constant__ float c_T[NMOM] = {1, 1, 1, 1, 1, 2, 2, 1, 2, 1, 1, 3, 3, 3, 6, 3, 1, 3, 3, 1};
+
+__device__ __forceinline__ void moments20(float x, float y, float z, float *M) {
+    M[0] = 1.f;
+    M[1] = x; M[2] = y; M[3] = z;
+    M[4] = x * x; M[5] = x * y; M[6] = x * z; M[7] = y * y; M[8] = y * z; M[9] = z * z;
+    M[10] = M[4] * x; M[11] = M[4] * y; M[12] = M[4] * z; M[13] = x * M[7]; M[14] = M[5] * z;
+    M[15] = x * M[9]; M[16] = M[7] * y; M[17] = M[7] * z; M[18] = y * M[9]; M[19] = M[9] * z;
+}
+
+// 2^x and 1/sqrt(x) from the special-function unit (PTX ex2.approx /
+// rsqrt.approx, relative error about 2^-22; flush-to-zero: a result below
+// 2^-126 becomes 0, and no argument here is subnormal)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// sin(pi t) and cos(pi t) for |t| <= 1/2 from their Taylor series in
+// y = pi t (|y| <= pi/2): the sine through y^13 and the cosine through y^12
+// leave truncation errors of at most 7e-10 and 7e-9.
+__device__ __forceinline__ void sincospi_half(float t, float &sn, float &cs) {
+    const float y = PI_F * t, u = y * y;
+    float p = 1.f / 6227020800.f;
+    p = fmaf(p, u, -1.f / 39916800.f);
+    p = fmaf(p, u, 1.f / 362880.f);
+    p = fmaf(p, u, -1.f / 5040.f);
+    p = fmaf(p, u, 1.f / 120.f);
+    p = fmaf(p, u, -1.f / 6.f);
+    sn = fmaf(y * u, p, y);
+    float q = 1.f / 479001600.f;
+    q = fmaf(q, u, -1.f / 3628800.f);
+    q = fmaf(q, u, 1.f / 40320.f);
+    q = fmaf(q, u, -1.f / 720.f);
+    q = fmaf(q, u, 1.f / 24.f);
+    q = fmaf(q, u, -0.5f);
+    cs = fmaf(u, q, 1.f);
+}
+
+// f_c = (cos(pi r / rc) + 1) / 2 and df_c/dr for r < rc, through t = r / rc - 1/2:
+// cos(pi r / rc) = -sin(pi t), sin(pi r / rc) = cos(pi t).
+__device__ __forceinline__ void cutoff_fn(float r, float inv_rc, float &fc, float &dfc) {
+    float sn, cs;
+    sincospi_half(fmaf(r, inv_rc, -0.5f), sn, cs);
+    fc = 0.5f - 0.5f * sn;
+    dfc = -0.5f * PI_F * inv_rc * cs;
+}
+
+// H_k = f_k f_c (and dH_k/dr when DERIV) for r < rc.  rad[k] = (mu_hi, mu_lo,
+// eta log2 e, 2 eta); r = r_hi + r_lo so that t = r - mu keeps ~FP64 accuracy
+// (the Gaussians are steep: dlnH/dr = -2 eta t amplifies any rounding of r).
+template <int K, bool DERIV>
+__device__ __forceinline__ void radial(const float4 *rad, float r_hi, float r_lo, float inv_rc, float *H, float *dH) {
+    float fc, dfc;
+    cutoff_fn(r_hi, inv_rc, fc, dfc);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 p = rad[k];
+        const float t = (r_hi - p.x) + (r_lo - p.y);
+        const float f = ex2_ftz(-p.z * t * t);
+        H[k] = f * fc;
+        if (DERIV) dH[k] = f * fmaf(-p.w * t, fc, dfc);
+    }
+}
+
+// Tabulated radial basis (Sec. "The H_abck tensor and Batch Rational 1D
+// Interpolation": H and H' read from a table with the cutoff folded in).
+// Interval g = [g/scale, (g+1)/scale) holds, per k, the coefficients
+// (c0, c1, c2, c3) of the cubic Hermite polynomial in t = r scale - g through
+// H and H' at both ends; H = c0 + t (c1 + t (c2 + t c3)) and
+// H' = scale (c1 + t (2 c2 + 3 t c3)).  scale is a power of two, so r_hi scale
+// and its integer part are exact and t carries r_lo.  tab = the intervals of
+// this species pair, [interval][k] float4.
+struct TabCell {
+    const float4 *c;   // this pair's interval: K float4
+    float t, t3;       // t and 3 t
+};
+
+__device__ __forceinline__ TabCell tab_cell(const float *tab, int K, float scale, float r_hi, float r_lo) {
+    const float x = r_hi * scale;
+    const float gf = floorf(x);
+    const int g = __float_as_int(gf + 12582912.0f) - 0x4B400000;   // exact: 0 <= gf < 2^22
+    TabCell c;
+    c.c = reinterpret_cast<const float4 *>(tab) + (size_t)g * K;
+    c.t = (x - gf) + r_lo * scale;
+    c.t3 = 3.f * c.t;
+    return c;
+}
+
+__device__ __forceinline__ void tab_eval(const TabCell &tc, int k, float scale, float &H, float &dH) {
+    const float4 q = __ldg(tc.c + k);
+    H = fmaf(tc.t, fmaf(tc.t, fmaf(tc.t, q.w, q.z), q.y), q.x);
+    dH = scale * fmaf(tc.t, fmaf(tc.t3, q.w, 2.f * q.z), q.y);
+}
+
+template <int K, bool DERIV>
+__device__ __forceinline__ void radial_tab(const float *tab, float scale, float r_hi, float r_lo, float *H, float *dH) {
+    const TabCell tc = tab_cell(tab, K, scale, r_hi, r_lo);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float h, d;
+        tab_eval(tc, k, scale, h, d);
+        H[k] = h;
+        if (DERIV) dH[k] = d;
+    }
+}
+
+// r = |D| as an unevaluated sum r_hi + r_lo from r^2 = r2_hi + r2_lo, and 1/r.
+// r_hi = r2 y with y ~ 1/sqrt(r2_hi) (pairs never coincide, r2_hi >= ~1); r_lo is the Newton correction (exact
+// residual by FMA), so r_hi + r_lo is accurate to ~1e-13 whatever the error of
+// y; 1/r is y refined by one Newton step against r_hi + r_lo.
+__device__ __forceinline__ void split_sqrt(float r2_hi, float r2_lo, float &r_hi, float &r_lo, float &ir) {
+    const float y = rsqrt_ftz(r2_hi);
+    r_hi = r2_hi * y;
+    r_lo = (fmaf(-r_hi, r_hi, r2_hi) + r2_lo) * 0.5f * y;
+    const float e = fmaf(-r_hi, y, 1.f) - r_lo * y;
+    ir = fmaf(y, e, y);
+}
+
+// Double-float helpers: a value is carried as an unevaluated sum hi + lo of two
+// floats.  two_sum is Knuth's error-free addition.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// D = (x_j + s L) - x_i on one axis from hi/lo positions and box length.
+__device__ __forceinline__ void diff_df(float xjh, float xjl, float xih, float xil, int s, float Lh, float Ll,
+                                        float &dh, float &dl) {
+    float u, e1;
+    two_sum(xjh, -xih, u, e1);
+    float lo = (xjl - xil) + e1;
+    if (s != 0) {
+        const float sf = __int_as_float(0x4B400000 + s) - 12582912.0f;  // (float)s, |s| <= 15
+        const float p = sf * Lh;
+        const float pe = fmaf(sf, Lh, -p);  // exact error of the product
+        float v, e2;
+        two_sum(u, p, v, e2);
+        u = v;
+        lo += e2 + fmaf(sf, Ll, pe);
+    }
+    dh = u + lo;
+    dl = lo - (dh - u);
+}
+
+// |D|^2 as hi + lo from hi/lo components (exact products, error-free sums).
+__device__ __forceinline__ void norm2_df(float xh, float xl, float yh, float yl, float zh, float zl, float &r2h,
+                                         float &r2l) {
+    const float px = xh * xh, ex = fmaf(xh, xh, -px);
+    const float py = yh * yh, ey = fmaf(yh, yh, -py);
+    const float pz = zh * zh, ez = fmaf(zh, zh, -pz);
+    float s1, e1, s2, e2;
+    two_sum(px, py, s1, e1);
+    two_sum(s1, pz, s2, e2);
+    const float lo = ((ex + ey) + ez) + (e1 + e2) + 2.f * fmaf(xh, xl, fmaf(yh, yl, zh * zl));
+    r2h = s2 + lo;
+    r2l = lo - (r2h - s2);
+}
+
+// Walk the entries [beg, end) of atom a, keep pairs with r^2 < rc^2 and hand
+// them to f in batches of up to 32 (one per lane).  D = x_j + s L - x_i and r^2
+// are formed in double-float FP32 arithmetic from hi/lo positions (no FP64
+// instructions: on this GPU FP64 runs at a small fraction of the FP32 rate).
+// The queue holds (Dx, Dy, Dz, j | b<<28) rounded to FP32 and r^2 as hi/lo.
+template <typename F>
+__device__ __forceinline__ int for_pairs(const DevNlist &nl, int a, int64_t beg, int64_t end, float rc2h, float rc2l,
+                                         float4 *q, float2 *q2, int lane, F &&f, bool to_cache = false) {
+    int qn = 0, kept = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    const float4 ih = nl.ph[a], il = nl.pl[a];
+    float Lh0 = nl.Lh[0], Lh1 = nl.Lh[1], Lh2 = nl.Lh[2], Ll0 = nl.Ll[0], Ll1 = nl.Ll[1], Ll2 = nl.Ll[2];
+    if (nl.sys_of) {  // batched: the box of this atom's system
+        const SysParams &q = nl.sp[nl.sys_of[a]];
+        Lh0 = q.Lh[0]; Lh1 = q.Lh[1]; Lh2 = q.Lh[2];
+        Ll0 = q.Ll[0]; Ll1 = q.Ll[1]; Ll2 = q.Ll[2];
+    }
+    int64_t base = beg;
+    while (true) {
+        while (qn < 32 && base < end) {
+            const int64_t c = base + lane;
+            bool v = false;
+            float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 e2 = make_float2(0.f, 0.f);
+            if (c < end) {
+                const int j = nl.nbr[c];
+                const char4 s = nl.shift[c];
+                const float4 jh = nl.ph[j], jl = nl.pl[j];
+                float dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l;
+                diff_df(jh.x, jl.x, ih.x, il.x, s.x, Lh0, Ll0, dxh, dxl);
+                diff_df(jh.y, jl.y, ih.y, il.y, s.y, Lh1, Ll1, dyh, dyl);
+                diff_df(jh.z, jl.z, ih.z, il.z, s.z, Lh2, Ll2, dzh, dzl);
+                norm2_df(dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l);
+                v = (r2h < rc2h) || (r2h == rc2h && r2l < rc2l);
+                e = make_float4(dxh, dyh, dzh, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
+                e2 = make_float2(r2h, r2l);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, v);
+            if (v) {
+                const int slot = qn + __popc(m & lt);
+                q[slot] = e;
+                q2[slot] = e2;
+                if (to_cache) {   // compacted in order at [beg, beg + kept)
+                    nl.pq[beg + kept + __popc(m & lt)] = e;
+                    nl.pq2[beg + kept + __popc(m & lt)] = e2;
+                }
+            }
+            qn += __popc(m);
+            kept += __popc(m);
+            base += 32;
+        }
+        if (qn == 0) break;
+        // one call site: full batches while entries remain, then the tail
+        const int nb = min(qn, 32);
+        __syncwarp();
+        f(q[lane], q2[lane], lane < nb, nb);
+        __syncwarp();
+        if (lane < qn - nb) {
+            q[lane] = q[lane + 32];
+            q2[lane] = q2[lane + 32];
+        }
+        __syncwarp();
+        qn -= nb;
+    }
+    return kept;
+}
+
+// The in-cutoff pairs of atom a from the pair cache written by the
+// descriptor pass, in batches of up to 32 (one per lane).
+template <typename F>
+__device__ __forceinline__ void cached_pairs(const DevNlist &nl, int a, int lane, F &&f) {
+    const int64_t pb = nl.beg[a];
+    const int np = nl.npair[a];
+    for (int base = 0; base < np; base += 32) {
+        const int nb = min(32, np - base);
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 e2 = make_float2(1.f, 0.f);
+        if (lane < nb) {
+            e = nl.pq[pb + base + lane];
+            e2 = nl.pq2[pb + base + lane];
+        }
+        f(e, e2, lane < nb, nb);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// descriptor forward: P and G per atom
+// ---------------------------------------------------------------------------
+template <int K, int S, bool TAB>
+__global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const double *__restrict__ pos,
+                                                  const int32_t *__restrict__ types, float *__restrict__ G,
+                                                  float *__restrict__ Pout) {
+    constexpr int KPL = K / 8;   // k values per lane
+    constexpr int RS = 44;       // row stride of the staged pair columns (>= 32 + 3 (S - 1) slots)
+    constexpr int Dd = S * K * 4;
+    __shared__ float4 s_rad[S * S * K];
+    __shared__ float4 s_q[PW][64];
+    __shared__ float2 s_q2[PW][64];
+    // staged pair data, one column per pair: H_k in row (k % KPL) 8 + k / KPL,
+    // M_d in row (d % 5) 4 + d / 5, so that the lane owning k-group kg and
+    // d-group g reads four pairs of a row with one conflict-free vector load
+    __shared__ __align__(16) float s_H[PW][K * RS];
+    __shared__ __align__(16) float s_M[PW][NMOM * RS];
+    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = lane >> 2, g = lane & 3;
+    const unsigned lt = (1u << lane) - 1u;
+    float Tg[5];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
+    const int64_t total = (int64_t)gridDim.x * PW;
+    for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
+        const int a = nl.perm[p];
+        const int ti = types[a];
+        float acc[S][KPL][5];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
+        float *sH = s_H[warp];
+        float *sM = s_M[warp];
+        // the in-cutoff pairs also go to the pair cache, when there is one
+        const int written = for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
+                  [&](const float4 e, const float2 e2, bool valid, int) {
+                      const uint32_t jb = __float_as_uint(e.w);
+                      const int b = valid ? (int)(jb >> 28) : S;
+                      // columns grouped by neighbour species, each group starting
+                      // on a multiple of 4
+                      int cnt[S], slot = 0, start = 0;
+#pragma unroll
+                      for (int s = 0; s < S; ++s) {
+                          const unsigned ms = __ballot_sync(0xffffffffu, b == s);
+                          if (b == s) slot = start + __popc(ms & lt);
+                          cnt[s] = __popc(ms);
+                          start += (cnt[s] + 3) & ~3;
+                      }
+                      if (valid) {
+                          float r_hi, r_lo, ir;
+                          split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
+                          float H[K], M[NMOM];
+                          if (TAB)
+                              radial_tab<K, false>(m.rtab + (size_t)(ti * S + b) * m.rtab_n * 4 * K, m.rtab_scale,
+                                                   r_hi, r_lo, H, nullptr);
+                          else
+                              radial<K, false>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, nullptr);
+                          moments20(e.x * ir, e.y * ir, e.z * ir, M);
+#pragma unroll
+                          for (int k = 0; k < K; ++k) sH[((k % KPL) * 8 + k / KPL) * RS + slot] = H[k];
+#pragma unroll
+                          for (int d = 0; d < NMOM; ++d) sM[((d % 5) * 4 + d / 5) * RS + slot] = M[d];
+                      }
+                      __syncwarp();
+                      // P[b][k][d] += H_k M_d: four pairs per step, the rest one at a time
+                      start = 0;
+#pragma unroll
+                      for (int s = 0; s < S; ++s) {
+                          const int stop = start + cnt[s];
+                          int q = start;
+                          for (; q + 4 <= stop; q += 4) {
+                              float4 hv[KPL], mv[5];
+#pragma unroll
+                              for (int kk = 0; kk < KPL; ++kk)
+                                  hv[kk] = *reinterpret_cast<const float4 *>(&sH[(kk * 8 + kg) * RS + q]);
+#pragma unroll
+                              for (int dd = 0; dd < 5; ++dd)
+                                  mv[dd] = *reinterpret_cast<const float4 *>(&sM[(dd * 4 + g) * RS + q]);
+#pragma unroll
+                              for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                                  for (int dd = 0; dd < 5; ++dd) {
+                                      float x = acc[s][kk][dd];
+                                      x = fmaf(hv[kk].x, mv[dd].x, x);
+                                      x = fmaf(hv[kk].y, mv[dd].y, x);
+                                      x = fmaf(hv[kk].z, mv[dd].z, x);
+                                      x = fmaf(hv[kk].w, mv[dd].w, x);
+                                      acc[s][kk][dd] = x;
+                                  }
+                          }
+                          for (; q < stop; ++q) {
+                              float hv[KPL], mv[5];
+#pragma unroll
+                              for (int kk = 0; kk < KPL; ++kk) hv[kk] = sH[(kk * 8 + kg) * RS + q];
+#pragma unroll
+                              for (int dd = 0; dd < 5; ++dd) mv[dd] = sM[(dd * 4 + g) * RS + q];
+#pragma unroll
+                              for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                                  for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = fmaf(hv[kk], mv[dd], acc[s][kk][dd]);
+                          }
+                          start += (cnt[s] + 3) & ~3;
+                      }
+                      __syncwarp();
+                  },
+                  nl.pq != nullptr);
+        if (nl.npair && lane == 0) nl.npair[a] = written;
+        // P[b][k][d] for the backward pass
+        float *Pa = Pout + (size_t)a * (S * K * NMOM);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) Pa[(s * K + kg * KPL + kk) * NMOM + 5 * g + dd] = acc[s][kk][dd];
+        // G[b][k][m] = sigma(sum_{d in rank m} T_d P^2)
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk) {
+                float sq[5];
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) sq[dd] = Tg[dd] * acc[s][kk][dd] * acc[s][kk][dd];
+                const float tot = sq[0] + sq[1] + sq[2] + sq[3] + sq[4];
+                float p0 = (g == 0) ? sq[0] : 0.f;
+                float p1 = (g == 0) ? sq[1] + sq[2] + sq[3] : 0.f;
+                float p2 = (g == 0) ? sq[4] : ((g == 1) ? tot : 0.f);
+                float p3 = (g >= 2) ? tot : 0.f;
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1) {
+                    p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+                    p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+                    p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+                    p3 += __shfl_xor_sync(0xffffffffu, p3, o);
+                }
+                const float val = (g == 0) ? sqrtf(p0) : ((g == 1) ? p1 : ((g == 2) ? p2 : p3));
+                G[(size_t)a * Dd + (s * K + kg * KPL + kk) * 4 + g] = val;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward: P', pair gradients, ScatterSum, virial
+// ---------------------------------------------------------------------------
+// round(g * 2^32) as int64 without a conversion instruction (on this GPU
+// float <-> int64 conversions issue on the slow FP64 pipe): three exact
+// 16-bit stages with the 1.5 * 2^23 rounding constant (valid for |g| < 2^21).
+__device__ __forceinline__ int round_magic(float v, float &vr) {
+    const float t = v + 12582912.0f;   // integer part in the low significand bits
+    vr = t - 12582912.0f;              // round(v) as a float
+    return __float_as_int(t) - 0x4B400000;
+}
+
+__device__ __forceinline__ long long to_fixed(float g) {
+    float f1, f2, f3;
+    const int h1 = round_magic(g, f1);
+    const float v2 = (g - f1) * 65536.0f;      // exact, |v2| <= 2^15
+    const int h2 = round_magic(v2, f2);
+    const float v3 = (v2 - f2) * 65536.0f;     // exact, |v3| <= 2^15
+    const int h3 = round_magic(v3, f3);
+    return (long long)h1 * 4294967296LL + (long long)h2 * 65536LL + (long long)h3;
+}
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// g_ij = dE/dD_ij of one in-cutoff pair (Eqs. dP_abkd, U_abck, F1_abcx,
+// F2_abcx): Pb = the centre atom's P' for the neighbour's species, rad = the
+// radial parameters of the (centre, neighbour) species pair.
+template <int K, bool TAB>
+__device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, const float2 e2, const float *Pb,
+                                          const float4 *rad, const float *tab, float &gxs, float &gys, float &gzs) {
+    float r_hi, r_lo, ir;
+    split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
+    const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
+    // V_d = sum_k P'_kd H_k and W_d = sum_k P'_kd H'_k, so that
+    // F1 = U H' R' = sum_d W_d M_d and F2 = V M'
+    float V[NMOM], Wd[NMOM];
+#pragma unroll
+    for (int d = 0; d < NMOM; ++d) V[d] = Wd[d] = 0.f;
+    float fc = 0.f, dfc = 0.f;
+    TabCell tc;
+    if (TAB)
+        tc = tab_cell(tab, K, m.rtab_scale, r_hi, r_lo);
+    else
+        cutoff_fn(r_hi, m.inv_rc, fc, dfc);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        // H_k and H'_k formed inside the loop (no per-pair arrays)
+        float Hk, dHk;
+        if (TAB) {
+            tab_eval(tc, k, m.rtab_scale, Hk, dHk);
+        } else {
+            const float4 rp = rad[k];
+            const float t = (r_hi - rp.x) + (r_lo - rp.y);
+            const float f = ex2_ftz(-rp.z * t * t);
+            Hk = f * fc;
+            dHk = f * fmaf(-rp.w * t, fc, dfc);
+        }
+#pragma unroll
+        for (int q4 = 0; q4 < NMOM / 4; ++q4) {
+            const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
+            V[4 * q4] = fmaf(pd.x, Hk, V[4 * q4]);
+            V[4 * q4 + 1] = fmaf(pd.y, Hk, V[4 * q4 + 1]);
+            V[4 * q4 + 2] = fmaf(pd.z, Hk, V[4 * q4 + 2]);
+            V[4 * q4 + 3] = fmaf(pd.w, Hk, V[4 * q4 + 3]);
+            Wd[4 * q4] = fmaf(pd.x, dHk, Wd[4 * q4]);
+            Wd[4 * q4 + 1] = fmaf(pd.y, dHk, Wd[4 * q4 + 1]);
+            Wd[4 * q4 + 2] = fmaf(pd.z, dHk, Wd[4 * q4 + 2]);
+            Wd[4 * q4 + 3] = fmaf(pd.w, dHk, Wd[4 * q4 + 3]);
+        }
+    }
+    float M[NMOM];
+    moments20(ux, uy, uz, M);
+    float w0 = Wd[0], w1 = 0.f, w2 = 0.f, w3 = 0.f;
+#pragma unroll
+    for (int d = 1; d < NMOM; d += 4) {
+        w1 = fmaf(Wd[d], M[d], w1);
+        w2 = fmaf(Wd[d + 1], M[d + 1], w2);
+        w3 = fmaf(Wd[d + 2], M[d + 2], w3);
+        if (d + 3 < NMOM) w0 = fmaf(Wd[d + 3], M[d + 3], w0);
+    }
+    const float dEdr = (w0 + w1) + (w2 + w3);
+    // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
+    const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
+    const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
+                     2.f * xy * V[11] + 2.f * xz * V[12] + yy * V[13] + yz * V[14] + zz * V[15];
+    const float gy = V[2] + ux * V[5] + 2.f * uy * V[7] + uz * V[8] + xx * V[11] + 2.f * xy * V[13] +
+                     xz * V[14] + 3.f * yy * V[16] + 2.f * yz * V[17] + zz * V[18];
+    const float gz = V[3] + ux * V[6] + uy * V[8] + 2.f * uz * V[9] + xx * V[12] + xy * V[14] +
+                     2.f * xz * V[15] + yy * V[17] + 2.f * yz * V[18] + 3.f * zz * V[19];
+    const float ug = ux * gx + uy * gy + uz * gz;
+    // g_ij = dE/dD_ij = dE/dr u + (I - u u^T) dE/du / r
+    gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
+    gys = fmaf(dEdr, uy, (gy - uy * ug) * ir);
+    gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
+}
+
+// P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm (for m = 0: G'_bk0 sign(P)) of atom a
+// into a shared slot, each lane its (K/8 x 5) block  (Eq. dP_abkd)
+template <int K, int S>
+__device__ __forceinline__ void pprime_setup(const float *__restrict__ Pin, const float *__restrict__ dG, int a,
+                                             float *slot, int kg, int g, const float (&Tg)[5]) {
+    constexpr int KPL = K / 8;
+    constexpr int PSTR = K * NMOM + 4;
+    constexpr int Dd = S * K * 4;
+    const float *Pa = Pin + (size_t)a * (S * K * NMOM);
+    const float *dGa = dG + (size_t)a * Dd;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int kk = 0; kk < KPL; ++kk) {
+            const int k = kg * KPL + kk;
+            const float4 gm = *reinterpret_cast<const float4 *>(dGa + (s * K + k) * 4);
+#pragma unroll
+            for (int dd = 0; dd < 5; ++dd) {
+                const int d = 5 * g + dd;
+                const float pv = Pa[(s * K + k) * NMOM + d];
+                float gg;
+                if (g == 0) gg = (dd == 0) ? gm.x : ((dd < 4) ? gm.y : gm.z);
+                else gg = (g == 1) ? gm.z : gm.w;
+                float v;
+                if (g == 0 && dd == 0) v = (pv > 0.f) ? gg : ((pv < 0.f) ? -gg : 0.f);
+                else v = 2.f * Tg[dd] * pv * gg;
+                slot[s * PSTR + k * NMOM + d] = v;
+            }
+        }
+}
+
+// Force pass over the pair cache with full lane batches: each warp walks a
+// contiguous run of atoms (perm order) and fills every batch of 32 lanes with
+// the rest of the current atom's pairs followed by the first pairs of the
+// next atom (two P' slots per warp, two self-force accumulators).
+template <int K, int S, bool TAB>
+__global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlist nl, const int32_t *__restrict__ types,
+                                                          const float *__restrict__ Pin, const float *__restrict__ dG,
+                                                          unsigned long long *__restrict__ Fq,
+                                                          double *__restrict__ part_w) {
+    constexpr int PSTR = K * NMOM + 4;
+    __shared__ float4 s_rad[S * S * K];
+    __shared__ __align__(16) float s_Pd[PW][2][S * PSTR];
+    __shared__ double s_w[PW][9];
+    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = lane >> 2, g = lane & 3;
+    float Tg[5];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
+    float wsum[9], wcmp[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) { wsum[t] = 0.f; wcmp[t] = 0.f; }
+    const int64_t nw = (int64_t)gridDim.x * PW, wid = (int64_t)blockIdx.x * PW + warp;
+    const int64_t chunk = (nl.n + nw - 1) / nw;
+    int64_t p = wid * chunk;
+    const int64_t pend = min(nl.n, p + chunk);
+    if (p < pend) {
+        int slot = 0;
+        int a = nl.perm[p], ta = types[a];
+        pprime_setup<K, S>(Pin, dG, a, s_Pd[warp][0], kg, g, Tg);
+        int64_t cb = nl.beg[a];
+        int cr = nl.npair[a];
+        long long fcx = 0, fcy = 0, fcz = 0;
+        while (p < pend) {
+            const int take_c = min(cr, 32);
+            const bool has_n = cr < 32 && p + 1 < pend;
+            int take_n = 0, an = 0, tn = 0, nr = 0;
+            int64_t nb = 0;
+            if (has_n) {   // bring in the next atom
+                an = nl.perm[p + 1];
+                tn = types[an];
+                pprime_setup<K, S>(Pin, dG, an, s_Pd[warp][slot ^ 1], kg, g, Tg);
+                nb = nl.beg[an];
+                nr = nl.npair[an];
+                take_n = min(nr, 32 - cr);
+            }
+            __syncwarp();
+            long long fnx = 0, fny = 0, fnz = 0;
+            float wa[9];   // this lane's pair of this batch
+#pragma unroll
+            for (int t = 0; t < 9; ++t) wa[t] = 0.f;
+            const bool isc = lane < take_c, isn = !isc && lane < take_c + take_n;
+            if (isc || isn) {
+                const int64_t c = isc ? cb + lane : nb + (lane - take_c);
+                const float4 e = nl.pq[c];
+                const float2 e2 = nl.pq2[c];
+                const uint32_t jb = __float_as_uint(e.w);
+                const int b = (int)(jb >> 28);
+                const int j = (int)(jb & 0x0FFFFFFFu);
+                const float *Pb = s_Pd[warp][isc ? slot : slot ^ 1] + b * PSTR;
+                const int tp = (isc ? ta : tn) * S + b;
+                float gxs, gys, gzs;
+                pair_grad<K, TAB>(m, e, e2, Pb, &s_rad[tp * K], TAB ? m.rtab + (size_t)tp * m.rtab_n * 4 * K : nullptr,
+                                  gxs, gys, gzs);
+                // ScatterSum in 2^-32 fixed point (exact, order independent)
+                const long long qx = to_fixed(gxs);
+                const long long qy = to_fixed(gys);
+                const long long qz = to_fixed(gzs);
+                if (isc) { fcx += qx; fcy += qy; fcz += qz; }
+                else { fnx = qx; fny = qy; fnz = qz; }
+                atomicAdd(&Fq[3 * (int64_t)j], (unsigned long long)(-qx));
+                atomicAdd(&Fq[3 * (int64_t)j + 1], (unsigned long long)(-qy));
+                atomicAdd(&Fq[3 * (int64_t)j + 2], (unsigned long long)(-qz));
+                const float D[3] = {e.x, e.y, e.z};
+                const float gv[3] = {gxs, gys, gzs};
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) wa[al * 3 + be] = -D[al] * gv[be];
+            }
+#pragma unroll
+            for (int t = 0; t < 9; ++t) kahan_add(wsum[t], wcmp[t], wa[t]);
+            cb += take_c;
+            cr -= take_c;
+            if (cr == 0) {   // the current atom is complete: its own force
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    fcx += __shfl_xor_sync(0xffffffffu, fcx, o);
+                    fcy += __shfl_xor_sync(0xffffffffu, fcy, o);
+                    fcz += __shfl_xor_sync(0xffffffffu, fcz, o);
+                }
+                if (lane == 0) {
+                    atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fcx);
+                    atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fcy);
+                    atomicAdd(&Fq[3 * (int64_t)a + 2], (unsigned long long)fcz);
+                }
+                ++p;
+                if (p < pend) {
+                    if (has_n) {   // the next atom (already set up) becomes the current one
+                        a = an;
+                        ta = tn;
+                        slot ^= 1;
+                        cb = nb + take_n;
+                        cr = nr - take_n;
+                        fcx = fnx; fcy = fny; fcz = fnz;
+                    } else {
+                        __syncwarp();
+                        a = nl.perm[p];
+                        ta = types[a];
+                        pprime_setup<K, S>(Pin, dG, a, s_Pd[warp][slot], kg, g, Tg);
+                        cb = nl.beg[a];
+                        cr = nl.npair[a];
+                        fcx = fcy = fcz = 0;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // virial: per-lane compensated sums -> warp total as an FP32 double-float -> FP64 block total
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        float hi = wsum[t], lo = -wcmp[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float sh, se;
+            two_sum(hi, oh, sh, se);
+            lo = (lo + ol) + se;
+            two_sum(sh, lo, hi, lo);
+        }
+        if (lane == 0) s_w[warp][t] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double v = 0.0;
+        for (int w = 0; w < PW; ++w) v += s_w[w][threadIdx.x];
+        part_w[(size_t)blockIdx.x * 9 + threadIdx.x] = v;
+    }
+}
+
+// PAW (batched): each atom's virial is summed over its own pairs and written
+// to w_atom [atoms][9] for per-system reductions; otherwise lanes keep
+// compensated running sums and each block writes one FP64 partial.
+template <int K, int S, bool PAW, bool CACHED, bool TAB>
+__global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, const double *__restrict__ pos,
+                                                   const int32_t *__restrict__ types, const float *__restrict__ Pin,
+                                                   const float *__restrict__ dG,
+                                                   unsigned long long *__restrict__ Fq,
+                                                   double *__restrict__ part_w, float *__restrict__ w_atom) {
+    constexpr int KPL = K / 8;
+    constexpr int PSTR = K * NMOM + 4;   // per-species stride of P' (bank offset between species)
+    constexpr int Dd = S * K * 4;
+    __shared__ float4 s_rad[S * S * K];
+    __shared__ float4 s_q[PW][64];
+    __shared__ float2 s_q2[PW][64];
+    __shared__ __align__(16) float s_Pd[PW][S * PSTR];
+    __shared__ double s_w[PW][9];
+    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = lane >> 2, g = lane & 3;
+    float Tg[5];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
+    float wsum[9], wcmp[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) { wsum[t] = 0.f; wcmp[t] = 0.f; }
+    float *sPd = s_Pd[warp];
+    const int64_t total = (int64_t)gridDim.x * PW;
+    for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
+        const int a = nl.perm[p];
+        const int ti = types[a];
+        // P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm; for m = 0: G'_bk0 sign(P)  (Eq. dP_abkd)
+        const float *Pa = Pin + (size_t)a * (S * K * NMOM);
+        const float *dGa = dG + (size_t)a * Dd;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk) {
+                const int k = kg * KPL + kk;
+                const float4 gm = *reinterpret_cast<const float4 *>(dGa + (s * K + k) * 4);
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) {
+                    const int d = 5 * g + dd;
+                    const float pv = Pa[(s * K + k) * NMOM + d];
+                    // rank of d: g==0 -> {0,1,1,1,2}, g==1 -> 2, g>=2 -> 3
+                    float gg;
+                    if (g == 0) gg = (dd == 0) ? gm.x : ((dd < 4) ? gm.y : gm.z);
+                    else gg = (g == 1) ? gm.z : gm.w;
+                    float v;
+                    if (g == 0 && dd == 0) v = (pv > 0.f) ? gg : ((pv < 0.f) ? -gg : 0.f);
+                    else v = 2.f * Tg[dd] * pv * gg;
+                    sPd[s * PSTR + k * NMOM + d] = v;
+                }
+            }
+        __syncwarp();
+        long long fx = 0, fy = 0, fz = 0;
+        float wa[9];  // this lane's pairs of this atom
+#pragma unroll
+        for (int t = 0; t < 9; ++t) wa[t] = 0.f;
+        auto pair_fn = [&](const float4 e, const float2 e2, bool valid, int) {
+                      if (!valid) return;
+                      const uint32_t jb = __float_as_uint(e.w);
+                      const int b = (int)(jb >> 28);
+                      const int j = (int)(jb & 0x0FFFFFFFu);
+                      float gxs, gys, gzs;
+                      pair_grad<K, TAB>(m, e, e2, sPd + b * PSTR, &s_rad[(ti * S + b) * K],
+                                        TAB ? m.rtab + (size_t)(ti * S + b) * m.rtab_n * 4 * K : nullptr, gxs, gys, gzs);
+                      // ScatterSum in 2^-32 fixed point: integer adds are exact and
+                      // order independent, so forces are bitwise reproducible.
+                      const long long qx = to_fixed(gxs);
+                      const long long qy = to_fixed(gys);
+                      const long long qz = to_fixed(gzs);
+                      fx += qx; fy += qy; fz += qz;
+                      atomicAdd(&Fq[3 * (int64_t)j], (unsigned long long)(-qx));
+                      atomicAdd(&Fq[3 * (int64_t)j + 1], (unsigned long long)(-qy));
+                      atomicAdd(&Fq[3 * (int64_t)j + 2], (unsigned long long)(-qz));
+                      const float D[3] = {e.x, e.y, e.z};
+                      const float gv[3] = {gxs, gys, gzs};
+#pragma unroll
+                      for (int al = 0; al < 3; ++al)
+#pragma unroll
+                          for (int be = 0; be < 3; ++be) wa[al * 3 + be] = fmaf(-D[al], gv[be], wa[al * 3 + be]);
+                  };
+        if constexpr (CACHED)
+            cached_pairs(nl, a, lane, pair_fn);
+        else
+            for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane, pair_fn);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fx);
+            atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fy);
+            atomicAdd(&Fq[3 * (int64_t)a + 2], (unsigned long long)fz);
+        }
+        if constexpr (PAW) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                float v = wa[t];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) w_atom[(size_t)a * 9 + t] = v;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) kahan_add(wsum[t], wcmp[t], wa[t]);
+        }
+        __syncwarp();
+    }
+    // virial: per-lane compensated sums (value = sum - comp) -> warp total as
+    // an FP32 double-float (error-free additions) -> FP64 block total
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        float hi = wsum[t], lo = -wcmp[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float sh, se;
+            two_sum(hi, oh, sh, se);
+            lo = (lo + ol) + se;
+            two_sum(sh, lo, hi, lo);
+        }
+        if (lane == 0) s_w[warp][t] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (!PAW && threadIdx.x < 9) {
+        double v = 0.0;
+        for (int w = 0; w < PW; ++w) v += s_w[w][threadIdx.x];
+        part_w[(size_t)blockIdx.x * 9 + threadIdx.x] = v;
+    }
+}
+
+template <int K, int S>
+tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
+                               tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool forward,
+                               float *w_atom) {
+    if (forward && dm.rtab)
+        TMD_LAUNCH("k_desc", s, k_desc<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+    else if (forward)
+        TMD_LAUNCH("k_desc", s, k_desc<K, S, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+    else if (w_atom && dm.rtab)   // batched evaluations always run with the pair cache
+        TMD_LAUNCH("k_force", s, k_force<K, S, true, true, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                        nl->dG, nl->Fq, part_w, w_atom));
+    else if (w_atom)
+        TMD_LAUNCH("k_force", s, k_force<K, S, true, true, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                         nl->dG, nl->Fq, part_w, w_atom));
+    else if (dn.pq && dm.rtab)
+        TMD_LAUNCH("k_force", s, k_force_merged<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, types, nl->P, nl->dG,
+                                                                                   nl->Fq, part_w));
+    else if (dn.pq)
+        TMD_LAUNCH("k_force", s, k_force_merged<K, S, false><<<nblk, PW * 32, 0, s>>>(dm, dn, types, nl->P, nl->dG,
+                                                                                    nl->Fq, part_w));
+    else if (dm.rtab)
+        TMD_LAUNCH("k_force", s, k_force<K, S, false, false, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                          nl->dG, nl->Fq, part_w, nullptr));
+    else
+        TMD_LAUNCH("k_force", s, k_force<K, S, false, false, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
+                                                                                           nl->dG, nl->Fq, part_w, nullptr));
+    TMD_CUDA(cudaGetLastError());
+    return TMD_OK;
+}
+
+}  // namespace
+
+}  // namespace tmd

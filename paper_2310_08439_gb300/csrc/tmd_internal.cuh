@@ -50,6 +50,7 @@ struct DevModel {
 };
 
 // persistent grid of the pair kernels for n atoms
+constexpr int PAIR_WARPS = 4;   // warps (atoms in flight) per block of the pair kernels
 int pair_blocks(const DevModel &dm, int64_t n);
 // shared memory of the FP32 network kernel with tr-atom tiles
 size_t mlp_smem_tr_public(const DevModel &dm, int tr);
@@ -267,6 +268,15 @@ void sys_reduce_launch(const int32_t *act, int n_act, const int64_t *off, const 
                        const double *vel, const double *mass, double *out, cudaStream_t s);
 tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, const double box[3],
                            const int32_t pbc[3], double r_list, tmd_nlist *nl, cudaStream_t s);
+// descriptor (fwd) or force pass of one evaluation, one function per radial
+// channel count K (pair_k<K>.cu); UNIMPLEMENTED for a species count without
+// an instance
+#define TMD_PAIR_LAUNCHER(name)                                                                            \
+    tmd_status name(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,       \
+                    tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool fwd, float *w_atom)
+TMD_PAIR_LAUNCHER(launch_pair_k8);
+TMD_PAIR_LAUNCHER(launch_pair_k16);
+TMD_PAIR_LAUNCHER(launch_pair_k32);
 tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, int64_t n_active);
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                        int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
