@@ -76,7 +76,8 @@ const char *tmd_version(void);
 /*
  * Description of a TensorMD potential (all pointers host, read at create).
  *  n_species  S, 1..TMD_MAX_SPECIES.  Species ids are 0..S-1.
- *  n_radial   K radial channels; this build supports K in {8, 16, 32}.
+ *  n_radial   K radial channels; this build supports K in {8, 16, 32, 64,
+ *             128} with at most 4, 4, 3, 2, 1 species respectively.
  *  rc         cutoff radius (A); pairs with R >= rc contribute nothing.
  *  mu, eta    [S][S][K] Gaussian centre and width of f_k(R) = exp(-eta (R-mu)^2)
  *             for (centre species, neighbour species, k).  f_c(R) =
@@ -114,7 +115,8 @@ typedef struct tmd_nlist tmd_nlist;   /* opaque; device neighbour table + worksp
 typedef struct tmd_system tmd_system; /* opaque; resident MD state */
 
 /* Copy a model to the current device.  Errors: INVALID_ARG (bad sizes or a
- * non-finite weight), UNIMPLEMENTED (K outside {8,16,32}), OOM, CUDA.
+ * non-finite weight), UNIMPLEMENTED (K or S outside the supported pairs, or a
+ * network whose activations do not fit on chip), OOM, CUDA.
  * Synchronises the device once. */
 tmd_status tmd_model_create(const tmd_model_desc *desc, tmd_model **out);
 tmd_status tmd_model_destroy(tmd_model *model);

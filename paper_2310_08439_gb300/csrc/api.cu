@@ -304,8 +304,13 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     *out = nullptr;
     const int S = d->n_species, K = d->n_radial, L = d->n_hidden;
     if (S < 1 || S > TMD_MAX_SPECIES) { set_error("n_species %d outside [1, %d]", S, TMD_MAX_SPECIES); return TMD_ERR_INVALID_ARG; }
-    if (K != 8 && K != 16 && K != 32) { set_error("n_radial %d: this build supports 8, 16, 32", K); return TMD_ERR_UNIMPLEMENTED; }
-    if (K == 32 && S > 3) { set_error("n_radial 32 supports at most 3 species"); return TMD_ERR_UNIMPLEMENTED; }
+    if (K != 8 && K != 16 && K != 32 && K != 64 && K != 128) {
+        set_error("n_radial %d: this build supports 8, 16, 32, 64, 128", K);
+        return TMD_ERR_UNIMPLEMENTED;
+    }
+    // species counts with kernel instances (the network input S K 4 <= 512)
+    const int s_max = K <= 16 ? 4 : (K == 32 ? 3 : (K == 64 ? 2 : 1));
+    if (S > s_max) { set_error("n_radial %d supports at most %d species", K, s_max); return TMD_ERR_UNIMPLEMENTED; }
     if (!(std::isfinite(d->rc) && d->rc > 0.0)) { set_error("rc must be finite and > 0"); return TMD_ERR_INVALID_ARG; }
     if (L < 1 || L > TMD_MAX_HIDDEN) { set_error("n_hidden %d outside [1, %d]", L, TMD_MAX_HIDDEN); return TMD_ERR_INVALID_ARG; }
     if (!d->widths || !d->weights || !d->mu || !d->eta) { set_error("null widths/weights/mu/eta"); return TMD_ERR_INVALID_ARG; }
@@ -404,6 +409,12 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     m->mu.assign(d->mu, d->mu + (size_t)S * S * K);
     m->eta.assign(d->eta, d->eta + (size_t)S * S * K);
     m->rc_exact = d->rc;
+    if (tmd::mlp_smem_tr_public(m->dm, 32) > 227 * 1024) {
+        set_error("network too wide: the activations of a 32-atom tile exceed the shared memory of an SM");
+        cudaFree(m->dev_block);
+        delete m;
+        return TMD_ERR_UNIMPLEMENTED;
+    }
     if (d->precision == TMD_PREC_BF16) {
         tmd_status st = tmd_model_set_precision(m, TMD_PREC_BF16);
         if (st != TMD_OK) { cudaFree(m->dev_block); delete m; return st; }
@@ -493,6 +504,10 @@ tmd_status tmd_model_set_precision(tmd_model *m, int32_t precision) {
                           m->dm.dims[l]);
                 return TMD_ERR_UNIMPLEMENTED;
             }
+    if (precision == TMD_PREC_BF16 && tmd::mlp_bf16_smem_bytes(m->dm) > 227 * 1024) {
+        set_error("network too wide for the BF16 tile (64 atoms) in the shared memory of an SM");
+        return TMD_ERR_UNIMPLEMENTED;
+    }
     m->precision = precision;
     m->dm.precision = precision;
     return TMD_OK;

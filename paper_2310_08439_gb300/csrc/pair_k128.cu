@@ -1,0 +1,16 @@
+// Pair kernels (descriptor forward, force backward) for K = 128 radial
+// channels: the instances of pair_kernels.cuh for every supported species count.
+#include "pair_kernels.cuh"
+
+namespace tmd {
+
+TMD_PAIR_LAUNCHER(launch_pair_k128) {
+    switch (dm.S) {
+    case 1: return launch_pair_kernels<128, 1>(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
+    default: break;
+    }
+    set_error("no kernel for K=%d S=%d", dm.K, dm.S);
+    return TMD_ERR_UNIMPLEMENTED;
+}
+
+}  // namespace tmd

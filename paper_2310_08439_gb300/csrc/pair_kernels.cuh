@@ -132,13 +132,15 @@ __device__ __forceinline__ void tab_eval(const TabCell &tc, int k, float scale, 
     dH = scale * fmaf(tc.t, fmaf(tc.t3, q.w, 2.f * q.z), q.y);
 }
 
-template <int K, bool DERIV>
-__device__ __forceinline__ void radial_tab(const float *tab, float scale, float r_hi, float r_lo, float *H, float *dH) {
+// channels k0 .. k0 + KC - 1 of a table of K channels
+template <int KC, bool DERIV>
+__device__ __forceinline__ void radial_tab(const float *tab, int K, int k0, float scale, float r_hi, float r_lo,
+                                           float *H, float *dH) {
     const TabCell tc = tab_cell(tab, K, scale, r_hi, r_lo);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < KC; ++k) {
         float h, d;
-        tab_eval(tc, k, scale, h, d);
+        tab_eval(tc, k0 + k, scale, h, d);
         H[k] = h;
         if (DERIV) dH[k] = d;
     }
@@ -267,9 +269,8 @@ __device__ __forceinline__ int for_pairs(const DevNlist &nl, int a, int64_t beg,
 // The in-cutoff pairs of atom a from the pair cache written by the
 // descriptor pass, in batches of up to 32 (one per lane).
 template <typename F>
-__device__ __forceinline__ void cached_pairs(const DevNlist &nl, int a, int lane, F &&f) {
+__device__ __forceinline__ void cached_pairs(const DevNlist &nl, int a, int np, int lane, F &&f) {
     const int64_t pb = nl.beg[a];
-    const int np = nl.npair[a];
     for (int base = 0; base < np; base += 32) {
         const int nb = min(32, np - base);
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -285,11 +286,16 @@ __device__ __forceinline__ void cached_pairs(const DevNlist &nl, int a, int lane
 // ---------------------------------------------------------------------------
 // descriptor forward: P and G per atom
 // ---------------------------------------------------------------------------
+// K > 32 runs in chunks of 32 channels: the first chunk walks the neighbour
+// table (and fills the pair cache), later chunks replay the atom's pairs from
+// the cache (or walk the table again when there is none), so that the
+// per-lane accumulators and the staged columns stay those of K = 32.
 template <int K, int S, bool TAB>
 __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                   const int32_t *__restrict__ types, float *__restrict__ G,
                                                   float *__restrict__ Pout) {
-    constexpr int KPL = K / 8;   // k values per lane
+    constexpr int KC = K > 32 ? 32 : K;   // channels per chunk
+    constexpr int KPL = KC / 8;           // k values per lane
     constexpr int RS = 44;       // row stride of the staged pair columns (>= 32 + 3 (S - 1) slots)
     constexpr int Dd = S * K * 4;
     __shared__ float4 s_rad[S * S * K];
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
     // staged pair data, one column per pair: H_k in row (k % KPL) 8 + k / KPL,
     // M_d in row (d % 5) 4 + d / 5, so that the lane owning k-group kg and
     // d-group g reads four pairs of a row with one conflict-free vector load
-    __shared__ __align__(16) float s_H[PW][K * RS];
+    __shared__ __align__(16) float s_H[PW][KC * RS];
     __shared__ __align__(16) float s_M[PW][NMOM * RS];
     for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
     __syncthreads();
@@ -312,6 +318,8 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
     for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
         const int a = nl.perm[p];
         const int ti = types[a];
+        int written = 0;
+        for (int k0 = 0; k0 < K; k0 += KC) {
         float acc[S][KPL][5];
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -321,9 +329,7 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                 for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
         float *sH = s_H[warp];
         float *sM = s_M[warp];
-        // the in-cutoff pairs also go to the pair cache, when there is one
-        const int written = for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane,
-                  [&](const float4 e, const float2 e2, bool valid, int) {
+        auto pair_fn = [&](const float4 e, const float2 e2, bool valid, int) {
                       const uint32_t jb = __float_as_uint(e.w);
                       const int b = valid ? (int)(jb >> 28) : S;
                       // columns grouped by neighbour species, each group starting
@@ -339,15 +345,15 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                       if (valid) {
                           float r_hi, r_lo, ir;
                           split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
-                          float H[K], M[NMOM];
+                          float H[KC], M[NMOM];
                           if (TAB)
-                              radial_tab<K, false>(m.rtab + (size_t)(ti * S + b) * m.rtab_n * 4 * K, m.rtab_scale,
-                                                   r_hi, r_lo, H, nullptr);
+                              radial_tab<KC, false>(m.rtab + (size_t)(ti * S + b) * m.rtab_n * 4 * K, K, k0,
+                                                    m.rtab_scale, r_hi, r_lo, H, nullptr);
                           else
-                              radial<K, false>(&s_rad[(ti * S + b) * K], r_hi, r_lo, m.inv_rc, H, nullptr);
+                              radial<KC, false>(&s_rad[(ti * S + b) * K + k0], r_hi, r_lo, m.inv_rc, H, nullptr);
                           moments20(e.x * ir, e.y * ir, e.z * ir, M);
 #pragma unroll
-                          for (int k = 0; k < K; ++k) sH[((k % KPL) * 8 + k / KPL) * RS + slot] = H[k];
+                          for (int k = 0; k < KC; ++k) sH[((k % KPL) * 8 + k / KPL) * RS + slot] = H[k];
 #pragma unroll
                           for (int d = 0; d < NMOM; ++d) sM[((d % 5) * 4 + d / 5) * RS + slot] = M[d];
                       }
@@ -392,9 +398,12 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                           start += (cnt[s] + 3) & ~3;
                       }
                       __syncwarp();
-                  },
-                  nl.pq != nullptr);
-        if (nl.npair && lane == 0) nl.npair[a] = written;
+                  };
+        if (k0 == 0 || !nl.pq)   // the in-cutoff pairs also go to the pair cache, when there is one
+            written = for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane, pair_fn,
+                                k0 == 0 && nl.pq != nullptr);
+        else
+            cached_pairs(nl, a, written, lane, pair_fn);   // this warp's own cache writes (ordered by __syncwarp)
         // P[b][k][d] for the backward pass
         float *Pa = Pout + (size_t)a * (S * K * NMOM);
 #pragma unroll
@@ -402,7 +411,8 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
 #pragma unroll
             for (int kk = 0; kk < KPL; ++kk)
 #pragma unroll
-                for (int dd = 0; dd < 5; ++dd) Pa[(s * K + kg * KPL + kk) * NMOM + 5 * g + dd] = acc[s][kk][dd];
+                for (int dd = 0; dd < 5; ++dd)
+                    Pa[(s * K + k0 + kg * KPL + kk) * NMOM + 5 * g + dd] = acc[s][kk][dd];
         // G[b][k][m] = sigma(sum_{d in rank m} T_d P^2)
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -424,9 +434,11 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                     p3 += __shfl_xor_sync(0xffffffffu, p3, o);
                 }
                 const float val = (g == 0) ? sqrtf(p0) : ((g == 1) ? p1 : ((g == 2) ? p2 : p3));
-                G[(size_t)a * Dd + (s * K + kg * KPL + kk) * 4 + g] = val;
+                G[(size_t)a * Dd + (s * K + k0 + kg * KPL + kk) * 4 + g] = val;
             }
         }
+        }
+        if (nl.npair && lane == 0) nl.npair[a] = written;
     }
 }
 
@@ -479,8 +491,12 @@ __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, con
         tc = tab_cell(tab, K, m.rtab_scale, r_hi, r_lo);
     else
         cutoff_fn(r_hi, m.inv_rc, fc, dfc);
+    constexpr int KU = K > 32 ? 32 : K;   // channels per unrolled block
+#pragma unroll 1
+    for (int kb = 0; kb < K; kb += KU)
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int ku = 0; ku < KU; ++ku) {
+        const int k = kb + ku;
         // H_k and H'_k formed inside the loop (no per-pair arrays)
         float Hk, dHk;
         if (TAB) {
@@ -789,7 +805,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
                           for (int be = 0; be < 3; ++be) wa[al * 3 + be] = fmaf(-D[al], gv[be], wa[al * 3 + be]);
                   };
         if constexpr (CACHED)
-            cached_pairs(nl, a, lane, pair_fn);
+            cached_pairs(nl, a, nl.npair[a], lane, pair_fn);
         else
             for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane, pair_fn);
 #pragma unroll

@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 3 : 2) k_mlp(DevModel 
 // ---------------------------------------------------------------------------
 constexpr int BT = 64;            // atoms per BF16 tile
 constexpr int BF_THREADS = 256;   // 8 warps: 4 row slabs x 2 column halves
-constexpr int BF_NC = 64;         // output columns per streamed weight chunk
+constexpr int BF_NC = 64;         // output columns per streamed weight chunk (fewer for wide inputs)
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -406,13 +406,19 @@ __device__ __forceinline__ BfStep bf_step(const DevModel &m, int s, int step) {
     return {m.hf[s] + m.off_f[l], m.dims[l + 1], m.dims[l]};
 }
 
-// Bt rows [n0, n0 + min(BF_NC, N - n0)) into buf (row stride K + 8), one
-// warp per row (K <= 256: a row is at most 32 16-byte copies)
-__device__ __forceinline__ void bf_issue(const BfStep &st, int n0, uint16_t *buf) {
-    const int nc = min(BF_NC, st.N - n0), c8 = st.K >> 3;
+// Bt rows [n0, n0 + min(bnc, N - n0)) into buf (row stride K + 8), one
+// warp per row in 16-byte copies
+__device__ __forceinline__ void bf_issue(const BfStep &st, int n0, int bnc, uint16_t *buf) {
+    const int nc = min(bnc, st.N - n0), c8 = st.K >> 3;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int r = warp; r < nc; r += BF_THREADS / 32)
-        if (lane < c8) cp_async16(buf + r * (st.K + 8) + 8 * lane, st.Bt + (size_t)(n0 + r) * st.K + 8 * lane);
+        for (int c = lane; c < c8; c += 32)
+            cp_async16(buf + r * (st.K + 8) + 8 * c, st.Bt + (size_t)(n0 + r) * st.K + 8 * c);
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const uint16_t *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
 struct BfStream {
@@ -422,7 +428,13 @@ struct BfStream {
 __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const int32_t *__restrict__ perm,
                                                          const int32_t *__restrict__ types, int64_t n,
                                                          const float *__restrict__ G, float *__restrict__ dG,
-                                                         float *__restrict__ e_atom, double *__restrict__ part_e) {
+                                                         float *__restrict__ e_atom, double *__restrict__ part_e,
+                                                         int bnc, int compact) {
+    // bnc: output columns per streamed weight chunk (BF_NC, or 32 / 16 when
+    // the input is wide enough that two BF_NC-column buffers would not fit).
+    // compact != 0 (wide inputs, at least two hidden layers): the gradient
+    // buffers reuse the G tile, which is dead after the first product, and
+    // the G tile is loaded again for each further species of the tile.
     extern __shared__ __align__(16) uint16_t smh[];
     __shared__ int s_atom[BT], s_type[BT], s_range[2];
     __shared__ float s_e[BT], s_epart[2][BT];
@@ -442,7 +454,7 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
     uint16_t *wbuf = smh;
     uint16_t *act[MAX_LAYERS + 1], *der[MAX_LAYERS + 1];
     int ld[MAX_LAYERS + 1];
-    uint16_t *ptr = smh + 2 * BF_NC * ldw_max;
+    uint16_t *ptr = smh + 2 * bnc * ldw_max;
     for (int l = 0; l < L; ++l) {
         ld[l] = m.dims[l] + 8;
         act[l] = ptr;
@@ -451,7 +463,8 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
         ptr += (l > 0) ? BT * ld[l] : 0;
     }
     const int ldz = maxw + 8;
-    uint16_t *dzA = ptr, *dzB = ptr + BT * ldz;
+    uint16_t *dzA = compact ? act[0] : ptr;
+    uint16_t *dzB = dzA + BT * ldz;
     if (tid < BT) {
         const int64_t p = p0 + tid;
         const int a = p < n ? perm[p] : -1;
@@ -474,18 +487,23 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
     __syncthreads();
     const int s_lo = s_range[0], s_hi = s_range[1];
     BfStream ws{s_lo, s_hi, 0, 0};
-    if (s_lo <= s_hi) bf_issue(bf_step(m, s_lo, 0), 0, wbuf);   // first chunk, under the G loads
+    if (s_lo <= s_hi) bf_issue(bf_step(m, s_lo, 0), 0, bnc, wbuf);   // first chunk, under the G loads
     cp_async_commit();
     // G rows -> act[0] as BF16 (warp per atom row)
-    for (int r = warp; r < BT; r += BF_THREADS / 32) {
-        const int a = s_atom[r];
-        for (int c2 = lane; c2 < (Dd >> 1); c2 += 32) {
-            float2 v = make_float2(0.f, 0.f);
-            if (a >= 0) v = __ldg(reinterpret_cast<const float2 *>(G + (size_t)a * Dd + 2 * c2));
-            *reinterpret_cast<uint32_t *>(act[0] + r * ld[0] + 2 * c2) = pack_bf16(v.x, v.y);
+    auto load_G = [&]() {
+        for (int r = warp; r < BT; r += BF_THREADS / 32) {
+            const int a = s_atom[r];
+            for (int c2 = lane; c2 < (Dd >> 1); c2 += 32) {
+                float2 v = make_float2(0.f, 0.f);
+                if (a >= 0) v = __ldg(reinterpret_cast<const float2 *>(G + (size_t)a * Dd + 2 * c2));
+                *reinterpret_cast<uint32_t *>(act[0] + r * ld[0] + 2 * c2) = pack_bf16(v.x, v.y);
+            }
         }
-    }
+    };
+    load_G();
     for (int s = s_lo; s <= s_hi; ++s) {
+        // every warp passed the barrier after the previous species' last chunk
+        if (compact && s > s_lo) load_G();
         const float *wf = m.wf[s];
         const float *wout = m.wb[s] + m.off_b[L];
         float epart[2] = {0.f, 0.f};   // E partial sums of rows g and g + 8 (last forward product)
@@ -497,21 +515,21 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
             const uint16_t *A = fwd ? act[step] : cur;
             const int lda = fwd ? ld[step] : ldz;
             const int ldw = st.K + 8;
-            for (int n0 = 0; n0 < st.N; n0 += BF_NC) {
+            for (int n0 = 0; n0 < st.N; n0 += bnc) {
                 // next chunk of the stream (same product, next product or next species)
                 {
-                    int s2 = s, step2 = step, n2 = n0 + BF_NC;
+                    int s2 = s, step2 = step, n2 = n0 + bnc;
                     if (n2 >= st.N) {
                         n2 = 0;
                         if (++step2 == 2 * L) { step2 = 0; ++s2; }
                     }
-                    if (s2 <= s_hi) bf_issue(bf_step(m, s2, step2), n2, wbuf + (ws.par ^ 1) * (BF_NC * ldw_max));
+                    if (s2 <= s_hi) bf_issue(bf_step(m, s2, step2), n2, bnc, wbuf + (ws.par ^ 1) * (bnc * ldw_max));
                     cp_async_commit();
                 }
                 cp_async_wait1();
                 __syncthreads();   // this chunk has landed; A is complete
-                const uint16_t *w = wbuf + ws.par * (BF_NC * ldw_max);
-                const int nc = min(BF_NC, st.N - n0);
+                const uint16_t *w = wbuf + ws.par * (bnc * ldw_max);
+                const int nc = min(bnc, st.N - n0);
                 const int hc = nc >> 1;                // columns of this warp's half
                 const int nt = hc >> 3;                // n-tiles of 8 (1..4)
                 float acc[4][4];
@@ -524,11 +542,15 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
                     ldsm_x4(a0, a1, a2, a3, pa + k0);
 #pragma unroll
                     for (int j = 0; j < 4; j += 2) {
-                        if (j < nt) {
+                        if (j + 1 < nt) {
                             uint32_t b0, b1, b2, b3;
                             ldsm_x4(b0, b1, b2, b3, pb + j * 8 * ldw + k0);
                             mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
                             mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+                        } else if (j < nt) {   // a single n-tile (lanes 0-15 give the addresses)
+                            uint32_t b0, b1;
+                            ldsm_x2(b0, b1, pb + j * 8 * ldw + k0);
+                            mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
                         }
                     }
                 }
@@ -707,6 +729,8 @@ tmd_status dispatch_pair(const DevModel &dm, const DevNlist &dn, const double *p
     case 8: return launch_pair_k8(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
     case 16: return launch_pair_k16(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
     case 32: return launch_pair_k32(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
+    case 64: return launch_pair_k64(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
+    case 128: return launch_pair_k128(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
     default: break;
     }
     set_error("no kernel for K=%d S=%d", dm.K, dm.S);
@@ -740,17 +764,38 @@ tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double
                              const int32_t *act_list, int n_act, const int64_t *sys_off, const double *vel,
                              const double *mass, double *sys_out, cudaStream_t s);
 
-size_t mlp_bf16_smem_bytes(const DevModel &dm) {
+static size_t mlp_bf16_smem_cfg(const DevModel &dm, int bnc, bool compact) {
     int maxw = 0, kmax = dm.Dd;
     for (int l = 1; l <= dm.L; ++l) {
         maxw = std::max(maxw, dm.dims[l]);
         kmax = std::max(kmax, dm.dims[l]);
     }
-    size_t el = (size_t)2 * BF_NC * (kmax + 8);           // two weight buffers
+    size_t el = (size_t)2 * bnc * (kmax + 8);              // two weight buffers
     el += (size_t)BT * (dm.dims[0] + 8);                   // G tile
     for (int l = 1; l < dm.L; ++l) el += 2 * (size_t)BT * (dm.dims[l] + 8);   // act, act'
-    el += 2 * (size_t)BT * (maxw + 8);                     // gradient buffers
+    if (!compact) el += 2 * (size_t)BT * (maxw + 8);       // gradient buffers
     return el * sizeof(uint16_t);
+}
+
+// launch shape of k_mlp_bf16: weight-chunk columns (BF_NC, 32 or 16) and
+// whether the gradient buffers share the G tile, the first that fits an SM
+struct BfCfg {
+    int bnc;
+    bool compact;
+};
+static BfCfg mlp_bf16_cfg(const DevModel &dm) {
+    int maxw = 0;
+    for (int l = 1; l <= dm.L; ++l) maxw = std::max(maxw, dm.dims[l]);
+    const bool can_compact = dm.L >= 2 && dm.Dd + 8 >= 2 * (maxw + 8);
+    for (int c = 0; c < (can_compact ? 2 : 1); ++c)
+        for (int bnc = BF_NC; bnc >= 16; bnc >>= 1)
+            if (mlp_bf16_smem_cfg(dm, bnc, c == 1) <= 227 * 1024) return {bnc, c == 1};
+    return {16, can_compact};
+}
+
+size_t mlp_bf16_smem_bytes(const DevModel &dm) {
+    const BfCfg c = mlp_bf16_cfg(dm);
+    return mlp_bf16_smem_cfg(dm, c.bnc, c.compact);
 }
 
 // dynamic shared memory of k_mlp<TR>: transposed activations of every layer
@@ -831,8 +876,9 @@ static tmd_status launch_network(const DevModel &dm, const int32_t *perm, const 
     if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
     if (dm.precision == TMD_PREC_BF16) {
         const int ntile = (int)((n + BT - 1) / BT);
+        const BfCfg bcfg = mlp_bf16_cfg(dm);
         TMD_LAUNCH("k_mlp_bf16", s, k_mlp_bf16<<<ntile, BF_THREADS, mlp_bf16_smem_bytes(dm), s>>>(
-                                        dm, perm, types, n, G, dG, e_atom, part_e));
+                                        dm, perm, types, n, G, dG, e_atom, part_e, bcfg.bnc, bcfg.compact ? 1 : 0));
         *ntile_out = ntile;
     } else {
         const int tr = mlp_tr(dm);

@@ -54,6 +54,7 @@ constexpr int PAIR_WARPS = 4;   // warps (atoms in flight) per block of the pair
 int pair_blocks(const DevModel &dm, int64_t n);
 // shared memory of the FP32 network kernel with tr-atom tiles
 size_t mlp_smem_tr_public(const DevModel &dm, int tr);
+size_t mlp_bf16_smem_bytes(const DevModel &dm);
 
 // One system of a batch (a single evaluation is a batch of one): box, cell
 // grid, first global cell, list radius and the FP32 screening band.
@@ -277,6 +278,8 @@ tmd_status build_neighbors(const double *pos, const int32_t *types, int64_t n, c
 TMD_PAIR_LAUNCHER(launch_pair_k8);
 TMD_PAIR_LAUNCHER(launch_pair_k16);
 TMD_PAIR_LAUNCHER(launch_pair_k32);
+TMD_PAIR_LAUNCHER(launch_pair_k64);
+TMD_PAIR_LAUNCHER(launch_pair_k128);
 tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, int64_t n_active);
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                        int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
