@@ -253,6 +253,65 @@ def batch_measure(tmd, torch, steps=5):
     return out
 
 
+def paper_models_measure(tmd, torch, steps=5):
+    """The paper's two potential geometries (Sec. "The Potential": k = 32 with a
+    128-128-128-1 network, k = 128 with 128-128-128-128-1, SquarePlus) on
+    random weights, on 1,024,000-atom bcc W lattices at the two lattice
+    constants of the paper's weak-scaling runs; tmd_compute on a fixed table,
+    FP32 and BF16 network forms."""
+    from oracle import oracle as O
+    from paper_2310_08439_gb300 import inputs as I
+
+    def bcc_w(a, reps, seed):
+        rng = np.random.default_rng(seed)
+        pos, box = I.lattice("bcc", reps, a)
+        return I.System(I.jitter_and_wrap(pos, box, 0.1, rng), np.zeros(len(pos), np.int32), box,
+                        np.ones(3, np.int32))
+
+    out = {"workload": "bcc W 80^3 x 2 = 1,024,000 atoms, jitter 0.1 A, rc 6 A (no skin), 1 species; "
+                       "first layer normalised by the descriptor RMS of a 432-atom cell"}
+    for k, widths in ((32, [128, 128, 128]), (128, [128, 128, 128, 128])):
+        for a in (3.1887, 2.8):
+            small = bcc_w(a, (6, 6, 6), 1)
+            p0 = I.random_model(1, k, 6.0, widths, seed=k, activation="squareplus", masses=[183.84])
+            G = O.evaluate(O.OracleModel(p0), small.pos, small.types, small.box, small.pbc, want_G=True)["G"]
+            p = I.random_model(1, k, 6.0, widths, seed=k, activation="squareplus", masses=[183.84],
+                               feature_scale=np.sqrt((G ** 2).mean(axis=0)).reshape(1, -1))
+            s = bcc_w(a, (80, 80, 80), 2)
+            m = tmd.Model(p)
+            pos = torch.as_tensor(s.pos, device="cuda")
+            types = torch.as_tensor(s.types, device="cuda")
+            nl = tmd.NeighborList()
+            nl.build(pos, types, s.box, s.pbc, 6.0)
+            E = torch.zeros(1, dtype=torch.float64, device="cuda")
+            F = torch.zeros((s.n, 3), dtype=torch.float32, device="cuda")
+            W = torch.zeros(9, dtype=torch.float64, device="cuda")
+            row = {"n": s.n, "pairs_listed": int(nl.size()[1])}
+            for prec in ("fp32", "bf16"):
+                m.set_precision(prec)
+                for _ in range(2):
+                    tmd.compute(m, nl, pos, types, s.box, E, None, F, W)
+                torch.cuda.synchronize()
+                tmd.profile_read(reset=True)
+                tmd.profile_enable(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(steps):
+                    tmd.compute(m, nl, pos, types, s.box, E, None, F, W)
+                e1.record()
+                torch.cuda.synchronize()
+                tmd.profile_enable(False)
+                ks = tmd.profile_read(reset=True)
+                ms = e0.elapsed_time(e1) / steps
+                row[prec] = {"atom_evals_per_s": s.n / (ms * 1e-3), "ms_per_eval": ms,
+                             "kernel_ms": {kk: v[1] / max(v[0], 1) for kk, v in ks.items()
+                                           if kk in ("k_desc", "k_force", "k_mlp", "k_mlp_bf16")}}
+            out[f"k{k}_a{a}"] = row
+            del nl, m, pos, types, E, F, W
+            torch.cuda.empty_cache()
+    return out
+
+
 def graphs_measure(tmd, torch, steps=60):
     """Launch overhead: the medium cell (16,384 atoms) advanced one step per
     call with the skin check (rebuild only when an atom moved > skin/2), eager
@@ -554,6 +613,7 @@ def main():
     if not args.no_extras and world == 1:
         extras["batch"] = batch_measure(tmd, torch)
         extras["radial_table"] = radial_table_measure(tmd, model, sysm, s, w, args.steps, torch, stream)
+        extras["paper_models"] = paper_models_measure(tmd, torch)
         extras["graphs"] = graphs_measure(tmd, torch)
         extras["serving"] = serving_measure(tmd, args.serve_seconds, torch)
 

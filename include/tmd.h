@@ -56,6 +56,7 @@ typedef enum {
 
 enum { TMD_ACT_TANH = 0, TMD_ACT_SQUAREPLUS = 1 };
 enum { TMD_PREC_FP32 = 0, TMD_PREC_BF16 = 1 };
+enum { TMD_NET_AUTO = 0, TMD_NET_TCGEN05 = 1, TMD_NET_MMA_SYNC = 2 };
 
 /* Limits of this build. */
 #define TMD_MAX_SPECIES 4
@@ -152,6 +153,25 @@ tmd_status tmd_model_set_radial_table(tmd_model *model, int32_t points_per_angst
  * default on).  tmd_graph_replays counts the replays so far.
  */
 tmd_status tmd_set_graphs(int32_t on);
+
+/* Network kernel of the BF16 form (process-wide; default TMD_NET_AUTO).  The
+ * per-species network E_a = NNP(G_a) and its input gradient run either on the
+ * fifth-generation tensor cores (tcgen05.mma into tensor memory, 128-atom
+ * tiles, weights bulk-copied in 64-wide K chunks; needs every layer width a
+ * multiple of 16, hidden widths <= 256, and the accumulators plus the stored
+ * activation derivatives within 512 TMEM columns) or on mma.sync m16n8k16
+ * (64-atom tiles).  AUTO takes tcgen05 when the shapes allow it;
+ * TMD_NET_TCGEN05 makes other shapes fail with UNIMPLEMENTED.  Both compute
+ * BF16 products with FP32 accumulation (results differ in rounding order
+ * only).  Errors: INVALID_ARG. */
+tmd_status tmd_set_network_kernel(int32_t kind);
+
+/* Status bits recorded by device kernels that have no neighbour table to
+ * report through (today: a bounded wait of the tcgen05 network kernel that
+ * gave up), read and cleared.  Returns TMD_ERR_TIMEOUT when such a wait ran
+ * out since the last call (the results of the calls in between are invalid),
+ * else TMD_OK; *bits receives the raw bits.  Synchronises the device. */
+tmd_status tmd_device_status(int32_t *bits);
 int64_t tmd_graph_replays(void);
 
 /*

@@ -98,6 +98,7 @@ void model_key(const tmd_model *m, std::vector<uintptr_t> &k) {
     k.push_back((uintptr_t)m->dm.rtab);
     k.push_back((uintptr_t)m->dm.rtab_n);
     k.push_back((uintptr_t)m->dm.rtab_scale);
+    k.push_back((uintptr_t)tmd::network_kernel());
 }
 
 uintptr_t bits_of(double x) {
@@ -409,15 +410,20 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     m->mu.assign(d->mu, d->mu + (size_t)S * S * K);
     m->eta.assign(d->eta, d->eta + (size_t)S * S * K);
     m->rc_exact = d->rc;
+    {
+        const tmd_status su = tmd::mlp_umma_build(m, d->weights);
+        if (su != TMD_OK) { cudaFree(m->dev_block); delete m; return su; }
+    }
     if (tmd::mlp_smem_tr_public(m->dm, 32) > 227 * 1024) {
         set_error("network too wide: the activations of a 32-atom tile exceed the shared memory of an SM");
         cudaFree(m->dev_block);
+        if (m->dev_umma) cudaFree(m->dev_umma);
         delete m;
         return TMD_ERR_UNIMPLEMENTED;
     }
     if (d->precision == TMD_PREC_BF16) {
         tmd_status st = tmd_model_set_precision(m, TMD_PREC_BF16);
-        if (st != TMD_OK) { cudaFree(m->dev_block); delete m; return st; }
+        if (st != TMD_OK) { cudaFree(m->dev_block); if (m->dev_umma) cudaFree(m->dev_umma); delete m; return st; }
     }
     *out = m;
     return TMD_OK;
@@ -427,6 +433,7 @@ tmd_status tmd_model_destroy(tmd_model *m) {
     if (!m) return TMD_OK;
     if (m->dev_block) cudaFree(m->dev_block);
     if (m->dev_rtab) cudaFree(m->dev_rtab);
+    if (m->dev_umma) cudaFree(m->dev_umma);
     delete m;
     return TMD_OK;
 }
@@ -504,12 +511,34 @@ tmd_status tmd_model_set_precision(tmd_model *m, int32_t precision) {
                           m->dm.dims[l]);
                 return TMD_ERR_UNIMPLEMENTED;
             }
-    if (precision == TMD_PREC_BF16 && tmd::mlp_bf16_smem_bytes(m->dm) > 227 * 1024) {
+    if (precision == TMD_PREC_BF16 && !tmd::mlp_umma_supported(m->dm) && tmd::mlp_bf16_smem_bytes(m->dm) > 227 * 1024) {
         set_error("network too wide for the BF16 tile (64 atoms) in the shared memory of an SM");
         return TMD_ERR_UNIMPLEMENTED;
     }
     m->precision = precision;
     m->dm.precision = precision;
+    return TMD_OK;
+}
+
+tmd_status tmd_set_network_kernel(int32_t kind) {
+    g_err[0] = 0;
+    if (kind < TMD_NET_AUTO || kind > TMD_NET_MMA_SYNC) {
+        set_error("network kernel must be TMD_NET_AUTO, TMD_NET_TCGEN05 or TMD_NET_MMA_SYNC");
+        return TMD_ERR_INVALID_ARG;
+    }
+    tmd::g_network_kernel = kind;
+    return TMD_OK;
+}
+
+tmd_status tmd_device_status(int32_t *bits) {
+    g_err[0] = 0;
+    if (!bits) { set_error("null output"); return TMD_ERR_INVALID_ARG; }
+    tmd_status st = tmd::umma_status(bits);
+    if (st != TMD_OK) return st;
+    if (*bits & tmd::DEV_ERR_TIMEOUT) {
+        set_error("a bounded wait of a tensor-core kernel gave up; the results since the last check are invalid");
+        return TMD_ERR_TIMEOUT;
+    }
     return TMD_OK;
 }
 

@@ -1,0 +1,547 @@
+// BF16 network form on the fifth-generation tensor cores (tcgen05): the
+// per-species atomic-energy network E_a = NNP(G_a) and its input gradient
+// G' = dE_a/dG_a (Sec. "The Tensor Formalism", the E_a / NNP equations and
+// the backward chain through the network), for 128-atom tiles.
+//
+// Every product of the chain -- forward layers a_{l+1} = act(a_l W_l^T + b_l),
+// then dz_l = (dz_{l+1} W_l) * act'(a_l) down to G' = dz_1 W_0 -- is one
+// [128 x K] x [K x N] tcgen05.mma GEMM with BF16 operands in shared memory and
+// the FP32 accumulator in tensor memory (TMEM lane = tile row = atom).  The
+// weight operand streams in 64-wide K chunks by bulk copy (cp.async.bulk,
+// completion on an mbarrier) into two stages; the first layer's operand is
+// the FP32 descriptor tile converted to BF16 by the threads, chunk by chunk.
+// After each product four warps read the accumulator back (tcgen05.ld, one
+// row per thread), apply bias and activation, keep act' in TMEM for the
+// backward chain (tcgen05.st) and write the BF16 operand of the next product.
+// One elected thread issues the MMAs and the copies.
+//
+// Operand layout (no swizzle, K-major): 8 x 8 BF16 core matrices of 128
+// contiguous bytes; along K the next core matrix is 128 B away (LBO), the
+// next group of 8 rows 1024 B away (SBO), i.e. a 64-wide K chunk of R rows is
+// [R/8][8 core matrices][8 rows][8 elements].
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "net_common.cuh"
+#include "tmd_internal.cuh"
+
+namespace tmd {
+
+// status bits of the tensor-core kernels (bounded waits that ran out)
+__device__ int32_t g_umma_status = 0;
+
+namespace {
+
+constexpr int UM = 128;                 // atoms per tile: the MMA M, one TMEM lane each
+constexpr int UTHREADS = 128;           // 4 warps; warp w owns TMEM lanes / rows 32w .. 32w + 31
+constexpr int UKC = 64;                 // K per streamed chunk
+constexpr int UNMAX = 256;              // largest N of one MMA
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr int CHUNK_EL = UM * UKC;      // elements of a 128-row K chunk
+
+struct UmmaNet {
+    int xchunks;        // 64-wide K chunks of an activation buffer (widest hidden layer)
+    int np_max;         // largest MMA N of any product
+    int npass0, np0;    // N passes of the last product (G') and their width
+    int tcols;          // TMEM columns allocated per block
+    int dercol[MAX_LAYERS];   // TMEM column of act'(a_l), l = 1 .. L-1
+    int smem;           // dynamic shared memory bytes
+    int blocks_per_sm;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr uint64_t WAIT_NS = 200000000ull;   // 0.2 s per wait
+
+// Bounded wait for the completion of the phase with this parity.  When it
+// gives up (0.2 s, or the iteration cap) it records DEV_ERR_TIMEOUT and sets
+// the block's abort flag, after which every later wait returns at once: the
+// kernel runs on to its end, waits (bounded) for its copies and MMAs in
+// flight, frees its tensor memory and the host reports the status; the
+// results of that call are not valid.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort) {
+    if (*abort) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 1; i < WAIT_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0 && (*abort || gtimer() - t0 > WAIT_NS)) break;
+    }
+    *abort = 1;
+    atomicOr(&g_umma_status, DEV_ERR_TIMEOUT);
+    return false;
+}
+// teardown after an abort: wait, bounded, for a phase regardless of the flag
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity) || ((i & 63) == 0 && gtimer() - t0 > WAIT_NS)) return;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: start address, LBO 128 B, SBO 1024 B,
+// descriptor version 1 (bits 46-48), base offset 0, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// instruction descriptor of kind::f16: D FP32 (bits 4-5), A BF16 (7-9),
+// B BF16 (10-12), A and B K-major (bits 15, 16 clear), N >> 3 (17-22),
+// M >> 4 (24-28)
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    // the registers are read only after the wait (tied through the asm operands)
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// element (row, k) of a chunked operand buffer, in elements from its start
+__device__ __forceinline__ int op_index(int row, int k) {
+    return (k / UKC) * CHUNK_EL + (row >> 3) * 512 + ((k % UKC) >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
+// 16 values as BF16 at (row, col0 .. col0 + 15), col0 a multiple of 16
+__device__ __forceinline__ void store_row16(uint16_t *X, int row, int col0, const float (&v)[16]) {
+    uint4 lo, hi;
+    lo.x = pack_bf16(v[0], v[1]);
+    lo.y = pack_bf16(v[2], v[3]);
+    lo.z = pack_bf16(v[4], v[5]);
+    lo.w = pack_bf16(v[6], v[7]);
+    hi.x = pack_bf16(v[8], v[9]);
+    hi.y = pack_bf16(v[10], v[11]);
+    hi.z = pack_bf16(v[12], v[13]);
+    hi.w = pack_bf16(v[14], v[15]);
+    const int i = op_index(row, col0);
+    *reinterpret_cast<uint4 *>(X + i) = lo;
+    *reinterpret_cast<uint4 *>(X + i + 64) = hi;   // next core matrix along K
+}
+
+__global__ void __launch_bounds__(UTHREADS, 1)
+    k_mlp_umma(DevModel m, UmmaNet u, const int32_t *__restrict__ perm, const int32_t *__restrict__ types, int64_t n,
+               const float *__restrict__ G, float *__restrict__ dG, float *__restrict__ e_atom,
+               double *__restrict__ part_e, int ntile) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t s_bar[5];   // full[2], empty[2], done
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ int s_atom[UM], s_type[UM], s_range[2];
+    __shared__ float s_e[UM];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = m.L, Dd = m.Dd;
+    // dynamic shared memory: X[2] activation buffers, A stages (G chunks), B stages
+    uint16_t *X[2];
+    X[0] = reinterpret_cast<uint16_t *>(smraw);
+    X[1] = X[0] + (size_t)u.xchunks * CHUNK_EL;
+    uint16_t *Ast[2], *Bst[2];
+    Ast[0] = X[1] + (size_t)u.xchunks * CHUNK_EL;
+    Ast[1] = Ast[0] + CHUNK_EL;
+    Bst[0] = Ast[1] + CHUNK_EL;
+    Bst[1] = Bst[0] + (size_t)u.np_max * UKC;
+    const uint32_t bar_full0 = smem_u32(&s_bar[0]), bar_empty0 = smem_u32(&s_bar[2]), bar_done = smem_u32(&s_bar[4]);
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&s_bar[i]), 1);
+        s_abort = 0;
+        fence_proxy_async();
+    }
+    volatile int *abort = &s_abort;
+    bool pending[2] = {false, false};   // thread 0: a copy into stage st not yet seen complete
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(u.tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lane quarter, column 0
+    uint32_t q = 0;    // K chunks issued (stage q & 1, use q >> 1)
+    uint32_t pd = 0;   // products (passes) completed
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t p0 = (int64_t)tile * UM;
+        {
+            const int64_t p = p0 + tid;
+            const int a = p < n ? perm[p] : -1;
+            s_atom[tid] = a;
+            s_type[tid] = a >= 0 ? types[a] : -1;
+            s_e[tid] = 0.f;
+        }
+        __syncthreads();
+        if (warp == 0) {   // species present in the tile (perm groups atoms by species)
+            int lo = TMD_MAX_SPECIES, hi = -1;
+            for (int r = lane; r < UM; r += 32)
+                if (s_type[r] >= 0) { lo = min(lo, s_type[r]); hi = max(hi, s_type[r]); }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) { s_range[0] = lo; s_range[1] = hi; }
+        }
+        __syncthreads();
+        const int s_lo = s_range[0], s_hi = s_range[1];
+        const int my_atom = s_atom[tid], my_type = s_type[tid];
+        for (int s = s_lo; s <= s_hi; ++s) {
+            const float *wf = m.wf[s];
+            for (int pr = 0; pr < 2 * L; ++pr) {
+                const bool fwd = pr < L, last = pr == 2 * L - 1;
+                const int l = fwd ? pr : 2 * L - 1 - pr;   // layer of this product
+                const int K = fwd ? m.dims[l] : m.dims[l + 1];
+                const int N = fwd ? m.dims[l + 1] : m.dims[l];
+                const int npass = last ? u.npass0 : 1, Np = last ? u.np0 : N;
+                const int nkc = (K + UKC - 1) / UKC;
+                const uint16_t *blob = m.ub[s] + m.uoff[pr];
+                uint16_t *Xin = X[(pr + 1) & 1], *Xout = X[pr & 1];
+                for (int P = 0; P < npass; ++P) {
+                    for (int c = 0; c < nkc; ++c, ++q) {
+                        const int st = q & 1;
+                        const uint32_t use = q >> 1;
+                        // the MMAs that last read this stage are done
+                        if (use >= 1) mbar_wait(bar_empty0 + 8 * st, (use - 1) & 1, abort);
+                        if (tid == 0) {
+                            const uint32_t bytes = (uint32_t)Np * UKC * 2;
+                            if (!*abort && !pending[st]) {
+                                mbar_expect_tx(bar_full0 + 8 * st, bytes);
+                                bulk_g2s(smem_u32(Bst[st]), blob + ((size_t)P * nkc + c) * Np * UKC, bytes,
+                                         bar_full0 + 8 * st);
+                                pending[st] = true;
+                            }
+                        }
+                        if (pr == 0) {   // G chunk c -> BF16 operand (half a warp per row, own rows)
+#pragma unroll 4
+                            for (int it = 0; it < 16; ++it) {
+                                const int r = warp * 32 + 2 * it + (lane >> 4);
+                                const int q4 = lane & 15, col = c * UKC + 4 * q4;
+                                const int a = s_atom[r];
+                                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (a >= 0 && col < Dd) v = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + col));
+                                uint2 w;
+                                w.x = pack_bf16(v.x, v.y);
+                                w.y = pack_bf16(v.z, v.w);
+                                *reinterpret_cast<uint2 *>(Ast[st] + op_index(r, 4 * q4)) = w;
+                            }
+                            fence_proxy_async();
+                        }
+                        __syncthreads();
+                        if (tid == 0 && !*abort) {
+                            if (mbar_wait(bar_full0 + 8 * st, use & 1, abort)) pending[st] = false;
+                            tc_fence_after();
+                            const int kl = min(UKC, K - c * UKC);
+                            const uint32_t a0 = smem_u32(pr == 0 ? Ast[st] : Xin + (size_t)c * CHUNK_EL);
+                            const uint32_t b0 = smem_u32(Bst[st]);
+                            const uint32_t id = idesc_bf16(Np);
+                            for (int j = 0; j < kl / 16; ++j)
+                                umma_bf16(tmem, sdesc(a0 + 256 * j), sdesc(b0 + 256 * j), id, (c | j) != 0);
+                            umma_commit(bar_empty0 + 8 * st);
+                        }
+                    }
+                    if (tid == 0) umma_commit(bar_done);
+                    mbar_wait(bar_done, pd & 1, abort);
+                    ++pd;
+                    tc_fence_after();
+                    // epilogue: this thread's row of the accumulator
+                    if (fwd) {
+                        const float *bias = wf + m.off_f[l] + (size_t)K * N;
+                        const bool last_fwd = l == L - 1;
+                        const float *wout = m.wb[s] + m.off_b[L];
+                        float eacc = 0.f;
+                        for (int c0 = 0; c0 < N; c0 += 16) {
+                            float v[16], a[16], d[16];
+                            tmem_ld16(trow + c0, v);
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                a[e] = act_f_bf16(m.act, v[e] + __ldg(bias + c0 + e), m.sp_b);
+                                d[e] = act_da(m.act, a[e], m.sp_b);
+                            }
+                            if (!last_fwd) {
+                                store_row16(Xout, tid, c0, a);
+                                tmem_st16(trow + u.dercol[l + 1] + c0, d);
+                            } else {   // E_a partial and dz_L = w_out * act'(a_L)
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) {
+                                    const float w = __ldg(wout + c0 + e);
+                                    eacc = fmaf(w, a[e], eacc);
+                                    d[e] *= w;
+                                }
+                                store_row16(Xout, tid, c0, d);
+                            }
+                        }
+                        if (last_fwd && my_type == s) {
+                            const float e = eacc + __ldg(wf + m.off_f[L] + m.dims[L]);
+                            s_e[tid] = e;
+                            if (e_atom) e_atom[my_atom] = e;
+                        }
+                    } else if (!last) {   // dz_l = (dz_{l+1} W_l) * act'(a_l)
+                        for (int c0 = 0; c0 < N; c0 += 16) {
+                            float v[16], d[16];
+                            tmem_ld16(trow + c0, v);
+                            tmem_ld16(trow + u.dercol[l] + c0, d);
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) v[e] *= d[e];
+                            store_row16(Xout, tid, c0, v);
+                        }
+                    } else {   // G' columns of this pass
+                        for (int c0 = 0; c0 < Np; c0 += 16) {
+                            float v[16];
+                            tmem_ld16(trow + c0, v);
+                            if (my_type == s) {
+                                float4 *o = reinterpret_cast<float4 *>(dG + (size_t)my_atom * Dd + P * Np + c0);
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                            }
+                        }
+                    }
+                    fence_proxy_async();   // the operand writes are read by the next MMA
+                    tc_fence_before();
+                    __syncthreads();
+                }
+            }
+        }
+        // tile energy in FP64, fixed order
+        if (warp == 0) {
+            double tsum = 0.0;
+            for (int r = lane; r < UM; r += 32) tsum += (double)s_e[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+            if (lane == 0) part_e[tile] = tsum;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && *abort) {   // bounded drain of this block's copies and MMAs in flight
+        for (int st = 0; st < 2; ++st)
+            if (pending[st]) mbar_drain(bar_full0 + 8 * st, ((q >> 1) + ((q & 1) > st ? 1 : 0) - 1) & 1);
+        umma_commit(bar_done);
+        mbar_drain(bar_done, pd & 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(u.tcols) : "memory");
+}
+
+// launch plan for a model, or false when the shapes do not fit
+bool plan(const DevModel &dm, UmmaNet &u) {
+    std::memset(&u, 0, sizeof(u));
+    const int L = dm.L;
+    for (int s = 0; s < dm.S; ++s)
+        if (!dm.ub[s]) return false;
+    int maxw = 0;
+    for (int l = 0; l <= L; ++l)
+        if (dm.dims[l] % 16) return false;
+    for (int l = 1; l <= L; ++l) maxw = std::max(maxw, dm.dims[l]);
+    if (maxw > UNMAX) return false;
+    u.npass0 = (dm.Dd + UNMAX - 1) / UNMAX;
+    if (dm.Dd % u.npass0) return false;
+    u.np0 = dm.Dd / u.npass0;
+    if (u.np0 % 16) return false;
+    u.np_max = std::max(maxw, u.np0);
+    u.xchunks = (maxw + UKC - 1) / UKC;
+    // TMEM: accumulator columns [0, maxw), then act'(a_l) for l = 1 .. L-1;
+    // the last product (G') may use every column (act' is dead by then)
+    int col = maxw;
+    for (int l = 1; l < L; ++l) {
+        u.dercol[l] = col;
+        col += dm.dims[l];
+    }
+    col = std::max(col, u.np0);
+    if (col > 512) return false;
+    u.tcols = 32;
+    while (u.tcols < col) u.tcols <<= 1;
+    const size_t smem = sizeof(uint16_t) * ((size_t)2 * u.xchunks * CHUNK_EL + 2 * CHUNK_EL + (size_t)2 * u.np_max * UKC);
+    if (smem > 200 * 1024) return false;
+    u.smem = (int)smem;
+    u.blocks_per_sm = std::max(1, std::min(512 / u.tcols, (int)((220 * 1024) / (smem + 2048))));
+    return true;
+}
+
+uint16_t bf16_bits(double x) {
+    const float f = (float)x;
+    uint32_t v;
+    std::memcpy(&v, &f, 4);
+    if ((v & 0x7f800000u) == 0x7f800000u) return (uint16_t)(v >> 16);
+    return (uint16_t)((v + 0x7fffu + ((v >> 16) & 1u)) >> 16);   // round to nearest even
+}
+
+}  // namespace
+
+int g_network_kernel = 0;
+int network_kernel() { return g_network_kernel; }
+
+bool mlp_umma_supported(const DevModel &dm) {
+    UmmaNet u;
+    return plan(dm, u);
+}
+
+tmd_status mlp_umma_launch(const DevModel &dm, const int32_t *perm, const int32_t *types, int64_t n, const float *G,
+                           float *dG, float *e_atom, double *part_e, int *ntile_out, cudaStream_t s) {
+    UmmaNet u;
+    if (!plan(dm, u)) {
+        set_error("network shapes outside the tcgen05 kernel");
+        return TMD_ERR_UNIMPLEMENTED;
+    }
+    static int smem_set = 0;
+    if (u.smem > 48 * 1024 && u.smem > smem_set) {
+        TMD_CUDA(cudaFuncSetAttribute(k_mlp_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, u.smem));
+        smem_set = u.smem;
+    }
+    const int ntile = (int)((n + UM - 1) / UM);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(ntile, std::max(1, nsm) * u.blocks_per_sm));
+    if (ntile > 0)
+        TMD_LAUNCH("k_mlp_umma", s, k_mlp_umma<<<grid, UTHREADS, u.smem, s>>>(dm, u, perm, types, n, G, dG, e_atom,
+                                                                              part_e, ntile));
+    TMD_CUDA(cudaGetLastError());
+    *ntile_out = ntile;
+    return TMD_OK;
+}
+
+// BF16 weights in the operand layout of k_mlp_umma (product order: forward
+// layers 0 .. L-1, then backward layers L-1 .. 0); B[n][k] is W_l[n][k]
+// forward and W_l[k][n] backward.
+tmd_status mlp_umma_build(tmd_model *m, const double *const *weights) {
+    DevModel &dm = m->dm;
+    const int L = dm.L, S = dm.S;
+    if (m->dev_umma) {
+        cudaFree(m->dev_umma);
+        m->dev_umma = nullptr;
+    }
+    for (int s = 0; s < TMD_MAX_SPECIES; ++s) dm.ub[s] = nullptr;
+    for (int l = 0; l <= L; ++l)
+        if (dm.dims[l] % 16) return TMD_OK;   // no BF16 form for these widths
+    size_t off = 0;
+    int npass[2 * MAX_LAYERS], np[2 * MAX_LAYERS], nk[2 * MAX_LAYERS];
+    for (int pr = 0; pr < 2 * L; ++pr) {
+        const bool fwd = pr < L;
+        const int l = fwd ? pr : 2 * L - 1 - pr;
+        const int K = fwd ? dm.dims[l] : dm.dims[l + 1], N = fwd ? dm.dims[l + 1] : dm.dims[l];
+        npass[pr] = (N + UNMAX - 1) / UNMAX;
+        np[pr] = N / npass[pr];
+        nk[pr] = (K + UKC - 1) / UKC;
+        if (N % npass[pr] || np[pr] % 16) return TMD_OK;
+        dm.uoff[pr] = (int)off;
+        off += (size_t)npass[pr] * nk[pr] * np[pr] * UKC;
+    }
+    const size_t per = (off + 511) & ~size_t(511);   // 1 KiB aligned species blocks
+    std::vector<uint16_t> h(per * S, 0);
+    for (int s = 0; s < S; ++s) {
+        const double *w = weights[s];
+        size_t lo[MAX_LAYERS];
+        size_t o = 0;
+        for (int l = 0; l <= L; ++l) {
+            lo[l] = o;
+            o += (size_t)dm.dims[l] * dm.dims[l + 1] + dm.dims[l + 1];
+        }
+        for (int pr = 0; pr < 2 * L; ++pr) {
+            const bool fwd = pr < L;
+            const int l = fwd ? pr : 2 * L - 1 - pr;
+            const int in = dm.dims[l];
+            const int K = fwd ? dm.dims[l] : dm.dims[l + 1], N = fwd ? dm.dims[l + 1] : dm.dims[l];
+            uint16_t *b = h.data() + per * s + dm.uoff[pr];
+            for (int nn = 0; nn < N; ++nn)
+                for (int k = 0; k < K; ++k) {
+                    const double v = fwd ? w[lo[l] + (size_t)nn * in + k] : w[lo[l] + (size_t)k * in + nn];
+                    const int P = nn / np[pr], r = nn % np[pr], c = k / UKC, kk = k % UKC;
+                    const size_t idx = ((size_t)P * nk[pr] + c) * np[pr] * UKC + (size_t)(r >> 3) * 512 +
+                                       (size_t)(kk >> 3) * 64 + (r & 7) * 8 + (kk & 7);
+                    b[idx] = bf16_bits(v);
+                }
+        }
+    }
+    void *dev = nullptr;
+    cudaError_t e = cudaMalloc(&dev, sizeof(uint16_t) * h.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc tcgen05 weights");
+    e = cudaMemcpy(dev, h.data(), sizeof(uint16_t) * h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return cuda_fail(e, "cudaMemcpy tcgen05 weights");
+    }
+    m->dev_umma = dev;
+    for (int s = 0; s < S; ++s) dm.ub[s] = static_cast<const uint16_t *>(dev) + per * s;
+    return TMD_OK;
+}
+
+tmd_status umma_status(int32_t *bits) {
+    int32_t v = 0;
+    TMD_CUDA(cudaMemcpyFromSymbol(&v, g_umma_status, sizeof(v)));
+    const int32_t zero = 0;
+    TMD_CUDA(cudaMemcpyToSymbol(g_umma_status, &zero, sizeof(zero)));
+    *bits = v;
+    return TMD_OK;
+}
+
+}  // namespace tmd

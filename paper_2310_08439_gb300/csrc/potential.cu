@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "tmd_internal.cuh"
+#include "net_common.cuh"
 
 namespace tmd {
 
@@ -33,27 +34,6 @@ __global__ void k_split_pos(const double *__restrict__ pos, int64_t n, float4 *_
     const float xh = (float)x, yh = (float)y, zh = (float)z;
     ph[i] = make_float4(xh, yh, zh, 0.f);
     pl[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
-}
-
-__device__ __forceinline__ float act_f(int act, float z, float b) {
-    if (act == TMD_ACT_TANH) return tanhf(z);
-    return 0.5f * (z + sqrtf(fmaf(z, z, b)));
-}
-// BF16 form: tanh from the hardware approximation (relative error about
-// 2^-11, below the 2^-9 rounding of the BF16 activation it feeds)
-__device__ __forceinline__ float act_f_bf16(int act, float z, float b) {
-    if (act == TMD_ACT_TANH) {
-        float r;
-        asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(z));
-        return r;
-    }
-    return 0.5f * (z + sqrtf(fmaf(z, z, b)));
-}
-// derivative expressed through the activation output a
-__device__ __forceinline__ float act_da(int act, float a, float b) {
-    if (act == TMD_ACT_TANH) return 1.f - a * a;
-    const float a2 = 4.f * a * a;
-    return a2 / (a2 + b);
 }
 
 // ---------------------------------------------------------------------------
@@ -366,16 +346,6 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 3 : 2) k_mlp(DevModel 
 constexpr int BT = 64;            // atoms per BF16 tile
 constexpr int BF_THREADS = 256;   // 8 warps: 4 row slabs x 2 column halves
 constexpr int BF_NC = 64;         // output columns per streamed weight chunk (fewer for wide inputs)
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-__device__ __forceinline__ float2 unpack_bf16(uint32_t u) {
-    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&u);
-    return __bfloat1622float2(v);
-}
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1) {
@@ -874,6 +844,12 @@ static tmd_status launch_network(const DevModel &dm, const int32_t *perm, const 
                                  cudaStream_t s) {
     tmd_status st;
     if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
+    if (dm.precision == TMD_PREC_BF16 && network_kernel() != 2 && mlp_umma_supported(dm))
+        return mlp_umma_launch(dm, perm, types, n, G, dG, e_atom, part_e, ntile_out, s);
+    if (dm.precision == TMD_PREC_BF16 && network_kernel() == 1) {
+        set_error("the tcgen05 network kernel does not support these network shapes");
+        return TMD_ERR_UNIMPLEMENTED;
+    }
     if (dm.precision == TMD_PREC_BF16) {
         const int ntile = (int)((n + BT - 1) / BT);
         const BfCfg bcfg = mlp_bf16_cfg(dm);

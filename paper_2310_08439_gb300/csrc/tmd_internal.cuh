@@ -23,6 +23,7 @@ enum : int32_t {
     DEV_ERR_DEGREE = 4,
     DEV_ERR_SHIFT = 8,
     DEV_ERR_CELL = 16,
+    DEV_ERR_TIMEOUT = 32,   // a bounded wait of a tensor-core kernel gave up
 };
 
 // Model as seen by kernels (passed by value).
@@ -42,11 +43,17 @@ struct DevModel {
     int tile_rows;                      // atoms per FP32 network tile: 32 or 64
     int pair_bps;                       // blocks per SM of the persistent pair-kernel grid
     // tabulated radial basis (nullptr = direct evaluation): per species pair
-    // p = t_i S + t_j, rtab_n grid points r_g = g / rtab_scale, each row
-    // [H_0 .. H_{K-1}, H'_0 .. H'_{K-1}] with the cutoff function folded in
+    // p = t_i S + t_j, rtab_n grid intervals [g, g + 1) / rtab_scale, each
+    // holding per k the four cubic coefficients (c0, c1, c2, c3) of H in
+    // t = r rtab_scale - g, the cutoff function folded in
     const float *rtab;
     float rtab_scale;                   // grid points per Angstrom (a power of two)
     int rtab_n;
+    // BF16 weights in the tcgen05 operand layout (nullptr: not built): per
+    // species, product p (forward layers, then the backward chain) at uoff[p]
+    // elements, as [N pass][64-wide K chunk][N/8][8 core matrices][8 x 8]
+    const uint16_t *ub[TMD_MAX_SPECIES];
+    int uoff[2 * MAX_LAYERS];
 };
 
 // persistent grid of the pair kernels for n atoms
@@ -55,6 +62,13 @@ int pair_blocks(const DevModel &dm, int64_t n);
 // shared memory of the FP32 network kernel with tr-atom tiles
 size_t mlp_smem_tr_public(const DevModel &dm, int tr);
 size_t mlp_bf16_smem_bytes(const DevModel &dm);
+// tcgen05 form of the BF16 network (mlp_umma.cu)
+bool mlp_umma_supported(const DevModel &dm);
+tmd_status mlp_umma_launch(const DevModel &dm, const int32_t *perm, const int32_t *types, int64_t n, const float *G,
+                           float *dG, float *e_atom, double *part_e, int *ntile_out, cudaStream_t s);
+// network kernel of the BF16 form: 0 = tcgen05 when the shapes allow it, else
+// mma.sync; 1 = tcgen05 only; 2 = mma.sync only
+int network_kernel();
 
 // One system of a batch (a single evaluation is a batch of one): box, cell
 // grid, first global cell, list radius and the FP32 screening band.
@@ -98,6 +112,7 @@ struct tmd_model {
     size_t dev_bytes = 0;
     int precision = TMD_PREC_FP32;
     float *dev_rtab = nullptr;  // tabulated radial basis (tmd_model_set_radial_table)
+    void *dev_umma = nullptr;   // BF16 weights in the tcgen05 operand layout
     std::vector<double> mu, eta; // radial parameters [S][S][K] (host copy, for tables)
     double rc_exact = 0.0;
 };
@@ -281,6 +296,12 @@ TMD_PAIR_LAUNCHER(launch_pair_k32);
 TMD_PAIR_LAUNCHER(launch_pair_k64);
 TMD_PAIR_LAUNCHER(launch_pair_k128);
 tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, int64_t n_active);
+// BF16 weights in the tcgen05 operand layout from the FP64 weights (leaves
+// dm.ub null when the widths have no BF16 form); status bits of the
+// tensor-core kernels, read and cleared (synchronises)
+tmd_status mlp_umma_build(tmd_model *m, const double *const *weights);
+tmd_status umma_status(int32_t *bits);
+extern int g_network_kernel;
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                        int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
                        double *virial, cudaStream_t s);

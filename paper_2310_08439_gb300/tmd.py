@@ -66,6 +66,8 @@ _SIGS = {
     "tmd_model_set_precision": (C.c_int, [_P, C.c_int32]),
     "tmd_model_set_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
     "tmd_model_set_radial_table": (C.c_int, [_P, C.c_int32]),
+    "tmd_set_network_kernel": (C.c_int, [C.c_int32]),
+    "tmd_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
     "tmd_model_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
     "tmd_autotune": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), C.POINTER(Tuning), _P]),
     "tmd_batch_autotune": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(Tuning), _P]),
@@ -121,6 +123,21 @@ def profile_read(reset=True):
 
 def launch_count():
     return int(lib().tmd_launch_count())
+
+
+NET = {"auto": 0, "tcgen05": 1, "mma_sync": 2}
+
+
+def set_network_kernel(kind="auto"):
+    """BF16 network kernel: "auto" (tcgen05 when the shapes allow), "tcgen05", "mma_sync"."""
+    check(lib().tmd_set_network_kernel(NET[kind]))
+
+
+def device_status():
+    """Raw status bits of the tensor-core kernels since the last call (raises on a timeout)."""
+    b = C.c_int32(0)
+    check(lib().tmd_device_status(C.byref(b)))
+    return int(b.value)
 
 
 def set_graphs(on=True):
