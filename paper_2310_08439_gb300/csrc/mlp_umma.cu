@@ -50,6 +50,11 @@ struct UmmaNet {
     int dercol[MAX_LAYERS];   // TMEM column of act'(a_l), l = 1 .. L-1
     int smem;           // dynamic shared memory bytes
     int blocks_per_sm;
+    int nst;            // weight-chunk stages (2 .. MAX_NST)
+    int block_chunks;   // weight chunks of one species block (all products)
+    int resident;       // one species whose chunks all fit the stages: copied once per block
+    int cstride;        // floats per species of the staged constants: biases, w_out, b_out
+    int cbias[MAX_LAYERS + 1];   // offset of the bias of layer l (l < L), of w_out (l = L), of b_out (l = L + 1)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -154,7 +159,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+__device__ __forceinline__ void tmem_st16_nowait(uint32_t taddr, const float (&v)[16]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
             taddr),
@@ -164,8 +169,8 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
         "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
         "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
         : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // element (row, k) of a chunked operand buffer, in elements from its start
 __device__ __forceinline__ int op_index(int row, int k) {
@@ -187,35 +192,74 @@ __device__ __forceinline__ void store_row16(uint16_t *X, int row, int col0, cons
     *reinterpret_cast<uint4 *>(X + i + 64) = hi;   // next core matrix along K
 }
 
+constexpr int MAX_NST = 4;   // weight-chunk stages at most
+
+// (product, pass, chunk) of chunk i of a species block: the products in
+// order, each as its N passes times its K chunks
+struct ChunkPos {
+    int pr, P, c;
+};
+__device__ __forceinline__ ChunkPos block_chunk(const DevModel &m, const UmmaNet &u, int i) {
+    const int L = m.L;
+    for (int pr = 0; pr < 2 * L; ++pr) {
+        const bool fwd = pr < L;
+        const int l = fwd ? pr : 2 * L - 1 - pr;
+        const int K = fwd ? m.dims[l] : m.dims[l + 1];
+        const int nkc = (K + UKC - 1) / UKC, npass = pr == 2 * L - 1 ? u.npass0 : 1;
+        if (i < nkc * npass) return {pr, i / nkc, i % nkc};
+        i -= nkc * npass;
+    }
+    return {2 * L - 1, 0, 0};
+}
+
 __global__ void __launch_bounds__(UTHREADS, 1)
     k_mlp_umma(DevModel m, UmmaNet u, const int32_t *__restrict__ perm, const int32_t *__restrict__ types, int64_t n,
                const float *__restrict__ G, float *__restrict__ dG, float *__restrict__ e_atom,
                double *__restrict__ part_e, int ntile) {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t s_bar[5];   // full[2], empty[2], done
+    // barriers: full[MAX_NST], empty[MAX_NST] (weight stages), aempty[2] (G stages), done
+    __shared__ __align__(8) uint64_t s_bar[2 * MAX_NST + 3];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ int s_atom[UM], s_type[UM], s_range[2];
     __shared__ float s_e[UM];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int L = m.L, Dd = m.Dd;
-    // dynamic shared memory: X[2] activation buffers, A stages (G chunks), B stages
-    uint16_t *X[2];
-    X[0] = reinterpret_cast<uint16_t *>(smraw);
-    X[1] = X[0] + (size_t)u.xchunks * CHUNK_EL;
-    uint16_t *Ast[2], *Bst[2];
-    Ast[0] = X[1] + (size_t)u.xchunks * CHUNK_EL;
-    Ast[1] = Ast[0] + CHUNK_EL;
-    Bst[0] = Ast[1] + CHUNK_EL;
-    Bst[1] = Bst[0] + (size_t)u.np_max * UKC;
-    const uint32_t bar_full0 = smem_u32(&s_bar[0]), bar_empty0 = smem_u32(&s_bar[2]), bar_done = smem_u32(&s_bar[4]);
+    const int L = m.L, Dd = m.Dd, NST = u.nst;
+    // dynamic shared memory: X[2] activation buffers, 2 G stages, NST weight stages
+    uint16_t *const X0 = reinterpret_cast<uint16_t *>(smraw);
+    uint16_t *const X1 = X0 + (size_t)u.xchunks * CHUNK_EL;
+    uint16_t *const A0 = X1 + (size_t)u.xchunks * CHUNK_EL;
+    uint16_t *const B0 = A0 + 2 * CHUNK_EL;
+    const size_t bstride = (size_t)u.np_max * UKC;   // elements per weight stage
+    // biases, w_out and b_out of every species (read by every epilogue)
+    float *const sconst = reinterpret_cast<float *>(B0 + (size_t)NST * bstride);
+    for (int sp = 0; sp < m.S; ++sp)
+        for (int i = tid; i < u.cstride; i += UTHREADS) {
+            float v = 0.f;
+            int l = 0;
+            while (l <= L && i >= u.cbias[l + 1]) ++l;   // the part i falls in
+            const int j = i - u.cbias[l];
+            if (l < L) {
+                if (j < m.dims[l + 1]) v = m.wf[sp][m.off_f[l] + (size_t)m.dims[l] * m.dims[l + 1] + j];
+            } else if (l == L) {
+                if (j < m.dims[L]) v = m.wb[sp][m.off_b[L] + j];
+            } else if (j == 0) {
+                v = m.wf[sp][m.off_f[L] + m.dims[L]];
+            }
+            sconst[sp * u.cstride + i] = v;
+        }
+    const uint32_t bar0 = smem_u32(&s_bar[0]);
+    auto bar_full = [&](int st) { return bar0 + 8 * st; };
+    auto bar_empty = [&](int st) { return bar0 + 8 * (MAX_NST + st); };
+    auto bar_aempty = [&](int st) { return bar0 + 8 * (2 * MAX_NST + st); };
+    const uint32_t bar_done = bar0 + 8 * (2 * MAX_NST + 2);
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&s_bar[i]), 1);
+        for (int i = 0; i < 2 * MAX_NST + 3; ++i) mbar_init(bar0 + 8 * i, 1);
         s_abort = 0;
         fence_proxy_async();
     }
     volatile int *abort = &s_abort;
-    bool pending[2] = {false, false};   // thread 0: a copy into stage st not yet seen complete
+    uint32_t pending = 0;   // thread 0: stages with a copy not yet seen complete
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(u.tcols)
@@ -227,17 +271,72 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lane quarter, column 0
-    uint32_t q = 0;    // K chunks issued (stage q & 1, use q >> 1)
+    uint32_t q = 0;    // weight chunks consumed (stage q % NST, use q / NST)
+    uint32_t qi = 0;   // weight chunks whose copy was issued (thread 0)
+    uint32_t ua = 0;   // G chunks consumed (stage ua & 1, use ua >> 1)
     uint32_t pd = 0;   // products (passes) completed
-    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int64_t p0 = (int64_t)tile * UM;
-        {
-            const int64_t p = p0 + tid;
-            const int a = p < n ? perm[p] : -1;
-            s_atom[tid] = a;
-            s_type[tid] = a >= 0 ? types[a] : -1;
-            s_e[tid] = 0.f;
+    // thread 0: issue the copies of this block's chunks up to global index lim
+    auto issue_upto = [&](uint32_t lim, uint32_t qbase, int s) {
+        if (u.resident && qi >= (uint32_t)NST) {   // the stages already hold every chunk
+            qi = max(qi, lim);
+            return;
         }
+        while (qi < lim && !*abort) {
+            const int st = qi % NST;
+            const uint32_t use = qi / NST;
+            if (use >= 1) mbar_wait(bar_empty(st), (use - 1) & 1, abort);   // the MMAs that read it are done
+            if (*abort) break;
+            const ChunkPos cp = block_chunk(m, u, (int)(qi - qbase));
+            const bool fwd = cp.pr < L, last = cp.pr == 2 * L - 1;
+            const int l = fwd ? cp.pr : 2 * L - 1 - cp.pr;
+            const int K = fwd ? m.dims[l] : m.dims[l + 1];
+            const int Np = last ? u.np0 : (fwd ? m.dims[l + 1] : m.dims[l]);
+            const int nkc = (K + UKC - 1) / UKC;
+            const uint32_t bytes = (uint32_t)Np * UKC * 2;
+            mbar_expect_tx(bar_full(st), bytes);
+            bulk_g2s(smem_u32(B0 + st * bstride), m.ub[s] + m.uoff[cp.pr] + ((size_t)cp.P * nkc + cp.c) * Np * UKC,
+                     bytes, bar_full(st));
+            pending |= 1u << st;
+            ++qi;
+        }
+    };
+    // Software pipeline over tiles: this thread's atom of the next tile, and
+    // its share of that tile's first G chunk, are loaded into registers while
+    // the current tile runs (half a warp per row: lane l covers rows
+    // 2 it + l / 16 of its warp, columns 4 (l % 16) .. + 3 of the chunk).
+    auto row_atom = [&](int t) -> int {
+        const int64_t p = (int64_t)t * UM + tid;
+        return (t < ntile && p < n) ? perm[p] : -1;
+    };
+    float4 gpre[16];
+    auto load_g0 = [&](int atom_of_my_row) {
+#pragma unroll
+        for (int it = 0; it < 16; ++it) {
+            const int a = __shfl_sync(0xffffffffu, atom_of_my_row, 2 * it + (lane >> 4));
+            const int col = 4 * (lane & 15);
+            // the null row of a missing atom reads as zeros
+            const bool ok = a >= 0 && col < Dd;
+            const float *src = G + (ok ? (size_t)a * Dd + col : 0);
+            float4 v;
+            // issued here, in program order with the surrounding tensor-core
+            // instructions, so that the loads overlap the rest of this tile
+            asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                         : "l"(src));
+            gpre[it] = ok ? v : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    int nx_atom = row_atom(blockIdx.x);
+    int nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
+    load_g0(nx_atom);
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        s_atom[tid] = nx_atom;
+        s_type[tid] = nx_type;
+        s_e[tid] = 0.f;
+        const int my_atom = nx_atom, my_type = nx_type;
+        bool g0_ready = true;   // gpre holds this tile's first chunk
+        // the tile after this one: atom ids now, species and G rows once gpre is consumed
+        nx_atom = row_atom(tile + gridDim.x);
         __syncthreads();
         if (warp == 0) {   // species present in the tile (perm groups atoms by species)
             int lo = TMD_MAX_SPECIES, hi = -1;
@@ -252,9 +351,9 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         }
         __syncthreads();
         const int s_lo = s_range[0], s_hi = s_range[1];
-        const int my_atom = s_atom[tid], my_type = s_type[tid];
         for (int s = s_lo; s <= s_hi; ++s) {
-            const float *wf = m.wf[s];
+            const uint32_t qbase = q, qend = q + (uint32_t)u.block_chunks;
+            if (tid == 0) issue_upto(min(qend, q + NST), qbase, s);
             for (int pr = 0; pr < 2 * L; ++pr) {
                 const bool fwd = pr < L, last = pr == 2 * L - 1;
                 const int l = fwd ? pr : 2 * L - 1 - pr;   // layer of this product
@@ -262,50 +361,56 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                 const int N = fwd ? m.dims[l + 1] : m.dims[l];
                 const int npass = last ? u.npass0 : 1, Np = last ? u.np0 : N;
                 const int nkc = (K + UKC - 1) / UKC;
-                const uint16_t *blob = m.ub[s] + m.uoff[pr];
-                uint16_t *Xin = X[(pr + 1) & 1], *Xout = X[pr & 1];
+                uint16_t *Xin = (pr & 1) ? X0 : X1, *Xout = (pr & 1) ? X1 : X0;
                 for (int P = 0; P < npass; ++P) {
                     for (int c = 0; c < nkc; ++c, ++q) {
-                        const int st = q & 1;
-                        const uint32_t use = q >> 1;
-                        // the MMAs that last read this stage are done
-                        if (use >= 1) mbar_wait(bar_empty0 + 8 * st, (use - 1) & 1, abort);
-                        if (tid == 0) {
-                            const uint32_t bytes = (uint32_t)Np * UKC * 2;
-                            if (!*abort && !pending[st]) {
-                                mbar_expect_tx(bar_full0 + 8 * st, bytes);
-                                bulk_g2s(smem_u32(Bst[st]), blob + ((size_t)P * nkc + c) * Np * UKC, bytes,
-                                         bar_full0 + 8 * st);
-                                pending[st] = true;
-                            }
-                        }
+                        const int st = q % NST;
+                        uint16_t *Ast = A0 + (ua & 1) * CHUNK_EL;
                         if (pr == 0) {   // G chunk c -> BF16 operand (half a warp per row, own rows)
-#pragma unroll 4
+                            if (!(c == 0 && g0_ready)) {
+                                const int r0 = warp * 32 + (lane >> 4);
+#pragma unroll
+                                for (int it = 0; it < 16; ++it) {
+                                    const int a = s_atom[r0 + 2 * it];
+                                    const int col = c * UKC + 4 * (lane & 15);
+                                    gpre[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                    if (a >= 0 && col < Dd)
+                                        gpre[it] = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + col));
+                                }
+                            }
+                            if (ua >= 2) mbar_wait(bar_aempty(ua & 1), ((ua >> 1) - 1) & 1, abort);
+#pragma unroll
                             for (int it = 0; it < 16; ++it) {
                                 const int r = warp * 32 + 2 * it + (lane >> 4);
-                                const int q4 = lane & 15, col = c * UKC + 4 * q4;
-                                const int a = s_atom[r];
-                                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                                if (a >= 0 && col < Dd) v = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + col));
                                 uint2 w;
-                                w.x = pack_bf16(v.x, v.y);
-                                w.y = pack_bf16(v.z, v.w);
-                                *reinterpret_cast<uint2 *>(Ast[st] + op_index(r, 4 * q4)) = w;
+                                w.x = pack_bf16(gpre[it].x, gpre[it].y);
+                                w.y = pack_bf16(gpre[it].z, gpre[it].w);
+                                *reinterpret_cast<uint2 *>(Ast + op_index(r, 4 * (lane & 15))) = w;
                             }
                             fence_proxy_async();
+                            __syncthreads();
+                            // gpre is free: (re)start on the next tile's first chunk
+                            if (g0_ready) nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
+                            g0_ready = false;
+                            load_g0(nx_atom);
                         }
-                        __syncthreads();
                         if (tid == 0 && !*abort) {
-                            if (mbar_wait(bar_full0 + 8 * st, use & 1, abort)) pending[st] = false;
+                            if (!(u.resident && q >= (uint32_t)NST) && mbar_wait(bar_full(st), (q / NST) & 1, abort))
+                                pending &= ~(1u << st);
                             tc_fence_after();
                             const int kl = min(UKC, K - c * UKC);
-                            const uint32_t a0 = smem_u32(pr == 0 ? Ast[st] : Xin + (size_t)c * CHUNK_EL);
-                            const uint32_t b0 = smem_u32(Bst[st]);
+                            const uint32_t a0 = smem_u32(pr == 0 ? Ast : Xin + (size_t)c * CHUNK_EL);
+                            const uint32_t b0 = smem_u32(B0 + st * bstride);
                             const uint32_t id = idesc_bf16(Np);
                             for (int j = 0; j < kl / 16; ++j)
                                 umma_bf16(tmem, sdesc(a0 + 256 * j), sdesc(b0 + 256 * j), id, (c | j) != 0);
-                            umma_commit(bar_empty0 + 8 * st);
+                            umma_commit(bar_empty(st));
+                            if (pr == 0) umma_commit(bar_aempty(ua & 1));
+                            // keep the stages filled: the copy for chunk q + NST - 1 reuses the
+                            // stage of chunk q - 1, whose MMAs were issued one chunk earlier
+                            issue_upto(min(qend, q + NST), qbase, s);
                         }
+                        if (pr == 0) ++ua;
                     }
                     if (tid == 0) umma_commit(bar_done);
                     mbar_wait(bar_done, pd & 1, abort);
@@ -313,33 +418,35 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                     tc_fence_after();
                     // epilogue: this thread's row of the accumulator
                     if (fwd) {
-                        const float *bias = wf + m.off_f[l] + (size_t)K * N;
+                        const float *cs = sconst + s * u.cstride;
+                        const float *bias = cs + u.cbias[l];
                         const bool last_fwd = l == L - 1;
-                        const float *wout = m.wb[s] + m.off_b[L];
+                        const float *wout = cs + u.cbias[L];
                         float eacc = 0.f;
                         for (int c0 = 0; c0 < N; c0 += 16) {
                             float v[16], a[16], d[16];
                             tmem_ld16(trow + c0, v);
 #pragma unroll
                             for (int e = 0; e < 16; ++e) {
-                                a[e] = act_f_bf16(m.act, v[e] + __ldg(bias + c0 + e), m.sp_b);
+                                a[e] = act_f_bf16(m.act, v[e] + bias[c0 + e], m.sp_b);
                                 d[e] = act_da(m.act, a[e], m.sp_b);
                             }
                             if (!last_fwd) {
                                 store_row16(Xout, tid, c0, a);
-                                tmem_st16(trow + u.dercol[l + 1] + c0, d);
+                                tmem_st16_nowait(trow + u.dercol[l + 1] + c0, d);
                             } else {   // E_a partial and dz_L = w_out * act'(a_L)
 #pragma unroll
                                 for (int e = 0; e < 16; ++e) {
-                                    const float w = __ldg(wout + c0 + e);
+                                    const float w = wout[c0 + e];
                                     eacc = fmaf(w, a[e], eacc);
                                     d[e] *= w;
                                 }
                                 store_row16(Xout, tid, c0, d);
                             }
                         }
+                        if (!last_fwd) tmem_st_wait();
                         if (last_fwd && my_type == s) {
-                            const float e = eacc + __ldg(wf + m.off_f[L] + m.dims[L]);
+                            const float e = eacc + cs[u.cbias[L + 1]];
                             s_e[tid] = e;
                             if (e_atom) e_atom[my_atom] = e;
                         }
@@ -381,8 +488,8 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         __syncthreads();
     }
     if (tid == 0 && *abort) {   // bounded drain of this block's copies and MMAs in flight
-        for (int st = 0; st < 2; ++st)
-            if (pending[st]) mbar_drain(bar_full0 + 8 * st, ((q >> 1) + ((q & 1) > st ? 1 : 0) - 1) & 1);
+        for (uint32_t k = (qi > (uint32_t)NST ? qi - NST : 0); k < qi; ++k)
+            if (pending & (1u << (k % NST))) mbar_drain(bar_full(k % NST), (k / NST) & 1);
         umma_commit(bar_done);
         mbar_drain(bar_done, pd & 1);
     }
@@ -420,8 +527,40 @@ bool plan(const DevModel &dm, UmmaNet &u) {
     if (col > 512) return false;
     u.tcols = 32;
     while (u.tcols < col) u.tcols <<= 1;
-    const size_t smem = sizeof(uint16_t) * ((size_t)2 * u.xchunks * CHUNK_EL + 2 * CHUNK_EL + (size_t)2 * u.np_max * UKC);
-    if (smem > 200 * 1024) return false;
+    u.block_chunks = 0;
+    for (int pr = 0; pr < 2 * L; ++pr) {
+        const bool fwd = pr < L;
+        const int l = fwd ? pr : 2 * L - 1 - pr;
+        const int K = fwd ? dm.dims[l] : dm.dims[l + 1];
+        u.block_chunks += ((K + UKC - 1) / UKC) * (pr == 2 * L - 1 ? u.npass0 : 1);
+    }
+    // staged constants per species: bias of each layer, w_out, b_out
+    int co = 0;
+    for (int l = 0; l < L; ++l) {
+        u.cbias[l] = co;
+        co += dm.dims[l + 1];
+    }
+    u.cbias[L] = co;
+    co += dm.dims[L];
+    u.cbias[L + 1] = co;
+    co += 1;
+    u.cstride = (co + 3) & ~3;
+    const size_t cbytes = sizeof(float) * (size_t)u.cstride * dm.S;
+    // as many weight stages (up to MAX_NST) as 200 KB of shared memory allow
+    const size_t fixed = (size_t)2 * u.xchunks * CHUNK_EL + 2 * CHUNK_EL;
+    size_t smem = 0;
+    for (u.nst = MAX_NST; u.nst >= 2; --u.nst) {
+        smem = sizeof(uint16_t) * (fixed + (size_t)u.nst * u.np_max * UKC) + cbytes;
+        if (smem <= 200 * 1024) break;
+    }
+    if (u.nst < 2) return false;
+    // one species with at most MAX_NST chunks: exactly that many stages, kept
+    // resident (chunk i of every block lives in stage i)
+    u.resident = dm.S == 1 && u.block_chunks <= u.nst;
+    if (u.resident) {
+        u.nst = u.block_chunks;
+        smem = sizeof(uint16_t) * (fixed + (size_t)u.nst * u.np_max * UKC) + cbytes;
+    }
     u.smem = (int)smem;
     u.blocks_per_sm = std::max(1, std::min(512 / u.tcols, (int)((220 * 1024) / (smem + 2048))));
     return true;
