@@ -305,7 +305,7 @@ def paper_models_measure(tmd, torch, steps=5):
                 ms = e0.elapsed_time(e1) / steps
                 row[prec] = {"atom_evals_per_s": s.n / (ms * 1e-3), "ms_per_eval": ms,
                              "kernel_ms": {kk: v[1] / max(v[0], 1) for kk, v in ks.items()
-                                           if kk in ("k_desc", "k_force", "k_mlp", "k_mlp_bf16")}}
+                                           if kk in ("k_desc", "k_force", "k_mlp", "k_mlp_bf16", "k_mlp_umma")}}
             out[f"k{k}_a{a}"] = row
             del nl, m, pos, types, E, F, W
             torch.cuda.empty_cache()
@@ -549,6 +549,32 @@ def main():
              other: {"value": replica_throughput(world, n, args.steps, t_other * 1e-3),
                      "ms_per_step": t_other / args.steps}}
     model.set_precision(args.precision)
+
+    # the same MD loop with the skin criterion of the velocity-Verlet step
+    # (rebuild only once an atom moved more than skin/2 since the last build):
+    # a longer run, so that the rebuilds it needs fall inside the timed region
+    skin_steps = max(4 * args.steps, 40)
+    for _ in range(args.warmup - 1):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=0, thermo=False)
+    builds0 = sysm.step(model, w.dt_fs, 1, rebuild_every=0, thermo=True)["rebuilds"]
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(skin_steps):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=0, thermo=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_skin = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    # one more (untimed) step reads the rebuild counter: the count covers the
+    # timed steps and that one
+    builds1 = sysm.step(model, w.dt_fs, 1, rebuild_every=0, thermo=True)["rebuilds"]
+    forms[args.precision + "_skin_rebuild"] = {
+        "value": replica_throughput(world, n, skin_steps, t_skin * 1e-3), "ms_per_step": t_skin / skin_steps,
+        "steps": skin_steps, "rebuilds_in_timed_steps_plus_one": int(builds1 - builds0),
+        "what": "neighbour table rebuilt only when an atom moved more than skin/2 (the MD loop's own criterion); "
+                "the host reads the rebuild flag once per step"}
 
     # end to end through the host-buffer C-ABI call (pinned host state)
     e2e = None
