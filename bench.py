@@ -611,7 +611,7 @@ def main():
     # units: in-cutoff pairs of the configuration at the timed state
     nl = tmd.NeighborList()
     p_now, _, _ = sysm.get_state()
-    pos_d = torch.as_tensor(p_now, device=dev)
+    pos_d = torch.as_tensor(np.mod(p_now, s.box), device=dev)   # unwrapped since the last rebuild
     types_d = torch.as_tensor(s.types, device=dev)
     nl.build(pos_d, types_d, s.box, s.pbc, w.model.rc)
     pairs = nl.size()[1]          # entries inside rc = in-cutoff pairs
