@@ -178,8 +178,7 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
 #pragma unroll
                             for (int o = 0; o < 4; ++o) pp[i][o] = 0.f;
                         const int ke = min(kg + 16, kc);
-#pragma unroll 8
-                        for (int k = kg; k < ke; ++k) {
+                        auto step = [&](int k) {
                             const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
                             const float4 bv = *reinterpret_cast<const float4 *>(b + k * np);
                             const float ai[4] = {av.x, av.y, av.z, av.w};
@@ -190,6 +189,12 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
                                 pp[i][2] = fmaf(ai[i], bv.z, pp[i][2]);
                                 pp[i][3] = fmaf(ai[i], bv.w, pp[i][3]);
                             }
+                        };
+                        if (ke - kg == 16) {
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) step(kg + k);
+                        } else {
+                            for (int k = kg; k < ke; ++k) step(k);
                         }
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
