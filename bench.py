@@ -130,22 +130,26 @@ class ClockSampler:
 
 def kernel_traffic(name):
     """Per-launch DRAM bytes of ``name`` from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+    taken on the current sources of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     import hashlib
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2310_08439_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
     with open(path) as f:
         d = json.load(f)
-    if d.get("csrc_sha256") != h.hexdigest():
-        return None
     k = d.get("kernels", {}).get(name)
-    return None if k is None else k.get("bytes_per_launch_full")
+    if k is None:
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2310_08439_gb300", "csrc")
+    for fn in k.get("sources", []):
+        fp = os.path.join(csrc, fn)
+        if not os.path.exists(fp):
+            return None
+        h.update(open(fp, "rb").read())
+    if k.get("sources_sha256") != h.hexdigest():
+        return None
+    return k.get("bytes_per_launch_full")
 
 
 def workload(name, reps=64):
