@@ -491,7 +491,7 @@ __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, con
         tc = tab_cell(tab, K, m.rtab_scale, r_hi, r_lo);
     else
         cutoff_fn(r_hi, m.inv_rc, fc, dfc);
-    constexpr int KU = K > 32 ? 32 : K;   // channels per unrolled block
+    constexpr int KU = K > 32 ? 16 : K;   // channels per unrolled block
 #pragma unroll 1
     for (int kb = 0; kb < K; kb += KU)
 #pragma unroll
