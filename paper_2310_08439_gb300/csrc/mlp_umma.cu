@@ -53,6 +53,7 @@ struct UmmaNet {
     int nst;            // weight-chunk stages (2 .. MAX_NST)
     int block_chunks;   // weight chunks of one species block (all products)
     int resident;       // one species whose chunks all fit the stages: copied once per block
+    int alias;          // one K chunk in the first layer: its G stage is also activation buffer X0
     int cstride;        // floats per species of the staged constants: biases, w_out, b_out
     int cbias[MAX_LAYERS + 1];   // offset of the bias of layer l (l < L), of w_out (l = L), of b_out (l = L + 1)
 };
@@ -226,10 +227,14 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = m.L, Dd = m.Dd, NST = u.nst;
     // dynamic shared memory: X[2] activation buffers, 2 G stages, NST weight stages
+    // (alias: the first layer has one K chunk, so the single G stage is also
+    // the first activation buffer -- each use of it is ordered by the
+    // product-completion waits)
+    const int na = u.alias ? 1 : 2;   // G stages
     uint16_t *const X0 = reinterpret_cast<uint16_t *>(smraw);
-    uint16_t *const X1 = X0 + (size_t)u.xchunks * CHUNK_EL;
-    uint16_t *const A0 = X1 + (size_t)u.xchunks * CHUNK_EL;
-    uint16_t *const B0 = A0 + 2 * CHUNK_EL;
+    uint16_t *const X1 = X0 + (size_t)(u.alias ? max(u.xchunks, 1) : u.xchunks) * CHUNK_EL;
+    uint16_t *const A0 = u.alias ? X0 : X1 + (size_t)u.xchunks * CHUNK_EL;
+    uint16_t *const B0 = u.alias ? X1 + (size_t)u.xchunks * CHUNK_EL : A0 + 2 * CHUNK_EL;
     const size_t bstride = (size_t)u.np_max * UKC;   // elements per weight stage
     // biases, w_out and b_out of every species (read by every epilogue)
     float *const sconst = reinterpret_cast<float *>(B0 + (size_t)NST * bstride);
@@ -365,7 +370,9 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                 for (int P = 0; P < npass; ++P) {
                     for (int c = 0; c < nkc; ++c, ++q) {
                         const int st = q % NST;
-                        uint16_t *Ast = A0 + (ua & 1) * CHUNK_EL;
+                        const int ast = ua % na;
+                        const uint32_t ause = ua / na;
+                        uint16_t *Ast = A0 + ast * CHUNK_EL;
                         if (pr == 0) {   // G chunk c -> BF16 operand (half a warp per row, own rows)
                             if (!(c == 0 && g0_ready)) {
                                 const int r0 = warp * 32 + (lane >> 4);
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                                         gpre[it] = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + col));
                                 }
                             }
-                            if (ua >= 2) mbar_wait(bar_aempty(ua & 1), ((ua >> 1) - 1) & 1, abort);
+                            if (ause >= 1) mbar_wait(bar_aempty(ast), (ause - 1) & 1, abort);
 #pragma unroll
                             for (int it = 0; it < 16; ++it) {
                                 const int r = warp * 32 + 2 * it + (lane >> 4);
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                             for (int j = 0; j < kl / 16; ++j)
                                 umma_bf16(tmem, sdesc(a0 + 256 * j), sdesc(b0 + 256 * j), id, (c | j) != 0);
                             umma_commit(bar_empty(st));
-                            if (pr == 0) umma_commit(bar_aempty(ua & 1));
+                            if (pr == 0) umma_commit(bar_aempty(ast));
                             // keep the stages filled: the copy for chunk q + NST - 1 reuses the
                             // stage of chunk q - 1, whose MMAs were issued one chunk earlier
                             issue_upto(min(qend, q + NST), qbase, s);
@@ -500,7 +507,10 @@ __global__ void __launch_bounds__(UTHREADS, 1)
 }
 
 // launch plan for a model, or false when the shapes do not fit
+int reg_blocks_per_sm();
+
 bool plan(const DevModel &dm, UmmaNet &u) {
+    const int reg_blocks = reg_blocks_per_sm();
     std::memset(&u, 0, sizeof(u));
     const int L = dm.L;
     for (int s = 0; s < dm.S; ++s)
@@ -546,24 +556,43 @@ bool plan(const DevModel &dm, UmmaNet &u) {
     co += 1;
     u.cstride = (co + 3) & ~3;
     const size_t cbytes = sizeof(float) * (size_t)u.cstride * dm.S;
-    // as many weight stages (up to MAX_NST) as 200 KB of shared memory allow
-    const size_t fixed = (size_t)2 * u.xchunks * CHUNK_EL + 2 * CHUNK_EL;
-    size_t smem = 0;
-    for (u.nst = MAX_NST; u.nst >= 2; --u.nst) {
-        smem = sizeof(uint16_t) * (fixed + (size_t)u.nst * u.np_max * UKC) + cbytes;
-        if (smem <= 200 * 1024) break;
+    // shared-memory layout: as many blocks per SM as TMEM, shared memory and
+    // registers allow, then resident weights, then the deepest weight ring
+    u.alias = (dm.Dd + UKC - 1) / UKC == 1;
+    const size_t fixed = u.alias ? (size_t)(std::max(u.xchunks, 1) + u.xchunks) * CHUNK_EL
+                                 : (size_t)2 * u.xchunks * CHUNK_EL + 2 * CHUNK_EL;
+    auto smem_of = [&](int nst) { return sizeof(uint16_t) * (fixed + (size_t)nst * u.np_max * UKC) + cbytes; };
+    auto blocks_of = [&](size_t sm) {
+        // 228 KB per SM, about 3 KB of static shared memory and 1 KB reserved per block
+        return std::min(std::min(512 / u.tcols, reg_blocks), (int)((228 * 1024) / (sm + 4096)));
+    };
+    int best = -1, best_key = -1;
+    for (int nst = 2; nst <= MAX_NST; ++nst) {
+        const size_t sm = smem_of(nst);
+        if (sm > 200 * 1024) continue;
+        const bool res = dm.S == 1 && u.block_chunks == nst;
+        const int key = blocks_of(sm) * 16 + (res ? 8 : 0) + nst;
+        if (key > best_key) { best_key = key; best = nst; }
     }
-    if (u.nst < 2) return false;
-    // one species with at most MAX_NST chunks: exactly that many stages, kept
-    // resident (chunk i of every block lives in stage i)
-    u.resident = dm.S == 1 && u.block_chunks <= u.nst;
-    if (u.resident) {
-        u.nst = u.block_chunks;
-        smem = sizeof(uint16_t) * (fixed + (size_t)u.nst * u.np_max * UKC) + cbytes;
-    }
-    u.smem = (int)smem;
-    u.blocks_per_sm = std::max(1, std::min(512 / u.tcols, (int)((220 * 1024) / (smem + 2048))));
+    if (best < 0) return false;
+    u.nst = best;
+    u.resident = dm.S == 1 && u.block_chunks == u.nst;
+    u.smem = (int)smem_of(u.nst);
+    u.blocks_per_sm = std::max(1, blocks_of(u.smem));
     return true;
+}
+
+// blocks of k_mlp_umma that the register file holds at once
+int reg_blocks_per_sm() {
+    static int blocks = 0;
+    if (!blocks) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, k_mlp_umma) == cudaSuccess && a.numRegs > 0)
+            blocks = std::max(1, 65536 / (a.numRegs * UTHREADS));
+        else
+            blocks = 1;
+    }
+    return blocks;
 }
 
 uint16_t bf16_bits(double x) {
