@@ -141,6 +141,21 @@ tmd_status tmd_model_set_precision(tmd_model *model, int32_t precision);
  * Synchronises the device. */
 tmd_status tmd_model_set_radial_table(tmd_model *model, int32_t points_per_angstrom);
 
+/* Tabulated radial basis from the caller's own radial functions (the same
+ * section: H_abck may come from any mapping of R, e.g. an embedding network,
+ * once tabulated).  H, dH (host, FP64) [S][S][n_points][K]: H_k and dH_k/dR
+ * for (centre species, neighbour species, k) at R_g = g / points_per_angstrom,
+ * g = 0 .. n_points - 1; n_points >= ceil(rc * points_per_angstrom) (every
+ * grid point below rc).  Values at R_g >= rc are ignored and taken as zero
+ * (the cutoff is folded into the table: the caller's functions should go
+ * smoothly to zero at rc).  Interpolation and storage as in
+ * tmd_model_set_radial_table, which (or this call) replaces the previous
+ * table; tmd_model_set_radial_table(model, 0) returns to the model's
+ * Gaussians.  Errors: INVALID_ARG (ppa not a power of two in [16, 1024], NULL
+ * arrays, too few points, a non-finite value), OOM/CUDA.  Synchronises. */
+tmd_status tmd_model_set_radial_table_values(tmd_model *model, int32_t points_per_angstrom, int32_t n_points,
+                                             const double *H, const double *dH);
+
 /*
  * CUDA graphs (the paper has no counterpart: a launch-overhead measure of this
  * implementation).  The MD step loops (tmd_step, tmd_batch_step) and

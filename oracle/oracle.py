@@ -54,7 +54,8 @@ class _CModel(C.Structure):
                 ("rc", C.c_double), ("sp_b", C.c_double),
                 ("mu", C.POINTER(C.c_double)), ("eta", C.POINTER(C.c_double)),
                 ("widths", C.POINTER(C.c_int32)), ("w", C.POINTER(C.POINTER(C.c_double))),
-                ("tab_ppa", C.c_int32)]
+                ("tab_ppa", C.c_int32), ("tab_n", C.c_int32),
+                ("tab_H", C.POINTER(C.c_double)), ("tab_dH", C.POINTER(C.c_double))]
 
 
 def _dp(a):
@@ -93,9 +94,17 @@ class OracleModel:
     radial_table = 0: H evaluated directly; > 0: H and H' interpolated from a
     table with that many grid points per Angstrom."""
 
-    def __init__(self, params, radial_table=0):
+    def __init__(self, params, radial_table=0, table_values=None):
         self.params = params
         self.radial_table = int(radial_table)
+        # table_values = (H, dH) [S][S][n][K]: the caller's radial functions at
+        # r_g = g / radial_table instead of the Gaussians
+        self._tab = None
+        if table_values is not None:
+            H, dH = (np.ascontiguousarray(a, dtype=np.float64) for a in table_values)
+            if H.shape != dH.shape or H.ndim != 4:
+                raise ValueError("table values must both be [S][S][n][K]")
+            self._tab = (H, dH)
         S, K = params.n_species, params.n_radial
         self._mu = np.ascontiguousarray(params.mu, dtype=np.float64).reshape(S * S * K)
         self._eta = np.ascontiguousarray(params.eta, dtype=np.float64).reshape(S * S * K)
@@ -108,7 +117,9 @@ class OracleModel:
         self.c = _CModel(S, K, len(params.widths), act, float(params.rc),
                          float(params.squareplus_b), _dp(self._mu), _dp(self._eta),
                          _ip(self._widths), C.cast(self._wptr, C.POINTER(C.POINTER(C.c_double))),
-                         self.radial_table)
+                         self.radial_table, 0 if self._tab is None else self._tab[0].shape[2],
+                         None if self._tab is None else _dp(self._tab[0]),
+                         None if self._tab is None else _dp(self._tab[1]))
 
     @property
     def n_desc(self):

@@ -52,6 +52,9 @@ typedef struct {
     const double *const *w;     /* [S] flat weights: per layer W[out][in], b */
     int32_t tab_ppa;    /* 0: H evaluated directly; > 0: tabulated H with    */
                         /* this many grid points per Angstrom (see below)    */
+    int32_t tab_n;      /* grid points of tab_H / tab_dH per species pair     */
+    const double *tab_H;   /* NULL: grid values from the Gaussians; else the  */
+    const double *tab_dH;  /* caller's H, H' [S][S][tab_n][K] at R_g = g/ppa  */
 } tmdo_model;
 
 #define NMOM 20
@@ -160,8 +163,20 @@ static void radial_tab(const tmdo_model *m, int ti, int tj, double r, double *H,
     const double t = x - g;
     double H0[256], dH0[256], H1[256], dH1[256];
     const double r0 = g * h, r1 = (g + 1.0) * h;
-    radial_direct(m, ti, tj, r0, H0, dH0);   /* zero for r0 >= rc */
-    radial_direct(m, ti, tj, r1, H1, dH1);
+    if (m->tab_H) {   /* the caller's grid values; zero from rc on */
+        const int gi = (int)g;
+        for (int k = 0; k < K; ++k) {
+            const size_t base = ((size_t)ti * m->S + tj) * (size_t)m->tab_n;
+            const int ok0 = r0 < m->rc && gi < m->tab_n, ok1 = r1 < m->rc && gi + 1 < m->tab_n;
+            H0[k] = ok0 ? m->tab_H[(base + gi) * K + k] : 0.0;
+            dH0[k] = ok0 ? m->tab_dH[(base + gi) * K + k] : 0.0;
+            H1[k] = ok1 ? m->tab_H[(base + gi + 1) * K + k] : 0.0;
+            dH1[k] = ok1 ? m->tab_dH[(base + gi + 1) * K + k] : 0.0;
+        }
+    } else {
+        radial_direct(m, ti, tj, r0, H0, dH0);   /* zero for r0 >= rc */
+        radial_direct(m, ti, tj, r1, H1, dH1);
+    }
     for (int k = 0; k < K; ++k) tmdo_hermite(H0[k], dH0[k], H1[k], dH1[k], h, t, &H[k], &dH[k]);
 }
 

@@ -438,12 +438,12 @@ tmd_status tmd_model_destroy(tmd_model *m) {
     return TMD_OK;
 }
 
-tmd_status tmd_model_set_radial_table(tmd_model *m, int32_t ppa) {
-    g_err[0] = 0;
-    if (!m || ppa < 0 || (ppa != 0 && (ppa < 16 || ppa > 1024 || (ppa & (ppa - 1)) != 0))) {
-        set_error("points_per_angstrom must be 0 or a power of two in [16, 1024]");
-        return TMD_ERR_INVALID_ARG;
-    }
+extern "C++" {
+namespace {
+
+bool table_ppa_ok(int32_t ppa) { return ppa >= 16 && ppa <= 1024 && (ppa & (ppa - 1)) == 0; }
+
+void table_clear(tmd_model *m) {
     if (m->dev_rtab) {
         cudaFree(m->dev_rtab);
         m->dev_rtab = nullptr;
@@ -451,37 +451,36 @@ tmd_status tmd_model_set_radial_table(tmd_model *m, int32_t ppa) {
     m->dm.rtab = nullptr;
     m->dm.rtab_scale = 0.f;
     m->dm.rtab_n = 0;
-    if (ppa == 0) return TMD_OK;
+}
+
+// Build and upload the tabulated radial basis from node values:
+// node(p, k, g, H, dH) gives H and H' of species pair p, channel k at
+// r_g = g / ppa (only called for r_g < rc; nodes from rc on are zero, the
+// cutoff folded into the table).  Interval g = [g h, (g + 1) h), h = 1/ppa,
+// holds the cubic Hermite polynomial through H and H' at both ends as
+// coefficients in t = (r - g h)/h: H = c0 + c1 t + c2 t^2 + c3 t^3,
+// H' = (c1 + 2 c2 t + 3 c3 t^2) ppa.  The coefficients are formed in FP64 and
+// rounded to FP32 (storing node values instead would lose H' to cancellation
+// in (H_g+1 - H_g) ppa once the grid is fine).  Intervals up to
+// floor(rc ppa) + 1: an FP32 r just below rc can round into the interval one
+// past floor(rc ppa) when rc ppa sits within an ulp of an integer.
+template <typename Node>
+tmd_status table_build(tmd_model *m, int32_t ppa, Node &&node) {
     const int S = m->dm.S, K = m->dm.K;
     const double rcd = m->rc_exact;
-    // Interval g = [g h, (g + 1) h), h = 1/ppa, holds the cubic Hermite
-    // polynomial through H and H' at both ends as coefficients in
-    // t = (r - g h)/h: H = c0 + c1 t + c2 t^2 + c3 t^3, H' = (c1 + 2 c2 t +
-    // 3 c3 t^2) ppa.  The coefficients are formed in FP64 and rounded to FP32
-    // (storing node values instead would lose H' to cancellation in
-    // (H_g+1 - H_g) ppa once the grid is fine).  Node values are zero from rc
-    // on (the cutoff folded into the table).  Intervals up to floor(rc ppa) + 1:
-    // an FP32 r just below rc can round into the interval one past
-    // floor(rc ppa) when rc ppa sits within an ulp of an integer.
     const int n = (int)std::floor(rcd * ppa) + 2;
     std::vector<float> h((size_t)S * S * n * 4 * K, 0.f);
-    const double pi = 3.14159265358979323846, hs = 1.0 / ppa;
-    auto node = [&](int p, int k, double r, double &H, double &dH) {
+    const double hs = 1.0 / ppa;
+    auto at = [&](int p, int k, int g, double &H, double &dH) {
         H = dH = 0.0;
-        if (!(r < rcd)) return;
-        const double fc = 0.5 * (std::cos(pi * r / rcd) + 1.0);
-        const double dfc = -0.5 * pi / rcd * std::sin(pi * r / rcd);
-        const double mu = m->mu[(size_t)p * K + k], eta = m->eta[(size_t)p * K + k];
-        const double t = r - mu, f = std::exp(-eta * t * t);
-        H = f * fc;
-        dH = f * (-2.0 * eta * t * fc + dfc);
+        if ((double)g * hs < rcd) node(p, k, g, H, dH);
     };
     for (int p = 0; p < S * S; ++p)
         for (int g = 0; g < n; ++g)
             for (int k = 0; k < K; ++k) {
                 double y0, d0, y1, d1;
-                node(p, k, g * hs, y0, d0);
-                node(p, k, (g + 1) * hs, y1, d1);
+                at(p, k, g, y0, d0);
+                at(p, k, g + 1, y1, d1);
                 const double dy = y1 - y0, s0 = d0 * hs, s1 = d1 * hs;
                 float *c = &h[(((size_t)p * n + g) * K + k) * 4];
                 c[0] = (float)y0;
@@ -497,6 +496,58 @@ tmd_status tmd_model_set_radial_table(tmd_model *m, int32_t ppa) {
     m->dm.rtab_scale = (float)ppa;
     m->dm.rtab_n = n;
     return TMD_OK;
+}
+
+}  // namespace
+}  // extern "C++"
+
+tmd_status tmd_model_set_radial_table(tmd_model *m, int32_t ppa) {
+    g_err[0] = 0;
+    if (!m || ppa < 0 || (ppa != 0 && !table_ppa_ok(ppa))) {
+        set_error("points_per_angstrom must be 0 or a power of two in [16, 1024]");
+        return TMD_ERR_INVALID_ARG;
+    }
+    table_clear(m);
+    if (ppa == 0) return TMD_OK;
+    // H_k = f_k f_c and H'_k of the model's Gaussians at the grid points, FP64
+    const int K = m->dm.K;
+    const double rcd = m->rc_exact, pi = 3.14159265358979323846, hs = 1.0 / ppa;
+    return table_build(m, ppa, [&](int p, int k, int g, double &H, double &dH) {
+        const double r = g * hs;
+        const double fc = 0.5 * (std::cos(pi * r / rcd) + 1.0);
+        const double dfc = -0.5 * pi / rcd * std::sin(pi * r / rcd);
+        const double mu = m->mu[(size_t)p * K + k], eta = m->eta[(size_t)p * K + k];
+        const double t = r - mu, f = std::exp(-eta * t * t);
+        H = f * fc;
+        dH = f * (-2.0 * eta * t * fc + dfc);
+    });
+}
+
+tmd_status tmd_model_set_radial_table_values(tmd_model *m, int32_t ppa, int32_t n_points, const double *H,
+                                             const double *dH) {
+    g_err[0] = 0;
+    if (!m || !table_ppa_ok(ppa) || !H || !dH) {
+        set_error("points_per_angstrom must be a power of two in [16, 1024]; H and dH non-NULL");
+        return TMD_ERR_INVALID_ARG;
+    }
+    const int S = m->dm.S, K = m->dm.K;
+    const int need = (int)std::ceil(m->rc_exact * ppa);   // every grid point below rc
+    if (n_points < need || n_points > need + 4096) {
+        set_error("n_points %d: the grid must cover [0, rc): at least %d points per species pair", n_points, need);
+        return TMD_ERR_INVALID_ARG;
+    }
+    const size_t total = (size_t)S * S * n_points * K;
+    if (!finite_all(H, total) || !finite_all(dH, total)) {
+        set_error("non-finite table value");
+        return TMD_ERR_INVALID_ARG;
+    }
+    table_clear(m);
+    // caller's values at r_g = g / ppa, [S][S][n_points][K]
+    return table_build(m, ppa, [&](int p, int k, int g, double &h, double &d) {
+        const size_t i = ((size_t)p * n_points + g) * K + k;
+        h = H[i];
+        d = dH[i];
+    });
 }
 
 tmd_status tmd_model_set_precision(tmd_model *m, int32_t precision) {

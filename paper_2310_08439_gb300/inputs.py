@@ -352,3 +352,28 @@ def cluster(n_atoms, radius, seed, n_species=1):
 
 
 WORKLOADS = {"tiny": tiny, "medium": medium, "large": large, "batch": batch, "serve": serve}
+
+
+def embedding_radial_table(S, K, rc, ppa, seed):
+    """Radial functions from a small DP-style embedding network, as a table:
+    per species pair m(R) = tanh(W2 tanh(W1 R + b1) + b2) (1 -> 8 -> K, seeded
+    random weights) times the smooth step (1 - (R/rc)^2)^2, which reaches zero
+    with zero slope at rc.  Returns (H, dH) [S][S][n][K] at R_g = g / ppa,
+    n = ceil(rc ppa), with the exact derivative."""
+    rng = np.random.default_rng(seed)
+    n = int(math.ceil(rc * ppa))
+    r = np.arange(n) / ppa
+    H = np.zeros((S, S, n, K))
+    dH = np.zeros_like(H)
+    w = np.clip(1.0 - (r / rc) ** 2, 0.0, None)
+    sw, dsw = w * w, -4.0 * w * r / (rc * rc)
+    for a in range(S):
+        for b in range(S):
+            W1, b1 = rng.normal(0, 1.0, 8), rng.normal(0, 0.5, 8)
+            W2, b2 = rng.normal(0, 0.5, (K, 8)), rng.normal(0, 0.3, K)
+            u = np.tanh(np.outer(r, W1) + b1)
+            m = np.tanh(u @ W2.T + b2)
+            dm = (1 - m * m) * (((1 - u * u) * W1) @ W2.T)
+            H[a, b] = sw[:, None] * m
+            dH[a, b] = dsw[:, None] * m + sw[:, None] * dm
+    return H, dH

@@ -66,6 +66,8 @@ _SIGS = {
     "tmd_model_set_precision": (C.c_int, [_P, C.c_int32]),
     "tmd_model_set_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
     "tmd_model_set_radial_table": (C.c_int, [_P, C.c_int32]),
+    "tmd_model_set_radial_table_values": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                                    C.POINTER(C.c_double)]),
     "tmd_set_network_kernel": (C.c_int, [C.c_int32]),
     "tmd_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
     "tmd_model_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
@@ -226,6 +228,18 @@ class Model:
         """Read H and H' from a table with this many points per Angstrom
         (a power of two in [16, 1024]); 0 returns to direct evaluation."""
         check(lib().tmd_model_set_radial_table(self.handle, int(points_per_angstrom)))
+        self.radial_table = int(points_per_angstrom)
+
+    def set_radial_table_values(self, points_per_angstrom, H, dH):
+        """Table from the caller's radial functions: H, dH [S][S][n_points][K]
+        (float64) at r_g = g / points_per_angstrom."""
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        dH = np.ascontiguousarray(dH, dtype=np.float64)
+        if H.shape != dH.shape or H.ndim != 4:
+            raise ValueError("H and dH must both be [S][S][n_points][K]")
+        check(lib().tmd_model_set_radial_table_values(self.handle, int(points_per_angstrom), int(H.shape[2]),
+                                                      H.ctypes.data_as(C.POINTER(C.c_double)),
+                                                      dH.ctypes.data_as(C.POINTER(C.c_double))))
         self.radial_table = int(points_per_angstrom)
 
     @property

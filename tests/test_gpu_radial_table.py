@@ -177,3 +177,45 @@ def test_table_md_graph_replay_matches_eager(tmdlib):
         res.append(g.get_state(stream=side))
     for a, b in zip(res[0], res[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("ppa", [64, 256])
+def test_embedding_network_radial_table(tmdlib, ppa):
+    """Radial functions from an embedding network (given as a table of H, H')
+    on the GPU against the oracle built from the same table.  The network's
+    first layer is normalised by the descriptor RMS of this radial basis (as
+    every workload's model is), so that the comparison is well conditioned."""
+    rng = np.random.default_rng(ppa)
+    pos, box = I.lattice("fcc", (5, 5, 4), 3.61)
+    s = I.System(I.jitter_and_wrap(pos, box, 0.1, rng), rng.integers(0, 2, len(pos)).astype(np.int32), box,
+                 np.ones(3, np.int32))
+    S, K, rc, widths = 2, 16, 6.0, [32, 32]
+    H, dH = I.embedding_radial_table(S, K, rc, ppa, seed=11)
+    p0 = I.random_model(S, K, rc, widths, seed=12)
+    G = O.evaluate(O.OracleModel(p0, radial_table=ppa, table_values=(H, dH)), s.pos, s.types, s.box, s.pbc,
+                   want_G=True)["G"]
+    rms = np.sqrt((G ** 2).mean(axis=0)).reshape(1, -1)
+    p = I.random_model(S, K, rc, widths, seed=12, feature_scale=np.repeat(rms, S, axis=0))
+    m = tmdlib.Model(p)
+    m.set_radial_table_values(ppa, H, dH)
+    g = _eval(tmdlib, m, s, rc)
+    o = O.evaluate(O.OracleModel(p, radial_table=ppa, table_values=(H, dH)), s.pos, s.types, s.box, s.pbc)
+    dE, dF, dW = _errs(g, o)
+    print(f"embedding-net table ppa {ppa}: dE/E={dE:.2e} dF/rms={dF:.2e} dW/max={dW:.2e}")
+    assert dE <= E_TOL and dF <= F_TOL and dW <= W_TOL
+    # back to the model's Gaussians: a different potential
+    m.set_radial_table(0)
+    d = _eval(tmdlib, m, s, rc)
+    assert not np.allclose(d["forces"], g["forces"])
+
+
+def test_table_values_rejected(tmdlib):
+    w = I.tiny()
+    p = w.model
+    H, dH = I.embedding_radial_table(p.n_species, p.n_radial, p.rc, 64, seed=1)
+    m = tmdlib.Model(p)
+    bad = [(48, H, dH), (64, H[:, :, :-1], dH[:, :, :-1]), (64, np.where(H == H, np.nan, H), dH)]
+    for ppa, h, d in bad:
+        with pytest.raises(tmdlib.TmdError) as e:
+            m.set_radial_table_values(ppa, h, d)
+        assert e.value.status == tmdlib.ERR_INVALID_ARG

@@ -24,6 +24,8 @@ MUTANTS = {
     "hermite_end_slope_sign": ("+ (t3 - t2) * h * d1;", "- (t3 - t2) * h * d1;"),
     "hermite_slope_unscaled": ("(t3 - 2.0 * t2 + t) * h * d0", "(t3 - 2.0 * t2 + t) * d0"),
     "table_wrong_upper_node": ("r1 = (g + 1.0) * h;", "r1 = (g + 2.0) * h;"),
+    "table_values_pair_transposed": ("const size_t base = ((size_t)ti * m->S + tj)",
+                                     "const size_t base = ((size_t)tj * m->S + ti)"),
 }
 
 

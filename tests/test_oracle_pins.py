@@ -162,6 +162,39 @@ def test_tabulated_forces_are_negative_energy_gradient():
         assert abs(fd - F[i, x]) <= 1e-7 * max(1.0, abs(F[i, x])) + 1e-8
 
 
+def test_table_values_match_the_gaussian_table_and_forces_are_gradients():
+    """Given the Gaussians' own values at the grid points, the table built from
+    caller values equals the Gaussian table (species pairs and channels kept
+    apart); with an embedding-network radial basis the forces are -grad E."""
+    p = I.random_model(2, 6, 4.5, [12, 10], seed=3)
+    p.mu = p.mu + 0.05 * np.arange(4).reshape(2, 2, 1)
+    p.eta = p.eta * (1.0 + 0.1 * np.arange(4).reshape(2, 2, 1))
+    ppa = 32
+    n = int(math.ceil(4.5 * ppa))
+    direct = O.OracleModel(p)
+    H = np.zeros((2, 2, n, 6))
+    dH = np.zeros_like(H)
+    for a in range(2):
+        for b in range(2):
+            for g in range(n):
+                H[a, b, g], dH[a, b, g] = O.radial(direct, a, b, g / ppa)
+    gauss = O.OracleModel(p, radial_table=ppa)
+    given = O.OracleModel(p, radial_table=ppa, table_values=(H, dH))
+    for r in (0.9, 1.7, 3.33, 4.49):
+        for a, b in ((0, 1), (1, 0), (1, 1)):
+            x, y = O.radial(gauss, a, b, r), O.radial(given, a, b, r)
+            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+    He, dHe = I.embedding_radial_table(2, 6, 4.5, ppa, seed=8)
+    om = O.OracleModel(p, radial_table=ppa, table_values=(He, dHe))
+    c = I.cluster(16, 3.6, seed=5, n_species=2)
+    F = O.evaluate(om, c.pos, c.types, c.box, c.pbc)["forces"]
+    rng = np.random.default_rng(3)
+    for _ in range(8):
+        i, x = int(rng.integers(c.n)), int(rng.integers(3))
+        fd = _fd_force(om, c.pos, c.types, c.box, c.pbc, i, x)
+        assert abs(fd - F[i, x]) <= 1e-7 * max(1.0, abs(F[i, x])) + 1e-8
+
+
 # ---------------------------------------------------------------- neighbours
 def _brute_pairs(pos, box, pbc, r):
     """Independent image enumeration: every s in a generous cube."""
