@@ -152,17 +152,18 @@ def kernel_traffic(name):
     return k.get("bytes_per_launch_full")
 
 
-def workload(name, reps=64):
+def workload(name, reps=64, rebuild_every=5):
     from paper_2310_08439_gb300 import inputs as I
+    cadence = ("neighbour table rebuilt every step" if rebuild_every == 1 else
+               f"neighbour table rebuilt every {rebuild_every} steps with a 1 A buffer (the paper's MD setting)")
     if name == "large":
         w = I.large(reps=reps)
         desc = (f"large: {reps}^3 fcc bulk, {w.systems[0].n:,} atoms, a=4.05 A, jitter 0.1 A, 1 species; rc 6 A, skin 1 A, "
-                "K=16, ranks 0-3, network 64-64-1 tanh (random init); velocity-Verlet dt=1 fs, "
-                "neighbour rebuild every step")
+                f"K=16, ranks 0-3, network 64-64-1 tanh (random init); velocity-Verlet dt=1 fs, {cadence}")
     elif name == "medium":
         w = I.medium()
         desc = ("medium: 16^3 fcc bulk, 16,384 atoms, a=3.61 A, 2 species, jitter 0.1 A; rc 6 A, skin 1 A, "
-                "K=16, network 64-64-1 per species; velocity-Verlet dt=1 fs, neighbour rebuild every step")
+                f"K=16, network 64-64-1 per species; velocity-Verlet dt=1 fs, {cadence}")
     else:
         raise SystemExit(f"unknown config {name}")
     return w, desc
@@ -376,32 +377,58 @@ def serving_measure(tmd, seconds, torch):
     return res
 
 
-def oracle_sample_rate(wname, min_seconds=10.0, max_steps=50):
-    """Oracle MD steps (neighbours + energy/forces/virial + velocity-Verlet) on a
-    bounded sample of the workload: a 12^3 cell of the same lattice, model and
-    jitter (6,912 atoms).  Returns (atom-steps/s, threads, description)."""
+class OracleMD:
+    """The FP64 oracle's MD loop on a bounded sample, with the neighbour
+    cadence of the GPU loop: velocity-Verlet from the oracle's own functions;
+    the table (radius rc + skin) is rebuilt every ``rebuild_every`` steps after
+    wrapping the positions, and between rebuilds the drift leaves them
+    unwrapped so that the table's image shifts stay valid (as on the GPU)."""
+
+    def __init__(self, O, w, s, rebuild_every):
+        self.O, self.w, self.s, self.R = O, w, s, max(1, int(rebuild_every))
+        self.om = O.OracleModel(w.model)
+        self.pos = s.pos.copy()
+        self.vel = s.vel.copy() if s.vel is not None else np.zeros_like(s.pos)
+        self.nopbc = np.zeros(3, np.int32)
+        self.k = 0
+        self._rebuild()
+        self.forces = O.compute(self.om, self.pos, s.types, s.box, self.nl)["forces"]
+
+    def _rebuild(self):
+        s = self.s
+        per = np.asarray(s.pbc, bool)
+        self.pos[:, per] = np.mod(self.pos[:, per], np.asarray(s.box)[per])
+        self.nl = self.O.neighbors(self.pos, s.box, s.pbc, self.w.model.rc + self.w.skin)
+
+    def step(self):
+        O, s = self.O, self.s
+        O.vv_first(self.pos, self.vel, self.forces, s.masses, s.box, self.nopbc, 1.0)   # kick + drift
+        self.k += 1
+        if self.k % self.R == 0:
+            self._rebuild()
+        self.forces = O.compute(self.om, self.pos, s.types, s.box, self.nl)["forces"]
+        O.vv_second(self.vel, self.forces, s.masses, 1.0)
+
+
+def oracle_sample_rate(wname, rebuild_every=5, min_seconds=10.0, max_steps=50):
+    """Oracle MD steps (velocity-Verlet, evaluation, the neighbour table every
+    ``rebuild_every`` steps) on a bounded sample of the workload: a 12^3 cell
+    of the same lattice, model and jitter (6,912 atoms).  Returns
+    (atom-steps/s, threads, description, atoms, steps, seconds)."""
     from oracle import oracle as O
     from paper_2310_08439_gb300 import inputs as I
     w, _ = workload(wname)
-    if wname == "large":
-        sw = I.large(reps=12)
-        s = sw.systems[0]
-    else:
-        s = w.systems[0]
-    om = O.OracleModel(w.model)
-    pos, vel = s.pos.copy(), (s.vel.copy() if s.vel is not None else np.zeros_like(s.pos))
-    out = O.evaluate(om, pos, s.types, s.box, s.pbc)
+    s = I.large(reps=12).systems[0] if wname == "large" else w.systems[0]
+    md = OracleMD(O, w, s, rebuild_every)
     steps, t0 = 0, time.perf_counter()
     while steps < max_steps:
-        O.vv_first(pos, vel, out["forces"], s.masses, s.box, s.pbc, 1.0)
-        out = O.evaluate(om, pos, s.types, s.box, s.pbc)
-        O.vv_second(vel, out["forces"], s.masses, 1.0)
+        md.step()
         steps += 1
         if time.perf_counter() - t0 >= min_seconds:
             break
     dt = time.perf_counter() - t0
-    desc = (f"FP64 C oracle (OpenMP), {steps} full MD steps (O(N^2) neighbour search + evaluation + "
-            f"velocity-Verlet) on a {s.n}-atom cell of the same lattice/model")
+    desc = (f"FP64 C oracle (OpenMP), {steps} MD steps (evaluation + velocity-Verlet, O(N^2) neighbour search "
+            f"every {md.R} steps) on a {s.n}-atom cell of the same lattice/model")
     return s.n * steps / dt, O.num_threads(), desc, s.n, steps, dt
 
 
@@ -431,18 +458,11 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from paper_2310_08439_gb300 import inputs as I
-    w, desc = workload(args.config)
+    w, desc = workload(args.config, rebuild_every=args.rebuild_every)
     sw = I.large(reps=12) if args.config == "large" else w
     s = sw.systems[0]
-    om = O.OracleModel(w.model)
-    pos, vel = s.pos.copy(), (s.vel.copy() if s.vel is not None else np.zeros_like(s.pos))
-    out = O.evaluate(om, pos, s.types, s.box, s.pbc)
-
-    def step():
-        nonlocal out
-        O.vv_first(pos, vel, out["forces"], s.masses, s.box, s.pbc, 1.0)
-        out = O.evaluate(om, pos, s.types, s.box, s.pbc)
-        O.vv_second(vel, out["forces"], s.masses, 1.0)
+    md = OracleMD(O, w, s, args.rebuild_every)
+    step = md.step
 
     for _ in range(args.warmup):
         step()
@@ -451,7 +471,8 @@ def run_reference(args):
         step()
     dt = time.perf_counter() - t0
     value = s.n * args.steps / dt
-    sample = f"{s.n}-atom cell of the same lattice and model, {args.steps} MD steps per run"
+    sample = (f"{s.n}-atom cell of the same lattice and model, {args.steps} MD steps per run, neighbour table "
+              f"every {md.R} steps")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -471,6 +492,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large", choices=["large", "medium"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--rebuild-every", type=int, default=5,
+                    help="neighbour rebuild cadence of the timed MD loop (the paper's setting: 5)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reps", type=int, default=64, help="fcc repeats of the large cell (64 = 1,048,576 atoms)")
@@ -500,7 +523,8 @@ def main():
     from paper_2310_08439_gb300 import build as B
     from paper_2310_08439_gb300 import tmd
     B.build()
-    w, desc = workload(args.config, args.reps)
+    w, desc = workload(args.config, args.reps, rebuild_every=args.rebuild_every)
+    R = args.rebuild_every
     s = w.systems[0]
     n = s.n
     model = tmd.Model(w.model, precision=args.precision)
@@ -514,13 +538,13 @@ def main():
             dist.barrier()
 
     for _ in range(args.warmup):
-        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+        sysm.step(model, w.dt_fs, 1, rebuild_every=R, thermo=False)
     torch.cuda.synchronize()
     # tile shapes picked by the autotuner on this system (kept in the model)
     if args.tuning == "auto":
         p_w, _, _ = sysm.get_state()
         nl_t = tmd.NeighborList()
-        pos_t = torch.as_tensor(p_w, device=dev)
+        pos_t = torch.as_tensor(np.mod(p_w, s.box), device=dev)   # unwrapped since the last rebuild
         types_t = torch.as_tensor(s.types, device=dev)
         nl_t.build(pos_t, types_t, s.box, s.pbc, w.model.rc + w.skin)
         tuning = tmd.autotune(model, nl_t, pos_t, types_t, s.box)
@@ -530,7 +554,7 @@ def main():
         model.tuning = {"tile_rows": rows, "pair_blocks_per_sm": bps}
         tuning = dict(model.tuning, ms=None)
     for _ in range(args.warmup):
-        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+        sysm.step(model, w.dt_fs, 1, rebuild_every=R, thermo=False)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -543,7 +567,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
+        sysm.step(model, w.dt_fs, 1, rebuild_every=R, thermo=False)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -558,6 +582,25 @@ def main():
     other = "bf16" if args.precision == "fp32" else "fp32"
     model.set_precision(other)
     for _ in range(args.warmup):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=R, thermo=False)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sysm.step(model, w.dt_fs, 1, rebuild_every=R, thermo=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_other = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    forms = {args.precision: {"value": value, "ms_per_step": elapsed_ms / args.steps},
+             other: {"value": replica_throughput(world, n, args.steps, t_other * 1e-3),
+                     "ms_per_step": t_other / args.steps}}
+    model.set_precision(args.precision)
+
+    # the same MD loop with a neighbour rebuild in every step (no reuse of the
+    # table at all)
+    for _ in range(args.warmup):
         sysm.step(model, w.dt_fs, 1, rebuild_every=1, thermo=False)
     barrier()
     torch.cuda.synchronize()
@@ -568,11 +611,10 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    t_other = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    forms = {args.precision: {"value": value, "ms_per_step": elapsed_ms / args.steps},
-             other: {"value": replica_throughput(world, n, args.steps, t_other * 1e-3),
-                     "ms_per_step": t_other / args.steps}}
-    model.set_precision(args.precision)
+    t_every = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    forms[args.precision + "_rebuild_every_step"] = {
+        "value": replica_throughput(world, n, args.steps, t_every * 1e-3), "ms_per_step": t_every / args.steps,
+        "what": "neighbour table rebuilt in every step"}
 
     # the same MD loop with the skin criterion of the velocity-Verlet step
     # (rebuild only once an atom moved more than skin/2 since the last build):
@@ -608,15 +650,15 @@ def main():
         vel_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
         f_h = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
         p_, v_, f_ = sysm.get_state()
-        pos_h.numpy()[:] = p_
+        pos_h.numpy()[:] = np.mod(p_, s.box)   # unwrapped since the last rebuild
         vel_h.numpy()[:] = v_
         f_h.numpy()[:] = f_
-        sysm.step_host(model, pos_h, vel_h, f_h, w.dt_fs, 1, rebuild_every=1)  # warm
+        sysm.step_host(model, pos_h, vel_h, f_h, w.dt_fs, 1, rebuild_every=R)  # warm
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            sysm.step_host(model, pos_h, vel_h, f_h, w.dt_fs, 1, rebuild_every=1)
+            sysm.step_host(model, pos_h, vel_h, f_h, w.dt_fs, 1, rebuild_every=R)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": replica_throughput(world, n, args.steps, e2e_s), "unit": UNIT,
@@ -669,7 +711,7 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        rate, cores, sdesc, sn, ssteps, sdt = oracle_sample_rate(args.config)
+        rate, cores, sdesc, sn, ssteps, sdt = oracle_sample_rate(args.config, rebuild_every=R)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc,
                "split": oracle_split(args.config)}
 
