@@ -51,6 +51,37 @@ def test_batch_equals_single_and_oracle(tmdlib, small_batch):
             assert np.abs(W[k] - o["virial"]).max() <= 1e-5 * np.abs(o["virial"]).max(), k
 
 
+@pytest.mark.parametrize("kind", ["tcgen05", "mma_sync"])
+def test_bf16_batch_equals_single(tmdlib, small_batch, kind):
+    """BF16 network form: the batch's network tiles hold atoms of several
+    systems, and each tile row is computed on its own, so every system's
+    result equals its single evaluation (up to the FP32 rounding of the
+    descriptors, which the BF16 rounding of the network input can amplify to
+    BF16 size on single elements)."""
+    import torch
+    w = small_batch
+    try:
+        tmdlib.set_network_kernel(kind)
+        m = tmdlib.Model(w.model, precision="bf16")
+        b = tmdlib.Batch(w.systems)
+        E, _ = b.compute(m, list(range(len(w.systems))))
+        for k, s in enumerate(w.systems):
+            nl = tmdlib.NeighborList()
+            pos = torch.as_tensor(s.pos, dtype=torch.float64, device="cuda")
+            types = torch.as_tensor(s.types, dtype=torch.int32, device="cuda")
+            nl.build(pos, types, s.box, s.pbc, w.model.rc)
+            out = tmdlib.evaluate(m, nl, pos, types, s.box)
+            torch.cuda.synchronize()
+            _, _, fb = b.get_system(k)
+            f1 = out["forces"].double().cpu().numpy()
+            rms = np.sqrt((f1 ** 2).mean())
+            assert np.sqrt(((fb - f1) ** 2).mean()) <= 1e-3 * rms, k
+            assert abs(E[k] - float(out["energy"].item())) <= 1e-6 * abs(E[k]), k
+    finally:
+        tmdlib.set_network_kernel("auto")
+    assert tmdlib.device_status() == 0
+
+
 def test_batch_subset_leaves_others_untouched(tmdlib, small_batch):
     w = small_batch
     m = tmdlib.Model(w.model)

@@ -9,9 +9,12 @@ from paper_2310_08439_gb300 import serve
 pytestmark = pytest.mark.gpu
 
 
-def test_requests_same_alone_and_in_the_mix(tmdlib):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_requests_same_alone_and_in_the_mix(tmdlib, precision):
+    """In the BF16 form the network tiles mix atoms of different systems; each
+    tile row is computed on its own, so the trajectories stay bitwise equal."""
     w = I.serve(n_systems=6, seed=31, n_max=2000)
-    m = tmdlib.Model(w.model)
+    m = tmdlib.Model(w.model, precision=precision)
     reqs_a = serve.poisson_requests(len(w.systems), rate=400.0, duration=0.05, seed=3, max_steps=4)
     assert len(reqs_a) >= 8
     reqs_b = [serve.Request(r.rid, r.system, r.steps, r.arrival) for r in reqs_a]
