@@ -220,8 +220,9 @@ def radial_table_measure(tmd, model, sysm, s, w, steps, torch, stream):
 
 def batch_measure(tmd, torch, steps=5):
     """512 uneven systems (configs: batch) evaluated by one set of launches, FP32
-    and BF16 network forms; errors against the FP64 oracle on a sample."""
-    from oracle import oracle as O
+    and BF16 network forms.  Returns the measurement and, for a sample of the
+    systems, their energies and forces (compared with the FP64 oracle in the
+    oracle leg, ``batch_errors``)."""
     from paper_2310_08439_gb300 import inputs as I
     w = I.batch()
     n_tot = int(sum(x.n for x in w.systems))
@@ -231,10 +232,8 @@ def batch_measure(tmd, torch, steps=5):
     m = tmd.Model(w.model)
     b = tmd.Batch(w.systems)
     rng = np.random.default_rng(0)
-    sample = [k for k in rng.permutation(len(w.systems)) if w.systems[k].n <= 1500][:8]
-    om = O.OracleModel(w.model)
-    ref = {k: O.evaluate(om, w.systems[k].pos, w.systems[k].types, w.systems[k].box, w.systems[k].pbc)
-           for k in sample}
+    sample = [int(k) for k in rng.permutation(len(w.systems)) if w.systems[k].n <= 1500][:8]
+    results = {}
     for prec in ("fp32", "bf16"):
         m.set_precision(prec)
         tuning = b.autotune(m, ids)   # tile shapes for this batch and form
@@ -244,18 +243,31 @@ def batch_measure(tmd, torch, steps=5):
         for _ in range(steps):
             E, Wv = b.compute(m, ids)
         dt = (time.perf_counter() - t0) / steps
-        errs = []
-        for k in sample:
-            _, _, f = b.get_system(k)
-            o = ref[k]
-            rms = float(np.sqrt((o["forces"] ** 2).mean()))
-            errs.append({"system": int(k), "n": int(w.systems[k].n),
-                         "dE_rel": abs(E[k] - o["energy"]) / abs(o["energy"]),
-                         "dF_max_over_rms": float(np.abs(f - o["forces"]).max() / rms)})
+        results[prec] = {k: (float(E[k]), b.get_system(k)[2].astype(np.float64)) for k in sample}
         out[prec] = {"atom_evals_per_s": n_tot / dt, "ms_per_batch_eval": dt * 1e3, "tuning": tuning,
-                     "max_dE_rel": max(e["dE_rel"] for e in errs),
-                     "max_dF_over_rms": max(e["dF_max_over_rms"] for e in errs), "per_system": errs}
-    return out
+                     "max_dE_rel": None, "max_dF_over_rms": None, "per_system": None}
+    return out, (w, sample, results)
+
+
+def batch_errors(extras_batch, sampled):
+    """Oracle leg: errors of the sampled batch systems against the FP64 oracle."""
+    from oracle import oracle as O
+    w, sample, results = sampled
+    om = O.OracleModel(w.model)
+    for k in sample:
+        s = w.systems[k]
+        o = O.evaluate(om, s.pos, s.types, s.box, s.pbc)
+        rms = float(np.sqrt((o["forces"] ** 2).mean()))
+        for prec, res in results.items():
+            e, f = res[k]
+            row = {"system": k, "n": int(s.n), "dE_rel": abs(e - o["energy"]) / abs(o["energy"]),
+                   "dF_max_over_rms": float(np.abs(f - o["forces"]).max() / rms)}
+            d = extras_batch[prec]
+            d["per_system"] = (d["per_system"] or []) + [row]
+    for prec in results:
+        d = extras_batch[prec]
+        d["max_dE_rel"] = max(r["dE_rel"] for r in d["per_system"])
+        d["max_dF_over_rms"] = max(r["dF_max_over_rms"] for r in d["per_system"])
 
 
 def paper_models_measure(tmd, torch, steps=5):
@@ -264,7 +276,6 @@ def paper_models_measure(tmd, torch, steps=5):
     random weights, on 1,024,000-atom bcc W lattices at the two lattice
     constants of the paper's weak-scaling runs; tmd_compute on a fixed table,
     FP32 and BF16 network forms."""
-    from oracle import oracle as O
     from paper_2310_08439_gb300 import inputs as I
 
     def bcc_w(a, reps, seed):
@@ -274,12 +285,19 @@ def paper_models_measure(tmd, torch, steps=5):
                         np.ones(3, np.int32))
 
     out = {"workload": "bcc W 80^3 x 2 = 1,024,000 atoms, jitter 0.1 A, rc 6 A (no skin), 1 species; "
-                       "first layer normalised by the descriptor RMS of a 432-atom cell"}
+                       "first layer normalised by the descriptor RMS of a 432-atom cell (GPU descriptors)"}
     for k, widths in ((32, [128, 128, 128]), (128, [128, 128, 128, 128])):
         for a in (3.1887, 2.8):
             small = bcc_w(a, (6, 6, 6), 1)
             p0 = I.random_model(1, k, 6.0, widths, seed=k, activation="squareplus", masses=[183.84])
-            G = O.evaluate(O.OracleModel(p0), small.pos, small.types, small.box, small.pbc, want_G=True)["G"]
+            # first-layer scale: descriptor RMS over a 432-atom cell (descriptors do not depend on the weights)
+            m0 = tmd.Model(p0)
+            nl0 = tmd.NeighborList()
+            pos0 = torch.as_tensor(small.pos, device="cuda")
+            typ0 = torch.as_tensor(small.types, device="cuda")
+            nl0.build(pos0, typ0, small.box, small.pbc, 6.0)
+            G = tmd.descriptors(m0, nl0, pos0, typ0, small.box).double().cpu().numpy()
+            del m0, nl0
             p = I.random_model(1, k, 6.0, widths, seed=k, activation="squareplus", masses=[183.84],
                                feature_scale=np.sqrt((G ** 2).mean(axis=0)).reshape(1, -1))
             s = bcc_w(a, (80, 80, 80), 2)
@@ -696,6 +714,14 @@ def main():
                 "frac": ach / fp32_peak, "traffic": kernel_traffic(dom),
                 "peak_source": f"FP32 FMA peak {nsm} SMs x 128 lanes x 2 flops x {clk_mhz:.0f} MHz "
                                f"(max SM clock, {peaks['source']} peaks file)"}
+        # the descriptor and force passes take nearly equal time, so the
+        # dominant one can change between runs: every pair/network kernel's
+        # figures, the same way
+        roof["all"] = {}
+        for kn, fl in per_launch_flops.items():
+            if kn in kstats:
+                a = fl / (kstats[kn][1] / max(kstats[kn][0], 1) * 1e-3) / 1e12
+                roof["all"][kn] = {"achieved": a, "frac": a / fp32_peak, "traffic": kernel_traffic(kn)}
     total_ms = sum(v[1] for v in kstats.values())
     kernels = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1), "share": v[1] / total_ms}
                for k, v in ranked}
@@ -703,7 +729,7 @@ def main():
     compute_only = compute_only_rate(tmd, model, sysm, s, w, args.steps, torch, stream)
     extras = {}
     if not args.no_extras and world == 1:
-        extras["batch"] = batch_measure(tmd, torch)
+        extras["batch"], batch_sample = batch_measure(tmd, torch)
         extras["radial_table"] = radial_table_measure(tmd, model, sysm, s, w, args.steps, torch, stream)
         extras["paper_models"] = paper_models_measure(tmd, torch)
         extras["graphs"] = graphs_measure(tmd, torch)
@@ -714,6 +740,8 @@ def main():
         rate, cores, sdesc, sn, ssteps, sdt = oracle_sample_rate(args.config, rebuild_every=R)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc,
                "split": oracle_split(args.config)}
+        if "batch" in extras:   # errors of the batch sample against the oracle
+            batch_errors(extras["batch"], batch_sample)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
