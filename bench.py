@@ -87,7 +87,10 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        import tempfile
+        # TMD_CLOCKS_DIR keeps the samples (e.g. next to the bench output); default: a temporary directory
+        self.path = os.path.join(os.environ.get("TMD_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
