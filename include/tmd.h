@@ -51,14 +51,14 @@ typedef enum {
     TMD_ERR_CUDA = 3,          /* a CUDA runtime call failed                    */
     TMD_ERR_OOM = 4,           /* device allocation failed                      */
     TMD_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                 */
-    TMD_ERR_UNIMPLEMENTED = 6  /* a configuration this build does not support   */
+    TMD_ERR_UNIMPLEMENTED = 6  /* a configuration the library does not support  */
 } tmd_status;
 
 enum { TMD_ACT_TANH = 0, TMD_ACT_SQUAREPLUS = 1 };
 enum { TMD_PREC_FP32 = 0, TMD_PREC_BF16 = 1 };
 enum { TMD_NET_AUTO = 0, TMD_NET_TCGEN05 = 1, TMD_NET_MMA_SYNC = 2 };
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define TMD_MAX_SPECIES 4
 #define TMD_MAX_HIDDEN 4
 #define TMD_MAX_WIDTH 256
@@ -77,7 +77,7 @@ const char *tmd_version(void);
 /*
  * Description of a TensorMD potential (all pointers host, read at create).
  *  n_species  S, 1..TMD_MAX_SPECIES.  Species ids are 0..S-1.
- *  n_radial   K radial channels; this build supports K in {8, 16, 32, 64,
+ *  n_radial   K radial channels; the library supports K in {8, 16, 32, 64,
  *             128} with at most 4, 4, 3, 2, 1 species respectively.
  *  rc         cutoff radius (A); pairs with R >= rc contribute nothing.
  *  mu, eta    [S][S][K] Gaussian centre and width of f_k(R) = exp(-eta (R-mu)^2)

@@ -306,7 +306,7 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
     const int S = d->n_species, K = d->n_radial, L = d->n_hidden;
     if (S < 1 || S > TMD_MAX_SPECIES) { set_error("n_species %d outside [1, %d]", S, TMD_MAX_SPECIES); return TMD_ERR_INVALID_ARG; }
     if (K != 8 && K != 16 && K != 32 && K != 64 && K != 128) {
-        set_error("n_radial %d: this build supports 8, 16, 32, 64, 128", K);
+        set_error("n_radial %d: the library supports 8, 16, 32, 64, 128", K);
         return TMD_ERR_UNIMPLEMENTED;
     }
     // species counts with kernel instances (the network input S K 4 <= 512)
