@@ -187,6 +187,15 @@ tmd_status tmd_set_network_kernel(int32_t kind);
  * out since the last call (the results of the calls in between are invalid),
  * else TMD_OK; *bits receives the raw bits.  Synchronises the device. */
 tmd_status tmd_device_status(int32_t *bits);
+
+/* Self-test of the bounded waits of the tensor-core kernels: one warp
+ * allocates tensor memory and waits, with the library's bounded wait, on an
+ * mbarrier that nothing signals.  The wait gives up after about 0.2 s,
+ * records the timeout (the next tmd_device_status returns TMD_ERR_TIMEOUT),
+ * and the kernel frees its tensor memory and returns, leaving the context
+ * usable.  *gave_up (host) = 1 when the wait gave up as designed.  Errors:
+ * INVALID_ARG, CUDA.  Synchronises the device. */
+tmd_status tmd_selftest_bounded_wait(int32_t *gave_up);
 int64_t tmd_graph_replays(void);
 
 /*

@@ -593,6 +593,12 @@ tmd_status tmd_device_status(int32_t *bits) {
     return TMD_OK;
 }
 
+tmd_status tmd_selftest_bounded_wait(int32_t *gave_up) {
+    g_err[0] = 0;
+    if (!gave_up) { set_error("null output"); return TMD_ERR_INVALID_ARG; }
+    return tmd::wait_probe(gave_up);
+}
+
 tmd_status tmd_set_graphs(int32_t on) {
     g_graphs = on != 0;
     return TMD_OK;

@@ -506,6 +506,34 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(u.tcols) : "memory");
 }
 
+// Self-test of the bounded waits: one warp allocates tensor memory, waits on
+// an mbarrier that nothing signals, and must give up (about 0.2 s), record
+// DEV_ERR_TIMEOUT, free its tensor memory and return.
+__global__ void __launch_bounds__(32, 1) k_wait_probe(int32_t *__restrict__ gave_up) {
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const uint32_t bar = smem_u32(&s_bar);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        s_abort = 0;
+        fence_proxy_async();
+    }
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)), "r"(32)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (threadIdx.x == 0) mbar_wait(bar, 0, &s_abort);   // nothing arrives: gives up
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
+    if (threadIdx.x == 0) *gave_up = s_abort;
+}
+
 // launch plan for a model, or false when the shapes do not fit
 int reg_blocks_per_sm();
 
@@ -700,6 +728,21 @@ tmd_status mlp_umma_build(tmd_model *m, const double *const *weights) {
     }
     m->dev_umma = dev;
     for (int s = 0; s < S; ++s) dm.ub[s] = static_cast<const uint16_t *>(dev) + per * s;
+    return TMD_OK;
+}
+
+tmd_status wait_probe(int32_t *gave_up) {
+    int32_t *d = nullptr;
+    TMD_CUDA(cudaMalloc(&d, sizeof(int32_t)));
+    cudaMemset(d, 0, sizeof(int32_t));
+    k_wait_probe<<<1, 32>>>(d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int32_t h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    *gave_up = h;
     return TMD_OK;
 }
 

@@ -301,6 +301,7 @@ tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, i
 // tensor-core kernels, read and cleared (synchronises)
 tmd_status mlp_umma_build(tmd_model *m, const double *const *weights);
 tmd_status umma_status(int32_t *bits);
+tmd_status wait_probe(int32_t *gave_up);
 extern int g_network_kernel;
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                        int64_t n, const double box[3], double *energy, float *e_atom, float *forces,

@@ -70,6 +70,7 @@ _SIGS = {
                                                     C.POINTER(C.c_double)]),
     "tmd_set_network_kernel": (C.c_int, [C.c_int32]),
     "tmd_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
+    "tmd_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int32)]),
     "tmd_model_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
     "tmd_autotune": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_double), C.POINTER(Tuning), _P]),
     "tmd_batch_autotune": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(Tuning), _P]),
@@ -140,6 +141,13 @@ def device_status():
     b = C.c_int32(0)
     check(lib().tmd_device_status(C.byref(b)))
     return int(b.value)
+
+
+def selftest_bounded_wait():
+    """Run the bounded-wait self-test kernel; True when its wait gave up as designed."""
+    g = C.c_int32(0)
+    check(lib().tmd_selftest_bounded_wait(C.byref(g)))
+    return g.value == 1
 
 
 def set_graphs(on=True):

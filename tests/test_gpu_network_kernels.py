@@ -107,3 +107,22 @@ def test_network_kernel_selection(tmdlib):
         assert e.value.status == tmdlib.ERR_INVALID_ARG
     finally:
         tmdlib.set_network_kernel("auto")
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(tmdlib):
+    """Failure detection without a fault: the self-test kernel waits on an
+    mbarrier that nothing signals; the bounded wait gives up, the status word
+    reports the timeout once, and the next tensor-core evaluation is normal."""
+    assert tmdlib.device_status() == 0
+    assert tmdlib.selftest_bounded_wait()
+    with pytest.raises(tmdlib.TmdError) as e:
+        tmdlib.device_status()
+    assert e.value.status == tmdlib.ERR_TIMEOUT
+    assert tmdlib.device_status() == 0          # read and cleared
+    p, s, r_list = _cases()["medium"]
+    o = O.evaluate(O.OracleModel(p), s.pos, s.types, s.box, s.pbc)
+    g = _eval(tmdlib, tmdlib.Model(p, precision="bf16"), s, r_list)
+    rms = float(np.sqrt((o["forces"] ** 2).mean()))
+    assert abs(g["energy"] - o["energy"]) / abs(o["energy"]) < 1e-3
+    assert np.sqrt(((g["forces"] - o["forces"]) ** 2).mean()) / rms < 5e-2
+    assert tmdlib.device_status() == 0
