@@ -81,6 +81,29 @@ def test_paper_potential_shapes(tmdlib, k, widths, a, capsys):
     assert bE < 1e-3 and bF < 0.5
 
 
+def test_k128_bf16_both_network_kernels(tmdlib):
+    """The k = 128 network (Dd 512) in the BF16 form on both kernels: tcgen05
+    (N passes of 256 for G') and mma.sync (narrow weight chunks, gradient
+    buffers sharing the G tile)."""
+    s = _bcc_w(3.1887, (3, 3, 3), seed=9)
+    p = _scaled_model(128, 1, [128, 128, 128, 128], s, seed=128)
+    o = O.evaluate(O.OracleModel(p), s.pos, s.types, s.box, s.pbc)
+    res = {}
+    try:
+        for kind in ("tcgen05", "mma_sync"):
+            tmdlib.set_network_kernel(kind)
+            res[kind] = _eval(tmdlib, tmdlib.Model(p, precision="bf16"), s, p.rc)
+    finally:
+        tmdlib.set_network_kernel("auto")
+    rms = float(np.sqrt((o["forces"] ** 2).mean()))
+    for kind, g in res.items():
+        bE, bF, _ = _errs(g, o)
+        assert bE < 1e-3 and bF < 0.5, (kind, bE, bF)
+    cross = np.sqrt(((res["tcgen05"]["forces"] - res["mma_sync"]["forces"]) ** 2).mean()) / rms
+    assert cross < 2e-2
+    assert tmdlib.device_status() == 0
+
+
 def test_k64_two_species(tmdlib):
     rng = np.random.default_rng(64)
     pos, box = I.lattice("bcc", (4, 4, 3), 3.1)
