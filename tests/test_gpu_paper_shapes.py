@@ -114,6 +114,12 @@ def test_k64_two_species(tmdlib):
     g = _eval(tmdlib, tmdlib.Model(p), s, p.rc)
     dE, dF, dW = _errs(g, o)
     assert dE <= E_TOL and dF <= F_TOL and dW <= W_TOL, (dE, dF, dW)
+    # BF16 form: Dd 512 with two species (G' in two N passes, tiles spanning species)
+    b = _eval(tmdlib, tmdlib.Model(p, precision="bf16"), s, p.rc)
+    bE, bF, _ = _errs(b, o)
+    rms = float(np.sqrt((o["forces"] ** 2).mean()))
+    assert bE < 1e-3 and np.sqrt(((b["forces"] - o["forces"]) ** 2).mean()) / rms < 5e-2, (bE, bF)
+    assert tmdlib.device_status() == 0
 
 
 def test_k128_with_radial_table_and_batch(tmdlib):
