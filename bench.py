@@ -473,6 +473,38 @@ def oracle_split(wname, reps=3):
             "compute_atom_evals_per_s": s.n / t_c}
 
 
+def size_sweep(tmd, torch, reps_list, steps, warmup, rebuild_every):
+    """The FP32 MD step of the large lattice (same recipe, 4 reps^3 atoms) at
+    several sizes: atom-steps/s, ms/step and the device memory the system,
+    model and workspaces take.  Built-in tile shapes (no autotuning)."""
+    out = []
+    for reps in reps_list:
+        w, _ = workload("large", reps, rebuild_every)
+        s = w.systems[0]
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        model = tmd.Model(w.model)
+        sysm = tmd.System(s.n, s.box, s.pbc, skin=w.skin)
+        sysm.set_state(s.pos, s.vel if s.vel is not None else np.zeros_like(s.pos), s.types, s.masses)
+        for _ in range(warmup):
+            sysm.step(model, w.dt_fs, 1, rebuild_every=rebuild_every, thermo=False)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sysm.step(model, w.dt_fs, 1, rebuild_every=rebuild_every, thermo=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        used = free0 - torch.cuda.mem_get_info()[0]
+        out.append({"reps": reps, "atoms": s.n, "atom_steps_per_s": s.n / (ms * 1e-3), "ms_per_step": ms,
+                    "device_bytes": int(used), "device_bytes_per_atom": used / s.n})
+        del sysm, model
+        torch.cuda.synchronize()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -520,6 +552,9 @@ def main():
     ap.add_argument("--reps", type=int, default=64, help="fcc repeats of the large cell (64 = 1,048,576 atoms)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--size-sweep", default="",
+                    help="instead of the bench line: the FP32 MD step of the large lattice at these fcc repeats "
+                         "(e.g. 32,64,128,160), throughput and device memory per size")
     ap.add_argument("--tuning", default="auto",
                     help="tile shapes 'ROWS,BLOCKS_PER_SM' instead of the autotuner (e.g. for profiler captures)")
     args = ap.parse_args()
@@ -544,6 +579,14 @@ def main():
     from paper_2310_08439_gb300 import build as B
     from paper_2310_08439_gb300 import tmd
     B.build()
+    if args.size_sweep:
+        if rank == 0:
+            reps = [int(x) for x in args.size_sweep.split(",")]
+            print(json.dumps({"size_sweep": size_sweep(tmd, torch, reps, args.steps, args.warmup,
+                                                       args.rebuild_every)}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     w, desc = workload(args.config, args.reps, rebuild_every=args.rebuild_every)
     R = args.rebuild_every
     s = w.systems[0]
