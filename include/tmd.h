@@ -397,9 +397,13 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
  * tmd_step from host buffers.  pos/vel [n][3] FP64 and forces_host [n][3]
  * FP32 are the caller's MD state in host memory (pinned memory gives
  * asynchronous copies).  The call uploads pos and vel, and the forces at pos
- * when forces_host is non-NULL (otherwise it recomputes them), rebuilds the
- * neighbour table, runs nsteps steps, and writes pos, vel and forces back into
- * the same host arrays.  Synchronises the stream.
+ * when forces_host is non-NULL (otherwise it recomputes them, with a
+ * neighbour rebuild), runs nsteps steps as tmd_step does, and writes pos, vel
+ * and forces back into the same host arrays.  The neighbour table follows
+ * tmd_step's rules across calls (rebuild_every and the skin check); the skin
+ * check compares the uploaded positions with those of the last build, so
+ * positions the caller changed by more than skin/2 (a wrap included) force a
+ * rebuild.  Synchronises the stream.
  */
 tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_host, double *vel_host,
                          float *forces_host, double dt_fs, int32_t nsteps, int32_t rebuild_every,

@@ -1017,7 +1017,10 @@ tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_ho
     } else {
         sys->have_forces = 0;
     }
-    sys->need_rebuild = 1;
+    // no forced rebuild: the skin check compares the uploaded positions with
+    // those of the last build, so positions the caller moved by more than
+    // skin/2 (a wrap included) rebuild the table, and the cadence holds
+    // across calls
     tmd_status st = tmd_step(model, sys, dt_fs, nsteps, rebuild_every, thermo, stream);
     if (st != TMD_OK) return st;
     TMD_CUDA(cudaMemcpyAsync(pos_host, sys->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));

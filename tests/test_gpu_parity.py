@@ -359,6 +359,43 @@ def test_step_host_matches_device_path(tmdlib):
     assert np.abs(pos - pa).max() < 1e-12 and np.abs(vel - va).max() < 1e-12
 
 
+def test_step_host_keeps_the_rebuild_cadence(tmdlib):
+    """One step per host call with the table rebuilt every 5 steps follows the
+    device loop exactly, and positions the caller moves by a whole period
+    still give the same forces (the skin check rebuilds the table)."""
+    w = I.tiny()
+    s = w.systems[0]
+    s.vel = I.maxwell_velocities(s.masses, 300.0, np.random.default_rng(8))
+    m = tmdlib.Model(w.model)
+    a = tmdlib.System(s.n, s.box, s.pbc, skin=0.5)
+    a.set_state(s.pos, s.vel, s.types, s.masses)
+    tha = a.step(m, 1.0, 11, rebuild_every=5)
+    pa, va, fa = a.get_state()
+    b = tmdlib.System(s.n, s.box, s.pbc, skin=0.5)
+    b.set_state(s.pos, s.vel, s.types, s.masses)
+    pos, vel = s.pos.copy(), s.vel.copy()
+    forces = np.zeros((s.n, 3), np.float32)
+    b.step_host(m, pos, vel, None, 1.0, 1, rebuild_every=5)
+    _, _, forces = b.get_state()
+    for _ in range(10):
+        b.step_host(m, pos, vel, forces, 1.0, 1, rebuild_every=5)
+    thb = b.step(m, 0.0, 0, rebuild_every=5)
+    assert np.array_equal(pos, pa) and np.array_equal(vel, va) and np.array_equal(forces, fa)
+    assert thb["rebuilds"] == tha["rebuilds"]
+    # the caller moves one atom by a whole box length: same physics; the skin
+    # check sees the jump and rebuilds the table
+    pos2, vel2, f2 = pos.copy(), vel.copy(), forces.copy()
+    pos2[0, 0] += s.box[0]
+    b.step_host(m, pos2, vel2, f2, 1.0, 1, rebuild_every=0)
+    c = tmdlib.System(s.n, s.box, s.pbc, skin=0.5)
+    c.set_state(np.mod(pos, s.box), vel, s.types, s.masses)
+    c_pos, c_vel, c_f = np.mod(pos, s.box), vel.copy(), forces.copy()
+    c.step_host(m, c_pos, c_vel, c_f, 1.0, 1, rebuild_every=0)
+    d = np.mod(pos2 - c_pos + 0.5 * s.box, s.box) - 0.5 * s.box
+    assert np.abs(d).max() < 1e-12
+    assert np.abs(f2 - c_f).max() <= 1e-6 * max(1.0, np.abs(c_f).max())
+
+
 def test_evaluate_host_matches_device(tmdlib):
     w = I.medium()
     s = w.systems[0]
