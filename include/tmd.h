@@ -120,6 +120,8 @@ typedef struct tmd_system tmd_system; /* opaque; resident MD state */
  * network whose activations do not fit on chip), OOM, CUDA.
  * Synchronises the device once. */
 tmd_status tmd_model_create(const tmd_model_desc *desc, tmd_model **out);
+/* Free a model and its device memory (synchronises the device through
+ * cudaFree).  NULL is accepted.  Always TMD_OK. */
 tmd_status tmd_model_destroy(tmd_model *model);
 /* Switch the network precision of an existing model (TMD_PREC_*). */
 tmd_status tmd_model_set_precision(tmd_model *model, int32_t precision);
@@ -235,6 +237,9 @@ tmd_status tmd_autotune(tmd_model *model, tmd_nlist *nl, const double *pos, cons
 /* Neighbour table (R_abc of Sec. "The Tensor Formalism"; cell binning with */
 /* a skin buffer, Sec. "Evaluation")                                        */
 /* ------------------------------------------------------------------------ */
+/* An empty table; device memory is taken by the first tmd_neighbors call
+ * and grown as needed.  Errors: INVALID_ARG (out NULL), OOM.  destroy frees
+ * it (NULL accepted; always TMD_OK). */
 tmd_status tmd_nlist_create(tmd_nlist **out);
 tmd_status tmd_nlist_destroy(tmd_nlist *nl);
 
@@ -360,6 +365,8 @@ typedef struct {
  * radius is rc + skin.  Allocates device memory.  Errors: INVALID_ARG, OOM. */
 tmd_status tmd_system_create(int64_t n, const double box[3], const int32_t pbc[3], double skin,
                              tmd_system **out);
+/* Free a system and its device and pinned host memory (NULL accepted;
+ * always TMD_OK). */
 tmd_status tmd_system_destroy(tmd_system *sys);
 
 /*
@@ -429,6 +436,8 @@ typedef struct tmd_batch tmd_batch;
  * Allocates the resident state.  Errors: INVALID_ARG, OOM. */
 tmd_status tmd_batch_create(int32_t n_systems, const int64_t *n_atoms, const double *boxes, const int32_t *pbc,
                             tmd_batch **out);
+/* Free a batch and its device and pinned host memory (NULL accepted;
+ * always TMD_OK). */
 tmd_status tmd_batch_destroy(tmd_batch *batch);
 /* Load one system from host arrays: pos [n][3] FP64 (A), vel [n][3] FP64
  * (A/fs, NULL = zero), types [n] int32, masses [n] FP64 (amu).  Synchronises. */

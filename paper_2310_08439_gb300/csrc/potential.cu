@@ -43,20 +43,23 @@ __global__ void k_split_pos(const double *__restrict__ pos, int64_t n, float4 *_
 // tile holds one species except at species boundaries).  Activations stay in
 // shared memory transposed, [unit][atom] with row stride TR + 4, so a thread
 // reads the 4 atoms of its row block for one unit with one vector load.  The
-// weights are streamed through two shared-memory buffers in chunks of KC
-// input rows by at most MLP_NP output columns: while the block multiplies with
-// one chunk, cp.async brings in the next chunk of the tile's fixed sequence of
-// products (forward layers, then the backward chain).  Every thread
-// accumulates a 4 x 4 block of outputs per item (one or two items per pass),
-// summing each group of 16 products separately before adding it to the
-// running total: the rounding error grows with 16 + Kin / 16 instead of Kin,
-// which halves the error of G' for the 192-128-128 networks.
+// weights are streamed through two shared-memory buffers in chunks of
+// MLP_KC input rows by at most NP output columns: while the block multiplies
+// with one chunk, cp.async brings in the next chunk of the tile's fixed
+// sequence of products (forward layers, then the backward chain).  Every
+// thread accumulates one 4 x 4 block of outputs per pass, summing each group
+// of 16 products separately before adding it to the running total: the
+// rounding error grows with 16 + Kin / 16 instead of Kin, which halves the
+// error of G' for the 192-128-128 networks.  For one species the input
+// activations are dead after the first product, so the second hidden layer
+// takes their place (a smaller block, one more block per SM).
 // ---------------------------------------------------------------------------
-// streamed weight rows per chunk: 16 for 64-atom tiles, 32 for 32-atom tiles
-// (whose activations leave the room)
+// streamed weight rows per chunk (32) and output columns per pass (64 for
+// 64-atom tiles, 128 for 32-atom tiles): one 4 x 4 output block per thread
+// and pass in both shapes
+constexpr int MLP_KC = 32;
 template <int TR>
-__host__ __device__ constexpr int mlp_kc() { return TR == 32 ? 32 : 16; }
-constexpr int MLP_NP = 128;    // output columns per pass
+__host__ __device__ constexpr int mlp_np() { return TR == 32 ? 128 : 64; }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
@@ -80,9 +83,9 @@ __device__ __forceinline__ MlpStep mlp_step(const DevModel &m, int s, int step) 
 }
 
 // Issue the copy of chunk (n0, k0) of product st into buf (all threads).
-template <int KC>
+template <int NP>
 __device__ __forceinline__ void mlp_issue(const MlpStep &st, int n0, int k0, float *buf) {
-    const int np = min(MLP_NP, st.N - n0), ncb = np >> 2, kc = min(KC, st.Kin - k0);
+    const int np = min(NP, st.N - n0), ncb = np >> 2, kc = min(MLP_KC, st.Kin - k0);
     if (np == st.N) {   // one contiguous block of W
         const float *src = st.W + (size_t)k0 * st.N;
         for (int idx = threadIdx.x; idx < kc * ncb; idx += MLP_THREADS) cp_async16(buf + 4 * idx, src + 4 * idx);
@@ -103,13 +106,13 @@ struct MlpStream {
 // Advance to the chunk after (n0, k0) of the current product (possibly the
 // first chunk of the next product or species) and issue it; always commits a
 // group so that wait_group 1 leaves exactly the current chunk pending.
-template <int KC>
+template <int NP>
 __device__ __forceinline__ void mlp_prefetch_next(const DevModel &m, const MlpStream &cur, const MlpStep &st,
                                                   float *wbuf) {
-    int s = cur.s, step = cur.step, n0 = cur.n0, k0 = cur.k0 + KC;
+    int s = cur.s, step = cur.step, n0 = cur.n0, k0 = cur.k0 + MLP_KC;
     if (k0 >= st.Kin) {
         k0 = 0;
-        n0 += MLP_NP;
+        n0 += NP;
         if (n0 >= st.N) {
             n0 = 0;
             if (++step == 2 * m.L) { step = 0; ++s; }
@@ -117,9 +120,28 @@ __device__ __forceinline__ void mlp_prefetch_next(const DevModel &m, const MlpSt
     }
     if (s <= cur.s_hi) {
         const MlpStep nx = (step == cur.step && s == cur.s) ? st : mlp_step(m, s, step);
-        mlp_issue<KC>(nx, n0, k0, wbuf + (cur.par ^ 1) * (KC * MLP_NP));
+        mlp_issue<NP>(nx, n0, k0, wbuf + (cur.par ^ 1) * (MLP_KC * NP));
     }
     cp_async_commit();
+}
+
+// Activation buffers act[0..L] from base on (row stride ldt); returns the
+// floats they take.  The input G (act[0]) is read by the first product only,
+// so for a one-species model (one pass over the products per tile) act[2],
+// written by the second product, shares its place.
+__host__ __device__ inline size_t mlp_act_layout(const DevModel &m, int ldt, float *base, float **act) {
+    const bool alias = m.S == 1 && m.L >= 2;
+    size_t off = 0;
+    for (int l = 0; l <= m.L; ++l) {
+        if (alias && l == 2) {
+            if (act) act[2] = act[0];
+            continue;
+        }
+        if (act) act[l] = base + off;
+        const int rows = (alias && l == 0 && m.dims[2] > m.dims[0]) ? m.dims[2] : m.dims[l];
+        off += (size_t)rows * ldt;
+    }
+    return off;
 }
 
 // One product of the stream.
@@ -132,112 +154,97 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
                                          float *__restrict__ gout, const int *s_atom, const int *s_type) {
     constexpr int LDT = TR + 4;
     constexpr int NRB = TR / 4;    // row blocks
-    constexpr int KC = mlp_kc<TR>();
+    constexpr int NP = mlp_np<TR>();
+    static_assert(NRB * (NP / 4) == MLP_THREADS, "one 4 x 4 output block per thread and pass");
     const int tid = threadIdx.x;
     const MlpStep st = mlp_step(m, ws.s, ws.step);
     const int N = st.N;
-    for (int n0 = 0; n0 < N; n0 += MLP_NP) {
-        const int np = min(MLP_NP, N - n0);
-        const int ncb = np >> 2;
-        const int items = NRB * ncb;
-        // row block fastest across the threads: conflict-free transposed loads and stores
-        int rb[2], cb[2];
+    // row block fastest across the threads: conflict-free transposed loads and stores
+    const int cb = tid / NRB, rb = tid - cb * NRB;
+    for (int n0 = 0; n0 < N; n0 += NP) {
+        const int np = min(NP, N - n0);
+        const bool active = cb < (np >> 2);
+        float acc[4][4];
 #pragma unroll
-        for (int ii = 0; ii < 2; ++ii) {
-            const int item = tid + ii * MLP_THREADS;
-            cb[ii] = item / NRB;
-            rb[ii] = item - cb[ii] * NRB;
-        }
-        float acc[2][4][4];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int ii = 0; ii < 2; ++ii)
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int o = 0; o < 4; ++o) acc[ii][i][o] = 0.f;
-        for (int k0 = 0; k0 < st.Kin; k0 += KC) {
-            const int kc = min(KC, st.Kin - k0);
+            for (int o = 0; o < 4; ++o) acc[i][o] = 0.f;
+        for (int k0 = 0; k0 < st.Kin; k0 += MLP_KC) {
+            const int kc = min(MLP_KC, st.Kin - k0);
             ws.n0 = n0;
             ws.k0 = k0;
-            mlp_prefetch_next<KC>(m, ws, st, wbuf);
+            mlp_prefetch_next<NP>(m, ws, st, wbuf);
             cp_async_wait1();
             __syncthreads();   // this chunk has landed for every thread; At is complete
-            const float *w = wbuf + ws.par * (KC * MLP_NP);
+            if (active) {
+                const float *a = At + (size_t)k0 * LDT + rb * 4;
+                const float *b = wbuf + ws.par * (MLP_KC * NP) + cb * 4;
+                // groups of 16 products summed separately, then added to acc
+                // (two-level summation; the same grouping for every tile
+                // shape, so the result does not depend on it)
+                for (int kg = 0; kg < kc; kg += 16) {
+                    float pp[4][4];
 #pragma unroll
-            for (int ii = 0; ii < 2; ++ii) {
-                if (tid + ii * MLP_THREADS < items) {
-                    const float *a = At + (size_t)k0 * LDT + rb[ii] * 4;
-                    const float *b = w + cb[ii] * 4;
-                    // groups of 16 products summed separately, then added to acc
-                    // (two-level summation; the same grouping for every KC, so
-                    // the result does not depend on the tile shape)
-                    for (int kg = 0; kg < kc; kg += 16) {
-                        float pp[4][4];
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
+                        for (int o = 0; o < 4; ++o) pp[i][o] = 0.f;
+                    const int ke = min(kg + 16, kc);
+                    auto step = [&](int k) {
+                        const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
+                        const float4 bv = *reinterpret_cast<const float4 *>(b + k * np);
+                        const float ai[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
-                            for (int o = 0; o < 4; ++o) pp[i][o] = 0.f;
-                        const int ke = min(kg + 16, kc);
-                        auto step = [&](int k) {
-                            const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
-                            const float4 bv = *reinterpret_cast<const float4 *>(b + k * np);
-                            const float ai[4] = {av.x, av.y, av.z, av.w};
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                pp[i][0] = fmaf(ai[i], bv.x, pp[i][0]);
-                                pp[i][1] = fmaf(ai[i], bv.y, pp[i][1]);
-                                pp[i][2] = fmaf(ai[i], bv.z, pp[i][2]);
-                                pp[i][3] = fmaf(ai[i], bv.w, pp[i][3]);
-                            }
-                        };
-                        if (ke - kg == 16) {
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) step(kg + k);
-                        } else {
-                            for (int k = kg; k < ke; ++k) step(k);
+                        for (int i = 0; i < 4; ++i) {
+                            pp[i][0] = fmaf(ai[i], bv.x, pp[i][0]);
+                            pp[i][1] = fmaf(ai[i], bv.y, pp[i][1]);
+                            pp[i][2] = fmaf(ai[i], bv.z, pp[i][2]);
+                            pp[i][3] = fmaf(ai[i], bv.w, pp[i][3]);
                         }
+                    };
+                    if (ke - kg == 16) {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int o = 0; o < 4; ++o) acc[ii][i][o] += pp[i][o];
+                        for (int k = 0; k < 16; ++k) step(kg + k);
+                    } else {
+                        for (int k = kg; k < ke; ++k) step(k);
                     }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) acc[i][o] += pp[i][o];
                 }
             }
             __syncthreads();   // every thread is done with this buffer
             ws.par ^= 1;
         }
+        if (!active) continue;
+        const int col = n0 + cb * 4;
+        if (EPI == 3) {
 #pragma unroll
-        for (int ii = 0; ii < 2; ++ii) {
-            if (tid + ii * MLP_THREADS >= items) continue;
-            const int col = n0 + cb[ii] * 4;
-            if (EPI == 3) {
+            for (int i = 0; i < 4; ++i) {
+                const int row = rb * 4 + i;
+                if (s_type[row] == ws.s)
+                    *reinterpret_cast<float4 *>(gout + (size_t)s_atom[row] * N + col) =
+                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            }
+        } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int row = rb[ii] * 4 + i;
-                    if (s_type[row] == ws.s)
-                        *reinterpret_cast<float4 *>(gout + (size_t)s_atom[row] * N + col) =
-                            make_float4(acc[ii][i][0], acc[ii][i][1], acc[ii][i][2], acc[ii][i][3]);
+            for (int o = 0; o < 4; ++o) {
+                float *c = Ct + (size_t)(col + o) * LDT + rb * 4;
+                float4 v;
+                if (EPI == 1) {
+                    const float bo = __ldg(bias + col + o);
+                    v.x = act_f(m.act, acc[0][o] + bo, m.sp_b);
+                    v.y = act_f(m.act, acc[1][o] + bo, m.sp_b);
+                    v.z = act_f(m.act, acc[2][o] + bo, m.sp_b);
+                    v.w = act_f(m.act, acc[3][o] + bo, m.sp_b);
+                } else {
+                    const float4 a = *reinterpret_cast<const float4 *>(c);
+                    v.x = acc[0][o] * act_da(m.act, a.x, m.sp_b);
+                    v.y = acc[1][o] * act_da(m.act, a.y, m.sp_b);
+                    v.z = acc[2][o] * act_da(m.act, a.z, m.sp_b);
+                    v.w = acc[3][o] * act_da(m.act, a.w, m.sp_b);
                 }
-            } else {
-#pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    float *c = Ct + (size_t)(col + o) * LDT + rb[ii] * 4;
-                    float4 v;
-                    if (EPI == 1) {
-                        const float bo = __ldg(bias + col + o);
-                        v.x = act_f(m.act, acc[ii][0][o] + bo, m.sp_b);
-                        v.y = act_f(m.act, acc[ii][1][o] + bo, m.sp_b);
-                        v.z = act_f(m.act, acc[ii][2][o] + bo, m.sp_b);
-                        v.w = act_f(m.act, acc[ii][3][o] + bo, m.sp_b);
-                    } else {
-                        const float4 a = *reinterpret_cast<const float4 *>(c);
-                        v.x = acc[ii][0][o] * act_da(m.act, a.x, m.sp_b);
-                        v.y = acc[ii][1][o] * act_da(m.act, a.y, m.sp_b);
-                        v.z = acc[ii][2][o] * act_da(m.act, a.z, m.sp_b);
-                        v.w = acc[ii][3][o] * act_da(m.act, a.w, m.sp_b);
-                    }
-                    *reinterpret_cast<float4 *>(c) = v;
-                }
+                *reinterpret_cast<float4 *>(c) = v;
             }
         }
     }
@@ -245,7 +252,7 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
 }
 
 template <int TR>
-__global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 3 : 2) k_mlp(DevModel m, const int32_t *__restrict__ perm,
+__global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel m, const int32_t *__restrict__ perm,
                                                         const int32_t *__restrict__ types, int64_t n,
                                                         const float *__restrict__ G, float *__restrict__ dG,
                                                         float *__restrict__ e_atom, double *__restrict__ part_e) {
@@ -256,15 +263,12 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 3 : 2) k_mlp(DevModel 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * TR;
     const int L = m.L, Dd = m.Dd;
-    // shared layout: two weight buffers, then act[l] = [dims[l]][LDT] for l = 0..L
+    // shared layout: two weight buffers, then act[l] = [dims[l]][LDT] for
+    // l = 0..L, with act[2] over act[0] for a one-species model
     float *wbuf = sm;
     float *act[MAX_LAYERS + 1];
-    constexpr int KC = mlp_kc<TR>();
-    float *ptr = sm + 2 * KC * MLP_NP;
-    for (int l = 0; l <= L; ++l) {
-        act[l] = ptr;
-        ptr += (size_t)m.dims[l] * LDT;
-    }
+    constexpr int NP = mlp_np<TR>();
+    mlp_act_layout(m, LDT, sm + 2 * MLP_KC * NP, act);
     if (tid < TR) {
         const int64_t p = p0 + tid;
         const int a = p < n ? perm[p] : -1;
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 3 : 2) k_mlp(DevModel 
     for (int r = 0; r < TR; ++r)
         if (s_type[r] >= 0) { s_lo = min(s_lo, s_type[r]); s_hi = max(s_hi, s_type[r]); }
     MlpStream ws{s_lo, s_hi, 0, 0, 0, 0};
-    if (s_lo <= s_hi) mlp_issue<KC>(mlp_step(m, s_lo, 0), 0, 0, wbuf);   // first chunk, under the G loads
+    if (s_lo <= s_hi) mlp_issue<NP>(mlp_step(m, s_lo, 0), 0, 0, wbuf);   // first chunk, under the G loads
     cp_async_commit();
     // G rows -> act[0] transposed (lane per atom row: conflict-free stores)
     for (int r = lane; r < TR; r += 32) {
@@ -776,9 +780,8 @@ size_t mlp_bf16_smem_bytes(const DevModel &dm) {
 // dynamic shared memory of k_mlp<TR>: transposed activations of every layer
 // plus one staged weight chunk
 static size_t mlp_smem_tr(const DevModel &dm, int tr) {
-    size_t fl = 0;
-    for (int l = 0; l <= dm.L; ++l) fl += (size_t)dm.dims[l] * (tr + 4);
-    fl += (size_t)2 * (tr == 32 ? 32 : 16) * MLP_NP;   // two weight chunks (mlp_kc)
+    size_t fl = mlp_act_layout(dm, tr + 4, nullptr, nullptr);
+    fl += (size_t)2 * MLP_KC * (tr == 32 ? mlp_np<32>() : mlp_np<64>());   // two weight chunks
     return fl * sizeof(float);
 }
 

@@ -151,7 +151,20 @@ def test_unsupported_shapes_are_rejected(tmdlib):
         with pytest.raises(tmdlib.TmdError) as e:
             tmdlib.Model(I.random_model(S, K, 5.0, widths, seed=1))
         assert e.value.status == tmdlib.ERR_UNIMPLEMENTED, (S, K)
-    # activations of a 32-atom tile beyond the shared memory of an SM
+    # activations of a 32-atom tile beyond the shared memory of an SM (two
+    # species: every activation buffer of its own)
     with pytest.raises(tmdlib.TmdError) as e:
-        tmdlib.Model(I.random_model(1, 128, 5.0, [256, 256, 256, 256], seed=1))
+        tmdlib.Model(I.random_model(2, 64, 5.0, [256, 256, 256, 256], seed=1))
     assert e.value.status == tmdlib.ERR_UNIMPLEMENTED
+
+
+def test_wide_network_with_shared_input_buffer(tmdlib):
+    """A one-species k = 128 model with four 256-wide layers: its FP32
+    network tile fits on chip only because the second hidden layer reuses the
+    input activations' buffer."""
+    s = _bcc_w(3.1887, (3, 3, 3), seed=256)
+    p = _scaled_model(128, 1, [256, 256, 256, 256], s, seed=256)
+    o = O.evaluate(O.OracleModel(p), s.pos, s.types, s.box, s.pbc)
+    g = _eval(tmdlib, tmdlib.Model(p), s, p.rc)
+    dE, dF, dW = _errs(g, o)
+    assert dE <= E_TOL and dF <= F_TOL and dW <= W_TOL, (dE, dF, dW)
