@@ -102,6 +102,26 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
+    def _lines(self):
+        try:
+            self.f.flush()
+            with open(self.path) as fh:
+                return fh.read().count("\n")
+        except Exception:
+            return 0
+
+    def wait_first(self, timeout=3.0):
+        """Block until nvidia-smi has written its first sample (its start-up
+        takes longer than a short timed region) and remember how many lines
+        precede the timed region: only later samples are kept."""
+        self.skip = 0
+        if self.proc is None:
+            return
+        t0 = time.time()
+        while self._lines() == 0 and time.time() - t0 < timeout:
+            time.sleep(0.02)
+        self.skip = self._lines()
+
     def stop(self):
         if self.proc is None:
             return None
@@ -113,7 +133,7 @@ class ClockSampler:
         self.f.close()
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in open(self.path).read().splitlines()[getattr(self, "skip", 0):]:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -540,7 +560,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large", choices=["large", "medium"])
@@ -628,6 +648,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks.start()
+    clocks.wait_first()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):

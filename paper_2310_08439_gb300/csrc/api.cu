@@ -24,6 +24,7 @@ void set_error(const char *fmt, ...) {
 
 tmd_status cuda_fail(cudaError_t e, const char *what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
+    (void)cudaGetLastError();   // report a non-sticky error once, not again on the next call
     if (e == cudaErrorMemoryAllocation) return TMD_ERR_OOM;
     return TMD_ERR_CUDA;
 }

@@ -824,8 +824,22 @@ static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, con
     return TMD_OK;
 }
 
-static tmd_status set_mlp_smem(const DevModel &dm) {
+// opt-in shared memory of the network kernel that runs: the FP32 k_mlp<TR>,
+// or (bf16 = true) the mma.sync kernel of the BF16 form
+static tmd_status set_mlp_smem(const DevModel &dm, bool bf16) {
     static size_t smem_set[2] = {0, 0}, smem_bf_set = 0;
+    if (bf16) {
+        const size_t sb = mlp_bf16_smem_bytes(dm);
+        if (sb > 227 * 1024) {
+            set_error("network too wide for the mma.sync BF16 kernel (%zu bytes of shared memory)", sb);
+            return TMD_ERR_UNIMPLEMENTED;
+        }
+        if (sb > 48 * 1024 && sb > smem_bf_set) {
+            TMD_CUDA(cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+            smem_bf_set = sb;
+        }
+        return TMD_OK;
+    }
     const int tr = mlp_tr(dm);
     const size_t smem = mlp_smem_bytes(dm);
     size_t &done = smem_set[tr == 64 ? 1 : 0];
@@ -836,28 +850,20 @@ static tmd_status set_mlp_smem(const DevModel &dm) {
             TMD_CUDA(cudaFuncSetAttribute(k_mlp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         done = smem;
     }
-    const size_t sb = mlp_bf16_smem_bytes(dm);
-    if (sb > 48 * 1024 && sb > smem_bf_set) {
-        TMD_CUDA(cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
-        smem_bf_set = sb;
-    }
     return TMD_OK;
 }
 
-// network forward + input gradient for n atoms in perm order (FP32 SIMT or
-// BF16 tensor cores, by the model's precision); part_e receives the per-tile
-// energy sums and *ntile_out their count.
 static tmd_status launch_network(const DevModel &dm, const int32_t *perm, const int32_t *types, int64_t n,
                                  const float *G, float *dG, float *e_atom, double *part_e, int *ntile_out,
                                  cudaStream_t s) {
     tmd_status st;
-    if ((st = set_mlp_smem(dm)) != TMD_OK) return st;
     if (dm.precision == TMD_PREC_BF16 && network_kernel() != 2 && mlp_umma_supported(dm))
         return mlp_umma_launch(dm, perm, types, n, G, dG, e_atom, part_e, ntile_out, s);
     if (dm.precision == TMD_PREC_BF16 && network_kernel() == 1) {
         set_error("the tcgen05 network kernel does not support these network shapes");
         return TMD_ERR_UNIMPLEMENTED;
     }
+    if ((st = set_mlp_smem(dm, dm.precision == TMD_PREC_BF16)) != TMD_OK) return st;
     if (dm.precision == TMD_PREC_BF16) {
         const int ntile = (int)((n + BT - 1) / BT);
         const BfCfg bcfg = mlp_bf16_cfg(dm);
