@@ -168,3 +168,25 @@ def test_wide_network_with_shared_input_buffer(tmdlib):
     g = _eval(tmdlib, tmdlib.Model(p), s, p.rc)
     dE, dF, dW = _errs(g, o)
     assert dE <= E_TOL and dF <= F_TOL and dW <= W_TOL, (dE, dF, dW)
+
+
+def test_wide_network_bf16_is_supported_or_rejected_cleanly(tmdlib):
+    """Switching the wide k = 128 model to the BF16 network either works on
+    one of the two kernels (loose BF16 bars) or is refused with
+    UNIMPLEMENTED; a refusal leaves the FP32 model usable."""
+    s = _bcc_w(3.1887, (3, 3, 3), seed=257)
+    p = _scaled_model(128, 1, [256, 256, 256, 256], s, seed=257)
+    o = O.evaluate(O.OracleModel(p), s.pos, s.types, s.box, s.pbc)
+    m = tmdlib.Model(p)
+    try:
+        m.set_precision("bf16")
+    except tmdlib.TmdError as e:
+        assert e.status == tmdlib.ERR_UNIMPLEMENTED
+        g = _eval(tmdlib, m, s, p.rc)
+        dE, dF, dW = _errs(g, o)
+        assert dE <= E_TOL and dF <= F_TOL and dW <= W_TOL, (dE, dF, dW)
+        return
+    b = _eval(tmdlib, m, s, p.rc)
+    bE, bF, _ = _errs(b, o)
+    assert bE < 1e-3 and bF < 0.5, (bE, bF)
+    assert tmdlib.device_status() == 0
