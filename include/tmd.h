@@ -178,7 +178,9 @@ tmd_status tmd_set_graphs(int32_t on);
  * multiple of 16, hidden widths <= 256, and the accumulators plus the stored
  * activation derivatives within 512 TMEM columns) or on mma.sync m16n8k16
  * (64-atom tiles).  AUTO takes tcgen05 when the shapes allow it;
- * TMD_NET_TCGEN05 makes other shapes fail with UNIMPLEMENTED.  Both compute
+ * TMD_NET_TCGEN05 makes other shapes fail with UNIMPLEMENTED, and so does
+ * TMD_NET_MMA_SYNC for a network whose 64-atom mma.sync tile exceeds the
+ * shared memory of an SM (reported by the evaluation call).  Both compute
  * BF16 products with FP32 accumulation (results differ in rounding order
  * only).  Errors: INVALID_ARG. */
 tmd_status tmd_set_network_kernel(int32_t kind);
