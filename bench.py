@@ -577,6 +577,8 @@ def main():
                          "(e.g. 32,64,128,160), throughput and device memory per size")
     ap.add_argument("--tuning", default="auto",
                     help="tile shapes 'ROWS,BLOCKS_PER_SM' instead of the autotuner (e.g. for profiler captures)")
+    ap.add_argument("--force-kernel", default="auto", choices=["auto", "simt", "tensor"],
+                    help="force pass of the unbatched evaluation (tmd_set_force_kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -599,6 +601,7 @@ def main():
     from paper_2310_08439_gb300 import build as B
     from paper_2310_08439_gb300 import tmd
     B.build()
+    tmd.set_force_kernel(args.force_kernel)
     if args.size_sweep:
         if rank == 0:
             reps = [int(x) for x in args.size_sweep.split(",")]

@@ -57,6 +57,8 @@ typedef enum {
 enum { TMD_ACT_TANH = 0, TMD_ACT_SQUAREPLUS = 1 };
 enum { TMD_PREC_FP32 = 0, TMD_PREC_BF16 = 1 };
 enum { TMD_NET_AUTO = 0, TMD_NET_TCGEN05 = 1, TMD_NET_MMA_SYNC = 2 };
+/* force pass of the unbatched evaluation (tmd_set_force_kernel) */
+enum { TMD_FORCE_AUTO = 0, TMD_FORCE_SIMT = 1, TMD_FORCE_TENSOR = 2 };
 
 /* Limits of the library. */
 #define TMD_MAX_SPECIES 4
@@ -184,6 +186,18 @@ tmd_status tmd_set_graphs(int32_t on);
  * BF16 products with FP32 accumulation (results differ in rounding order
  * only).  Errors: INVALID_ARG. */
 tmd_status tmd_set_network_kernel(int32_t kind);
+
+/* Force pass of the unbatched evaluation (process-wide; default
+ * TMD_FORCE_AUTO = TMD_FORCE_SIMT).  The per-pair sums V_d = sum_k P'_kd H_k
+ * and W_d = sum_k P'_kd H'_k (Eqs. U_abck, F1_abcx, F2_abcx) run either as
+ * FP32 FMAs, one pair per lane (SIMT), or per atom as one matrix product
+ * [H; H'] P' on the tensor cores (TENSOR: mma.sync on TF32 operands, each
+ * operand split into two TF32 parts and three products accumulated in FP32,
+ * which keeps FP32 accuracy).  TENSOR needs one species, K <= 32, the direct
+ * radial basis and a table with the pair cache; other models then fail with
+ * UNIMPLEMENTED.  Batched evaluations always use the SIMT pass.  Errors:
+ * INVALID_ARG. */
+tmd_status tmd_set_force_kernel(int32_t kind);
 
 /* Status bits recorded by device kernels that have no neighbour table to
  * report through (today: a bounded wait of the tcgen05 network kernel that

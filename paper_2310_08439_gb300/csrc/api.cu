@@ -22,6 +22,9 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 
+int g_force_kernel = TMD_FORCE_AUTO;   // tmd_set_force_kernel
+int force_kernel() { return g_force_kernel; }
+
 tmd_status cuda_fail(cudaError_t e, const char *what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
     (void)cudaGetLastError();   // report a non-sticky error once, not again on the next call
@@ -100,6 +103,7 @@ void model_key(const tmd_model *m, std::vector<uintptr_t> &k) {
     k.push_back((uintptr_t)m->dm.rtab_n);
     k.push_back((uintptr_t)m->dm.rtab_scale);
     k.push_back((uintptr_t)tmd::network_kernel());
+    k.push_back((uintptr_t)tmd::force_kernel());
 }
 
 uintptr_t bits_of(double x) {
@@ -579,6 +583,16 @@ tmd_status tmd_set_network_kernel(int32_t kind) {
         return TMD_ERR_INVALID_ARG;
     }
     tmd::g_network_kernel = kind;
+    return TMD_OK;
+}
+
+tmd_status tmd_set_force_kernel(int32_t kind) {
+    g_err[0] = 0;
+    if (kind < TMD_FORCE_AUTO || kind > TMD_FORCE_TENSOR) {
+        set_error("force kernel must be TMD_FORCE_AUTO, TMD_FORCE_SIMT or TMD_FORCE_TENSOR");
+        return TMD_ERR_INVALID_ARG;
+    }
+    tmd::g_force_kernel = kind;
     return TMD_OK;
 }
 

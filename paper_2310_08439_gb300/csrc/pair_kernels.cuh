@@ -471,6 +471,35 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
+// The rest of g_ij once V_d and W_d of the pair are known.
+__device__ __forceinline__ void pair_grad_tail(const float (&V)[NMOM], const float (&Wd)[NMOM], float ux, float uy,
+                                               float uz, float ir, float &gxs, float &gys, float &gzs) {
+    float M[NMOM];
+    moments20(ux, uy, uz, M);
+    float w0 = Wd[0], w1 = 0.f, w2 = 0.f, w3 = 0.f;
+#pragma unroll
+    for (int d = 1; d < NMOM; d += 4) {
+        w1 = fmaf(Wd[d], M[d], w1);
+        w2 = fmaf(Wd[d + 1], M[d + 1], w2);
+        w3 = fmaf(Wd[d + 2], M[d + 2], w3);
+        if (d + 3 < NMOM) w0 = fmaf(Wd[d + 3], M[d + 3], w0);
+    }
+    const float dEdr = (w0 + w1) + (w2 + w3);
+    // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
+    const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
+    const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
+                     2.f * xy * V[11] + 2.f * xz * V[12] + yy * V[13] + yz * V[14] + zz * V[15];
+    const float gy = V[2] + ux * V[5] + 2.f * uy * V[7] + uz * V[8] + xx * V[11] + 2.f * xy * V[13] +
+                     xz * V[14] + 3.f * yy * V[16] + 2.f * yz * V[17] + zz * V[18];
+    const float gz = V[3] + ux * V[6] + uy * V[8] + 2.f * uz * V[9] + xx * V[12] + xy * V[14] +
+                     2.f * xz * V[15] + yy * V[17] + 2.f * yz * V[18] + 3.f * zz * V[19];
+    const float ug = ux * gx + uy * gy + uz * gz;
+    // g_ij = dE/dD_ij = dE/dr u + (I - u u^T) dE/du / r
+    gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
+    gys = fmaf(dEdr, uy, (gy - uy * ug) * ir);
+    gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
+}
+
 // g_ij = dE/dD_ij of one in-cutoff pair (Eqs. dP_abkd, U_abck, F1_abcx,
 // F2_abcx): Pb = the centre atom's P' for the neighbour's species, rad = the
 // radial parameters of the (centre, neighbour) species pair.
@@ -521,31 +550,9 @@ __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, con
             Wd[4 * q4 + 3] = fmaf(pd.w, dHk, Wd[4 * q4 + 3]);
         }
     }
-    float M[NMOM];
-    moments20(ux, uy, uz, M);
-    float w0 = Wd[0], w1 = 0.f, w2 = 0.f, w3 = 0.f;
-#pragma unroll
-    for (int d = 1; d < NMOM; d += 4) {
-        w1 = fmaf(Wd[d], M[d], w1);
-        w2 = fmaf(Wd[d + 1], M[d + 1], w2);
-        w3 = fmaf(Wd[d + 2], M[d + 2], w3);
-        if (d + 3 < NMOM) w0 = fmaf(Wd[d + 3], M[d + 3], w0);
-    }
-    const float dEdr = (w0 + w1) + (w2 + w3);
-    // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
-    const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
-    const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
-                     2.f * xy * V[11] + 2.f * xz * V[12] + yy * V[13] + yz * V[14] + zz * V[15];
-    const float gy = V[2] + ux * V[5] + 2.f * uy * V[7] + uz * V[8] + xx * V[11] + 2.f * xy * V[13] +
-                     xz * V[14] + 3.f * yy * V[16] + 2.f * yz * V[17] + zz * V[18];
-    const float gz = V[3] + ux * V[6] + uy * V[8] + 2.f * uz * V[9] + xx * V[12] + xy * V[14] +
-                     2.f * xz * V[15] + yy * V[17] + 2.f * yz * V[18] + 3.f * zz * V[19];
-    const float ug = ux * gx + uy * gy + uz * gz;
-    // g_ij = dE/dD_ij = dE/dr u + (I - u u^T) dE/du / r
-    gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
-    gys = fmaf(dEdr, uy, (gy - uy * ug) * ir);
-    gzs = fmaf(dEdr, uz, (gz - uz * ug) * ir);
+    pair_grad_tail(V, Wd, ux, uy, uz, ir, gxs, gys, gzs);
 }
+
 
 // P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm (for m = 0: G'_bk0 sign(P)) of atom a
 // into a shared slot, each lane its (K/8 x 5) block  (Eq. dP_abkd)
@@ -720,6 +727,225 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
     }
 }
 
+// ---------------------------------------------------------------------------
+// force pass with the per-atom contractions on tensor cores
+// ---------------------------------------------------------------------------
+// For one atom the pair sums V_jd = sum_k H_jk P'_kd and W_jd = sum_k H'_jk P'_kd
+// (Eqs. U_abck, F1_abcx, F2_abcx) are one matrix product: [H; H'] (rows =
+// pairs, columns = k) times P' (k x d).  Each warp takes its atom's cached
+// pairs 32 at a time: every lane forms H and H' of its pair into a shared
+// 64 x K tile (rows 0-31 H, rows 32-63 H'), the warp multiplies the tile by P'
+// with mma.sync m16n8k8 on TF32 operands (d padded to 24 with zeros), and
+// every lane reads back the V and W rows of its pair for the rest of g_ij.
+// FP32 accuracy from TF32 products: each operand x is split into
+// x_hi = tf32(x) and x_lo = tf32(x - x_hi), and a product is accumulated as
+// a_lo b_hi + a_hi b_lo + a_hi b_hi in FP32 (the dropped a_lo b_lo and the
+// split remainders are about 2^-22 of |a b|).
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    const float rest = x - __uint_as_float(hi);   // exact
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(rest));
+}
+
+// c += a b for one m16n8k8 tile (a: 16 x 8 row-major, b: 8 x 8, c: 16 x 8)
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One species, direct radial basis, pair cache present.
+template <int K>
+__global__ void __launch_bounds__(PW * 32, 4) k_force_tc(DevModel m, DevNlist nl, const float *__restrict__ Pin,
+                                                      const float *__restrict__ dG,
+                                                      unsigned long long *__restrict__ Fq,
+                                                      double *__restrict__ part_w) {
+    static_assert(K % 8 == 0 && K <= 32, "k steps of 8, one pass");
+    constexpr int KS = K / 8;        // k steps of the product
+    constexpr int AS = K + 4;        // row stride of the H / H' tile (conflict-free fragment loads)
+    constexpr int CS = 28;           // row stride of the V / W tile (24 columns, 16-byte rows)
+    constexpr int PSTR = K * NMOM + 4;
+    // the V / W tile is written over the H / H' tile, one m tile at a time,
+    // in descending order when its rows are longer (CS > AS) and ascending
+    // otherwise: the words a tile's results land on then hold only H / H'
+    // rows of this tile (already in registers) or of tiles already multiplied
+    constexpr int TILE = (64 * CS > 64 * AS) ? 64 * CS : 64 * AS;
+    constexpr bool ASCENDING = AS >= CS;
+    __shared__ float4 s_rad[K];
+    __shared__ __align__(16) float s_Pd[PW][PSTR];
+    __shared__ __align__(16) float s_T[PW][TILE];
+    __shared__ double s_w[PW][9];
+    for (int t = threadIdx.x; t < K; t += blockDim.x) s_rad[t] = m.radial[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = lane >> 2, g = lane & 3;   // P' setup block; also the fragment row / column group
+    float Tg[5];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
+    float wsum[9], wcmp[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) { wsum[t] = 0.f; wcmp[t] = 0.f; }
+    float *sPd = s_Pd[warp];
+    float *sT = s_T[warp];
+    const int64_t total = (int64_t)gridDim.x * PW;
+    for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
+        const int a = nl.perm[p];
+        pprime_setup<K, 1>(Pin, dG, a, sPd, kg, g, Tg);
+        __syncwarp();
+        // B fragments of P' (k x 24), hi and lo parts: b0 = (k = t, n = g), b1 = (k = t + 4, n = g)
+        uint32_t bh[KS][3][2], bl[KS][3][2];
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+            for (int nt = 0; nt < 3; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = ks * 8 + g + 4 * h, d = nt * 8 + kg;
+                    split_tf32(d < NMOM ? sPd[k * NMOM + d] : 0.f, bh[ks][nt][h], bl[ks][nt][h]);
+                }
+        const int np = nl.npair[a];
+        const int64_t pb = nl.beg[a];
+        long long fx = 0, fy = 0, fz = 0;
+        float wa[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) wa[t] = 0.f;
+        for (int base = 0; base < np; base += 32) {
+            const int nb = min(32, np - base);
+            const bool valid = lane < nb;
+            float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 e2 = make_float2(1.f, 0.f);
+            if (valid) {
+                e = nl.pq[pb + base + lane];
+                e2 = nl.pq2[pb + base + lane];
+            }
+            float r_hi, r_lo, ir;
+            split_sqrt(e2.x, e2.y, r_hi, r_lo, ir);
+            {   // H and H' of this lane's pair into rows lane and 32 + lane (zeros for idle lanes)
+                float fc, dfc;
+                cutoff_fn(r_hi, m.inv_rc, fc, dfc);
+                if (!valid) fc = dfc = 0.f;
+                float *hrow = sT + lane * AS, *drow = sT + (32 + lane) * AS;
+#pragma unroll
+                for (int k4 = 0; k4 < K; k4 += 4) {
+                    float hv[4], dv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 rp = s_rad[k4 + u];
+                        const float t = (r_hi - rp.x) + (r_lo - rp.y);
+                        const float f = ex2_ftz(-rp.z * t * t);
+                        hv[u] = f * fc;
+                        dv[u] = f * fmaf(-rp.w * t, fc, dfc);
+                    }
+                    *reinterpret_cast<float4 *>(hrow + k4) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<float4 *>(drow + k4) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                }
+            }
+            __syncwarp();
+            // [H; H'] P' -> V / W rows (m tiles 0, 1: H; 2, 3: H'); tiles past
+            // the last pair are skipped
+            const int mt_used = (nb + 15) >> 4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int mt = ASCENDING ? i : 3 - i;
+                if ((mt & 1) >= mt_used) continue;
+                float c[3][4];
+#pragma unroll
+                for (int nt = 0; nt < 3; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) c[nt][q] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    const float *r0 = sT + (mt * 16 + kg) * AS + ks * 8 + g;
+                    const float *r1 = r0 + 8 * AS;
+                    uint32_t ah[4], al[4];
+                    split_tf32(r0[0], ah[0], al[0]);
+                    split_tf32(r1[0], ah[1], al[1]);
+                    split_tf32(r0[4], ah[2], al[2]);
+                    split_tf32(r1[4], ah[3], al[3]);
+#pragma unroll
+                    for (int nt = 0; nt < 3; ++nt) {
+                        mma_tf32(c[nt], al, bh[ks][nt][0], bh[ks][nt][1]);
+                        mma_tf32(c[nt], ah, bl[ks][nt][0], bl[ks][nt][1]);
+                        mma_tf32(c[nt], ah, bh[ks][nt][0], bh[ks][nt][1]);
+                    }
+                }
+                __syncwarp();   // every lane's fragment loads of this tile precede the stores below
+#pragma unroll
+                for (int nt = 0; nt < 3; ++nt) {
+                    float *c0 = sT + (mt * 16 + kg) * CS + nt * 8 + 2 * g;
+                    *reinterpret_cast<float2 *>(c0) = make_float2(c[nt][0], c[nt][1]);
+                    *reinterpret_cast<float2 *>(c0 + 8 * CS) = make_float2(c[nt][2], c[nt][3]);
+                }
+                __syncwarp();
+            }
+            if (valid) {
+                float V[NMOM], Wd[NMOM];
+                const float *vr = sT + lane * CS, *wr = sT + (32 + lane) * CS;
+#pragma unroll
+                for (int q4 = 0; q4 < NMOM / 4; ++q4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(vr + 4 * q4);
+                    const float4 w = *reinterpret_cast<const float4 *>(wr + 4 * q4);
+                    V[4 * q4] = v.x; V[4 * q4 + 1] = v.y; V[4 * q4 + 2] = v.z; V[4 * q4 + 3] = v.w;
+                    Wd[4 * q4] = w.x; Wd[4 * q4 + 1] = w.y; Wd[4 * q4 + 2] = w.z; Wd[4 * q4 + 3] = w.w;
+                }
+                float gxs, gys, gzs;
+                pair_grad_tail(V, Wd, e.x * ir, e.y * ir, e.z * ir, ir, gxs, gys, gzs);
+                const int j = (int)(__float_as_uint(e.w) & 0x0FFFFFFFu);
+                // ScatterSum in 2^-32 fixed point (exact, order independent)
+                const long long qx = to_fixed(gxs);
+                const long long qy = to_fixed(gys);
+                const long long qz = to_fixed(gzs);
+                fx += qx; fy += qy; fz += qz;
+                atomicAdd(&Fq[3 * (int64_t)j], (unsigned long long)(-qx));
+                atomicAdd(&Fq[3 * (int64_t)j + 1], (unsigned long long)(-qy));
+                atomicAdd(&Fq[3 * (int64_t)j + 2], (unsigned long long)(-qz));
+                const float D[3] = {e.x, e.y, e.z};
+                const float gv[3] = {gxs, gys, gzs};
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) wa[al * 3 + be] = fmaf(-D[al], gv[be], wa[al * 3 + be]);
+            }
+            __syncwarp();   // the tile is rewritten by the next batch
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fx);
+            atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fy);
+            atomicAdd(&Fq[3 * (int64_t)a + 2], (unsigned long long)fz);
+        }
+#pragma unroll
+        for (int t = 0; t < 9; ++t) kahan_add(wsum[t], wcmp[t], wa[t]);
+        __syncwarp();   // sPd is rewritten by the next atom
+    }
+    // virial: per-lane compensated sums -> warp total as an FP32 double-float -> FP64 block total
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        float hi = wsum[t], lo = -wcmp[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float sh, se;
+            two_sum(hi, oh, sh, se);
+            lo = (lo + ol) + se;
+            two_sum(sh, lo, hi, lo);
+        }
+        if (lane == 0) s_w[warp][t] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double v = 0.0;
+        for (int w = 0; w < PW; ++w) v += s_w[w][threadIdx.x];
+        part_w[(size_t)blockIdx.x * 9 + threadIdx.x] = v;
+    }
+}
+
 // PAW (batched): each atom's virial is summed over its own pairs and written
 // to w_atom [atoms][9] for per-system reductions; otherwise lanes keep
 // compensated running sums and each block writes one FP64 partial.
@@ -870,7 +1096,13 @@ tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const dou
     else if (w_atom)
         TMD_LAUNCH("k_force", s, k_force<K, S, true, true, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
                                                                                          nl->dG, nl->Fq, part_w, w_atom));
-    else if (dn.pq && dm.rtab)
+    else if (force_kernel() == TMD_FORCE_TENSOR && !(dn.pq && !dm.rtab && S == 1 && K <= 32)) {
+        set_error("the tensor-core force pass needs one species, K <= 32, the direct radial basis and the pair cache");
+        return TMD_ERR_UNIMPLEMENTED;
+    } else if (force_kernel() == TMD_FORCE_TENSOR) {
+        if constexpr (S == 1 && K <= 32)
+            TMD_LAUNCH("k_force", s, k_force_tc<K><<<nblk, PW * 32, 0, s>>>(dm, dn, nl->P, nl->dG, nl->Fq, part_w));
+    } else if (dn.pq && dm.rtab)
         TMD_LAUNCH("k_force", s, k_force_merged<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, types, nl->P, nl->dG,
                                                                                    nl->Fq, part_w));
     else if (dn.pq)

@@ -69,6 +69,8 @@ tmd_status mlp_umma_launch(const DevModel &dm, const int32_t *perm, const int32_
 // network kernel of the BF16 form: 0 = tcgen05 when the shapes allow it, else
 // mma.sync; 1 = tcgen05 only; 2 = mma.sync only
 int network_kernel();
+// force pass of the FP32 path: TMD_FORCE_AUTO / _SIMT / _TENSOR (api.cu)
+int force_kernel();
 
 // One system of a batch (a single evaluation is a batch of one): box, cell
 // grid, first global cell, list radius and the FP32 screening band.

@@ -69,6 +69,7 @@ _SIGS = {
     "tmd_model_set_radial_table_values": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                                     C.POINTER(C.c_double)]),
     "tmd_set_network_kernel": (C.c_int, [C.c_int32]),
+    "tmd_set_force_kernel": (C.c_int, [C.c_int32]),
     "tmd_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
     "tmd_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int32)]),
     "tmd_model_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
@@ -134,6 +135,15 @@ NET = {"auto": 0, "tcgen05": 1, "mma_sync": 2}
 def set_network_kernel(kind="auto"):
     """BF16 network kernel: "auto" (tcgen05 when the shapes allow), "tcgen05", "mma_sync"."""
     check(lib().tmd_set_network_kernel(NET[kind]))
+
+
+FORCE = {"auto": 0, "simt": 1, "tensor": 2}
+
+
+def set_force_kernel(kind="auto"):
+    """Force pass of the unbatched evaluation: "auto", "simt" (FP32 FMAs) or
+    "tensor" (per-atom products on TF32 tensor cores with split operands)."""
+    check(lib().tmd_set_force_kernel(FORCE[kind]))
 
 
 def device_status():
