@@ -525,6 +525,31 @@ def size_sweep(tmd, torch, reps_list, steps, warmup, rebuild_every):
     return out
 
 
+def nve_run(tmd, torch, total_steps, every, rebuild_every):
+    """Energy conservation of the FP32 MD loop on the 1,048,576-atom lattice
+    (300 K start, 1 fs steps): total energy per atom every ``every`` steps,
+    with the table rebuilt every ``rebuild_every`` steps (0: only when an atom
+    moved more than skin/2)."""
+    w, _ = workload("large", 64, rebuild_every)
+    s = w.systems[0]
+    model = tmd.Model(w.model)
+    sysm = tmd.System(s.n, s.box, s.pbc, skin=w.skin)
+    sysm.set_state(s.pos, s.vel, s.types, s.masses)
+    th = sysm.step(model, w.dt_fs, 0)
+    rows = [{"step": 0, "e_tot_per_atom": (th["e_pot"] + th["e_kin"]) / s.n, "temperature": th["temperature"]}]
+    done = 0
+    while done < total_steps:
+        k = min(every, total_steps - done)
+        th = sysm.step(model, w.dt_fs, k, rebuild_every=rebuild_every)
+        done += k
+        rows.append({"step": done, "e_tot_per_atom": (th["e_pot"] + th["e_kin"]) / s.n,
+                     "temperature": th["temperature"], "rebuilds": th["rebuilds"]})
+    torch.cuda.synchronize()
+    e = np.array([r["e_tot_per_atom"] for r in rows])
+    return {"atoms": s.n, "dt_fs": w.dt_fs, "rebuild_every": rebuild_every, "steps": total_steps,
+            "max_abs_drift_per_atom_eV": float(np.abs(e - e[0]).max()), "trace": rows}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -577,6 +602,9 @@ def main():
                          "(e.g. 32,64,128,160), throughput and device memory per size")
     ap.add_argument("--tuning", default="auto",
                     help="tile shapes 'ROWS,BLOCKS_PER_SM' instead of the autotuner (e.g. for profiler captures)")
+    ap.add_argument("--nve", default="",
+                    help="instead of the bench line: 'STEPS,EVERY' of an NVE run of the large lattice, total energy "
+                         "per atom every EVERY steps (table cadence from --rebuild-every)")
     ap.add_argument("--force-kernel", default="auto", choices=["auto", "simt", "tensor"],
                     help="force pass of the unbatched evaluation (tmd_set_force_kernel)")
     args = ap.parse_args()
@@ -602,6 +630,11 @@ def main():
     from paper_2310_08439_gb300 import tmd
     B.build()
     tmd.set_force_kernel(args.force_kernel)
+    if args.nve:
+        if rank == 0:
+            steps_n, every = (int(x) for x in args.nve.split(","))
+            print(json.dumps({"nve": nve_run(tmd, torch, steps_n, every, args.rebuild_every)}), flush=True)
+        return
     if args.size_sweep:
         if rank == 0:
             reps = [int(x) for x in args.size_sweep.split(",")]
