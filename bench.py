@@ -525,14 +525,14 @@ def size_sweep(tmd, torch, reps_list, steps, warmup, rebuild_every):
     return out
 
 
-def nve_run(tmd, torch, total_steps, every, rebuild_every):
-    """Energy conservation of the FP32 MD loop on the 1,048,576-atom lattice
+def nve_run(tmd, torch, total_steps, every, rebuild_every, precision="fp32"):
+    """Energy conservation of the MD loop on the 1,048,576-atom lattice
     (300 K start, 1 fs steps): total energy per atom every ``every`` steps,
     with the table rebuilt every ``rebuild_every`` steps (0: only when an atom
-    moved more than skin/2)."""
+    moved more than skin/2); ``precision`` is the network form."""
     w, _ = workload("large", 64, rebuild_every)
     s = w.systems[0]
-    model = tmd.Model(w.model)
+    model = tmd.Model(w.model, precision=precision)
     sysm = tmd.System(s.n, s.box, s.pbc, skin=w.skin)
     sysm.set_state(s.pos, s.vel, s.types, s.masses)
     th = sysm.step(model, w.dt_fs, 0)
@@ -546,7 +546,8 @@ def nve_run(tmd, torch, total_steps, every, rebuild_every):
                      "temperature": th["temperature"], "rebuilds": th["rebuilds"]})
     torch.cuda.synchronize()
     e = np.array([r["e_tot_per_atom"] for r in rows])
-    return {"atoms": s.n, "dt_fs": w.dt_fs, "rebuild_every": rebuild_every, "steps": total_steps,
+    return {"atoms": s.n, "dt_fs": w.dt_fs, "rebuild_every": rebuild_every, "precision": precision,
+            "steps": total_steps,
             "max_abs_drift_per_atom_eV": float(np.abs(e - e[0]).max()), "trace": rows}
 
 
@@ -633,7 +634,8 @@ def main():
     if args.nve:
         if rank == 0:
             steps_n, every = (int(x) for x in args.nve.split(","))
-            print(json.dumps({"nve": nve_run(tmd, torch, steps_n, every, args.rebuild_every)}), flush=True)
+            print(json.dumps({"nve": nve_run(tmd, torch, steps_n, every, args.rebuild_every, args.precision)}),
+                  flush=True)
         return
     if args.size_sweep:
         if rank == 0:
