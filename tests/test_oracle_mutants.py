@@ -28,19 +28,52 @@ MUTANTS = {
                                      "const size_t base = ((size_t)tj * m->S + ti)"),
 }
 
+# Mutants that must be caught by one named pin (not only by a finite-difference
+# tolerance somewhere): name -> ([(old, new, occurrences)], pin test).
+TARGETED = {
+    # SquarePlus with b^2 in place of b, in the value and the derivative alike
+    "squareplus_b_squared": ([("m->sp_b", "m->sp_b * m->sp_b", 2)], "test_squareplus_special_values_and_slope"),
+    # SquarePlus slope halved at every z (value intact)
+    "squareplus_slope_halved": ([("return 0.5 * (1.0 + z / sqrt(z * z + m->sp_b));",
+                                  "return 0.25 * (1.0 + z / sqrt(z * z + m->sp_b));", 1)],
+                                "test_squareplus_special_values_and_slope"),
+    # Gaussian twice as wide, exp(-eta t^2 / 2), with the derivative to match
+    "gaussian_width_halved": ([("const double fk = exp(-eta * (r - mu) * (r - mu));",
+                                "const double fk = exp(-0.5 * eta * (r - mu) * (r - mu));", 1),
+                               ("const double dfk = -2.0 * eta * (r - mu) * fk;",
+                                "const double dfk = -eta * (r - mu) * fk;", 1)],
+                              "test_radial_gaussian_width_away_from_centre"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_reject_planted_bug(name, tmp_path):
-    old, new = MUTANTS[name]
+
+def _run_pins(edits, tmp_path, select=None):
     src = open(SRC).read()
-    assert src.count(old) == 1, name
+    for old, new, count in edits:
+        assert src.count(old) == count, old
+        src = src.replace(old, new)
     mut = tmp_path / "mut.c"
-    mut.write_text(src.replace(old, new))
+    mut.write_text(src)
     so = tmp_path / "libmut.so"
     subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                     "-D_GNU_SOURCE", "-o", str(so), str(mut), "-lm"], check=True)
     env = dict(os.environ, TMD_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    target = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+    if select:
+        target += "::" + select
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", target],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_planted_bug(name, tmp_path):
+    old, new = MUTANTS[name]
+    r = _run_pins([(old, new, 1)], tmp_path)
     assert r.returncode != 0, f"planted bug {name} survived the pins"
+
+
+@pytest.mark.parametrize("name", sorted(TARGETED))
+def test_named_pin_rejects_planted_bug(name, tmp_path):
+    edits, pin = TARGETED[name]
+    r = _run_pins(edits, tmp_path, select=pin)
+    assert r.returncode != 0, f"planted bug {name} survived {pin}"
+    assert "1 failed" in r.stdout, r.stdout[-2000:]

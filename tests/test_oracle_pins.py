@@ -92,6 +92,46 @@ def test_radial_special_values_and_derivative():
         assert np.allclose(dH, (hp - hm) / 2e-6, atol=1e-8)
 
 
+def test_radial_gaussian_width_away_from_centre():
+    """The width of f_k = exp(-eta (r - mu)^2) (reading c2), checked away from
+    the centres, where H = 1 at mu cannot see it:
+    - two channels at the same r share f_c, so ln(H_k / H_l) equals
+      -eta_k (r - mu_k)^2 + eta_l (r - mu_l)^2 for arbitrary centres and widths;
+    - one standard deviation out, r = mu_k + 1/sqrt(2 eta_k), the Gaussian is
+      e^(-1/2), and f_c there is the closed form (cos(pi r / rc) + 1) / 2;
+    - with the default spacing (eta = 1/(2 delta^2)) neighbouring channels
+      cross half way between their centres at e^(-1/8) f_c, and at mu_k the
+      next channel has fallen to e^(-1/2) of channel k."""
+    rc = 4.0
+    p, m = _small_model(K=5, rc=rc)
+    fc = lambda r: 0.5 * (math.cos(math.pi * r / rc) + 1.0)
+    delta = p.mu[0, 0, 1] - p.mu[0, 0, 0]
+    for k in range(4):
+        mid = 0.5 * (p.mu[0, 0, k] + p.mu[0, 0, k + 1])
+        H, _ = O.radial(m, 0, 0, mid)
+        assert abs(H[k] - math.exp(-0.125) * fc(mid)) < 1e-14
+        assert abs(H[k + 1] - math.exp(-0.125) * fc(mid)) < 1e-14
+        H, _ = O.radial(m, 0, 0, p.mu[0, 0, k])
+        assert abs(H[k + 1] / H[k] - math.exp(-0.5)) < 1e-14
+    assert abs(delta - rc / 4) < 1e-15
+    rng = np.random.default_rng(11)
+    p.mu[:] = rng.uniform(0.0, rc, size=p.mu.shape)
+    p.eta[:] = rng.uniform(0.3, 3.0, size=p.eta.shape)
+    m = O.OracleModel(p)
+    for k in range(5):
+        eta, mu = p.eta[0, 0, k], p.mu[0, 0, k]
+        r = mu + 1.0 / math.sqrt(2.0 * eta)
+        if r < rc:
+            H, _ = O.radial(m, 0, 0, r)
+            assert abs(H[k] - math.exp(-0.5) * fc(r)) < 1e-14
+    for r in rng.uniform(0.2, rc - 0.2, size=20):
+        H, _ = O.radial(m, 0, 0, r)
+        for k in range(5):
+            for l in range(5):
+                want = -p.eta[0, 0, k] * (r - p.mu[0, 0, k]) ** 2 + p.eta[0, 0, l] * (r - p.mu[0, 0, l]) ** 2
+                assert abs(math.log(H[k] / H[l]) - want) < 1e-11
+
+
 # ---------------------------------------------------------------- tabulated H
 def test_hermite_reproduces_cubics_and_quartic_error():
     """Cubic Hermite interpolation from end values and slopes reproduces every
@@ -378,6 +418,46 @@ def test_network_bias_only_and_single_unit():
     out = O.evaluate(om, c.pos, c.types, c.box, c.pbc, want_G=True)
     ref = 1.3 * np.tanh(0.7 * out["G"][:, col]) + 0.25
     assert np.allclose(out["e_atom"], ref, rtol=1e-14, atol=1e-15)
+
+
+def test_squareplus_special_values_and_slope():
+    """SquarePlus (Barron's smooth ReLU, the activation of the paper's
+    potentials in Sec. "Evaluation") through a one-unit network whose hidden
+    input is fixed by its bias (E_a = sp(z0)):
+    - sp(0) = sqrt(b)/2;
+    - sp(z) - z -> b / (4 z) for z >> sqrt(b) (so sp(z) -> z);
+    - sp(-z) -> b / (4 z) for z >> sqrt(b) (so sp -> 0 on the left).
+    The slope at 0 is 1/2: with a tiny first-layer weight eps on one column
+    (z = eps G), every force of the SquarePlus network is half the force of
+    the same network with tanh (slope 1 at 0), up to O(eps)."""
+    for b in (4.0, 2.5):
+        p, _ = _small_model(K=4, rc=4.5, widths=(1,), activation="squareplus")
+        p.squareplus_b = b
+        c = I.cluster(6, 2.5, seed=4)
+        Dd = p.n_desc
+        for z0, want, tol in [(0.0, 0.5 * math.sqrt(b), 1e-15),
+                              (1e4, 1e4 + b / 4e4, 1e-10),
+                              (-1e4, b / 4e4, 1e-10)]:
+            w = p.weights[0]
+            w[:] = 0.0
+            w[Dd] = z0            # b1[0] (after W1 [1 x Dd])
+            w[Dd + 1] = 1.0       # W2[0, 0]
+            out = O.evaluate(O.OracleModel(p), c.pos, c.types, c.box, c.pbc)
+            assert np.all(np.abs(out["e_atom"] - want) < tol), (b, z0)
+    eps = 1e-7
+    col = 4 * 1 + 0                       # channel 1, rank 0
+    Dd = 4 * 4
+    F = {}
+    for act in ("squareplus", "tanh"):
+        p, _ = _small_model(K=4, rc=4.5, widths=(1,), activation=act)
+        w = p.weights[0]
+        w[:] = 0.0
+        w[col] = eps              # W1[0, col]
+        w[Dd + 1] = 1.0           # W2[0, 0]
+        c = I.cluster(10, 3.0, seed=6)
+        F[act] = O.evaluate(O.OracleModel(p), c.pos, c.types, c.box, c.pbc)["forces"]
+    assert np.abs(F["tanh"]).max() > 0
+    assert np.allclose(F["squareplus"], 0.5 * F["tanh"], rtol=1e-5, atol=1e-6 * np.abs(F["tanh"]).max())
 
 
 # ---------------------------------------------------------------- forces
