@@ -243,9 +243,9 @@ def radial_table_measure(tmd, model, sysm, s, w, steps, torch, stream):
 
 def batch_measure(tmd, torch, steps=5):
     """512 uneven systems (configs: batch) evaluated by one set of launches, FP32
-    and BF16 network forms.  Returns the measurement and, for a sample of the
-    systems, their energies and forces (compared with the FP64 oracle in the
-    oracle leg, ``batch_errors``)."""
+    and BF16 network forms.  Returns the measurement and every system's energy
+    and forces in both forms (compared with the FP64 oracle in the oracle leg,
+    ``batch_errors``)."""
     from paper_2310_08439_gb300 import inputs as I
     w = I.batch()
     n_tot = int(sum(x.n for x in w.systems))
@@ -253,9 +253,8 @@ def batch_measure(tmd, torch, steps=5):
     out = {"workload": "512 periodic systems, n ~ logU(32, 8192) (total %d atoms), fcc/bcc/hcp a ~ U(2.9, 4.1), "
                        "1-3 species, rc 6, K 16, network 192-128-128-1" % n_tot}
     m = tmd.Model(w.model)
-    b = tmd.Batch(w.systems)
-    rng = np.random.default_rng(0)
-    sample = [int(k) for k in rng.permutation(len(w.systems)) if w.systems[k].n <= 1500][:8]
+    b = tmd.Batch(w.systems, skin=1.0)   # resident tables, built once (the positions do not move)
+    sample = ids
     results = {}
     for prec in ("fp32", "bf16"):
         m.set_precision(prec)
@@ -268,29 +267,40 @@ def batch_measure(tmd, torch, steps=5):
         dt = (time.perf_counter() - t0) / steps
         results[prec] = {k: (float(E[k]), b.get_system(k)[2].astype(np.float64)) for k in sample}
         out[prec] = {"atom_evals_per_s": n_tot / dt, "ms_per_batch_eval": dt * 1e3, "tuning": tuning,
-                     "max_dE_rel": None, "max_dF_over_rms": None, "per_system": None}
+                     "errors": None}
     return out, (w, sample, results)
 
 
 def batch_errors(extras_batch, sampled):
-    """Oracle leg: errors of the sampled batch systems against the FP64 oracle."""
+    """Oracle leg: every batch system's energy and force errors against the
+    FP64 oracle, both network forms (per-system lists in system order, and
+    their summary)."""
     from oracle import oracle as O
     w, sample, results = sampled
     om = O.OracleModel(w.model)
+    t0 = time.perf_counter()
+    rows = {prec: {"dE_rel": [], "dF_max_over_rms": []} for prec in results}
     for k in sample:
         s = w.systems[k]
         o = O.evaluate(om, s.pos, s.types, s.box, s.pbc)
         rms = float(np.sqrt((o["forces"] ** 2).mean()))
         for prec, res in results.items():
             e, f = res[k]
-            row = {"system": k, "n": int(s.n), "dE_rel": abs(e - o["energy"]) / abs(o["energy"]),
-                   "dF_max_over_rms": float(np.abs(f - o["forces"]).max() / rms)}
-            d = extras_batch[prec]
-            d["per_system"] = (d["per_system"] or []) + [row]
-    for prec in results:
-        d = extras_batch[prec]
-        d["max_dE_rel"] = max(r["dE_rel"] for r in d["per_system"])
-        d["max_dF_over_rms"] = max(r["dF_max_over_rms"] for r in d["per_system"])
+            rows[prec]["dE_rel"].append(abs(e - o["energy"]) / abs(o["energy"]))
+            rows[prec]["dF_max_over_rms"].append(float(np.abs(f - o["forces"]).max() / rms))
+    secs = time.perf_counter() - t0
+    for prec, r in rows.items():
+        dE, dF = np.array(r["dE_rel"]), np.array(r["dF_max_over_rms"])
+        extras_batch[prec]["errors"] = {
+            "systems": len(sample), "atoms": int(sum(w.systems[k].n for k in sample)),
+            "max_dE_rel": float(dE.max()), "median_dE_rel": float(np.median(dE)),
+            "max_dF_over_rms": float(dF.max()), "median_dF_over_rms": float(np.median(dF)),
+            "p99_dF_over_rms": float(np.percentile(dF, 99)),
+            "systems_over_1e-5_dF": int((dF > 1e-5).sum()),
+            "per_system": {"n": [int(w.systems[k].n) for k in sample],
+                           "dE_rel": [float("%.3g" % x) for x in dE],
+                           "dF_max_over_rms": [float("%.3g" % x) for x in dF]},
+            "oracle_seconds": secs}
 
 
 def paper_models_measure(tmd, torch, steps=5):
@@ -390,31 +400,70 @@ def graphs_measure(tmd, torch, steps=60):
 
 
 def serving_measure(tmd, seconds, torch):
-    """Serving workload: 256 resident systems, Poisson requests (2,000/s, 1-10
-    MD steps each); continuous batching vs each request alone (plain FP32)."""
+    """Serving workload (configs: serve): 256 systems of 64-50,000 atoms,
+    Poisson requests of 1-10 MD steps on a uniformly chosen system.  Each arm's
+    capacity is measured first (batched: every system stepped in every tick;
+    per request: back-to-back calls), then a load sweep offers 0.25 / 0.5 /
+    0.75 / 0.9 of that capacity over the same arrival window and reports the
+    steady-state p50 / p99 latency; the batched FP32 arm also runs the per
+    request arm's own request streams.  Systems are admitted by device memory
+    (serve.Residency, half of the free memory) with resident tables (1 A skin,
+    rebuilt every 5 steps or on the skin criterion)."""
     from paper_2310_08439_gb300 import inputs as I
     from paper_2310_08439_gb300 import serve
     w = I.serve()
+    systems = w.systems
     free, _ = torch.cuda.mem_get_info()
-    ids, used = serve.admit(w.systems, w.model, int(0.5 * free))
-    systems = [w.systems[k] for k in ids]
+    per = serve.bytes_per_atom(w.model)
+    need = [int(x.n) * per for x in systems]
+    budget = int(0.5 * free)
     m = tmd.Model(w.model)
-    res = {"workload": "%d resident systems (%d atoms, 64-50,000 each, fcc/bcc, 1-2 species), Poisson 2,000 "
-                       "requests/s, 1-10 MD steps each, network 128-128-1" % (len(systems), sum(x.n for x in systems)),
-           "admitted": len(ids), "admission_bytes": used}
-    for prec in ("fp32", "bf16"):
+    mean_work = float(np.mean([x.n for x in systems])) * 5.5          # atom-steps per request
+    fracs = (0.25, 0.5, 0.75, 0.9)
+    res = {"workload": "%d systems (%d atoms, 64-50,000 each, fcc/bcc, 1-2 species), Poisson requests of "
+                       "U{1..10} MD steps, network 128-128-1; arrival window %.2f s per load point"
+                       % (len(systems), sum(x.n for x in systems), seconds),
+           "budget_bytes": budget, "estimated_bytes_all": int(sum(need)), "mean_atom_steps_per_request": mean_work}
+    ids = list(range(len(systems)))
+
+    def batched(prec):
         m.set_precision(prec)
-        b = tmd.Batch(systems)
-        b.step(m, list(range(len(systems))), 1.0, 0)   # initial forces, warm-up
-        reqs = serve.poisson_requests(len(systems), 2000.0, seconds, seed=7)
-        _, st = serve.serve_batched(b, m, reqs)
-        res["batched_" + prec] = st
+        b = tmd.Batch(systems, skin=1.0, rebuild_every=5)
+        b.step(m, ids, 1.0, 1)                      # tables, initial forces, graphs
+        return b
+
+    def sweep(arm, b, cap, seed0, rates=None):
+        pts = []
+        for i, f in enumerate(fracs):
+            rate = (rates[i] if rates else f * cap / mean_work)
+            reqs = serve.poisson_requests(len(systems), rate, seconds, seed=seed0 + i)
+            if arm == "alone":
+                _, st = serve.serve_alone(b, m, reqs)
+            else:
+                _, st = serve.serve_batched(b, m, reqs, residency=serve.Residency(b, need, budget))
+            st.update(offered_fraction=f if not rates else None, rate_per_s=rate,
+                      offered_atom_steps_per_s=rate * mean_work)
+            pts.append(st)
+        return pts
+
+    for prec in ("fp32", "bf16"):
+        b = batched(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ticks = 4
+        b.step(m, ids, 1.0, ticks)
+        cap = ticks * float(sum(x.n for x in systems)) / (time.perf_counter() - t0)
+        res["batched_" + prec] = {"capacity_atom_steps_per_s": cap, "sweep": sweep("batched", b, cap, 100)}
     m.set_precision("fp32")
-    b = tmd.Batch(systems)
-    b.step(m, list(range(len(systems))), 1.0, 0)
-    reqs = serve.poisson_requests(len(systems), 2000.0, min(seconds, 0.25), seed=7)
-    _, st = serve.serve_alone(b, m, reqs)
-    res["per_request_fp32"] = st
+    b = batched("fp32")
+    burst = serve.poisson_requests(len(systems), 1e6, 1e-4 * 60, seed=7)    # ~60 requests at t ~ 0
+    _, st = serve.serve_alone(b, m, burst, realtime=False)
+    cap_alone = st["atom_steps"] / st["wall_s"]
+    alone_pts = sweep("alone", b, cap_alone, 200)
+    res["per_request_fp32"] = {"capacity_atom_steps_per_s": cap_alone, "sweep": alone_pts}
+    b = batched("fp32")
+    res["batched_fp32_at_per_request_loads"] = sweep("batched", b, None, 200,
+                                                     rates=[p["rate_per_s"] for p in alone_pts])
     return res
 
 
@@ -597,7 +646,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reps", type=int, default=64, help="fcc repeats of the large cell (64 = 1,048,576 atoms)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of each serving load point")
     ap.add_argument("--size-sweep", default="",
                     help="instead of the bench line: the FP32 MD step of the large lattice at these fcc repeats "
                          "(e.g. 32,64,128,160), throughput and device memory per size")

@@ -338,13 +338,16 @@ tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
  *  off      dev [n+1] int64 CSR offsets, off[0] = 0, off[n] = nnz.
  *  nbr      dev [nnz] int32 neighbour ids in [0, n).
  *  shift4   dev [nnz][4] int8 (sx, sy, sz, species of j), 4-byte aligned;
- *           the table must hold every pair closer than rc (entries beyond rc
- *           are skipped).
+ *           the species byte must equal types[j]; |s| box < 4096 A on every
+ *           axis; the table must hold every pair closer than rc (entries
+ *           beyond rc are skipped).
  *  pos, types, box, energy, e_atom, forces, virial: as tmd_compute.
  * The first call on a device looks up the array's device address (make that
  * first call before any stream capture).  Each call checks the table and the
- * species on the device and synchronises the stream once to read the verdict
- * (TMD_ERR_INVALID_ARG on a bad table).  Every call shares the one array and
+ * species on the device and synchronises the stream once, before any force
+ * kernel runs, to read the verdict (TMD_ERR_INVALID_ARG on a bad table).  It
+ * runs the SIMT force pass even when tmd_set_force_kernel chose the
+ * tensor-core one (that pass reads a pair cache this call does not keep).  Every call shares the one array and
  * clears what must start at zero; calls that overlap on the GPU (several
  * streams or threads at once) race on it and must be serialised by the caller.
  */
@@ -441,10 +444,17 @@ tmd_status tmd_step_host(const tmd_model *model, tmd_system *sys, double *pos_ho
  * or advanced by one set of launches: the cell list, neighbour table, pair
  * kernels and network run over the atoms of the listed systems only, each atom
  * using its own system's box, and energies / virials are reduced per system in
- * FP64.  The neighbour tables of the listed systems are rebuilt (r_list = rc)
- * on every evaluation.  Each system's energy, forces and virial are those of
- * tmd_compute on that system alone (the method is per system; Sec. "The
- * Tensor Formalism").
+ * FP64.  Each system's energy, forces and virial are those of tmd_compute on
+ * that system alone (the method is per system; Sec. "The Tensor Formalism").
+ *
+ * Neighbour tables stay resident between calls, one region of a shared entry
+ * pool per system, built with r_list = rc + skin (tmd_batch_set_skin; skin 0,
+ * the default, rebuilds the listed systems' tables on every evaluation).  A
+ * system's table is rebuilt, alone or with the others due at the same step,
+ * when it has none, on the cadence of rebuild_every steps, or when one of its
+ * atoms moved more than skin / 2 since the build (the MD setting of Sec.
+ * "Evaluation": binning with a 1 A buffer, rebuilt every 5 steps), as
+ * tmd_step does for one system.  Positions are wrapped at each rebuild only.
  */
 typedef struct tmd_batch tmd_batch;
 
@@ -469,11 +479,30 @@ tmd_status tmd_batch_get_system(const tmd_batch *batch, int32_t sys, double *pos
 tmd_status tmd_batch_compute(const tmd_model *model, tmd_batch *batch, const int32_t *systems, int32_t n_active,
                              double *energy, double *virial, tmd_stream_t stream);
 /* Advance the listed systems by nsteps velocity-Verlet steps of dt_fs (as
- * tmd_step, neighbour tables rebuilt every step); thermo host [n_active]
- * (may be NULL) receives each system's state after the last step.  Systems
- * evaluated for the first time get their initial forces first. */
+ * tmd_step, with the batch's table policy; the skin criterion reads one flag
+ * per system back once per step); thermo host [n_active] (may be NULL)
+ * receives each system's state after the last step (rebuilds = that system's
+ * table builds since tmd_batch_set_system).  Systems evaluated for the first
+ * time get their initial forces first. */
 tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *batch, const int32_t *systems, int32_t n_active,
                           double dt_fs, int32_t nsteps, tmd_thermo *thermo, tmd_stream_t stream);
+
+/* Table policy (no counterpart in the paper beyond its 1 A buffer and
+ * 5-step cadence): skin >= 0 A added to rc for the tables, rebuild_every >= 0
+ * steps (0 = the skin criterion only).  A new skin invalidates every table.
+ * Errors: INVALID_ARG. */
+tmd_status tmd_batch_set_skin(tmd_batch *batch, double skin, int32_t rebuild_every);
+/* Give back system sys's table region (its pool entries are reused by the
+ * next system that needs one); the system keeps its state and builds a new
+ * table when it is next listed.  For servers that admit systems by device
+ * memory: an idle system releases its table so that another can be admitted.
+ * Errors: INVALID_ARG. */
+tmd_status tmd_batch_release(tmd_batch *batch, int32_t sys);
+/* Host outputs (NULL skips): entries of system sys's region (0 = none), of
+ * the whole pool (its device memory is 8 B per entry for the table plus 24 B
+ * for the in-cutoff pair cache), and the system's table builds. */
+tmd_status tmd_batch_table_info(const tmd_batch *batch, int32_t sys, int64_t *region_entries,
+                                int64_t *pool_entries, int64_t *rebuilds);
 
 /*
  * Autotuner for batched evaluations: builds the tables of the listed systems

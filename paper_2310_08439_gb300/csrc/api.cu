@@ -207,18 +207,95 @@ __global__ void k_inv_mass(const double *__restrict__ mass, double *__restrict__
     if (i < n) inv[i] = 1.0 / mass[i];
 }
 
-// velocity-Verlet halves and wrap for the atoms of the active systems of a batch
+// velocity-Verlet halves and wrap for the atoms of the active systems of a
+// batch.  The first half kick and drift also run each system's skin check:
+// an atom that moved more than skin/2 since its system's last table build
+// sets moved[system] (lim2 = (skin/2)^2; no check when moved is null).
 __global__ void k_vv_first_b(double *__restrict__ pos, double *__restrict__ vel, const float *__restrict__ F,
                              const double *__restrict__ inv_mass, int64_t n, double dt,
-                             const int32_t *__restrict__ sys_of, const uint8_t *__restrict__ active) {
+                             const int32_t *__restrict__ sys_of, const uint8_t *__restrict__ active,
+                             const double *__restrict__ pos_ref, double lim2, int32_t *__restrict__ moved) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !active[sys_of[i]]) return;
+    if (i >= n) return;
+    const int sys = sys_of[i];
+    if (!active[sys]) return;
     const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
+    double d2 = 0.0;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         const double v = vel[3 * i + x] + h * (double)F[3 * i + x];
+        const double p = pos[3 * i + x] + dt * v;
         vel[3 * i + x] = v;
-        pos[3 * i + x] += dt * v;
+        pos[3 * i + x] = p;
+        if (moved) {
+            const double d = p - pos_ref[3 * i + x];
+            d2 += d * d;
+        }
+    }
+    if (moved && d2 > lim2) atomicOr(&moved[sys], 1);
+}
+
+// pos_ref = pos for the atoms of the flagged systems (after their rebuild)
+__global__ void k_copy_ref_b(const double *__restrict__ pos, double *__restrict__ pos_ref, int64_t n,
+                             const int32_t *__restrict__ sys_of, const uint8_t *__restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[sys_of[i]]) return;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) pos_ref[3 * i + x] = pos[3 * i + x];
+}
+
+// The evaluation order of the active atoms: grouped by species, within a
+// species by system (in the order of the active list) and atom index.
+// rank[i] = the index of atom i among the atoms of its species in its system;
+// pbase[sys * MAX_SPECIES + t] = the first perm position of that block.
+__global__ void k_eval_perm(int64_t n, const int32_t *__restrict__ sys_of, const uint8_t *__restrict__ active,
+                            const int32_t *__restrict__ types, const int32_t *__restrict__ rank,
+                            const int64_t *__restrict__ pbase, int32_t *__restrict__ perm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int sys = sys_of[i];
+    if (!active[sys]) return;
+    perm[pbase[(int64_t)sys * TMD_MAX_SPECIES + types[i]] + rank[i]] = (int32_t)i;
+}
+
+// Move the segments of a fresh build (scratch table, the atoms in sperm) into
+// the resident table: each system's entries go to its own region of the pool
+// (region[2 sys] = first entry, region[2 sys + 1] = capacity), reserved per
+// atom from fill[sys].  A region too small for its system's entries gets
+// empty segments and overflow = 1; fill then holds the entries it needed.
+// One warp per atom.
+__global__ void k_region_copy(const int64_t *__restrict__ sbeg, const int64_t *__restrict__ send,
+                              const int32_t *__restrict__ snbr, const char4 *__restrict__ sshift,
+                              const int32_t *__restrict__ sperm, int64_t nr, const int32_t *__restrict__ sys_of,
+                              const int64_t *__restrict__ region, unsigned long long *__restrict__ fill,
+                              int64_t *__restrict__ beg, int64_t *__restrict__ end, int32_t *__restrict__ nbr,
+                              char4 *__restrict__ shift, int32_t *__restrict__ overflow) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < nr; p += nw) {
+        const int i = sperm[p];
+        const int sys = sys_of[i];
+        const int64_t b0 = sbeg[i], len = send[i] - b0;
+        unsigned long long off = 0;
+        if (lane == 0) off = atomicAdd(&fill[sys], (unsigned long long)len);
+        off = __shfl_sync(0xffffffffu, off, 0);
+        const int64_t base = region[2 * sys], cap = region[2 * sys + 1];
+        if ((int64_t)off + len > cap) {
+            if (lane == 0) {
+                beg[i] = end[i] = base;
+                atomicOr(overflow, 1);
+            }
+            continue;
+        }
+        const int64_t d0 = base + (int64_t)off;
+        for (int64_t c = lane; c < len; c += 32) {
+            nbr[d0 + c] = snbr[b0 + c];
+            shift[d0 + c] = sshift[b0 + c];
+        }
+        if (lane == 0) {
+            beg[i] = d0;
+            end[i] = d0 + len;
+        }
     }
 }
 
@@ -1071,7 +1148,30 @@ struct tmd_batch {
     uint8_t *h_flags = nullptr;      // pinned staging of the flags
     std::vector<uint8_t> has_forces;
     std::vector<int64_t> steps;
-    tmd_nlist nl;
+    // resident neighbour tables: every system's segments live in its own
+    // region of one entry pool (pool.nbr / pool.shift, capacity pool_cap),
+    // kept between calls and rebuilt per system
+    double skin = 0.0;               // tables hold pairs within rc + skin
+    int32_t rebuild_every = 0;       // cadence (0: the skin criterion only)
+    tmd_nlist pool;                  // resident tables; perm = evaluation order of the active atoms
+    tmd_nlist scratch;               // one build of the systems being rebuilt
+    int64_t pool_cap = 0, pool_used = 0;
+    std::vector<int64_t> rbase, rcap;                // region of each system (rcap 0: none)
+    std::vector<std::pair<int64_t, int64_t>> holes;  // released regions (base, capacity)
+    std::vector<uint8_t> built;      // table valid for the positions since its build
+    std::vector<int64_t> rebuilds;
+    std::vector<int64_t> species;    // [S][MAX_SPECIES] atoms per species
+    double *pos_ref = nullptr;       // [n][3] positions at each system's last build
+    int32_t *rank = nullptr;         // [n] index of an atom among its system's atoms of its species
+    int32_t *d_moved = nullptr;      // [S] skin check
+    int32_t *h_moved = nullptr;      // pinned mirror
+    int64_t *d_region = nullptr;     // [S][2] region base, capacity
+    unsigned long long *d_fill = nullptr;  // [S] entries placed per region
+    int32_t *d_overflow = nullptr;
+    unsigned long long *h_fill = nullptr;  // pinned: fill [S] then overflow
+    int64_t *d_pbase = nullptr;      // [S][MAX_SPECIES] evaluation order blocks
+    std::vector<int64_t> h_pbase;
+    uint8_t *d_rflags = nullptr;     // [S] systems being rebuilt
     tmd::GraphCache g_eval, g_step;   // captured evaluation / evaluation + second half kick
 };
 
@@ -1079,18 +1179,26 @@ namespace {
 
 tmd_status batch_params(tmd_batch *b, double r_list) {
     if (b->r_list == r_list && !b->sp.empty()) return TMD_OK;
-    b->sp.resize(b->S);
-    b->cell_off.resize(b->S);
+    std::vector<tmd::SysParams> sp(b->S);
+    std::vector<int32_t> cell_off(b->S);
     int64_t total = 0;
     for (int k = 0; k < b->S; ++k) {
         int64_t nc = 0;
-        tmd_status st = tmd::make_sys_params(&b->box[3 * k], &b->pbc[3 * k], r_list, &b->sp[k], &nc);
+        tmd_status st = tmd::make_sys_params(&b->box[3 * k], &b->pbc[3 * k], r_list, &sp[k], &nc);
         if (st != TMD_OK) return st;
-        b->sp[k].cell_off = (int)total;
+        sp[k].cell_off = (int)total;
         total += nc;
     }
+    b->sp.swap(sp);
+    b->cell_off.swap(cell_off);
     b->ncell = total;
+    // a new list radius invalidates every resident table
+    if (b->r_list != r_list)
+        for (int k = 0; k < b->S; ++k) b->built[k] = 0;
     b->r_list = r_list;
+    tmd_status st;
+    if ((st = tmd::grow(&b->pool.sp, &b->pool.cap_sp, b->S)) != TMD_OK) return st;
+    TMD_CUDA(cudaMemcpy(b->pool.sp, b->sp.data(), sizeof(tmd::SysParams) * b->S, cudaMemcpyHostToDevice));
     return TMD_OK;
 }
 
@@ -1114,25 +1222,175 @@ tmd_status batch_activate(tmd_batch *b, const int32_t *systems, int32_t n_act, c
     return TMD_OK;
 }
 
-// wrap and rebuild the tables of the active systems (flags already set)
-tmd_status batch_prepare(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
+// ---- entry pool: one region per system, first fit over released regions
+void region_free(tmd_batch *b, int k) {
+    if (b->rcap[k] > 0) b->holes.push_back({b->rbase[k], b->rcap[k]});
+    b->rbase[k] = 0;
+    b->rcap[k] = 0;
+    b->built[k] = 0;
+}
+
+tmd_status region_alloc(tmd_batch *b, int k, int64_t want, cudaStream_t s) {
+    for (size_t h = 0; h < b->holes.size(); ++h)
+        if (b->holes[h].second >= want) {
+            b->rbase[k] = b->holes[h].first;
+            b->rcap[k] = want;
+            if (b->holes[h].second == want) b->holes.erase(b->holes.begin() + h);
+            else b->holes[h] = {b->holes[h].first + want, b->holes[h].second - want};
+            return TMD_OK;
+        }
+    if (b->pool_used + want > b->pool_cap) {
+        // a larger pool keeps every region where it is (same entry offsets)
+        const int64_t cap = std::max<int64_t>(b->pool_used + want, b->pool_cap + b->pool_cap / 2);
+        int32_t *nbr = nullptr;
+        char4 *sh = nullptr;
+        cudaError_t e = cudaMalloc(&nbr, sizeof(int32_t) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&sh, sizeof(char4) * cap);
+        if (e != cudaSuccess) {
+            if (nbr) cudaFree(nbr);
+            cudaGetLastError();
+            tmd::set_error("neighbour table pool of %lld entries: %s", (long long)cap, cudaGetErrorString(e));
+            return TMD_ERR_OOM;
+        }
+        if (b->pool_used > 0) {
+            TMD_CUDA(cudaMemcpyAsync(nbr, b->pool.nbr, sizeof(int32_t) * b->pool_used, cudaMemcpyDeviceToDevice, s));
+            TMD_CUDA(cudaMemcpyAsync(sh, b->pool.shift, sizeof(char4) * b->pool_used, cudaMemcpyDeviceToDevice, s));
+            TMD_CUDA(cudaStreamSynchronize(s));
+        }
+        if (b->pool.nbr) cudaFree(b->pool.nbr);
+        if (b->pool.shift) cudaFree(b->pool.shift);
+        b->pool.nbr = nbr;
+        b->pool.shift = sh;
+        b->pool.cap_nnz = b->pool.cap_shift = cap;
+        b->pool_cap = cap;
+        b->pool.nnz = cap;   // sizes the pair cache: one slot per pool entry
+    }
+    b->rbase[k] = b->pool_used;
+    b->rcap[k] = want;
+    b->pool_used += want;
+    return TMD_OK;
+}
+
+// entries of system k from the uniform-density estimate, with headroom
+int64_t region_estimate(const tmd_batch *b, int k, double r_list) {
+    const double nk = (double)(b->off[k + 1] - b->off[k]);
+    const double vol = b->box[3 * k] * b->box[3 * k + 1] * b->box[3 * k + 2];
+    return (int64_t)(1.3 * nk * (nk / vol) * (4.0 / 3.0) * M_PI * r_list * r_list * r_list) + 64;
+}
+
+// Wrap and rebuild the tables of the systems flagged in rflags (host [S]):
+// one build over their atoms (r_list = rc + skin) into the scratch table,
+// whose segments then move to the systems' regions of the pool.
+tmd_status batch_rebuild(const tmd_model *model, tmd_batch *b, const std::vector<uint8_t> &rflags, cudaStream_t s) {
     tmd_status st;
-    if ((st = batch_params(b, (double)model->dm.rc)) != TMD_OK) return st;
-    // the device copy of the parameters is made by build_tables; wrapping reads it
+    const double r_list = (double)model->dm.rc + b->skin;
+    if ((st = batch_params(b, r_list)) != TMD_OK) return st;
+    std::vector<int64_t> nsys(b->S, 0);
+    int64_t nr = 0;
+    for (int k = 0; k < b->S; ++k)
+        if (rflags[k]) {
+            nsys[k] = b->off[k + 1] - b->off[k];
+            nr += nsys[k];
+        }
+    if (nr == 0) return TMD_OK;
+    std::memcpy(b->h_flags, rflags.data(), b->S);
+    TMD_CUDA(cudaMemcpyAsync(b->d_rflags, b->h_flags, b->S, cudaMemcpyHostToDevice, s));
     const unsigned nb = (unsigned)((b->n + 255) / 256);
-    std::vector<int64_t> nsys(b->S);
-    for (int k = 0; k < b->S; ++k) nsys[k] = b->h_flags[k] ? b->off[k + 1] - b->off[k] : 0;
-    if ((st = tmd::grow(&b->nl.sp, &b->nl.cap_sp, b->S)) != TMD_OK) return st;
-    TMD_CUDA(cudaMemcpyAsync(b->nl.sp, b->sp.data(), sizeof(tmd::SysParams) * b->S, cudaMemcpyHostToDevice, s));
-    TMD_LAUNCH("k_wrap_b", s, k_wrap_b<<<nb, 256, 0, s>>>(b->pos, b->n, b->nl.sp, b->sys_of, b->active));
-    (void)n_act;
-    return tmd::build_tables(b->pos, b->types, b->n, b->S, b->sp.data(), b->sys_of, b->active, nsys.data(), b->ncell,
-                             &b->nl, s);
+    TMD_LAUNCH("k_wrap_b", s, k_wrap_b<<<nb, 256, 0, s>>>(b->pos, b->n, b->pool.sp, b->sys_of, b->d_rflags));
+    if ((st = tmd::build_tables(b->pos, b->types, b->n, b->S, b->sp.data(), b->sys_of, b->d_rflags, nsys.data(),
+                                b->ncell, &b->scratch, s)) != TMD_OK)
+        return st;
+    // per-atom segment bounds of the pool cover every atom of the batch
+    if ((st = tmd::grow(&b->pool.beg, &b->pool.cap_beg, b->n)) != TMD_OK) return st;
+    if ((st = tmd::grow(&b->pool.end, &b->pool.cap_end, b->n)) != TMD_OK) return st;
+    for (int k = 0; k < b->S; ++k)
+        if (rflags[k] && b->rcap[k] == 0 && (st = region_alloc(b, k, region_estimate(b, k, r_list), s)) != TMD_OK)
+            return st;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        std::vector<int64_t> reg(2 * (size_t)b->S);
+        for (int k = 0; k < b->S; ++k) {
+            reg[2 * k] = b->rbase[k];
+            reg[2 * k + 1] = b->rcap[k];
+        }
+        TMD_CUDA(cudaMemcpyAsync(b->d_region, reg.data(), sizeof(int64_t) * 2 * b->S, cudaMemcpyHostToDevice, s));
+        TMD_CUDA(cudaMemsetAsync(b->d_fill, 0, sizeof(unsigned long long) * b->S, s));
+        TMD_CUDA(cudaMemsetAsync(b->d_overflow, 0, sizeof(int32_t), s));
+        const unsigned cb = (unsigned)std::min<int64_t>((nr + 7) / 8, 65535);
+        TMD_LAUNCH("k_region_copy", s, k_region_copy<<<cb, 256, 0, s>>>(
+                                           b->scratch.beg, b->scratch.end, b->scratch.nbr, b->scratch.shift,
+                                           b->scratch.perm, nr, b->sys_of, b->d_region, b->d_fill, b->pool.beg,
+                                           b->pool.end, b->pool.nbr, b->pool.shift, b->d_overflow));
+        TMD_CUDA(cudaGetLastError());
+        TMD_CUDA(cudaMemcpyAsync(b->h_fill, b->d_fill, sizeof(unsigned long long) * b->S, cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaMemcpyAsync(b->h_fill + b->S, b->d_overflow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaStreamSynchronize(s));
+        int32_t over = 0;
+        std::memcpy(&over, b->h_fill + b->S, sizeof(int32_t));
+        if (!over) break;
+        if (attempt == 2) {
+            tmd::set_error("neighbour table regions still too small after resizing");
+            return TMD_ERR_CAPACITY;
+        }
+        // a region too small for its system: a new one with headroom
+        for (int k = 0; k < b->S; ++k)
+            if (rflags[k] && (int64_t)b->h_fill[k] > b->rcap[k]) {
+                const int64_t want = (int64_t)b->h_fill[k] + (int64_t)b->h_fill[k] / 4 + 64;
+                region_free(b, k);
+                if ((st = region_alloc(b, k, want, s)) != TMD_OK) return st;
+            }
+    }
+    TMD_LAUNCH("k_copy_ref_b", s, k_copy_ref_b<<<nb, 256, 0, s>>>(b->pos, b->pos_ref, b->n, b->sys_of, b->d_rflags));
+    TMD_CUDA(cudaGetLastError());
+    for (int k = 0; k < b->S; ++k)
+        if (rflags[k]) {
+            b->built[k] = 1;
+            b->rebuilds[k]++;
+        }
+    b->pool.r_list = r_list;
+    b->pool.built = 1;
+    return TMD_OK;
+}
+
+// evaluation order of the active atoms (flags already on the device)
+tmd_status batch_order(tmd_batch *b, int32_t n_act, cudaStream_t s) {
+    tmd_status st;
+    int64_t run = 0;
+    for (int t = 0; t < TMD_MAX_SPECIES; ++t) {
+        int64_t c = 0;
+        for (int k = 0; k < n_act; ++k) {
+            const int sys = b->h_act[k];
+            b->h_pbase[(size_t)sys * TMD_MAX_SPECIES + t] = run + c;
+            c += b->species[(size_t)sys * TMD_MAX_SPECIES + t];
+        }
+        b->pool.type_count[t] = (int32_t)c;
+        run += c;
+    }
+    b->pool.n_active = run;
+    if ((st = tmd::grow(&b->pool.perm, &b->pool.cap_perm, std::max<int64_t>(run, 1))) != TMD_OK) return st;
+    TMD_CUDA(cudaMemcpyAsync(b->d_pbase, b->h_pbase.data(), sizeof(int64_t) * TMD_MAX_SPECIES * b->S,
+                             cudaMemcpyHostToDevice, s));
+    const unsigned nb = (unsigned)((b->n + 255) / 256);
+    TMD_LAUNCH("k_eval_perm", s, k_eval_perm<<<nb, 256, 0, s>>>(b->n, b->sys_of, b->active, b->types, b->rank,
+                                                                b->d_pbase, b->pool.perm));
+    TMD_CUDA(cudaGetLastError());
+    // the pageable h_pbase is read by the copy above before it is rewritten
+    TMD_CUDA(cudaStreamSynchronize(s));
+    return TMD_OK;
+}
+
+// tables for the active systems that have none (or all of them without a skin)
+tmd_status batch_prepare(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s, bool all) {
+    std::vector<uint8_t> rf(b->S, 0);
+    for (int k = 0; k < n_act; ++k) {
+        const int sys = b->h_act[k];
+        if (all || b->skin <= 0.0 || !b->built[sys] || b->r_list != (double)model->dm.rc + b->skin) rf[sys] = 1;
+    }
+    return batch_rebuild(model, b, rf, s);
 }
 
 void batch_key(const tmd_model *model, const tmd_batch *b, int32_t n_act, std::vector<uintptr_t> &key) {
     model_key(model, key);
-    nlist_key(b->nl, key);
+    nlist_key(b->pool, key);
     const void *bp[] = {b->pos, b->vel, b->mass, b->inv_mass, b->types, b->sys_of, b->forces, b->e_atom, b->w_atom,
                         b->d_off, b->active, b->act_list, b->sys_out};
     for (const void *q : bp) key.push_back((uintptr_t)q);
@@ -1143,19 +1401,20 @@ void batch_key(const tmd_model *model, const tmd_batch *b, int32_t n_act, std::v
 // evaluate the active systems on their current tables (captured graph when repeated)
 tmd_status batch_compute_only(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
     tmd_status st;
-    if ((st = tmd::reserve_compute(model->dm, &b->nl, b->n, b->nl.n_active)) != TMD_OK) return st;
+    if ((st = tmd::reserve_compute(model->dm, &b->pool, b->n, b->pool.n_active)) != TMD_OK) return st;
     std::vector<uintptr_t> key;
     batch_key(model, b, n_act, key);
     return graphed(b->g_eval, key, s, [&]() {
-        return tmd::run_compute_batch(model, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom,
+        return tmd::run_compute_batch(model, &b->pool, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom,
                                       b->w_atom, b->act_list, n_act, b->d_off, b->vel, b->mass, b->sys_out, s);
     });
 }
 
-// wrap, rebuild and evaluate the active systems (flags already set)
+// tables where needed, evaluation order, evaluation (flags already set)
 tmd_status batch_eval(const tmd_model *model, tmd_batch *b, int32_t n_act, cudaStream_t s) {
     tmd_status st;
-    if ((st = batch_prepare(model, b, n_act, s)) != TMD_OK) return st;
+    if ((st = batch_prepare(model, b, n_act, s, false)) != TMD_OK) return st;
+    if ((st = batch_order(b, n_act, s)) != TMD_OK) return st;
     return batch_compute_only(model, b, n_act, s);
 }
 
@@ -1181,7 +1440,7 @@ void batch_results(tmd_batch *b, int32_t n_act, double *energy, double *virial, 
                 th.pressure[t] = (mvv[t] * conv + r[1 + t]) / V;
             }
             th.step = b->steps[sys];
-            th.rebuilds = b->steps[sys];
+            th.rebuilds = b->rebuilds[sys];
         }
     }
 }
@@ -1211,6 +1470,12 @@ tmd_status tmd_batch_create(int32_t n_systems, const int64_t *n_atoms, const dou
     if (b->n >= (int64_t(1) << 28)) { delete b; set_error("too many atoms in the batch"); return TMD_ERR_INVALID_ARG; }
     b->has_forces.assign(n_systems, 0);
     b->steps.assign(n_systems, 0);
+    b->built.assign(n_systems, 0);
+    b->rebuilds.assign(n_systems, 0);
+    b->rbase.assign(n_systems, 0);
+    b->rcap.assign(n_systems, 0);
+    b->species.assign((size_t)n_systems * TMD_MAX_SPECIES, 0);
+    b->h_pbase.assign((size_t)n_systems * TMD_MAX_SPECIES, 0);
     const int64_t n = b->n;
     cudaError_t e = cudaMalloc(&b->pos, sizeof(double) * 3 * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->vel, sizeof(double) * 3 * n);
@@ -1225,11 +1490,23 @@ tmd_status tmd_batch_create(int32_t n_systems, const int64_t *n_atoms, const dou
     if (e == cudaSuccess) e = cudaMalloc(&b->active, n_systems);
     if (e == cudaSuccess) e = cudaMalloc(&b->act_list, sizeof(int32_t) * n_systems);
     if (e == cudaSuccess) e = cudaMalloc(&b->sys_out, sizeof(double) * 16 * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->pos_ref, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->rank, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_moved, sizeof(int32_t) * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_region, sizeof(int64_t) * 2 * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_fill, sizeof(unsigned long long) * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_overflow, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_pbase, sizeof(int64_t) * TMD_MAX_SPECIES * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rflags, n_systems);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, sizeof(double) * 16 * n_systems);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_act, sizeof(int32_t) * n_systems);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_flags, n_systems);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_moved, sizeof(int32_t) * n_systems);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_fill, sizeof(unsigned long long) * (n_systems + 1));
     if (e == cudaSuccess) e = cudaMemset(b->vel, 0, sizeof(double) * 3 * n);
     if (e == cudaSuccess) e = cudaMemset(b->forces, 0, sizeof(float) * 3 * n);
+    if (e == cudaSuccess) e = cudaMemset(b->types, 0, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMemset(b->rank, 0, sizeof(int32_t) * n);
     if (e == cudaSuccess) {
         std::vector<int32_t> so((size_t)n);
         for (int k = 0; k < n_systems; ++k)
@@ -1243,6 +1520,8 @@ tmd_status tmd_batch_create(int32_t n_systems, const int64_t *n_atoms, const dou
         set_error("batch allocation: %s", cudaGetErrorString(e));
         return TMD_ERR_OOM;
     }
+    for (int k = 0; k < n_systems; ++k)   // until set_system: every atom species 0
+        b->species[(size_t)k * TMD_MAX_SPECIES] = b->off[k + 1] - b->off[k];
     *out = b;
     return TMD_OK;
 }
@@ -1250,13 +1529,15 @@ tmd_status tmd_batch_create(int32_t n_systems, const int64_t *n_atoms, const dou
 tmd_status tmd_batch_destroy(tmd_batch *b) {
     if (!b) return TMD_OK;
     void *p[] = {b->pos, b->vel, b->mass, b->inv_mass, b->types, b->sys_of, b->forces, b->e_atom, b->w_atom,
-                 b->d_off, b->active, b->act_list, b->sys_out};
+                 b->d_off, b->active, b->act_list, b->sys_out, b->pos_ref, b->rank, b->d_moved, b->d_region,
+                 b->d_fill, b->d_overflow, b->d_pbase, b->d_rflags};
     for (void *q : p)
         if (q) cudaFree(q);
-    if (b->h_out) cudaFreeHost(b->h_out);
-    if (b->h_act) cudaFreeHost(b->h_act);
-    if (b->h_flags) cudaFreeHost(b->h_flags);
-    nlist_free(&b->nl);
+    void *hp[] = {b->h_out, b->h_act, b->h_flags, b->h_moved, b->h_fill};
+    for (void *q : hp)
+        if (q) cudaFreeHost(q);
+    nlist_free(&b->pool);
+    nlist_free(&b->scratch);
     delete b;
     return TMD_OK;
 }
@@ -1269,16 +1550,30 @@ tmd_status tmd_batch_set_system(tmd_batch *b, int32_t sys, const double *pos, co
     const int64_t o = b->off[sys], n = b->off[sys + 1] - o;
     for (int64_t i = 0; i < n; ++i)
         if (!(masses[i] > 0.0 && std::isfinite(masses[i]))) { set_error("mass[%lld] must be > 0", (long long)i); return TMD_ERR_INVALID_ARG; }
+    // per-species counts and each atom's rank among its species (evaluation order)
+    std::vector<int32_t> rank((size_t)n);
+    int64_t cnt[TMD_MAX_SPECIES] = {0, 0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        if (types[i] < 0 || types[i] >= TMD_MAX_SPECIES) {
+            set_error("types[%lld] = %d outside [0, %d)", (long long)i, types[i], TMD_MAX_SPECIES);
+            return TMD_ERR_INVALID_ARG;
+        }
+        rank[i] = (int32_t)cnt[types[i]]++;
+    }
     TMD_CUDA(cudaMemcpyAsync(b->pos + 3 * o, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
     TMD_CUDA(cudaMemcpyAsync(b->types + o, types, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     TMD_CUDA(cudaMemcpyAsync(b->mass + o, masses, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    TMD_CUDA(cudaMemcpyAsync(b->rank + o, rank.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     if (vel) TMD_CUDA(cudaMemcpyAsync(b->vel + 3 * o, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
     else TMD_CUDA(cudaMemsetAsync(b->vel + 3 * o, 0, sizeof(double) * 3 * n, s));
     TMD_LAUNCH("k_inv_mass", s, k_inv_mass<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b->mass + o, b->inv_mass + o, n));
     TMD_CUDA(cudaGetLastError());
     TMD_CUDA(cudaStreamSynchronize(s));  // host arrays may be pageable and reused
+    for (int t = 0; t < TMD_MAX_SPECIES; ++t) b->species[(size_t)sys * TMD_MAX_SPECIES + t] = cnt[t];
     b->has_forces[sys] = 0;
     b->steps[sys] = 0;
+    b->rebuilds[sys] = 0;
+    b->built[sys] = 0;   // new positions: the table is built again (in its region) before use
     return TMD_OK;
 }
 
@@ -1291,6 +1586,35 @@ tmd_status tmd_batch_get_system(const tmd_batch *b, int32_t sys, double *pos, do
     if (vel) TMD_CUDA(cudaMemcpyAsync(vel, b->vel + 3 * o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
     if (forces) TMD_CUDA(cudaMemcpyAsync(forces, b->forces + 3 * o, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
     TMD_CUDA(cudaStreamSynchronize(s));
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_set_skin(tmd_batch *b, double skin, int32_t rebuild_every) {
+    g_err[0] = 0;
+    if (!b || !(std::isfinite(skin) && skin >= 0.0) || rebuild_every < 0) {
+        set_error("bad arguments: skin must be finite and >= 0, rebuild_every >= 0");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (skin != b->skin)
+        for (int k = 0; k < b->S; ++k) b->built[k] = 0;
+    b->skin = skin;
+    b->rebuild_every = rebuild_every;
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_release(tmd_batch *b, int32_t sys) {
+    g_err[0] = 0;
+    if (!b || sys < 0 || sys >= b->S) { set_error("bad arguments"); return TMD_ERR_INVALID_ARG; }
+    region_free(b, sys);
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_table_info(const tmd_batch *b, int32_t sys, int64_t *region_entries, int64_t *pool_entries,
+                                int64_t *rebuilds) {
+    if (!b || sys < 0 || sys >= b->S) { set_error("bad arguments"); return TMD_ERR_INVALID_ARG; }
+    if (region_entries) *region_entries = b->rcap[sys];
+    if (pool_entries) *pool_entries = b->pool_cap;
+    if (rebuilds) *rebuilds = b->rebuilds[sys];
     return TMD_OK;
 }
 
@@ -1322,23 +1646,50 @@ tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *b, const int32_t *s
     tmd_status st;
     if ((st = batch_activate(b, systems, n_act, s, &na)) != TMD_OK) return st;
     bool need_init = false;
-    for (int k = 0; k < n_act; ++k) need_init = need_init || !b->has_forces[systems[k]];
-    if (need_init) {  // initial forces (the systems that have them are recomputed identically)
-        if ((st = batch_eval(model, b, n_act, s)) != TMD_OK) return st;
+    for (int k = 0; k < n_act; ++k) need_init = need_init || !b->has_forces[systems[k]] || !b->built[systems[k]];
+    if (need_init) {  // initial forces (systems that have them and a table are recomputed identically)
+        std::vector<uint8_t> rf(b->S, 0);
+        for (int k = 0; k < n_act; ++k)
+            if (!b->has_forces[systems[k]] || !b->built[systems[k]]) rf[systems[k]] = 1;
+        if ((st = batch_rebuild(model, b, rf, s)) != TMD_OK) return st;
+        if ((st = batch_order(b, n_act, s)) != TMD_OK) return st;
+        if ((st = batch_compute_only(model, b, n_act, s)) != TMD_OK) return st;
         for (int k = 0; k < n_act; ++k) b->has_forces[systems[k]] = 1;
+    } else if ((st = batch_order(b, n_act, s)) != TMD_OK) {
+        return st;
     }
     const unsigned nb = (unsigned)((b->n + 255) / 256);
+    const bool skin = b->skin > 0.0;
+    const double lim = 0.5 * b->skin;
+    std::vector<uint8_t> rf(b->S);
     for (int it = 0; it < nsteps; ++it) {
-        TMD_LAUNCH("k_vv_first_b", s, k_vv_first_b<<<nb, 256, 0, s>>>(b->pos, b->vel, b->forces, b->inv_mass, b->n, dt_fs,
-                                                                      b->sys_of, b->active));
-        if ((st = batch_prepare(model, b, n_act, s)) != TMD_OK) return st;
+        if (skin) TMD_CUDA(cudaMemsetAsync(b->d_moved, 0, sizeof(int32_t) * b->S, s));
+        TMD_LAUNCH("k_vv_first_b", s, k_vv_first_b<<<nb, 256, 0, s>>>(b->pos, b->vel, b->forces, b->inv_mass, b->n,
+                                                                      dt_fs, b->sys_of, b->active, b->pos_ref,
+                                                                      lim * lim, skin ? b->d_moved : nullptr));
+        TMD_CUDA(cudaGetLastError());
+        for (int k = 0; k < n_act; ++k) b->steps[systems[k]]++;
+        // which tables to rebuild: without a skin every step; else on the
+        // cadence, or when an atom of the system moved more than skin / 2
+        // (the skin criterion, read back once per step)
+        std::fill(rf.begin(), rf.end(), 0);
+        if (skin) {
+            TMD_CUDA(cudaMemcpyAsync(b->h_moved, b->d_moved, sizeof(int32_t) * b->S, cudaMemcpyDeviceToHost, s));
+            TMD_CUDA(cudaStreamSynchronize(s));
+        }
+        for (int k = 0; k < n_act; ++k) {
+            const int sys = systems[k];
+            const bool due = b->rebuild_every > 0 && (b->steps[sys] % b->rebuild_every) == 0;
+            if (!skin || due || b->h_moved[sys] || !b->built[sys]) rf[sys] = 1;
+        }
+        if ((st = batch_rebuild(model, b, rf, s)) != TMD_OK) return st;
         // evaluation and second half kick: one captured graph per table layout
-        if ((st = tmd::reserve_compute(model->dm, &b->nl, b->n, b->nl.n_active)) != TMD_OK) return st;
+        if ((st = tmd::reserve_compute(model->dm, &b->pool, b->n, b->pool.n_active)) != TMD_OK) return st;
         std::vector<uintptr_t> key;
         batch_key(model, b, n_act, key);
         key.push_back(bits_of(dt_fs));
         st = graphed(b->g_step, key, s, [&]() {
-            tmd_status st2 = tmd::run_compute_batch(model, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces,
+            tmd_status st2 = tmd::run_compute_batch(model, &b->pool, b->pos, b->types, b->n, b->sys_of, b->forces,
                                                     b->e_atom, b->w_atom, b->act_list, n_act, b->d_off, b->vel,
                                                     b->mass, b->sys_out, s);
             if (st2 != TMD_OK) return st2;
@@ -1348,7 +1699,6 @@ tmd_status tmd_batch_step(const tmd_model *model, tmd_batch *b, const int32_t *s
             return TMD_OK;
         });
         if (st != TMD_OK) return st;
-        for (int k = 0; k < n_act; ++k) b->steps[systems[k]]++;
     }
     if (thermo || nsteps == 0) {
         // kinetic terms after the second half kick
@@ -1371,7 +1721,7 @@ tmd_status tmd_batch_autotune(tmd_model *m, tmd_batch *b, const int32_t *systems
     if ((st = batch_activate(b, systems, n_act, s, &na)) != TMD_OK) return st;
     if ((st = batch_eval(m, b, n_act, s)) != TMD_OK) return st;   // tables of the listed systems
     return tune_shapes(m, s, best, [&]() {
-        return tmd::run_compute_batch(m, &b->nl, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom, b->w_atom,
+        return tmd::run_compute_batch(m, &b->pool, b->pos, b->types, b->n, b->sys_of, b->forces, b->e_atom, b->w_atom,
                                       b->act_list, n_act, b->d_off, b->vel, b->mass, b->sys_out, s);
     });
 }

@@ -314,14 +314,16 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         return (t < ntile && p < n) ? perm[p] : -1;
     };
     float4 gpre[16];
-    auto load_g0 = [&](int atom_of_my_row) {
+    // G and G' rows are indexed by perm position: row r of tile t is t UM + r
+    auto load_g0 = [&](int atom_of_my_row, int t) {
 #pragma unroll
         for (int it = 0; it < 16; ++it) {
             const int a = __shfl_sync(0xffffffffu, atom_of_my_row, 2 * it + (lane >> 4));
             const int col = 4 * (lane & 15);
             // the null row of a missing atom reads as zeros
             const bool ok = a >= 0 && col < Dd;
-            const float *src = G + (ok ? (size_t)a * Dd + col : 0);
+            const size_t p = (size_t)t * UM + warp * 32 + 2 * it + (lane >> 4);
+            const float *src = G + (ok ? p * Dd + col : 0);
             float4 v;
             // issued here, in program order with the surrounding tensor-core
             // instructions, so that the loads overlap the rest of this tile
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     };
     int nx_atom = row_atom(blockIdx.x);
     int nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
-    load_g0(nx_atom);
+    load_g0(nx_atom, blockIdx.x);
     for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         s_atom[tid] = nx_atom;
         s_type[tid] = nx_type;
@@ -382,7 +384,8 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                                     const int col = c * UKC + 4 * (lane & 15);
                                     gpre[it] = make_float4(0.f, 0.f, 0.f, 0.f);
                                     if (a >= 0 && col < Dd)
-                                        gpre[it] = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + col));
+                                        gpre[it] = __ldg(reinterpret_cast<const float4 *>(
+                                            G + ((size_t)tile * UM + r0 + 2 * it) * Dd + col));
                                 }
                             }
                             if (ause >= 1) mbar_wait(bar_aempty(ast), (ause - 1) & 1, abort);
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                             // gpre is free: (re)start on the next tile's first chunk
                             if (g0_ready) nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
                             g0_ready = false;
-                            load_g0(nx_atom);
+                            load_g0(nx_atom, tile + gridDim.x);
                         }
                         if (tid == 0 && !*abort) {
                             if (!(u.resident && q >= (uint32_t)NST) && mbar_wait(bar_full(st), (q / NST) & 1, abort))
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                             float v[16];
                             tmem_ld16(trow + c0, v);
                             if (my_type == s) {
-                                float4 *o = reinterpret_cast<float4 *>(dG + (size_t)my_atom * Dd + P * Np + c0);
+                                float4 *o = reinterpret_cast<float4 *>(dG + ((size_t)tile * UM + tid) * Dd + P * Np + c0);
 #pragma unroll
                                 for (int e = 0; e < 4; ++e)
                                     o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);

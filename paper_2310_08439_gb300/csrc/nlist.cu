@@ -773,6 +773,7 @@ tmd_status make_sys_params(const double box[3], const int32_t pbc[3], double r_l
         q->ic[x] = nc / box[x];
         q->Lh[x] = (float)box[x];
         q->Ll[x] = (float)(box[x] - (double)q->Lh[x]);
+        grid_split(box[x], q->Gh[x], q->Gl[x]);
         if (pbc[x]) {
             const int lo = -((R + nc - 1) / nc), hi = (nc - 1 + R) / nc;
             smax = std::max(smax, std::max(-lo, hi));
@@ -782,6 +783,11 @@ tmd_status make_sys_params(const double box[3], const int32_t pbc[3], double r_l
     }
     if (smax > 15) {
         set_error("r_list %.3f needs image shifts beyond +-15 boxes", r_list);
+        return TMD_ERR_CAPACITY;
+    }
+    if ((1.0 + smax) * Lmax >= GRID_LIMIT / 2) {
+        set_error("box length %.1f A with image shifts up to %d: the pair geometry needs (1 + |s|) L < %.0f A",
+                  Lmax, smax, GRID_LIMIT / 2);
         return TMD_ERR_CAPACITY;
     }
     q->r2 = r_list * r_list;

@@ -7,10 +7,11 @@
 //                   fly); ScatterSum into forces, virial
 //                                        -- Eqs. dP_abkd, U_abck, F1_abcx, F2_abcx
 //
-// One warp owns one centre atom.  In k_desc, neighbour entries beyond rc are
-// dropped and the survivors are compacted through a per-warp shared-memory
-// queue (and into the pair cache, from which k_force reads them back), so
-// every lane works on an in-cutoff pair.  Each lane computes H and M for one
+// One warp owns one centre atom.  The in-cutoff pairs of each atom come from
+// the pair cache (filled by k_screen in screen.cu, read by both passes) or,
+// without a cache, from screening the table in the pass itself, compacted
+// through a per-warp shared-memory queue; either way every lane works on an
+// in-cutoff pair.  Each lane computes H and M for one
 // neighbour and stages them in shared memory; the warp then accumulates the
 // per-atom P[b][k][d] outer products with each lane owning a (K/8 x 5) block
 // of P in registers.  In k_force each lane owns one cached pair and reads the
@@ -85,21 +86,36 @@ __device__ __forceinline__ void cutoff_fn(float r, float inv_rc, float &fc, floa
     dfc = -0.5f * PI_F * inv_rc * cs;
 }
 
-// H_k = f_k f_c (and dH_k/dr when DERIV) for r < rc.  rad[k] = (mu_hi, mu_lo,
-// eta log2 e, 2 eta); r = r_hi + r_lo so that t = r - mu keeps ~FP64 accuracy
-// (the Gaussians are steep: dlnH/dr = -2 eta t amplifies any rounding of r).
-template <int K, bool DERIV>
-__device__ __forceinline__ void radial(const float4 *rad, float r_hi, float r_lo, float inv_rc, float *H, float *dH) {
-    float fc, dfc;
-    cutoff_fn(r_hi, inv_rc, fc, dfc);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float4 p = rad[k];
-        const float t = (r_hi - p.x) + (r_lo - p.y);
-        const float f = ex2_ftz(-p.z * t * t);
-        H[k] = f * fc;
-        if (DERIV) dH[k] = f * fmaf(-p.w * t, fc, dfc);
+// H_k = f_k f_c (and dH_k/dr when DERIV) for r < rc, two channels at a time
+// on packed FP32x2 arithmetic (fma/add/mul .f32x2 issue two FP32 operations as
+// one instruction, each rounded as its scalar form).  The model's table holds
+// (mu_hi, mu_lo, eta log2 e, 2 eta) per channel; r = r_hi + r_lo so that
+// t = r - mu keeps ~FP64 accuracy (the Gaussians are steep: dlnH/dr = -2 eta t
+// amplifies any rounding of r).  rad2 = the channel pairs of one species pair,
+// two float4 per pair (k, k+1): (-mu_hi, -mu_hi', -mu_lo, -mu_lo') and
+// (-eta log2 e, -eta' log2 e, -2 eta, -2 eta'), written by stage_rad2.
+__device__ __forceinline__ void stage_rad2(float4 *dst, const float4 *src, int n) {
+    for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
+        const float4 a = src[2 * t], b = src[2 * t + 1];
+        dst[2 * t] = make_float4(-a.x, -b.x, -a.y, -b.y);
+        dst[2 * t + 1] = make_float4(-a.z, -b.z, -a.w, -b.w);
     }
+}
+
+struct Radial2 {
+    float2 H, dH;
+};
+
+template <bool DERIV>
+__device__ __forceinline__ Radial2 radial2(const float4 *rad2, int k, float2 rh2, float2 rl2, float2 fc2, float2 dfc2) {
+    const float4 A = rad2[k], B = rad2[k + 1];   // channel pair k / 2
+    const float2 t = __fadd2_rn(__fadd2_rn(rh2, make_float2(A.x, A.y)), __fadd2_rn(rl2, make_float2(A.z, A.w)));
+    const float2 a = __fmul2_rn(__fmul2_rn(make_float2(B.x, B.y), t), t);
+    const float2 f = make_float2(ex2_ftz(a.x), ex2_ftz(a.y));
+    Radial2 o;
+    o.H = __fmul2_rn(f, fc2);
+    if (DERIV) o.dH = __fmul2_rn(f, __ffma2_rn(__fmul2_rn(make_float2(B.z, B.w), t), fc2, dfc2));
+    return o;
 }
 
 // Tabulated radial basis (Sec. "The H_abck tensor and Batch Rational 1D
@@ -166,37 +182,50 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// D = (x_j + s L) - x_i on one axis from hi/lo positions and box length.
-__device__ __forceinline__ void diff_df(float xjh, float xjl, float xih, float xil, int s, float Lh, float Ll,
-                                        float &dh, float &dl) {
-    float u, e1;
-    two_sum(xjh, -xih, u, e1);
-    float lo = (xjl - xil) + e1;
-    if (s != 0) {
-        const float sf = __int_as_float(0x4B400000 + s) - 12582912.0f;  // (float)s, |s| <= 15
-        const float p = sf * Lh;
-        const float pe = fmaf(sf, Lh, -p);  // exact error of the product
-        float v, e2;
-        two_sum(u, p, v, e2);
-        u = v;
-        lo += e2 + fmaf(sf, Ll, pe);
+// The box on the 2^-10 grid split: of the atom's system when batched
+__device__ __forceinline__ void pair_box(const DevNlist &nl, int a, float (&Lh)[3], float (&Ll)[3]) {
+    if (nl.sys_of) {
+        const SysParams &q = nl.sp[nl.sys_of[a]];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) { Lh[x] = q.Gh[x]; Ll[x] = q.Gl[x]; }
+    } else {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) { Lh[x] = nl.Lh[x]; Ll[x] = nl.Ll[x]; }
     }
-    dh = u + lo;
-    dl = lo - (dh - u);
 }
 
-// |D|^2 as hi + lo from hi/lo components (exact products, error-free sums).
-__device__ __forceinline__ void norm2_df(float xh, float xl, float yh, float yl, float zh, float zl, float &r2h,
-                                         float &r2l) {
-    const float px = xh * xh, ex = fmaf(xh, xh, -px);
-    const float py = yh * yh, ey = fmaf(yh, yh, -py);
-    const float pz = zh * zh, ez = fmaf(zh, zh, -pz);
+// Pair geometry on the 2^-10 grid split (grid_split): every position and box
+// length is hi + lo with hi a multiple of 2^-10 A and |lo| <= 2^-11 A.  Then
+// D_hi = (x_j,hi - x_i,hi) + s L_hi is exact in FP32 (a multiple of 2^-10
+// below 2^13 A in magnitude needs at most 23 significand bits; the box
+// checks keep |s| L below 2^13), and D_lo = (x_j,lo - x_i,lo) + s L_lo is a
+// small correction carried to ~1e-10 A.  |D|^2 is formed as an FP32 hi + lo
+// pair from the exact squares of D_hi (FMA residuals, error-free sums) and the
+// cross terms (2 D_hi + D_lo) D_lo, so r^2 keeps ~FP64 accuracy with no FP64
+// instruction.  D itself is returned rounded to FP32.
+__device__ __forceinline__ void pair_geom(const float4 jh, const float4 jl, const float4 ih, const float4 il,
+                                          const char4 sh, const float (&Lh)[3], const float (&Ll)[3], float &dx,
+                                          float &dy, float &dz, float &r2h, float &r2l) {
+    // (float)s from the signed byte with one add and one subtract (|s| < 2^22)
+    const float sx = __int_as_float(0x4B400000 + (int)sh.x) - 12582912.0f;
+    const float sy = __int_as_float(0x4B400000 + (int)sh.y) - 12582912.0f;
+    const float sz = __int_as_float(0x4B400000 + (int)sh.z) - 12582912.0f;
+    const float hx = fmaf(sx, Lh[0], jh.x - ih.x), lx = fmaf(sx, Ll[0], jl.x - il.x);
+    const float hy = fmaf(sy, Lh[1], jh.y - ih.y), ly = fmaf(sy, Ll[1], jl.y - il.y);
+    const float hz = fmaf(sz, Lh[2], jh.z - ih.z), lz = fmaf(sz, Ll[2], jl.z - il.z);
+    const float px = hx * hx, ex = fmaf(hx, hx, -px);
+    const float py = hy * hy, ey = fmaf(hy, hy, -py);
+    const float pz = hz * hz, ez = fmaf(hz, hz, -pz);
     float s1, e1, s2, e2;
     two_sum(px, py, s1, e1);
     two_sum(s1, pz, s2, e2);
-    const float lo = ((ex + ey) + ez) + (e1 + e2) + 2.f * fmaf(xh, xl, fmaf(yh, yl, zh * zl));
+    const float cross = fmaf(fmaf(2.f, hx, lx), lx, fmaf(fmaf(2.f, hy, ly), ly, fmaf(2.f, hz, lz) * lz));
+    const float lo = ((ex + ey) + ez) + (e1 + e2) + cross;
     r2h = s2 + lo;
     r2l = lo - (r2h - s2);
+    dx = hx + lx;
+    dy = hy + ly;
+    dz = hz + lz;
 }
 
 // Walk the entries [beg, end) of atom a, keep pairs with r^2 < rc^2 and hand
@@ -204,18 +233,16 @@ __device__ __forceinline__ void norm2_df(float xh, float xl, float yh, float yl,
 // are formed in double-float FP32 arithmetic from hi/lo positions (no FP64
 // instructions: on this GPU FP64 runs at a small fraction of the FP32 rate).
 // The queue holds (Dx, Dy, Dz, j | b<<28) rounded to FP32 and r^2 as hi/lo.
+// Used when there is no pair cache (k_screen in screen.cu fills the cache
+// with the same pairs, in the same order, by the same arithmetic).
 template <typename F>
 __device__ __forceinline__ int for_pairs(const DevNlist &nl, int a, int64_t beg, int64_t end, float rc2h, float rc2l,
-                                         float4 *q, float2 *q2, int lane, F &&f, bool to_cache = false) {
+                                         float4 *q, float2 *q2, int lane, F &&f) {
     int qn = 0, kept = 0;
     const unsigned lt = (1u << lane) - 1u;
     const float4 ih = nl.ph[a], il = nl.pl[a];
-    float Lh0 = nl.Lh[0], Lh1 = nl.Lh[1], Lh2 = nl.Lh[2], Ll0 = nl.Ll[0], Ll1 = nl.Ll[1], Ll2 = nl.Ll[2];
-    if (nl.sys_of) {  // batched: the box of this atom's system
-        const SysParams &q = nl.sp[nl.sys_of[a]];
-        Lh0 = q.Lh[0]; Lh1 = q.Lh[1]; Lh2 = q.Lh[2];
-        Ll0 = q.Ll[0]; Ll1 = q.Ll[1]; Ll2 = q.Ll[2];
-    }
+    float Lh[3], Ll[3];
+    pair_box(nl, a, Lh, Ll);
     int64_t base = beg;
     while (true) {
         while (qn < 32 && base < end) {
@@ -227,13 +254,10 @@ __device__ __forceinline__ int for_pairs(const DevNlist &nl, int a, int64_t beg,
                 const int j = nl.nbr[c];
                 const char4 s = nl.shift[c];
                 const float4 jh = nl.ph[j], jl = nl.pl[j];
-                float dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l;
-                diff_df(jh.x, jl.x, ih.x, il.x, s.x, Lh0, Ll0, dxh, dxl);
-                diff_df(jh.y, jl.y, ih.y, il.y, s.y, Lh1, Ll1, dyh, dyl);
-                diff_df(jh.z, jl.z, ih.z, il.z, s.z, Lh2, Ll2, dzh, dzl);
-                norm2_df(dxh, dxl, dyh, dyl, dzh, dzl, r2h, r2l);
+                float dx, dy, dz, r2h, r2l;
+                pair_geom(jh, jl, ih, il, s, Lh, Ll, dx, dy, dz, r2h, r2l);
                 v = (r2h < rc2h) || (r2h == rc2h && r2l < rc2l);
-                e = make_float4(dxh, dyh, dzh, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
+                e = make_float4(dx, dy, dz, __uint_as_float((uint32_t)j | ((uint32_t)s.w << 28)));
                 e2 = make_float2(r2h, r2l);
             }
             const unsigned m = __ballot_sync(0xffffffffu, v);
@@ -241,10 +265,6 @@ __device__ __forceinline__ int for_pairs(const DevNlist &nl, int a, int64_t beg,
                 const int slot = qn + __popc(m & lt);
                 q[slot] = e;
                 q2[slot] = e2;
-                if (to_cache) {   // compacted in order at [beg, beg + kept)
-                    nl.pq[beg + kept + __popc(m & lt)] = e;
-                    nl.pq2[beg + kept + __popc(m & lt)] = e2;
-                }
             }
             qn += __popc(m);
             kept += __popc(m);
@@ -266,8 +286,8 @@ __device__ __forceinline__ int for_pairs(const DevNlist &nl, int a, int64_t beg,
     return kept;
 }
 
-// The in-cutoff pairs of atom a from the pair cache written by the
-// descriptor pass, in batches of up to 32 (one per lane).
+// The in-cutoff pairs of atom a from the pair cache written by k_screen, in
+// batches of up to 32 (one per lane).
 template <typename F>
 __device__ __forceinline__ void cached_pairs(const DevNlist &nl, int a, int np, int lane, F &&f) {
     const int64_t pb = nl.beg[a];
@@ -283,14 +303,69 @@ __device__ __forceinline__ void cached_pairs(const DevNlist &nl, int a, int np, 
     }
 }
 
+// A warp's stream of pair-cache batches over its atoms p, p + total, ...
+// (perm order), read one batch ahead.
+struct PairStream {
+    int a = -1, np = 0;          // current atom and its in-cutoff pair count
+    int64_t pb = 0;
+    int an = -1, npn = 0;        // next atom (segment start and count read one atom ahead)
+    int64_t pbn = 0;
+    int an2 = -1;                // the atom after next (perm entry read two atoms ahead)
+    float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 pf2 = make_float2(1.f, 0.f);
+
+    __device__ __forceinline__ void load(const DevNlist &nl, int64_t at, bool ok) {
+        pf = make_float4(0.f, 0.f, 0.f, 0.f);
+        pf2 = make_float2(1.f, 0.f);
+        if (ok) {
+            pf = nl.pq[at];
+            pf2 = nl.pq2[at];
+        }
+    }
+    __device__ __forceinline__ void start(const DevNlist &nl, int64_t p, int64_t total, int lane) {
+        if (p < nl.n) {
+            a = nl.perm[p];
+            pb = nl.beg[a];
+            np = nl.npair[a];
+            load(nl, pb + lane, lane < np);
+        }
+        an = p + total < nl.n ? nl.perm[p + total] : -1;
+    }
+    // at the start of atom p: the next atom's segment, the perm entry after it
+    __device__ __forceinline__ void atom_begins(const DevNlist &nl, int64_t p, int64_t total) {
+        if (an >= 0) {
+            pbn = nl.beg[an];
+            npn = nl.npair[an];
+        }
+        an2 = p + 2 * total < nl.n ? nl.perm[p + 2 * total] : -1;
+    }
+    // the batch after the one starting at base: the atom's next batch, its
+    // first batch again (another channel chunk follows), or the next atom's first
+    __device__ __forceinline__ void advance(const DevNlist &nl, int base, bool again, int lane) {
+        if (base + 32 < np)
+            load(nl, pb + base + 32 + lane, lane < np - base - 32);
+        else if (again)
+            load(nl, pb + lane, lane < np);
+        else
+            load(nl, pbn + lane, an >= 0 && lane < npn);
+    }
+    __device__ __forceinline__ void atom_ends() {
+        a = an;
+        pb = pbn;
+        np = an >= 0 ? npn : 0;
+        an = an2;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // descriptor forward: P and G per atom
 // ---------------------------------------------------------------------------
-// K > 32 runs in chunks of 32 channels: the first chunk walks the neighbour
-// table (and fills the pair cache), later chunks replay the atom's pairs from
-// the cache (or walk the table again when there is none), so that the
-// per-lane accumulators and the staged columns stay those of K = 32.
-template <int K, int S, bool TAB>
+// CACHED: the atom's in-cutoff pairs come from the pair cache filled by
+// k_screen; otherwise the pass screens the table itself (for_pairs).  K > 32
+// runs in chunks of 32 channels, each chunk going over the atom's pairs again,
+// so that the per-lane accumulators and the staged columns stay those of
+// K = 32.
+template <int K, int S, bool TAB, bool CACHED>
 __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const double *__restrict__ pos,
                                                   const int32_t *__restrict__ types, float *__restrict__ G,
                                                   float *__restrict__ Pout) {
@@ -298,7 +373,7 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
     constexpr int KPL = KC / 8;           // k values per lane
     constexpr int RS = 44;       // row stride of the staged pair columns (>= 32 + 3 (S - 1) slots)
     constexpr int Dd = S * K * 4;
-    __shared__ float4 s_rad[S * S * K];
+    __shared__ float4 s_rad2[S * S * K];
     __shared__ float4 s_q[PW][64];
     __shared__ float2 s_q2[PW][64];
     // staged pair data, one column per pair: H_k in row (k % KPL) 8 + k / KPL,
@@ -306,7 +381,7 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
     // d-group g reads four pairs of a row with one conflict-free vector load
     __shared__ __align__(16) float s_H[PW][KC * RS];
     __shared__ __align__(16) float s_M[PW][NMOM * RS];
-    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    stage_rad2(s_rad2, m.radial, S * S * K);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kg = lane >> 2, g = lane & 3;
@@ -315,18 +390,26 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
 #pragma unroll
     for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
     const int64_t total = (int64_t)gridDim.x * PW;
+    // CACHED: the pair-cache batches are read one batch ahead, across chunk
+    // and atom boundaries (the next atom's segment one atom ahead, its perm
+    // entry two atoms ahead), so that the pass waits on no load of its own
+    // stream.  pf / pf2 hold the batch the next pair_fn call takes.
+    PairStream ps;
+    if constexpr (CACHED) ps.start(nl, (int64_t)blockIdx.x * PW + warp, total, lane);
     for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
-        const int a = nl.perm[p];
+        const int a = CACHED ? ps.a : nl.perm[p];
         const int ti = types[a];
-        int written = 0;
+        if constexpr (CACHED) ps.atom_begins(nl, p, total);
         for (int k0 = 0; k0 < K; k0 += KC) {
-        float acc[S][KPL][5];
+        // two partial sums per P entry (even and odd pair slots), so that
+        // the accumulation runs on packed FP32x2 multiply-adds
+        float2 acc2[S][KPL][5];
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int kk = 0; kk < KPL; ++kk)
 #pragma unroll
-                for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = 0.f;
+                for (int dd = 0; dd < 5; ++dd) acc2[s][kk][dd] = make_float2(0.f, 0.f);
         float *sH = s_H[warp];
         float *sM = s_M[warp];
         auto pair_fn = [&](const float4 e, const float2 e2, bool valid, int) {
@@ -349,8 +432,19 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                           if (TAB)
                               radial_tab<KC, false>(m.rtab + (size_t)(ti * S + b) * m.rtab_n * 4 * K, K, k0,
                                                     m.rtab_scale, r_hi, r_lo, H, nullptr);
-                          else
-                              radial<KC, false>(&s_rad[(ti * S + b) * K + k0], r_hi, r_lo, m.inv_rc, H, nullptr);
+                          else {
+                              float fc, dfc;
+                              cutoff_fn(r_hi, m.inv_rc, fc, dfc);
+                              const float4 *rad2 = &s_rad2[(ti * S + b) * K + k0];
+#pragma unroll
+                              for (int k = 0; k < KC; k += 2) {
+                                  const Radial2 o = radial2<false>(rad2, k, make_float2(r_hi, r_hi),
+                                                                   make_float2(r_lo, r_lo), make_float2(fc, fc),
+                                                                   make_float2(dfc, dfc));
+                                  H[k] = o.H.x;
+                                  H[k + 1] = o.H.y;
+                              }
+                          }
                           moments20(e.x * ir, e.y * ir, e.z * ir, M);
 #pragma unroll
                           for (int k = 0; k < KC; ++k) sH[((k % KPL) * 8 + k / KPL) * RS + slot] = H[k];
@@ -376,12 +470,10 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                               for (int kk = 0; kk < KPL; ++kk)
 #pragma unroll
                                   for (int dd = 0; dd < 5; ++dd) {
-                                      float x = acc[s][kk][dd];
-                                      x = fmaf(hv[kk].x, mv[dd].x, x);
-                                      x = fmaf(hv[kk].y, mv[dd].y, x);
-                                      x = fmaf(hv[kk].z, mv[dd].z, x);
-                                      x = fmaf(hv[kk].w, mv[dd].w, x);
-                                      acc[s][kk][dd] = x;
+                                      float2 x = acc2[s][kk][dd];
+                                      x = __ffma2_rn(make_float2(hv[kk].x, hv[kk].y), make_float2(mv[dd].x, mv[dd].y), x);
+                                      x = __ffma2_rn(make_float2(hv[kk].z, hv[kk].w), make_float2(mv[dd].z, mv[dd].w), x);
+                                      acc2[s][kk][dd] = x;
                                   }
                           }
                           for (; q < stop; ++q) {
@@ -393,19 +485,34 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
 #pragma unroll
                               for (int kk = 0; kk < KPL; ++kk)
 #pragma unroll
-                                  for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = fmaf(hv[kk], mv[dd], acc[s][kk][dd]);
+                                  for (int dd = 0; dd < 5; ++dd)
+                                      acc2[s][kk][dd].x = fmaf(hv[kk], mv[dd], acc2[s][kk][dd].x);
                           }
                           start += (cnt[s] + 3) & ~3;
                       }
                       __syncwarp();
                   };
-        if (k0 == 0 || !nl.pq)   // the in-cutoff pairs also go to the pair cache, when there is one
-            written = for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane, pair_fn,
-                                k0 == 0 && nl.pq != nullptr);
-        else
-            cached_pairs(nl, a, written, lane, pair_fn);   // this warp's own cache writes (ordered by __syncwarp)
+        if constexpr (CACHED) {
+            for (int base = 0; base < ps.np; base += 32) {
+                const float4 e = ps.pf;
+                const float2 e2 = ps.pf2;
+                const int nb = min(32, ps.np - base);
+                ps.advance(nl, base, k0 + KC < K, lane);
+                pair_fn(e, e2, lane < nb, nb);
+            }
+            if (ps.np == 0 && k0 + KC >= K) ps.advance(nl, 0, false, lane);
+        } else {
+            for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane, pair_fn);
+        }
+        float acc[S][KPL][5];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int kk = 0; kk < KPL; ++kk)
+#pragma unroll
+                for (int dd = 0; dd < 5; ++dd) acc[s][kk][dd] = acc2[s][kk][dd].x + acc2[s][kk][dd].y;
         // P[b][k][d] for the backward pass
-        float *Pa = Pout + (size_t)a * (S * K * NMOM);
+        float *Pa = Pout + (size_t)p * (S * K * NMOM);   // workspaces are indexed by perm position
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
@@ -434,11 +541,11 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                     p3 += __shfl_xor_sync(0xffffffffu, p3, o);
                 }
                 const float val = (g == 0) ? sqrtf(p0) : ((g == 1) ? p1 : ((g == 2) ? p2 : p3));
-                G[(size_t)a * Dd + (s * K + k0 + kg * KPL + kk) * 4 + g] = val;
+                G[(size_t)p * Dd + (s * K + k0 + kg * KPL + kk) * 4 + g] = val;
             }
         }
         }
-        if (nl.npair && lane == 0) nl.npair[a] = written;
+        if constexpr (CACHED) ps.atom_ends();
     }
 }
 
@@ -502,7 +609,8 @@ __device__ __forceinline__ void pair_grad_tail(const float (&V)[NMOM], const flo
 
 // g_ij = dE/dD_ij of one in-cutoff pair (Eqs. dP_abkd, U_abck, F1_abcx,
 // F2_abcx): Pb = the centre atom's P' for the neighbour's species, rad = the
-// radial parameters of the (centre, neighbour) species pair.
+// radial parameters of the (centre, neighbour) species pair in the packed
+// layout of stage_rad2.
 template <int K, bool TAB>
 __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, const float2 e2, const float *Pb,
                                           const float4 *rad, const float *tab, float &gxs, float &gys, float &gzs) {
@@ -511,59 +619,70 @@ __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, con
     const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
     // V_d = sum_k P'_kd H_k and W_d = sum_k P'_kd H'_k, so that
     // F1 = U H' R' = sum_d W_d M_d and F2 = V M'
-    float V[NMOM], Wd[NMOM];
+    // V and W as packed pairs (d, d + 1): every multiply-add of the channel
+    // loop is one FP32x2 instruction (each half rounded as fmaf)
+    float2 V2[NMOM / 2], W2[NMOM / 2];
 #pragma unroll
-    for (int d = 0; d < NMOM; ++d) V[d] = Wd[d] = 0.f;
+    for (int d = 0; d < NMOM / 2; ++d) V2[d] = W2[d] = make_float2(0.f, 0.f);
     float fc = 0.f, dfc = 0.f;
     TabCell tc;
     if (TAB)
         tc = tab_cell(tab, K, m.rtab_scale, r_hi, r_lo);
     else
         cutoff_fn(r_hi, m.inv_rc, fc, dfc);
+    const float2 rh2 = make_float2(r_hi, r_hi), rl2 = make_float2(r_lo, r_lo);
+    const float2 fc2 = make_float2(fc, fc), dfc2 = make_float2(dfc, dfc);
     constexpr int KU = K > 32 ? 16 : K;   // channels per unrolled block
 #pragma unroll 1
     for (int kb = 0; kb < K; kb += KU)
 #pragma unroll
-    for (int ku = 0; ku < KU; ++ku) {
+    for (int ku = 0; ku < KU; ku += 2) {
         const int k = kb + ku;
-        // H_k and H'_k formed inside the loop (no per-pair arrays)
-        float Hk, dHk;
+        // H and H' of channels k, k + 1 formed inside the loop (no per-pair arrays)
+        float Hk[2], dHk[2];
         if (TAB) {
-            tab_eval(tc, k, m.rtab_scale, Hk, dHk);
+            tab_eval(tc, k, m.rtab_scale, Hk[0], dHk[0]);
+            tab_eval(tc, k + 1, m.rtab_scale, Hk[1], dHk[1]);
         } else {
-            const float4 rp = rad[k];
-            const float t = (r_hi - rp.x) + (r_lo - rp.y);
-            const float f = ex2_ftz(-rp.z * t * t);
-            Hk = f * fc;
-            dHk = f * fmaf(-rp.w * t, fc, dfc);
+            const Radial2 o = radial2<true>(rad, k, rh2, rl2, fc2, dfc2);
+            Hk[0] = o.H.x; Hk[1] = o.H.y;
+            dHk[0] = o.dH.x; dHk[1] = o.dH.y;
         }
 #pragma unroll
-        for (int q4 = 0; q4 < NMOM / 4; ++q4) {
-            const float4 pd = *reinterpret_cast<const float4 *>(Pb + k * NMOM + 4 * q4);
-            V[4 * q4] = fmaf(pd.x, Hk, V[4 * q4]);
-            V[4 * q4 + 1] = fmaf(pd.y, Hk, V[4 * q4 + 1]);
-            V[4 * q4 + 2] = fmaf(pd.z, Hk, V[4 * q4 + 2]);
-            V[4 * q4 + 3] = fmaf(pd.w, Hk, V[4 * q4 + 3]);
-            Wd[4 * q4] = fmaf(pd.x, dHk, Wd[4 * q4]);
-            Wd[4 * q4 + 1] = fmaf(pd.y, dHk, Wd[4 * q4 + 1]);
-            Wd[4 * q4 + 2] = fmaf(pd.z, dHk, Wd[4 * q4 + 2]);
-            Wd[4 * q4 + 3] = fmaf(pd.w, dHk, Wd[4 * q4 + 3]);
+        for (int c = 0; c < 2; ++c) {
+            const float2 h2 = make_float2(Hk[c], Hk[c]), d2 = make_float2(dHk[c], dHk[c]);
+#pragma unroll
+            for (int q4 = 0; q4 < NMOM / 4; ++q4) {
+                const float4 pd = *reinterpret_cast<const float4 *>(Pb + (k + c) * NMOM + 4 * q4);
+                const float2 plo = make_float2(pd.x, pd.y), phi = make_float2(pd.z, pd.w);
+                V2[2 * q4] = __ffma2_rn(plo, h2, V2[2 * q4]);
+                V2[2 * q4 + 1] = __ffma2_rn(phi, h2, V2[2 * q4 + 1]);
+                W2[2 * q4] = __ffma2_rn(plo, d2, W2[2 * q4]);
+                W2[2 * q4 + 1] = __ffma2_rn(phi, d2, W2[2 * q4 + 1]);
+            }
         }
+    }
+    float V[NMOM], Wd[NMOM];
+#pragma unroll
+    for (int d = 0; d < NMOM / 2; ++d) {
+        V[2 * d] = V2[d].x; V[2 * d + 1] = V2[d].y;
+        Wd[2 * d] = W2[d].x; Wd[2 * d + 1] = W2[d].y;
     }
     pair_grad_tail(V, Wd, ux, uy, uz, ir, gxs, gys, gzs);
 }
 
 
-// P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm (for m = 0: G'_bk0 sign(P)) of atom a
-// into a shared slot, each lane its (K/8 x 5) block  (Eq. dP_abkd)
+// P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm (for m = 0: G'_bk0 sign(P)) of the
+// atom at perm position p (P and G' are indexed by perm position) into a
+// shared slot, each lane its (K/8 x 5) block  (Eq. dP_abkd)
 template <int K, int S>
-__device__ __forceinline__ void pprime_setup(const float *__restrict__ Pin, const float *__restrict__ dG, int a,
+__device__ __forceinline__ void pprime_setup(const float *__restrict__ Pin, const float *__restrict__ dG, int p,
                                              float *slot, int kg, int g, const float (&Tg)[5]) {
     constexpr int KPL = K / 8;
     constexpr int PSTR = K * NMOM + 4;
     constexpr int Dd = S * K * 4;
-    const float *Pa = Pin + (size_t)a * (S * K * NMOM);
-    const float *dGa = dG + (size_t)a * Dd;
+    const float *Pa = Pin + (size_t)p * (S * K * NMOM);
+    const float *dGa = dG + (size_t)p * Dd;
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
@@ -585,6 +704,22 @@ __device__ __forceinline__ void pprime_setup(const float *__restrict__ Pin, cons
         }
 }
 
+// Lane sums of the virial -> warp total (FP32, fixed butterfly order) added to
+// the warp's FP64 accumulator; the lane sums restart from zero.  A lane sums
+// the pairs of about VFLUSH / 32 of the warp's atoms between flushes, so the
+// FP32 rounding stays at the level of one atom's virial.
+constexpr int VFLUSH = 8;
+__device__ __forceinline__ void virial_flush(float (&wacc)[9], double *acc, int lane) {
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        float v = wacc[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) acc[t] += (double)v;
+        wacc[t] = 0.f;
+    }
+}
+
 // Force pass over the pair cache with full lane batches: each warp walks a
 // contiguous run of atoms (perm order) and fills every batch of 32 lanes with
 // the rest of the current atom's pairs followed by the first pairs of the
@@ -598,16 +733,20 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
     __shared__ float4 s_rad[S * S * K];
     __shared__ __align__(16) float s_Pd[PW][2][S * PSTR];
     __shared__ double s_w[PW][9];
-    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
-    __syncthreads();
+    stage_rad2(s_rad, m.radial, S * S * K);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < 9) s_w[warp][lane] = 0.0;
+    __syncthreads();
     const int kg = lane >> 2, g = lane & 3;
     float Tg[5];
 #pragma unroll
     for (int dd = 0; dd < 5; ++dd) Tg[dd] = c_T[5 * g + dd];
-    float wsum[9], wcmp[9];
+    // virial: each lane's pairs summed in FP32 over VFLUSH atoms, then the
+    // warp's total added to an FP64 accumulator in shared memory
+    float wacc[9];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) { wsum[t] = 0.f; wcmp[t] = 0.f; }
+    for (int t = 0; t < 9; ++t) wacc[t] = 0.f;
+    int since = 0;
     const int64_t nw = (int64_t)gridDim.x * PW, wid = (int64_t)blockIdx.x * PW + warp;
     const int64_t chunk = (nl.n + nw - 1) / nw;
     int64_t p = wid * chunk;
@@ -615,7 +754,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
     if (p < pend) {
         int slot = 0;
         int a = nl.perm[p], ta = types[a];
-        pprime_setup<K, S>(Pin, dG, a, s_Pd[warp][0], kg, g, Tg);
+        pprime_setup<K, S>(Pin, dG, (int)p, s_Pd[warp][0], kg, g, Tg);
         int64_t cb = nl.beg[a];
         int cr = nl.npair[a];
         long long fcx = 0, fcy = 0, fcz = 0;
@@ -627,16 +766,13 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
             if (has_n) {   // bring in the next atom
                 an = nl.perm[p + 1];
                 tn = types[an];
-                pprime_setup<K, S>(Pin, dG, an, s_Pd[warp][slot ^ 1], kg, g, Tg);
+                pprime_setup<K, S>(Pin, dG, (int)p + 1, s_Pd[warp][slot ^ 1], kg, g, Tg);
                 nb = nl.beg[an];
                 nr = nl.npair[an];
                 take_n = min(nr, 32 - cr);
             }
             __syncwarp();
             long long fnx = 0, fny = 0, fnz = 0;
-            float wa[9];   // this lane's pair of this batch
-#pragma unroll
-            for (int t = 0; t < 9; ++t) wa[t] = 0.f;
             const bool isc = lane < take_c, isn = !isc && lane < take_c + take_n;
             if (isc || isn) {
                 const int64_t c = isc ? cb + lane : nb + (lane - take_c);
@@ -664,10 +800,8 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
 #pragma unroll
                 for (int al = 0; al < 3; ++al)
 #pragma unroll
-                    for (int be = 0; be < 3; ++be) wa[al * 3 + be] = -D[al] * gv[be];
+                    for (int be = 0; be < 3; ++be) wacc[al * 3 + be] = fmaf(-D[al], gv[be], wacc[al * 3 + be]);
             }
-#pragma unroll
-            for (int t = 0; t < 9; ++t) kahan_add(wsum[t], wcmp[t], wa[t]);
             cb += take_c;
             cr -= take_c;
             if (cr == 0) {   // the current atom is complete: its own force
@@ -682,6 +816,10 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
                     atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fcy);
                     atomicAdd(&Fq[3 * (int64_t)a + 2], (unsigned long long)fcz);
                 }
+                if (++since == VFLUSH) {
+                    virial_flush(wacc, s_w[warp], lane);
+                    since = 0;
+                }
                 ++p;
                 if (p < pend) {
                     if (has_n) {   // the next atom (already set up) becomes the current one
@@ -695,7 +833,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
                         __syncwarp();
                         a = nl.perm[p];
                         ta = types[a];
-                        pprime_setup<K, S>(Pin, dG, a, s_Pd[warp][slot], kg, g, Tg);
+                        pprime_setup<K, S>(Pin, dG, (int)p, s_Pd[warp][slot], kg, g, Tg);
                         cb = nl.beg[a];
                         cr = nl.npair[a];
                         fcx = fcy = fcz = 0;
@@ -705,20 +843,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
             __syncwarp();
         }
     }
-    // virial: per-lane compensated sums -> warp total as an FP32 double-float -> FP64 block total
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        float hi = wsum[t], lo = -wcmp[t];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
-            float sh, se;
-            two_sum(hi, oh, sh, se);
-            lo = (lo + ol) + se;
-            two_sum(sh, lo, hi, lo);
-        }
-        if (lane == 0) s_w[warp][t] = (double)hi + (double)lo;
-    }
+    virial_flush(wacc, s_w[warp], lane);
     __syncthreads();
     if (threadIdx.x < 9) {
         double v = 0.0;
@@ -791,7 +916,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_tc(DevModel m, DevNlist nl
     const int64_t total = (int64_t)gridDim.x * PW;
     for (int64_t p = (int64_t)blockIdx.x * PW + warp; p < nl.n; p += total) {
         const int a = nl.perm[p];
-        pprime_setup<K, 1>(Pin, dG, a, sPd, kg, g, Tg);
+        pprime_setup<K, 1>(Pin, dG, (int)p, sPd, kg, g, Tg);
         __syncwarp();
         // B fragments of P' (k x 24), hi and lo parts: b0 = (k = t, n = g), b1 = (k = t + 4, n = g)
         uint32_t bh[KS][3][2], bl[KS][3][2];
@@ -963,7 +1088,7 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
     __shared__ float2 s_q2[PW][64];
     __shared__ __align__(16) float s_Pd[PW][S * PSTR];
     __shared__ double s_w[PW][9];
-    for (int t = threadIdx.x; t < S * S * K; t += blockDim.x) s_rad[t] = m.radial[t];
+    stage_rad2(s_rad, m.radial, S * S * K);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kg = lane >> 2, g = lane & 3;
@@ -979,8 +1104,8 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
         const int a = nl.perm[p];
         const int ti = types[a];
         // P'_bkd = 2 T_d sigma'_m P_bkd G'_bkm; for m = 0: G'_bk0 sign(P)  (Eq. dP_abkd)
-        const float *Pa = Pin + (size_t)a * (S * K * NMOM);
-        const float *dGa = dG + (size_t)a * Dd;
+        const float *Pa = Pin + (size_t)p * (S * K * NMOM);
+        const float *dGa = dG + (size_t)p * Dd;
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
@@ -1086,20 +1211,29 @@ template <int K, int S>
 tmd_status launch_pair_kernels(const DevModel &dm, const DevNlist &dn, const double *pos, const int32_t *types,
                                tmd_nlist *nl, double *part_w, int nblk, cudaStream_t s, bool forward,
                                float *w_atom) {
-    if (forward && dm.rtab)
-        TMD_LAUNCH("k_desc", s, k_desc<K, S, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+    if (forward && dn.pq) {   // screen into the pair cache, then stream it
+        const tmd_status st = launch_screen(dm, dn, s);
+        if (st != TMD_OK) return st;
+        if (dm.rtab)
+            TMD_LAUNCH("k_desc", s, k_desc<K, S, true, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+        else
+            TMD_LAUNCH("k_desc", s, k_desc<K, S, false, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+    } else if (forward && dm.rtab)
+        TMD_LAUNCH("k_desc", s, k_desc<K, S, true, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
     else if (forward)
-        TMD_LAUNCH("k_desc", s, k_desc<K, S, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
+        TMD_LAUNCH("k_desc", s, k_desc<K, S, false, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->G, nl->P));
     else if (w_atom && dm.rtab)   // batched evaluations always run with the pair cache
         TMD_LAUNCH("k_force", s, k_force<K, S, true, true, true><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
                                                                                         nl->dG, nl->Fq, part_w, w_atom));
     else if (w_atom)
         TMD_LAUNCH("k_force", s, k_force<K, S, true, true, false><<<nblk, PW * 32, 0, s>>>(dm, dn, pos, types, nl->P,
                                                                                          nl->dG, nl->Fq, part_w, w_atom));
-    else if (force_kernel() == TMD_FORCE_TENSOR && !(dn.pq && !dm.rtab && S == 1 && K <= 32)) {
-        set_error("the tensor-core force pass needs one species, K <= 32, the direct radial basis and the pair cache");
+    // the tensor-core pass reads the pair cache; an evaluation without one
+    // (the allocation-free call) runs the SIMT pass whatever the setting
+    else if (force_kernel() == TMD_FORCE_TENSOR && dn.pq && !(!dm.rtab && S == 1 && K <= 32)) {
+        set_error("the tensor-core force pass needs one species, K <= 32 and the direct radial basis");
         return TMD_ERR_UNIMPLEMENTED;
-    } else if (force_kernel() == TMD_FORCE_TENSOR) {
+    } else if (force_kernel() == TMD_FORCE_TENSOR && dn.pq) {
         if constexpr (S == 1 && K <= 32)
             TMD_LAUNCH("k_force", s, k_force_tc<K><<<nblk, PW * 32, 0, s>>>(dm, dn, nl->P, nl->dG, nl->Fq, part_w));
     } else if (dn.pq && dm.rtab)

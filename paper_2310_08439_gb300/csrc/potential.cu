@@ -25,15 +25,30 @@ constexpr int MT = 32;          // smallest network tile (sizes the per-tile ene
 constexpr int MLP_THREADS = 256;
 constexpr double FQ_INV = 1.0 / 4294967296.0;   // forces accumulate in units of 2^-32 eV/A
 
-// positions -> hi/lo FP32 pairs (once per evaluation)
+// dst[perm[p]] = src[p] for rows of `width` floats (a multiple of 4): the
+// per-atom view of a workspace kept in perm order
+__global__ void k_rows_to_atoms(const float *__restrict__ src, const int32_t *__restrict__ perm, int64_t n, int width,
+                                float *__restrict__ dst) {
+    const int w4 = width >> 2;
+    const int64_t total = n * w4;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / w4;
+        const int c = (int)(t - p * w4);
+        reinterpret_cast<float4 *>(dst + (size_t)perm[p] * width)[c] =
+            reinterpret_cast<const float4 *>(src + (size_t)p * width)[c];
+    }
+}
+
+// positions -> hi/lo FP32 pairs on the 2^-10 grid (grid_split; once per evaluation)
 __global__ void k_split_pos(const double *__restrict__ pos, int64_t n, float4 *__restrict__ ph,
                             float4 *__restrict__ pl) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-    const float xh = (float)x, yh = (float)y, zh = (float)z;
-    ph[i] = make_float4(xh, yh, zh, 0.f);
-    pl[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
+    float h[3], l[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) grid_split(pos[3 * i + x], h[x], l[x]);
+    ph[i] = make_float4(h[0], h[1], h[2], 0.f);
+    pl[i] = make_float4(l[0], l[1], l[2], 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -218,12 +233,12 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
         }
         if (!active) continue;
         const int col = n0 + cb * 4;
-        if (EPI == 3) {
+        if (EPI == 3) {   // gout = the tile's first G' row (rows by perm position)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int row = rb * 4 + i;
                 if (s_type[row] == ws.s)
-                    *reinterpret_cast<float4 *>(gout + (size_t)s_atom[row] * N + col) =
+                    *reinterpret_cast<float4 *>(gout + (size_t)row * N + col) =
                         make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
             }
         } else {
@@ -288,7 +303,7 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
         const int a = s_atom[r];
         for (int c4 = warp; c4 < (Dd >> 2); c4 += MLP_THREADS / 32) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (a >= 0) v = __ldg(reinterpret_cast<const float4 *>(G + (size_t)a * Dd + 4 * c4));
+            if (a >= 0) v = __ldg(reinterpret_cast<const float4 *>(G + (size_t)(p0 + r) * Dd + 4 * c4));
             act[0][(4 * c4) * LDT + r] = v.x;
             act[0][(4 * c4 + 1) * LDT + r] = v.y;
             act[0][(4 * c4 + 2) * LDT + r] = v.z;
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
         for (int l = L - 1; l >= 1; --l)
             mlp_gemm<TR, 2>(m, ws, act[l + 1], nullptr, act[l], wbuf, nullptr, s_atom, s_type);
         // G' = dz_1 W_0^T
-        mlp_gemm<TR, 3>(m, ws, act[1], nullptr, nullptr, wbuf, dG, s_atom, s_type);
+        mlp_gemm<TR, 3>(m, ws, act[1], nullptr, nullptr, wbuf, dG + (size_t)p0 * Dd, s_atom, s_type);
     }
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
@@ -474,7 +489,7 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
             const int a = s_atom[r];
             for (int c2 = lane; c2 < (Dd >> 1); c2 += 32) {
                 float2 v = make_float2(0.f, 0.f);
-                if (a >= 0) v = __ldg(reinterpret_cast<const float2 *>(G + (size_t)a * Dd + 2 * c2));
+                if (a >= 0) v = __ldg(reinterpret_cast<const float2 *>(G + (size_t)(p0 + r) * Dd + 2 * c2));
                 *reinterpret_cast<uint32_t *>(act[0] + r * ld[0] + 2 * c2) = pack_bf16(v.x, v.y);
             }
         }
@@ -567,7 +582,7 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
                                 *reinterpret_cast<uint32_t *>(nxt + row * ldz + col) =
                                     pack_bf16(acc[j][2 * h] * d.x, acc[j][2 * h + 1] * d.y);
                             } else if (s_type[row] == s) {   // G'
-                                *reinterpret_cast<float2 *>(dG + (size_t)s_atom[row] * Dd + col) =
+                                *reinterpret_cast<float2 *>(dG + (size_t)(p0 + row) * Dd + col) =
                                     make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
                             }
                         }
@@ -909,9 +924,9 @@ static tmd_status pair_cache(tmd_nlist *nl, int64_t n_atoms, cudaStream_t) {
 tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, int64_t n_active) {
     tmd_status st;
     const int64_t nt = std::max<int64_t>(n_total, 1), na = std::max<int64_t>(n_active, 1);
-    if ((st = grow(&nl->G, &nl->cap_G, nt * dm.Dd)) != TMD_OK) return st;
-    if ((st = grow(&nl->dG, &nl->cap_dG, nt * dm.Dd)) != TMD_OK) return st;
-    if ((st = grow(&nl->P, &nl->cap_P, nt * dm.S * dm.K * NMOM)) != TMD_OK) return st;
+    if ((st = grow(&nl->G, &nl->cap_G, na * dm.Dd)) != TMD_OK) return st;
+    if ((st = grow(&nl->dG, &nl->cap_dG, na * dm.Dd)) != TMD_OK) return st;
+    if ((st = grow(&nl->P, &nl->cap_P, na * dm.S * dm.K * NMOM)) != TMD_OK) return st;
     if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * nt)) != TMD_OK) return st;
     if ((st = grow(&nl->ph, &nl->cap_ph, nt)) != TMD_OK) return st;
     if ((st = grow(&nl->pl, &nl->cap_pl, nt)) != TMD_OK) return st;
@@ -932,8 +947,7 @@ static DevNlist dev_nlist(const tmd_nlist *nl, int64_t n, const double box[3]) {
     dn.n = n;
     for (int x = 0; x < 3; ++x) {
         dn.box[x] = box[x];
-        dn.Lh[x] = (float)box[x];
-        dn.Ll[x] = (float)(box[x] - (double)dn.Lh[x]);
+        grid_split(box[x], dn.Lh[x], dn.Ll[x]);
     }
     return dn;
 }
@@ -945,18 +959,24 @@ tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
     if (n == 0) return TMD_OK;
     const DevModel &dm = model->dm;
     if ((st = grow(&nl->P, &nl->cap_P, n * dm.S * dm.K * NMOM)) != TMD_OK) return st;
+    if ((st = grow(&nl->G, &nl->cap_G, n * dm.Dd)) != TMD_OK) return st;
+    if (dEdG && (st = grow(&nl->dG, &nl->cap_dG, n * dm.Dd)) != TMD_OK) return st;
     const int nblk = pair_blocks(dm, n);
     if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
     const DevNlist dn = dev_nlist(nl, n, box);
-    float *keep = nl->G;
-    nl->G = G;
-    st = dispatch_pair(dm, dn, pos, types, nl, nullptr, nblk, s, true);
-    nl->G = keep;
-    if (st != TMD_OK || !dEdG) return st;
+    if ((st = dispatch_pair(dm, dn, pos, types, nl, nullptr, nblk, s, true)) != TMD_OK) return st;
+    // the workspaces hold rows in perm order; the caller's arrays are per atom
+    const unsigned gb = (unsigned)std::min<int64_t>((n * dm.Dd / 4 + 255) / 256, 65535);
+    TMD_LAUNCH("k_rows_to_atoms", s, k_rows_to_atoms<<<gb, 256, 0, s>>>(nl->G, nl->perm, n, dm.Dd, G));
+    TMD_CUDA(cudaGetLastError());
+    if (!dEdG) return TMD_OK;
     const int ntile = (int)((n + MT - 1) / MT);
     if ((st = grow(&nl->part, &nl->cap_part, ntile + 16)) != TMD_OK) return st;
     int nt = 0;
-    return launch_network(dm, nl->perm, types, n, G, dEdG, nullptr, nl->part, &nt, s);
+    if ((st = launch_network(dm, nl->perm, types, n, nl->G, nl->dG, nullptr, nl->part, &nt, s)) != TMD_OK) return st;
+    TMD_LAUNCH("k_rows_to_atoms", s, k_rows_to_atoms<<<gb, 256, 0, s>>>(nl->dG, nl->perm, n, dm.Dd, dEdG));
+    TMD_CUDA(cudaGetLastError());
+    return TMD_OK;
 }
 
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
@@ -1037,7 +1057,7 @@ __global__ void k_iota(int32_t *__restrict__ perm, int64_t n) {
 // tables with them) and records a violation in *flag.
 __global__ void k_noalloc_check(const int64_t *__restrict__ off, const int32_t *__restrict__ nbr,
                                 const char4 *__restrict__ shift, const int32_t *__restrict__ types, int64_t n,
-                                int64_t nnz, int S, int32_t *__restrict__ flag) {
+                                int64_t nnz, int S, double Lx, double Ly, double Lz, int32_t *__restrict__ flag) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t0 == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(flag, 1);
@@ -1046,8 +1066,15 @@ __global__ void k_noalloc_check(const int64_t *__restrict__ off, const int32_t *
         if (types[i] < 0 || types[i] >= S) atomicOr(flag, 2);
     }
     for (int64_t c = t0; c < nnz; c += stride) {
-        if (nbr[c] < 0 || nbr[c] >= n) atomicOr(flag, 4);
-        if (shift[c].w < 0 || shift[c].w >= S) atomicOr(flag, 8);
+        const int j = nbr[c];
+        const int b = shift[c].w;
+        if (j < 0 || j >= n) atomicOr(flag, 4);
+        else if (b != types[j]) atomicOr(flag, 16);   // the species byte must be that of j
+        if (b < 0 || b >= S) atomicOr(flag, 8);
+        const char4 sh = shift[c];   // the pair geometry keeps |s| L below the grid limit
+        if (abs((int)sh.x) * Lx >= GRID_LIMIT / 2 || abs((int)sh.y) * Ly >= GRID_LIMIT / 2 ||
+            abs((int)sh.z) * Lz >= GRID_LIMIT / 2)
+            atomicOr(flag, 32);
     }
 }
 
@@ -1082,8 +1109,8 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
         return TMD_ERR_INVALID_ARG;
     }
     for (int x = 0; x < 3; ++x)
-        if (!(std::isfinite(box[x]) && box[x] > 0.0)) {
-            set_error("box[%d] must be finite and > 0", x);
+        if (!(std::isfinite(box[x]) && box[x] > 0.0 && box[x] < GRID_LIMIT / 2)) {
+            set_error("box[%d] must be finite, > 0 and below %.0f A", x, GRID_LIMIT / 2);
             return TMD_ERR_INVALID_ARG;
         }
     if (n > 0 && (!off || !pos || !types || (nnz > 0 && (!nbr || !shift4)))) {
@@ -1148,13 +1175,15 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
     const int cb = (int)std::min<int64_t>((std::max(n, nnz) + 255) / 256, 4096);
     TMD_LAUNCH("k_noalloc_check", s, k_noalloc_check<<<cb, 256, 0, s>>>(off, nbr, reinterpret_cast<const char4 *>(shift4),
-                                                                        types, n, nnz, dm.S, flag));
+                                                                        types, n, nnz, dm.S, box[0], box[1], box[2],
+                                                                        flag));
     TMD_CUDA(cudaGetLastError());
     int32_t bad = 0;
     TMD_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     TMD_CUDA(cudaStreamSynchronize(s));
     if (bad) {
-        set_error("invalid neighbour table or species (check code %d: 1 offsets, 2 types, 4 nbr ids, 8 shift4 species)",
+        set_error("invalid neighbour table or species (check code %d: 1 offsets, 2 types, 4 nbr ids, 8 shift4 species "
+                  "out of range, 16 shift4 species differs from types[nbr], 32 |shift| box >= 4096 A)",
                   bad);
         return TMD_ERR_INVALID_ARG;
     }
@@ -1173,8 +1202,7 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     dn.n = n;
     for (int x = 0; x < 3; ++x) {
         dn.box[x] = box[x];
-        dn.Lh[x] = (float)box[x];
-        dn.Ll[x] = (float)(box[x] - (double)dn.Lh[x]);
+        grid_split(box[x], dn.Lh[x], dn.Ll[x]);
     }
     double *part_e = w.part;
     double *part_w = w.part + ntile;
@@ -1222,9 +1250,10 @@ tmd_status run_compute_batch(const tmd_model *model, tmd_nlist *nl, const double
     const int64_t na = nl->n_active;  // atoms of the active systems, in perm
     tmd_status st;
     if (na > 0) {
-        if ((st = grow(&nl->G, &nl->cap_G, n_total * dm.Dd)) != TMD_OK) return st;
-        if ((st = grow(&nl->dG, &nl->cap_dG, n_total * dm.Dd)) != TMD_OK) return st;
-        if ((st = grow(&nl->P, &nl->cap_P, n_total * dm.S * dm.K * NMOM)) != TMD_OK) return st;
+        // P, G and G' are indexed by perm position: room for the active atoms only
+        if ((st = grow(&nl->G, &nl->cap_G, na * dm.Dd)) != TMD_OK) return st;
+        if ((st = grow(&nl->dG, &nl->cap_dG, na * dm.Dd)) != TMD_OK) return st;
+        if ((st = grow(&nl->P, &nl->cap_P, na * dm.S * dm.K * NMOM)) != TMD_OK) return st;
         if ((st = grow(&nl->Fq, &nl->cap_Fq, 3 * n_total)) != TMD_OK) return st;
         const int nblk = pair_blocks(dm, na);
         const int ntile = (int)((na + MT - 1) / MT);

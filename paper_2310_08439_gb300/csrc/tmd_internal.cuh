@@ -78,11 +78,24 @@ struct SysParams {
     double L[3];        // box lengths
     double ic[3];       // cells per unit length (nc / L)
     double r2;          // list radius squared (FP64, as the definition)
-    float Lh[3], Ll[3]; // box as FP32 hi + lo
+    float Lh[3], Ll[3]; // box as FP32 hi + lo (neighbour table build)
+    float Gh[3], Gl[3]; // box on the 2^-10 grid split (pair kernels, grid_split)
     float r2lo, r2hi;   // FP32 band outside which the FP32 screen decides
     int nc[3], R[3], pbc[3];
     int cell_off;       // first global cell of this system
 };
+
+// v = hi + lo with hi = v rounded to a multiple of 2^-10 (exact in FP32 for
+// |v| < 2^13) and lo = v - hi rounded to FP32 (|lo| <= 2^-11): differences of
+// hi parts are exact in FP32, which keeps the pair geometry accurate without
+// error-free transformations (pair_geom).
+__host__ __device__ inline void grid_split(double v, float &hi, float &lo) {
+    const double h = rint(v * 1024.0) * (1.0 / 1024.0);
+    hi = (float)h;
+    lo = (float)(v - h);
+}
+// largest |s| L, position or box length the grid split keeps exact
+constexpr double GRID_LIMIT = 8192.0;
 
 // Neighbour table as seen by kernels.
 struct DevNlist {
@@ -96,11 +109,11 @@ struct DevNlist {
     const SysParams *sp = nullptr;  // per-system boxes (batched), or nullptr
     const int32_t *sys_of = nullptr; // [atoms] system of each atom (batched), or nullptr
     double box[3] = {0, 0, 0};
-    float Lh[3] = {0, 0, 0}, Ll[3] = {0, 0, 0};  // box as hi + lo (single system)
+    float Lh[3] = {0, 0, 0}, Ll[3] = {0, 0, 0};  // box on the 2^-10 grid split (single system)
     int64_t n = 0;                  // atoms in perm
     // in-cutoff pairs of atom a, compacted at [beg[a], beg[a] + npair[a]):
-    // (Dx, Dy, Dz, j | b << 28) and r^2 as hi + lo; written by the descriptor
-    // pass when non-null, read by the force pass
+    // (Dx, Dy, Dz, j | b << 28) and r^2 as hi + lo; written by k_screen
+    // when non-null, read by the descriptor and force passes
     float4 *pq = nullptr;
     float2 *pq2 = nullptr;
     int32_t *npair = nullptr;
@@ -298,6 +311,8 @@ TMD_PAIR_LAUNCHER(launch_pair_k32);
 TMD_PAIR_LAUNCHER(launch_pair_k64);
 TMD_PAIR_LAUNCHER(launch_pair_k128);
 tmd_status reserve_compute(const DevModel &dm, tmd_nlist *nl, int64_t n_total, int64_t n_active);
+// the in-cutoff pairs of the atoms of dn into its pair cache (screen.cu)
+tmd_status launch_screen(const DevModel &dm, const DevNlist &dn, cudaStream_t s);
 // BF16 weights in the tcgen05 operand layout from the FP64 weights (leaves
 // dm.ub null when the widths have no BF16 form); status bits of the
 // tensor-core kernels, read and cleared (synchronises)

@@ -1,14 +1,20 @@
 """Continuous-batching MD force server over resident systems.
 
-Systems are admitted into one resident batch (``tmd.Batch``) while their
-device memory fits the budget.  Requests (system id, number of MD steps)
-arrive open-loop; every tick the server advances all systems that have an
-active request by one velocity-Verlet step in a single batched call (one set
-of launches over the union of their atoms), retires the requests that are
-done and admits the ones that arrived meanwhile.  Requests for the same
-system are served in arrival order, so every system's trajectory is the one
-it would have alone.  ``serve_alone`` is the baseline: each request as its
-own plain FP32 call, first come first served.
+Every system's state lives in one batch (``tmd.Batch``); its neighbour table
+and the evaluation workspace of its atoms are what a system holds on the
+device while it is *resident*.  Requests (system id, number of MD steps)
+arrive open-loop.  Every tick the server
+- queues the requests that arrived,
+- admits systems with queued requests while the device-memory budget allows
+  (releasing the tables of idle resident systems, least recently used first,
+  when it does not), so a request whose system cannot be admitted waits,
+- advances all systems that have an active request by one velocity-Verlet
+  step in a single batched call (one set of launches over the union of their
+  atoms; tables kept between ticks with the batch's skin policy),
+- retires the requests that are done.
+Requests for the same system are served in arrival order, so every system's
+trajectory is the one it would have alone.  ``serve_alone`` is the baseline:
+each request as its own call, first come first served.
 """
 from __future__ import annotations
 
@@ -54,36 +60,69 @@ def poisson_requests(n_systems, rate, duration, seed, max_steps=10):
     return out
 
 
-def admit(systems, model_params, budget_bytes):
-    """Indices of the systems admitted by the device-memory budget (in order)."""
-    per = bytes_per_atom(model_params)
-    used, ids = 0, []
-    for k, s in enumerate(systems):
-        need = s.n * per
-        if used + need > budget_bytes:
-            continue
-        used += need
-        ids.append(k)
-    return ids, used
+class Residency:
+    """Device-memory admission: which systems hold a table and workspace.
+
+    need[k] = bytes system k holds while resident.  A system is admitted when
+    the resident total plus its need fits the budget; otherwise idle resident
+    systems (no active or queued request) are released, least recently used
+    first, until it fits.  A system larger than the whole budget is refused
+    at construction (it could never run)."""
+
+    def __init__(self, batch, need, budget_bytes):
+        self.batch, self.need, self.budget = batch, list(need), budget_bytes
+        self.resident = collections.OrderedDict()     # system -> last use (LRU order)
+        self.used = 0
+        self.admissions = self.releases = 0
+        too_big = [k for k, b in enumerate(self.need) if budget_bytes is not None and b > budget_bytes]
+        if too_big:
+            raise ValueError(f"systems {too_big} need more than the whole budget of {budget_bytes} bytes")
+
+    def admit(self, k, busy):
+        """True when system k is (now) resident; busy = systems that must stay."""
+        if k in self.resident:
+            self.resident.move_to_end(k)
+            return True
+        if self.budget is not None:
+            if self.used + self.need[k] > self.budget:
+                idle = [j for j in self.resident if j not in busy]
+                freed = sum(self.need[j] for j in idle)
+                if self.used - freed + self.need[k] > self.budget:
+                    return False                      # wait: not enough idle memory to release
+                for j in idle:
+                    if self.used + self.need[k] <= self.budget:
+                        break
+                    self.batch.release(j)
+                    self.used -= self.need[j]
+                    del self.resident[j]
+                    self.releases += 1
+        self.resident[k] = True
+        self.used += self.need[k]
+        self.admissions += 1
+        return True
 
 
-def serve_batched(batch, model, requests, dt=1.0, clock=time.perf_counter, realtime=True):
-    """Run the continuous-batching loop; returns (requests, stats)."""
+def serve_batched(batch, model, requests, dt=1.0, clock=time.perf_counter, realtime=True, residency=None):
+    """Run the continuous-batching loop; returns (requests, stats).
+    residency: a Residency (device-memory admission), or None (no budget)."""
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
     queues = collections.defaultdict(collections.deque)   # system -> waiting requests
     active = {}                                           # system -> [request, steps left]
     t0 = clock()
-    atom_steps, ticks = 0, 0
+    atom_steps, ticks, waited = 0, 0, set()
     finished = []
     while pending or queues or active:
         now = clock() - t0
-        if not realtime and not active and pending:
+        if not realtime and not active and pending and not queues:
             now = max(now, pending[0].arrival)
         while pending and pending[0].arrival <= now:
             r = pending.popleft()
             queues[r.system].append(r)
-        for sysid in list(queues):
+        for sysid in sorted(queues, key=lambda k: queues[k][0].arrival):
             if sysid not in active and queues[sysid]:
+                if residency is not None and not residency.admit(sysid, set(active) | set(queues)):
+                    waited.add(queues[sysid][0].rid)
+                    continue
                 r = queues[sysid].popleft()
                 r.start = now
                 active[sysid] = [r, r.steps]
@@ -92,6 +131,8 @@ def serve_batched(batch, model, requests, dt=1.0, clock=time.perf_counter, realt
         if not active:
             if pending and realtime:
                 time.sleep(max(0.0, min(pending[0].arrival - (clock() - t0), 0.002)))
+            elif not pending and queues:
+                raise RuntimeError("requests wait on memory that no idle system can free")
             continue
         ids = sorted(active)
         th = batch.step(model, ids, dt, 1)
@@ -108,7 +149,10 @@ def serve_batched(batch, model, requests, dt=1.0, clock=time.perf_counter, realt
                 finished.append(r)
                 del active[sysid]
     wall = clock() - t0
-    return finished, _stats(finished, atom_steps, wall, ticks)
+    st = _stats(finished, atom_steps, wall, ticks)
+    if residency is not None:
+        st.update(admissions=residency.admissions, releases=residency.releases, waited_on_memory=len(waited))
+    return finished, st
 
 
 def serve_alone(batch, model, requests, dt=1.0, clock=time.perf_counter, realtime=True):

@@ -101,6 +101,10 @@ _SIGS = {
     "tmd_batch_get_system": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "tmd_batch_compute": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, _P]),
     "tmd_batch_step": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int32, _P, _P]),
+    "tmd_batch_set_skin": (C.c_int, [_P, C.c_double, C.c_int32]),
+    "tmd_batch_release": (C.c_int, [_P, C.c_int32]),
+    "tmd_batch_table_info": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_int64)]),
     "tmd_profile_enable": (C.c_int, [C.c_int32]),
     "tmd_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
     "tmd_launch_count": (C.c_int64, []),
@@ -354,7 +358,18 @@ def evaluate(model, nl, pos, types, box, stream=None):
 def compute_noalloc(model, off, nbr, shift4, pos, types, box, energy=None, e_atom=None, forces=None, virial=None,
                     stream=None):
     """tmd_compute_noalloc: cuda tensors off [n+1] int64, nbr [nnz] int32,
-    shift4 [nnz, 4] int8 (sx, sy, sz, species of j); outputs as ``compute``."""
+    shift4 [nnz, 4] int8 (sx, sy, sz, species of j); outputs as ``compute``.
+    Shapes, dtypes and contiguity are checked here, before the library reads
+    off[n] or shift4[nnz - 1] on the device."""
+    import torch
+    n, nnz = int(pos.shape[0]), int(nbr.shape[0])
+    want = [(off, (n + 1,), torch.int64, "off"), (nbr, (nnz,), torch.int32, "nbr"),
+            (shift4, (nnz, 4), torch.int8, "shift4"), (pos, (n, 3), torch.float64, "pos"),
+            (types, (n,), torch.int32, "types")]
+    for t, shape, dtype, name in want:
+        if tuple(t.shape) != shape or t.dtype != dtype or not t.is_contiguous() or not t.is_cuda:
+            raise TmdError(ERR_INVALID_ARG, f"{name}: want a contiguous cuda {dtype} tensor of shape {shape}, "
+                                            f"got {t.dtype} {tuple(t.shape)} on {t.device}")
     check(lib().tmd_compute_noalloc(model.handle, _dptr(off), _dptr(nbr), _dptr(shift4), int(nbr.shape[0]),
                                     _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box), _dptr(energy),
                                     _dptr(e_atom), _dptr(forces), _dptr(virial), _stream(stream)))
@@ -423,8 +438,9 @@ class System:
 class Batch:
     """Many resident systems evaluated / advanced together (tmd_batch)."""
 
-    def __init__(self, systems):
-        """systems: list of inputs.System (pos, types, box, pbc, vel, masses)."""
+    def __init__(self, systems, skin=0.0, rebuild_every=0):
+        """systems: list of inputs.System (pos, types, box, pbc, vel, masses);
+        skin / rebuild_every: the resident tables' policy (tmd_batch_set_skin)."""
         S = len(systems)
         n = np.array([x.n for x in systems], dtype=np.int64)
         boxes = np.ascontiguousarray(np.array([x.box for x in systems], dtype=np.float64))
@@ -436,6 +452,21 @@ class Batch:
         self.n = n
         for k, x in enumerate(systems):
             self.set_system(k, x)
+        if skin or rebuild_every:
+            self.set_skin(skin, rebuild_every)
+
+    def set_skin(self, skin, rebuild_every=0):
+        check(lib().tmd_batch_set_skin(self.handle, float(skin), int(rebuild_every)))
+
+    def release(self, k):
+        """Give back system k's resident table (tmd_batch_release)."""
+        check(lib().tmd_batch_release(self.handle, int(k)))
+
+    def table_info(self, k):
+        """(region entries of system k, pool entries, table builds of k)."""
+        r, p, b = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().tmd_batch_table_info(self.handle, int(k), C.byref(r), C.byref(p), C.byref(b)))
+        return int(r.value), int(p.value), int(b.value)
 
     def set_system(self, k, x, stream=None):
         pos = np.ascontiguousarray(x.pos, dtype=np.float64)

@@ -133,3 +133,53 @@ def test_fp32_batch_network_small_force_systems(tmdlib, k):
     assert abs(e - o["energy"]) <= 1e-6 * abs(o["energy"])
     assert np.abs(f - o["forces"]).max() <= 1e-5 * rms
     assert np.abs(v - o["virial"]).max() <= 1e-5 * np.abs(o["virial"]).max()
+
+
+@pytest.mark.parametrize("skin,every", [(1.0, 5), (0.03, 0)])
+def test_resident_tables_follow_tmd_step(tmdlib, skin, every):
+    """Resident neighbour tables (rc + skin, rebuilt per system on the cadence
+    or by the skin criterion, Sec. "Evaluation"): every system of a batch of
+    uneven systems follows, bitwise, its own tmd_step trajectory with the same
+    table policy, and the batch counts the same table builds.  The 0.03 A skin
+    makes the skin criterion fire at different steps in different systems."""
+    w = I.serve(n_systems=6, seed=31, n_max=2000)
+    m = tmdlib.Model(w.model)
+    b = tmdlib.Batch(w.systems, skin=skin, rebuild_every=every)
+    ids = list(range(len(w.systems)))
+    nsteps = 12
+    th_b = b.step(m, ids, 1.0, nsteps)
+    rebuilds = []
+    for k, s in enumerate(w.systems):
+        sy = tmdlib.System(s.n, s.box, s.pbc, skin)
+        sy.set_state(s.pos, s.vel, s.types, s.masses)
+        th = sy.step(m, 1.0, nsteps, rebuild_every=every)
+        p, v, f = sy.get_state()
+        pb, vb, fb = b.get_system(k)
+        assert np.array_equal(p, pb) and np.array_equal(v, vb) and np.array_equal(f, fb), k
+        assert th_b[k]["rebuilds"] == th["rebuilds"], (k, th_b[k]["rebuilds"], th["rebuilds"])
+        assert abs(th_b[k]["e_pot"] - th["e_pot"]) <= 1e-9 * abs(th["e_pot"]), k
+        rebuilds.append(th["rebuilds"])
+    if every:
+        assert all(r == 1 + nsteps // every for r in rebuilds), rebuilds
+    else:
+        assert len(set(rebuilds)) > 1 and max(rebuilds) > 1, rebuilds
+
+
+def test_released_table_is_rebuilt_with_the_same_forces(tmdlib):
+    """A released system keeps its state; its next evaluation builds a new
+    table in a (reused) pool region and gives the same forces."""
+    w = I.serve(n_systems=4, seed=32, n_max=1500)
+    m = tmdlib.Model(w.model)
+    b = tmdlib.Batch(w.systems, skin=1.0, rebuild_every=0)
+    ids = list(range(len(w.systems)))
+    b.compute(m, ids)
+    f0 = [b.get_system(k)[2] for k in ids]
+    reg0, pool0, builds0 = b.table_info(1)
+    assert reg0 > 0 and pool0 >= reg0 and builds0 == 1
+    b.release(1)
+    assert b.table_info(1)[0] == 0
+    b.compute(m, [1, 3])
+    reg1, pool1, builds1 = b.table_info(1)
+    assert reg1 > 0 and builds1 == 2 and pool1 == pool0    # the released region was reused
+    for k in ids:
+        assert np.array_equal(b.get_system(k)[2], f0[k]), k

@@ -1,8 +1,8 @@
 """Launch machinery around the kernels: tile shapes (set by hand or picked by
 the autotuner) and the captured CUDA graphs of the MD and batch loops.  None
 of it may change a result: forces accumulate in fixed point and are compared
-bit for bit; energies and virials only differ in the grouping of FP64 partial
-sums."""
+bit for bit; energies differ only in the grouping of FP64 partial sums, and
+virials in that and in which pairs share a lane's FP32 sum."""
 import numpy as np
 import pytest
 
@@ -57,7 +57,9 @@ def test_tile_shapes_do_not_change_results(tmdlib, precision):
             e, f, v = _eval(tmdlib, m, nl, pos, types, s.box)
             assert np.array_equal(f, f0), (rows, bps)
             assert abs(e - e0) <= 1e-12 * abs(e0), (rows, bps)
-            assert np.abs(v - v0).max() <= 1e-9 * np.abs(v0).max(), (rows, bps)
+            # the force pass sums each lane's virial terms in FP32 between
+            # FP64 flushes, and the grid decides which pairs share a lane
+            assert np.abs(v - v0).max() <= 1e-8 * np.abs(v0).max(), (rows, bps)
 
 
 def test_autotune_keeps_a_candidate_and_the_results(tmdlib):

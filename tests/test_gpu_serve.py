@@ -33,3 +33,30 @@ def test_requests_same_alone_and_in_the_mix(tmdlib, precision):
         pb, vb, fb = alone.get_system(k)
         assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
     assert st_mix["calls"] < st_alone["calls"] * max(r.steps for r in reqs_a)
+
+
+def test_memory_admission_waits_and_matches_alone(tmdlib):
+    """A device-memory budget that holds two of three systems: the third
+    system's request waits, the system is admitted once an idle system's table
+    is released, and its trajectory equals the one it has alone."""
+    w = I.serve(n_systems=3, seed=33, n_max=1200)
+    m = tmdlib.Model(w.model)
+    per = serve.bytes_per_atom(w.model)
+    need = [int(s.n) * per for s in w.systems]
+    budget = max(need[0] + need[1], need[0] + need[2])   # never all three at once
+    assert budget < sum(need)
+    reqs = [serve.Request(0, 0, 4, 0.0), serve.Request(1, 1, 1, 0.0), serve.Request(2, 2, 2, 0.0)]
+    b = tmdlib.Batch(w.systems, skin=1.0, rebuild_every=5)
+    res = serve.Residency(b, need, budget)
+    done, st = serve.serve_batched(b, m, reqs, realtime=False, residency=res)
+    assert st["requests"] == 3 and st["waited_on_memory"] >= 1 and st["releases"] >= 1, st
+    assert res.used <= budget
+    by = {r.rid: r for r in done}
+    assert by[2].start >= by[1].done      # system 2 started after system 1 finished and was released
+    alone = tmdlib.Batch([w.systems[2]], skin=1.0, rebuild_every=5)
+    alone.step(m, [0], 1.0, 2)
+    pa, va, fa = alone.get_system(0)
+    pb, vb, fb = b.get_system(2)
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
+    with pytest.raises(ValueError):
+        serve.Residency(b, need, min(need) - 1)

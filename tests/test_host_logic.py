@@ -6,14 +6,44 @@ from paper_2310_08439_gb300 import inputs as I
 from paper_2310_08439_gb300 import serve
 
 
-def test_admission_by_memory_budget():
-    w = I.serve(n_systems=10, seed=32, n_max=3000)
-    per = serve.bytes_per_atom(w.model)
-    total = sum(s.n for s in w.systems) * per
-    ids, used = serve.admit(w.systems, w.model, total // 2)
-    assert 0 < len(ids) < len(w.systems) and used <= total // 2
-    ids, used = serve.admit(w.systems, w.model, total)
-    assert len(ids) == len(w.systems)
+class _FakeBatch:
+    """Stands in for tmd.Batch in the host-side serving logic."""
+
+    def __init__(self, n):
+        self.n = np.array(n)
+        self.released, self.ticks = [], []
+
+    def release(self, k):
+        self.released.append(k)
+
+    def step(self, model, ids, dt, nsteps):
+        self.ticks.append(list(ids))
+        return [{"e_pot": 0.0, "e_kin": 0.0, "rebuilds": 0} for _ in ids]
+
+
+def test_admission_waits_for_memory_and_releases_idle_systems():
+    """Budget 11 with needs (5, 4, 6): systems 0 and 1 fit; system 2 waits
+    until system 1 is idle, whose table is then released (system 0, still
+    busy, stays)."""
+    fb = _FakeBatch([50, 40, 60])
+    res = serve.Residency(fb, [5, 4, 6], 11)
+    reqs = [serve.Request(0, 0, 4, 0.0), serve.Request(1, 1, 1, 0.0), serve.Request(2, 2, 2, 0.0)]
+    done, st = serve.serve_batched(fb, None, reqs, realtime=False, residency=res)
+    by = {r.rid: r for r in done}
+    assert st["requests"] == 3 and st["waited_on_memory"] == 1 and fb.released == [1]
+    assert fb.ticks[0] == [0, 1] and fb.ticks[1] == [0, 2]
+    assert by[2].start >= by[1].done and res.used <= 11
+    assert st["atom_steps"] == 4 * 50 + 1 * 40 + 2 * 60
+
+
+def test_admission_refuses_a_system_larger_than_the_budget():
+    fb = _FakeBatch([50, 40])
+    try:
+        serve.Residency(fb, [5, 12], 11)
+    except ValueError as e:
+        assert "[1]" in str(e)
+    else:
+        raise AssertionError("a system larger than the budget was accepted")
 
 
 def test_poisson_requests_rate_and_ranges():

@@ -41,27 +41,45 @@ def _outputs(n):
             torch.zeros((n, 3), dtype=torch.float32, device="cuda"), torch.zeros(9, dtype=torch.float64, device="cuda"))
 
 
-@pytest.mark.parametrize("wname", ["tiny", "medium"])
-def test_noalloc_matches_compute_two_calls(tmdlib, wname):
+@pytest.mark.parametrize("wname,precision,force_kernel", [("tiny", "fp32", "auto"), ("medium", "fp32", "auto"),
+                                                         ("tiny", "bf16", "auto"), ("medium", "bf16", "auto"),
+                                                         ("tiny", "fp32", "tensor")])
+def test_noalloc_matches_compute_two_calls(tmdlib, wname, precision, force_kernel):
+    """Both network forms; with the tensor-core force pass chosen, tmd_compute
+    runs it and the allocation-free call runs the SIMT pass (it keeps no pair
+    cache), and the two still agree within the FP32 bars."""
     torch = _torch()
     w = getattr(I, wname)()
     s = w.systems[0]
     m = tmdlib.Model(w.model)
+    if precision == "bf16":
+        m.set_precision("bf16")
     nl, pos, types, off, nbr, shift4 = _table(tmdlib, s, w.model.rc + (0.0 if wname == "tiny" else 1.0))
-    ref = _outputs(s.n)
-    tmdlib.compute(m, nl, pos, types, s.box, *ref)
-    torch.cuda.synchronize()
-    rE, rEa, rF, rW = (t.double().cpu().numpy() for t in ref)
-    rms = np.sqrt((rF ** 2).mean())
-    for call in range(2):
-        out = _outputs(s.n)
-        tmdlib.compute_noalloc(m, off, nbr, shift4, pos, types, s.box, *out)
+    tmdlib.set_force_kernel(force_kernel)
+    try:
+        ref = _outputs(s.n)
+        tmdlib.compute(m, nl, pos, types, s.box, *ref)
         torch.cuda.synchronize()
-        E, Ea, F, W = (t.double().cpu().numpy() for t in out)
-        assert abs(E[0] - rE[0]) <= E_TOL * abs(rE[0]), call
-        assert np.abs(F - rF).max() <= F_TOL * rms, call
-        assert np.abs(W - rW).max() <= W_TOL * np.abs(rW).max(), call
-        assert np.abs(Ea - rEa).max() <= 1e-5 * np.abs(rEa).max(), call
+        rE, rEa, rF, rW = (t.double().cpu().numpy() for t in ref)
+        rms = np.sqrt((rF ** 2).mean())
+        for call in range(2):
+            out = _outputs(s.n)
+            tmdlib.compute_noalloc(m, off, nbr, shift4, pos, types, s.box, *out)
+            torch.cuda.synchronize()
+            E, Ea, F, W = (t.double().cpu().numpy() for t in out)
+            # The caller's table is the exported one, sorted per atom, so the
+            # descriptor sums run in another order than tmd_compute's; FP32
+            # results agree to rounding, while in the BF16 form a descriptor
+            # that rounds to the neighbouring BF16 value moves that atom's
+            # energy and forces by a few 1e-3 relative (the BF16 form's own
+            # error against the oracle is ~1e-2 of RMS(F)).
+            et, ft, wt, at = (E_TOL, F_TOL, W_TOL, 1e-5) if precision == "fp32" else (1e-5, 1e-2, 1e-3, 1e-2)
+            assert abs(E[0] - rE[0]) <= et * abs(rE[0]), call
+            assert np.abs(F - rF).max() <= ft * rms, call
+            assert np.abs(W - rW).max() <= wt * np.abs(rW).max(), call
+            assert np.abs(Ea - rEa).max() <= at * np.abs(rEa).max(), call
+    finally:
+        tmdlib.set_force_kernel("auto")
 
 
 def test_noalloc_rejects_oversized_and_bad_tables(tmdlib):
@@ -87,6 +105,30 @@ def test_noalloc_rejects_oversized_and_bad_tables(tmdlib):
         tmdlib.compute_noalloc(m, off, nbr, bad, pos, types, s.box, *_outputs(s.n))
     assert e.value.status == tmdlib.ERR_INVALID_ARG
     # and a good table still works afterwards
+    out = _outputs(s.n)
+    tmdlib.compute_noalloc(m, off, nbr, shift4, pos, types, s.box, *out)
+    torch.cuda.synchronize()
+    assert np.isfinite(out[0].item())
+
+
+def test_noalloc_rejects_mismatched_species_and_bad_shapes(tmdlib):
+    """A species byte that is a valid species but not that of j is rejected on
+    the device (check code 16); tensors of the wrong shape or dtype are
+    rejected by the binding before the library reads them."""
+    torch = _torch()
+    w = I.medium()       # two species
+    s = w.systems[0]
+    m = tmdlib.Model(w.model)
+    nl, pos, types, off, nbr, shift4 = _table(tmdlib, s, w.model.rc)
+    bad = shift4.clone()
+    bad[7, 3] = 1 - bad[7, 3]
+    with pytest.raises(tmdlib.TmdError) as e:
+        tmdlib.compute_noalloc(m, off, nbr, bad, pos, types, s.box, *_outputs(s.n))
+    assert e.value.status == tmdlib.ERR_INVALID_ARG and "16" in str(e.value)
+    for args in [(off[:-1], nbr, shift4), (off, nbr, shift4[:, :3].contiguous()), (off.int(), nbr, shift4)]:
+        with pytest.raises(tmdlib.TmdError) as e:
+            tmdlib.compute_noalloc(m, *args, pos, types, s.box, *_outputs(s.n))
+        assert e.value.status == tmdlib.ERR_INVALID_ARG
     out = _outputs(s.n)
     tmdlib.compute_noalloc(m, off, nbr, shift4, pos, types, s.box, *out)
     torch.cuda.synchronize()
