@@ -600,6 +600,40 @@ def nve_run(tmd, torch, total_steps, every, rebuild_every, precision="fp32"):
             "max_abs_drift_per_atom_eV": float(np.abs(e - e[0]).max()), "trace": rows}
 
 
+def decompose_run(args, tmd, torch, dist, rank, world):
+    """Strong scaling of one system over the ranks (the paper's spatial
+    decomposition): the large lattice cut into slabs along x; per evaluation
+    every rank exchanges its ghost halo (rc wide), builds its table and runs
+    tmd_compute_owned, hands the ghost forces back and all-reduces E and W.
+    Returns the JSON line (rank 0)."""
+    from paper_2310_08439_gb300 import domain as Dm
+    w, desc = workload(args.config, args.reps, rebuild_every=1)
+    s = w.systems[0]
+    model = tmd.Model(w.model, precision=args.precision)
+    slabs = Dm.Slabs(s.box, s.pbc, world, w.model.rc)
+    d = Dm.split(slabs, s.pos, np.zeros_like(s.pos), s.types, s.masses)[rank]
+    comm = Dm.TorchComm(dist, device="cuda") if dist is not None else Dm.LocalComm()
+    engine = Dm.gpu_engine(tmd, model, torch, w.model.rc)
+    for _ in range(args.warmup):
+        Dm.evaluate(comm, d, engine)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, E, W = Dm.evaluate(comm, d, engine)
+    torch.cuda.synchronize()
+    t = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    value = s.n * args.steps / t
+    return {"metric": "decomposed force evaluations, atom-evals/s (one system over the ranks)", "value": value,
+            "unit": "atom-evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "atoms": s.n, "slabs": world, "halo_A": w.model.rc,
+                       "owned_atoms_rank0": int(d.n)},
+            "energy": E}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -655,6 +689,9 @@ def main():
     ap.add_argument("--nve", default="",
                     help="instead of the bench line: 'STEPS,EVERY' of an NVE run of the large lattice, total energy "
                          "per atom every EVERY steps (table cadence from --rebuild-every)")
+    ap.add_argument("--decompose", action="store_true",
+                    help="instead of the bench line: one system split into slabs over the ranks (strong scaling "
+                         "of the decomposed force evaluation; ghost halo and reverse force exchange)")
     ap.add_argument("--force-kernel", default="auto", choices=["auto", "simt", "tensor"],
                     help="force pass of the unbatched evaluation (tmd_set_force_kernel)")
     args = ap.parse_args()
@@ -685,6 +722,13 @@ def main():
             steps_n, every = (int(x) for x in args.nve.split(","))
             print(json.dumps({"nve": nve_run(tmd, torch, steps_n, every, args.rebuild_every, args.precision)}),
                   flush=True)
+        return
+    if args.decompose:
+        line = decompose_run(args, tmd, torch, dist, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
         return
     if args.size_sweep:
         if rank == 0:

@@ -314,6 +314,25 @@ tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
                        double *virial, tmd_stream_t stream);
 
 /*
+ * tmd_compute for one domain of a spatially decomposed system (the paper's
+ * MPI decomposition, Sec. "Evaluation": each process evaluates the atoms of
+ * its own domain with ghost copies of its neighbours' atoms).  Atoms
+ * [0, n_owned) are owned centres; atoms [n_owned, n) are ghosts: copies of
+ * other domains' atoms within the table radius of this domain, placed at the
+ * image positions they have next to it.  Ghosts are neighbours of the centres
+ * only: they have no energy term here (e_atom 0), and forces[ghost] holds the
+ * ghost's share of the pair forces of this domain's centres, which the caller
+ * adds to the forces of the atom the ghost copies (reverse exchange).
+ * energy and virial sum over the owned centres, so the totals over domains
+ * are those of the whole system.  Table and other arguments as tmd_compute
+ * (the table is built over all n atoms).  Synchronises once (owned atoms per
+ * species).  Errors: as tmd_compute; INVALID_ARG for n_owned outside [0, n].
+ */
+tmd_status tmd_compute_owned(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                             int64_t n, int64_t n_owned, const double box[3], double *energy, float *e_atom,
+                             float *forces, double *virial, tmd_stream_t stream);
+
+/*
  * Descriptor matrix G_abkm = sigma(T_dm (H_abck M_abcd)^2) (Eqs.
  * tensor_formalism, sigma_function), written to G dev [n][Dd] FP32, row a,
  * column ((b*K) + k)*4 + m.  When dEdG (dev [n][Dd] FP32) is non-NULL the

@@ -862,6 +862,15 @@ tmd_status tmd_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     return run_compute(model, nl, pos, types, n, box, energy, e_atom, forces, virial, (cudaStream_t)stream);
 }
 
+tmd_status tmd_compute_owned(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
+                             int64_t n_owned, const double box[3], double *energy, float *e_atom, float *forces,
+                             double *virial, tmd_stream_t stream) {
+    g_err[0] = 0;
+    if (!model || !nl || !box) { set_error("null model, table or box"); return TMD_ERR_INVALID_ARG; }
+    return run_compute_owned(model, nl, pos, types, n, n_owned, box, energy, e_atom, forces, virial,
+                             (cudaStream_t)stream);
+}
+
 tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                            int64_t n, const double box[3], float *G, float *dEdG, tmd_stream_t stream) {
     g_err[0] = 0;

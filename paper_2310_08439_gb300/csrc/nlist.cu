@@ -736,7 +736,8 @@ tmd_status scan_inclusive(T *data, int64_t n, int64_t **tmp, int64_t *cap_tmp, c
 void nlist_free(tmd_nlist *nl) {
     void *ptrs[] = {nl->cell_of, nl->cell_atoms, nl->cell_pos, nl->perm, nl->beg, nl->end, nl->counter, nl->sp, nl->cell_sys, nl->todo, nl->todo_count, nl->cell_start, nl->cell_fill, nl->nbr, nl->shift, nl->status, nl->type_block,
                     nl->type_start, nl->scan_tmp, nl->G, nl->dG, nl->P, nl->Fq, nl->part, nl->ph, nl->pl,
-                    nl->io_pos, nl->io_types, nl->io_forces, nl->io_red, nl->pq, nl->pq2, nl->npair};
+                    nl->io_pos, nl->io_types, nl->io_forces, nl->io_red, nl->pq, nl->pq2, nl->npair,
+                    nl->perm_own, nl->own_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (nl->h_pinned) cudaFreeHost(nl->h_pinned);

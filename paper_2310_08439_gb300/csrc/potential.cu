@@ -1025,6 +1025,92 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     return TMD_OK;
 }
 
+// owned atoms [0, n_owned) per species
+__global__ void k_count_species(const int32_t *__restrict__ types, int64_t n_owned, int32_t *__restrict__ count) {
+    __shared__ int32_t c[TMD_MAX_SPECIES];
+    if (threadIdx.x < TMD_MAX_SPECIES) c[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_owned; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&c[types[i]], 1);
+    __syncthreads();
+    if (threadIdx.x < TMD_MAX_SPECIES) atomicAdd(&count[threadIdx.x], c[threadIdx.x]);
+}
+
+// The centres are the owned atoms [0, n_owned); atoms [n_owned, n) are ghosts
+// (copies of other domains' atoms within the list radius of this one): they
+// are neighbours of the centres, hold no energy term of their own, and
+// receive their share of the pair forces, which the caller hands back to the
+// domains that own them.  The table's perm groups atoms by species in index
+// order, so the owned atoms of species t are the first owned-count[t] of
+// block t.
+tmd_status run_compute_owned(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                             int64_t n, int64_t n_owned, const double box[3], double *energy, float *e_atom,
+                             float *forces, double *virial, cudaStream_t s) {
+    tmd_status st = validate(model, nl, n, box);
+    if (st != TMD_OK) return st;
+    if (n_owned < 0 || n_owned > n) {
+        set_error("n_owned = %lld outside [0, %lld]", (long long)n_owned, (long long)n);
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (n_owned == n) return run_compute(model, nl, pos, types, n, box, energy, e_atom, forces, virial, s);
+    const DevModel &dm = model->dm;
+    if ((st = grow(&nl->own_count, &nl->cap_own_count, TMD_MAX_SPECIES)) != TMD_OK) return st;
+    if ((st = grow(&nl->perm_own, &nl->cap_perm_own, std::max<int64_t>(n_owned, 1))) != TMD_OK) return st;
+    TMD_CUDA(cudaMemsetAsync(nl->own_count, 0, sizeof(int32_t) * TMD_MAX_SPECIES, s));
+    if (n_owned > 0)
+        TMD_LAUNCH("k_count_species", s, k_count_species<<<(unsigned)std::min<int64_t>((n_owned + 255) / 256, 1024), 256, 0,
+                                                           s>>>(types, n_owned, nl->own_count));
+    TMD_CUDA(cudaGetLastError());
+    int32_t own[TMD_MAX_SPECIES];
+    TMD_CUDA(cudaMemcpyAsync(own, nl->own_count, sizeof(own), cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    int64_t src = 0, dst = 0;
+    for (int t = 0; t < TMD_MAX_SPECIES; ++t) {
+        if (own[t] > 0)
+            TMD_CUDA(cudaMemcpyAsync(nl->perm_own + dst, nl->perm + src, sizeof(int32_t) * own[t],
+                                     cudaMemcpyDeviceToDevice, s));
+        dst += own[t];
+        src += nl->type_count[t];
+    }
+    if (dst != n_owned) {
+        set_error("owned atoms per species do not add up to n_owned");
+        return TMD_ERR_INVALID_ARG;
+    }
+    if (e_atom) TMD_CUDA(cudaMemsetAsync(e_atom, 0, sizeof(float) * n, s));
+    if (n_owned == 0) {
+        if (energy) TMD_CUDA(cudaMemsetAsync(energy, 0, sizeof(double), s));
+        if (virial) TMD_CUDA(cudaMemsetAsync(virial, 0, 9 * sizeof(double), s));
+        if (forces) TMD_CUDA(cudaMemsetAsync(forces, 0, sizeof(float) * 3 * n, s));
+        return TMD_OK;
+    }
+    if ((st = reserve_compute(dm, nl, n, n_owned)) != TMD_OK) return st;
+    const int nblk = pair_blocks(dm, n_owned);
+    const int ntile = (int)((n_owned + MT - 1) / MT);
+    double *part_e = nl->part;
+    double *part_w = nl->part + ntile;
+    if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
+    DevNlist dn = dev_nlist(nl, n_owned, box);
+    dn.perm = nl->perm_own;
+    dn.pq = nl->pq;
+    dn.pq2 = nl->pq2;
+    dn.npair = nl->npair;
+    TMD_CUDA(cudaMemsetAsync(nl->Fq, 0, sizeof(long long) * 3 * n, s));
+    if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, true)) != TMD_OK) return st;
+    int ne = 0;
+    if ((st = launch_network(dm, nl->perm_own, types, n_owned, nl->G, nl->dG, e_atom, part_e, &ne, s)) != TMD_OK)
+        return st;
+    if ((st = dispatch_pair(dm, dn, pos, types, nl, part_w, nblk, s, false)) != TMD_OK) return st;
+    TMD_LAUNCH("k_reduce", s, k_reduce_part<<<RED_BLOCKS, 256, 0, s>>>(part_e, ne, part_w, nblk, part_w + 9 * (size_t)nblk + 16));
+    TMD_LAUNCH("k_reduce", s, k_reduce<<<1, 32, 0, s>>>(part_w + 9 * (size_t)nblk + 16, energy, virial));
+    TMD_CUDA(cudaGetLastError());
+    if (forces) {
+        TMD_LAUNCH("k_forces_out", s, k_forces_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(
+                                           reinterpret_cast<const long long *>(nl->Fq), n, forces));
+        TMD_CUDA(cudaGetLastError());
+    }
+    return TMD_OK;
+}
+
 }  // namespace tmd
 
 // ---------------------------------------------------------------------------

@@ -179,6 +179,8 @@ struct tmd_nlist {
     float4 *pq = nullptr;     int64_t cap_pq = 0;   // [nnz] in-cutoff pair cache (geometry)
     float2 *pq2 = nullptr;    int64_t cap_pq2 = 0;  // [nnz] r^2 hi / lo
     int32_t *npair = nullptr; int64_t cap_npair = 0; // [n] in-cutoff pairs per atom
+    int32_t *perm_own = nullptr; int64_t cap_perm_own = 0; // [n_owned] evaluation order of owned centres
+    int32_t *own_count = nullptr; int64_t cap_own_count = 0; // [MAX_SPECIES] owned atoms per species
 
     // staging for the host-buffer entry point
     double *io_pos = nullptr;   int64_t cap_io_pos = 0;
@@ -325,6 +327,11 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
                        double *virial, cudaStream_t s);
 tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                            int64_t n, const double box[3], float *G, float *dEdG, cudaStream_t s);
+// tmd_compute with atoms [n_owned, n) as ghosts: neighbours only, no energy
+// term of their own (domain decomposition)
+tmd_status run_compute_owned(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
+                             int64_t n, int64_t n_owned, const double box[3], double *energy, float *e_atom,
+                             float *forces, double *virial, cudaStream_t s);
 tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const int32_t *nbr, const int8_t *shift4,
                                int64_t nnz, const double *pos, const int32_t *types, int64_t n, const double box[3],
                                double *energy, float *e_atom, float *forces, double *virial, cudaStream_t s);

@@ -102,6 +102,8 @@ _SIGS = {
     "tmd_batch_compute": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, _P]),
     "tmd_batch_step": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int32, _P, _P]),
     "tmd_batch_set_skin": (C.c_int, [_P, C.c_double, C.c_int32]),
+    "tmd_compute_owned": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.POINTER(C.c_double), _P, _P, _P, _P,
+                                    _P]),
     "tmd_batch_release": (C.c_int, [_P, C.c_int32]),
     "tmd_batch_table_info": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                        C.POINTER(C.c_int64)]),
@@ -322,6 +324,14 @@ def compute(model, nl, pos, types, box, energy=None, e_atom=None, forces=None, v
     """tmd_compute into caller-provided cuda tensors (any may be None)."""
     check(lib().tmd_compute(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]), _box(box),
                             _dptr(energy), _dptr(e_atom), _dptr(forces), _dptr(virial), _stream(stream)))
+
+
+def compute_owned(model, nl, pos, types, n_owned, box, energy=None, e_atom=None, forces=None, virial=None,
+                  stream=None):
+    """tmd_compute_owned: atoms [0, n_owned) are centres, the rest ghosts."""
+    check(lib().tmd_compute_owned(model.handle, nl.handle, _dptr(pos), _dptr(types), int(pos.shape[0]),
+                                  int(n_owned), _box(box), _dptr(energy), _dptr(e_atom), _dptr(forces),
+                                  _dptr(virial), _stream(stream)))
 
 
 def autotune(model, nl, pos, types, box, stream=None):
