@@ -396,6 +396,26 @@ def graphs_measure(tmd, torch, steps=60):
         out["graphs" if graphs else "eager"] = {"value": s.n * steps / (ms * 1e-3), "unit": UNIT,
                                                "ms_per_step": ms / steps, "replays": tmd.graph_replays() - r0}
     tmd.set_graphs(True)
+    # many steps per call: runs of steps decided on the device (tmd_step),
+    # with the paper's cadence (table every 5 steps) and with the skin
+    # criterion alone
+    for every, name in ((5, "runs_every_5"), (0, "runs_skin_criterion")):
+        g = tmd.System(s.n, s.box, s.pbc, skin=w.skin)
+        g.set_state(s.pos, s.vel, s.types, s.masses, stream=side)
+        g.step(m, w.dt_fs, 12, rebuild_every=every, stream=side, thermo=False)   # captures
+        side.synchronize()
+        c0 = g.counters()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nsteps = 10 * steps
+        e0.record(side)
+        g.step(m, w.dt_fs, nsteps, rebuild_every=every, stream=side, thermo=False)
+        e1.record(side)
+        side.synchronize()
+        ms = e0.elapsed_time(e1)
+        c1 = g.counters()
+        out[name] = {"value": s.n * nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / nsteps,
+                     "steps": nsteps, "runs": c1["runs"] - c0["runs"], "reruns": c1["reruns"] - c0["reruns"],
+                     "rebuilds": c1["rebuilds"] - c0["rebuilds"]}
     return out
 
 

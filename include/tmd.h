@@ -421,6 +421,11 @@ tmd_status tmd_system_set_state(tmd_system *sys, const double *pos, const double
  * skips); on_device as above.  Synchronises the stream. */
 tmd_status tmd_system_get_state(const tmd_system *sys, double *pos, double *vel, float *forces,
                                 int32_t on_device, tmd_stream_t stream);
+/* Host outputs (NULL skips): steps taken, table builds, runs of steps
+ * completed as one launch sequence, and runs undone and stepped again one
+ * step at a time (see tmd_step).  No GPU work. */
+tmd_status tmd_system_counters(const tmd_system *sys, int64_t *steps, int64_t *rebuilds, int64_t *runs,
+                               int64_t *reruns);
 
 /*
  * Advance nsteps velocity-Verlet steps of dt_fs femtoseconds:
@@ -432,8 +437,18 @@ tmd_status tmd_system_get_state(const tmd_system *sys, double *pos, double *vel,
  *   table's image shifts refer to the positions at the last build.
  * (a = F/m * 1/103.6427 converts eV/(A amu) to A/fs^2.)  The first call after
  * set_state also computes the initial forces.  thermo (host, may be NULL)
- * receives the state after the last step.  Synchronises the stream once per
- * step (to read the rebuild flag).  Errors: as tmd_neighbors / tmd_compute.
+ * receives the state after the last step.
+ * With a skin and graphs on (tmd_set_graphs), steps run in runs decided on
+ * the device: with rebuild_every > 0 from a cadence step to the step before
+ * the next one (up to 16 steps), otherwise 16 steps at a time; a run is one
+ * launch sequence (a captured graph on a non-default stream) whose cadence
+ * rebuild runs on the device, and the host reads the skin flags of its steps
+ * and the table's status once at the end.  A run in which an atom moved more
+ * than skin/2 before a rebuild was due, or whose table overflowed, is undone
+ * (its state was copied aside first) and stepped again one step at a time,
+ * the host reading the skin flag after each step, so every trajectory is the
+ * one that step-by-step path gives.  Steps outside runs synchronise once per
+ * step.  Errors: as tmd_neighbors / tmd_compute.
  */
 tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32_t nsteps,
                     int32_t rebuild_every, tmd_thermo *thermo, tmd_stream_t stream);

@@ -137,7 +137,9 @@ __global__ void k_vv_first(double *__restrict__ pos, double *__restrict__ vel, c
         const double d = p - pos_ref[3 * i + x];
         d2 += d * d;
     }
-    if (d2 > lim2) atomicOr(flag, 1);
+    // bit 0: moved more than skin/2 (rebuild); bit 1: more than 0.7 skin/2
+    // (close to it: the step loop stops running steps ahead, see tmd_step)
+    if (d2 > 0.49 * lim2) atomicOr(flag, d2 > lim2 ? 3 : 2);
 }
 
 // Wrap positions into [0, L) on periodic axes (before a neighbour rebuild).
@@ -954,6 +956,10 @@ tmd_status tmd_system_create(int64_t n, const double box[3], const int32_t pbc[3
 
 tmd_status tmd_system_destroy(tmd_system *sys) {
     if (!sys) return TMD_OK;
+    void *sp_[] = {sys->snap_pos, sys->snap_vel, sys->snap_forces, sys->run_flags};
+    for (void *q : sp_)
+        if (q) cudaFree(q);
+    if (sys->h_run) cudaFreeHost(sys->h_run);
     void *p[] = {sys->pos, sys->vel, sys->pos_ref, sys->inv_mass, sys->mass, sys->types, sys->forces, sys->red,
                  sys->part};
     for (void *q : p)
@@ -1028,6 +1034,161 @@ static tmd_status rebuild_and_compute(const tmd_model *model, tmd_system *sys, b
                        sys->red + 1, s);
 }
 
+// One velocity-Verlet step with the table policy, deciding on the host
+// (reads the skin flag back unless the cadence already asks for a rebuild).
+static tmd_status step_eager(const tmd_model *model, tmd_system *sys, double dt_fs, int32_t rebuild_every,
+                             cudaStream_t s) {
+    tmd_status st;
+    const int64_t n = sys->n;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    int32_t *flag = reinterpret_cast<int32_t *>(sys->red + 20);
+    const double lim = 0.5 * sys->skin;
+    TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n,
+                                                              dt_fs, sys->pos_ref, lim * lim, flag));
+    TMD_CUDA(cudaGetLastError());
+    sys->step++;
+    bool rebuild = sys->need_rebuild || (rebuild_every > 0 && (sys->step % rebuild_every) == 0);
+    if (!rebuild) {
+        TMD_CUDA(cudaMemcpyAsync(sys->h_red + 20, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TMD_CUDA(cudaStreamSynchronize(s));
+        int32_t f = 0;
+        std::memcpy(&f, sys->h_red + 20, sizeof(int32_t));
+        rebuild = (f & 1) != 0;
+    }
+    if (rebuild && (st = rebuild_only(model, sys, s)) != TMD_OK) return st;
+    if (rebuild) sys->near_skin = 0;
+    // force evaluation and second half kick: one captured graph per table layout
+    if ((st = reserve_compute(model->dm, &sys->nl, n, n)) != TMD_OK) return st;
+    std::vector<uintptr_t> key;
+    model_key(model, key);
+    nlist_key(sys->nl, key);
+    const void *sp[] = {sys->pos, sys->vel, sys->types, sys->forces, sys->red, sys->inv_mass};
+    for (const void *q : sp) key.push_back((uintptr_t)q);
+    key.push_back((uintptr_t)n);
+    key.push_back(bits_of(dt_fs));
+    for (int x = 0; x < 3; ++x) key.push_back(bits_of(sys->box[x]));
+    return graphed(sys->g_step, key, s, [&]() {
+        tmd_status st2 = run_compute(model, &sys->nl, sys->pos, sys->types, sys->n, sys->box, sys->red, nullptr,
+                                     sys->forces, sys->red + 1, s);
+        if (st2 != TMD_OK) return st2;
+        TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
+        TMD_CUDA(cudaGetLastError());
+        return TMD_OK;
+    });
+}
+
+constexpr int RUN_MAX = 16;   // steps per launch sequence when no cadence sets the length
+
+// k steps as one launch sequence with no host decision in between: the state
+// is copied aside first; with a cadence the run starts on a cadence step,
+// whose rebuild runs on the device (build_tables device_only), and every
+// other step records its skin check in its own flag.  The flags, the table's
+// entry counter and its status are read once at the end.  A run in which an
+// atom moved more than skin / 2 before a rebuild was due, or whose table
+// overflowed, is undone and stepped again on the host-decided path, so the
+// trajectory is always the one that path gives.
+static tmd_status step_run(const tmd_model *model, tmd_system *sys, double dt_fs, int k, bool rebuild_first,
+                           cudaStream_t s, bool *redo) {
+    tmd_status st;
+    *redo = false;
+    const int64_t n = sys->n;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const double lim = 0.5 * sys->skin;
+    if (!sys->snap_pos) {
+        cudaError_t e = cudaMalloc(&sys->snap_pos, sizeof(double) * 3 * n);
+        if (e == cudaSuccess) e = cudaMalloc(&sys->snap_vel, sizeof(double) * 3 * n);
+        if (e == cudaSuccess) e = cudaMalloc(&sys->snap_forces, sizeof(float) * 3 * n);
+        if (e == cudaSuccess) e = cudaMalloc(&sys->run_flags, sizeof(int32_t) * RUN_MAX);
+        if (e == cudaSuccess) e = cudaMallocHost(&sys->h_run, sizeof(int64_t) * (RUN_MAX + 4));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("run state: %s", cudaGetErrorString(e));
+            return TMD_ERR_OOM;
+        }
+    }
+    if ((st = reserve_compute(model->dm, &sys->nl, n, n)) != TMD_OK) return st;
+    tmd_nlist *nl = &sys->nl;
+    SysParams q;
+    int64_t ncell = 0;
+    if (rebuild_first &&
+        (st = make_sys_params(sys->box, sys->pbc, (double)model->dm.rc + sys->skin, &q, &ncell)) != TMD_OK)
+        return st;
+    std::vector<uintptr_t> key;
+    model_key(model, key);
+    nlist_key(*nl, key);
+    const void *sp[] = {sys->pos, sys->vel, sys->types, sys->forces, sys->red, sys->inv_mass, sys->snap_pos};
+    for (const void *p : sp) key.push_back((uintptr_t)p);
+    key.push_back((uintptr_t)n);
+    key.push_back((uintptr_t)k);
+    key.push_back((uintptr_t)rebuild_first);
+    key.push_back(bits_of(dt_fs));
+    key.push_back(bits_of(sys->skin));
+    for (int x = 0; x < 3; ++x) key.push_back(bits_of(sys->box[x]));
+    st = graphed(sys->g_run, key, s, [&]() {
+        TMD_CUDA(cudaMemcpyAsync(sys->snap_pos, sys->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+        TMD_CUDA(cudaMemcpyAsync(sys->snap_vel, sys->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+        TMD_CUDA(cudaMemcpyAsync(sys->snap_forces, sys->forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, s));
+        TMD_CUDA(cudaMemsetAsync(sys->run_flags, 0, sizeof(int32_t) * RUN_MAX, s));
+        for (int j = 0; j < k; ++j) {
+            TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass,
+                                                                      n, dt_fs, sys->pos_ref, lim * lim,
+                                                                      sys->run_flags + j));
+            if (j == 0 && rebuild_first) {
+                TMD_LAUNCH("k_wrap", s, k_wrap<<<nb, 256, 0, s>>>(sys->pos, n, sys->box[0], sys->box[1], sys->box[2],
+                                                                  sys->pbc[0], sys->pbc[1], sys->pbc[2]));
+                tmd_status b = build_tables(sys->pos, sys->types, n, 1, &q, nullptr, nullptr, nullptr, ncell, nl, s,
+                                            true);
+                if (b != TMD_OK) return b;
+                TMD_CUDA(cudaMemcpyAsync(sys->pos_ref, sys->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+            }
+            tmd_status c = run_compute(model, nl, sys->pos, sys->types, n, sys->box, sys->red, nullptr, sys->forces,
+                                       sys->red + 1, s);
+            if (c != TMD_OK) return c;
+            TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
+            TMD_CUDA(cudaGetLastError());
+        }
+        return TMD_OK;
+    });
+    if (st != TMD_OK) return st;
+    TMD_CUDA(cudaMemcpyAsync(sys->h_run, sys->run_flags, sizeof(int32_t) * RUN_MAX, cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaMemcpyAsync(sys->h_run + RUN_MAX / 2, nl->counter, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaMemcpyAsync(sys->h_run + RUN_MAX / 2 + 1, nl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TMD_CUDA(cudaStreamSynchronize(s));
+    int32_t flags[RUN_MAX];
+    std::memcpy(flags, sys->h_run, sizeof(flags));
+    bool moved = false, near = false;
+    for (int j = rebuild_first ? 1 : 0; j < k; ++j) {
+        moved = moved || (flags[j] & 1) != 0;
+        near = near || (flags[j] & 2) != 0;
+    }
+    bool bad_table = false;
+    if (rebuild_first) {
+        int32_t status = 0;
+        std::memcpy(&status, sys->h_run + RUN_MAX / 2 + 1, sizeof(int32_t));
+        bad_table = sys->h_run[RUN_MAX / 2] > std::min(nl->cap_nnz, nl->cap_shift) || status != 0;
+    }
+    if (moved || bad_table) {   // undo: back to the state at the start of the run
+        TMD_CUDA(cudaMemcpyAsync(sys->pos, sys->snap_pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+        TMD_CUDA(cudaMemcpyAsync(sys->vel, sys->snap_vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+        TMD_CUDA(cudaMemcpyAsync(sys->forces, sys->snap_forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, s));
+        if (bad_table) sys->need_rebuild = 1;   // the host-decided path rebuilds with room for every entry
+        sys->reruns++;
+        *redo = true;
+        return TMD_OK;
+    }
+    if (rebuild_first) {
+        sys->rebuilds++;
+        sys->need_rebuild = 0;
+    }
+    // an atom came close to skin/2: step one at a time until the next rebuild
+    // (instead of running ahead into a run that would be undone)
+    sys->near_skin = near ? 1 : 0;
+    sys->step += k;
+    sys->runs++;
+    return TMD_OK;
+}
+
 tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32_t nsteps, int32_t rebuild_every,
                     tmd_thermo *thermo, tmd_stream_t stream) {
     g_err[0] = 0;
@@ -1036,47 +1197,43 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
     cudaStream_t s = (cudaStream_t)stream;
     tmd_status st;
     const int64_t n = sys->n;
-    const unsigned nb = (unsigned)((n + 255) / 256);
-    int32_t *flag = reinterpret_cast<int32_t *>(sys->red + 20);
     if (!sys->have_forces) {
         if ((st = rebuild_and_compute(model, sys, true, s)) != TMD_OK) return st;
         sys->have_forces = 1;
     }
-    const double lim = 0.5 * sys->skin;
-    for (int it = 0; it < nsteps; ++it) {
-        TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
-        TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n,
-                                                                  dt_fs, sys->pos_ref, lim * lim, flag));
-        TMD_CUDA(cudaGetLastError());
-        sys->step++;
-        bool rebuild = sys->need_rebuild || (rebuild_every > 0 && (sys->step % rebuild_every) == 0);
-        if (!rebuild) {
-            TMD_CUDA(cudaMemcpyAsync(sys->h_red + 20, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            TMD_CUDA(cudaStreamSynchronize(s));
-            int32_t f = 0;
-            std::memcpy(&f, sys->h_red + 20, sizeof(int32_t));
-            rebuild = f != 0;
+    // Runs of steps as one launch sequence where they are exact: with a
+    // cadence, from a cadence step up to the step before the next one; with
+    // the skin criterion alone, RUN_MAX steps at a time.  The rest, and every
+    // run that had to be undone, step one at a time with the host reading the
+    // skin flag.
+    const bool runs = g_graphs && sys->skin > 0.0 && (rebuild_every == 0 || rebuild_every <= RUN_MAX);
+    int it = 0;
+    while (it < nsteps) {
+        const int64_t next = sys->step + 1;
+        int k = 0;
+        bool rebuild_first = false;
+        if (runs && !sys->need_rebuild && sys->nl.built && (!sys->near_skin || rebuild_every > 0)) {
+            if (rebuild_every > 0 && next % rebuild_every == 0 && nsteps - it >= rebuild_every) {
+                k = rebuild_every;
+                rebuild_first = true;
+            } else if (rebuild_every == 0 && nsteps - it >= 2) {
+                k = std::min(RUN_MAX, nsteps - it);
+            }
         }
-        if (rebuild && (st = rebuild_only(model, sys, s)) != TMD_OK) return st;
-        // force evaluation and second half kick: one captured graph per table layout
-        if ((st = reserve_compute(model->dm, &sys->nl, n, n)) != TMD_OK) return st;
-        std::vector<uintptr_t> key;
-        model_key(model, key);
-        nlist_key(sys->nl, key);
-        const void *sp[] = {sys->pos, sys->vel, sys->types, sys->forces, sys->red, sys->inv_mass};
-        for (const void *q : sp) key.push_back((uintptr_t)q);
-        key.push_back((uintptr_t)n);
-        key.push_back(bits_of(dt_fs));
-        for (int x = 0; x < 3; ++x) key.push_back(bits_of(sys->box[x]));
-        st = graphed(sys->g_step, key, s, [&]() {
-            tmd_status st2 = run_compute(model, &sys->nl, sys->pos, sys->types, sys->n, sys->box, sys->red, nullptr,
-                                         sys->forces, sys->red + 1, s);
-            if (st2 != TMD_OK) return st2;
-            TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
-            TMD_CUDA(cudaGetLastError());
-            return TMD_OK;
-        });
-        if (st != TMD_OK) return st;
+        if (k > 0) {
+            bool redo = false;
+            if ((st = step_run(model, sys, dt_fs, k, rebuild_first, s, &redo)) != TMD_OK) return st;
+            if (!redo) {
+                it += k;
+                continue;
+            }
+            for (int j = 0; j < k; ++j)
+                if ((st = step_eager(model, sys, dt_fs, rebuild_every, s)) != TMD_OK) return st;
+            it += k;
+            continue;
+        }
+        if ((st = step_eager(model, sys, dt_fs, rebuild_every, s)) != TMD_OK) return st;
+        ++it;
     }
     if (thermo) {
         const int kb = (int)std::min<int64_t>((n + 255) / 256, 1024);
@@ -1101,6 +1258,16 @@ tmd_status tmd_step(const tmd_model *model, tmd_system *sys, double dt_fs, int32
         thermo->step = sys->step;
         thermo->rebuilds = sys->rebuilds;
     }
+    return TMD_OK;
+}
+
+tmd_status tmd_system_counters(const tmd_system *sys, int64_t *steps, int64_t *rebuilds, int64_t *runs,
+                               int64_t *reruns) {
+    if (!sys) { set_error("null system"); return TMD_ERR_INVALID_ARG; }
+    if (steps) *steps = sys->step;
+    if (rebuilds) *rebuilds = sys->rebuilds;
+    if (runs) *runs = sys->runs;
+    if (reruns) *reruns = sys->reruns;
     return TMD_OK;
 }
 

@@ -230,6 +230,7 @@ __device__ __forceinline__ int wrap_cell(int u, int nc, int &k) {
 
 struct NbrParams {
     const int32_t *todo;  // per-atom pass: atoms to list (nullptr = all n)
+    const unsigned long long *todo_n;  // per-atom pass: their count on the device (nullptr = n)
     const double *pos;
     const int32_t *cell_of;
     const int32_t *cell_start;
@@ -294,13 +295,8 @@ __device__ __forceinline__ void emit_entries(const NbrParams &p, int64_t i, cons
 
 // Per-atom pass (one warp per atom walks its own stencil): used for the atoms
 // of cells whose stencil is too large for the cell-cooperative pass.
-__global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
-    extern __shared__ uint64_t s_keys[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * NBR_WARPS + warp;
-    if (w >= p.n) return;
+__device__ __forceinline__ void nbr_atom(const NbrParams &p, int64_t w, uint64_t *keys, int lane) {
     const int64_t i = p.todo ? (int64_t)p.todo[w] : w;
-    uint64_t *keys = s_keys + (size_t)warp * TMD_MAX_DEGREE;
     const int cg = p.cell_of[i];
     if (cg < 0) {  // atom of an inactive system
         if (lane == 0) { p.beg[i] = 0; p.end[i] = 0; }
@@ -371,6 +367,16 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
         }
     }
     emit_entries(p, i, keys, count, lane);
+}
+
+// One warp per atom, over a grid-stride loop: the count comes from the host
+// (p.n) or, when the host has not read it, from the device (p.todo_n).
+__global__ void __launch_bounds__(NBR_WARPS * 32) k_nbr(NbrParams p) {
+    extern __shared__ uint64_t s_keys[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n = p.todo_n ? (int64_t)*p.todo_n : p.n;
+    for (int64_t w = (int64_t)blockIdx.x * NBR_WARPS + warp; w < n; w += (int64_t)gridDim.x * NBR_WARPS)
+        nbr_atom(p, w, s_keys + (size_t)warp * TMD_MAX_DEGREE, lane);
 }
 
 // Cell-cooperative pass: one block per cell stages the cell's whole stencil
@@ -811,7 +817,11 @@ tmd_status make_sys_params(const double box[3], const int32_t pbc[3], double r_l
 
 tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int n_sys, const SysParams *sp_host,
                         const int32_t *sys_of, const uint8_t *active, const int64_t *n_of_sys, int64_t ncell_total,
-                        tmd_nlist *nl, cudaStream_t s) {
+                        tmd_nlist *nl, cudaStream_t s, bool device_only) {
+    if (device_only && (!nl->built || nl->n != n || nl->ncell != ncell_total || nl->cap_nnz < 1)) {
+        set_error("a device-only rebuild needs a table built before with the same atoms and cells");
+        return TMD_ERR_INVALID_ARG;
+    }
     if (n < 0 || n >= (int64_t(1) << 28)) {
         set_error("n = %lld outside [0, 2^28)", (long long)n);
         return TMD_ERR_INVALID_ARG;
@@ -826,7 +836,7 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     }
     nl->ncell = ncell_total;
     nl->n = n;
-    nl->built = 0;
+    if (!device_only) nl->built = 0;
     tmd_status st;
     const int64_t nb_bin = (n + BIN_THREADS - 1) / BIN_THREADS;
     if ((st = grow(&nl->cell_of, &nl->cap_atoms, n)) != TMD_OK) return st;
@@ -843,11 +853,13 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     if ((st = grow(&nl->counter, &nl->cap_counter, 1)) != TMD_OK) return st;
     if ((st = grow(&nl->sp, &nl->cap_sp, n_sys)) != TMD_OK) return st;
     if (!nl->h_pinned) TMD_CUDA(cudaMallocHost((void **)&nl->h_pinned, 16 * sizeof(int64_t)));
-    TMD_CUDA(cudaMemcpyAsync(nl->sp, sp_host, sizeof(SysParams) * n_sys, cudaMemcpyHostToDevice, s));
+    // device_only: the parameters and the capacities are those of the build
+    // before (same box, same atoms); nothing is read back here
+    if (!device_only) TMD_CUDA(cudaMemcpyAsync(nl->sp, sp_host, sizeof(SysParams) * n_sys, cudaMemcpyHostToDevice, s));
     // capacity for the entries: the previous table's size, or the uniform
     // density estimate, with headroom; a build that overflows is rerun once
     // with the exact size
-    {
+    if (!device_only) {
         double est = 0.0;
         for (int k = 0; k < n_sys; ++k) {
             const double nk = (double)(n_of_sys ? n_of_sys[k] : n);
@@ -922,6 +934,26 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const unsigned nb_cell = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ncell_total, (int64_t)std::max(nsm, 1) * 12));
+    p.todo_n = nullptr;
+    if (device_only) {
+        // the cell pass, then the per-atom pass over a device-side count; the
+        // caller checks the counter against the capacity and the status later
+        p.nbr = nl->nbr;
+        p.shift = nl->shift;
+        p.cap = std::min(nl->cap_nnz, nl->cap_shift);
+        TMD_CUDA(cudaMemsetAsync(nl->todo_count, 0, sizeof(unsigned long long), s));
+        if (n > 0) {
+            TMD_LAUNCH("k_nbr_cell", s, k_nbr_cell<<<nb_cell, CELL_WARPS * 32, smem_cell, s>>>(
+                                            p, ncell_total, cell_sys, nl->cell_atoms, nl->todo, nl->todo_count));
+            p.todo = nl->todo;
+            p.todo_n = nl->todo_count;
+            const unsigned gt = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + NBR_WARPS - 1) / NBR_WARPS,
+                                                                                 (int64_t)std::max(nsm, 1) * 2));
+            TMD_LAUNCH("k_nbr", s, k_nbr<<<gt, NBR_WARPS * 32, smem_atom, s>>>(p));
+            TMD_CUDA(cudaGetLastError());
+        }
+        return TMD_OK;
+    }
     int64_t nnz = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         p.nbr = nl->nbr;

@@ -221,6 +221,15 @@ struct tmd_system {
     int64_t step = 0, rebuilds = 0;
     int need_rebuild = 1, have_forces = 0;
     tmd::GraphCache g_step;      // force evaluation + second half kick
+    // runs of steps as one launch sequence (tmd_step): state at the start of
+    // the run (for an exact rerun), skin-check flag of each step, host mirror
+    double *snap_pos = nullptr, *snap_vel = nullptr;
+    float *snap_forces = nullptr;
+    int32_t *run_flags = nullptr;
+    int64_t *h_run = nullptr;    // pinned: flags, entry counter, status
+    tmd::GraphCache g_run;
+    int64_t runs = 0, reruns = 0;
+    int near_skin = 0;           // an atom moved more than 0.7 skin/2 since the last build
 };
 
 namespace tmd {
@@ -286,10 +295,13 @@ void nlist_free(tmd_nlist *nl);
 // needs image shifts beyond +-15 boxes.
 tmd_status make_sys_params(const double box[3], const int32_t pbc[3], double r_list, SysParams *sp, int64_t *ncell);
 // Bin and list the atoms of the active systems (sys_of / active may be
-// nullptr for a single system); synchronises once.
+// nullptr for a single system); synchronises once.  device_only: the same
+// build with no host read and no allocation, for a stream capture; it needs
+// a build with the same atoms and cells before, and the caller checks the
+// entry counter against the capacity and the status word afterwards.
 tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int n_sys, const SysParams *sp_host,
                         const int32_t *sys_of, const uint8_t *active, const int64_t *n_of_sys, int64_t ncell_total,
-                        tmd_nlist *nl, cudaStream_t s);
+                        tmd_nlist *nl, cudaStream_t s, bool device_only = false);
 // Evaluate the atoms listed by the last build_tables of nl (batched): per
 // atom energies and virials, forces of the active atoms, per-system FP64
 // reductions (energy, virial, m v v) for the active systems in act_list.

@@ -102,6 +102,8 @@ _SIGS = {
     "tmd_batch_compute": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, _P]),
     "tmd_batch_step": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int32, _P, _P]),
     "tmd_batch_set_skin": (C.c_int, [_P, C.c_double, C.c_int32]),
+    "tmd_system_counters": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64)]),
     "tmd_compute_owned": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.POINTER(C.c_double), _P, _P, _P, _P,
                                     _P]),
     "tmd_batch_release": (C.c_int, [_P, C.c_int32]),
@@ -422,6 +424,12 @@ class System:
         check(lib().tmd_system_get_state(self.handle, pos.ctypes.data_as(_P), vel.ctypes.data_as(_P),
                                          f.ctypes.data_as(_P), 0, _stream(stream)))
         return pos, vel, f
+
+    def counters(self):
+        """{steps, rebuilds, runs, reruns} (tmd_system_counters)."""
+        v = [C.c_int64() for _ in range(4)]
+        check(lib().tmd_system_counters(self.handle, *[C.byref(x) for x in v]))
+        return dict(zip(("steps", "rebuilds", "runs", "reruns"), (int(x.value) for x in v)))
 
     def step(self, model, dt, nsteps, rebuild_every=0, stream=None, thermo=True):
         th = Thermo()

@@ -146,3 +146,39 @@ def test_batch_graph_replay_matches_eager(tmdlib):
     for a, c in zip(out[0], out[1]):
         for x, y in zip(a, c):
             assert np.array_equal(x, y)
+
+
+def _md_call(tmd, w, graphs, stream, nsteps, rebuild_every, skin):
+    s = w.systems[0]
+    m = tmd.Model(w.model)
+    g = tmd.System(s.n, s.box, s.pbc, skin=skin)
+    g.set_state(s.pos, s.vel, s.types, s.masses, stream=stream)
+    tmd.set_graphs(graphs)
+    try:
+        g.step(m, 1.0, 2, rebuild_every=rebuild_every, stream=stream)           # initial forces, off-cadence start
+        th = g.step(m, 1.0, nsteps, rebuild_every=rebuild_every, stream=stream)
+    finally:
+        tmd.set_graphs(True)
+    p, v, f = g.get_state(stream=stream)
+    return p, v, f, th, g.counters()
+
+
+@pytest.mark.parametrize("rebuild_every,skin,nsteps", [(5, 1.0, 33), (0, 1.0, 40), (0, 0.02, 40)])
+def test_md_runs_match_step_by_step(tmdlib, rebuild_every, skin, nsteps):
+    """Runs of steps decided on the device (cadence rebuild inside, skin flags
+    read once per run) give the step-by-step trajectory bitwise.  The 0.02 A
+    skin makes the skin criterion fire inside runs, which are then undone
+    and stepped again one step at a time."""
+    torch = _torch()
+    w = I.medium()
+    w.systems[0].vel = I.maxwell_velocities(w.systems[0].masses, 300.0, np.random.default_rng(5))
+    side = torch.cuda.Stream()
+    pr, vr, fr, thr, cr = _md_call(tmdlib, w, True, side, nsteps, rebuild_every, skin)
+    pe, ve, fe, the, ce = _md_call(tmdlib, w, False, side, nsteps, rebuild_every, skin)
+    assert np.array_equal(pr, pe) and np.array_equal(vr, ve) and np.array_equal(fr, fe)
+    assert thr["rebuilds"] == the["rebuilds"] and cr["steps"] == ce["steps"] == nsteps + 2
+    assert ce["runs"] == 0 and cr["runs"] + cr["reruns"] >= 2
+    if skin >= 1.0:
+        assert cr["reruns"] == 0 and cr["runs"] >= 2
+    else:
+        assert cr["reruns"] >= 1 and thr["rebuilds"] > 3
