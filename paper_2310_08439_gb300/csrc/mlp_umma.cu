@@ -10,8 +10,9 @@
 // weight operand streams in 64-wide K chunks by bulk copy (cp.async.bulk,
 // completion on an mbarrier) into two stages; the first layer's operand is
 // the FP32 descriptor tile converted to BF16 by the threads, chunk by chunk.
-// After each product four warps read the accumulator back (tcgen05.ld, one
-// row per thread), apply bias and activation, keep act' in TMEM for the
+// After each product eight warps read the accumulator back (tcgen05.ld, one
+// row per thread; the two warps of a TMEM lane quarter take alternate
+// 16-column blocks), apply bias and activation, keep act' in TMEM for the
 // backward chain (tcgen05.st) and write the BF16 operand of the next product.
 // One elected thread issues the MMAs and the copies.
 //
@@ -36,7 +37,8 @@ __device__ int32_t g_umma_status = 0;
 namespace {
 
 constexpr int UM = 128;                 // atoms per tile: the MMA M, one TMEM lane each
-constexpr int UTHREADS = 128;           // 4 warps; warp w owns TMEM lanes / rows 32w .. 32w + 31
+constexpr int UTHREADS = 256;           // 8 warps; warp w owns TMEM lanes / rows 32 (w % 4) .. + 31 and
+                                        // the 16-column blocks b of each epilogue with b % 2 == w / 4
 constexpr int UKC = 64;                 // K per streamed chunk
 constexpr int UNMAX = 256;              // largest N of one MMA
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
@@ -213,7 +215,7 @@ __device__ __forceinline__ ChunkPos block_chunk(const DevModel &m, const UmmaNet
     return {2 * L - 1, 0, 0};
 }
 
-__global__ void __launch_bounds__(UTHREADS, 1)
+__global__ void __launch_bounds__(UTHREADS, 2)
     k_mlp_umma(DevModel m, UmmaNet u, const int32_t *__restrict__ perm, const int32_t *__restrict__ types, int64_t n,
                const float *__restrict__ G, float *__restrict__ dG, float *__restrict__ e_atom,
                double *__restrict__ part_e, int ntile) {
@@ -223,8 +225,10 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ int s_atom[UM], s_type[UM], s_range[2];
-    __shared__ float s_e[UM];
+    __shared__ float s_e[UM], s_ep[2][UM];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rq = warp & 3, ch = warp >> 2;   // TMEM lane quarter, column-block parity
+    const int row = rq * 32 + lane;            // this thread's tile row
     const int L = m.L, Dd = m.Dd, NST = u.nst;
     // dynamic shared memory: X[2] activation buffers, 2 G stages, NST weight stages
     // (alias: the first layer has one K chunk, so the single G stage is also
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lane quarter, column 0
+    const uint32_t trow = tmem + ((uint32_t)(rq * 32) << 16);   // this warp's lane quarter, column 0
     uint32_t q = 0;    // weight chunks consumed (stage q % NST, use q / NST)
     uint32_t qi = 0;   // weight chunks whose copy was issued (thread 0)
     uint32_t ua = 0;   // G chunks consumed (stage ua & 1, use ua >> 1)
@@ -307,22 +311,23 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     };
     // Software pipeline over tiles: this thread's atom of the next tile, and
     // its share of that tile's first G chunk, are loaded into registers while
-    // the current tile runs (half a warp per row: lane l covers rows
-    // 2 it + l / 16 of its warp, columns 4 (l % 16) .. + 3 of the chunk).
+    // the current tile runs (a quarter warp per row: lane l covers row
+    // 4 it + l / 8 of its lane quarter, columns 32 ch + 4 (l % 8) .. + 3 of
+    // the chunk).
     auto row_atom = [&](int t) -> int {
-        const int64_t p = (int64_t)t * UM + tid;
+        const int64_t p = (int64_t)t * UM + row;
         return (t < ntile && p < n) ? perm[p] : -1;
     };
-    float4 gpre[16];
+    float4 gpre[8];
     // G and G' rows are indexed by perm position: row r of tile t is t UM + r
     auto load_g0 = [&](int atom_of_my_row, int t) {
 #pragma unroll
-        for (int it = 0; it < 16; ++it) {
-            const int a = __shfl_sync(0xffffffffu, atom_of_my_row, 2 * it + (lane >> 4));
-            const int col = 4 * (lane & 15);
+        for (int it = 0; it < 8; ++it) {
+            const int a = __shfl_sync(0xffffffffu, atom_of_my_row, 4 * it + (lane >> 3));
+            const int col = 32 * ch + 4 * (lane & 7);
             // the null row of a missing atom reads as zeros
             const bool ok = a >= 0 && col < Dd;
-            const size_t p = (size_t)t * UM + warp * 32 + 2 * it + (lane >> 4);
+            const size_t p = (size_t)t * UM + rq * 32 + 4 * it + (lane >> 3);
             const float *src = G + (ok ? p * Dd + col : 0);
             float4 v;
             // issued here, in program order with the surrounding tensor-core
@@ -337,9 +342,11 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     int nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
     load_g0(nx_atom, blockIdx.x);
     for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        s_atom[tid] = nx_atom;
-        s_type[tid] = nx_type;
-        s_e[tid] = 0.f;
+        if (ch == 0) {
+            s_atom[row] = nx_atom;
+            s_type[row] = nx_type;
+            s_e[row] = 0.f;
+        }
         const int my_atom = nx_atom, my_type = nx_type;
         bool g0_ready = true;   // gpre holds this tile's first chunk
         // the tile after this one: atom ids now, species and G rows once gpre is consumed
@@ -375,27 +382,27 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                         const int ast = ua % na;
                         const uint32_t ause = ua / na;
                         uint16_t *Ast = A0 + ast * CHUNK_EL;
-                        if (pr == 0) {   // G chunk c -> BF16 operand (half a warp per row, own rows)
+                        if (pr == 0) {   // G chunk c -> BF16 operand (a quarter warp per row, own rows)
                             if (!(c == 0 && g0_ready)) {
-                                const int r0 = warp * 32 + (lane >> 4);
+                                const int r0 = rq * 32 + (lane >> 3);
 #pragma unroll
-                                for (int it = 0; it < 16; ++it) {
-                                    const int a = s_atom[r0 + 2 * it];
-                                    const int col = c * UKC + 4 * (lane & 15);
+                                for (int it = 0; it < 8; ++it) {
+                                    const int a = s_atom[r0 + 4 * it];
+                                    const int col = c * UKC + 32 * ch + 4 * (lane & 7);
                                     gpre[it] = make_float4(0.f, 0.f, 0.f, 0.f);
                                     if (a >= 0 && col < Dd)
                                         gpre[it] = __ldg(reinterpret_cast<const float4 *>(
-                                            G + ((size_t)tile * UM + r0 + 2 * it) * Dd + col));
+                                            G + ((size_t)tile * UM + r0 + 4 * it) * Dd + col));
                                 }
                             }
                             if (ause >= 1) mbar_wait(bar_aempty(ast), (ause - 1) & 1, abort);
 #pragma unroll
-                            for (int it = 0; it < 16; ++it) {
-                                const int r = warp * 32 + 2 * it + (lane >> 4);
+                            for (int it = 0; it < 8; ++it) {
+                                const int r = rq * 32 + 4 * it + (lane >> 3);
                                 uint2 w;
                                 w.x = pack_bf16(gpre[it].x, gpre[it].y);
                                 w.y = pack_bf16(gpre[it].z, gpre[it].w);
-                                *reinterpret_cast<uint2 *>(Ast + op_index(r, 4 * (lane & 15))) = w;
+                                *reinterpret_cast<uint2 *>(Ast + op_index(r, 32 * ch + 4 * (lane & 7))) = w;
                             }
                             fence_proxy_async();
                             __syncthreads();
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                         const bool last_fwd = l == L - 1;
                         const float *wout = cs + u.cbias[L];
                         float eacc = 0.f;
-                        for (int c0 = 0; c0 < N; c0 += 16) {
+                        for (int c0 = 16 * ch; c0 < N; c0 += 32) {
                             float v[16], a[16], d[16];
                             tmem_ld16(trow + c0, v);
 #pragma unroll
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                                 d[e] = act_da(m.act, a[e], m.sp_b);
                             }
                             if (!last_fwd) {
-                                store_row16(Xout, tid, c0, a);
+                                store_row16(Xout, row, c0, a);
                                 tmem_st16_nowait(trow + u.dercol[l + 1] + c0, d);
                             } else {   // E_a partial and dz_L = w_out * act'(a_L)
 #pragma unroll
@@ -451,30 +458,26 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                                     eacc = fmaf(w, a[e], eacc);
                                     d[e] *= w;
                                 }
-                                store_row16(Xout, tid, c0, d);
+                                store_row16(Xout, row, c0, d);
                             }
                         }
                         if (!last_fwd) tmem_st_wait();
-                        if (last_fwd && my_type == s) {
-                            const float e = eacc + cs[u.cbias[L + 1]];
-                            s_e[tid] = e;
-                            if (e_atom) e_atom[my_atom] = e;
-                        }
+                        if (last_fwd) s_ep[ch][row] = eacc;   // halves added after the product's barrier
                     } else if (!last) {   // dz_l = (dz_{l+1} W_l) * act'(a_l)
-                        for (int c0 = 0; c0 < N; c0 += 16) {
+                        for (int c0 = 16 * ch; c0 < N; c0 += 32) {
                             float v[16], d[16];
                             tmem_ld16(trow + c0, v);
                             tmem_ld16(trow + u.dercol[l] + c0, d);
 #pragma unroll
                             for (int e = 0; e < 16; ++e) v[e] *= d[e];
-                            store_row16(Xout, tid, c0, v);
+                            store_row16(Xout, row, c0, v);
                         }
                     } else {   // G' columns of this pass
-                        for (int c0 = 0; c0 < Np; c0 += 16) {
+                        for (int c0 = 16 * ch; c0 < Np; c0 += 32) {
                             float v[16];
                             tmem_ld16(trow + c0, v);
                             if (my_type == s) {
-                                float4 *o = reinterpret_cast<float4 *>(dG + ((size_t)tile * UM + tid) * Dd + P * Np + c0);
+                                float4 *o = reinterpret_cast<float4 *>(dG + ((size_t)tile * UM + row) * Dd + P * Np + c0);
 #pragma unroll
                                 for (int e = 0; e < 4; ++e)
                                     o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
@@ -484,6 +487,11 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                     fence_proxy_async();   // the operand writes are read by the next MMA
                     tc_fence_before();
                     __syncthreads();
+                    if (pr == L - 1 && ch == 0 && my_type == s) {   // E_a of this species' rows
+                        const float e = s_ep[0][row] + s_ep[1][row] + sconst[s * u.cstride + u.cbias[L + 1]];
+                        s_e[row] = e;
+                        if (e_atom) e_atom[my_atom] = e;
+                    }
                 }
             }
         }
