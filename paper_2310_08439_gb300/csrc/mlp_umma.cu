@@ -196,24 +196,7 @@ __device__ __forceinline__ void store_row16(uint16_t *X, int row, int col0, cons
 }
 
 constexpr int MAX_NST = 4;   // weight-chunk stages at most
-
-// (product, pass, chunk) of chunk i of a species block: the products in
-// order, each as its N passes times its K chunks
-struct ChunkPos {
-    int pr, P, c;
-};
-__device__ __forceinline__ ChunkPos block_chunk(const DevModel &m, const UmmaNet &u, int i) {
-    const int L = m.L;
-    for (int pr = 0; pr < 2 * L; ++pr) {
-        const bool fwd = pr < L;
-        const int l = fwd ? pr : 2 * L - 1 - pr;
-        const int K = fwd ? m.dims[l] : m.dims[l + 1];
-        const int nkc = (K + UKC - 1) / UKC, npass = pr == 2 * L - 1 ? u.npass0 : 1;
-        if (i < nkc * npass) return {pr, i / nkc, i % nkc};
-        i -= nkc * npass;
-    }
-    return {2 * L - 1, 0, 0};
-}
+constexpr int MAX_CHUNKS = 64;   // weight chunks of one species block at most
 
 __global__ void __launch_bounds__(UTHREADS, 2)
     k_mlp_umma(DevModel m, UmmaNet u, const int32_t *__restrict__ perm, const int32_t *__restrict__ types, int64_t n,
@@ -225,7 +208,13 @@ __global__ void __launch_bounds__(UTHREADS, 2)
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ int s_atom[UM], s_type[UM], s_range[2];
-    __shared__ float s_e[UM], s_ep[2][UM];
+    __shared__ float s_e[2][UM], s_ep[2][UM];   // s_e: E_a of the rows, by tile parity
+    // per product pr: (K, N, N of a pass, npass | nkc << 8 | layer << 16) and
+    // (bias offset, TMEM column of the act' written (forward) or read
+    // (backward), w_out offset, b_out offset); per weight chunk of a species
+    // block: (element offset in ub[s], bytes)
+    __shared__ int4 s_pa[2 * MAX_LAYERS], s_pb[2 * MAX_LAYERS];
+    __shared__ int2 s_ck[MAX_CHUNKS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rq = warp & 3, ch = warp >> 2;   // TMEM lane quarter, column-block parity
     const int row = rq * 32 + lane;            // this thread's tile row
@@ -266,6 +255,19 @@ __global__ void __launch_bounds__(UTHREADS, 2)
         for (int i = 0; i < 2 * MAX_NST + 3; ++i) mbar_init(bar0 + 8 * i, 1);
         s_abort = 0;
         fence_proxy_async();
+        int i = 0;
+        for (int pr = 0; pr < 2 * L; ++pr) {
+            const bool fwd = pr < L, last = pr == 2 * L - 1;
+            const int l = fwd ? pr : 2 * L - 1 - pr;
+            const int K = fwd ? m.dims[l] : m.dims[l + 1], N = fwd ? m.dims[l + 1] : m.dims[l];
+            const int npass = last ? u.npass0 : 1, Np = last ? u.np0 : N, nkc = (K + UKC - 1) / UKC;
+            s_pa[pr] = make_int4(K, N, Np, npass | nkc << 8 | l << 16);
+            const int der = fwd ? (l < L - 1 ? u.dercol[l + 1] : 0) : (l >= 1 ? u.dercol[l] : 0);
+            s_pb[pr] = make_int4(fwd ? u.cbias[l] : 0, der, u.cbias[L], u.cbias[L + 1]);
+            for (int P = 0; P < npass; ++P)
+                for (int c = 0; c < nkc; ++c, ++i)
+                    s_ck[i] = make_int2(m.uoff[pr] + (P * nkc + c) * Np * UKC, Np * UKC * 2);
+        }
     }
     volatile int *abort = &s_abort;
     uint32_t pending = 0;   // thread 0: stages with a copy not yet seen complete
@@ -280,8 +282,12 @@ __global__ void __launch_bounds__(UTHREADS, 2)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t trow = tmem + ((uint32_t)(rq * 32) << 16);   // this warp's lane quarter, column 0
-    uint32_t q = 0;    // weight chunks consumed (stage q % NST, use q / NST)
+    uint32_t q = 0;    // weight chunks consumed
+    int qs = 0;        // its stage, q % NST
+    uint32_t qph = 0;  // the parity of its use, (q / NST) & 1
     uint32_t qi = 0;   // weight chunks whose copy was issued (thread 0)
+    int qis = 0;       // its stage, qi % NST
+    uint32_t qiu = 0;  // its use, qi / NST
     uint32_t ua = 0;   // G chunks consumed (stage ua & 1, use ua >> 1)
     uint32_t pd = 0;   // products (passes) completed
     // thread 0: issue the copies of this block's chunks up to global index lim
@@ -291,22 +297,15 @@ __global__ void __launch_bounds__(UTHREADS, 2)
             return;
         }
         while (qi < lim && !*abort) {
-            const int st = qi % NST;
-            const uint32_t use = qi / NST;
-            if (use >= 1) mbar_wait(bar_empty(st), (use - 1) & 1, abort);   // the MMAs that read it are done
+            const int st = qis;
+            if (qiu >= 1) mbar_wait(bar_empty(st), (qiu - 1) & 1, abort);   // the MMAs that read it are done
             if (*abort) break;
-            const ChunkPos cp = block_chunk(m, u, (int)(qi - qbase));
-            const bool fwd = cp.pr < L, last = cp.pr == 2 * L - 1;
-            const int l = fwd ? cp.pr : 2 * L - 1 - cp.pr;
-            const int K = fwd ? m.dims[l] : m.dims[l + 1];
-            const int Np = last ? u.np0 : (fwd ? m.dims[l + 1] : m.dims[l]);
-            const int nkc = (K + UKC - 1) / UKC;
-            const uint32_t bytes = (uint32_t)Np * UKC * 2;
-            mbar_expect_tx(bar_full(st), bytes);
-            bulk_g2s(smem_u32(B0 + st * bstride), m.ub[s] + m.uoff[cp.pr] + ((size_t)cp.P * nkc + cp.c) * Np * UKC,
-                     bytes, bar_full(st));
+            const int2 ck = s_ck[qi - qbase];
+            mbar_expect_tx(bar_full(st), (uint32_t)ck.y);
+            bulk_g2s(smem_u32(B0 + st * bstride), m.ub[s] + ck.x, (uint32_t)ck.y, bar_full(st));
             pending |= 1u << st;
             ++qi;
+            if (++qis == NST) { qis = 0; ++qiu; }
         }
     };
     // Software pipeline over tiles: this thread's atom of the next tile, and
@@ -319,8 +318,10 @@ __global__ void __launch_bounds__(UTHREADS, 2)
         return (t < ntile && p < n) ? perm[p] : -1;
     };
     float4 gpre[8];
+    uint32_t gok = 0;   // bit it: gpre[it] holds a row of an atom (else it reads as zeros)
     // G and G' rows are indexed by perm position: row r of tile t is t UM + r
     auto load_g0 = [&](int atom_of_my_row, int t) {
+        gok = 0;
 #pragma unroll
         for (int it = 0; it < 8; ++it) {
             const int a = __shfl_sync(0xffffffffu, atom_of_my_row, 4 * it + (lane >> 3));
@@ -335,17 +336,32 @@ __global__ void __launch_bounds__(UTHREADS, 2)
             asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                          : "l"(src));
-            gpre[it] = ok ? v : make_float4(0.f, 0.f, 0.f, 0.f);
+            // raw registers: nothing here waits for the loads, the staging
+            // of the next tile's first chunk does
+            gpre[it] = v;
+            gok |= (uint32_t)ok << it;
         }
     };
+    // tile energy in FP64, fixed order (one warp): taken for the previous
+    // tile while the current one waits on its first product
+    auto tile_energy = [&](const float *e, int t) {
+        double tsum = 0.0;
+        for (int r = lane; r < UM; r += 32) tsum += (double)e[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+        if (lane == 0) part_e[t] = tsum;
+    };
+    constexpr int EWARP = UTHREADS / 32 - 1;   // the warp that sums (not the MMA issuer's)
+    int kt = 0, prev_tile = -1;                // tiles done by this block, the last of them
     int nx_atom = row_atom(blockIdx.x);
     int nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
     load_g0(nx_atom, blockIdx.x);
     for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int eb = kt & 1;
         if (ch == 0) {
             s_atom[row] = nx_atom;
             s_type[row] = nx_type;
-            s_e[row] = 0.f;
+            s_e[eb][row] = 0.f;
         }
         const int my_atom = nx_atom, my_type = nx_type;
         bool g0_ready = true;   // gpre holds this tile's first chunk
@@ -370,17 +386,15 @@ __global__ void __launch_bounds__(UTHREADS, 2)
             if (tid == 0) issue_upto(min(qend, q + NST), qbase, s);
             for (int pr = 0; pr < 2 * L; ++pr) {
                 const bool fwd = pr < L, last = pr == 2 * L - 1;
-                const int l = fwd ? pr : 2 * L - 1 - pr;   // layer of this product
-                const int K = fwd ? m.dims[l] : m.dims[l + 1];
-                const int N = fwd ? m.dims[l + 1] : m.dims[l];
-                const int npass = last ? u.npass0 : 1, Np = last ? u.np0 : N;
-                const int nkc = (K + UKC - 1) / UKC;
+                const int4 pa = s_pa[pr], pb = s_pb[pr];
+                const int K = pa.x, N = pa.y, Np = pa.z;
+                const int npass = pa.w & 255, nkc = (pa.w >> 8) & 255, l = pa.w >> 16;   // l: layer of this product
                 uint16_t *Xin = (pr & 1) ? X0 : X1, *Xout = (pr & 1) ? X1 : X0;
                 for (int P = 0; P < npass; ++P) {
-                    for (int c = 0; c < nkc; ++c, ++q) {
-                        const int st = q % NST;
-                        const int ast = ua % na;
-                        const uint32_t ause = ua / na;
+                    for (int c = 0; c < nkc; ++c) {
+                        const int st = qs;
+                        const int ast = ua & (na - 1);           // na is 1 or 2
+                        const uint32_t ause = ua >> (na - 1);
                         uint16_t *Ast = A0 + ast * CHUNK_EL;
                         if (pr == 0) {   // G chunk c -> BF16 operand (a quarter warp per row, own rows)
                             if (!(c == 0 && g0_ready)) {
@@ -394,69 +408,95 @@ __global__ void __launch_bounds__(UTHREADS, 2)
                                         gpre[it] = __ldg(reinterpret_cast<const float4 *>(
                                             G + ((size_t)tile * UM + r0 + 4 * it) * Dd + col));
                                 }
+                                gok = 0xffu;
                             }
                             if (ause >= 1) mbar_wait(bar_aempty(ast), (ause - 1) & 1, abort);
 #pragma unroll
                             for (int it = 0; it < 8; ++it) {
                                 const int r = rq * 32 + 4 * it + (lane >> 3);
+                                const float4 gv = (gok >> it) & 1u ? gpre[it] : make_float4(0.f, 0.f, 0.f, 0.f);
                                 uint2 w;
-                                w.x = pack_bf16(gpre[it].x, gpre[it].y);
-                                w.y = pack_bf16(gpre[it].z, gpre[it].w);
+                                w.x = pack_bf16(gv.x, gv.y);
+                                w.y = pack_bf16(gv.z, gv.w);
                                 *reinterpret_cast<uint2 *>(Ast + op_index(r, 32 * ch + 4 * (lane & 7))) = w;
                             }
                             fence_proxy_async();
                             __syncthreads();
-                            // gpre is free: (re)start on the next tile's first chunk
-                            if (g0_ready) nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
-                            g0_ready = false;
-                            load_g0(nx_atom, tile + gridDim.x);
                         }
                         if (tid == 0 && !*abort) {
-                            if (!(u.resident && q >= (uint32_t)NST) && mbar_wait(bar_full(st), (q / NST) & 1, abort))
+                            if (!(u.resident && q >= (uint32_t)NST) && mbar_wait(bar_full(st), qph, abort))
                                 pending &= ~(1u << st);
                             tc_fence_after();
                             const int kl = min(UKC, K - c * UKC);
-                            const uint32_t a0 = smem_u32(pr == 0 ? Ast : Xin + (size_t)c * CHUNK_EL);
-                            const uint32_t b0 = smem_u32(B0 + st * bstride);
+                            // the descriptors of the next K16 step are 256 bytes on (16 in the address field)
+                            const uint64_t da = sdesc(smem_u32(pr == 0 ? Ast : Xin + (size_t)c * CHUNK_EL));
+                            const uint64_t db = sdesc(smem_u32(B0 + st * bstride));
                             const uint32_t id = idesc_bf16(Np);
                             for (int j = 0; j < kl / 16; ++j)
-                                umma_bf16(tmem, sdesc(a0 + 256 * j), sdesc(b0 + 256 * j), id, (c | j) != 0);
-                            umma_commit(bar_empty(st));
+                                umma_bf16(tmem, da + 16 * j, db + 16 * j, id, (c | j) != 0);
+                            // resident weights: no copy ever waits for a stage to drain
+                            if (!u.resident) umma_commit(bar_empty(st));
                             if (pr == 0) umma_commit(bar_aempty(ast));
                             // keep the stages filled: the copy for chunk q + NST - 1 reuses the
                             // stage of chunk q - 1, whose MMAs were issued one chunk earlier
                             issue_upto(min(qend, q + NST), qbase, s);
                         }
-                        if (pr == 0) ++ua;
+                        // the rest of warp 0 waits here rather than polling an
+                        // mbarrier beside the issuing lane
+                        if (warp == 0) __syncwarp();
+                        if (pr == 0) {
+                            // gpre is free: (re)start on the next tile's first chunk
+                            // (after the MMA issue, which then waits on none of these loads)
+                            if (g0_ready) nx_type = nx_atom >= 0 ? types[nx_atom] : -1;
+                            g0_ready = false;
+                            load_g0(nx_atom, tile + gridDim.x);
+                            ++ua;
+                        }
+                        ++q;
+                        if (++qs == NST) { qs = 0; qph ^= 1u; }
                     }
                     if (tid == 0) umma_commit(bar_done);
+                    if (warp == 0) __syncwarp();
+                    if (pr == 0 && P == 0 && s == s_lo && warp == EWARP && prev_tile >= 0)
+                        tile_energy(s_e[eb ^ 1], prev_tile);
                     mbar_wait(bar_done, pd & 1, abort);
                     ++pd;
                     tc_fence_after();
                     // epilogue: this thread's row of the accumulator
                     if (fwd) {
                         const float *cs = sconst + s * u.cstride;
-                        const float *bias = cs + u.cbias[l];
+                        const float *bias = cs + pb.x;
                         const bool last_fwd = l == L - 1;
-                        const float *wout = cs + u.cbias[L];
+                        const float *wout = cs + pb.z;
                         float eacc = 0.f;
                         for (int c0 = 16 * ch; c0 < N; c0 += 32) {
                             float v[16], a[16], d[16];
                             tmem_ld16(trow + c0, v);
+                            const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                a[e] = act_f_bf16(m.act, v[e] + bias[c0 + e], m.sp_b);
-                                d[e] = act_da(m.act, a[e], m.sp_b);
+                            for (int e4 = 0; e4 < 4; ++e4) {
+                                const float4 bb = b4[e4];
+                                act_fd_bf16(m.act, v[4 * e4] + bb.x, m.sp_b, a[4 * e4], d[4 * e4]);
+                                act_fd_bf16(m.act, v[4 * e4 + 1] + bb.y, m.sp_b, a[4 * e4 + 1], d[4 * e4 + 1]);
+                                act_fd_bf16(m.act, v[4 * e4 + 2] + bb.z, m.sp_b, a[4 * e4 + 2], d[4 * e4 + 2]);
+                                act_fd_bf16(m.act, v[4 * e4 + 3] + bb.w, m.sp_b, a[4 * e4 + 3], d[4 * e4 + 3]);
                             }
                             if (!last_fwd) {
                                 store_row16(Xout, row, c0, a);
-                                tmem_st16_nowait(trow + u.dercol[l + 1] + c0, d);
+                                tmem_st16_nowait(trow + pb.y + c0, d);
                             } else {   // E_a partial and dz_L = w_out * act'(a_L)
+                                const float4 *w4 = reinterpret_cast<const float4 *>(wout + c0);
 #pragma unroll
-                                for (int e = 0; e < 16; ++e) {
-                                    const float w = wout[c0 + e];
-                                    eacc = fmaf(w, a[e], eacc);
-                                    d[e] *= w;
+                                for (int e4 = 0; e4 < 4; ++e4) {
+                                    const float4 w = w4[e4];
+                                    eacc = fmaf(w.x, a[4 * e4], eacc);
+                                    eacc = fmaf(w.y, a[4 * e4 + 1], eacc);
+                                    eacc = fmaf(w.z, a[4 * e4 + 2], eacc);
+                                    eacc = fmaf(w.w, a[4 * e4 + 3], eacc);
+                                    d[4 * e4] *= w.x;
+                                    d[4 * e4 + 1] *= w.y;
+                                    d[4 * e4 + 2] *= w.z;
+                                    d[4 * e4 + 3] *= w.w;
                                 }
                                 store_row16(Xout, row, c0, d);
                             }
@@ -467,44 +507,56 @@ __global__ void __launch_bounds__(UTHREADS, 2)
                         for (int c0 = 16 * ch; c0 < N; c0 += 32) {
                             float v[16], d[16];
                             tmem_ld16(trow + c0, v);
-                            tmem_ld16(trow + u.dercol[l] + c0, d);
+                            tmem_ld16(trow + pb.y + c0, d);
 #pragma unroll
                             for (int e = 0; e < 16; ++e) v[e] *= d[e];
                             store_row16(Xout, row, c0, v);
                         }
                     } else {   // G' columns of this pass
+                        // each warp's 32 x 16 blocks go out through shared memory
+                        // (X1, unused during the last product) as 64-byte row
+                        // pieces, four lanes to a row; the 16-byte groups of a
+                        // staged row are permuted by bits 1-2 of the row so that
+                        // both the row-wise writes and the transposed reads are
+                        // free of bank conflicts
+                        float *stg = reinterpret_cast<float *>(Xout) + warp * 512;
+                        const int tc = lane & 3;
                         for (int c0 = 16 * ch; c0 < Np; c0 += 32) {
                             float v[16];
                             tmem_ld16(trow + c0, v);
-                            if (my_type == s) {
-                                float4 *o = reinterpret_cast<float4 *>(dG + ((size_t)tile * UM + row) * Dd + P * Np + c0);
 #pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                            for (int e = 0; e < 4; ++e)
+                                *reinterpret_cast<float4 *>(stg + lane * 16 + 4 * (e ^ ((lane >> 1) & 3))) =
+                                    make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                            __syncwarp();
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int r = 8 * i + (lane >> 2);
+                                const float4 w =
+                                    *reinterpret_cast<const float4 *>(stg + r * 16 + 4 * (tc ^ ((r >> 1) & 3)));
+                                if (s_type[rq * 32 + r] == s)
+                                    *reinterpret_cast<float4 *>(dG + ((size_t)tile * UM + rq * 32 + r) * Dd + P * Np +
+                                                                c0 + 4 * tc) = w;
                             }
+                            __syncwarp();
                         }
                     }
                     fence_proxy_async();   // the operand writes are read by the next MMA
                     tc_fence_before();
                     __syncthreads();
                     if (pr == L - 1 && ch == 0 && my_type == s) {   // E_a of this species' rows
-                        const float e = s_ep[0][row] + s_ep[1][row] + sconst[s * u.cstride + u.cbias[L + 1]];
-                        s_e[row] = e;
+                        const float e = s_ep[0][row] + s_ep[1][row] + sconst[s * u.cstride + pb.w];
+                        s_e[eb][row] = e;
                         if (e_atom) e_atom[my_atom] = e;
                     }
                 }
             }
         }
-        // tile energy in FP64, fixed order
-        if (warp == 0) {
-            double tsum = 0.0;
-            for (int r = lane; r < UM; r += 32) tsum += (double)s_e[r];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
-            if (lane == 0) part_e[tile] = tsum;
-        }
-        __syncthreads();
+        prev_tile = tile;
+        ++kt;
     }
+    __syncthreads();
+    if (warp == EWARP && prev_tile >= 0) tile_energy(s_e[(kt - 1) & 1], prev_tile);
     if (tid == 0 && *abort) {   // bounded drain of this block's copies and MMAs in flight
         for (uint32_t k = (qi > (uint32_t)NST ? qi - NST : 0); k < qi; ++k)
             if (pending & (1u << (k % NST))) mbar_drain(bar_full(k % NST), (k / NST) & 1);
@@ -583,6 +635,7 @@ bool plan(const DevModel &dm, UmmaNet &u) {
         const int K = fwd ? dm.dims[l] : dm.dims[l + 1];
         u.block_chunks += ((K + UKC - 1) / UKC) * (pr == 2 * L - 1 ? u.npass0 : 1);
     }
+    if (u.block_chunks > MAX_CHUNKS) return false;
     // staged constants per species: bias of each layer, w_out, b_out
     int co = 0;
     for (int l = 0; l < L; ++l) {

@@ -14,15 +14,22 @@ __device__ __forceinline__ float act_f(int act, float z, float b) {
     if (act == TMD_ACT_TANH) return tanhf(z);
     return 0.5f * (z + sqrtf(fmaf(z, z, b)));
 }
-// BF16 form: tanh from the hardware approximation (relative error about
-// 2^-11, below the 2^-9 rounding of the BF16 activation it feeds)
-__device__ __forceinline__ float act_f_bf16(int act, float z, float b) {
+// BF16 form: the activation a and its derivative d from the hardware
+// approximations, whose relative errors (about 2^-11 for tanh.approx, 2^-22
+// for rsqrt.approx) lie below the 2^-9 rounding of the BF16 operands they
+// feed.  SquarePlus through u = 1/sqrt(z^2 + b): sqrt(z^2 + b) = (z^2 + b) u,
+// a = (z + sqrt(z^2 + b)) / 2 and da/dz = (1 + z u) / 2.
+__device__ __forceinline__ void act_fd_bf16(int act, float z, float b, float &a, float &d) {
     if (act == TMD_ACT_TANH) {
-        float r;
-        asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(z));
-        return r;
+        asm("tanh.approx.f32 %0, %1;" : "=f"(a) : "f"(z));
+        d = fmaf(-a, a, 1.f);
+        return;
     }
-    return 0.5f * (z + sqrtf(fmaf(z, z, b)));
+    const float t = fmaf(z, z, b);
+    float u;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(u) : "f"(t));
+    a = 0.5f * fmaf(t, u, z);
+    d = fmaf(0.5f * z, u, 0.5f);
 }
 // derivative expressed through the activation output a
 __device__ __forceinline__ float act_da(int act, float a, float b) {

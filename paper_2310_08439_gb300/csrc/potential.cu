@@ -562,9 +562,9 @@ __global__ void __launch_bounds__(BF_THREADS, 3) k_mlp_bf16(DevModel m, const in
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int row = slab * 16 + g + 8 * h;
-                            const float a0v = act_f_bf16(m.act, acc[j][2 * h] + b0, m.sp_b);
-                            const float a1v = act_f_bf16(m.act, acc[j][2 * h + 1] + b1, m.sp_b);
-                            const float d0 = act_da(m.act, a0v, m.sp_b), d1 = act_da(m.act, a1v, m.sp_b);
+                            float a0v, a1v, d0, d1;
+                            act_fd_bf16(m.act, acc[j][2 * h] + b0, m.sp_b, a0v, d0);
+                            act_fd_bf16(m.act, acc[j][2 * h + 1] + b1, m.sp_b, a1v, d1);
                             if (last_fwd) {   // E_r partial and dz_L = w_out * act'(a_L)
                                 epart[h] = fmaf(w0, a0v, fmaf(w1, a1v, epart[h]));
                                 *reinterpret_cast<uint32_t *>(dzA + row * ldz + col) = pack_bf16(w0 * d0, w1 * d1);
