@@ -918,6 +918,7 @@ def main():
     nl.build(pos_d, types_d, s.box, s.pbc, w.model.rc)
     pairs = nl.size()[1]          # entries inside rc = in-cutoff pairs
     nl.build(pos_d, types_d, s.box, s.pbc, w.model.rc + w.skin)
+    entries = nl.size()[1]        # table entries screened per step (rc + skin)
     K = w.model.n_radial
     dims = [w.model.n_desc] + list(w.model.widths) + [1]
     per_launch_flops = {"k_force": pairs * bwd_flops_per_pair(K), "k_desc": pairs * fwd_flops_per_pair(K),
@@ -940,6 +941,15 @@ def main():
             if kn in kstats:
                 a = fl / (kstats[kn][1] / max(kstats[kn][0], 1) * 1e-3) / 1e12
                 roof["all"][kn] = {"achieved": a, "frac": a / fp32_peak, "traffic": kernel_traffic(kn)}
+        # the in-cutoff screen is a stream: table entries in (nbr int32 +
+        # shift char4), pair-cache entries out (float4 + float2 per pair), per
+        # atom its split position (2 float4), segment bounds and pair count
+        if "k_screen" in kstats:
+            sb = entries * 8 + pairs * 24 + n * (32 + 16 + 4)
+            a = sb / (kstats["k_screen"][1] / max(kstats["k_screen"][0], 1) * 1e-3) / 1e9
+            roof["all"]["k_screen"] = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                       "frac": a / peaks["hbm_gbs"], "bytes_per_launch": sb,
+                                       "traffic": kernel_traffic("k_screen")}
     total_ms = sum(v[1] for v in kstats.values())
     kernels = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1), "share": v[1] / total_ms}
                for k, v in ranked}
