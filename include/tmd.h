@@ -361,8 +361,8 @@ tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
  *           axis; the table must hold every pair closer than rc (entries
  *           beyond rc are skipped).
  *  pos, types, box, energy, e_atom, forces, virial: as tmd_compute.
- * The first call on a device looks up the array's device address (make that
- * first call before any stream capture).  Each call checks the table and the
+ * The first call on a device looks up the array's device address.  Each call
+ * checks the table and the
  * species on the device and synchronises the stream once, before any force
  * kernel runs, to read the verdict (TMD_ERR_INVALID_ARG on a bad table).  It
  * runs the SIMT force pass even when tmd_set_force_kernel chose the
