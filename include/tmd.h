@@ -362,13 +362,13 @@ tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
  *           beyond rc are skipped).
  *  pos, types, box, energy, e_atom, forces, virial: as tmd_compute.
  * The first call on a device looks up the array's device address.  Each call
- * checks the table and the
- * species on the device and synchronises the stream once, before any force
- * kernel runs, to read the verdict (TMD_ERR_INVALID_ARG on a bad table).  It
- * runs the SIMT force pass even when tmd_set_force_kernel chose the
- * tensor-core one (that pass reads a pair cache this call does not keep).  Every call shares the one array and
- * clears what must start at zero; calls that overlap on the GPU (several
- * streams or threads at once) race on it and must be serialised by the caller.
+ * checks the table and the species on the device and synchronises the stream
+ * once, before any force kernel runs, to read the verdict (TMD_ERR_INVALID_ARG
+ * on a bad table).  It runs the SIMT force pass even when
+ * tmd_set_force_kernel chose the tensor-core one (that pass reads a pair cache
+ * this call does not keep).  Every call shares the one array and clears what
+ * must start at zero; calls that overlap on the GPU (several streams or
+ * threads at once) race on it and must be serialised by the caller.
  */
 tmd_status tmd_compute_noalloc(const tmd_model *model, const int64_t *off, const int32_t *nbr, const int8_t *shift4,
                                int64_t nnz, const double *pos, const int32_t *types, int64_t n, const double box[3],
