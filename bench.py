@@ -520,6 +520,26 @@ class OracleMD:
         O.vv_second(self.vel, self.forces, s.masses, 1.0)
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo where the kernel gives one)."""
+    import platform
+    arm = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+                if key in ("cpu implementer", "cpu part") and key not in arm:
+                    arm[key] = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    if arm:   # Arm cores name themselves by implementer and part number
+        return (f"{platform.machine()} (CPU implementer {arm.get('cpu implementer', '?')}, "
+                f"part {arm.get('cpu part', '?')})")
+    return platform.processor() or platform.machine()
+
+
 def oracle_sample_rate(wname, rebuild_every=5, min_seconds=10.0, max_steps=50):
     """Oracle MD steps (velocity-Verlet, evaluation, the neighbour table every
     ``rebuild_every`` steps) on a bounded sample of the workload: a 12^3 cell
@@ -681,6 +701,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": desc, "reference": "FP64 CPU oracle (no code ships "
                                             "with the paper)", "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "cpu": cpu_model(), "nproc": os.cpu_count(),
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -967,7 +988,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sdesc, sn, ssteps, sdt = oracle_sample_rate(args.config, rebuild_every=R)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc,
-               "split": oracle_split(args.config)}
+               "cpu": cpu_model(), "nproc": os.cpu_count(), "split": oracle_split(args.config)}
         if "batch" in extras:   # errors of the batch sample against the oracle
             batch_errors(extras["batch"], batch_sample)
 
