@@ -267,6 +267,25 @@ def large(feature_scale=True, reps=64):
                     dt_fs=1.0, md_steps=20)
 
 
+def sparse_gas(n=400, L=60.0, dmin=2.2, seed=23):
+    """Random dilute gas of two species in a periodic cube (no two atoms closer
+    than dmin, seed 23): about 1.7 neighbours within 6 A and 2.7 within 7 A
+    per atom, so that many atoms have no pair within 6 A, some of them with
+    table entries in a 1 A skin shell."""
+    rng = np.random.default_rng(seed)
+    box = np.array([L, L, L])
+    pos = []
+    while len(pos) < n:
+        x = rng.uniform(0.0, L, 3)
+        if pos:
+            d = np.array(pos) - x
+            d -= np.round(d / box) * box
+            if (d * d).sum(axis=1).min() < dmin * dmin:
+                continue
+        pos.append(x)
+    return System(np.array(pos), rng.integers(0, 2, n).astype(np.int32), box, np.ones(3, np.int32))
+
+
 def _best_reps(n_target, n_basis, cell):
     """(nx, ny, nz) minimising |basis*nx*ny*nz - n| with box aspect ratio <= 2
     (ties: the first found scanning nx, ny ascending)."""

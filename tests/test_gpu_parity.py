@@ -243,6 +243,28 @@ def test_degenerate_systems(tmdlib):
     assert e.item() == 0.0 and vir.abs().max().item() == 0.0
 
 
+def test_sparse_gas_atoms_without_in_cutoff_pairs(tmdlib):
+    """A dilute periodic gas with the table built at rc + skin: atoms whose
+    entries all lie in the skin shell reach the descriptor and force passes
+    with no in-cutoff pair (the force pass then merges the next atoms' pairs
+    into its batches); parity with the oracle, alone and batched."""
+    w = I.medium()
+    s = I.sparse_gas()
+    o = O.evaluate(O.OracleModel(w.model), s.pos, s.types, s.box, s.pbc)
+    off, nbr, sh = O.neighbors(s.pos, s.box, s.pbc, w.model.rc)
+    counts = np.diff(off)
+    assert (counts == 0).sum() >= 20      # the case this test is about
+    g = gpu_eval(tmdlib, w.model, s, r_list=w.model.rc + 1.0)
+    assert_parity(g, o, "sparse gas")
+    # batched with the medium cell (resident tables with a skin)
+    b = tmdlib.Batch([s, w.systems[0]], skin=1.0)
+    m = tmdlib.Model(w.model)
+    E, W = b.compute(m, [0, 1])
+    _, _, fb = b.get_system(0)
+    bo = {"energy": float(E[0]), "forces": fb.astype(np.float64), "virial": W[0], "e_atom": o["e_atom"]}
+    assert_parity(bo, o, "sparse gas, batched")
+
+
 def test_compute_argument_errors(tmdlib):
     torch = _torch()
     w = I.medium()

@@ -133,3 +133,25 @@ def test_noalloc_rejects_mismatched_species_and_bad_shapes(tmdlib):
     tmdlib.compute_noalloc(m, off, nbr, shift4, pos, types, s.box, *out)
     torch.cuda.synchronize()
     assert np.isfinite(out[0].item())
+
+
+def test_noalloc_sparse_gas_matches_compute(tmdlib):
+    """A dilute gas (many atoms whose table entries all lie in the skin shell):
+    the allocation-free call, which screens the table itself, equals
+    tmd_compute within the FP32 bars."""
+    torch = _torch()
+    w = I.medium()
+    s = I.sparse_gas()
+    m = tmdlib.Model(w.model)
+    nl, pos, types, off, nbr, shift4 = _table(tmdlib, s, w.model.rc + 1.0)
+    ref = _outputs(s.n)
+    tmdlib.compute(m, nl, pos, types, s.box, *ref)
+    out = _outputs(s.n)
+    tmdlib.compute_noalloc(m, off, nbr, shift4, pos, types, s.box, *out)
+    torch.cuda.synchronize()
+    rE, rEa, rF, rW = (t.double().cpu().numpy() for t in ref)
+    E, Ea, F, W = (t.double().cpu().numpy() for t in out)
+    rms = np.sqrt((rF ** 2).mean())
+    assert abs(E[0] - rE[0]) <= E_TOL * abs(rE[0])
+    assert np.abs(F - rF).max() <= F_TOL * rms
+    assert np.abs(W - rW).max() <= W_TOL * np.abs(rW).max()
