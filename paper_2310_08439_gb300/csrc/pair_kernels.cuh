@@ -552,23 +552,19 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
 // ---------------------------------------------------------------------------
 // backward: P', pair gradients, ScatterSum, virial
 // ---------------------------------------------------------------------------
-// round(g * 2^32) as int64 without a conversion instruction (on this GPU
-// float <-> int64 conversions issue on the slow FP64 pipe): three exact
-// 16-bit stages with the 1.5 * 2^23 rounding constant (valid for |g| < 2^21).
-__device__ __forceinline__ int round_magic(float v, float &vr) {
-    const float t = v + 12582912.0f;   // integer part in the low significand bits
-    vr = t - 12582912.0f;              // round(v) as a float
-    return __float_as_int(t) - 0x4B400000;
-}
-
+// round(g * 2^32) as int64 (the 2^-32 fixed point of the ScatterSum) from
+// 32-bit conversions only (on this GPU float <-> int64 conversions issue on
+// the slow FP64 pipe); valid for |g| < 2^21.
 __device__ __forceinline__ long long to_fixed(float g) {
-    float f1, f2, f3;
-    const int h1 = round_magic(g, f1);
-    const float v2 = (g - f1) * 65536.0f;      // exact, |v2| <= 2^15
-    const int h2 = round_magic(v2, f2);
-    const float v3 = (v2 - f2) * 65536.0f;     // exact, |v3| <= 2^15
-    const int h3 = round_magic(v3, f3);
-    return (long long)h1 * 4294967296LL + (long long)h2 * 65536LL + (long long)h3;
+    // two 32-bit stages: x = g 2^10 = r + v with r = rint(x) (|r| < 2^31 for
+    // |g| < 2^21) and |v| <= 1/2 exact; then round(v 2^22) (exact scaling,
+    // |.| <= 2^21): round(g 2^32) = r 2^22 + round(v 2^22), both roundings to
+    // nearest even as a single rounding of g 2^32 would be
+    const float x = g * 1024.0f;
+    const float r = rintf(x);
+    const int h1 = __float2int_rz(r);              // exact: r is an integer
+    const int h2 = __float2int_rn((x - r) * 4194304.0f);
+    return (long long)h1 * 4194304LL + (long long)h2;
 }
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
