@@ -484,6 +484,20 @@ def serving_measure(tmd, seconds, torch):
     b = batched("fp32")
     res["batched_fp32_at_per_request_loads"] = sweep("batched", b, None, 200,
                                                      rates=[p["rate_per_s"] for p in alone_pts])
+    # the serving configuration's own rate, 2,000 requests/s, on every arm
+    # (the same arrivals; the per-request arm is past its capacity there and
+    # drains its queue after the window)
+    res["at_2000_per_s"] = {}
+    for arm, prec in (("batched_fp32", "fp32"), ("batched_bf16", "bf16"), ("per_request_fp32", "fp32")):
+        b = batched(prec)
+        reqs = serve.poisson_requests(len(systems), 2000.0, seconds, seed=300)
+        if arm == "per_request_fp32":
+            _, st = serve.serve_alone(b, m, reqs)
+        else:
+            _, st = serve.serve_batched(b, m, reqs, residency=serve.Residency(b, need, budget))
+        st.update(rate_per_s=2000.0, offered_atom_steps_per_s=2000.0 * mean_work)
+        res["at_2000_per_s"][arm] = st
+    m.set_precision("fp32")
     return res
 
 
