@@ -8,8 +8,9 @@
 // [128 x K] x [K x N] tcgen05.mma GEMM with BF16 operands in shared memory and
 // the FP32 accumulator in tensor memory (TMEM lane = tile row = atom).  The
 // weight operand streams in 64-wide K chunks by bulk copy (cp.async.bulk,
-// completion on an mbarrier) into two stages; the first layer's operand is
-// the FP32 descriptor tile converted to BF16 by the threads, chunk by chunk.
+// completion on an mbarrier) into a ring of two to four stages (resident when
+// one species' whole chain fits); the first layer's operand is the FP32
+// descriptor tile converted to BF16 by the threads, chunk by chunk.
 // After each product eight warps read the accumulator back (tcgen05.ld, one
 // row per thread; the two warps of a TMEM lane quarter take alternate
 // 16-column blocks), apply bias and activation, keep act' in TMEM for the
