@@ -183,3 +183,27 @@ def test_released_table_is_rebuilt_with_the_same_forces(tmdlib):
     assert reg1 > 0 and builds1 == 2 and pool1 == pool0    # the released region was reused
     for k in ids:
         assert np.array_equal(b.get_system(k)[2], f0[k]), k
+
+
+def test_resident_table_and_owned_call_argument_errors(tmdlib):
+    """The batch's table calls and the owned-centre evaluation reject bad
+    arguments with TMD_ERR_INVALID_ARG before touching the GPU."""
+    import torch
+    w = I.medium()
+    s = w.systems[0]
+    b = tmdlib.Batch([s], skin=1.0)
+    for bad in (lambda: b.set_skin(-1.0), lambda: b.set_skin(float("nan")), lambda: b.set_skin(1.0, -1),
+                lambda: b.release(1), lambda: b.release(-1), lambda: b.table_info(1)):
+        with pytest.raises(tmdlib.TmdError) as e:
+            bad()
+        assert e.value.status == tmdlib.ERR_INVALID_ARG
+    m = tmdlib.Model(w.model)
+    pos = torch.as_tensor(s.pos, device="cuda")
+    types = torch.as_tensor(s.types, device="cuda")
+    nl = tmdlib.NeighborList()
+    nl.build(pos, types, s.box, s.pbc, w.model.rc)
+    for n_owned in (-1, s.n + 1):
+        with pytest.raises(tmdlib.TmdError) as e:
+            tmdlib.compute_owned(m, nl, pos, types, n_owned, s.box,
+                                 energy=torch.zeros(1, dtype=torch.float64, device="cuda"))
+        assert e.value.status == tmdlib.ERR_INVALID_ARG
