@@ -363,7 +363,7 @@ tmd_status tmd_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
  *  pos, types, box, energy, e_atom, forces, virial: as tmd_compute.
  * The first call on a device looks up the array's device address.  Each call
  * checks the table and the species on the device and synchronises the stream
- * once, before any force kernel runs, to read the verdict (TMD_ERR_INVALID_ARG
+ * once, before any force kernel runs, to read the result (TMD_ERR_INVALID_ARG
  * on a bad table).  It runs the SIMT force pass even when
  * tmd_set_force_kernel chose the tensor-core one (that pass reads a pair cache
  * this call does not keep).  Every call shares the one array and clears what

@@ -1257,7 +1257,7 @@ tmd_status run_compute_noalloc(const tmd_model *model, const int64_t *off, const
     w.part = static_cast<double *>(take(sizeof(double) * (ntile + 9 * (size_t)nblk + 16 + RED_PART)));
     int32_t *flag = static_cast<int32_t *>(take(sizeof(int32_t) * 4));
 
-    // validate the caller's table on the device, then read the verdict
+    // validate the caller's table on the device, then read the result
     TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
     const int cb = (int)std::min<int64_t>((std::max(n, nnz) + 255) / 256, 4096);
     TMD_LAUNCH("k_noalloc_check", s, k_noalloc_check<<<cb, 256, 0, s>>>(off, nbr, reinterpret_cast<const char4 *>(shift4),
