@@ -126,3 +126,28 @@ def test_bounded_wait_gives_up_and_the_context_survives(tmdlib):
     assert abs(g["energy"] - o["energy"]) / abs(o["energy"]) < 1e-3
     assert np.sqrt(((g["forces"] - o["forces"]) ** 2).mean()) / rms < 5e-2
     assert tmdlib.device_status() == 0
+
+
+def test_tile_energies_over_many_tiles_per_block(tmdlib):
+    """131,072 atoms (1,024 tcgen05 tiles, several per block): the energy the
+    kernels reduce per tile equals the sum of the per-atom energies they write
+    (to FP64 rounding), for both kernels of the BF16 form, and the two kernels'
+    forces agree as on the small cells."""
+    w = I.large(reps=32)
+    s = w.systems[0]
+    m = tmdlib.Model(w.model)
+    m.set_precision("bf16")
+    res = {}
+    try:
+        for kind in ("tcgen05", "mma_sync"):
+            tmdlib.set_network_kernel(kind)
+            g = _eval(tmdlib, m, s, w.model.rc + 1.0)
+            assert abs(g["energy"] - g["e_atom"].sum()) <= 1e-12 * abs(g["energy"]), kind
+            res[kind] = g
+    finally:
+        tmdlib.set_network_kernel("auto")
+    assert tmdlib.device_status() == 0
+    a, b = res["tcgen05"], res["mma_sync"]
+    rms = np.sqrt((b["forces"] ** 2).mean())
+    assert np.sqrt(((a["forces"] - b["forces"]) ** 2).mean()) <= 2e-2 * rms
+    assert abs(a["energy"] - b["energy"]) <= 1e-4 * abs(b["energy"])
