@@ -116,6 +116,7 @@ namespace {
 
 // eV/(A amu) -> A/fs^2
 constexpr double ACC_CONV = 1.0 / 103.6427;
+constexpr double FQ_UNIT = 1.0 / 4294967296.0;   // the force accumulator's unit, 2^-32 eV/A
 constexpr double KB_EV = 8.617333262e-5;
 
 // Half kick and drift.  Positions are not wrapped here: the neighbour table's
@@ -162,13 +163,20 @@ __global__ void k_wrap(double *__restrict__ pos, int64_t n, double L0, double L1
     }
 }
 
-__global__ void k_vv_second(double *__restrict__ vel, const float *__restrict__ F, const double *__restrict__ inv_mass,
-                            int64_t n, double dt) {
+// the second half kick fused with the conversion of the pair passes' force
+// accumulator (int64, 2^-32 eV/A) to the FP32 forces it also writes: the
+// same values as the conversion and the kick launched one after the other
+__global__ void k_vv_second_fq(double *__restrict__ vel, const long long *__restrict__ Fq, float *__restrict__ F,
+                               const double *__restrict__ inv_mass, int64_t n, double dt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
 #pragma unroll
-    for (int x = 0; x < 3; ++x) vel[3 * i + x] += h * (double)F[3 * i + x];
+    for (int x = 0; x < 3; ++x) {
+        const float f = (float)((double)Fq[3 * i + x] * FQ_UNIT);
+        F[3 * i + x] = f;
+        vel[3 * i + x] += h * (double)f;
+    }
 }
 
 // block partials of sum m v_a v_b (FP64), 6 components
@@ -1070,9 +1078,11 @@ static tmd_status step_eager(const tmd_model *model, tmd_system *sys, double dt_
     for (int x = 0; x < 3; ++x) key.push_back(bits_of(sys->box[x]));
     return graphed(sys->g_step, key, s, [&]() {
         tmd_status st2 = run_compute(model, &sys->nl, sys->pos, sys->types, sys->n, sys->box, sys->red, nullptr,
-                                     sys->forces, sys->red + 1, s);
+                                     nullptr, sys->red + 1, s);
         if (st2 != TMD_OK) return st2;
-        TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
+        TMD_LAUNCH("k_vv_second", s, k_vv_second_fq<<<nb, 256, 0, s>>>(
+                                         sys->vel, reinterpret_cast<const long long *>(sys->nl.Fq), sys->forces,
+                                         sys->inv_mass, n, dt_fs));
         TMD_CUDA(cudaGetLastError());
         return TMD_OK;
     });
@@ -1142,10 +1152,12 @@ static tmd_status step_run(const tmd_model *model, tmd_system *sys, double dt_fs
                 if (b != TMD_OK) return b;
                 TMD_CUDA(cudaMemcpyAsync(sys->pos_ref, sys->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
             }
-            tmd_status c = run_compute(model, nl, sys->pos, sys->types, n, sys->box, sys->red, nullptr, sys->forces,
+            tmd_status c = run_compute(model, nl, sys->pos, sys->types, n, sys->box, sys->red, nullptr, nullptr,
                                        sys->red + 1, s);
             if (c != TMD_OK) return c;
-            TMD_LAUNCH("k_vv_second", s, k_vv_second<<<nb, 256, 0, s>>>(sys->vel, sys->forces, sys->inv_mass, n, dt_fs));
+            TMD_LAUNCH("k_vv_second", s, k_vv_second_fq<<<nb, 256, 0, s>>>(
+                                             sys->vel, reinterpret_cast<const long long *>(nl->Fq), sys->forces,
+                                             sys->inv_mass, n, dt_fs));
             TMD_CUDA(cudaGetLastError());
         }
         return TMD_OK;
