@@ -122,21 +122,31 @@ constexpr double KB_EV = 8.617333262e-5;
 // Half kick and drift.  Positions are not wrapped here: the neighbour table's
 // image shifts refer to the positions at the last build, so atoms move
 // continuously until the next rebuild, which wraps them first.
+// First half kick and drift; the drifted positions are also written as the
+// pair kernels' hi/lo split (ph, pl), so that the evaluation that follows
+// need not form it again.
 __global__ void k_vv_first(double *__restrict__ pos, double *__restrict__ vel, const float *__restrict__ F,
                            const double *__restrict__ inv_mass, int64_t n, double dt,
-                           const double *__restrict__ pos_ref, double lim2, int32_t *__restrict__ flag) {
+                           const double *__restrict__ pos_ref, double lim2, int32_t *__restrict__ flag,
+                           float4 *__restrict__ ph, float4 *__restrict__ pl) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double h = 0.5 * dt * inv_mass[i] * ACC_CONV;
     double d2 = 0.0;
+    float sh[3], sl[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         const double v = vel[3 * i + x] + h * (double)F[3 * i + x];
         const double p = pos[3 * i + x] + dt * v;
         vel[3 * i + x] = v;
         pos[3 * i + x] = p;
+        grid_split(p, sh[x], sl[x]);
         const double d = p - pos_ref[3 * i + x];
         d2 += d * d;
+    }
+    if (ph) {
+        ph[i] = make_float4(sh[0], sh[1], sh[2], 0.f);
+        pl[i] = make_float4(sl[0], sl[1], sl[2], 0.f);
     }
     // bit 0: moved more than skin/2 (rebuild); bit 1: more than 0.7 skin/2
     // (close to it: the step loop stops running steps ahead, see tmd_step)
@@ -144,12 +154,15 @@ __global__ void k_vv_first(double *__restrict__ pos, double *__restrict__ vel, c
 }
 
 // Wrap positions into [0, L) on periodic axes (before a neighbour rebuild).
+// Wrap positions into [0, L) on periodic axes (before a neighbour rebuild);
+// a wrapped atom's hi/lo split (ph, pl) is formed again.
 __global__ void k_wrap(double *__restrict__ pos, int64_t n, double L0, double L1, double L2, int p0, int p1,
-                       int p2) {
+                       int p2, float4 *__restrict__ ph, float4 *__restrict__ pl) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double L[3] = {L0, L1, L2};
     const int pb[3] = {p0, p1, p2};
+    bool moved = false;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         if (!pb[x]) continue;
@@ -159,7 +172,15 @@ __global__ void k_wrap(double *__restrict__ pos, int64_t n, double L0, double L1
             if (p >= L[x]) p -= L[x];
             if (p < 0.0) p += L[x];
             pos[3 * i + x] = p;
+            moved = true;
         }
+    }
+    if (moved && ph) {
+        float sh[3], sl[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) grid_split(pos[3 * i + x], sh[x], sl[x]);
+        ph[i] = make_float4(sh[0], sh[1], sh[2], 0.f);
+        pl[i] = make_float4(sl[0], sl[1], sl[2], 0.f);
     }
 }
 
@@ -1018,6 +1039,14 @@ tmd_status tmd_system_get_state(const tmd_system *sys, double *pos, double *vel,
     return TMD_OK;
 }
 
+// The system's split-position arrays when they have room for its atoms (the
+// drift and the wrap then keep them current and the evaluation does not form
+// them again), else null.
+static float4 *split_hi(const tmd_system *sys) {
+    return sys->nl.ph && sys->nl.pl && sys->nl.cap_ph >= sys->n && sys->nl.cap_pl >= sys->n ? sys->nl.ph : nullptr;
+}
+static float4 *split_lo(const tmd_system *sys) { return split_hi(sys) ? sys->nl.pl : nullptr; }
+
 static tmd_status rebuild_only(const tmd_model *model, tmd_system *sys, cudaStream_t s) {
     tmd_status st;
     {
@@ -1025,7 +1054,8 @@ static tmd_status rebuild_only(const tmd_model *model, tmd_system *sys, cudaStre
         const int64_t n = sys->n;
         TMD_LAUNCH("k_wrap", s, k_wrap<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys->pos, n, sys->box[0], sys->box[1],
                                                                                   sys->box[2], sys->pbc[0], sys->pbc[1],
-                                                                                  sys->pbc[2]));
+                                                                                  sys->pbc[2], split_hi(sys),
+                                                                                  split_lo(sys)));
         if ((st = build_neighbors(sys->pos, sys->types, sys->n, sys->box, sys->pbc, r_list, &sys->nl, s)) != TMD_OK)
             return st;
         TMD_CUDA(cudaMemcpyAsync(sys->pos_ref, sys->pos, sizeof(double) * 3 * sys->n, cudaMemcpyDeviceToDevice, s));
@@ -1052,8 +1082,9 @@ static tmd_status step_eager(const tmd_model *model, tmd_system *sys, double dt_
     int32_t *flag = reinterpret_cast<int32_t *>(sys->red + 20);
     const double lim = 0.5 * sys->skin;
     TMD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    float4 *const ph = split_hi(sys), *const pl = split_lo(sys);
     TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass, n,
-                                                              dt_fs, sys->pos_ref, lim * lim, flag));
+                                                              dt_fs, sys->pos_ref, lim * lim, flag, ph, pl));
     TMD_CUDA(cudaGetLastError());
     sys->step++;
     bool rebuild = sys->need_rebuild || (rebuild_every > 0 && (sys->step % rebuild_every) == 0);
@@ -1075,10 +1106,11 @@ static tmd_status step_eager(const tmd_model *model, tmd_system *sys, double dt_
     for (const void *q : sp) key.push_back((uintptr_t)q);
     key.push_back((uintptr_t)n);
     key.push_back(bits_of(dt_fs));
+    key.push_back((uintptr_t)ph);
     for (int x = 0; x < 3; ++x) key.push_back(bits_of(sys->box[x]));
     return graphed(sys->g_step, key, s, [&]() {
         tmd_status st2 = run_compute(model, &sys->nl, sys->pos, sys->types, sys->n, sys->box, sys->red, nullptr,
-                                     nullptr, sys->red + 1, s);
+                                     nullptr, sys->red + 1, s, ph != nullptr);
         if (st2 != TMD_OK) return st2;
         TMD_LAUNCH("k_vv_second", s, k_vv_second_fq<<<nb, 256, 0, s>>>(
                                          sys->vel, reinterpret_cast<const long long *>(sys->nl.Fq), sys->forces,
@@ -1135,6 +1167,8 @@ static tmd_status step_run(const tmd_model *model, tmd_system *sys, double dt_fs
     key.push_back(bits_of(dt_fs));
     key.push_back(bits_of(sys->skin));
     for (int x = 0; x < 3; ++x) key.push_back(bits_of(sys->box[x]));
+    float4 *const ph = split_hi(sys), *const pl = split_lo(sys);
+    key.push_back((uintptr_t)ph);
     st = graphed(sys->g_run, key, s, [&]() {
         TMD_CUDA(cudaMemcpyAsync(sys->snap_pos, sys->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
         TMD_CUDA(cudaMemcpyAsync(sys->snap_vel, sys->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
@@ -1143,17 +1177,17 @@ static tmd_status step_run(const tmd_model *model, tmd_system *sys, double dt_fs
         for (int j = 0; j < k; ++j) {
             TMD_LAUNCH("k_vv_first", s, k_vv_first<<<nb, 256, 0, s>>>(sys->pos, sys->vel, sys->forces, sys->inv_mass,
                                                                       n, dt_fs, sys->pos_ref, lim * lim,
-                                                                      sys->run_flags + j));
+                                                                      sys->run_flags + j, ph, pl));
             if (j == 0 && rebuild_first) {
                 TMD_LAUNCH("k_wrap", s, k_wrap<<<nb, 256, 0, s>>>(sys->pos, n, sys->box[0], sys->box[1], sys->box[2],
-                                                                  sys->pbc[0], sys->pbc[1], sys->pbc[2]));
+                                                                  sys->pbc[0], sys->pbc[1], sys->pbc[2], ph, pl));
                 tmd_status b = build_tables(sys->pos, sys->types, n, 1, &q, nullptr, nullptr, nullptr, ncell, nl, s,
                                             true);
                 if (b != TMD_OK) return b;
                 TMD_CUDA(cudaMemcpyAsync(sys->pos_ref, sys->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
             }
             tmd_status c = run_compute(model, nl, sys->pos, sys->types, n, sys->box, sys->red, nullptr, nullptr,
-                                       sys->red + 1, s);
+                                       sys->red + 1, s, ph != nullptr);
             if (c != TMD_OK) return c;
             TMD_LAUNCH("k_vv_second", s, k_vv_second_fq<<<nb, 256, 0, s>>>(
                                              sys->vel, reinterpret_cast<const long long *>(nl->Fq), sys->forces,

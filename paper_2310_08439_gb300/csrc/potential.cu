@@ -981,7 +981,7 @@ tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *
 
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types, int64_t n,
                        const double box[3], double *energy, float *e_atom, float *forces, double *virial,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool pos_split) {
     tmd_status st0 = validate(model, nl, n, box);
     if (st0 != TMD_OK) return st0;
     const DevModel &dm = model->dm;
@@ -1002,7 +1002,8 @@ tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos,
     double *part_e = nl->part;
     double *part_w = nl->part + ntile;
 
-    if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
+    if (!(pos_split && nl->cap_ph >= n && nl->cap_pl >= n))
+        if ((st = split_positions(nl, pos, n, s)) != TMD_OK) return st;
     if ((st = pair_cache(nl, n, s)) != TMD_OK) return st;
     DevNlist dn = dev_nlist(nl, n, box);
     dn.pq = nl->pq;

@@ -334,9 +334,11 @@ tmd_status mlp_umma_build(tmd_model *m, const double *const *weights);
 tmd_status umma_status(int32_t *bits);
 tmd_status wait_probe(int32_t *gave_up);
 extern int g_network_kernel;
+// pos_split: the table's split positions (nl->ph, nl->pl) already hold pos
+// (the MD step writes them in its drift); otherwise they are formed here
 tmd_status run_compute(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                        int64_t n, const double box[3], double *energy, float *e_atom, float *forces,
-                       double *virial, cudaStream_t s);
+                       double *virial, cudaStream_t s, bool pos_split = false);
 tmd_status run_descriptors(const tmd_model *model, tmd_nlist *nl, const double *pos, const int32_t *types,
                            int64_t n, const double box[3], float *G, float *dEdG, cudaStream_t s);
 // tmd_compute with atoms [n_owned, n) as ghosts: neighbours only, no energy
