@@ -361,7 +361,7 @@ def paper_models_measure(tmd, torch, steps=5):
                 ms = e0.elapsed_time(e1) / steps
                 row[prec] = {"atom_evals_per_s": s.n / (ms * 1e-3), "ms_per_eval": ms,
                              "kernel_ms": {kk: v[1] / max(v[0], 1) for kk, v in ks.items()
-                                           if kk in ("k_desc", "k_force", "k_mlp", "k_mlp_bf16", "k_mlp_umma")}}
+                                           if kk in ("k_desc", "k_force", "k_mlp", "k_mlp_res", "k_mlp_bf16", "k_mlp_umma")}}
             out[f"k{k}_a{a}"] = row
             del nl, m, pos, types, E, F, W
             torch.cuda.empty_cache()
@@ -957,7 +957,7 @@ def main():
     K = w.model.n_radial
     dims = [w.model.n_desc] + list(w.model.widths) + [1]
     per_launch_flops = {"k_force": pairs * bwd_flops_per_pair(K), "k_desc": pairs * fwd_flops_per_pair(K),
-                        "k_mlp": n * mlp_flops_per_atom(dims)}
+                        "k_mlp": n * mlp_flops_per_atom(dims), "k_mlp_res": n * mlp_flops_per_atom(dims)}
     ranked = sorted(kstats.items(), key=lambda kv: -kv[1][1])
     dom, (dl, dms) = ranked[0]
     avg_ms = dms / max(dl, 1)

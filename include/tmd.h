@@ -218,10 +218,16 @@ int64_t tmd_graph_replays(void);
 
 /*
  * Tile shapes of this implementation's kernels (the paper has no counterpart:
- * they are launch choices of the GPU path and do not change any result beyond
- * the order of FP64 partial sums).
+ * they are launch choices of the GPU path).  32 and 64 give the same results
+ * up to the order of FP64 partial sums; 128 runs the network's FP32 sums in
+ * another order (results agree to FP32 rounding).
  *  tile_rows           atoms per tile of the FP32 network kernel: 32 or 64
- *                      (0 = built-in choice by shared-memory footprint);
+ *                      (weights streamed through shared memory), 128
+ *                      (weights resident in shared memory; networks whose
+ *                      descriptor length and hidden widths are all 64, one or
+ *                      two hidden layers; other networks fall back to the
+ *                      built-in choice), 0 = built-in choice (128 where it
+ *                      applies, else 64 or 32 by shared-memory footprint);
  *  pair_blocks_per_sm  blocks per SM of the persistent descriptor / force
  *                      grids (0 = built-in 16);
  *  ms                  output of the tuners: measured milliseconds of one
@@ -234,14 +240,15 @@ typedef struct {
 } tmd_tuning;
 
 /* Set / read a model's tile shapes.  set rejects tile_rows other than 0, 32,
- * 64 and pair_blocks_per_sm outside [0, 64] (TMD_ERR_INVALID_ARG). */
+ * 64, 128 and pair_blocks_per_sm outside [0, 64] (TMD_ERR_INVALID_ARG). */
 tmd_status tmd_model_set_tuning(tmd_model *model, const tmd_tuning *tuning);
 tmd_status tmd_model_get_tuning(const tmd_model *model, tmd_tuning *tuning);
 
 /*
  * Autotuner: times tmd_compute on the caller's own system (dev pos [n][3],
  * dev types [n], built table nl) for every candidate tile shape (tile_rows
- * 32 / 64 where the shared memory allows it, pair_blocks_per_sm 4, 8, 16,
+ * 32 / 64 where the shared memory allows it, 128 where the network allows
+ * it, pair_blocks_per_sm 4, 8, 16,
  * 32), with CUDA events on the stream, keeps the fastest in the model and
  * writes it to *best (host).  Results computed while tuning are discarded.
  * Synchronises the stream.  Errors: as tmd_compute.

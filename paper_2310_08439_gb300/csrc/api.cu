@@ -731,9 +731,9 @@ int64_t tmd_graph_replays(void) { return g_replays; }
 
 tmd_status tmd_model_set_tuning(tmd_model *m, const tmd_tuning *t) {
     g_err[0] = 0;
-    if (!m || !t || (t->tile_rows != 0 && t->tile_rows != 32 && t->tile_rows != 64) || t->pair_blocks_per_sm < 0 ||
-        t->pair_blocks_per_sm > 64) {
-        set_error("bad model or tuning (tile_rows 0/32/64, pair_blocks_per_sm 0..64)");
+    if (!m || !t || (t->tile_rows != 0 && t->tile_rows != 32 && t->tile_rows != 64 && t->tile_rows != 128) ||
+        t->pair_blocks_per_sm < 0 || t->pair_blocks_per_sm > 64) {
+        set_error("bad model or tuning (tile_rows 0/32/64/128, pair_blocks_per_sm 0..64)");
         return TMD_ERR_INVALID_ARG;
     }
     m->dm.tile_rows = t->tile_rows;
@@ -758,9 +758,9 @@ namespace {
 // the workspaces), then three timed back to back.
 template <typename F>
 tmd_status tune_shapes(tmd_model *m, cudaStream_t s, tmd_tuning *best, F &&run) {
-    const int rows_fp32[2] = {32, 64};
+    const int rows_fp32[3] = {32, 64, 128};
     const int bps[4] = {4, 8, 16, 32};
-    const int nrows = (m->dm.precision == TMD_PREC_FP32) ? 2 : 1;
+    const int nrows = (m->dm.precision == TMD_PREC_FP32) ? 3 : 1;
     cudaEvent_t e0, e1;
     TMD_CUDA(cudaEventCreate(&e0));
     TMD_CUDA(cudaEventCreate(&e1));
@@ -769,7 +769,7 @@ tmd_status tune_shapes(tmd_model *m, cudaStream_t s, tmd_tuning *best, F &&run) 
     tmd_status st = TMD_OK;
     for (int r = 0; r < nrows && st == TMD_OK; ++r) {
         m->dm.tile_rows = (m->dm.precision == TMD_PREC_FP32) ? rows_fp32[r] : 0;
-        if (m->dm.tile_rows && tmd::mlp_smem_tr_public(m->dm, m->dm.tile_rows) > 227 * 1024) continue;
+        if (m->dm.tile_rows && !tmd::mlp_rows_ok(m->dm, m->dm.tile_rows)) continue;
         for (int b = 0; b < 4 && st == TMD_OK; ++b) {
             m->dm.pair_bps = bps[b];
             if ((st = run()) != TMD_OK) break;

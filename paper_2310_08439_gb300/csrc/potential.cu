@@ -358,6 +358,280 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
 }
 
 // ---------------------------------------------------------------------------
+// network, FP32 SIMT with resident weights: networks whose descriptor length
+// and hidden widths are all 64, with one or two hidden layers.
+//
+// A persistent block of 128 threads keeps one species' weight matrices in
+// shared memory and walks a contiguous range of 128-atom tiles (perm order,
+// so the species changes at most S - 1 times per block).  Every product of
+// the chain (forward layers, then the input-gradient chain) is
+// [128 x 64] x [64 x 64]: each thread owns an 8 x 8 block of the result
+// (atoms 4 rb .. 4 rb + 3 and 64 + 4 rb .. 64 + 4 rb + 3, columns 8 cb ..
+// 8 cb + 7) and runs 64 multiply-adds per two float4 activation loads and two
+// float4 weight loads.  Each weight matrix is stored once in 4 x 4 blocks:
+// the forward products read rows of a block, the backward products (which
+// multiply by W^T) read its columns from the same copy after loading the
+// whole block.  The rows inside a block are XOR-swizzled so that the four
+// column groups of a warp read distinct banks in both directions.  The output
+// layer (E_a and dz_L) is formed in the epilogue of the last forward product.
+// ---------------------------------------------------------------------------
+constexpr int RW_TR = 128;              // atoms per tile
+constexpr int RW_THREADS = 128;         // 4 warps, an 8 x 8 result block per thread
+constexpr int RW_N = 64;                // descriptor length and every hidden width
+constexpr int RW_LDT = RW_TR + 4;       // row stride of the transposed activations
+constexpr int RW_MAXL = 2;              // hidden layers
+constexpr int RW_WF = RW_N * RW_N;      // floats per weight matrix
+
+// dynamic shared memory: weights, two activation buffers, biases, output
+// weights and bias, the energy partials of the two column halves
+constexpr size_t RW_SMEM_FLOATS =
+    (size_t)RW_MAXL * RW_WF + 2 * (size_t)RW_N * RW_LDT + RW_MAXL * RW_N + RW_N + 4 + 2 * RW_TR;
+
+// place of element (k, o) of a 64 x 64 matrix in the blocked, swizzled layout
+__device__ __forceinline__ int rw_widx(int k, int o) {
+    const int kb = k >> 2, ob = o >> 2, f = ((kb >> 1) ^ (ob >> 1)) & 3;
+    return ((kb * 16 + ob) << 4) + (((k & 3) ^ f) << 2) + (o & 3);
+}
+
+__device__ __forceinline__ float rw_comp(const float4 v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// acc[i][c] = sum_k At[k][atom i] B[k][col c] over k = 0..63, where B = W
+// (forward: W stored [in][out]) or B = W^T (backward)
+template <bool BWD>
+__device__ __forceinline__ void rw_product(const float *At, const float *Wm, int rb, int cb, float (&acc)[8][8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[i][c] = 0.f;
+#pragma unroll 1
+    for (int g = 0; g < RW_N / 4; ++g) {
+        // forward: blocks (g, 2 cb) and (g, 2 cb + 1), one row per k;
+        // backward: blocks (2 cb, g) and (2 cb + 1, g), one column per k
+        const int f = (cb ^ (g >> 1)) & 3;
+        const float *b0 = Wm + (BWD ? 16 * (32 * cb + g) : 16 * (16 * g + 2 * cb));
+        const float *b1 = b0 + (BWD ? 256 : 16);
+        float4 w0[4], w1[4];   // logical rows 0..3 of the two blocks
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            w0[r] = *reinterpret_cast<const float4 *>(b0 + 4 * (r ^ f));
+            w1[r] = *reinterpret_cast<const float4 *>(b1 + 4 * (r ^ f));
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float *a = At + (4 * g + r) * RW_LDT + 4 * rb;
+            const float4 a0 = *reinterpret_cast<const float4 *>(a);
+            const float4 a1 = *reinterpret_cast<const float4 *>(a + 64);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float wv[8];
+            if (!BWD) {
+                wv[0] = w0[r].x; wv[1] = w0[r].y; wv[2] = w0[r].z; wv[3] = w0[r].w;
+                wv[4] = w1[r].x; wv[5] = w1[r].y; wv[6] = w1[r].z; wv[7] = w1[r].w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    wv[q] = rw_comp(w0[q], r);
+                    wv[4 + q] = rw_comp(w1[q], r);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[i][c] = fmaf(av[i], wv[c], acc[i][c]);
+        }
+    }
+}
+
+// the 8 atoms of a thread's result block as two float4 of a transposed row
+__device__ __forceinline__ void rw_store_col(float *Ct, int col, int rb, const float (&v)[8]) {
+    float *c = Ct + col * RW_LDT + 4 * rb;
+    *reinterpret_cast<float4 *>(c) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(c + 64) = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// weights of species s into shared memory: W_l blocked (rw_widx), biases,
+// output weights and bias
+__device__ __forceinline__ void rw_load_species(const DevModel &m, int s, float *sW, float *sBias, float *sWout,
+                                                float *sBout) {
+    const int L = m.L;
+    for (int l = 0; l < L; ++l) {
+        const float *W = m.wf[s] + m.off_f[l];   // [64 in][64 out], then the bias [64]
+        for (int idx = threadIdx.x; idx < RW_N * (RW_N / 4); idx += RW_THREADS) {
+            const int k = idx >> 4, o = 4 * (idx & 15);
+            *reinterpret_cast<float4 *>(sW + l * RW_WF + rw_widx(k, o)) =
+                __ldg(reinterpret_cast<const float4 *>(W + k * RW_N + o));
+        }
+        if (threadIdx.x < RW_N) sBias[l * RW_N + threadIdx.x] = __ldg(W + RW_WF + threadIdx.x);
+    }
+    const float *wo = m.wf[s] + m.off_f[L];   // output layer: [64][1], then its bias
+    if (threadIdx.x < RW_N) sWout[threadIdx.x] = __ldg(wo + threadIdx.x);
+    if (threadIdx.x == 0) sBout[0] = __ldg(wo + RW_N);
+}
+
+__global__ void __launch_bounds__(RW_THREADS, 2) k_mlp_res(DevModel m, const int32_t *__restrict__ perm,
+                                                        const int32_t *__restrict__ types, int64_t n,
+                                                        const float *__restrict__ G, float *__restrict__ dG,
+                                                        float *__restrict__ e_atom, double *__restrict__ part_e) {
+    extern __shared__ __align__(16) float sm[];
+    float *sW = sm;                                  // L blocked 64 x 64 matrices
+    float *bufA = sW + RW_MAXL * RW_WF;              // G, then dz_L        ([64][RW_LDT])
+    float *bufB = bufA + RW_N * RW_LDT;              // a_1 (L = 2) or dz_1 (L = 1), then dz_1
+    float *sBias = bufB + RW_N * RW_LDT;             // [L][64]
+    float *sWout = sBias + RW_MAXL * RW_N;           // [64]
+    float *sBout = sWout + RW_N;                     // [1] (+ 3 pad)
+    float *sEp = sBout + 4;                          // [2][RW_TR]
+    __shared__ int s_atom[RW_TR], s_type[RW_TR];
+    __shared__ float s_e[RW_TR];
+    __shared__ int s_lohi[RW_THREADS / 32][2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rb = (lane & 7) + 8 * (warp & 1), cb = (lane >> 3) + 4 * (warp >> 1);
+    const int L = m.L, act = m.act;
+    const float spb = m.sp_b;
+    const int64_t ntile = (n + RW_TR - 1) / RW_TR;
+    const int64_t t_beg = ntile * blockIdx.x / gridDim.x, t_end = ntile * (blockIdx.x + 1) / gridDim.x;
+    int loaded = -1;   // species whose weights are in sW
+    float acc[8][8];
+    for (int64_t tile = t_beg; tile < t_end; ++tile) {
+        const int64_t p0 = tile * RW_TR;
+        __syncthreads();   // the previous tile is done with every buffer
+        {
+            const int64_t p = p0 + tid;
+            const int a = p < n ? perm[p] : -1;
+            const int ty = a >= 0 ? types[a] : -1;
+            s_atom[tid] = a;
+            s_type[tid] = ty;
+            s_e[tid] = 0.f;
+            const int lo = __reduce_min_sync(0xffffffffu, ty >= 0 ? ty : TMD_MAX_SPECIES);
+            const int hi = __reduce_max_sync(0xffffffffu, ty);
+            if (lane == 0) { s_lohi[warp][0] = lo; s_lohi[warp][1] = hi; }
+        }
+        __syncthreads();
+        int s_lo = TMD_MAX_SPECIES, s_hi = -1;
+#pragma unroll
+        for (int w = 0; w < RW_THREADS / 32; ++w) {
+            s_lo = min(s_lo, s_lohi[w][0]);
+            s_hi = max(s_hi, s_lohi[w][1]);
+        }
+        for (int s = s_lo; s <= s_hi; ++s) {
+            if (s != s_lo) __syncthreads();   // the last pass is done with bufA / bufB
+            if (s != loaded) {
+                rw_load_species(m, s, sW, sBias, sWout, sBout);
+                loaded = s;
+            }
+            {   // G row of this thread's atom -> bufA transposed (consecutive atoms: conflict-free)
+                const int a = s_atom[tid];
+                const float4 *g4 = reinterpret_cast<const float4 *>(G + (size_t)(p0 + tid) * RW_N);
+#pragma unroll 4
+                for (int c4 = 0; c4 < RW_N / 4; ++c4) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (a >= 0) v = __ldg(g4 + c4);
+                    bufA[(4 * c4) * RW_LDT + tid] = v.x;
+                    bufA[(4 * c4 + 1) * RW_LDT + tid] = v.y;
+                    bufA[(4 * c4 + 2) * RW_LDT + tid] = v.z;
+                    bufA[(4 * c4 + 3) * RW_LDT + tid] = v.w;
+                }
+            }
+            __syncthreads();
+            // forward layers; the last one also forms E_a and dz_L = w act'(a_L)
+            for (int l = 0; l < L; ++l) {
+                const float *Ain = (l == 0) ? bufA : bufB;
+                float *Cout = (l == L - 1) ? ((L == 1) ? bufB : bufA) : bufB;
+                rw_product<false>(Ain, sW + l * RW_WF, rb, cb, acc);
+                const float4 bl = *reinterpret_cast<const float4 *>(sBias + l * RW_N + 8 * cb);
+                const float4 bh = *reinterpret_cast<const float4 *>(sBias + l * RW_N + 8 * cb + 4);
+                const float bias[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
+                if (l < L - 1) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float v[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v[i] = act_f(act, acc[i][c] + bias[c], spb);
+                        rw_store_col(Cout, 8 * cb + c, rb, v);
+                    }
+                    __syncthreads();
+                } else {
+                    const float4 wl = *reinterpret_cast<const float4 *>(sWout + 8 * cb);
+                    const float4 wh = *reinterpret_cast<const float4 *>(sWout + 8 * cb + 4);
+                    const float wout[8] = {wl.x, wl.y, wl.z, wl.w, wh.x, wh.y, wh.z, wh.w};
+                    float ep[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) ep[i] = 0.f;
+                    // a_L is read by nothing but this epilogue: dz_L is
+                    // written where the product's input no longer lives
+                    // (L = 1: bufB; L = 2: bufA, G being dead)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float v[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float a = act_f(act, acc[i][c] + bias[c], spb);
+                            ep[i] = fmaf(a, wout[c], ep[i]);
+                            v[i] = wout[c] * act_da(act, a, spb);
+                        }
+                        rw_store_col(Cout, 8 * cb + c, rb, v);
+                    }
+                    // E partials over this thread's 8 columns -> the 4 column
+                    // groups of the warp (lanes 8 apart) -> the two warp pairs
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        ep[i] += __shfl_xor_sync(0xffffffffu, ep[i], 8);
+                        ep[i] += __shfl_xor_sync(0xffffffffu, ep[i], 16);
+                    }
+                    if ((lane >> 3) == 0) {
+                        float *e = sEp + (warp >> 1) * RW_TR + 4 * rb;
+                        *reinterpret_cast<float4 *>(e) = make_float4(ep[0], ep[1], ep[2], ep[3]);
+                        *reinterpret_cast<float4 *>(e + 64) = make_float4(ep[4], ep[5], ep[6], ep[7]);
+                    }
+                    __syncthreads();
+                    if (s_type[tid] == s) {
+                        const float e = (sEp[tid] + sEp[RW_TR + tid]) + sBout[0];
+                        s_e[tid] = e;
+                        if (e_atom) e_atom[s_atom[tid]] = e;
+                    }
+                }
+            }
+            // backward: dz_l = (dz_{l+1} W_l^T) act'(a_l) for l = L - 1 .. 1
+            // (L = 2: dz_2 in bufA, a_1 in bufB, dz_1 written over a_1)
+            if (L == 2) {
+                rw_product<true>(bufA, sW + RW_WF, rb, cb, acc);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float *cp = bufB + (8 * cb + c) * RW_LDT + 4 * rb;
+                    const float4 a0 = *reinterpret_cast<const float4 *>(cp);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(cp + 64);
+                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    float v[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] = acc[i][c] * act_da(act, av[i], spb);
+                    rw_store_col(bufB, 8 * cb + c, rb, v);
+                }
+                __syncthreads();
+            }
+            // G' = dz_1 W_0^T -> dG rows of species s (perm position)
+            rw_product<true>(bufB, sW, rb, cb, acc);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int row = (i < 4) ? 4 * rb + i : 64 + 4 * rb + (i - 4);
+                if (s_type[row] == s) {
+                    float4 *o = reinterpret_cast<float4 *>(dG + (size_t)(p0 + row) * RW_N + 8 * cb);
+                    o[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                    o[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+                }
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {   // tile energy in FP64, fixed order
+            double t = 0.0;
+            for (int r = lane; r < RW_TR; r += 32) t += (double)s_e[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) part_e[tile] = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // network on BF16 tensor cores (FP32 accumulation): the same forward / input-
 // gradient chain as k_mlp for a 64-atom tile.  Eight warps: warp w owns rows
 // 16 (w % 4) .. + 16 and one half of each weight chunk's output columns, and
@@ -811,6 +1085,25 @@ size_t mlp_smem_bytes(const DevModel &dm) { return mlp_smem_tr(dm, mlp_tr(dm)); 
 
 size_t mlp_smem_tr_public(const DevModel &dm, int tr) { return mlp_smem_tr(dm, tr); }
 
+// the resident-weight FP32 network applies: descriptor length and hidden
+// widths all 64, one or two hidden layers, 16-byte aligned weight rows
+static bool mlp_res_ok(const DevModel &dm) {
+    if (dm.precision != TMD_PREC_FP32 || dm.L < 1 || dm.L > RW_MAXL || dm.dims[dm.L + 1] != 1) return false;
+    for (int l = 0; l <= dm.L; ++l)
+        if (dm.dims[l] != RW_N || dm.off_f[l] % 4 != 0) return false;
+    for (int s = 0; s < dm.S; ++s)
+        if (reinterpret_cast<uintptr_t>(dm.wf[s]) % 16 != 0) return false;
+    return true;
+}
+
+// tile_rows 0 (built-in choice) or 128 selects it where it applies
+static bool mlp_use_res(const DevModel &dm) { return (dm.tile_rows == 0 || dm.tile_rows == RW_TR) && mlp_res_ok(dm); }
+
+bool mlp_rows_ok(const DevModel &dm, int tr) {
+    if (tr == RW_TR) return mlp_res_ok(dm);
+    return (tr == 32 || tr == 64) && mlp_smem_tr(dm, tr) <= 227 * 1024;
+}
+
 static tmd_status validate(const tmd_model *model, tmd_nlist *nl, int64_t n, const double box[3]) {
     if (!model || !nl) {
         set_error("null model or neighbour table");
@@ -855,6 +1148,7 @@ static tmd_status set_mlp_smem(const DevModel &dm, bool bf16) {
         }
         return TMD_OK;
     }
+    if (mlp_use_res(dm)) return TMD_OK;   // k_mlp_res sets its own
     const int tr = mlp_tr(dm);
     const size_t smem = mlp_smem_bytes(dm);
     size_t &done = smem_set[tr == 64 ? 1 : 0];
@@ -885,6 +1179,22 @@ static tmd_status launch_network(const DevModel &dm, const int32_t *perm, const 
         TMD_LAUNCH("k_mlp_bf16", s, k_mlp_bf16<<<ntile, BF_THREADS, mlp_bf16_smem_bytes(dm), s>>>(
                                         dm, perm, types, n, G, dG, e_atom, part_e, bcfg.bnc, bcfg.compact ? 1 : 0));
         *ntile_out = ntile;
+    } else if (mlp_use_res(dm)) {
+        static int per_sm = 0, nsm = 0;   // resident blocks of k_mlp_res per SM
+        if (!per_sm) {
+            const int smem = (int)(RW_SMEM_FLOATS * sizeof(float));
+            TMD_CUDA(cudaFuncSetAttribute(k_mlp_res, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            int dev = 0;
+            TMD_CUDA(cudaGetDevice(&dev));
+            TMD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            TMD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_res, RW_THREADS, smem));
+            per_sm = std::max(per_sm, 1);
+        }
+        const int64_t ntile = (n + RW_TR - 1) / RW_TR;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntile, (int64_t)per_sm * nsm));
+        TMD_LAUNCH("k_mlp_res", s, k_mlp_res<<<grid, RW_THREADS, RW_SMEM_FLOATS * sizeof(float), s>>>(
+                                       dm, perm, types, n, G, dG, e_atom, part_e));
+        *ntile_out = (int)ntile;
     } else {
         const int tr = mlp_tr(dm);
         const int ntile = (int)((n + tr - 1) / tr);

@@ -61,6 +61,8 @@ constexpr int PAIR_WARPS = 4;   // warps (atoms in flight) per block of the pair
 int pair_blocks(const DevModel &dm, int64_t n);
 // shared memory of the FP32 network kernel with tr-atom tiles
 size_t mlp_smem_tr_public(const DevModel &dm, int tr);
+// tile_rows tr (32 / 64: streamed weights; 128: resident weights) can run this network
+bool mlp_rows_ok(const DevModel &dm, int tr);
 size_t mlp_bf16_smem_bytes(const DevModel &dm);
 // tcgen05 form of the BF16 network (mlp_umma.cu)
 bool mlp_umma_supported(const DevModel &dm);

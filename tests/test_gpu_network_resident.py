@@ -1,0 +1,101 @@
+"""The FP32 network kernel with resident weights (k_mlp_res: 128-atom tiles,
+an 8 x 8 result block per thread, the weights of one species kept in shared
+memory for the whole launch), chosen by default for networks whose
+descriptor length and hidden widths are all 64.  It is held to the plain FP32
+bars against the FP64 oracle, agrees with the streamed-weight kernel
+(tile_rows 64) to FP32 rounding, and covers ragged last tiles, tiles holding
+two species (a weight reload inside a tile), one hidden layer and SquarePlus."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2310_08439_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _eval(tmd, m, s, r_list):
+    import torch
+    nl = tmd.NeighborList()
+    pos = torch.as_tensor(s.pos, dtype=torch.float64, device="cuda")
+    types = torch.as_tensor(s.types, dtype=torch.int32, device="cuda")
+    nl.build(pos, types, s.box, s.pbc, r_list)
+    tmd.profile_read(reset=True)
+    tmd.profile_enable(True)
+    try:
+        out = tmd.evaluate(m, nl, pos, types, s.box)
+        torch.cuda.synchronize()
+        names = set(tmd.profile_read(reset=True))
+    finally:
+        tmd.profile_enable(False)
+    return {"energy": float(out["energy"].item()), "e_atom": out["e_atom"].double().cpu().numpy(),
+            "forces": out["forces"].double().cpu().numpy(), "virial": out["virial"].cpu().numpy().reshape(3, 3),
+            "kernels": names}
+
+
+def _system(reps, a, n_species, seed):
+    rng = np.random.default_rng(seed)
+    pos, box = I.lattice("fcc", reps, a)
+    types = rng.integers(0, n_species, len(pos)).astype(np.int32)
+    return I.System(I.jitter_and_wrap(pos, box, 0.1, rng), types, box, np.ones(3, np.int32))
+
+
+def _cases():
+    large = I.large(reps=6)   # 864 atoms of the 1M-atom cell's lattice and model: 6 full tiles + 96 rows
+    return {
+        "large_model_ragged": (large.model, large.systems[0]),
+        # 2 species x K = 8 -> 64 descriptor columns; random species: most tiles hold both
+        "two_species_squareplus": (I.random_model(2, 8, 5.5, [64, 64], seed=12, activation="squareplus"),
+                                   _system((5, 5, 4), 3.7, 2, 13)),
+        "one_hidden_layer": (I.random_model(1, 16, 5.0, [64], seed=14), _system((4, 4, 4), 3.6, 1, 15)),
+    }
+
+
+@pytest.mark.parametrize("case", ["large_model_ragged", "two_species_squareplus", "one_hidden_layer"])
+def test_resident_network_matches_oracle_and_streamed_kernel(tmdlib, case, capsys):
+    p, s = _cases()[case]
+    o = O.evaluate(O.OracleModel(p), s.pos, s.types, s.box, s.pbc)
+    rms = float(np.sqrt((o["forces"] ** 2).mean()))
+    m = tmdlib.Model(p)
+    res = _eval(tmdlib, m, s, p.rc)
+    assert "k_mlp_res" in res["kernels"] and "k_mlp" not in res["kernels"], res["kernels"]
+    m.tuning = {"tile_rows": 64, "pair_blocks_per_sm": 0}
+    ref = _eval(tmdlib, m, s, p.rc)
+    assert "k_mlp" in ref["kernels"] and "k_mlp_res" not in ref["kernels"], ref["kernels"]
+    dE = abs(res["energy"] - o["energy"]) / abs(o["energy"])
+    dF = np.abs(res["forces"] - o["forces"]).max() / rms
+    dW = np.abs(res["virial"] - o["virial"]).max() / np.abs(o["virial"]).max()
+    dEa = np.abs(res["e_atom"] - o["e_atom"]).max() / np.abs(o["e_atom"]).max()
+    cross_F = np.abs(res["forces"] - ref["forces"]).max() / rms
+    cross_Ea = np.abs(res["e_atom"] - ref["e_atom"]).max() / np.abs(ref["e_atom"]).max()
+    with capsys.disabled():
+        print(f"\n[{case} n={len(s.pos)}] dE/E={dE:.2e} max|dF|/rms={dF:.2e} dW/max={dW:.2e} "
+              f"dEa/max={dEa:.2e}; vs streamed kernel max|dF|/rms={cross_F:.2e} dEa/max={cross_Ea:.2e}")
+    assert dE <= 1e-6 and dF <= 1e-5 and dW <= 1e-5 and dEa <= 1e-5
+    # two FP32 summation orders of the same products
+    assert cross_F <= 2e-6 and cross_Ea <= 2e-6
+
+
+def test_resident_network_tuning_choice(tmdlib):
+    """tile_rows 128 selects the resident kernel where it applies and is a
+    candidate of the autotuner; on a network it cannot run (descriptor
+    length 128) the built-in choice stays the streamed kernel."""
+    import torch
+    w = I.large(reps=4)
+    s = w.systems[0]
+    m = tmdlib.Model(w.model)
+    m.tuning = {"tile_rows": 128, "pair_blocks_per_sm": 0}
+    assert m.tuning["tile_rows"] == 128
+    res = _eval(tmdlib, m, s, w.model.rc)
+    assert "k_mlp_res" in res["kernels"]
+    pos = torch.as_tensor(s.pos, dtype=torch.float64, device="cuda")
+    types = torch.as_tensor(s.types, dtype=torch.int32, device="cuda")
+    nl = tmdlib.NeighborList()
+    nl.build(pos, types, s.box, s.pbc, w.model.rc)
+    best = tmdlib.autotune(m, nl, pos, types, s.box)
+    assert best["tile_rows"] in (32, 64, 128)
+    med = I.medium()
+    m2 = tmdlib.Model(med.model)
+    m2.tuning = {"tile_rows": 128, "pair_blocks_per_sm": 0}
+    r2 = _eval(tmdlib, m2, _system((4, 4, 4), 3.61, 2, 3), med.model.rc)
+    assert "k_mlp" in r2["kernels"] and "k_mlp_res" not in r2["kernels"]
