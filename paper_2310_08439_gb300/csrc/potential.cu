@@ -361,35 +361,46 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
 // network, FP32 SIMT with resident weights: networks whose descriptor length
 // and hidden widths are all 64, with one or two hidden layers.
 //
-// A persistent block of 128 threads keeps one species' weight matrices in
+// A persistent block of 256 threads keeps one species' weight matrices in
 // shared memory and walks a contiguous range of 128-atom tiles (perm order,
 // so the species changes at most S - 1 times per block).  Every product of
 // the chain (forward layers, then the input-gradient chain) is
-// [128 x 64] x [64 x 64]: each thread owns an 8 x 8 block of the result
-// (atoms 4 rb .. 4 rb + 3 and 64 + 4 rb .. 64 + 4 rb + 3, columns 8 cb ..
-// 8 cb + 7) and runs 64 multiply-adds per two float4 activation loads and two
-// float4 weight loads.  Each weight matrix is stored once in 4 x 4 blocks:
-// the forward products read rows of a block, the backward products (which
-// multiply by W^T) read its columns from the same copy after loading the
-// whole block.  The rows inside a block are XOR-swizzled so that the four
-// column groups of a warp read distinct banks in both directions.  The output
-// layer (E_a and dz_L) is formed in the epilogue of the last forward product.
+// [128 x 64] x [64 x 64]: each thread owns an 8 x 4 block of the result
+// (atoms 4 rb .. 4 rb + 3 and 64 + 4 rb .. 64 + 4 rb + 3, columns 4 cb ..
+// 4 cb + 3) and runs 32 multiply-adds per two float4 activation loads and
+// one float4 weight load.  Each weight matrix is stored once in 4 x 4
+// blocks: the forward products read rows of a block, the backward products
+// (which multiply by W^T) read its columns from the same copy after loading
+// the whole block.  The rows inside a block are XOR-swizzled so that the
+// four column groups of a warp read distinct banks in both directions.  The
+// output layer (E_a and dz_L) is formed in the epilogue of the last forward
+// product.
+//
+// Two activation buffers X and Y alternate their roles from tile to tile.
+// A tile starts with its G rows already in X (row-major, copied by cp.async
+// while the previous tile ran its last product); they are transposed into Y,
+// and the chain runs Y -> X (a_1) -> Y (dz_2) -> X (dz_1 over a_1) -> G'.
+// The last product reads only X, so the next tile's G rows are copied into
+// Y meanwhile, and Y becomes the next tile's X.
 // ---------------------------------------------------------------------------
 constexpr int RW_TR = 128;              // atoms per tile
-constexpr int RW_THREADS = 128;         // 4 warps, an 8 x 8 result block per thread
+constexpr int RW_THREADS = 256;         // 8 warps, an 8 x 4 result block per thread
 constexpr int RW_N = 64;                // descriptor length and every hidden width
 constexpr int RW_LDT = RW_TR + 4;       // row stride of the transposed activations
+constexpr int RW_LDG = RW_N + 4;        // row stride of staged G rows (conflict-free float4 reads)
 constexpr int RW_MAXL = 2;              // hidden layers
 constexpr int RW_WF = RW_N * RW_N;      // floats per weight matrix
+constexpr int RW_BUF = (RW_N * RW_LDT > RW_TR * RW_LDG) ? RW_N * RW_LDT : RW_TR * RW_LDG;
+constexpr int RW_CG = 4;                // column groups: energy partials of a row come from 4 warp pairs
 
 // dynamic shared memory: weights, two activation buffers, biases, output
-// weights and bias, the energy partials of the two column halves
+// weights and bias, the energy partials of the column groups
 constexpr size_t RW_SMEM_FLOATS =
-    (size_t)RW_MAXL * RW_WF + 2 * (size_t)RW_N * RW_LDT + RW_MAXL * RW_N + RW_N + 4 + 2 * RW_TR;
+    (size_t)RW_MAXL * RW_WF + 2 * (size_t)RW_BUF + RW_MAXL * RW_N + RW_N + 4 + RW_CG * RW_TR;
 
 // place of element (k, o) of a 64 x 64 matrix in the blocked, swizzled layout
 __device__ __forceinline__ int rw_widx(int k, int o) {
-    const int kb = k >> 2, ob = o >> 2, f = ((kb >> 1) ^ (ob >> 1)) & 3;
+    const int kb = k >> 2, ob = o >> 2, f = (kb ^ (ob >> 1)) & 3;
     return ((kb * 16 + ob) << 4) + (((k & 3) ^ f) << 2) + (o & 3);
 }
 
@@ -397,50 +408,55 @@ __device__ __forceinline__ float rw_comp(const float4 v, int c) {
     return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
-// acc[i][c] = sum_k At[k][atom i] B[k][col c] over k = 0..63, where B = W
-// (forward: W stored [in][out]) or B = W^T (backward)
+// acc[i][c] = sum_k At[k][atom i] B[k][4 cb + c] over k = 0..63, where B = W
+// (forward: W stored [in][out]) or B = W^T (backward).  The multiply-adds run
+// on packed FP32x2 (fma.rn.f32x2, each half rounded as fmaf): atom pairs
+// (i, i + 1) against a duplicated weight, so one instruction does two.
 template <bool BWD>
-__device__ __forceinline__ void rw_product(const float *At, const float *Wm, int rb, int cb, float (&acc)[8][8]) {
+__device__ __forceinline__ void rw_product(const float *At, const float *Wm, int rb, int cb, float (&acc)[8][4]) {
+    float2 acc2[4][4];   // acc2[j][c] = (acc[2 j][c], acc[2 j + 1][c])
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[i][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc2[j][c] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int g = 0; g < RW_N / 4; ++g) {
-        // forward: blocks (g, 2 cb) and (g, 2 cb + 1), one row per k;
-        // backward: blocks (2 cb, g) and (2 cb + 1, g), one column per k
-        const int f = (cb ^ (g >> 1)) & 3;
-        const float *b0 = Wm + (BWD ? 16 * (32 * cb + g) : 16 * (16 * g + 2 * cb));
-        const float *b1 = b0 + (BWD ? 256 : 16);
-        float4 w0[4], w1[4];   // logical rows 0..3 of the two blocks
+        // forward: block (g, cb), row k & 3 for k = 4 g .. 4 g + 3;
+        // backward: block (cb, g), column k & 3
+        const float *bk = Wm + (BWD ? 16 * (16 * cb + g) : 16 * (16 * g + cb));
+        const int f = BWD ? ((cb ^ (g >> 1)) & 3) : ((g ^ (cb >> 1)) & 3);
+        float4 w[4];   // logical rows 0..3 of the block
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            w0[r] = *reinterpret_cast<const float4 *>(b0 + 4 * (r ^ f));
-            w1[r] = *reinterpret_cast<const float4 *>(b1 + 4 * (r ^ f));
-        }
+        for (int r = 0; r < 4; ++r) w[r] = *reinterpret_cast<const float4 *>(bk + 4 * (r ^ f));
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const float *a = At + (4 * g + r) * RW_LDT + 4 * rb;
             const float4 a0 = *reinterpret_cast<const float4 *>(a);
             const float4 a1 = *reinterpret_cast<const float4 *>(a + 64);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float wv[8];
+            const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                                  make_float2(a1.z, a1.w)};
+            float wv[4];
             if (!BWD) {
-                wv[0] = w0[r].x; wv[1] = w0[r].y; wv[2] = w0[r].z; wv[3] = w0[r].w;
-                wv[4] = w1[r].x; wv[5] = w1[r].y; wv[6] = w1[r].z; wv[7] = w1[r].w;
+                wv[0] = w[r].x; wv[1] = w[r].y; wv[2] = w[r].z; wv[3] = w[r].w;
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    wv[q] = rw_comp(w0[q], r);
-                    wv[4 + q] = rw_comp(w1[q], r);
-                }
+                for (int q = 0; q < 4; ++q) wv[q] = rw_comp(w[q], r);
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int c = 0; c < 4; ++c) {
+                const float2 w2 = make_float2(wv[c], wv[c]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[i][c] = fmaf(av[i], wv[c], acc[i][c]);
+                for (int j = 0; j < 4; ++j) acc2[j][c] = __ffma2_rn(ap[j], w2, acc2[j][c]);
+            }
         }
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc[2 * j][c] = acc2[j][c].x;
+            acc[2 * j + 1][c] = acc2[j][c].y;
+        }
 }
 
 // the 8 atoms of a thread's result block as two float4 of a transposed row
@@ -469,21 +485,39 @@ __device__ __forceinline__ void rw_load_species(const DevModel &m, int s, float 
     if (threadIdx.x == 0) sBout[0] = __ldg(wo + RW_N);
 }
 
+// half h (threadIdx.x >> 7) of the G row at perm position p0 + (threadIdx.x
+// & 127) (zeros beyond n) -> the staging buffer (row-major, stride RW_LDG),
+// by cp.async; not waited for
+__device__ __forceinline__ void rw_stage_g(const float *__restrict__ G, int64_t p0, int64_t n, float *X) {
+    const int row = threadIdx.x & (RW_TR - 1), h = threadIdx.x >> 7;
+    const int64_t p = p0 + row;
+    const bool ok = p < n;
+    const float *src = ok ? G + (size_t)p * RW_N + 32 * h : G;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(X + row * RW_LDG + 32 * h);
+    const int bytes = ok ? 16 : 0;   // 0: the 16 bytes are zero-filled
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + 16 * c4),
+                     "l"(src + (ok ? 4 * c4 : 0)), "r"(bytes));
+    cp_async_commit();
+}
+
 __global__ void __launch_bounds__(RW_THREADS, 2) k_mlp_res(DevModel m, const int32_t *__restrict__ perm,
                                                         const int32_t *__restrict__ types, int64_t n,
                                                         const float *__restrict__ G, float *__restrict__ dG,
                                                         float *__restrict__ e_atom, double *__restrict__ part_e) {
     extern __shared__ __align__(16) float sm[];
     float *sW = sm;                                  // L blocked 64 x 64 matrices
-    float *bufA = sW + RW_MAXL * RW_WF;              // G, then dz_L        ([64][RW_LDT])
-    float *bufB = bufA + RW_N * RW_LDT;              // a_1 (L = 2) or dz_1 (L = 1), then dz_1
-    float *sBias = bufB + RW_N * RW_LDT;             // [L][64]
+    float *buf0 = sW + RW_MAXL * RW_WF;              // the two activation buffers
+    float *sBias = buf0 + 2 * RW_BUF;                // [L][64]
     float *sWout = sBias + RW_MAXL * RW_N;           // [64]
     float *sBout = sWout + RW_N;                     // [1] (+ 3 pad)
-    float *sEp = sBout + 4;                          // [2][RW_TR]
-    __shared__ int s_atom[RW_TR], s_type[RW_TR];
-    __shared__ float s_e[RW_TR];
-    __shared__ int s_lohi[RW_THREADS / 32][2];
+    float *sEp = sBout + 4;                          // [RW_CG][RW_TR]
+    // per tile parity: atoms, species, energies and the warps' species
+    // ranges (a tile's are written during the previous tile's last product)
+    __shared__ int s_atom2[2][RW_TR], s_type2[2][RW_TR];
+    __shared__ float s_e2[2][RW_TR];
+    __shared__ int s_lohi2[2][RW_THREADS / 32][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rb = (lane & 7) + 8 * (warp & 1), cb = (lane >> 3) + 4 * (warp >> 1);
     const int L = m.L, act = m.act;
@@ -491,77 +525,96 @@ __global__ void __launch_bounds__(RW_THREADS, 2) k_mlp_res(DevModel m, const int
     const int64_t ntile = (n + RW_TR - 1) / RW_TR;
     const int64_t t_beg = ntile * blockIdx.x / gridDim.x, t_end = ntile * (blockIdx.x + 1) / gridDim.x;
     int loaded = -1;   // species whose weights are in sW
-    float acc[8][8];
+    int xb = 0;        // buffer holding the tile's staged G rows
+    float acc[8][4];
+    // atoms and species of tile t at parity par (threads >= RW_TR only take
+    // part in the warp reductions)
+    auto publish = [&](int par, int a, int ty) {
+        if (tid < RW_TR) {
+            s_atom2[par][tid] = a;
+            s_type2[par][tid] = ty;
+            s_e2[par][tid] = 0.f;
+        }
+        const int lo = __reduce_min_sync(0xffffffffu, ty >= 0 ? ty : TMD_MAX_SPECIES);
+        const int hi = __reduce_max_sync(0xffffffffu, ty);
+        if (lane == 0) { s_lohi2[par][warp][0] = lo; s_lohi2[par][warp][1] = hi; }
+    };
+    if (t_beg < t_end) {
+        rw_stage_g(G, t_beg * RW_TR, n, buf0);
+        const int64_t p = t_beg * RW_TR + tid;
+        const int a = (tid < RW_TR && p < n) ? perm[p] : -1;
+        publish(0, a, a >= 0 ? types[a] : -1);
+        __syncthreads();
+    }
     for (int64_t tile = t_beg; tile < t_end; ++tile) {
         const int64_t p0 = tile * RW_TR;
-        __syncthreads();   // the previous tile is done with every buffer
-        {
-            const int64_t p = p0 + tid;
-            const int a = p < n ? perm[p] : -1;
-            const int ty = a >= 0 ? types[a] : -1;
-            s_atom[tid] = a;
-            s_type[tid] = ty;
-            s_e[tid] = 0.f;
-            const int lo = __reduce_min_sync(0xffffffffu, ty >= 0 ? ty : TMD_MAX_SPECIES);
-            const int hi = __reduce_max_sync(0xffffffffu, ty);
-            if (lane == 0) { s_lohi[warp][0] = lo; s_lohi[warp][1] = hi; }
-        }
-        __syncthreads();
+        float *X = buf0 + xb * RW_BUF, *Y = buf0 + (xb ^ 1) * RW_BUF;
+        const int *s_atom = s_atom2[xb], *s_type = s_type2[xb];
+        float *s_e = s_e2[xb];
+        const bool more = tile + 1 < t_end;
+        int next_a = -1, next_ty = -1;   // the next tile's atom and species of this thread's row
+        asm volatile("cp.async.wait_all;\n" ::);   // this thread's staged G row (read by it alone)
         int s_lo = TMD_MAX_SPECIES, s_hi = -1;
 #pragma unroll
         for (int w = 0; w < RW_THREADS / 32; ++w) {
-            s_lo = min(s_lo, s_lohi[w][0]);
-            s_hi = max(s_hi, s_lohi[w][1]);
+            s_lo = min(s_lo, s_lohi2[xb][w][0]);
+            s_hi = max(s_hi, s_lohi2[xb][w][1]);
         }
         for (int s = s_lo; s <= s_hi; ++s) {
-            if (s != s_lo) __syncthreads();   // the last pass is done with bufA / bufB
+            if (s != s_lo) {   // a second species in this tile: its G rows again (X was overwritten)
+                __syncthreads();
+                rw_stage_g(G, p0, n, X);
+                asm volatile("cp.async.wait_all;\n" ::);
+                __syncthreads();
+            }
             if (s != loaded) {
                 rw_load_species(m, s, sW, sBias, sWout, sBout);
                 loaded = s;
             }
-            {   // G row of this thread's atom -> bufA transposed (consecutive atoms: conflict-free)
-                const int a = s_atom[tid];
-                const float4 *g4 = reinterpret_cast<const float4 *>(G + (size_t)(p0 + tid) * RW_N);
-#pragma unroll 4
-                for (int c4 = 0; c4 < RW_N / 4; ++c4) {
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (a >= 0) v = __ldg(g4 + c4);
-                    bufA[(4 * c4) * RW_LDT + tid] = v.x;
-                    bufA[(4 * c4 + 1) * RW_LDT + tid] = v.y;
-                    bufA[(4 * c4 + 2) * RW_LDT + tid] = v.z;
-                    bufA[(4 * c4 + 3) * RW_LDT + tid] = v.w;
+            if (s == s_hi && more && tid < RW_TR) {   // read ahead: the next tile's atom (used before G')
+                const int64_t p = p0 + RW_TR + tid;
+                next_a = p < n ? perm[p] : -1;
+            }
+            {   // half of G row (tid & 127) (X, row-major) -> Y transposed (conflict-free both ways)
+                const int row = tid & (RW_TR - 1), h = tid >> 7;
+                const float *xr = X + row * RW_LDG + 32 * h;
+#pragma unroll
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(xr + 4 * c4);
+                    const int k = 32 * h + 4 * c4;
+                    Y[k * RW_LDT + row] = v.x;
+                    Y[(k + 1) * RW_LDT + row] = v.y;
+                    Y[(k + 2) * RW_LDT + row] = v.z;
+                    Y[(k + 3) * RW_LDT + row] = v.w;
                 }
             }
             __syncthreads();
-            // forward layers; the last one also forms E_a and dz_L = w act'(a_L)
+            // forward layers: G (Y) -> a_1 (X); the last one also forms E_a
+            // and dz_L = w act'(a_L): L = 1 writes dz_1 into X, L = 2 writes
+            // dz_2 into Y (G is dead)
             for (int l = 0; l < L; ++l) {
-                const float *Ain = (l == 0) ? bufA : bufB;
-                float *Cout = (l == L - 1) ? ((L == 1) ? bufB : bufA) : bufB;
+                const float *Ain = (l == 0) ? Y : X;
+                float *Cout = (l == 0) ? X : Y;
                 rw_product<false>(Ain, sW + l * RW_WF, rb, cb, acc);
-                const float4 bl = *reinterpret_cast<const float4 *>(sBias + l * RW_N + 8 * cb);
-                const float4 bh = *reinterpret_cast<const float4 *>(sBias + l * RW_N + 8 * cb + 4);
-                const float bias[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
+                const float4 bv = *reinterpret_cast<const float4 *>(sBias + l * RW_N + 4 * cb);
+                const float bias[4] = {bv.x, bv.y, bv.z, bv.w};
                 if (l < L - 1) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
+                    for (int c = 0; c < 4; ++c) {
                         float v[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) v[i] = act_f(act, acc[i][c] + bias[c], spb);
-                        rw_store_col(Cout, 8 * cb + c, rb, v);
+                        rw_store_col(Cout, 4 * cb + c, rb, v);
                     }
                     __syncthreads();
                 } else {
-                    const float4 wl = *reinterpret_cast<const float4 *>(sWout + 8 * cb);
-                    const float4 wh = *reinterpret_cast<const float4 *>(sWout + 8 * cb + 4);
-                    const float wout[8] = {wl.x, wl.y, wl.z, wl.w, wh.x, wh.y, wh.z, wh.w};
+                    const float4 wv = *reinterpret_cast<const float4 *>(sWout + 4 * cb);
+                    const float wout[4] = {wv.x, wv.y, wv.z, wv.w};
                     float ep[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) ep[i] = 0.f;
-                    // a_L is read by nothing but this epilogue: dz_L is
-                    // written where the product's input no longer lives
-                    // (L = 1: bufB; L = 2: bufA, G being dead)
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
+                    for (int c = 0; c < 4; ++c) {
                         float v[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -569,10 +622,10 @@ __global__ void __launch_bounds__(RW_THREADS, 2) k_mlp_res(DevModel m, const int
                             ep[i] = fmaf(a, wout[c], ep[i]);
                             v[i] = wout[c] * act_da(act, a, spb);
                         }
-                        rw_store_col(Cout, 8 * cb + c, rb, v);
+                        rw_store_col(Cout, 4 * cb + c, rb, v);
                     }
-                    // E partials over this thread's 8 columns -> the 4 column
-                    // groups of the warp (lanes 8 apart) -> the two warp pairs
+                    // E partials over this thread's 4 columns -> the 4 column
+                    // groups of the warp (lanes 8 apart) -> the 4 warp pairs
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         ep[i] += __shfl_xor_sync(0xffffffffu, ep[i], 8);
@@ -584,43 +637,49 @@ __global__ void __launch_bounds__(RW_THREADS, 2) k_mlp_res(DevModel m, const int
                         *reinterpret_cast<float4 *>(e + 64) = make_float4(ep[4], ep[5], ep[6], ep[7]);
                     }
                     __syncthreads();
-                    if (s_type[tid] == s) {
-                        const float e = (sEp[tid] + sEp[RW_TR + tid]) + sBout[0];
+                    if (tid < RW_TR && s_type[tid] == s) {
+                        const float e = ((sEp[tid] + sEp[RW_TR + tid]) + (sEp[2 * RW_TR + tid] + sEp[3 * RW_TR + tid])) +
+                                        sBout[0];
                         s_e[tid] = e;
                         if (e_atom) e_atom[s_atom[tid]] = e;
                     }
                 }
             }
-            // backward: dz_l = (dz_{l+1} W_l^T) act'(a_l) for l = L - 1 .. 1
-            // (L = 2: dz_2 in bufA, a_1 in bufB, dz_1 written over a_1)
+            // L = 2: dz_1 = (dz_2 W_1^T) act'(a_1), written over a_1 (each
+            // thread reads and writes only its own block)
             if (L == 2) {
-                rw_product<true>(bufA, sW + RW_WF, rb, cb, acc);
+                rw_product<true>(Y, sW + RW_WF, rb, cb, acc);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    float *cp = bufB + (8 * cb + c) * RW_LDT + 4 * rb;
+                for (int c = 0; c < 4; ++c) {
+                    const float *cp = X + (4 * cb + c) * RW_LDT + 4 * rb;
                     const float4 a0 = *reinterpret_cast<const float4 *>(cp);
                     const float4 a1 = *reinterpret_cast<const float4 *>(cp + 64);
                     const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                     float v[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) v[i] = acc[i][c] * act_da(act, av[i], spb);
-                    rw_store_col(bufB, 8 * cb + c, rb, v);
+                    rw_store_col(X, 4 * cb + c, rb, v);
                 }
                 __syncthreads();
             }
+            // Y is free from here on: the next tile's G rows go there while
+            // the last product runs
+            if (s == s_hi && more) {
+                rw_stage_g(G, p0 + RW_TR, n, Y);
+                if (next_a >= 0) next_ty = types[next_a];
+            }
             // G' = dz_1 W_0^T -> dG rows of species s (perm position)
-            rw_product<true>(bufB, sW, rb, cb, acc);
+            rw_product<true>(X, sW, rb, cb, acc);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int row = (i < 4) ? 4 * rb + i : 64 + 4 * rb + (i - 4);
-                if (s_type[row] == s) {
-                    float4 *o = reinterpret_cast<float4 *>(dG + (size_t)(p0 + row) * RW_N + 8 * cb);
-                    o[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-                    o[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-                }
+                if (s_type[row] == s)
+                    *reinterpret_cast<float4 *>(dG + (size_t)(p0 + row) * RW_N + 4 * cb) =
+                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
             }
         }
-        __syncthreads();
+        if (more) publish(xb ^ 1, next_a, next_ty);
+        __syncthreads();   // every thread is done with X and s_e; the next tile's atoms are visible
         if (warp == 0) {   // tile energy in FP64, fixed order
             double t = 0.0;
             for (int r = lane; r < RW_TR; r += 32) t += (double)s_e[r];
@@ -628,7 +687,9 @@ __global__ void __launch_bounds__(RW_THREADS, 2) k_mlp_res(DevModel m, const int
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == 0) part_e[tile] = t;
         }
+        xb ^= 1;
     }
+    asm volatile("cp.async.wait_all;\n" ::);
 }
 
 // ---------------------------------------------------------------------------
