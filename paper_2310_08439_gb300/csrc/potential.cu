@@ -159,6 +159,19 @@ __host__ __device__ inline size_t mlp_act_layout(const DevModel &m, int ldt, flo
     return off;
 }
 
+// floats from the first activation buffer to act[l] in the layout above
+__device__ __forceinline__ int mlp_act_offset(const DevModel &m, int ldt, int l) {
+    const bool alias = m.S == 1 && m.L >= 2;
+    if (alias && l == 2) l = 0;
+    int off = 0;
+    for (int q = 0; q < l; ++q) {
+        if (alias && q == 2) continue;
+        const int rows = (alias && q == 0 && m.dims[2] > m.dims[0]) ? m.dims[2] : m.dims[q];
+        off += rows * ldt;
+    }
+    return off;
+}
+
 // One product of the stream.
 // EPI 1: C^T[col][row] = act(acc + bias[col])           (hidden layer forward)
 // EPI 2: C^T[col][row] = acc * act'(C^T[col][row])      (hidden layer backward, in place)
@@ -281,9 +294,11 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
     // shared layout: two weight buffers, then act[l] = [dims[l]][LDT] for
     // l = 0..L, with act[2] over act[0] for a one-species model
     float *wbuf = sm;
-    float *act[MAX_LAYERS + 1];
     constexpr int NP = mlp_np<TR>();
-    mlp_act_layout(m, LDT, sm + 2 * MLP_KC * NP, act);
+    float *const abase = sm + 2 * MLP_KC * NP;
+    // act[l]: computed where it is used (a pointer array indexed by the
+    // runtime layer would live in local memory)
+    auto act = [&](int l) -> float * { return abase + mlp_act_offset(m, LDT, l); };
     if (tid < TR) {
         const int64_t p = p0 + tid;
         const int a = p < n ? perm[p] : -1;
@@ -299,26 +314,27 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
     if (s_lo <= s_hi) mlp_issue<NP>(mlp_step(m, s_lo, 0), 0, 0, wbuf);   // first chunk, under the G loads
     cp_async_commit();
     // G rows -> act[0] transposed (lane per atom row: conflict-free stores)
+    float *const a0 = act(0);
     for (int r = lane; r < TR; r += 32) {
         const int a = s_atom[r];
         for (int c4 = warp; c4 < (Dd >> 2); c4 += MLP_THREADS / 32) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (a >= 0) v = __ldg(reinterpret_cast<const float4 *>(G + (size_t)(p0 + r) * Dd + 4 * c4));
-            act[0][(4 * c4) * LDT + r] = v.x;
-            act[0][(4 * c4 + 1) * LDT + r] = v.y;
-            act[0][(4 * c4 + 2) * LDT + r] = v.z;
-            act[0][(4 * c4 + 3) * LDT + r] = v.w;
+            a0[(4 * c4) * LDT + r] = v.x;
+            a0[(4 * c4 + 1) * LDT + r] = v.y;
+            a0[(4 * c4 + 2) * LDT + r] = v.z;
+            a0[(4 * c4 + 3) * LDT + r] = v.w;
         }
     }
     for (int s = s_lo; s <= s_hi; ++s) {
         const float *wf = m.wf[s], *wb = m.wb[s];
         for (int l = 0; l < L; ++l)
-            mlp_gemm<TR, 1>(m, ws, act[l], wf + m.off_f[l] + m.dims[l] * m.dims[l + 1], act[l + 1], wbuf, nullptr,
+            mlp_gemm<TR, 1>(m, ws, act(l), wf + m.off_f[l] + m.dims[l] * m.dims[l + 1], act(l + 1), wbuf, nullptr,
                             s_atom, s_type);
         __syncthreads();
         // output layer (linear): E_r = b + w . a_L, then dz_L = w * act'(a_L) in place
         const int wl = m.dims[L];
-        float *aL = act[L];
+        float *aL = act(L);
         const float *wout = wb + m.off_b[L];
         if (tid < TR) {
             float v0 = 0.f, v1 = 0.f;
@@ -341,9 +357,9 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
         }
         // dz_l = (dz_{l+1} W_l^T) * act'(a_l), in place over a_l; B[k = o][n = i] = W_l[i][o]
         for (int l = L - 1; l >= 1; --l)
-            mlp_gemm<TR, 2>(m, ws, act[l + 1], nullptr, act[l], wbuf, nullptr, s_atom, s_type);
+            mlp_gemm<TR, 2>(m, ws, act(l + 1), nullptr, act(l), wbuf, nullptr, s_atom, s_type);
         // G' = dz_1 W_0^T
-        mlp_gemm<TR, 3>(m, ws, act[1], nullptr, nullptr, wbuf, dG + (size_t)p0 * Dd, s_atom, s_type);
+        mlp_gemm<TR, 3>(m, ws, act(1), nullptr, nullptr, wbuf, dG + (size_t)p0 * Dd, s_atom, s_type);
     }
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
