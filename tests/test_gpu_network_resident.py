@@ -99,3 +99,58 @@ def test_resident_network_tuning_choice(tmdlib):
     m2.tuning = {"tile_rows": 128, "pair_blocks_per_sm": 0}
     r2 = _eval(tmdlib, m2, _system((4, 4, 4), 3.61, 2, 3), med.model.rc)
     assert "k_mlp" in r2["kernels"] and "k_mlp_res" not in r2["kernels"]
+
+
+def test_resident_network_species_changes_between_tiles_of_a_block(tmdlib, capsys):
+    """More tiles than resident blocks (55,296 atoms, 432 tiles on 304
+    blocks): a block walks a contiguous run of tiles and reloads the weights
+    where the species changes.  Perm order groups atoms by species, and
+    exactly 215 x 128 atoms are species 0, so the change falls between tiles
+    214 and 215, which one block takes in a row on a 152-SM GPU with two
+    blocks per SM.  Checked against the streamed-weight kernel, itself held to
+    the oracle by the other tests."""
+    import torch
+    p = I.random_model(2, 8, 5.5, [64, 64], seed=16)
+    s = _system((24, 24, 24), 3.7, 2, 17)
+    rng = np.random.default_rng(18)
+    types = np.ones(len(s.pos), np.int32)
+    types[rng.choice(len(s.pos), 215 * 128, replace=False)] = 0
+    s = I.System(s.pos, types, s.box, s.pbc)
+    m = tmdlib.Model(p)
+    res = _eval(tmdlib, m, s, p.rc)
+    assert "k_mlp_res" in res["kernels"]
+    m.tuning = {"tile_rows": 64, "pair_blocks_per_sm": 0}
+    ref = _eval(tmdlib, m, s, p.rc)
+    rms = float(np.sqrt((ref["forces"] ** 2).mean()))
+    cross_F = np.abs(res["forces"] - ref["forces"]).max() / rms
+    cross_Ea = np.abs(res["e_atom"] - ref["e_atom"]).max() / np.abs(ref["e_atom"]).max()
+    with capsys.disabled():
+        print(f"\n[n={len(s.pos)}] resident vs streamed max|dF|/rms={cross_F:.2e} dEa/max={cross_Ea:.2e} "
+              f"dE/E={abs(res['energy'] - ref['energy']) / abs(ref['energy']):.2e}")
+    # two FP32 summation orders, each within ~3e-6 of the oracle's forces
+    # (the 1e-5 bar); the maximum over 55k atoms reaches further into the
+    # tail than over the small cells above.  A weight-reload mistake would
+    # show as errors of order one.
+    assert cross_F <= 5e-6 and cross_Ea <= 2e-6
+    assert abs(res["energy"] - ref["energy"]) <= 1e-7 * abs(ref["energy"])
+    del torch
+
+
+def test_resident_network_in_a_batch(tmdlib):
+    """A batch of uneven systems with a 64-wide network: the batched
+    evaluation (one set of launches over the CSR layout) equals each system
+    evaluated alone."""
+    import torch
+    p = I.random_model(1, 16, 5.0, [64, 64], seed=18)
+    systems = [_system(r, a, 1, 19 + k) for k, (r, a) in enumerate([((3, 3, 3), 3.6), ((5, 4, 4), 3.7),
+                                                                   ((6, 6, 5), 3.65), ((4, 4, 3), 3.8)])]
+    m = tmdlib.Model(p)
+    b = tmdlib.Batch(systems)
+    E, W = b.compute(m, list(range(len(systems))))
+    for k, s in enumerate(systems):
+        one = _eval(tmdlib, m, s, p.rc)
+        assert "k_mlp_res" in one["kernels"]
+        _, _, fb = b.get_system(k)
+        assert abs(E[k] - one["energy"]) <= 1e-12 * abs(one["energy"]) + 1e-9, k
+        assert np.abs(fb - one["forces"]).max() <= 1e-6 * max(np.abs(one["forces"]).max(), 1e-6), k
+    del torch

@@ -43,13 +43,15 @@ def _outputs(n):
 
 @pytest.mark.parametrize("wname,precision,force_kernel", [("tiny", "fp32", "auto"), ("medium", "fp32", "auto"),
                                                          ("tiny", "bf16", "auto"), ("medium", "bf16", "auto"),
-                                                         ("tiny", "fp32", "tensor")])
+                                                         ("tiny", "fp32", "tensor"), ("large", "fp32", "auto")])
 def test_noalloc_matches_compute_two_calls(tmdlib, wname, precision, force_kernel):
     """Both network forms; with the tensor-core force pass chosen, tmd_compute
     runs it and the allocation-free call runs the SIMT pass (it keeps no pair
     cache), and the two still agree within the FP32 bars."""
     torch = _torch()
-    w = getattr(I, wname)()
+    # "large": 2,048 atoms of the 1M-atom cell's lattice and model, whose
+    # 64-wide network runs on the resident-weight kernel
+    w = I.large(reps=8) if wname == "large" else getattr(I, wname)()
     s = w.systems[0]
     m = tmdlib.Model(w.model)
     if precision == "bf16":
