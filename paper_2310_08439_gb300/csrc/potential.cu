@@ -204,7 +204,46 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
             mlp_prefetch_next<NP>(m, ws, st, wbuf);
             cp_async_wait1();
             __syncthreads();   // this chunk has landed for every thread; At is complete
-            if (active) {
+            if (active && TR == 32) {
+                // the same sums on packed FP32x2 multiply-adds (each half
+                // rounds as fmaf): atom pairs (0, 1) and (2, 3) of the row
+                // block against a duplicated weight
+                const float *a = At + (size_t)k0 * LDT + rb * 4;
+                const float *b = wbuf + ws.par * (MLP_KC * NP) + cb * 4;
+                for (int kg = 0; kg < kc; kg += 16) {
+                    float2 pp2[2][4];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) pp2[j][o] = make_float2(0.f, 0.f);
+                    const int ke = min(kg + 16, kc);
+                    auto step2 = [&](int k) {
+                        const float4 av = *reinterpret_cast<const float4 *>(a + k * LDT);
+                        const float4 bv = *reinterpret_cast<const float4 *>(b + k * np);
+                        const float2 a01 = make_float2(av.x, av.y), a23 = make_float2(av.z, av.w);
+                        const float bo[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) {
+                            const float2 w2 = make_float2(bo[o], bo[o]);
+                            pp2[0][o] = __ffma2_rn(a01, w2, pp2[0][o]);
+                            pp2[1][o] = __ffma2_rn(a23, w2, pp2[1][o]);
+                        }
+                    };
+                    if (ke - kg == 16) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) step2(kg + k);
+                    } else {
+                        for (int k = kg; k < ke; ++k) step2(k);
+                    }
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        acc[0][o] += pp2[0][o].x;
+                        acc[1][o] += pp2[0][o].y;
+                        acc[2][o] += pp2[1][o].x;
+                        acc[3][o] += pp2[1][o].y;
+                    }
+                }
+            } else if (active) {
                 const float *a = At + (size_t)k0 * LDT + rb * 4;
                 const float *b = wbuf + ws.par * (MLP_KC * NP) + cb * 4;
                 // groups of 16 products summed separately, then added to acc
