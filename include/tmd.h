@@ -227,7 +227,7 @@ int64_t tmd_graph_replays(void);
  *                      descriptor length and hidden widths are all 64, one or
  *                      two hidden layers; other networks fall back to the
  *                      built-in choice), 0 = built-in choice (128 where it
- *                      applies, else 64 or 32 by shared-memory footprint);
+ *                      applies, else 32);
  *  pair_blocks_per_sm  blocks per SM of the persistent descriptor / force
  *                      grids (0 = built-in 16);
  *  ms                  output of the tuners: measured milliseconds of one

@@ -244,6 +244,8 @@ __device__ __forceinline__ void mlp_gemm(const DevModel &m, MlpStream &ws, const
                     }
                 }
             } else if (active) {
+                // 64-atom tiles run four blocks per SM at 64 registers, where
+                // the packed form's register pairs would cost a block
                 const float *a = At + (size_t)k0 * LDT + rb * 4;
                 const float *b = wbuf + ws.par * (MLP_KC * NP) + cb * 4;
                 // groups of 16 products summed separately, then added to acc
@@ -1190,11 +1192,11 @@ static size_t mlp_smem_tr(const DevModel &dm, int tr) {
     return fl * sizeof(float);
 }
 
-// atoms per tile: 64 unless the activations of the wider networks would leave
-// room for fewer than two blocks per SM
+// atoms per tile of the streamed-weight kernel: the tuning's 32 or 64, else
+// 32 (its inner product runs on packed FP32x2 multiply-adds)
 static int mlp_tr(const DevModel &dm) {
     if ((dm.tile_rows == 32 || dm.tile_rows == 64) && mlp_smem_tr(dm, dm.tile_rows) <= 227 * 1024) return dm.tile_rows;
-    return mlp_smem_tr(dm, 64) <= 100 * 1024 ? 64 : 32;
+    return 32;
 }
 
 size_t mlp_smem_bytes(const DevModel &dm) { return mlp_smem_tr(dm, mlp_tr(dm)); }
