@@ -415,8 +415,9 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
 }
 
 // ---------------------------------------------------------------------------
-// network, FP32 SIMT with resident weights: networks whose descriptor length
-// and hidden widths are all 64, with one or two hidden layers.
+// network, FP32 SIMT with resident weights (E_a = NNP(G_a) and G' = dE_a/dG_a,
+// Sec. "The Tensor Formalism"): networks whose descriptor length and hidden
+// widths are all 64, with one or two hidden layers.
 //
 // A persistent block of 256 threads keeps one species' weight matrices in
 // shared memory and walks a contiguous range of 128-atom tiles (perm order,
@@ -424,8 +425,8 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
 // the chain (forward layers, then the input-gradient chain) is
 // [128 x 64] x [64 x 64]: each thread owns an 8 x 4 block of the result
 // (atoms 4 rb .. 4 rb + 3 and 64 + 4 rb .. 64 + 4 rb + 3, columns 4 cb ..
-// 4 cb + 3) and runs 32 multiply-adds per two float4 activation loads and
-// one float4 weight load.  Each weight matrix is stored once in 4 x 4
+// 4 cb + 3) and runs 32 multiply-adds (16 packed FP32x2 instructions) per
+// two float4 activation loads and one float4 weight load.  Each weight matrix is stored once in 4 x 4
 // blocks: the forward products read rows of a block, the backward products
 // (which multiply by W^T) read its columns from the same copy after loading
 // the whole block.  The rows inside a block are XOR-swizzled so that the
@@ -436,9 +437,10 @@ __global__ void __launch_bounds__(MLP_THREADS, TR == 64 ? 4 : 2) k_mlp(DevModel 
 // Two activation buffers X and Y alternate their roles from tile to tile.
 // A tile starts with its G rows already in X (row-major, copied by cp.async
 // while the previous tile ran its last product); they are transposed into Y,
-// and the chain runs Y -> X (a_1) -> Y (dz_2) -> X (dz_1 over a_1) -> G'.
-// The last product reads only X, so the next tile's G rows are copied into
-// Y meanwhile, and Y becomes the next tile's X.
+// and the chain runs Y -> X (a_1) -> Y (dz_2) -> X (dz_1 over a_1) -> G'
+// (one hidden layer: Y -> X (dz_1) -> G').  The last product reads only X,
+// so the next tile's G rows are copied into Y meanwhile, and Y becomes the
+// next tile's X.
 // ---------------------------------------------------------------------------
 constexpr int RW_TR = 128;              // atoms per tile
 constexpr int RW_THREADS = 256;         // 8 warps, an 8 x 4 result block per thread
