@@ -567,6 +567,18 @@ __device__ __forceinline__ long long to_fixed(float g) {
     return (long long)h1 * 4194304LL + (long long)h2;
 }
 
+// Sum of a fixed-point value over the 32 lanes of a warp, exact modulo 2^64
+// (two's complement): each lane's value is cut into 21-, 21- and 22-bit
+// chunks, whose lane sums (< 2^27) fit the 32-bit warp reduction, and the
+// three sums are put back together.  Every lane receives the total.
+__device__ __forceinline__ long long warp_sum_fixed(long long v) {
+    const unsigned long long u = (unsigned long long)v;
+    const unsigned c0 = __reduce_add_sync(0xffffffffu, (unsigned)(u & 0x1FFFFFull));
+    const unsigned c1 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> 21) & 0x1FFFFFull));
+    const unsigned c2 = __reduce_add_sync(0xffffffffu, (unsigned)(u >> 42));
+    return (long long)((unsigned long long)c0 + ((unsigned long long)c1 << 21) + ((unsigned long long)c2 << 42));
+}
+
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     const float y = x - comp;
     const float t = sum + y;
@@ -574,28 +586,39 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
-// The rest of g_ij once V_d and W_d of the pair are known.
-__device__ __forceinline__ void pair_grad_tail(const float (&V)[NMOM], const float (&Wd)[NMOM], float ux, float uy,
-                                               float uz, float ir, float &gxs, float &gys, float &gzs) {
-    float M[NMOM];
-    moments20(ux, uy, uz, M);
-    float w0 = Wd[0], w1 = 0.f, w2 = 0.f, w3 = 0.f;
+// The rest of g_ij once V_d and W_d of the pair are known, as packed pairs
+// (d, d + 1).  The moments are formed in the same pairs, so that
+// dE/dr = sum_d W_d M_d runs on FP32x2 multiply-adds.
+__device__ __forceinline__ void pair_grad_tail(const float2 (&V2)[NMOM / 2], const float2 (&W2)[NMOM / 2], float ux,
+                                               float uy, float uz, float ir, float &gxs, float &gys, float &gzs) {
+    // M2[q] = (M_2q, M_2q+1) in the row order of moments20
+    float2 M2[NMOM / 2];
+    M2[0] = make_float2(1.f, ux);
+    M2[1] = make_float2(uy, uz);
+    M2[2] = make_float2(ux * ux, ux * uy);
+    M2[3] = make_float2(ux * uz, uy * uy);
+    M2[4] = make_float2(uy * uz, uz * uz);
+    M2[5] = make_float2(M2[2].x * ux, M2[2].x * uy);
+    M2[6] = make_float2(M2[2].x * uz, ux * M2[3].y);
+    M2[7] = make_float2(M2[2].y * uz, ux * M2[4].y);
+    M2[8] = make_float2(M2[3].y * uy, M2[3].y * uz);
+    M2[9] = make_float2(uy * M2[4].y, M2[4].y * uz);
+    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int d = 1; d < NMOM; d += 4) {
-        w1 = fmaf(Wd[d], M[d], w1);
-        w2 = fmaf(Wd[d + 1], M[d + 1], w2);
-        w3 = fmaf(Wd[d + 2], M[d + 2], w3);
-        if (d + 3 < NMOM) w0 = fmaf(Wd[d + 3], M[d + 3], w0);
+    for (int q = 0; q < NMOM / 2; q += 2) {
+        s0 = __ffma2_rn(W2[q], M2[q], s0);
+        s1 = __ffma2_rn(W2[q + 1], M2[q + 1], s1);
     }
-    const float dEdr = (w0 + w1) + (w2 + w3);
+    const float dEdr = (s0.x + s0.y) + (s1.x + s1.y);
     // F2 = V M': dE/du_y = sum_d V_d dM_d/du_y (M' formed on the fly)
-    const float xx = M[4], xy = M[5], xz = M[6], yy = M[7], yz = M[8], zz = M[9];
-    const float gx = V[1] + 2.f * ux * V[4] + uy * V[5] + uz * V[6] + 3.f * xx * V[10] +
-                     2.f * xy * V[11] + 2.f * xz * V[12] + yy * V[13] + yz * V[14] + zz * V[15];
-    const float gy = V[2] + ux * V[5] + 2.f * uy * V[7] + uz * V[8] + xx * V[11] + 2.f * xy * V[13] +
-                     xz * V[14] + 3.f * yy * V[16] + 2.f * yz * V[17] + zz * V[18];
-    const float gz = V[3] + ux * V[6] + uy * V[8] + 2.f * uz * V[9] + xx * V[12] + xy * V[14] +
-                     2.f * xz * V[15] + yy * V[17] + 2.f * yz * V[18] + 3.f * zz * V[19];
+    const float xx = M2[2].x, xy = M2[2].y, xz = M2[3].x, yy = M2[3].y, yz = M2[4].x, zz = M2[4].y;
+    auto V = [&](int d) { return (d & 1) ? V2[d >> 1].y : V2[d >> 1].x; };
+    const float gx = V(1) + 2.f * ux * V(4) + uy * V(5) + uz * V(6) + 3.f * xx * V(10) +
+                     2.f * xy * V(11) + 2.f * xz * V(12) + yy * V(13) + yz * V(14) + zz * V(15);
+    const float gy = V(2) + ux * V(5) + 2.f * uy * V(7) + uz * V(8) + xx * V(11) + 2.f * xy * V(13) +
+                     xz * V(14) + 3.f * yy * V(16) + 2.f * yz * V(17) + zz * V(18);
+    const float gz = V(3) + ux * V(6) + uy * V(8) + 2.f * uz * V(9) + xx * V(12) + xy * V(14) +
+                     2.f * xz * V(15) + yy * V(17) + 2.f * yz * V(18) + 3.f * zz * V(19);
     const float ug = ux * gx + uy * gy + uz * gz;
     // g_ij = dE/dD_ij = dE/dr u + (I - u u^T) dE/du / r
     gxs = fmaf(dEdr, ux, (gx - ux * ug) * ir);
@@ -658,13 +681,7 @@ __device__ __forceinline__ void pair_grad(const DevModel &m, const float4 e, con
             }
         }
     }
-    float V[NMOM], Wd[NMOM];
-#pragma unroll
-    for (int d = 0; d < NMOM / 2; ++d) {
-        V[2 * d] = V2[d].x; V[2 * d + 1] = V2[d].y;
-        Wd[2 * d] = W2[d].x; Wd[2 * d + 1] = W2[d].y;
-    }
-    pair_grad_tail(V, Wd, ux, uy, uz, ir, gxs, gys, gzs);
+    pair_grad_tail(V2, W2, ux, uy, uz, ir, gxs, gys, gzs);
 }
 
 
@@ -801,12 +818,9 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_merged(DevModel m, DevNlis
             cb += take_c;
             cr -= take_c;
             if (cr == 0) {   // the current atom is complete: its own force
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    fcx += __shfl_xor_sync(0xffffffffu, fcx, o);
-                    fcy += __shfl_xor_sync(0xffffffffu, fcy, o);
-                    fcz += __shfl_xor_sync(0xffffffffu, fcz, o);
-                }
+                fcx = warp_sum_fixed(fcx);
+                fcy = warp_sum_fixed(fcy);
+                fcz = warp_sum_fixed(fcz);
                 if (lane == 0) {
                     atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fcx);
                     atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fcy);
@@ -1001,17 +1015,17 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_tc(DevModel m, DevNlist nl
                 __syncwarp();
             }
             if (valid) {
-                float V[NMOM], Wd[NMOM];
+                float2 V2[NMOM / 2], W2[NMOM / 2];
                 const float *vr = sT + lane * CS, *wr = sT + (32 + lane) * CS;
 #pragma unroll
                 for (int q4 = 0; q4 < NMOM / 4; ++q4) {
                     const float4 v = *reinterpret_cast<const float4 *>(vr + 4 * q4);
                     const float4 w = *reinterpret_cast<const float4 *>(wr + 4 * q4);
-                    V[4 * q4] = v.x; V[4 * q4 + 1] = v.y; V[4 * q4 + 2] = v.z; V[4 * q4 + 3] = v.w;
-                    Wd[4 * q4] = w.x; Wd[4 * q4 + 1] = w.y; Wd[4 * q4 + 2] = w.z; Wd[4 * q4 + 3] = w.w;
+                    V2[2 * q4] = make_float2(v.x, v.y); V2[2 * q4 + 1] = make_float2(v.z, v.w);
+                    W2[2 * q4] = make_float2(w.x, w.y); W2[2 * q4 + 1] = make_float2(w.z, w.w);
                 }
                 float gxs, gys, gzs;
-                pair_grad_tail(V, Wd, e.x * ir, e.y * ir, e.z * ir, ir, gxs, gys, gzs);
+                pair_grad_tail(V2, W2, e.x * ir, e.y * ir, e.z * ir, ir, gxs, gys, gzs);
                 const int j = (int)(__float_as_uint(e.w) & 0x0FFFFFFFu);
                 // ScatterSum in 2^-32 fixed point (exact, order independent)
                 const long long qx = to_fixed(gxs);
@@ -1030,12 +1044,9 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force_tc(DevModel m, DevNlist nl
             }
             __syncwarp();   // the tile is rewritten by the next batch
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        }
+        fx = warp_sum_fixed(fx);
+        fy = warp_sum_fixed(fy);
+        fz = warp_sum_fixed(fz);
         if (lane == 0) {
             atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fx);
             atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fy);
@@ -1155,12 +1166,9 @@ __global__ void __launch_bounds__(PW * 32, 4) k_force(DevModel m, DevNlist nl, c
             cached_pairs(nl, a, nl.npair[a], lane, pair_fn);
         else
             for_pairs(nl, a, nl.beg[a], nl.end[a], m.rc2h, m.rc2l, s_q[warp], s_q2[warp], lane, pair_fn);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        }
+        fx = warp_sum_fixed(fx);
+        fy = warp_sum_fixed(fy);
+        fz = warp_sum_fixed(fz);
         if (lane == 0) {
             atomicAdd(&Fq[3 * (int64_t)a], (unsigned long long)fx);
             atomicAdd(&Fq[3 * (int64_t)a + 1], (unsigned long long)fy);
