@@ -529,18 +529,17 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
 #pragma unroll
                 for (int dd = 0; dd < 5; ++dd) sq[dd] = Tg[dd] * acc[s][kk][dd] * acc[s][kk][dd];
                 const float tot = sq[0] + sq[1] + sq[2] + sq[3] + sq[4];
-                float p0 = (g == 0) ? sq[0] : 0.f;
-                float p1 = (g == 0) ? sq[1] + sq[2] + sq[3] : 0.f;
-                float p2 = (g == 0) ? sq[4] : ((g == 1) ? tot : 0.f);
-                float p3 = (g >= 2) ? tot : 0.f;
-#pragma unroll
-                for (int o = 1; o <= 2; o <<= 1) {
-                    p0 += __shfl_xor_sync(0xffffffffu, p0, o);
-                    p1 += __shfl_xor_sync(0xffffffffu, p1, o);
-                    p2 += __shfl_xor_sync(0xffffffffu, p2, o);
-                    p3 += __shfl_xor_sync(0xffffffffu, p3, o);
-                }
-                const float val = (g == 0) ? sqrtf(p0) : ((g == 1) ? p1 : ((g == 2) ? p2 : p3));
+                // rank m of the four lanes g = 0..3 of this k: lane 0 holds
+                // d = 0 (m = 0), d = 1..3 (m = 1) and d = 4 (m = 2); lane 1
+                // d = 5..9 (m = 2); lanes 2 and 3 d = 10..19 (m = 3).  Lane g
+                // writes G for m = g: m = 2 and m = 3 are pair sums (xor 1),
+                // and lanes 1 and 2 fetch theirs from lane 0.
+                const float s123 = sq[1] + sq[2] + sq[3];
+                const float a = (g == 0) ? sq[4] : tot;
+                const float asum = a + __shfl_xor_sync(0xffffffffu, a, 1);    // lanes 0, 1: m = 2; lanes 2, 3: m = 3
+                const float m1 = __shfl_xor_sync(0xffffffffu, s123, 1);      // lane 1: lane 0's d = 1..3
+                const float m2 = __shfl_xor_sync(0xffffffffu, asum, 2);      // lane 2: lane 0's m = 2
+                const float val = (g == 0) ? sqrtf(sq[0]) : ((g == 1) ? m1 : ((g == 2) ? m2 : asum));
                 G[(size_t)p * Dd + (s * K + k0 + kg * KPL + kk) * 4 + g] = val;
             }
         }
