@@ -40,7 +40,7 @@ struct DevModel {
     int off_f[MAX_LAYERS];              // offset of layer l in wf[s] / hf[s]
     int off_b[MAX_LAYERS];              // offset of layer l in wb[s] / hb[s]
     // tile shapes (host-side launch choices; 0 = built-in default)
-    int tile_rows;                      // atoms per FP32 network tile: 32 or 64
+    int tile_rows;                      // atoms per FP32 network tile: 32 or 64 (streamed weights), 128 (resident)
     int pair_bps;                       // blocks per SM of the persistent pair-kernel grid
     // tabulated radial basis (nullptr = direct evaluation): per species pair
     // p = t_i S + t_j, rtab_n grid intervals [g, g + 1) / rtab_scale, each
