@@ -61,7 +61,7 @@ enum { TMD_NET_AUTO = 0, TMD_NET_TCGEN05 = 1, TMD_NET_MMA_SYNC = 2 };
 enum { TMD_FORCE_AUTO = 0, TMD_FORCE_SIMT = 1, TMD_FORCE_TENSOR = 2 };
 
 /* Limits of the library. */
-#define TMD_MAX_SPECIES 4
+#define TMD_MAX_SPECIES 5
 #define TMD_MAX_HIDDEN 4
 #define TMD_MAX_WIDTH 256
 #define TMD_MAX_DEGREE 1024 /* neighbour entries per atom inside r_list */
@@ -80,7 +80,8 @@ const char *tmd_version(void);
  * Description of a TensorMD potential (all pointers host, read at create).
  *  n_species  S, 1..TMD_MAX_SPECIES.  Species ids are 0..S-1.
  *  n_radial   K radial channels; the library supports K in {8, 16, 32, 64,
- *             128} with at most 4, 4, 3, 2, 1 species respectively.
+ *             128} with at most 5, 5, 3, 2, 1 species respectively (the
+ *             paper's pair-type index b runs over 1..5).
  *  rc         cutoff radius (A); pairs with R >= rc contribute nothing.
  *  mu, eta    [S][S][K] Gaussian centre and width of f_k(R) = exp(-eta (R-mu)^2)
  *             for (centre species, neighbour species, k).  f_c(R) =

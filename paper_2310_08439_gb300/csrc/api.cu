@@ -423,7 +423,7 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
         return TMD_ERR_UNIMPLEMENTED;
     }
     // species counts with kernel instances (the network input S K 4 <= 512)
-    const int s_max = K <= 16 ? 4 : (K == 32 ? 3 : (K == 64 ? 2 : 1));
+    const int s_max = K <= 16 ? 5 : (K == 32 ? 3 : (K == 64 ? 2 : 1));
     if (S > s_max) { set_error("n_radial %d supports at most %d species", K, s_max); return TMD_ERR_UNIMPLEMENTED; }
     if (!(std::isfinite(d->rc) && d->rc > 0.0)) { set_error("rc must be finite and > 0"); return TMD_ERR_INVALID_ARG; }
     if (L < 1 || L > TMD_MAX_HIDDEN) { set_error("n_hidden %d outside [1, %d]", L, TMD_MAX_HIDDEN); return TMD_ERR_INVALID_ARG; }
@@ -1774,7 +1774,7 @@ tmd_status tmd_batch_set_system(tmd_batch *b, int32_t sys, const double *pos, co
         if (!(masses[i] > 0.0 && std::isfinite(masses[i]))) { set_error("mass[%lld] must be > 0", (long long)i); return TMD_ERR_INVALID_ARG; }
     // per-species counts and each atom's rank among its species (evaluation order)
     std::vector<int32_t> rank((size_t)n);
-    int64_t cnt[TMD_MAX_SPECIES] = {0, 0, 0, 0};
+    int64_t cnt[TMD_MAX_SPECIES] = {};
     for (int64_t i = 0; i < n; ++i) {
         if (types[i] < 0 || types[i] >= TMD_MAX_SPECIES) {
             set_error("types[%lld] = %d outside [0, %d)", (long long)i, types[i], TMD_MAX_SPECIES);

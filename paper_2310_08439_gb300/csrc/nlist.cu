@@ -77,60 +77,73 @@ __global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict_
     if (threadIdx.x < TMD_MAX_SPECIES) type_block[blockIdx.x * TMD_MAX_SPECIES + threadIdx.x] = s_cnt[threadIdx.x];
 }
 
-// exclusive scan of the per-block species counts (one warp per species);
-// writes the species start offsets type_start[0..MAX_SPECIES].
+// exclusive scan of the per-block species counts; writes the species start
+// offsets type_start[0..MAX_SPECIES].
 __global__ void __launch_bounds__(128) k_type_scan(int32_t *__restrict__ type_block, int nblocks,
                                                   int32_t *__restrict__ type_start) {
     // exclusive scan over the binning blocks, every species at once: thread t
     // owns a contiguous run of blocks (sums it, block-wide scan of the run
     // totals, then writes its run's offsets)
-    static_assert(TMD_MAX_SPECIES == 4, "one int4 per block");
-    __shared__ int4 s_tot[128];
+    constexpr int NS = TMD_MAX_SPECIES;
+    __shared__ int32_t s_tot[128][NS];
     const int t = threadIdx.x;
     const int per = (nblocks + 127) / 128;
     const int b0 = min(nblocks, t * per), b1 = min(nblocks, b0 + per);
-    int4 *tb = reinterpret_cast<int4 *>(type_block);
-    int4 sum = make_int4(0, 0, 0, 0);
-    for (int b = b0; b < b1; ++b) {
-        const int4 v = tb[b];
-        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
-    }
-    s_tot[t] = sum;
+    int sum[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sum[s] = 0;
+    for (int b = b0; b < b1; ++b)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) sum[s] += type_block[(size_t)b * NS + s];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_tot[t][s] = sum[s];
     __syncthreads();
     if (t < 32) {   // scan of the 128 run totals: 4 per lane, then across lanes
-        int4 r[4], acc = make_int4(0, 0, 0, 0);
+        int r[4][NS], acc[NS];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            r[q] = acc;
-            const int4 v = s_tot[4 * t + q];
-            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-        }
-        int4 x = acc;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int yx = __shfl_up_sync(0xffffffffu, x.x, d), yy = __shfl_up_sync(0xffffffffu, x.y, d);
-            const int yz = __shfl_up_sync(0xffffffffu, x.z, d), yw = __shfl_up_sync(0xffffffffu, x.w, d);
-            if (t >= d) { x.x += yx; x.y += yy; x.z += yz; x.w += yw; }
-        }
-        const int4 ex = make_int4(x.x - acc.x, x.y - acc.y, x.z - acc.z, x.w - acc.w);
+        for (int s = 0; s < NS; ++s) acc[s] = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            s_tot[4 * t + q] = make_int4(ex.x + r[q].x, ex.y + r[q].y, ex.z + r[q].z, ex.w + r[q].w);
-        if (t == 31) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                r[q][s] = acc[s];
+                acc[s] += s_tot[4 * t + q][s];
+            }
+        int x[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) x[s] = acc[s];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int y = __shfl_up_sync(0xffffffffu, x[s], d);
+                if (t >= d) x[s] += y;
+            }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) s_tot[4 * t + q][s] = (x[s] - acc[s]) + r[q][s];
+        if (t == 31) {   // x = the species totals
+            int run = 0;
             type_start[0] = 0;
-            type_start[1] = x.x;
-            type_start[2] = x.x + x.y;
-            type_start[3] = x.x + x.y + x.z;
-            type_start[4] = x.x + x.y + x.z + x.w;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                run += x[s];
+                type_start[s + 1] = run;
+            }
         }
     }
     __syncthreads();
-    int4 run = s_tot[t];
-    for (int b = b0; b < b1; ++b) {
-        const int4 v = tb[b];
-        tb[b] = run;
-        run.x += v.x; run.y += v.y; run.z += v.z; run.w += v.w;
-    }
+    int run[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) run[s] = s_tot[t][s];
+    for (int b = b0; b < b1; ++b)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int v = type_block[(size_t)b * NS + s];
+            type_block[(size_t)b * NS + s] = run[s];
+            run[s] += v;
+        }
 }
 
 // scatter atom ids into cells (order within a cell fixed by k_cell_sort) and

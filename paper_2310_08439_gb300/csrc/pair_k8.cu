@@ -10,6 +10,7 @@ TMD_PAIR_LAUNCHER(launch_pair_k8) {
     case 2: return launch_pair_kernels<8, 2>(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
     case 3: return launch_pair_kernels<8, 3>(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
     case 4: return launch_pair_kernels<8, 4>(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
+    case 5: return launch_pair_kernels<8, 5>(dm, dn, pos, types, nl, part_w, nblk, s, fwd, w_atom);
     default: break;
     }
     set_error("no kernel for K=%d S=%d", dm.K, dm.S);

@@ -146,7 +146,7 @@ struct tmd_nlist {
     int64_t nnz = 0;
     int64_t n_active = 0;   // atoms binned and listed by the last build
     int built = 0;
-    int32_t type_count[TMD_MAX_SPECIES] = {0, 0, 0, 0};
+    int32_t type_count[TMD_MAX_SPECIES] = {};
 
     // device arrays (capacities in elements)
     int32_t *cell_of = nullptr;      int64_t cap_atoms = 0;
