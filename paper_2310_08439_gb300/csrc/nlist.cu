@@ -29,6 +29,10 @@ namespace {
 
 constexpr int BIN_THREADS = 256;
 constexpr int NBR_WARPS = 4;
+// per-block species counts: rows of TB_STRIDE ints (the species, then
+// padding), two aligned int4 per row
+constexpr int TB_STRIDE = 8;
+static_assert(TMD_MAX_SPECIES <= TB_STRIDE, "species counts fit a row");
 
 // cell index of each atom of an active system (global cell = the system's
 // first cell + local cell), cell occupancy counts (stored at start[c+1]), per
@@ -74,7 +78,7 @@ __global__ void k_bin(const double *__restrict__ pos, const int32_t *__restrict_
         if (lane == 0 && m) atomicAdd(&s_cnt[s], __popc(m));
     }
     __syncthreads();
-    if (threadIdx.x < TMD_MAX_SPECIES) type_block[blockIdx.x * TMD_MAX_SPECIES + threadIdx.x] = s_cnt[threadIdx.x];
+    if (threadIdx.x < TMD_MAX_SPECIES) type_block[blockIdx.x * TB_STRIDE + threadIdx.x] = s_cnt[threadIdx.x];
 }
 
 // exclusive scan of the per-block species counts; writes the species start
@@ -89,12 +93,16 @@ __global__ void __launch_bounds__(128) k_type_scan(int32_t *__restrict__ type_bl
     const int t = threadIdx.x;
     const int per = (nblocks + 127) / 128;
     const int b0 = min(nblocks, t * per), b1 = min(nblocks, b0 + per);
+    int4 *rows = reinterpret_cast<int4 *>(type_block);   // two int4 per block
     int sum[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) sum[s] = 0;
-    for (int b = b0; b < b1; ++b)
+    for (int b = b0; b < b1; ++b) {
+        const int4 lo = rows[2 * (size_t)b], hi = rows[2 * (size_t)b + 1];
+        const int v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-        for (int s = 0; s < NS; ++s) sum[s] += type_block[(size_t)b * NS + s];
+        for (int s = 0; s < NS; ++s) sum[s] += v[s];
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s) s_tot[t][s] = sum[s];
     __syncthreads();
@@ -134,16 +142,17 @@ __global__ void __launch_bounds__(128) k_type_scan(int32_t *__restrict__ type_bl
         }
     }
     __syncthreads();
-    int run[NS];
+    int run[TB_STRIDE];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) run[s] = s_tot[t][s];
-    for (int b = b0; b < b1; ++b)
+    for (int s = 0; s < TB_STRIDE; ++s) run[s] = s < NS ? s_tot[t][s] : 0;
+    for (int b = b0; b < b1; ++b) {
+        const int4 lo = rows[2 * (size_t)b], hi = rows[2 * (size_t)b + 1];
+        const int v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        rows[2 * (size_t)b] = make_int4(run[0], run[1], run[2], run[3]);
+        rows[2 * (size_t)b + 1] = make_int4(run[4], run[5], run[6], run[7]);
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int v = type_block[(size_t)b * NS + s];
-            type_block[(size_t)b * NS + s] = run[s];
-            run[s] += v;
-        }
+        for (int s = 0; s < NS; ++s) run[s] += v[s];
+    }
 }
 
 // scatter atom ids into cells (order within a cell fixed by k_cell_sort) and
@@ -176,7 +185,7 @@ __global__ void k_fill(const double *__restrict__ pos, const int32_t *__restrict
         int before = 0;
         for (int w = 0; w < warp; ++w) before += s_warp[w][t];
         before += __popc(masks[t] & ((1u << lane) - 1u));
-        perm[type_start[t] + type_block[blockIdx.x * TMD_MAX_SPECIES + t] + before] = (int32_t)i;
+        perm[type_start[t] + type_block[blockIdx.x * TB_STRIDE + t] + before] = (int32_t)i;
     }
 }
 
@@ -860,7 +869,7 @@ tmd_status build_tables(const double *pos, const int32_t *types, int64_t n, int 
     if ((st = grow(&nl->end, &nl->cap_end, n)) != TMD_OK) return st;
     if ((st = grow(&nl->cell_start, &nl->cap_cells, ncell_total + 1)) != TMD_OK) return st;
     if ((st = grow(&nl->cell_fill, &nl->cap_cell_fill, ncell_total)) != TMD_OK) return st;
-    if ((st = grow(&nl->type_block, &nl->cap_type_blocks, (nb_bin + 1) * TMD_MAX_SPECIES)) != TMD_OK) return st;
+    if ((st = grow(&nl->type_block, &nl->cap_type_blocks, (nb_bin + 1) * TB_STRIDE)) != TMD_OK) return st;
     if ((st = grow(&nl->status, &nl->cap_status, 4)) != TMD_OK) return st;
     if ((st = grow(&nl->type_start, &nl->cap_type_start, TMD_MAX_SPECIES + 1)) != TMD_OK) return st;
     if ((st = grow(&nl->counter, &nl->cap_counter, 1)) != TMD_OK) return st;

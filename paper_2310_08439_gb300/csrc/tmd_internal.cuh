@@ -161,7 +161,7 @@ struct tmd_nlist {
     int32_t *nbr = nullptr;          int64_t cap_nnz = 0;
     char4 *shift = nullptr;          int64_t cap_shift = 0;
     int32_t *status = nullptr;       int64_t cap_status = 0;       // [1] device status bits
-    int32_t *type_block = nullptr;   int64_t cap_type_blocks = 0;  // [blocks][MAX_SPECIES]
+    int32_t *type_block = nullptr;   int64_t cap_type_blocks = 0;  // [blocks][8]: species counts, padded
     int32_t *type_start = nullptr;   int64_t cap_type_start = 0;   // [MAX_SPECIES + 1]
     tmd::SysParams *sp = nullptr;    int64_t cap_sp = 0;           // per-system parameters (device)
     int32_t *cell_sys = nullptr;     int64_t cap_cell_sys = 0;     // [ncell] system of each cell (batched)
