@@ -306,12 +306,14 @@ def test_large_full_size_sampled(tmdlib):
     g = gpu_eval(tmdlib, w.model, s, r_list=7.0)
     om = O.OracleModel(w.model)
     rng = np.random.default_rng(1)
-    atoms = rng.choice(s.n, size=8, replace=False)
+    atoms = rng.choice(s.n, size=32, replace=False)
     ea, fa = O.sampled(om, s.pos, s.types, s.box, s.pbc, atoms)
     rms = np.sqrt((g["forces"] ** 2).mean())
     assert np.abs(g["forces"][atoms] - fa).max() <= F_TOL * rms
     assert np.abs(g["e_atom"][atoms] - ea).max() <= EA_TOL * np.abs(ea).max()
     assert abs(g["energy"] - g["e_atom"].sum()) <= 1e-6 * abs(g["energy"])
+    # the int64 scatter sums to zero exactly; what is left is the FP32
+    # rounding of each reported force (~sqrt(N) ulp(|F|) ~ 4e-5 RMS here)
     assert np.abs(g["forces"].sum(axis=0)).max() <= 1e-2 * rms
 
 
