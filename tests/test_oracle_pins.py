@@ -633,3 +633,29 @@ def test_velocity_verlet_reversible_and_conserving():
     d -= np.rint(d / s.box) * s.box
     assert np.abs(d).max() < 1e-9
     assert np.allclose(-vel, s.vel, atol=1e-10)
+
+
+def test_five_species_pins():
+    """Five species (the paper's pair-type index b = 1..5): the descriptor
+    equals the angular double sum column by column for every pair type, the
+    forces are the negative energy gradient, and relabelling atoms of equal
+    species leaves E_a and F permuted alike."""
+    p, om = _small_model(S=5, K=4, rc=4.5, widths=(10, 8), seed=7)
+    c = I.cluster(20, 3.8, seed=8, n_species=5)
+    assert set(c.types.tolist()) == {0, 1, 2, 3, 4}
+    out = O.evaluate(om, c.pos, c.types, c.box, c.pbc, want_G=True)
+    assert out["G"].shape == (c.n, 5 * 4 * 4)
+    for a in range(c.n):
+        ref = _double_sum_G(p, om, c.pos, c.types, c.box, c.pbc, a)
+        assert np.allclose(out["G"][a], ref, rtol=1e-12, atol=1e-14)
+    F = out["forces"]
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        i, x = int(rng.integers(c.n)), int(rng.integers(3))
+        fd = _fd_force(om, c.pos, c.types, c.box, c.pbc, i, x)
+        assert abs(fd - F[i, x]) <= 1e-7 * max(1.0, abs(F[i, x])) + 1e-8
+    perm = rng.permutation(c.n)
+    out2 = O.evaluate(om, c.pos[perm], c.types[perm], c.box, c.pbc)
+    assert abs(out2["energy"] - out["energy"]) < 1e-12 * abs(out["energy"])
+    assert np.allclose(out2["e_atom"], out["e_atom"][perm], atol=1e-12)
+    assert np.allclose(out2["forces"], F[perm], atol=1e-11)
