@@ -80,7 +80,7 @@ const char *tmd_version(void);
  * Description of a TensorMD potential (all pointers host, read at create).
  *  n_species  S, 1..TMD_MAX_SPECIES.  Species ids are 0..S-1.
  *  n_radial   K radial channels; the library supports K in {8, 16, 32, 64,
- *             128} with at most 5, 5, 3, 2, 1 species respectively (the
+ *             128} with at most 5, 5, 5, 2, 1 species respectively (the
  *             paper's pair-type index b runs over 1..5).
  *  rc         cutoff radius (A); pairs with R >= rc contribute nothing.
  *  mu, eta    [S][S][K] Gaussian centre and width of f_k(R) = exp(-eta (R-mu)^2)

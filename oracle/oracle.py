@@ -109,8 +109,8 @@ class OracleModel:
         self._mu = np.ascontiguousarray(params.mu, dtype=np.float64).reshape(S * S * K)
         self._eta = np.ascontiguousarray(params.eta, dtype=np.float64).reshape(S * S * K)
         self._widths = np.ascontiguousarray(params.widths, dtype=np.int32)
-        if max([params.n_desc] + list(params.widths)) > 520 or K > 256 or len(params.widths) > 7:
-            raise ValueError("oracle limits: widths <= 520, K <= 256, <= 7 hidden layers")
+        if max([params.n_desc] + list(params.widths)) > 656 or K > 256 or len(params.widths) > 7:
+            raise ValueError("oracle limits: widths <= 656, K <= 256, <= 7 hidden layers")
         self._w = [np.ascontiguousarray(w, dtype=np.float64) for w in params.weights]
         self._wptr = (C.POINTER(C.c_double) * S)(*[_dp(w) for w in self._w])
         act = {"tanh": 0, "squareplus": 1}[params.activation]

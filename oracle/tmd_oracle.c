@@ -287,7 +287,7 @@ static double act_df(const tmdo_model *m, double z) {
     return 0.5 * (1.0 + z / sqrt(z * z + m->sp_b));
 }
 
-#define MAXW 520
+#define MAXW 656
 
 static double nnp(const tmdo_model *m, int s, const double *G, double *dEdG) {
     const int D = m->S * m->K * MMAX;

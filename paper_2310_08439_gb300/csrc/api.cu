@@ -422,8 +422,8 @@ tmd_status tmd_model_create(const tmd_model_desc *d, tmd_model **out) {
         set_error("n_radial %d: the library supports 8, 16, 32, 64, 128", K);
         return TMD_ERR_UNIMPLEMENTED;
     }
-    // species counts with kernel instances (the network input S K 4 <= 512)
-    const int s_max = K <= 16 ? 5 : (K == 32 ? 3 : (K == 64 ? 2 : 1));
+    // species counts with kernel instances (network inputs S K 4 up to 640)
+    const int s_max = K <= 32 ? 5 : (K == 64 ? 2 : 1);
     if (S > s_max) { set_error("n_radial %d supports at most %d species", K, s_max); return TMD_ERR_UNIMPLEMENTED; }
     if (!(std::isfinite(d->rc) && d->rc > 0.0)) { set_error("rc must be finite and > 0"); return TMD_ERR_INVALID_ARG; }
     if (L < 1 || L > TMD_MAX_HIDDEN) { set_error("n_hidden %d outside [1, %d]", L, TMD_MAX_HIDDEN); return TMD_ERR_INVALID_ARG; }

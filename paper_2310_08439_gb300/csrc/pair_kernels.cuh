@@ -539,7 +539,10 @@ __global__ void __launch_bounds__(PW * 32) k_desc(DevModel m, DevNlist nl, const
                 const float asum = a + __shfl_xor_sync(0xffffffffu, a, 1);    // lanes 0, 1: m = 2; lanes 2, 3: m = 3
                 const float m1 = __shfl_xor_sync(0xffffffffu, s123, 1);      // lane 1: lane 0's d = 1..3
                 const float m2 = __shfl_xor_sync(0xffffffffu, asum, 2);      // lane 2: lane 0's m = 2
-                const float val = (g == 0) ? sqrtf(sq[0]) : ((g == 1) ? m1 : ((g == 2) ? m2 : asum));
+                // m = 0: sqrt(T_0 P^2) = |P| (T_0 = 1), taken as |P| so that a
+                // channel's tiny P (|P| < 1e-19, whose square underflows in
+                // FP32) is not read as 0; elsewhere bitwise the same value
+                const float val = (g == 0) ? fabsf(acc[s][kk][0]) : ((g == 1) ? m1 : ((g == 2) ? m2 : asum));
                 G[(size_t)p * Dd + (s * K + k0 + kg * KPL + kk) * 4 + g] = val;
             }
         }

