@@ -45,6 +45,21 @@ def test_model_create_rejects_bad_descriptors(L):
     d.rc = 6.0
     d.n_hidden = 9
     assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_INVALID_ARG
+    # species: at most five (the pair-type index b = 1..5); K = 64 and 128
+    # take at most 2 and 1 (descriptor length S K 4 up to 640); these are
+    # decided before the hidden-layer count is read
+    d.n_hidden = 9
+    d.n_radial, d.n_species = 16, 6
+    assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_INVALID_ARG
+    assert b"n_species" in L.tmd_last_error()
+    for K, S in [(64, 3), (128, 2)]:
+        d.n_radial, d.n_species = K, S
+        assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_UNIMPLEMENTED
+        assert b"species" in L.tmd_last_error()
+    for K, S in [(32, 5), (64, 2), (128, 1)]:
+        d.n_radial, d.n_species = K, S   # accepted shapes: the next check (n_hidden 9) decides
+        assert L.tmd_model_create(C.byref(d), C.byref(h)) == tmd.ERR_INVALID_ARG
+        assert b"n_hidden" in L.tmd_last_error()
 
 
 def test_neighbors_and_system_reject_bad_host_args(L):
