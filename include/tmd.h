@@ -32,6 +32,11 @@
  *    the device can see (an atom outside the box, a neighbour count above the
  *    list capacity) are recorded in a device status word and returned by the
  *    next call that synchronises (tmd_neighbors, tmd_nlist_*, tmd_step).
+ *  - Host threads: calls from several threads must be serialised by the
+ *    caller.  The library's one-time set-up (kernel shared-memory limits,
+ *    occupancy queries) and its process-wide switches (tmd_set_graphs,
+ *    tmd_set_network_kernel, tmd_set_force_kernel, profiling) are plain
+ *    process state without locks; only the error string above is per thread.
  */
 #ifndef TMD_H
 #define TMD_H
