@@ -43,6 +43,15 @@ TARGETED = {
                                ("const double dfk = -2.0 * eta * (r - mu) * fk;",
                                 "const double dfk = -eta * (r - mu) * fk;", 1)],
                               "test_radial_gaussian_width_away_from_centre"),
+    # pair type b taken from the centre atom instead of the neighbour, in the
+    # forward and backward passes alike (still a smooth, invariant potential
+    # whose forces are its gradient: only the column placement can tell)
+    "pair_type_is_centre_species": ([("const int b = types[j];", "const int b = ti;", 2)],
+                                    "test_descriptor_equals_double_sum"),
+    # pair types beyond the third folded onto the first ones (a three-species
+    # limit left in the indexing): seen only with four or more species
+    "pair_type_wraps_at_three": ([("const int b = types[j];", "const int b = types[j] % 3;", 2)],
+                                 "test_five_species_pins"),
 }
 
 
