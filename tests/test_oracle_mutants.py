@@ -52,6 +52,10 @@ TARGETED = {
     # limit left in the indexing): seen only with four or more species
     "pair_type_wraps_at_three": ([("const int b = types[j];", "const int b = types[j] % 3;", 2)],
                                  "test_five_species_pins"),
+    # every weight matrix read as [in][out] instead of [out][in], forward and
+    # backward alike (again a consistent potential)
+    "weights_read_transposed": ([("W[l][(size_t)o * dims[l] + c]", "W[l][(size_t)c * dims[l + 1] + o]", 2)],
+                                "test_network_bias_only_and_single_unit"),
 }
 
 
