@@ -52,6 +52,10 @@ TARGETED = {
     # limit left in the indexing): seen only with four or more species
     "pair_type_wraps_at_three": ([("const int b = types[j];", "const int b = types[j] % 3;", 2)],
                                  "test_five_species_pins"),
+    # Gaussian centres and widths of pair (neighbour, centre) instead of
+    # (centre, neighbour): invisible while the parameters are symmetric
+    "radial_params_pair_transposed": ([("((size_t)ti * m->S + tj) * K + k]", "((size_t)tj * m->S + ti) * K + k]", 2)],
+                                      "test_radial_parameters_follow_centre_then_neighbour"),
     # every weight matrix read as [in][out] instead of [out][in], forward and
     # backward alike (again a consistent potential)
     "weights_read_transposed": ([("W[l][(size_t)o * dims[l] + c]", "W[l][(size_t)c * dims[l + 1] + o]", 2)],

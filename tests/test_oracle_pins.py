@@ -92,6 +92,26 @@ def test_radial_special_values_and_derivative():
         assert np.allclose(dH, (hp - hm) / 2e-6, atol=1e-8)
 
 
+def test_radial_parameters_follow_centre_then_neighbour():
+    """The radial parameters of a pair are those of (centre species, neighbour
+    species) (the H_abck subscripts: centre atom a, pair type b).  Two atoms of
+    species 0 and 1 at r = rc/2, where f_c = 1/2: channel 0 of pair (0, 1) is
+    centred on r and channel 0 of pair (1, 0) one width away, so the rank-0
+    descriptor of atom 0 reads 1/2 and that of atom 1 reads e^-1/2 in the
+    column of the other species, and both read 0 in their own species' one."""
+    p, _ = _small_model(S=2, K=4, rc=5.0, widths=(4,))
+    r = 2.5
+    p.mu[0, 1, 0], p.eta[0, 1, 0] = r, 1.0
+    p.mu[1, 0, 0], p.eta[1, 0, 0] = r + 1.0, 1.0
+    om = O.OracleModel(p)
+    pos = np.array([[10.0, 10.0, 10.0], [10.0, 10.0 + r, 10.0]])
+    G = O.evaluate(om, pos, np.array([0, 1], np.int32), np.full(3, 40.0), np.zeros(3, np.int32),
+                   want_G=True)["G"].reshape(2, 2, 4, 4)   # [atom][b][k][m]
+    assert abs(G[0, 1, 0, 0] - 0.5) < 1e-15
+    assert abs(G[1, 0, 0, 0] - 0.5 * math.exp(-1.0)) < 1e-15
+    assert np.all(G[0, 0] == 0.0) and np.all(G[1, 1] == 0.0)
+
+
 def test_radial_gaussian_width_away_from_centre():
     """The width of f_k = exp(-eta (r - mu)^2) (reading c2), checked away from
     the centres, where H = 1 at mu cannot see it:
