@@ -56,6 +56,10 @@ TARGETED = {
     # (centre, neighbour): invisible while the parameters are symmetric
     "radial_params_pair_transposed": ([("((size_t)ti * m->S + tj) * K + k]", "((size_t)tj * m->S + ti) * K + k]", 2)],
                                       "test_radial_parameters_follow_centre_then_neighbour"),
+    # the network of species 0 evaluated for every atom (invisible with one
+    # species, and still a consistent potential with several)
+    "network_of_species_zero": ([("const double *p = m->w[s];", "const double *p = m->w[0];", 1)],
+                                "test_centre_species_selects_its_network"),
     # every weight matrix read as [in][out] instead of [out][in], forward and
     # backward alike (again a consistent potential)
     "weights_read_transposed": ([("W[l][(size_t)o * dims[l] + c]", "W[l][(size_t)c * dims[l + 1] + o]", 2)],

@@ -440,6 +440,27 @@ def test_network_bias_only_and_single_unit():
     assert np.allclose(out["e_atom"], ref, rtol=1e-14, atol=1e-15)
 
 
+def test_centre_species_selects_its_network():
+    """E_a = NNP_{species of a}(G_a): with every weight zero but the output
+    biases (-1 for species 0, -3 for species 1), each atom's energy is the
+    bias of its own species' network; then a one-unit first layer in species
+    1 alone changes the energies of species-1 atoms only."""
+    p, _ = _small_model(S=2, K=4, rc=4.5, widths=(3,))
+    for s, b in enumerate((-1.0, -3.0)):
+        p.weights[s][:] = 0.0
+        p.weights[s][-1] = b
+    c = I.cluster(12, 3.2, seed=6, n_species=2)
+    assert set(c.types.tolist()) == {0, 1}
+    out = O.evaluate(O.OracleModel(p), c.pos, c.types, c.box, c.pbc, want_G=True)
+    assert np.array_equal(out["e_atom"], np.where(c.types == 0, -1.0, -3.0))
+    Dd = p.n_desc
+    p.weights[1][0 * Dd + 1] = 0.9        # W1[0, column 1] of species 1
+    p.weights[1][3 * Dd + 3 + 0] = 2.0    # W2[0, 0] of species 1
+    out = O.evaluate(O.OracleModel(p), c.pos, c.types, c.box, c.pbc, want_G=True)
+    want = np.where(c.types == 0, -1.0, 2.0 * np.tanh(0.9 * out["G"][:, 1]) - 3.0)
+    assert np.allclose(out["e_atom"], want, rtol=1e-14, atol=1e-15)
+
+
 def test_squareplus_special_values_and_slope():
     """SquarePlus (Barron's smooth ReLU, the activation of the paper's
     potentials in Sec. "Evaluation") through a one-unit network whose hidden
